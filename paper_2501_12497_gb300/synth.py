@@ -1,0 +1,239 @@
+"""Seeded synthetic workloads: moving disk/ellipse phantoms, their exact
+parallel-beam sinograms, and Gaussian noise.
+
+This module holds none of the reconstruction method's arithmetic. It only
+makes inputs: the phantoms are drawn from seeded random numbers, and the data
+are the analytic Radon transform of the ellipses (chord length times
+intensity), so the data are not produced by the discrete projector that the
+method uses. Both the CUDA path and the oracle are fed from here.
+
+Geometry convention shared by every workload: pixel centres
+x_i = (i - (nx-1)/2) h, bin centres sigma_k = (k - (nb-1)/2) db, the ray of
+angle theta and bin k is {x cos(theta) + y sin(theta) = sigma_k}; the angles
+of frame t are theta_{t,a} = (a*180/na + t*180/(na*nt)) degrees, i.e. each
+frame's fan of na equispaced angles is shifted by 180/(na*nt) degrees from the
+previous frame's (the "shifted intervals" scheme of Sec. 5.1.1).
+"""
+from dataclasses import dataclass, field
+import math
+
+import numpy as np
+
+
+@dataclass
+class Ellipse:
+    cx: float
+    cy: float
+    a: float        # semi-axis along the ellipse's own x axis
+    b: float        # semi-axis along its own y axis
+    phi: float      # orientation, radians
+    rho: float      # intensity (added where ellipses overlap)
+    vx: float = 0.0  # translation per frame (pixels)
+    vy: float = 0.0
+    omega: float = 0.0  # rotation per frame (radians)
+
+    def at(self, t):
+        """The ellipse at frame t (rigid motion: translate, rotate about its centre)."""
+        return (self.cx + t * self.vx, self.cy + t * self.vy, self.a, self.b,
+                self.phi + t * self.omega, self.rho)
+
+
+@dataclass
+class Workload:
+    name: str
+    nx: int
+    ny: int
+    nt: int
+    nb: int
+    na: np.ndarray          # angles per frame, int32 (nt,)
+    angles: np.ndarray      # radians, float64 (sum na,)
+    h: float
+    db: float
+    u_true: np.ndarray      # (nt, ny, nx) float64, area-averaged phantom
+    b_clean: np.ndarray     # (m,) exact line integrals
+    b: np.ndarray           # (m,) noisy data
+    noise_norm: float       # delta = ||b - b_clean||
+    ellipses: list = field(default_factory=list)
+
+    @property
+    def m(self):
+        return int(self.na.sum()) * self.nb
+
+    @property
+    def n(self):
+        return self.nx * self.ny * self.nt
+
+
+def shifted_angles(nt, na):
+    """Angles (radians) of every frame, concatenated: a*180/na + t*180/(na*nt) degrees."""
+    na_arr = np.full(nt, na, dtype=np.int32) if np.isscalar(na) else np.asarray(na, np.int32)
+    out = []
+    for t in range(nt):
+        k = int(na_arr[t])
+        deg = np.arange(k) * 180.0 / k + t * 180.0 / (k * nt)
+        out.append(np.deg2rad(deg))
+    return na_arr, np.concatenate(out)
+
+
+def ellipse_radon(e, theta, sigma):
+    """Exact line integral of one ellipse (cx, cy, a, b, phi, rho) along the rays
+    {x cos(theta) + y sin(theta) = sigma}: rho times the chord length."""
+    cx, cy, a, b, phi, rho = e
+    s = sigma - (cx * np.cos(theta) + cy * np.sin(theta))
+    d = theta - phi
+    a2 = (a * np.cos(d)) ** 2 + (b * np.sin(d)) ** 2
+    q = a2 - s * s
+    return np.where(q > 0, rho * 2.0 * a * b * np.sqrt(np.maximum(q, 0.0)) / a2, 0.0)
+
+
+def raster(e_list, nx, ny, h=1.0, ss=4):
+    """Area-averaged raster (ss x ss sub-samples per pixel) of a sum of ellipses."""
+    off = (np.arange(ss) + 0.5) / ss - 0.5
+    xs = ((np.arange(nx) - 0.5 * (nx - 1))[:, None] + off[None, :]).ravel() * h
+    ys = ((np.arange(ny) - 0.5 * (ny - 1))[:, None] + off[None, :]).ravel() * h
+    X, Y = np.meshgrid(xs, ys)
+    img = np.zeros_like(X)
+    for (cx, cy, a, b, phi, rho) in e_list:
+        dx, dy = X - cx, Y - cy
+        c, s = np.cos(phi), np.sin(phi)
+        xr, yr = c * dx + s * dy, -s * dx + c * dy
+        img += rho * ((xr / a) ** 2 + (yr / b) ** 2 <= 1.0)
+    return img.reshape(ny, ss, nx, ss).mean(axis=(1, 3))
+
+
+def _make(name, nx, ny, nt, na, nb, ellipses, noise_rel, seed, h=1.0, db=1.0):
+    na_arr, angles = shifted_angles(nt, na)
+    sig = (np.arange(nb) - 0.5 * (nb - 1)) * db
+    u_true = np.empty((nt, ny, nx))
+    b_clean = np.empty(int(na_arr.sum()) * nb)
+    off = 0
+    aoff = 0
+    for t in range(nt):
+        ets = [e.at(t) for e in ellipses]
+        u_true[t] = raster(ets, nx, ny, h)
+        th = angles[aoff:aoff + na_arr[t]]
+        blk = np.zeros((na_arr[t], nb))
+        for et in ets:
+            blk += ellipse_radon(et, th[:, None], sig[None, :])
+        b_clean[off:off + blk.size] = blk.ravel()
+        off += blk.size
+        aoff += na_arr[t]
+    rng = np.random.default_rng(seed + 7919)
+    m = b_clean.size
+    e = noise_rel * np.linalg.norm(b_clean) / math.sqrt(m) * rng.standard_normal(m)
+    return Workload(name=name, nx=nx, ny=ny, nt=nt, nb=nb, na=na_arr, angles=angles, h=h, db=db,
+                    u_true=u_true, b_clean=b_clean, b=b_clean + e,
+                    noise_norm=float(np.linalg.norm(e)), ellipses=ellipses)
+
+
+def _inside(e, nt, R):
+    """True if the ellipse stays inside the disk of radius R for frames 0..nt-1."""
+    for t in range(nt):
+        cx, cy, a, b, _, _ = e.at(t)
+        if math.hypot(cx, cy) + max(a, b) > R:
+            return False
+    return True
+
+
+def moving_disks(n=64, nt=8, na=16, nb=64, radii=(8.0, 12.0), rhos=(1.0, 0.6), speed=1.0,
+                 noise=0.01, seed=0, name=None):
+    """Uniform disks translating `speed` px/frame in fixed seeded directions, kept
+    inside the inscribed circle of the grid for every frame."""
+    rng = np.random.default_rng(seed)
+    R = 0.5 * (n - 1)
+    ell = []
+    for r, rho in zip(radii, rhos):
+        for _ in range(10000):
+            ang = rng.uniform(0, 2 * np.pi)
+            vx, vy = speed * np.cos(ang), speed * np.sin(ang)
+            rr = (R - r) * np.sqrt(rng.uniform(0, 1))
+            pa = rng.uniform(0, 2 * np.pi)
+            e = Ellipse(rr * np.cos(pa), rr * np.sin(pa), r, r, 0.0, rho, vx, vy, 0.0)
+            if _inside(e, nt, R):
+                ell.append(e)
+                break
+        else:
+            raise RuntimeError("could not place disk")
+    return _make(name or "disks%dx%dx%d" % (n, n, nt), n, n, nt, na, nb, ell, noise, seed)
+
+
+def moving_ellipses(n=256, nt=32, na=30, nb=363, n_ell=6, axes=(8.0, 40.0), rho=(0.2, 1.0),
+                    speed=(0.5, 2.0), rot_deg=2.0, noise=0.01, seed=0, name=None):
+    """Seeded ellipses, each in rigid motion: translation of U(speed) px/frame and
+    rotation of U(-rot_deg, rot_deg) degrees/frame about its own centre."""
+    rng = np.random.default_rng(seed)
+    R = 0.5 * (n - 1)
+    ell = []
+    scale = n / 256.0
+    for _ in range(n_ell):
+        for _ in range(10000):
+            a = rng.uniform(*axes) * scale
+            b = rng.uniform(*axes) * scale
+            phi = rng.uniform(0, np.pi)
+            sp = rng.uniform(*speed)
+            ang = rng.uniform(0, 2 * np.pi)
+            om = np.deg2rad(rng.uniform(-rot_deg, rot_deg))
+            rr = (R - max(a, b)) * np.sqrt(rng.uniform(0, 1))
+            pa = rng.uniform(0, 2 * np.pi)
+            e = Ellipse(rr * np.cos(pa), rr * np.sin(pa), a, b, phi, rng.uniform(*rho),
+                        sp * np.cos(ang), sp * np.sin(ang), om)
+            if _inside(e, nt, R):
+                ell.append(e)
+                break
+        else:
+            raise RuntimeError("could not place ellipse")
+    return _make(name or "ellipses%dx%dx%d" % (n, n, nt), n, n, nt, na, nb, ell, noise, seed)
+
+
+# The workloads of the method's benchmark configurations.
+def plain_fp64(seed=0):
+    """64x64 frames, T=8, 16 angles/frame, 64 bins, two disks (r 8/12, rho 1.0/0.6)
+    at 1 px/frame, 1% noise."""
+    return moving_disks(64, 8, 16, 64, seed=seed, name="disks64x64x8")
+
+
+def precision_form(seed=0):
+    """256x256 frames, T=32, 30 angles/frame, 363 bins, six ellipses in rigid motion, 1% noise."""
+    return moving_ellipses(256, 32, 30, 363, seed=seed, name="ellipses256x256x32")
+
+
+def precision_form_small(seed=0):
+    """A reduced instance of the same generator (96x96, T=6, 30 angles, 137 bins) that
+    the FP64 oracle finishes in seconds; used for end-to-end parity."""
+    return moving_ellipses(96, 6, 30, 137, seed=seed, name="ellipses96x96x6")
+
+
+def differentiation_form(seed=0):
+    """The two-disk generator at 256x256, T=32 (radii 32/48 px, 1 px/frame), 16 angles,
+    256 bins."""
+    return moving_disks(256, 32, 16, 256, radii=(32.0, 48.0), seed=seed, name="disks256x256x32")
+
+
+# ------------------------------------------------------- generic random inputs
+
+def random_images(nt, ny, nx, seed=0, smooth=2):
+    """Seeded smooth random images (box-filtered white noise), float64."""
+    rng = np.random.default_rng(seed)
+    u = rng.standard_normal((nt, ny, nx))
+    for _ in range(smooth):
+        u = (u + np.roll(u, 1, -1) + np.roll(u, -1, -1)) / 3.0
+        u = (u + np.roll(u, 1, -2) + np.roll(u, -1, -2)) / 3.0
+    return u
+
+
+def random_velocities(npairs, ny, nx, vmax=2.0, seed=0):
+    """Seeded smooth velocity fields (npairs, 2, ny, nx) with |s| <= vmax, float64."""
+    rng = np.random.default_rng(seed)
+    yy, xx = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    s = np.zeros((npairs, 2, ny, nx))
+    for p in range(npairs):
+        for c in range(2):
+            f = np.zeros((ny, nx))
+            for _ in range(3):
+                cx, cy = rng.uniform(0, nx), rng.uniform(0, ny)
+                sg = rng.uniform(0.1, 0.3) * max(nx, ny)
+                f += rng.uniform(-1, 1) * np.exp(-((xx - cx) ** 2 + (yy - cy) ** 2) / (2 * sg * sg))
+            s[p, c] = f
+        mx = np.max(np.abs(s[p])) or 1.0
+        s[p] *= vmax * rng.uniform(0.5, 1.0) / mx
+    return s
