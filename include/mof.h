@@ -1,0 +1,213 @@
+/*
+ * mof.h -- C ABI of the GB300 MMGKS-OF library (libmof.so).
+ *
+ * MMGKS-OF (arXiv 2501.12497) reconstructs an image sequence u from
+ * per-frame tomographic data b by alternating an optical-flow motion
+ * estimate (Alg. 2, "Solve-OF") with one majorization-minimization
+ * generalized-Krylov step on ||H u - b||^2 + lambda ||Theta u||_1,
+ * Theta = [Psi; Mhat(s, s')] (Alg. 1, Sec. 4.1.1). This header exposes the
+ * operators of that method and the solver.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Array arguments are DEVICE pointers owned by the caller and borrowed for
+ *    the duration of the call (the library keeps no reference), except where
+ *    a parameter is documented as a host pointer. Element type is float for a
+ *    problem created with MOF_FP32 and double for MOF_FP64.
+ *  - Every call that takes `stream` enqueues its work on that CUDA stream
+ *    (cudaStream_t passed as void*; NULL = the legacy default stream) and
+ *    returns without synchronising, unless documented otherwise.
+ *  - Argument errors are detected on the host and returned synchronously;
+ *    nothing is enqueued then. The text of the last error of the calling
+ *    thread is available from mof_last_error().
+ *  - Layouts (x fastest, all contiguous):
+ *      image sequence  u[nt][ny][nx]        (Sec. 2.1: vec of column-stacked
+ *                                            frames; pixel row index y*nx + x)
+ *      sinogram        b[sum_t na[t]][nb]   (frame t's na[t] angles in order)
+ *      velocities      s[nt-1][2][ny][nx]   (component 0 = s_x, 1 = s_y);
+ *                      s[p] maps frame p to frame p+1 (M(s(p)) u_{p+1} ~ u_p)
+ *      reverse flow    sr[nt-1][2][ny][nx]  (sr[p] = s'(p+1), on frame p+1)
+ *      gradient        g[nf][2][ny][nx]     (d=0: u(x+1)-u(x), d=1: u(y+1)-u(y),
+ *                                            last column/row identically 0)
+ *      flow residual   r[2][nt-1][ny][nx]   (r[0] = Mbar rows, r[1] = Mbar' rows)
+ *      OF fields       ux, uy, ut [nt-1][ny][nx]
+ *      velocity grad.  gs[nt-1][2 comp][2 dir][ny][nx]
+ *  - Geometry: 2D parallel beam. Pixel centres x_i = (i - (nx-1)/2) h,
+ *    y_j = (j - (ny-1)/2) h; bin centres sigma_k = (k - (nb-1)/2) db; the ray
+ *    (theta, k) is { x cos(theta) + y sin(theta) = sigma_k }.
+ */
+#ifndef MOF_H
+#define MOF_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MOF_OK = 0,
+    MOF_EINVAL = 1,        /* bad argument (null pointer, size, value) */
+    MOF_ENOMEM = 2,        /* device or host allocation failed */
+    MOF_ECUDA = 3,         /* a CUDA runtime call failed (text in mof_last_error) */
+    MOF_ENUMERIC = 4,      /* non-finite value or failed factorisation detected on device */
+    MOF_ETIMEOUT = 5,      /* a bounded device wait expired */
+    MOF_EUNSUPPORTED = 6   /* valid but not supported by this build */
+} mof_status;
+
+typedef enum { MOF_FP32 = 0, MOF_FP64 = 1 } mof_precision;
+
+typedef enum { MOF_RULE_DP = 0, MOF_RULE_GCV = 1, MOF_RULE_FIXED = 2 } mof_rule;
+
+/* Geometry of one problem (Sec. 2.1: H = blockdiag(H^1, ..., H^nt)).
+ * na and angles are HOST arrays, read during mof_problem_create only. */
+typedef struct {
+    int nx, ny, nt;        /* frame width, height, number of frames (nt >= 2) */
+    int nb;                /* detector bins per angle */
+    const int *na;         /* [nt] angles of each frame (>= 1) */
+    const double *angles;  /* [sum na] projection angles in radians */
+    double pixel_size;     /* h > 0 */
+    double bin_size;       /* db > 0 */
+} mof_geometry;
+
+typedef struct mof_problem mof_problem;
+
+/* Parameters of Alg. 1 / Alg. 2. mof_default_params fills the defaults. */
+typedef struct {
+    int ell;               /* initial GKB subspace of the image step (Sec. 5: 10) */
+    int tau;               /* Solve-OF every tau outer iterations (Sec. 4.1.5); 0 = never */
+    int of_iters;          /* GKS iterations per Solve-OF (Sec. 5: 20) */
+    int of_ell;            /* GKB start of Solve-OF (10) */
+    int of_dr;             /* box half-width Delta r of App. C (1) */
+    int image_rule;        /* mof_rule for lambda of the image step (DP when delta known) */
+    double eps;            /* l1 smoothing epsilon of Alg. 1 (1e-3) */
+    double eta;            /* DP safety factor (Sec. 4.1.3: 1.01) */
+    double noise_norm;     /* delta = ||e||, required by MOF_RULE_DP */
+    double lam_fixed;      /* lambda for MOF_RULE_FIXED */
+    double breakdown_tol;  /* <= 0: 1e-10 (FP64) / 1e-6 (FP32) relative breakdown threshold */
+} mof_solver_params;
+
+/* One record per outer iteration k of mof_solve (host struct). */
+typedef struct {
+    double lambda;         /* regularisation parameter chosen at iteration k */
+    double resid;          /* ||H u^(k+1) - b|| */
+    double rnorm;          /* ||r^(k+1)|| before normalisation (0 if not expanded) */
+    int basis;             /* dimension l+k of the image-step subspace used */
+    int flag;              /* DP: 0 root, 1 no root (residual > target), 2 (< target) */
+    int of_basis_min;      /* smallest Solve-OF basis over pairs (0 if no OF this k) */
+    int of_basis_max;      /* largest Solve-OF basis over pairs */
+} mof_report;
+
+void mof_default_params(mof_solver_params *p);
+
+/* Create a problem: validates the geometry, uploads the angle tables.
+ * precision: MOF_FP32 (operators in FP32, Krylov bookkeeping and small
+ * solves in FP64) or MOF_FP64 (everything FP64). Uses the current device.
+ * On success *out owns its device memory until mof_problem_destroy. */
+mof_status mof_problem_create(const mof_geometry *g, int precision, mof_problem **out);
+void mof_problem_destroy(mof_problem *p);
+
+/* Sizes: n = nx*ny*nt pixels, m = nb * sum(na) data values,
+ * nv = (nt-1)*2*nx*ny values of one velocity field. Any pointer may be NULL. */
+mof_status mof_problem_sizes(const mof_problem *p, long long *n, long long *m, long long *nv);
+
+/* b = H u: per frame, per angle and bin, Joseph's line integral along the
+ * ray (Sec. 2.1 block-diagonal H; entry a = (h/mu) max(0, 1 - |sigma - p|/(mu h)),
+ * p = x cos + y sin, mu = max(|cos|, |sin|)). Ray-driven. u: n, b: m. */
+mof_status mof_apply_A(mof_problem *p, const void *u, void *b, void *stream);
+
+/* u = H^T b: the exact transpose of mof_apply_A (same entries), pixel-driven
+ * gather (Sec. 4.1.1: H^T in the normal-equation residual). b: m, u: n. */
+mof_status mof_apply_AT(mof_problem *p, const void *b, void *u, void *stream);
+
+/* g = Psi u, forward differences along x and y of every frame
+ * (eq. (L), Psi = blockdiag(L, ..., L)). u: n, g: 2n. */
+mof_status mof_apply_grad(mof_problem *p, const void *u, void *g, void *stream);
+
+/* u = Psi^T g (exact transpose; padded zero rows ignore g there). */
+mof_status mof_apply_gradT(mof_problem *p, const void *g, void *u, void *stream);
+
+/* r = Mhat(s, s') u (Sec. 3, bilinear-warp encoding of M(s); Sec. 4:
+ * Mhat = [Mbar; Mbar']):  r[0][p] = u_p - M(s_p) u_{p+1},
+ * r[1][p] = u_{p+1} - M(sr_p) u_p. M(s) samples its argument at r + s(r),
+ * clipped to the image, with bilinear weights. u: n, s, sr: nv, r: 2*(nt-1)*nx*ny. */
+mof_status mof_apply_flow(mof_problem *p, const void *u, const void *s, const void *sr,
+                          void *r, void *stream);
+
+/* u = Mhat(s, s')^T r (exact transpose of mof_apply_flow; deterministic gather). */
+mof_status mof_apply_flowT(mof_problem *p, const void *r, const void *s, const void *sr,
+                           void *u, void *stream);
+
+/* App. C derivative fields of every pair (u_p, u_{p+1}), box half-width dr,
+ * image flipped about its edges:  ux = box-averaged central x-difference of
+ * u_p, uy likewise in y, ut = box average of u_{p+1} - u_p. u: n; outputs (nt-1)*nx*ny. */
+mof_status mof_of_fields(mof_problem *p, const void *u, int dr, void *ux, void *uy, void *ut,
+                         void *stream);
+
+/* r = Upsilon s + u_t per pair (Sec. 2.2: the pointwise row [u_x u_y]).
+ * s: nv, r: (nt-1)*nx*ny. */
+mof_status mof_apply_flow_lin(mof_problem *p, const void *ux, const void *uy, const void *ut,
+                              const void *s, void *r, void *stream);
+
+/* gs = Upsilon^T r per pair: gs[p][0] = ux r, gs[p][1] = uy r. */
+mof_status mof_apply_flow_linT(mof_problem *p, const void *ux, const void *uy, const void *r,
+                               void *gs, void *stream);
+
+/* gs = (L (+) L) s: forward-difference gradient of each velocity component
+ * (Sec. 2.2, the discrete gradient of the velocity regulariser). gs: 2*nv. */
+mof_status mof_apply_vgrad(mof_problem *p, const void *s, void *gs, void *stream);
+
+/* s = (L (+) L)^T gs. */
+mof_status mof_apply_vgradT(mof_problem *p, const void *gs, void *s, void *stream);
+
+/* sr = reverse flow from s by the remark of Sec. 3: the pixel r of frame p
+ * moves to round(r + s_p(r)) (half away from zero, clipped) in frame p+1 and
+ * carries -s_p(r) there; arrivals are averaged, pixels without arrivals get 0. */
+mof_status mof_reverse_flow(mof_problem *p, const void *s, void *sr, void *stream);
+
+/* y = Theta^T W Theta x with Theta = [Psi; Mhat(s, s')] and IRLS weights
+ * W = diag(((Theta uk)^2 + eps^2)^(-1/2)) recomputed from uk (Alg. 1:
+ * P^2 with P = diag((nu^2 + eps^2)^(-1/4)), nu = Theta u^(k)). x, uk, y: n. */
+mof_status mof_apply_reg_normal(mof_problem *p, const void *x, const void *uk, const void *s,
+                                const void *sr, double eps, void *y, void *stream);
+
+/* Solve-OF (Alg. 2, p = q = 2) on every consecutive pair of u at once:
+ * GKB start of prm->of_ell steps from -u_t, then prm->of_iters GKS
+ * iterations on min ||Upsilon s + u_t||^2 + gamma ||(L (+) L) s||^2 with
+ * gamma chosen by GCV every iteration. Pairs whose u_t is zero get s = 0.
+ * u: n, s: nv. Synchronises `stream` before returning (reads status). */
+mof_status mof_solve_of(mof_problem *p, const mof_solver_params *prm, const void *u, void *s,
+                        void *stream);
+
+/* MMGKS-OF (Alg. 1) for n_outer outer iterations from u^(0) = 0, s^(0) = 0.
+ * b: m (device). u_out: n. s_out, sr_out: nv each, may be NULL (the flow
+ * used by the last iteration). report: HOST array of n_outer records, may
+ * be NULL. The library allocates its workspace (Krylov bases, Gram
+ * matrices) on first use and keeps it until mof_problem_destroy.
+ * Synchronises `stream` before returning; device-detected numerical errors
+ * return MOF_ENUMERIC. */
+mof_status mof_solve(mof_problem *p, const mof_solver_params *prm, int n_outer, const void *b,
+                     void *u_out, void *s_out, void *sr_out, mof_report *report, void *stream);
+
+/* mof_solve with HOST input and output buffers (b: m, u_out: n, s_out and
+ * sr_out: nv or NULL); copies in and out on `stream` inside the call. Host
+ * buffers may be pageable or pinned; pinned buffers overlap better. */
+mof_status mof_solve_host(mof_problem *p, const mof_solver_params *prm, int n_outer,
+                          const void *b_host, void *u_host, void *s_host, void *sr_host,
+                          mof_report *report, void *stream);
+
+/* Per-kernel-class device time of the last mof_solve when timing was
+ * enabled with mof_set_timing(p, 1): fills up to `cap` entries of names
+ * (static strings), milliseconds and launch counts; returns the number of
+ * classes in *count. Timing records CUDA events around each launch on the
+ * solver's stream. */
+mof_status mof_set_timing(mof_problem *p, int enable);
+mof_status mof_get_timing(const mof_problem *p, int cap, const char **names, double *ms,
+                          long long *launches, int *count);
+
+/* Text of the last error on the calling thread ("" if none). */
+const char *mof_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MOF_H */

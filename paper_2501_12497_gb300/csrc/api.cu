@@ -1,0 +1,323 @@
+// C ABI entry points of libmof (include/mof.h): problem lifetime, argument
+// validation, precision dispatch and error text. Numerical work happens in
+// the kernels of ops_*.cu, krylov.cu, small.cu and solver.cu.
+#include "common.cuh"
+#include "solver.cuh"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <new>
+
+namespace mof {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+mof_status fail(mof_status st, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+mof_status cuda_fail(cudaError_t e, const char *what, const char *file, int line) {
+    set_error("CUDA error %d (%s) in %s at %s:%d", (int)e, cudaGetErrorString(e), what, file, line);
+    return e == cudaErrorMemoryAllocation ? MOF_ENOMEM : MOF_ECUDA;
+}
+
+// Round v to 12 significant bits (head) and keep the remainder (tail).
+static void split12(double v, float &hi, float &lo) {
+    if (v == 0.0 || !std::isfinite(v)) {
+        hi = (float)v;
+        lo = 0.0f;
+        return;
+    }
+    int e;
+    std::frexp(v, &e);
+    const double sc = std::ldexp(1.0, 12 - e);
+    const double h = std::nearbyint(v * sc) / sc;
+    hi = (float)h;
+    lo = (float)(v - h);
+}
+
+static AngleParams angle_params(double theta, int frame, int nx, int ny, int nb, double h, double db) {
+    AngleParams P{};
+    const double c = std::cos(theta), s = std::sin(theta);
+    P.c = c;
+    P.s = s;
+    P.frame = frame;
+    const int rows = std::fabs(c) >= std::fabs(s);
+    P.rows = rows;
+    const double cc = rows ? c : s, ss = rows ? s : c;
+    const int nfast = rows ? nx : ny, nstep = rows ? ny : nx;
+    // f(k, j) = sigma_k / (cc h) + (nfast-1)/2 + ((nstep-1)/2 - j) (ss/cc)
+    P.f0_k = db / (cc * h);
+    P.f0_c = -0.5 * (nb - 1) * db / (cc * h) + 0.5 * (nfast - 1) + 0.5 * (nstep - 1) * (ss / cc);
+    P.df = -ss / cc;
+    split12(P.df, P.df_hi, P.df_lo);
+    P.wstep = (float)(h / std::fabs(cc));
+    // t(i, j) = (x_i c + y_j s)/db + (nb-1)/2
+    P.tA = h * c / db;
+    P.tB = h * s / db;
+    P.t0 = 0.5 * (nb - 1) - 0.5 * (nx - 1) * P.tA - 0.5 * (ny - 1) * P.tB;
+    split12(P.tA, P.tA_hi, P.tA_lo);
+    split12(P.tB, P.tB_hi, P.tB_lo);
+    const double mu = std::fmax(std::fabs(c), std::fabs(s));
+    P.rfoot = (float)(mu * h / db);
+    P.wfoot = (float)(h / mu);
+    return P;
+}
+
+static mof_status check_problem(const mof_problem *p) {
+    if (!p) return fail(MOF_EINVAL, "null problem");
+    return MOF_OK;
+}
+
+static cudaStream_t S(void *stream) { return reinterpret_cast<cudaStream_t>(stream); }
+
+}  // namespace mof
+
+using namespace mof;
+
+extern "C" {
+
+const char *mof_last_error(void) { return g_err; }
+
+void mof_default_params(mof_solver_params *p) {
+    if (!p) return;
+    p->ell = 10;
+    p->tau = 1;
+    p->of_iters = 20;
+    p->of_ell = 10;
+    p->of_dr = 1;
+    p->image_rule = MOF_RULE_DP;
+    p->eps = 1e-3;
+    p->eta = 1.01;
+    p->noise_norm = -1.0;
+    p->lam_fixed = 0.0;
+    p->breakdown_tol = 0.0;
+}
+
+mof_status mof_problem_create(const mof_geometry *g, int precision, mof_problem **out) {
+    g_err[0] = 0;
+    if (!g || !out) return fail(MOF_EINVAL, "null geometry or output pointer");
+    *out = nullptr;
+    if (g->nx < 2 || g->ny < 2 || g->nt < 2 || g->nb < 1)
+        return fail(MOF_EINVAL, "need nx, ny, nt >= 2 and nb >= 1 (got %d %d %d %d)", g->nx, g->ny, g->nt, g->nb);
+    if (g->nx > 4096 || g->ny > 4096) return fail(MOF_EUNSUPPORTED, "frames wider than 4096 pixels are not supported");
+    if (!g->na || !g->angles) return fail(MOF_EINVAL, "null angle tables");
+    if (!(g->pixel_size > 0) || !(g->bin_size > 0)) return fail(MOF_EINVAL, "pixel_size and bin_size must be > 0");
+    if (precision != MOF_FP32 && precision != MOF_FP64) return fail(MOF_EINVAL, "unknown precision %d", precision);
+    long long A = 0;
+    for (int t = 0; t < g->nt; ++t) {
+        if (g->na[t] < 1) return fail(MOF_EINVAL, "frame %d has %d angles", t, g->na[t]);
+        A += g->na[t];
+    }
+    if ((long long)g->nx * g->ny * g->nt >= (1LL << 31) / 2 || A * g->nb >= (1LL << 31))
+        return fail(MOF_EUNSUPPORTED, "problem too large for 32-bit pixel indexing");
+    for (long long a = 0; a < A; ++a)
+        if (!std::isfinite(g->angles[a])) return fail(MOF_EINVAL, "angle %lld is not finite", a);
+
+    mof_problem *p = new (std::nothrow) mof_problem();
+    if (!p) return fail(MOF_ENOMEM, "host allocation failed");
+    p->nx = g->nx; p->ny = g->ny; p->nt = g->nt; p->nb = g->nb;
+    p->precision = precision;
+    p->h = g->pixel_size; p->db = g->bin_size;
+    p->ns = (long long)g->nx * g->ny;
+    p->n = p->ns * g->nt;
+    p->m = A * g->nb;
+    p->nv = (long long)(g->nt - 1) * 2 * p->ns;
+    p->A = (int)A;
+    p->na.assign(g->na, g->na + g->nt);
+    p->aoff.resize(g->nt + 1);
+    p->aoff[0] = 0;
+    for (int t = 0; t < g->nt; ++t) p->aoff[t + 1] = p->aoff[t] + g->na[t];
+    std::vector<AngleParams> tab(A);
+    for (int t = 0; t < g->nt; ++t)
+        for (int a = p->aoff[t]; a < p->aoff[t + 1]; ++a)
+            tab[a] = angle_params(g->angles[a], t, g->nx, g->ny, g->nb, g->pixel_size, g->bin_size);
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_ang, sizeof(AngleParams) * A);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_aoff, sizeof(int) * (g->nt + 1));
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_ang, tab.data(), sizeof(AngleParams) * A, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_aoff, p->aoff.data(), sizeof(int) * (g->nt + 1), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        mof_status st = cuda_fail(e, "mof_problem_create", __FILE__, __LINE__);
+        mof_problem_destroy(p);
+        return st;
+    }
+    *out = p;
+    return MOF_OK;
+}
+
+void mof_problem_destroy(mof_problem *p) {
+    if (!p) return;
+    free_workspace(p);
+    if (p->d_ang) cudaFree(p->d_ang);
+    if (p->d_aoff) cudaFree(p->d_aoff);
+    delete p;
+}
+
+mof_status mof_problem_sizes(const mof_problem *p, long long *n, long long *m, long long *nv) {
+    MOF_TRY(check_problem(p));
+    if (n) *n = p->n;
+    if (m) *m = p->m;
+    if (nv) *nv = p->nv;
+    return MOF_OK;
+}
+
+#define DISPATCH(p, call_f, call_d) ((p)->precision == MOF_FP64 ? (call_d) : (call_f))
+#define F(x) ((float *)(x))
+#define CF(x) ((const float *)(x))
+#define D(x) ((double *)(x))
+#define CD(x) ((const double *)(x))
+
+mof_status mof_apply_A(mof_problem *p, const void *u, void *b, void *stream) {
+    g_err[0] = 0;
+    MOF_TRY(check_problem(p));
+    if (!u || !b) return fail(MOF_EINVAL, "null array");
+    void *uT = nullptr;
+    MOF_TRY(apply_scratch(p, SCR_IMAGE, &uT));
+    return DISPATCH(p, launch_project<float>(p, CF(u), F(uT), F(b), S(stream)),
+                    launch_project<double>(p, CD(u), D(uT), D(b), S(stream)));
+}
+
+mof_status mof_apply_AT(mof_problem *p, const void *b, void *u, void *stream) {
+    g_err[0] = 0;
+    MOF_TRY(check_problem(p));
+    if (!u || !b) return fail(MOF_EINVAL, "null array");
+    return DISPATCH(p, launch_backproject<float>(p, CF(b), F(u), S(stream)),
+                    launch_backproject<double>(p, CD(b), D(u), S(stream)));
+}
+
+mof_status mof_apply_grad(mof_problem *p, const void *u, void *g, void *stream) {
+    g_err[0] = 0;
+    MOF_TRY(check_problem(p));
+    if (!u || !g) return fail(MOF_EINVAL, "null array");
+    return DISPATCH(p, launch_grad<float>(p, p->nt, CF(u), F(g), S(stream)),
+                    launch_grad<double>(p, p->nt, CD(u), D(g), S(stream)));
+}
+
+mof_status mof_apply_gradT(mof_problem *p, const void *g, void *u, void *stream) {
+    g_err[0] = 0;
+    MOF_TRY(check_problem(p));
+    if (!u || !g) return fail(MOF_EINVAL, "null array");
+    return DISPATCH(p, launch_gradT<float>(p, p->nt, CF(g), F(u), S(stream)),
+                    launch_gradT<double>(p, p->nt, CD(g), D(u), S(stream)));
+}
+
+mof_status mof_apply_flow(mof_problem *p, const void *u, const void *s, const void *sr, void *r, void *stream) {
+    g_err[0] = 0;
+    MOF_TRY(check_problem(p));
+    if (!u || !s || !sr || !r) return fail(MOF_EINVAL, "null array");
+    return DISPATCH(p, launch_flow<float>(p, CF(u), CF(s), CF(sr), F(r), S(stream)),
+                    launch_flow<double>(p, CD(u), CD(s), CD(sr), D(r), S(stream)));
+}
+
+mof_status mof_apply_flowT(mof_problem *p, const void *r, const void *s, const void *sr, void *u, void *stream) {
+    g_err[0] = 0;
+    MOF_TRY(check_problem(p));
+    if (!u || !s || !sr || !r) return fail(MOF_EINVAL, "null array");
+    void *rad = nullptr;
+    MOF_TRY(apply_scratch(p, SCR_RADIUS, &rad));
+    if (p->precision == MOF_FP64) {
+        MOF_TRY(launch_window_radius<double>(p, CD(s), CD(sr), (int *)rad, S(stream)));
+        return launch_flowT<double>(p, CD(r), CD(s), CD(sr), (const int *)rad, D(u), S(stream));
+    }
+    MOF_TRY(launch_window_radius<float>(p, CF(s), CF(sr), (int *)rad, S(stream)));
+    return launch_flowT<float>(p, CF(r), CF(s), CF(sr), (const int *)rad, F(u), S(stream));
+}
+
+mof_status mof_of_fields(mof_problem *p, const void *u, int dr, void *ux, void *uy, void *ut, void *stream) {
+    g_err[0] = 0;
+    MOF_TRY(check_problem(p));
+    if (!u || !ux || !uy || !ut) return fail(MOF_EINVAL, "null array");
+    if (dr < 1 || dr > 64) return fail(MOF_EINVAL, "dr must be in [1, 64] (got %d)", dr);
+    return DISPATCH(p, launch_of_fields<float>(p, CF(u), dr, F(ux), F(uy), F(ut), S(stream)),
+                    launch_of_fields<double>(p, CD(u), dr, D(ux), D(uy), D(ut), S(stream)));
+}
+
+mof_status mof_apply_flow_lin(mof_problem *p, const void *ux, const void *uy, const void *ut, const void *s, void *r,
+                              void *stream) {
+    g_err[0] = 0;
+    MOF_TRY(check_problem(p));
+    if (!ux || !uy || !ut || !s || !r) return fail(MOF_EINVAL, "null array");
+    return DISPATCH(p, launch_flow_lin<float>(p, CF(ux), CF(uy), CF(ut), CF(s), F(r), S(stream)),
+                    launch_flow_lin<double>(p, CD(ux), CD(uy), CD(ut), CD(s), D(r), S(stream)));
+}
+
+mof_status mof_apply_flow_linT(mof_problem *p, const void *ux, const void *uy, const void *r, void *gs, void *stream) {
+    g_err[0] = 0;
+    MOF_TRY(check_problem(p));
+    if (!ux || !uy || !r || !gs) return fail(MOF_EINVAL, "null array");
+    return DISPATCH(p, launch_flow_linT<float>(p, CF(ux), CF(uy), CF(r), F(gs), S(stream)),
+                    launch_flow_linT<double>(p, CD(ux), CD(uy), CD(r), D(gs), S(stream)));
+}
+
+mof_status mof_apply_vgrad(mof_problem *p, const void *s, void *gs, void *stream) {
+    g_err[0] = 0;
+    MOF_TRY(check_problem(p));
+    if (!s || !gs) return fail(MOF_EINVAL, "null array");
+    const int nf = 2 * (p->nt - 1);
+    return DISPATCH(p, launch_grad<float>(p, nf, CF(s), F(gs), S(stream)),
+                    launch_grad<double>(p, nf, CD(s), D(gs), S(stream)));
+}
+
+mof_status mof_apply_vgradT(mof_problem *p, const void *gs, void *s, void *stream) {
+    g_err[0] = 0;
+    MOF_TRY(check_problem(p));
+    if (!s || !gs) return fail(MOF_EINVAL, "null array");
+    const int nf = 2 * (p->nt - 1);
+    return DISPATCH(p, launch_gradT<float>(p, nf, CF(gs), F(s), S(stream)),
+                    launch_gradT<double>(p, nf, CD(gs), D(s), S(stream)));
+}
+
+mof_status mof_reverse_flow(mof_problem *p, const void *s, void *sr, void *stream) {
+    g_err[0] = 0;
+    MOF_TRY(check_problem(p));
+    if (!s || !sr) return fail(MOF_EINVAL, "null array");
+    void *rad = nullptr, *dest = nullptr;
+    MOF_TRY(apply_scratch(p, SCR_RADIUS, &rad));
+    MOF_TRY(apply_scratch(p, SCR_DEST, &dest));
+    if (p->precision == MOF_FP64) {
+        MOF_TRY(launch_window_radius<double>(p, CD(s), nullptr, (int *)rad, S(stream)));
+        return launch_reverse_flow<double>(p, CD(s), (const int *)rad, (int *)dest, D(sr), S(stream));
+    }
+    MOF_TRY(launch_window_radius<float>(p, CF(s), nullptr, (int *)rad, S(stream)));
+    return launch_reverse_flow<float>(p, CF(s), (const int *)rad, (int *)dest, F(sr), S(stream));
+}
+
+mof_status mof_apply_reg_normal(mof_problem *p, const void *x, const void *uk, const void *s, const void *sr, double eps,
+                                void *y, void *stream) {
+    g_err[0] = 0;
+    MOF_TRY(check_problem(p));
+    if (!x || !uk || !s || !sr || !y) return fail(MOF_EINVAL, "null array");
+    if (!(eps > 0) || !std::isfinite(eps)) return fail(MOF_EINVAL, "eps must be finite and > 0");
+    void *rad = nullptr, *q = nullptr;
+    MOF_TRY(apply_scratch(p, SCR_RADIUS, &rad));
+    MOF_TRY(apply_scratch(p, SCR_FLOWROWS, &q));
+    if (p->precision == MOF_FP64) {
+        MOF_TRY(launch_window_radius<double>(p, CD(s), CD(sr), (int *)rad, S(stream)));
+        return launch_reg_normal<double>(p, CD(x), CD(uk), CD(s), CD(sr), (const int *)rad, eps, 1.0, nullptr, nullptr,
+                                         D(q), D(y), S(stream));
+    }
+    MOF_TRY(launch_window_radius<float>(p, CF(s), CF(sr), (int *)rad, S(stream)));
+    return launch_reg_normal<float>(p, CF(x), CF(uk), CF(s), CF(sr), (const int *)rad, eps, 1.0, nullptr, nullptr, F(q),
+                                    F(y), S(stream));
+}
+
+mof_status mof_set_timing(mof_problem *p, int enable) {
+    MOF_TRY(check_problem(p));
+    p->timing = enable ? 1 : 0;
+    return MOF_OK;
+}
+
+}  // extern "C"

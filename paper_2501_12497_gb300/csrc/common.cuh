@@ -1,0 +1,132 @@
+// Internal declarations of libmof: the problem object, per-angle tables,
+// error plumbing and small device helpers shared by the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "mof.h"
+
+namespace mof {
+
+// ----------------------------------------------------------------- errors
+void set_error(const char *fmt, ...);
+mof_status fail(mof_status st, const char *fmt, ...);
+mof_status cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+
+#define MOF_CUDA(call)                                                               \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess) return ::mof::cuda_fail(e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define MOF_TRY(expr)                       \
+    do {                                    \
+        mof_status s_ = (expr);             \
+        if (s_ != MOF_OK) return s_;        \
+    } while (0)
+
+// Launch-error check after a kernel launch.
+#define MOF_LAUNCH_CHECK() MOF_CUDA(cudaGetLastError())
+
+// ------------------------------------------------------- per-angle tables
+// Host-computed (FP64) parameters of one projection angle. The FP32
+// kernels evaluate affine coordinates base + j * step with the step split
+// into a 12-significant-bit head (exact products with |j| < 4096) and a
+// tail, so that the fractional interpolation weight keeps ~1e-7 absolute
+// accuracy at any grid size (see affine_frac below).
+struct AngleParams {
+    double c, s;        // cos, sin
+    // Ray-driven (Joseph) march, in the frame of the stepping axis:
+    //   f(j) = k * f0_k + f0_c + j * df   (fractional index along the fast axis)
+    double f0_k;        // d f0 / d bin
+    double f0_c;        // constant part
+    double df;          // step of f per step index
+    float df_hi, df_lo; // split of df
+    float wstep;        // h / max(|c|, |s|): path length per step
+    int rows;           // 1: step over rows y (|c| >= |s|), fast axis x; 0: transposed
+    // Pixel-driven footprint: bin coordinate t(i, j) = t0 + i * tA + j * tB
+    double t0, tA, tB;
+    float tA_hi, tA_lo, tB_hi, tB_lo;
+    float rfoot;        // half-width of the footprint in bins: mu h / db
+    float wfoot;        // footprint height h / mu
+    int frame;          // frame this angle belongs to
+    int pad_;
+};
+
+}  // namespace mof
+
+struct mof_problem {
+    int nx = 0, ny = 0, nt = 0, nb = 0, precision = MOF_FP32;
+    double h = 1.0, db = 1.0;
+    long long ns = 0, n = 0, m = 0, nv = 0;
+    int A = 0;                          // total number of angles
+    std::vector<int> na, aoff;          // host: angles per frame, offsets (nt+1)
+    mof::AngleParams *d_ang = nullptr;  // device [A]
+    int *d_aoff = nullptr;              // device [nt+1] first angle of each frame
+    int device = 0;
+    void *ws = nullptr;                 // solver workspace (solver.cu)
+    int timing = 0;
+    void *timer = nullptr;              // kernel-class timer (solver.cu)
+};
+
+namespace mof {
+
+// Operator launchers (ops_*.cu). Templated on the element type; `stream` is
+// the caller's stream. All return MOF_OK or a launch error.
+template <typename real> mof_status launch_project(const mof_problem *p, const real *u, real *uT_scratch, real *b, cudaStream_t st);
+template <typename real> mof_status launch_backproject(const mof_problem *p, const real *b, real *u, cudaStream_t st);
+template <typename real> mof_status launch_grad(const mof_problem *p, int nf, const real *u, real *g, cudaStream_t st);
+template <typename real> mof_status launch_gradT(const mof_problem *p, int nf, const real *g, real *u, cudaStream_t st);
+template <typename real> mof_status launch_flow(const mof_problem *p, const real *u, const real *s, const real *sr, real *r, cudaStream_t st);
+template <typename real> mof_status launch_window_radius(const mof_problem *p, const real *s, const real *sr, int *d_radius, cudaStream_t st);
+template <typename real> mof_status launch_flowT(const mof_problem *p, const real *r, const real *s, const real *sr, const int *d_radius, real *u, cudaStream_t st);
+template <typename real> mof_status launch_of_fields(const mof_problem *p, const real *u, int dr, real *ux, real *uy, real *ut, cudaStream_t st);
+template <typename real> mof_status launch_flow_lin(const mof_problem *p, const real *ux, const real *uy, const real *ut, const real *s, real *r, cudaStream_t st);
+template <typename real> mof_status launch_flow_linT(const mof_problem *p, const real *ux, const real *uy, const real *r, real *gs, cudaStream_t st);
+template <typename real> mof_status launch_reverse_flow(const mof_problem *p, const real *s, const int *d_radius, int *dest_scratch, real *sr, cudaStream_t st);
+// Weighted regulariser normal operator: y = y_add + scale * Theta^T W Theta x,
+// W from uk; q_scratch holds 2*(nt-1)*ns weighted flow rows. lam_dev (may be
+// null) multiplies `scale` by *lam_dev.
+template <typename real> mof_status launch_reg_normal(const mof_problem *p, const real *x, const real *uk, const real *s, const real *sr,
+                                                      const int *d_radius, double eps, double scale, const double *lam_dev, const real *y_add,
+                                                      real *q_scratch, real *y, cudaStream_t st);
+
+// ----------------------------------------------------------- device helpers
+template <typename T>
+__device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_maxf(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// floor and fraction of base + j * (hi + lo), base = ibase + fbase with
+// fbase in [0, 1): j * hi is exact for |j| < 4096, so the fraction carries
+// only the rounding of a sum of O(1) terms.
+__device__ __forceinline__ void affine_frac(int ibase, float fbase, float hi, float lo, int j,
+                                            int &ifl, float &frac) {
+    const float pj = (float)j * hi;  // exact
+    const float pf = floorf(pj);
+    const float r = fbase + (pj - pf) + (float)j * lo;
+    const float rf = floorf(r);
+    ifl = ibase + (int)pf + (int)rf;
+    frac = r - rf;
+}
+
+}  // namespace mof

@@ -1,0 +1,301 @@
+// K10: batched Krylov vector operations on B independent bases
+// (the outer image step has B = 1; Solve-OF has one basis per frame pair).
+//
+// A basis is stored as V[b][j][N] (vector j of problem b contiguous), with
+// the current size K[b] in device memory, so kernel grids never depend on
+// the basis size and a whole solver iteration can be replayed as a graph.
+//
+// Reductions (dot products, norms) are deterministic: products in the
+// storage precision, summed in a fixed tree within a chunk of CHUNK
+// elements, chunk partials written out and combined in FP64 in chunk order.
+#include "common.cuh"
+#include "solver.cuh"
+
+namespace mof {
+
+constexpr int KT = 256;                    // threads per block
+constexpr int KE = 8;                      // elements per thread per chunk
+constexpr int CHUNK = KT * KE;             // elements per chunk
+
+long long krylov_chunks(long long N) { return (N + CHUNK - 1) / CHUNK; }
+
+// block-wide sum of one value per thread into thread 0's return (FP64 across warps)
+template <typename acc_t>
+__device__ __forceinline__ double block_sum_to_double(acc_t v, double *sh) {
+    if constexpr (sizeof(acc_t) == 4) v = warp_sumf(v);
+    else v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = (double)v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < KT / 32; ++i) r += sh[i];
+    __syncthreads();
+    return r;
+}
+
+// partial[b][chunk][v][j] = sum_{i in chunk} V[b][j][i] * x_v[b][i], j < K[b], v < NV
+template <typename real, int NV>
+__global__ void __launch_bounds__(KT) k_mdot(const real *__restrict__ V, long long N, int Kmax, const int *__restrict__ K,
+                                             const int *__restrict__ act, DotVecs<real> xs, double *__restrict__ partial,
+                                             int nchunk) {
+    __shared__ real sw[NV][KT / 32][32];
+    const int b = blockIdx.y, chunk = blockIdx.x;
+    if (act && !act[b]) return;
+    const int Kb = min(K[b], Kmax);
+    const long long i0 = (long long)chunk * CHUNK + threadIdx.x;
+    const real *Vb = V + (long long)b * Kmax * N;
+    real xv[NV][KE];
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int e = 0; e < KE; ++e) {
+            const long long i = i0 + (long long)e * KT;
+            xv[v][e] = i < N ? xs.x[v][b * xs.stride[v] + i] : (real)0;
+        }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    for (int j0 = 0; j0 < Kb; j0 += 32) {
+        const int jn = min(32, Kb - j0);
+        for (int jj = 0; jj < jn; ++jj) {
+            const real *vj = Vb + (long long)(j0 + jj) * N;
+            real a[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) a[v] = 0;
+#pragma unroll
+            for (int e = 0; e < KE; ++e) {
+                const long long i = i0 + (long long)e * KT;
+                if (i < N) {
+                    const real vv = vj[i];
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) a[v] += vv * xv[v][e];
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                real t = a[v];
+                if constexpr (sizeof(real) == 4) t = warp_sumf(t);
+                else t = warp_sum(t);
+                if (l == 0) sw[v][w][jj] = t;
+            }
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < NV * jn; e += KT) {
+            const int v = e / jn, jj = e % jn;
+            double s = 0.0;
+#pragma unroll
+            for (int ww = 0; ww < KT / 32; ++ww) s += (double)sw[v][ww][jj];
+            partial[(((long long)b * nchunk + chunk) * NV + v) * Kmax + j0 + jj] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// out_v[b*bstride + i*istride + col*jstride] = sign * sum_chunk partial[b][chunk][v][i], i < K[b];
+// col = K[b] - 1 when last_col, else 0.
+__global__ void k_sum_chunks(const double *__restrict__ partial, int nchunk, int NV, int Kmax, const int *__restrict__ K,
+                             const int *__restrict__ act, DotOuts outs) {
+    const int b = blockIdx.x;
+    if (act && !act[b]) return;
+    const int Kb = min(K[b], Kmax);
+    for (int e = threadIdx.x; e < NV * Kb; e += blockDim.x) {
+        const int v = e / Kb, i = e % Kb;
+        const DotOut &o = outs.o[v];
+        if (!o.out) continue;
+        double s = 0.0;
+        for (int c = 0; c < nchunk; ++c) s += partial[(((long long)b * nchunk + c) * NV + v) * Kmax + i];
+        const long long col = o.last_col ? (long long)(Kb - 1) : 0;
+        o.out[b * o.bstride + (long long)i * o.istride + col * o.jstride] = o.sign * s;
+    }
+}
+
+// out[b] = sum_j V[b][j] c[b][j] (mode 0), x[b] - sum_j V[b][j] c[b][j] (mode 1),
+// sum_j V[b][j] c[b][j] - x[b] (mode 2); optionally ||out[b]||^2 per chunk.
+template <typename real, int MODE>
+__global__ void __launch_bounds__(KT) k_combine(const real *__restrict__ V, long long N, int Kmax, const int *__restrict__ K,
+                                                const int *__restrict__ act, const double *__restrict__ c, long long cstride,
+                                                const real *__restrict__ x, long long xstride, real *__restrict__ out,
+                                                long long ostride, double *__restrict__ nrm_partial, int nchunk) {
+    __shared__ real sc[64];
+    __shared__ double sh[KT / 32];
+    const int b = blockIdx.y, chunk = blockIdx.x;
+    if (act && !act[b]) return;
+    const int Kb = min(K[b], Kmax);
+    const long long i0 = (long long)chunk * CHUNK + threadIdx.x;
+    const real *Vb = V + (long long)b * Kmax * N;
+    real acc[KE];
+#pragma unroll
+    for (int e = 0; e < KE; ++e) acc[e] = 0;
+    for (int j0 = 0; j0 < Kb; j0 += 64) {
+        const int jn = min(64, Kb - j0);
+        __syncthreads();
+        if (threadIdx.x < jn) sc[threadIdx.x] = (real)c[b * cstride + j0 + threadIdx.x];
+        __syncthreads();
+        for (int jj = 0; jj < jn; ++jj) {
+            const real *vj = Vb + (long long)(j0 + jj) * N;
+            const real cj = sc[jj];
+#pragma unroll
+            for (int e = 0; e < KE; ++e) {
+                const long long i = i0 + (long long)e * KT;
+                if (i < N) acc[e] += vj[i] * cj;
+            }
+        }
+    }
+    real n2 = 0;
+#pragma unroll
+    for (int e = 0; e < KE; ++e) {
+        const long long i = i0 + (long long)e * KT;
+        if (i < N) {
+            const real v = MODE == 1 ? x[b * xstride + i] - acc[e] : (MODE == 2 ? acc[e] - x[b * xstride + i] : acc[e]);
+            out[b * ostride + i] = v;
+            n2 += v * v;
+        }
+    }
+    if (nrm_partial) {
+        const double s = block_sum_to_double(n2, sh);
+        if (threadIdx.x == 0) nrm_partial[(long long)b * nchunk + chunk] = s;
+    }
+}
+
+// ||x[b]||^2 per chunk
+template <typename real>
+__global__ void __launch_bounds__(KT) k_norm2(const real *__restrict__ x, long long N, long long xstride,
+                                              double *__restrict__ partial, int nchunk) {
+    __shared__ double sh[KT / 32];
+    const int b = blockIdx.y, chunk = blockIdx.x;
+    const long long i0 = (long long)chunk * CHUNK + threadIdx.x;
+    real n2 = 0;
+#pragma unroll
+    for (int e = 0; e < KE; ++e) {
+        const long long i = i0 + (long long)e * KT;
+        if (i < N) {
+            const real v = x[b * xstride + i];
+            n2 += v * v;
+        }
+    }
+    const double s = block_sum_to_double(n2, sh);
+    if (threadIdx.x == 0) partial[(long long)b * nchunk + chunk] = s;
+}
+
+__global__ void k_sum_scalar_chunks(const double *__restrict__ partial, int nchunk, double *__restrict__ out, int B) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    double s = 0.0;
+    for (int c = 0; c < nchunk; ++c) s += partial[(long long)b * nchunk + c];
+    out[b] = s;
+}
+
+// Append x[b] / ||x[b]|| as vector K[b] when ||x[b]|| > tol * scale[b] and the
+// problem is still growing (scale == null: only ||x|| > 0 is required); the
+// new vector is also written to stage[b] when stage != null.
+__device__ __forceinline__ bool append_ok(int grow, int Kb, int Kmax, double nrm2, const double *scale, int b, double tol) {
+    const double nr = sqrt(nrm2);
+    const double sc = scale ? scale[b] : 0.0;
+    return grow && Kb < Kmax && (nr > tol * sc) && (nr > 0.0) && isfinite(nr);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(KT) k_append(real *__restrict__ V, long long N, int Kmax, const int *__restrict__ K,
+                                               const real *__restrict__ x, long long xstride, const double *__restrict__ nrm2,
+                                               const double *__restrict__ scale, double tol, const int *__restrict__ grow,
+                                               real *__restrict__ stage) {
+    const int b = blockIdx.y;
+    const int Kb = K[b];
+    if (!append_ok(grow[b], Kb, Kmax, nrm2[b], scale, b, tol)) return;
+    const real inv = (real)(1.0 / sqrt(nrm2[b]));
+    real *vd = V + ((long long)b * Kmax + Kb) * N;
+    for (long long i = blockIdx.x * (long long)KT + threadIdx.x; i < N; i += (long long)gridDim.x * KT) {
+        const real v = x[b * xstride + i] * inv;
+        vd[i] = v;
+        if (stage) stage[b * N + i] = v;
+    }
+}
+
+// Commit the append: K[b] += 1 where k_append wrote, else clear grow[b].
+__global__ void k_commit(int *__restrict__ K, int Kmax, const double *__restrict__ nrm2, const double *__restrict__ scale,
+                         double tol, int *__restrict__ grow, int B, int *__restrict__ appended) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const int ok = append_ok(grow[b], K[b], Kmax, nrm2[b], scale, b, tol);
+    if (ok) K[b] += 1;
+    else grow[b] = 0;
+    if (appended) appended[b] = ok;
+}
+
+// ------------------------------------------------------------ host launchers
+template <typename real>
+void Krylov<real>::dots(const BasisRef<real> &B, const real *x, long long xstride, double *out, long long ostride, double sign,
+                        cudaStream_t st) const {
+    DotVecs<real> xs{};
+    xs.x[0] = x;
+    xs.stride[0] = xstride;
+    DotOuts o{};
+    o.o[0] = DotOut{out, ostride, 1, 0, 0, sign};
+    multidot(B, 1, xs, o, st);
+}
+
+template <typename real>
+void Krylov<real>::multidot(const BasisRef<real> &B, int nv, const DotVecs<real> &xs, const DotOuts &outs,
+                            cudaStream_t st) const {
+    const int nc = (int)krylov_chunks(B.N);
+    const dim3 grid(nc, B.B);
+    if (nv == 1) k_mdot<real, 1><<<grid, KT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, xs, partial, nc);
+    else if (nv == 2) k_mdot<real, 2><<<grid, KT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, xs, partial, nc);
+    else k_mdot<real, 3><<<grid, KT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, xs, partial, nc);
+    k_sum_chunks<<<B.B, 128, 0, st>>>(partial, nc, nv, B.Kmax, B.K, B.act, outs);
+}
+
+template <typename real>
+void Krylov<real>::combine(const BasisRef<real> &B, const double *c, long long cstride, real *out, long long ostride,
+                           cudaStream_t st) const {
+    const int nc = (int)krylov_chunks(B.N);
+    k_combine<real, 0><<<dim3(nc, B.B), KT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, c, cstride, nullptr, 0, out, ostride, nullptr,
+                                                     nc);
+}
+
+template <typename real>
+void Krylov<real>::combine_minus(const BasisRef<real> &B, const double *c, long long cstride, const real *x, long long xstride,
+                                 real *out, long long ostride, double *nrm2_out, cudaStream_t st) const {
+    const int nc = (int)krylov_chunks(B.N);
+    k_combine<real, 2><<<dim3(nc, B.B), KT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, c, cstride, x, xstride, out, ostride,
+                                                     nrm2_out ? partial : nullptr, nc);
+    if (nrm2_out) k_sum_scalar_chunks<<<(B.B + 63) / 64, 64, 0, st>>>(partial, nc, nrm2_out, B.B);
+}
+
+template <typename real>
+void Krylov<real>::subtract(const BasisRef<real> &B, const double *c, long long cstride, const real *x, long long xstride,
+                            real *out, long long ostride, double *nrm2_out, cudaStream_t st) const {
+    const int nc = (int)krylov_chunks(B.N);
+    k_combine<real, 1><<<dim3(nc, B.B), KT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, c, cstride, x, xstride, out, ostride,
+                                                     nrm2_out ? partial : nullptr, nc);
+    if (nrm2_out) k_sum_scalar_chunks<<<(B.B + 63) / 64, 64, 0, st>>>(partial, nc, nrm2_out, B.B);
+}
+
+template <typename real>
+void Krylov<real>::norm2(const real *x, long long N, long long xstride, int nb, double *out, cudaStream_t st) const {
+    const int nc = (int)krylov_chunks(N);
+    k_norm2<real><<<dim3(nc, nb), KT, 0, st>>>(x, N, xstride, partial, nc);
+    k_sum_scalar_chunks<<<(nb + 63) / 64, 64, 0, st>>>(partial, nc, out, nb);
+}
+
+template <typename real>
+void Krylov<real>::reorth(const BasisRef<real> &B, real *x, long long xstride, double *coef, double *nrm2_out,
+                          cudaStream_t st) const {
+    // classical Gram-Schmidt against V, twice (CGS2); coef is [B][Kmax] scratch
+    dots(B, x, xstride, coef, B.Kmax, 1.0, st);
+    subtract(B, coef, B.Kmax, x, xstride, x, xstride, nullptr, st);
+    dots(B, x, xstride, coef, B.Kmax, 1.0, st);
+    subtract(B, coef, B.Kmax, x, xstride, x, xstride, nrm2_out, st);
+}
+
+template <typename real>
+void Krylov<real>::append(const BasisRef<real> &B, int *Kmut, const real *x, long long xstride, const double *nrm2,
+                          const double *scale, double tol, int *grow, int *appended, real *stage, cudaStream_t st) const {
+    const int blocks = (int)std::min<long long>(1024, (B.N + KT - 1) / KT);
+    k_append<real><<<dim3(blocks, B.B), KT, 0, st>>>(B.V, B.N, B.Kmax, B.K, x, xstride, nrm2, scale, tol, grow, stage);
+    k_commit<<<(B.B + 63) / 64, 64, 0, st>>>(Kmut, B.Kmax, nrm2, scale, tol, grow, B.B, appended);
+}
+
+template struct Krylov<float>;
+template struct Krylov<double>;
+
+}  // namespace mof

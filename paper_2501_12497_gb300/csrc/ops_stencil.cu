@@ -1,0 +1,468 @@
+// Stencil and flow operators of MMGKS-OF:
+//   K3  Psi / Psi^T            forward differences of every frame (eq. (L))
+//   K4  Mhat / Mhat^T          bilinear temporal warp rows (Sec. 3, Sec. 4)
+//   K5  Theta^T W Theta        IRLS-weighted regulariser normal operator (Alg. 1)
+//   K6  reverse flow           s' from s (remark of Sec. 3)
+//   K7  App. C derivative fields u_x, u_y, u_t
+//   K8  Upsilon s + u_t, Upsilon^T r (Sec. 2.2)
+//
+// The transposes of the warp are computed as deterministic gathers: an output
+// pixel q collects the contributions of the sources p within a window of
+// radius R = floor(max |s|) + 1 around q (a source can only reach the four
+// pixels around r + s(r), and clipping only moves the sample towards r), in
+// a fixed order, so repeated runs are bit-identical.
+#include "common.cuh"
+
+#include <cfloat>
+
+namespace mof {
+
+namespace {
+
+constexpr int TX = 32, TY = 8;
+
+inline dim3 grid2d(int nx, int ny, int nz) { return dim3((nx + TX - 1) / TX, (ny + TY - 1) / TY, nz); }
+
+// Sample coordinate of M(s) along one axis: X = clamp(x + v, 0, n - 1),
+// i0 = floor(X), i1 = min(i0 + 1, n - 1), w = X - i0. The fraction is taken
+// from v itself (v - floor(v) is exact), so the weights do not lose bits to
+// the magnitude of x.
+template <typename real>
+__device__ __forceinline__ void warp_axis(int x, real v, int n, int &i0, int &i1, real &w) {
+    const real vc = v > (real)16777216 ? (real)16777216 : (v < (real)-16777216 ? (real)-16777216 : v);
+    const real fv = floor(vc);
+    const int I = x + (int)fv;
+    if (I < 0) {
+        i0 = 0; w = 0;
+    } else if (I >= n - 1) {
+        i0 = n - 1; w = 0;
+    } else {
+        i0 = I; w = vc - fv;
+    }
+    if (!(v == v)) { i0 = x; w = 0; }  // NaN velocity: identity sample (flagged elsewhere)
+    i1 = min(i0 + 1, n - 1);
+}
+
+template <typename real>
+__device__ __forceinline__ real bilinear(const real *__restrict__ f, int nx, int ny, int x, int y, real vx, real vy) {
+    int x0, x1, y0, y1;
+    real wx, wy;
+    warp_axis(x, vx, nx, x0, x1, wx);
+    warp_axis(y, vy, ny, y0, y1, wy);
+    const real a = ldg(f + (long long)y0 * nx + x0), b = ldg(f + (long long)y0 * nx + x1);
+    const real c = ldg(f + (long long)y1 * nx + x0), d = ldg(f + (long long)y1 * nx + x1);
+    const real top = (1 - wx) * a + wx * b, bot = (1 - wx) * c + wx * d;
+    return (1 - wy) * top + wy * bot;
+}
+
+// Weight with which the source pixel (px, py), sampling at r + s(r), reaches
+// the pixel (qx, qy): the transposed bilinear weight.
+template <typename real>
+__device__ __forceinline__ real warp_weight_to(int px, int py, real vx, real vy, int nx, int ny, int qx, int qy) {
+    int x0, x1, y0, y1;
+    real wx, wy;
+    warp_axis(px, vx, nx, x0, x1, wx);
+    warp_axis(py, vy, ny, y0, y1, wy);
+    const real ax = (qx == x0 ? 1 - wx : (real)0) + (qx == x1 ? wx : (real)0);
+    const real ay = (qy == y0 ? 1 - wy : (real)0) + (qy == y1 ? wy : (real)0);
+    return ax * ay;
+}
+
+// (M(v)^T r)(q) by a gather over the window of radius R around q.
+template <typename real>
+__device__ __forceinline__ real warpT_gather(const real *__restrict__ r, const real *__restrict__ vx,
+                                             const real *__restrict__ vy, int nx, int ny, int qx, int qy, int R) {
+    real acc = 0;
+    const int ylo = max(0, qy - R), yhi = min(ny - 1, qy + R);
+    const int xlo = max(0, qx - R), xhi = min(nx - 1, qx + R);
+    for (int py = ylo; py <= yhi; ++py) {
+        for (int px = xlo; px <= xhi; ++px) {
+            const long long i = (long long)py * nx + px;
+            const real w = warp_weight_to(px, py, ldg(vx + i), ldg(vy + i), nx, ny, qx, qy);
+            if (w != (real)0) acc += w * ldg(r + i);
+        }
+    }
+    return acc;
+}
+
+}  // namespace
+
+// =================================================================== K3 Psi
+template <typename real>
+__global__ void k_grad(const real *__restrict__ u, real *__restrict__ g, int nx, int ny) {
+    const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, t = blockIdx.z;
+    if (x >= nx || y >= ny) return;
+    const long long ns = (long long)nx * ny, i = (long long)y * nx + x;
+    const real *f = u + t * ns;
+    const real c = f[i];
+    g[(2LL * t) * ns + i] = (x < nx - 1) ? f[i + 1] - c : (real)0;
+    g[(2LL * t + 1) * ns + i] = (y < ny - 1) ? f[i + nx] - c : (real)0;
+}
+
+template <typename real>
+__global__ void k_gradT(const real *__restrict__ g, real *__restrict__ u, int nx, int ny) {
+    const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, t = blockIdx.z;
+    if (x >= nx || y >= ny) return;
+    const long long ns = (long long)nx * ny, i = (long long)y * nx + x;
+    const real *gx = g + (2LL * t) * ns, *gy = g + (2LL * t + 1) * ns;
+    real v = 0;
+    if (x > 0) v += gx[i - 1];
+    if (x < nx - 1) v -= gx[i];
+    if (y > 0) v += gy[i - nx];
+    if (y < ny - 1) v -= gy[i];
+    u[t * ns + i] = v;
+}
+
+template <typename real>
+mof_status launch_grad(const mof_problem *p, int nf, const real *u, real *g, cudaStream_t st) {
+    k_grad<real><<<grid2d(p->nx, p->ny, nf), dim3(TX, TY), 0, st>>>(u, g, p->nx, p->ny);
+    MOF_LAUNCH_CHECK();
+    return MOF_OK;
+}
+template <typename real>
+mof_status launch_gradT(const mof_problem *p, int nf, const real *g, real *u, cudaStream_t st) {
+    k_gradT<real><<<grid2d(p->nx, p->ny, nf), dim3(TX, TY), 0, st>>>(g, u, p->nx, p->ny);
+    MOF_LAUNCH_CHECK();
+    return MOF_OK;
+}
+
+// ================================================================= K4 Mhat
+template <typename real>
+__global__ void k_flow(const real *__restrict__ u, const real *__restrict__ s, const real *__restrict__ sr,
+                       real *__restrict__ r, int nx, int ny, int np) {
+    const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, p = blockIdx.z;
+    if (x >= nx || y >= ny) return;
+    const long long ns = (long long)nx * ny, i = (long long)y * nx + x;
+    const real *u0 = u + p * ns, *u1 = u0 + ns;
+    const real *sp = s + 2LL * p * ns, *srp = sr + 2LL * p * ns;
+    r[p * ns + i] = u0[i] - bilinear(u1, nx, ny, x, y, sp[i], sp[ns + i]);
+    r[(np + p) * ns + i] = u1[i] - bilinear(u0, nx, ny, x, y, srp[i], srp[ns + i]);
+}
+
+template <typename real>
+mof_status launch_flow(const mof_problem *p, const real *u, const real *s, const real *sr, real *r, cudaStream_t st) {
+    const int np = p->nt - 1;
+    k_flow<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(u, s, sr, r, p->nx, p->ny, np);
+    MOF_LAUNCH_CHECK();
+    return MOF_OK;
+}
+
+// Window radius for the transposes: R = floor(max |v|) + 1 over the given
+// fields (sr may be null), as an int written to *d_radius. A non-finite
+// velocity sets R = -1 (the gathers then treat the warp as the identity and
+// the solver reports MOF_ENUMERIC).
+template <typename real>
+__global__ void k_absmax(const real *__restrict__ a, long long n, unsigned *__restrict__ out) {
+    float m = 0.0f;
+    bool bad = false;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const real v = a[i];
+        if (!(v == v) || v > (real)FLT_MAX || v < -(real)FLT_MAX) bad = true;
+        else m = fmaxf(m, (float)fabs((double)v));
+    }
+    m = warp_maxf(m);
+    const unsigned badw = __any_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0) atomicMax(out, badw ? 0x7f800000u : __float_as_uint(m));
+}
+
+__global__ void k_radius_finish(const unsigned *__restrict__ bits, int *__restrict__ radius, int cap) {
+    const unsigned b = bits[0];
+    if (b >= 0x7f800000u) { *radius = -1; return; }
+    const float m = __uint_as_float(b);
+    *radius = (int)fminf(floorf(m) + 1.0f, (float)cap);
+}
+
+__global__ void k_zero_u32(unsigned *p) { *p = 0u; }
+
+template <typename real>
+mof_status launch_window_radius(const mof_problem *p, const real *s, const real *sr, int *d_radius, cudaStream_t st) {
+    // the int slot right after *d_radius holds the running max bits
+    unsigned *bits = reinterpret_cast<unsigned *>(d_radius + 1);
+    k_zero_u32<<<1, 1, 0, st>>>(bits);
+    MOF_LAUNCH_CHECK();
+    const long long nv = p->nv;
+    const int blocks = (int)std::min<long long>(1184, (nv + 255) / 256);
+    k_absmax<real><<<blocks, 256, 0, st>>>(s, nv, bits);
+    MOF_LAUNCH_CHECK();
+    if (sr) {
+        k_absmax<real><<<blocks, 256, 0, st>>>(sr, nv, bits);
+        MOF_LAUNCH_CHECK();
+    }
+    k_radius_finish<<<1, 1, 0, st>>>(bits, d_radius, std::max(p->nx, p->ny));
+    MOF_LAUNCH_CHECK();
+    return MOF_OK;
+}
+
+// u = Mhat^T r (+ optional addend, times scale), one thread per pixel of a frame:
+//   u_t = [t<P] r0_t + [t>0] r1_{t-1} - [t<P] M(sr_t)^T r1_t - [t>0] M(s_{t-1})^T r0_{t-1}
+template <typename real>
+__device__ __forceinline__ real flowT_at(const real *__restrict__ r, const real *__restrict__ s,
+                                         const real *__restrict__ sr, int nx, int ny, int np, int t,
+                                         int x, int y, int R) {
+    const long long ns = (long long)nx * ny, i = (long long)y * nx + x;
+    const int Rw = R < 0 ? 0 : R;
+    real v = 0;
+    if (t < np) {
+        const real *r1 = r + (np + t) * ns;
+        const real *srp = sr + 2LL * t * ns;
+        v += r[t * ns + i];
+        v -= R < 0 ? r1[i] : warpT_gather(r1, srp, srp + ns, nx, ny, x, y, Rw);
+    }
+    if (t > 0) {
+        const real *r0 = r + (long long)(t - 1) * ns;
+        const real *sp = s + 2LL * (t - 1) * ns;
+        v += r[(np + t - 1) * ns + i];
+        v -= R < 0 ? r0[i] : warpT_gather(r0, sp, sp + ns, nx, ny, x, y, Rw);
+    }
+    return v;
+}
+
+template <typename real>
+__global__ void k_flowT(const real *__restrict__ r, const real *__restrict__ s, const real *__restrict__ sr,
+                        const int *__restrict__ radius, real *__restrict__ u, int nx, int ny, int np) {
+    const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, t = blockIdx.z;
+    if (x >= nx || y >= ny) return;
+    const int R = *radius;
+    u[(long long)t * nx * ny + (long long)y * nx + x] = flowT_at(r, s, sr, nx, ny, np, t, x, y, R);
+}
+
+template <typename real>
+mof_status launch_flowT(const mof_problem *p, const real *r, const real *s, const real *sr, const int *d_radius, real *u,
+                        cudaStream_t st) {
+    k_flowT<real><<<grid2d(p->nx, p->ny, p->nt), dim3(TX, TY), 0, st>>>(r, s, sr, d_radius, u, p->nx, p->ny, p->nt - 1);
+    MOF_LAUNCH_CHECK();
+    return MOF_OK;
+}
+
+// ============================================================ K6 reverse flow
+// Destination of each source pixel, round half away from zero of r + s(r),
+// clipped. With v = fv + fr (fv = floor(v), fr in [0,1) exact) and
+// I = x + fv: for I >= 0 the position is >= 0 and rounds up iff fr >= 1/2;
+// for I < 0 it is negative and rounds up (towards zero) iff fr > 1/2. This
+// takes the decision exactly, as an FP64 evaluation of x + v would.
+template <typename real>
+__device__ __forceinline__ int round_axis(int x, real v, int n) {
+    const real vc = v > (real)16777216 ? (real)16777216 : (v < (real)-16777216 ? (real)-16777216 : v);
+    const real fv = floor(vc);
+    const real fr = vc - fv;
+    int I = x + (int)fv;
+    if (I >= 0) I += (fr >= (real)0.5) ? 1 : 0;
+    else I += (fr > (real)0.5) ? 1 : 0;
+    if (!(v == v)) I = x;
+    return I < 0 ? 0 : (I > n - 1 ? n - 1 : I);
+}
+
+template <typename real>
+__global__ void k_rev_dest(const real *__restrict__ s, int *__restrict__ dest, int nx, int ny) {
+    const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, p = blockIdx.z;
+    if (x >= nx || y >= ny) return;
+    const long long ns = (long long)nx * ny, i = (long long)y * nx + x;
+    const real *sp = s + 2LL * p * ns;
+    const int dx = round_axis(x, sp[i], nx), dy = round_axis(y, sp[ns + i], ny);
+    dest[p * ns + i] = dy * nx + dx;
+}
+
+template <typename real>
+__global__ void k_rev_gather(const real *__restrict__ s, const int *__restrict__ dest, const int *__restrict__ radius,
+                             real *__restrict__ sr, int nx, int ny) {
+    const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, p = blockIdx.z;
+    if (x >= nx || y >= ny) return;
+    const long long ns = (long long)nx * ny, q = (long long)y * nx + x;
+    const real *sx = s + 2LL * p * ns, *sy = sx + ns;
+    const int *dp = dest + p * ns;
+    const int R = max(*radius, 0);
+    double ax = 0.0, ay = 0.0;
+    int cnt = 0;
+    // sources in row-major order, as the arrivals are accumulated in order of source
+    const int ylo = max(0, y - R), yhi = min(ny - 1, y + R);
+    const int xlo = max(0, x - R), xhi = min(nx - 1, x + R);
+    for (int py = ylo; py <= yhi; ++py)
+        for (int px = xlo; px <= xhi; ++px) {
+            const long long i = (long long)py * nx + px;
+            if (ldg(dp + i) == (int)q) {
+                ax -= (double)ldg(sx + i);
+                ay -= (double)ldg(sy + i);
+                ++cnt;
+            }
+        }
+    real *rx = sr + 2LL * p * ns, *ry = rx + ns;
+    rx[q] = cnt ? (real)(ax / cnt) : (real)0;
+    ry[q] = cnt ? (real)(ay / cnt) : (real)0;
+}
+
+template <typename real>
+mof_status launch_reverse_flow(const mof_problem *p, const real *s, const int *d_radius, int *dest, real *sr, cudaStream_t st) {
+    const int np = p->nt - 1;
+    k_rev_dest<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(s, dest, p->nx, p->ny);
+    MOF_LAUNCH_CHECK();
+    k_rev_gather<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(s, dest, d_radius, sr, p->nx, p->ny);
+    MOF_LAUNCH_CHECK();
+    return MOF_OK;
+}
+
+// ============================================================ K7 App. C fields
+__device__ __forceinline__ int reflect_idx(int i, int n) {
+    while (i < 0 || i >= n) {
+        if (i < 0) i = -i - 1;
+        if (i >= n) i = 2 * n - 1 - i;
+    }
+    return i;
+}
+
+template <typename real>
+__global__ void k_of_fields(const real *__restrict__ u, int dr, real *__restrict__ ux, real *__restrict__ uy,
+                            real *__restrict__ ut, int nx, int ny) {
+    const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, p = blockIdx.z;
+    if (x >= nx || y >= ny) return;
+    const long long ns = (long long)nx * ny;
+    const real *a = u + p * ns, *b = a + ns;
+    const real inv2 = (real)1 / (real)(2 * dr), box = (real)(2 * dr + 1);
+    const int xp = reflect_idx(x + dr, nx), xm = reflect_idx(x - dr, nx);
+    const int yp = reflect_idx(y + dr, ny), ym = reflect_idx(y - dr, ny);
+    real sx = 0, sy = 0, st = 0;
+    for (int k = -dr; k <= dr; ++k) {
+        const int yk = reflect_idx(y + k, ny), xk = reflect_idx(x + k, nx);
+        sx += (ldg(a + (long long)yk * nx + xp) - ldg(a + (long long)yk * nx + xm)) * inv2;
+        sy += (ldg(a + (long long)yp * nx + xk) - ldg(a + (long long)ym * nx + xk)) * inv2;
+        for (int j = -dr; j <= dr; ++j) {
+            const long long q = (long long)yk * nx + reflect_idx(x + j, nx);
+            st += ldg(b + q) - ldg(a + q);
+        }
+    }
+    const long long i = p * ns + (long long)y * nx + x;
+    ux[i] = sx / box;
+    uy[i] = sy / box;
+    ut[i] = st / (box * box);
+}
+
+template <typename real>
+mof_status launch_of_fields(const mof_problem *p, const real *u, int dr, real *ux, real *uy, real *ut, cudaStream_t st) {
+    k_of_fields<real><<<grid2d(p->nx, p->ny, p->nt - 1), dim3(TX, TY), 0, st>>>(u, dr, ux, uy, ut, p->nx, p->ny);
+    MOF_LAUNCH_CHECK();
+    return MOF_OK;
+}
+
+// ================================================================ K8 Upsilon
+template <typename real>
+__global__ void k_flow_lin(const real *__restrict__ ux, const real *__restrict__ uy, const real *__restrict__ ut,
+                           const real *__restrict__ s, real *__restrict__ r, long long ns, long long total) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total; q += (long long)gridDim.x * blockDim.x) {
+        const long long p = q / ns, i = q - p * ns;
+        r[q] = ux[q] * s[2 * p * ns + i] + uy[q] * s[(2 * p + 1) * ns + i] + ut[q];
+    }
+}
+
+template <typename real>
+__global__ void k_flow_linT(const real *__restrict__ ux, const real *__restrict__ uy, const real *__restrict__ r,
+                            real *__restrict__ gs, long long ns, long long total) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total; q += (long long)gridDim.x * blockDim.x) {
+        const long long p = q / ns, i = q - p * ns;
+        gs[2 * p * ns + i] = ux[q] * r[q];
+        gs[(2 * p + 1) * ns + i] = uy[q] * r[q];
+    }
+}
+
+inline int flat_blocks(long long total) { return (int)std::min<long long>(152LL * 16, (total + 255) / 256); }
+
+template <typename real>
+mof_status launch_flow_lin(const mof_problem *p, const real *ux, const real *uy, const real *ut, const real *s, real *r,
+                           cudaStream_t st) {
+    const long long total = (long long)(p->nt - 1) * p->ns;
+    k_flow_lin<real><<<flat_blocks(total), 256, 0, st>>>(ux, uy, ut, s, r, p->ns, total);
+    MOF_LAUNCH_CHECK();
+    return MOF_OK;
+}
+template <typename real>
+mof_status launch_flow_linT(const mof_problem *p, const real *ux, const real *uy, const real *r, real *gs, cudaStream_t st) {
+    const long long total = (long long)(p->nt - 1) * p->ns;
+    k_flow_linT<real><<<flat_blocks(total), 256, 0, st>>>(ux, uy, r, gs, p->ns, total);
+    MOF_LAUNCH_CHECK();
+    return MOF_OK;
+}
+
+// ============================================================ K5 Theta^T W Theta
+// Stage 1: q = W_M (Mhat x), W_M = ((Mhat uk)^2 + eps^2)^(-1/2), per flow row.
+template <typename real>
+__global__ void k_regn_flow_rows(const real *__restrict__ x, const real *__restrict__ uk, const real *__restrict__ s,
+                                 const real *__restrict__ sr, real eps2, real *__restrict__ q, int nx, int ny, int np) {
+    const int xx = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, p = blockIdx.z;
+    if (xx >= nx || y >= ny) return;
+    const long long ns = (long long)nx * ny, i = (long long)y * nx + xx;
+    const real *sp = s + 2LL * p * ns, *srp = sr + 2LL * p * ns;
+    const real svx = sp[i], svy = sp[ns + i], rvx = srp[i], rvy = srp[ns + i];
+    const real *x0 = x + p * ns, *x1 = x0 + ns, *k0 = uk + p * ns, *k1 = k0 + ns;
+    const real fx = x0[i] - bilinear(x1, nx, ny, xx, y, svx, svy);
+    const real fk = k0[i] - bilinear(k1, nx, ny, xx, y, svx, svy);
+    const real bx = x1[i] - bilinear(x0, nx, ny, xx, y, rvx, rvy);
+    const real bk = k1[i] - bilinear(k0, nx, ny, xx, y, rvx, rvy);
+    q[p * ns + i] = fx / sqrt(fk * fk + eps2);
+    q[(np + p) * ns + i] = bx / sqrt(bk * bk + eps2);
+}
+
+// Stage 2: y = y_add + scale * (Psi^T W_Psi Psi x + Mhat^T q).
+template <typename real>
+__global__ void k_regn_apply(const real *__restrict__ x, const real *__restrict__ uk, const real *__restrict__ s,
+                             const real *__restrict__ sr, const real *__restrict__ q, const int *__restrict__ radius,
+                             real eps2, double scale, const double *__restrict__ lam, const real *__restrict__ y_add,
+                             real *__restrict__ y, int nx, int ny, int np) {
+    const int xx = blockIdx.x * TX + threadIdx.x, yy = blockIdx.y * TY + threadIdx.y, t = blockIdx.z;
+    if (xx >= nx || yy >= ny) return;
+    const long long ns = (long long)nx * ny, i = (long long)yy * nx + xx;
+    const real *f = x + t * ns, *k = uk + t * ns;
+    // weighted differences d(i) = w(i) * (f(i+e) - f(i)), w from uk
+    auto wdx = [&](long long j) -> real {
+        const real g = f[j + 1] - f[j], gk = k[j + 1] - k[j];
+        return g / sqrt(gk * gk + eps2);
+    };
+    auto wdy = [&](long long j) -> real {
+        const real g = f[j + nx] - f[j], gk = k[j + nx] - k[j];
+        return g / sqrt(gk * gk + eps2);
+    };
+    real v = 0;
+    if (xx > 0) v += wdx(i - 1);
+    if (xx < nx - 1) v -= wdx(i);
+    if (yy > 0) v += wdy(i - nx);
+    if (yy < ny - 1) v -= wdy(i);
+    if (np > 0) v += flowT_at(q, s, sr, nx, ny, np, t, xx, yy, *radius);
+    const double sc = lam ? scale * *lam : scale;
+    const real out = (real)sc * v;
+    y[t * ns + i] = y_add ? y_add[t * ns + i] + out : out;
+}
+
+template <typename real>
+mof_status launch_reg_normal(const mof_problem *p, const real *x, const real *uk, const real *s, const real *sr,
+                             const int *d_radius, double eps, double scale, const double *lam_dev, const real *y_add,
+                             real *q, real *y, cudaStream_t st) {
+    const int np = p->nt - 1;
+    const real eps2 = (real)(eps * eps);
+    if (np > 0) {
+        k_regn_flow_rows<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(x, uk, s, sr, eps2, q, p->nx, p->ny, np);
+        MOF_LAUNCH_CHECK();
+    }
+    k_regn_apply<real><<<grid2d(p->nx, p->ny, p->nt), dim3(TX, TY), 0, st>>>(x, uk, s, sr, q, d_radius, eps2, scale, lam_dev,
+                                                                            y_add, y, p->nx, p->ny, np);
+    MOF_LAUNCH_CHECK();
+    return MOF_OK;
+}
+
+#define MOF_INST(real)                                                                                                        \
+    template mof_status launch_grad<real>(const mof_problem *, int, const real *, real *, cudaStream_t);                      \
+    template mof_status launch_gradT<real>(const mof_problem *, int, const real *, real *, cudaStream_t);                     \
+    template mof_status launch_flow<real>(const mof_problem *, const real *, const real *, const real *, real *, cudaStream_t); \
+    template mof_status launch_window_radius<real>(const mof_problem *, const real *, const real *, int *, cudaStream_t);     \
+    template mof_status launch_flowT<real>(const mof_problem *, const real *, const real *, const real *, const int *, real *, \
+                                           cudaStream_t);                                                                     \
+    template mof_status launch_reverse_flow<real>(const mof_problem *, const real *, const int *, int *, real *, cudaStream_t); \
+    template mof_status launch_of_fields<real>(const mof_problem *, const real *, int, real *, real *, real *, cudaStream_t);   \
+    template mof_status launch_flow_lin<real>(const mof_problem *, const real *, const real *, const real *, const real *,     \
+                                              real *, cudaStream_t);                                                          \
+    template mof_status launch_flow_linT<real>(const mof_problem *, const real *, const real *, const real *, real *,          \
+                                               cudaStream_t);                                                                 \
+    template mof_status launch_reg_normal<real>(const mof_problem *, const real *, const real *, const real *, const real *,   \
+                                                const int *, double, double, const double *, const real *, real *, real *,    \
+                                                cudaStream_t);
+
+MOF_INST(float)
+MOF_INST(double)
+
+}  // namespace mof

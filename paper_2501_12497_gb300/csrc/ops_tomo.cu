@@ -1,0 +1,186 @@
+// K1 ray-driven Joseph projector b = H u and K2 pixel-driven exact transpose
+// u = H^T b (Sec. 2.1: H = blockdiag(H^1..H^nt), 2D parallel beam).
+//
+// Both evaluate the same matrix entry
+//     a(theta, k; i, j) = (h/mu) * max(0, 1 - |sigma_k - p_ij| / (mu h)),
+//     p_ij = x_i cos(theta) + y_j sin(theta),  mu = max(|cos|, |sin|),
+// K1 from the ray side (march over the axis the ray is least inclined to,
+// two linear-interpolation taps per step, weight h/mu), K2 from the pixel
+// side (the <= 2 bins within mu*h of p_ij), so <H u, b> = <u, H^T b> holds to
+// rounding.
+#include "common.cuh"
+
+namespace mof {
+
+// --------------------------------------------------------------- transpose
+// uT[t][x][y] = u[t][y][x], 32x32 tiles through shared memory.
+template <typename real>
+__global__ void k_transpose(const real *__restrict__ u, real *__restrict__ uT, int nx, int ny) {
+    __shared__ real tile[32][33];
+    const long long off = (long long)blockIdx.z * nx * ny;
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+    for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+        const int x = x0 + threadIdx.x, y = y0 + dy;
+        if (x < nx && y < ny) tile[dy][threadIdx.x] = u[off + (long long)y * nx + x];
+    }
+    __syncthreads();
+    for (int dx = threadIdx.y; dx < 32; dx += blockDim.y) {
+        const int y = y0 + threadIdx.x, x = x0 + dx;
+        if (x < nx && y < ny) uT[off + (long long)x * ny + y] = tile[threadIdx.x][dx];
+    }
+}
+
+// -------------------------------------------------------------- K1 project
+// One thread per ray (angle a = blockIdx.y, bin k). Rays of one warp are 32
+// adjacent bins of one angle, so at each step they read adjacent pixels of
+// one image row (of the transposed frame for steep angles): coalesced.
+template <typename real>
+__global__ void __launch_bounds__(128) k_project(const real *__restrict__ u, const real *__restrict__ uT,
+                                                 real *__restrict__ b, const AngleParams *__restrict__ ang,
+                                                 int nx, int ny, int nb) {
+    const int a = blockIdx.y;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nb) return;
+    const AngleParams &P = ang[a];
+    const long long ns = (long long)nx * ny;
+    const int rows = P.rows;
+    const real *img = rows ? u + P.frame * ns : uT + P.frame * ns;
+    const int nfast = rows ? nx : ny, nstep = rows ? ny : nx;
+    const double f0 = (double)k * P.f0_k + P.f0_c;  // fractional fast index at step 0
+    // steps whose crossing lies in (-1, nfast); one step of margin each side
+    int jlo = 0, jhi = nstep - 1;
+    if (P.df != 0.0) {
+        double ja = (-1.0 - f0) / P.df, jb = ((double)nfast - f0) / P.df;
+        double lo = fmin(ja, jb), hi = fmax(ja, jb);
+        lo = fmax(lo, -1.0);
+        hi = fmin(hi, (double)nstep);
+        jlo = max(0, (int)floor(lo) - 1);
+        jhi = min(nstep - 1, (int)ceil(hi) + 1);
+    } else if (!(f0 > -1.0 && f0 < (double)nfast)) {
+        jhi = -1;
+    }
+    real acc = 0;
+    if constexpr (sizeof(real) == 4) {
+        const double fl0 = floor(f0);
+        const int ibase = (int)fmax(fmin(fl0, 1e9), -1e9);
+        const float fbase = (float)(f0 - fl0);
+        for (int j = jlo; j <= jhi; ++j) {
+            int i0;
+            float w1;
+            affine_frac(ibase, fbase, P.df_hi, P.df_lo, j, i0, w1);
+            const real *row = img + (long long)j * nfast;
+            if (i0 >= 0 && i0 < nfast) acc = fmaf(1.0f - w1, ldg(row + i0), acc);
+            if (i0 + 1 >= 0 && i0 + 1 < nfast) acc = fmaf(w1, ldg(row + i0 + 1), acc);
+        }
+    } else {
+        for (int j = jlo; j <= jhi; ++j) {
+            const double f = fma((double)j, P.df, f0);
+            const double fl = floor(f);
+            const int i0 = (int)fl;
+            const double w1 = f - fl;
+            const real *row = img + (long long)j * nfast;
+            if (i0 >= 0 && i0 < nfast) acc = fma(1.0 - w1, ldg(row + i0), acc);
+            if (i0 + 1 >= 0 && i0 + 1 < nfast) acc = fma(w1, ldg(row + i0 + 1), acc);
+        }
+    }
+    b[(long long)a * nb + k] = acc * (real)P.wstep;
+}
+
+template <typename real>
+mof_status launch_project(const mof_problem *p, const real *u, real *uT, real *b, cudaStream_t st) {
+    dim3 tb(32, 8), tg((p->nx + 31) / 32, (p->ny + 31) / 32, p->nt);
+    k_transpose<real><<<tg, tb, 0, st>>>(u, uT, p->nx, p->ny);
+    MOF_LAUNCH_CHECK();
+    dim3 grid((p->nb + 127) / 128, p->A);
+    k_project<real><<<grid, 128, 0, st>>>(u, uT, b, p->d_ang, p->nx, p->ny, p->nb);
+    MOF_LAUNCH_CHECK();
+    return MOF_OK;
+}
+
+// ---------------------------------------------------------- K2 backproject
+// One thread per pixel (tile 32 x 8 per block), looping over the angles of
+// its frame. Per angle the block's base bin coordinate at the tile origin is
+// computed once in FP64 (shared memory); each pixel adds its small in-tile
+// offset with the split-step evaluation, keeping the footprint weight
+// accurate to ~1e-7 at any grid size.
+constexpr int BP_TX = 32, BP_TY = 8, BP_CHUNK = 64;
+
+template <typename real>
+__global__ void __launch_bounds__(BP_TX *BP_TY) k_backproject(const real *__restrict__ b, real *__restrict__ u,
+                                                              const AngleParams *__restrict__ ang,
+                                                              const int *__restrict__ aoff, int nx, int ny, int nb) {
+    __shared__ int s_ib[BP_CHUNK];
+    __shared__ float s_fb[BP_CHUNK];
+    __shared__ double s_tb[BP_CHUNK];
+    const int t = blockIdx.z;
+    const int x0 = blockIdx.x * BP_TX, y0 = blockIdx.y * BP_TY;
+    const int di = threadIdx.x, dj = threadIdx.y;
+    const int x = x0 + di, y = y0 + dj;
+    const int tid = threadIdx.y * BP_TX + threadIdx.x;
+    const int a_begin = aoff[t], a_end = aoff[t + 1];
+    real acc = 0;
+    for (int ac = a_begin; ac < a_end; ac += BP_CHUNK) {
+        const int cn = min(BP_CHUNK, a_end - ac);
+        __syncthreads();
+        if (tid < cn) {
+            const AngleParams &P = ang[ac + tid];
+            const double tb = P.t0 + (double)x0 * P.tA + (double)y0 * P.tB;
+            const double fl = floor(tb);
+            s_ib[tid] = (int)fmax(fmin(fl, 1e9), -1e9);
+            s_fb[tid] = (float)(tb - fl);
+            s_tb[tid] = tb;
+        }
+        __syncthreads();
+        if (x < nx && y < ny) {
+            for (int q = 0; q < cn; ++q) {
+                const AngleParams &P = ang[ac + q];
+                const real *row = b + (long long)(ac + q) * nb;
+                const float r = P.rfoot;
+                if constexpr (sizeof(real) == 4) {
+                    // bin coordinate t = ib + fr of this pixel
+                    const float pa = (float)di * P.tA_hi, pb = (float)dj * P.tB_hi;  // exact
+                    const float pfa = floorf(pa), pfb = floorf(pb);
+                    float fr = s_fb[q] + (pa - pfa) + (pb - pfb) + fmaf((float)di, P.tA_lo, (float)dj * P.tB_lo);
+                    const float ff = floorf(fr);
+                    const int ib = s_ib[q] + (int)pfa + (int)pfb + (int)ff;
+                    fr -= ff;
+                    // bins k with |k - t| < r: k = ib - m (distance fr + m) and ib + 1 + m (1 - fr + m)
+                    for (int m = 0; (float)m < r; ++m) {
+                        const float d0 = fr + (float)m, d1 = 1.0f - fr + (float)m;
+                        const int k0 = ib - m, k1 = ib + 1 + m;
+                        if (d0 < r && k0 >= 0 && k0 < nb) acc = fmaf(P.wfoot * (1.0f - d0 / r), ldg(row + k0), acc);
+                        if (d1 < r && k1 >= 0 && k1 < nb) acc = fmaf(P.wfoot * (1.0f - d1 / r), ldg(row + k1), acc);
+                    }
+                } else {
+                    const double tt = s_tb[q] + (double)di * P.tA + (double)dj * P.tB;
+                    const double ff = floor(tt);
+                    const int ib = (int)ff;
+                    const double fr = tt - ff;
+                    const double rd = (double)P.rfoot, wf = (double)P.wfoot;
+                    for (int m = 0; (double)m < rd; ++m) {
+                        const double d0 = fr + m, d1 = 1.0 - fr + m;
+                        const int k0 = ib - m, k1 = ib + 1 + m;
+                        if (d0 < rd && k0 >= 0 && k0 < nb) acc = fma(wf * (1.0 - d0 / rd), ldg(row + k0), acc);
+                        if (d1 < rd && k1 >= 0 && k1 < nb) acc = fma(wf * (1.0 - d1 / rd), ldg(row + k1), acc);
+                    }
+                }
+            }
+        }
+    }
+    if (x < nx && y < ny) u[(long long)t * nx * ny + (long long)y * nx + x] = acc;
+}
+
+template <typename real>
+mof_status launch_backproject(const mof_problem *p, const real *b, real *u, cudaStream_t st) {
+    dim3 grid((p->nx + BP_TX - 1) / BP_TX, (p->ny + BP_TY - 1) / BP_TY, p->nt);
+    k_backproject<real><<<grid, dim3(BP_TX, BP_TY), 0, st>>>(b, u, p->d_ang, p->d_aoff, p->nx, p->ny, p->nb);
+    MOF_LAUNCH_CHECK();
+    return MOF_OK;
+}
+
+template mof_status launch_project<float>(const mof_problem *, const float *, float *, float *, cudaStream_t);
+template mof_status launch_project<double>(const mof_problem *, const double *, double *, double *, cudaStream_t);
+template mof_status launch_backproject<float>(const mof_problem *, const float *, float *, cudaStream_t);
+template mof_status launch_backproject<double>(const mof_problem *, const double *, double *, cudaStream_t);
+
+}  // namespace mof

@@ -1,0 +1,1000 @@
+// Solver layer of libmof: Solve-OF (Alg. 2) batched over all frame pairs,
+// MMGKS-OF (Alg. 1), their workspace, and per-kernel-class timing.
+//
+// Every quantity that steers the iteration (basis sizes, growth flags,
+// lambda, z, norms) lives in device memory, and every kernel reads it there:
+// the host enqueues a fixed sequence of launches per outer iteration and
+// synchronises only at the end of mof_solve.
+#include "solver.cuh"
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+namespace mof {
+
+// ============================================================ kernel timing
+struct Timer {
+    std::vector<std::string> names;
+    std::vector<double> ms;
+    std::vector<long long> count;
+    struct Pending {
+        int cls;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+
+    int cls(const char *name) {
+        for (size_t i = 0; i < names.size(); ++i)
+            if (names[i] == name) return (int)i;
+        names.push_back(name);
+        ms.push_back(0.0);
+        count.push_back(0);
+        return (int)names.size() - 1;
+    }
+    cudaEvent_t ev() {
+        if (used == pool.size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            pool.push_back(e);
+        }
+        return pool[used++];
+    }
+    void reset() {
+        for (auto &v : ms) v = 0.0;
+        for (auto &c : count) c = 0;
+        pending.clear();
+        used = 0;
+    }
+    void collect() {
+        for (auto &p : pending) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) {
+                ms[p.cls] += t;
+                count[p.cls] += 1;
+            }
+        }
+        pending.clear();
+        used = 0;
+    }
+    ~Timer() {
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+// Scoped timing of one launch group on `st` when timing is enabled.
+struct Scope {
+    Timer *t;
+    int c;
+    cudaEvent_t b;
+    cudaStream_t st;
+    Scope(Timer *tm, const char *name, cudaStream_t s) : t(tm), c(-1), b(nullptr), st(s) {
+        if (!t) return;
+        c = t->cls(name);
+        cudaEvent_t a = t->ev();
+        b = t->ev();
+        cudaEventRecord(a, st);
+        t->pending.push_back({c, a, b});
+    }
+    ~Scope() {
+        if (t) cudaEventRecord(b, st);
+    }
+};
+
+// ============================================================ workspace
+struct Arena {
+    char *base = nullptr;
+    size_t off = 0, cap = 0;
+    template <typename T>
+    T *take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T *p = reinterpret_cast<T *>(base + off);
+        off += sizeof(T) * count;
+        return p;
+    }
+};
+
+template <typename real>
+struct WS {
+    int Kmax = 0, Kof = 0, of_ell = 0, ell = 0, max_outer = 0;
+    char *mem = nullptr;
+    size_t bytes = 0;
+    // ---- image step (one problem)
+    real *V, *HV, *U, *u, *un, *r, *tm, *tn, *b, *q, *uT, *s, *sr, *vnew, *hvnew;
+    int *radius, *dest;
+    double *GH, *GT, *gH, *z, *lam, *coef, *nrm2, *nrm2b, *scaleR, *alpha, *beta, *beta1, *alpha1, *bb, *gpart;
+    int *K, *KU, *grow, *gkb, *flag, *err, *appended;
+    double *report;  // [max_outer][8]
+    // ---- Solve-OF (P pairs)
+    real *ux, *uy, *ut, *bof, *Vof, *Uof, *AtB, *wv, *wu, *y1, *y2, *sof, *vnew_of;
+    double *GA, *GL, *gof, *zof, *gam, *nrm_of, *coef_of, *coefU_of, *scale_of, *alpha_of, *alpha1_of, *beta_of,
+        *beta1_of, *bb_of;
+    int *Kv_of, *Ku_of, *grow_of, *gkb_of, *act_of, *app_of, *flag_of;
+    double *partial;
+    int gram_ctas = 0;
+};
+
+struct Holder {
+    void *scr[SCR_COUNT] = {};
+    WS<float> *w32 = nullptr;
+    WS<double> *w64 = nullptr;
+    void *host_stage = nullptr;  // device staging of mof_solve_host: b | u | s | sr
+    Timer timer;
+};
+
+template <typename real>
+static WS<real> *&ws_slot(Holder *h) {
+    if constexpr (sizeof(real) == 8) return h->w64;
+    else return h->w32;
+}
+
+static Holder *holder(mof_problem *p) {
+    if (!p->ws) p->ws = new Holder();
+    return static_cast<Holder *>(p->ws);
+}
+
+template <typename real>
+static void free_ws(WS<real> *w) {
+    if (!w) return;
+    if (w->mem) cudaFree(w->mem);
+    delete w;
+}
+
+void free_workspace(mof_problem *p) {
+    if (!p->ws) return;
+    Holder *h = static_cast<Holder *>(p->ws);
+    for (auto &s : h->scr)
+        if (s) cudaFree(s);
+    if (h->host_stage) cudaFree(h->host_stage);
+    free_ws(h->w32);
+    free_ws(h->w64);
+    delete h;
+    p->ws = nullptr;
+}
+
+mof_status apply_scratch(mof_problem *p, ScratchKind kind, void **out) {
+    Holder *h = holder(p);
+    if (!h->scr[kind]) {
+        const size_t es = p->precision == MOF_FP64 ? 8 : 4;
+        size_t bytes = 0;
+        switch (kind) {
+            case SCR_IMAGE: bytes = es * p->n; break;
+            case SCR_RADIUS: bytes = 16; break;
+            case SCR_DEST: bytes = sizeof(int) * (p->nt - 1) * p->ns; break;
+            case SCR_FLOWROWS: bytes = es * 2 * (p->nt - 1) * p->ns; break;
+            default: return fail(MOF_EINVAL, "bad scratch kind");
+        }
+        MOF_CUDA(cudaMalloc(&h->scr[kind], bytes));
+    }
+    *out = h->scr[kind];
+    return MOF_OK;
+}
+
+constexpr int TG_T = 256;      // theta-gram block
+constexpr int TG_PIX = 64;     // pixels per theta-gram tile
+constexpr int TG_ROWS = 4 * TG_PIX;
+
+template <typename real>
+static size_t theta_gram_smem(int Kmax) {
+    const int Ks = ((Kmax + 3) / 4) * 4 + 4;
+    return sizeof(real) * TG_ROWS * Ks + sizeof(double) * Kmax * Kmax;
+}
+
+template <typename real>
+static mof_status ensure_ws(mof_problem *p, const mof_solver_params &prm, int n_outer, WS<real> *&w) {
+    const int Kmax = prm.ell + n_outer;
+    const int Kof = prm.of_ell + prm.of_iters;
+    if (w && w->Kmax >= Kmax && w->Kof >= Kof && w->of_ell >= prm.of_ell && w->ell >= prm.ell && w->max_outer >= n_outer)
+        return MOF_OK;
+    free_ws(w);
+    w = new WS<real>();
+    w->Kmax = Kmax;
+    w->Kof = Kof;
+    w->of_ell = prm.of_ell;
+    w->ell = prm.ell;
+    w->max_outer = n_outer;
+    const long long n = p->n, m = p->m, ns = p->ns, P = p->nt - 1, N2 = 2 * ns;
+    int dev_sms = 152;
+    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, p->device);
+    w->gram_ctas = 2 * dev_sms;
+    const long long chunks_n = krylov_chunks(std::max(n, m)), chunks_of = krylov_chunks(N2);
+    const long long partial = std::max(chunks_n * 3 * Kmax, P * chunks_of * 3 * (long long)Kof);
+    for (int pass = 0; pass < 2; ++pass) {
+        Arena a;
+        a.base = w->mem;
+        // image step
+        w->V = a.take<real>((size_t)Kmax * n);
+        w->HV = a.take<real>((size_t)Kmax * m);
+        w->U = a.take<real>((size_t)(prm.ell + 1) * m);
+        w->u = a.take<real>(n);
+        w->un = a.take<real>(n);
+        w->r = a.take<real>(n);
+        w->tm = a.take<real>(m);
+        w->tn = a.take<real>(n);
+        w->b = a.take<real>(m);
+        w->q = a.take<real>(2 * P * ns);
+        w->uT = a.take<real>(n);
+        w->s = a.take<real>(P * N2);
+        w->sr = a.take<real>(P * N2);
+        w->vnew = a.take<real>(n);
+        w->hvnew = a.take<real>(m);
+        w->radius = a.take<int>(4);
+        w->dest = a.take<int>(P * ns);
+        w->GH = a.take<double>((size_t)Kmax * Kmax);
+        w->GT = a.take<double>((size_t)Kmax * Kmax);
+        w->gH = a.take<double>(Kmax);
+        w->z = a.take<double>(Kmax);
+        w->lam = a.take<double>(1);
+        w->coef = a.take<double>(Kmax + 8);
+        w->nrm2 = a.take<double>(1);
+        w->nrm2b = a.take<double>(1);
+        w->scaleR = a.take<double>(1);
+        w->alpha = a.take<double>(prm.ell + 2);
+        w->beta = a.take<double>(prm.ell + 2);
+        w->beta1 = a.take<double>(1);
+        w->alpha1 = a.take<double>(1);
+        w->bb = a.take<double>(1);
+        w->gpart = a.take<double>((size_t)w->gram_ctas * Kmax * Kmax);
+        w->K = a.take<int>(1);
+        w->KU = a.take<int>(1);
+        w->grow = a.take<int>(1);
+        w->gkb = a.take<int>(1);
+        w->flag = a.take<int>(1);
+        w->err = a.take<int>(1);
+        w->appended = a.take<int>(1);
+        w->report = a.take<double>((size_t)n_outer * 8);
+        // Solve-OF
+        w->ux = a.take<real>(P * ns);
+        w->uy = a.take<real>(P * ns);
+        w->ut = a.take<real>(P * ns);
+        w->bof = a.take<real>(P * ns);
+        w->Vof = a.take<real>((size_t)P * Kof * N2);
+        w->Uof = a.take<real>((size_t)P * (prm.of_ell + 1) * ns);
+        w->AtB = a.take<real>(P * N2);
+        w->wv = a.take<real>(P * N2);
+        w->wu = a.take<real>(P * ns);
+        w->y1 = a.take<real>(P * N2);
+        w->y2 = a.take<real>(P * N2);
+        w->sof = a.take<real>(P * N2);
+        w->vnew_of = a.take<real>(P * N2);
+        w->GA = a.take<double>((size_t)P * Kof * Kof);
+        w->GL = a.take<double>((size_t)P * Kof * Kof);
+        w->gof = a.take<double>((size_t)P * Kof);
+        w->zof = a.take<double>((size_t)P * Kof);
+        w->gam = a.take<double>(P);
+        w->nrm_of = a.take<double>(P);
+        w->coef_of = a.take<double>((size_t)P * Kof);
+        w->coefU_of = a.take<double>((size_t)P * (prm.of_ell + 1));
+        w->scale_of = a.take<double>(P);
+        w->alpha_of = a.take<double>(P);
+        w->alpha1_of = a.take<double>(P);
+        w->beta_of = a.take<double>(P);
+        w->beta1_of = a.take<double>(P);
+        w->bb_of = a.take<double>(P);
+        w->Kv_of = a.take<int>(P);
+        w->Ku_of = a.take<int>(P);
+        w->grow_of = a.take<int>(P);
+        w->gkb_of = a.take<int>(P);
+        w->act_of = a.take<int>(P);
+        w->app_of = a.take<int>(P);
+        w->flag_of = a.take<int>(P);
+        w->partial = a.take<double>((size_t)partial);
+        if (pass == 0) {
+            w->bytes = a.off + 256;
+            cudaError_t e = cudaMalloc(&w->mem, w->bytes);
+            if (e != cudaSuccess) {
+                delete w;
+                w = nullptr;
+                return cuda_fail(e, "workspace allocation", __FILE__, __LINE__);
+            }
+            MOF_CUDA(cudaMemset(w->mem, 0, w->bytes));
+        }
+    }
+    const size_t sm = theta_gram_smem<real>(Kmax);
+    (void)sm;
+    return MOF_OK;
+}
+
+// ============================================================ small kernels
+template <typename real>
+__global__ void k_fill(real *x, long long n, real v) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) x[i] = v;
+}
+__global__ void k_fill_int(int *x, int n, int v) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = v;
+}
+template <typename real>
+__global__ void k_copy(const real *__restrict__ a, real *__restrict__ b, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) b[i] = a[i];
+}
+template <typename real>
+__global__ void k_neg(const real *__restrict__ a, real *__restrict__ b, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) b[i] = -a[i];
+}
+// x[b] -= coef[b] * y[b]  (coef device, per problem)
+template <typename real>
+__global__ void k_axpy_dev(real *__restrict__ x, long long xstride, const real *__restrict__ y, long long ystride,
+                           const double *__restrict__ coef, long long N, const int *__restrict__ act) {
+    const int b = blockIdx.y;
+    if (act && !act[b]) return;
+    const real c = (real)coef[b];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+        x[b * xstride + i] -= c * y[b * ystride + i];
+}
+__global__ void k_sqrt_into(const double *__restrict__ a, double *__restrict__ b, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = sqrt(a[i]);
+}
+__global__ void k_sqrt_into_if(const double *__restrict__ a, double *__restrict__ b, int n, const int *__restrict__ act) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && (!act || act[i])) b[i] = sqrt(a[i]);
+}
+__global__ void k_mul_into(const double *__restrict__ a, const double *__restrict__ c, double *__restrict__ out, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = a[i] * c[i];
+}
+__global__ void k_of_activate(const double *__restrict__ bb, int *__restrict__ act, int *__restrict__ gkb,
+                              int *__restrict__ grow, int *__restrict__ Kv, int *__restrict__ Ku, double *__restrict__ beta1,
+                              int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int a = bb[i] > 0.0 && isfinite(bb[i]);
+    act[i] = a;
+    gkb[i] = a;
+    grow[i] = a;
+    Kv[i] = 0;
+    Ku[i] = 0;
+    beta1[i] = sqrt(bb[i]);
+}
+// copy column K-1 of a [B][ld][ld] matrix into row K-1
+__global__ void k_sym_last(double *__restrict__ G, int ld, const int *__restrict__ K, const int *__restrict__ act) {
+    const int b = blockIdx.x;
+    if (act && !act[b]) return;
+    const int j = K[b] - 1;
+    if (j < 0) return;
+    double *Gb = G + (long long)b * ld * ld;
+    for (int i = threadIdx.x; i < j; i += blockDim.x) Gb[j * ld + i] = Gb[i * ld + j];
+}
+// copy a staged vector into slot K-1 of a basis of one problem
+template <typename real>
+__global__ void k_store_slot(real *__restrict__ base, long long N, const int *__restrict__ K, const int *__restrict__ app,
+                             const real *__restrict__ v) {
+    if (!app[0]) return;
+    real *d = base + (long long)(K[0] - 1) * N;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) d[i] = v[i];
+}
+
+// ------------------------------------------------------------ Upsilon kernels
+// GKB steps of Solve-OF, one problem per frame pair (blockIdx.y):
+//   out = Upsilon^T u_j - beta_j v_{j-1}     (V side, length 2 ns)
+template <typename real>
+__global__ void k_of_upsT(const real *__restrict__ ux, const real *__restrict__ uy, const real *__restrict__ U, int ldU,
+                          int j, const real *__restrict__ V, int ldV, const double *__restrict__ beta,
+                          real *__restrict__ out, long long ns, const int *__restrict__ act) {
+    const int b = blockIdx.y;
+    if (!act[b]) return;
+    const real *uj = U + ((long long)b * ldU + j) * ns;
+    const real *vp = j > 0 ? V + ((long long)b * ldV + j - 1) * 2 * ns : nullptr;
+    const real bj = j > 0 ? (real)beta[b] : (real)0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ns; i += (long long)gridDim.x * blockDim.x) {
+        const real r = uj[i];
+        real o0 = ux[b * ns + i] * r, o1 = uy[b * ns + i] * r;
+        if (vp) {
+            o0 -= bj * vp[i];
+            o1 -= bj * vp[ns + i];
+        }
+        out[b * 2 * ns + i] = o0;
+        out[b * 2 * ns + ns + i] = o1;
+    }
+}
+//   out = Upsilon v_j - alpha_j u_j           (U side, length ns)
+template <typename real>
+__global__ void k_of_ups(const real *__restrict__ ux, const real *__restrict__ uy, const real *__restrict__ V, int ldV, int j,
+                         const real *__restrict__ U, int ldU, const double *__restrict__ alpha, real *__restrict__ out,
+                         long long ns, const int *__restrict__ act) {
+    const int b = blockIdx.y;
+    if (!act[b]) return;
+    const real *vj = V + ((long long)b * ldV + j) * 2 * ns;
+    const real *uj = U + ((long long)b * ldU + j) * ns;
+    const real aj = (real)alpha[b];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ns; i += (long long)gridDim.x * blockDim.x)
+        out[b * ns + i] = ux[b * ns + i] * vj[i] + uy[b * ns + i] * vj[ns + i] - aj * uj[i];
+}
+
+// Graph Laplacian of one component with free boundary: (Psi^T Psi f)(x,y).
+template <typename real>
+__device__ __forceinline__ real lap_at(const real *__restrict__ f, int nx, int ny, int x, int y) {
+    const long long i = (long long)y * nx + x;
+    const real c = f[i];
+    real v = 0;
+    if (x > 0) v += c - f[i - 1];
+    if (x < nx - 1) v += c - f[i + 1];
+    if (y > 0) v += c - f[i - nx];
+    if (y < ny - 1) v += c - f[i + nx];
+    return v;
+}
+
+// y1 = Upsilon^T Upsilon v, y2 = (L(+)L)^T (L(+)L) v for v = src[b] (length 2 ns)
+template <typename real>
+__global__ void k_of_normal_parts(const real *__restrict__ ux, const real *__restrict__ uy, const real *__restrict__ src,
+                                  long long sstride, real *__restrict__ y1, real *__restrict__ y2, int nx, int ny,
+                                  const int *__restrict__ act) {
+    const int b = blockIdx.z;
+    if (act && !act[b]) return;
+    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    const long long ns = (long long)nx * ny, i = (long long)y * nx + x;
+    const real *v = src + b * sstride;
+    const real ax = ux[b * ns + i], ay = uy[b * ns + i];
+    const real a = ax * v[i] + ay * v[ns + i];
+    y1[b * 2 * ns + i] = ax * a;
+    y1[b * 2 * ns + ns + i] = ay * a;
+    y2[b * 2 * ns + i] = lap_at(v, nx, ny, x, y);
+    y2[b * 2 * ns + ns + i] = lap_at(v + ns, nx, ny, x, y);
+}
+
+// r = Ups^T Ups s - Ups^T b + gamma (L(+)L)^T (L(+)L) s  (normal-equation residual of Alg. 2)
+template <typename real>
+__global__ void k_of_resid(const real *__restrict__ ux, const real *__restrict__ uy, const real *__restrict__ AtB,
+                           const real *__restrict__ s, const double *__restrict__ gam, real *__restrict__ r, int nx, int ny,
+                           const int *__restrict__ act) {
+    const int b = blockIdx.z;
+    if (!act[b]) return;
+    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    const long long ns = (long long)nx * ny, i = (long long)y * nx + x;
+    const real *v = s + b * 2 * ns;
+    const real ax = ux[b * ns + i], ay = uy[b * ns + i];
+    const real a = ax * v[i] + ay * v[ns + i];
+    const real g = (real)gam[b];
+    r[b * 2 * ns + i] = ax * a - AtB[b * 2 * ns + i] + g * lap_at(v, nx, ny, x, y);
+    r[b * 2 * ns + ns + i] = ay * a - AtB[b * 2 * ns + ns + i] + g * lap_at(v + ns, nx, ny, x, y);
+}
+
+// AtB = Upsilon^T b with b = -u_t, and bof = -u_t
+template <typename real>
+__global__ void k_of_rhs(const real *__restrict__ ux, const real *__restrict__ uy, const real *__restrict__ ut,
+                         real *__restrict__ bof, real *__restrict__ AtB, long long ns) {
+    const int b = blockIdx.y;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ns; i += (long long)gridDim.x * blockDim.x) {
+        const real bv = -ut[b * ns + i];
+        bof[b * ns + i] = bv;
+        AtB[b * 2 * ns + i] = ux[b * ns + i] * bv;
+        AtB[b * 2 * ns + ns + i] = uy[b * ns + i] * bv;
+    }
+}
+
+// ------------------------------------------------------ weighted Theta Gram
+// G = (P Theta V)^T (P Theta V), P^2 = diag(((Theta uk)^2 + eps^2)^(-1/2)), over the
+// first K columns of V. Each tile of TG_PIX pixels of one frame yields 4 rows per
+// pixel (Psi_x, Psi_y of the frame; Mbar and Mbar' rows of the pair starting at
+// the frame), written to shared memory scaled by P; the block then adds their
+// outer products to a per-block FP64 Gram (4x4 register blocks of the upper
+// triangle, FP32 within a tile for the FP32 path).
+template <typename real>
+__device__ __forceinline__ real bil_sample(const real *__restrict__ f, int nx, int x0, int x1, int y0, int y1, real wx, real wy) {
+    const real a = f[(long long)y0 * nx + x0], b = f[(long long)y0 * nx + x1];
+    const real c = f[(long long)y1 * nx + x0], d = f[(long long)y1 * nx + x1];
+    return (1 - wy) * ((1 - wx) * a + wx * b) + wy * ((1 - wx) * c + wx * d);
+}
+
+template <typename real>
+__device__ __forceinline__ void warp_axis_s(int x, real v, int n, int &i0, int &i1, real &w) {
+    const real vc = v > (real)16777216 ? (real)16777216 : (v < (real)-16777216 ? (real)-16777216 : v);
+    const real fv = floor(vc);
+    const int I = x + (int)fv;
+    if (I < 0) { i0 = 0; w = 0; }
+    else if (I >= n - 1) { i0 = n - 1; w = 0; }
+    else { i0 = I; w = vc - fv; }
+    if (!(v == v)) { i0 = x; w = 0; }
+    i1 = min(i0 + 1, n - 1);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(TG_T) k_theta_gram(const real *__restrict__ V, long long n, int Kmax, const int *__restrict__ Kp,
+                                                     const real *__restrict__ uk, const real *__restrict__ s,
+                                                     const real *__restrict__ sr, real eps2, int nx, int ny, int nt,
+                                                     double *__restrict__ partial) {
+    extern __shared__ unsigned char smraw[];
+    const int Ks = ((Kmax + 3) / 4) * 4 + 4;
+    real *A = reinterpret_cast<real *>(smraw);
+    double *Gs = reinterpret_cast<double *>(smraw + sizeof(real) * TG_ROWS * Ks);
+    const int K = min(Kp[0], Kmax);
+    const int K4 = (K + 3) / 4;
+    const int nblk = K4 * (K4 + 1) / 2;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < Kmax * Kmax; e += TG_T) Gs[e] = 0.0;
+    const long long ns = (long long)nx * ny;
+    const long long tpf = (ns + TG_PIX - 1) / TG_PIX;
+    const long long ntiles = tpf * nt;
+    const int np = nt - 1;
+    const int q = tid & 3;
+    const int group = tid >> 6, gl = tid & 63;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int t = (int)(tile / tpf);
+        const long long pix = (tile % tpf) * TG_PIX + (tid >> 2);
+        const bool inpix = pix < ns;
+        const int x = inpix ? (int)(pix % nx) : 0, y = inpix ? (int)(pix / nx) : 0;
+        bool valid = inpix && (q < 2 || t < np);
+        if (q == 0 && x >= nx - 1) valid = false;
+        if (q == 1 && y >= ny - 1) valid = false;
+        int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+        real wx = 0, wy = 0;
+        long long fa = 0, fb = 0;  // frame offsets: row = v[fa + i] - interp(v[fb + .])
+        if (valid && q >= 2) {
+            const real *sv = (q == 2 ? s : sr) + 2LL * t * ns;
+            warp_axis_s(x, sv[pix], nx, x0, x1, wx);
+            warp_axis_s(y, sv[ns + pix], ny, y0, y1, wy);
+            fa = (q == 2 ? t : t + 1) * ns;
+            fb = (q == 2 ? t + 1 : t) * ns;
+        }
+        real sw = 0;
+        if (valid) {
+            real nu;
+            const real *f = uk;
+            if (q == 0) nu = f[t * ns + pix + 1] - f[t * ns + pix];
+            else if (q == 1) nu = f[t * ns + pix + nx] - f[t * ns + pix];
+            else nu = f[fa + pix] - bil_sample(f + fb, nx, x0, x1, y0, y1, wx, wy);
+            sw = (real)1 / sqrt(sqrt(nu * nu + eps2));
+        }
+        real *Arow = A + tid * Ks;
+        for (int j = 0; j < K; ++j) {
+            real val = 0;
+            if (valid) {
+                const real *f = V + (long long)j * n;
+                if (q == 0) val = f[t * ns + pix + 1] - f[t * ns + pix];
+                else if (q == 1) val = f[t * ns + pix + nx] - f[t * ns + pix];
+                else val = f[fa + pix] - bil_sample(f + fb, nx, x0, x1, y0, y1, wx, wy);
+            }
+            Arow[j] = sw * val;
+        }
+        for (int j = K; j < K4 * 4; ++j) Arow[j] = 0;
+        __syncthreads();
+        for (int blk = gl; blk < nblk; blk += 64) {
+            // blk -> (I, J), I <= J, row-major over the upper triangle
+            int I = 0, rem = blk;
+            while (rem >= K4 - I) {
+                rem -= K4 - I;
+                ++I;
+            }
+            const int J = I + rem;
+            real acc[4][4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[a][c] = 0;
+            for (int rr = 0; rr < 64; ++rr) {
+                const real *row = A + (group * 64 + rr) * Ks;
+                real va[4], vb[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    va[a] = row[4 * I + a];
+                    vb[a] = row[4 * J + a];
+                }
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[a][c] += va[a] * vb[c];
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int i = 4 * I + a, jj = 4 * J + c;
+                    if (i < K && jj < K) atomicAdd(&Gs[i * Kmax + jj], (double)acc[a][c]);
+                }
+        }
+        __syncthreads();
+    }
+    double *out = partial + (long long)blockIdx.x * Kmax * Kmax;
+    for (int e = tid; e < Kmax * Kmax; e += TG_T) out[e] = Gs[e];
+}
+
+// G[i][j] = sum over blocks of the upper-triangle partials, mirrored
+__global__ void k_gram_reduce(const double *__restrict__ partial, int nparts, int Kmax, const int *__restrict__ Kp,
+                              double *__restrict__ G) {
+    const int K = min(Kp[0], Kmax);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < K * K; e += gridDim.x * blockDim.x) {
+        const int i = e / K, j = e % K;
+        if (i > j) continue;
+        // entries inside a 4x4 diagonal block were produced both ways; take i <= j
+        double s = 0.0;
+        for (int c = 0; c < nparts; ++c) s += partial[(long long)c * Kmax * Kmax + i * Kmax + j];
+        G[i * Kmax + j] = s;
+        G[j * Kmax + i] = s;
+    }
+}
+
+// report[k] = {lam, resid, rnorm, basis, flag, of_min, of_max}
+__global__ void k_report(double *__restrict__ rep, int k, const double *__restrict__ lam, const double *__restrict__ resid2,
+                         const double *__restrict__ rn2, const int *__restrict__ K, const int *__restrict__ flag,
+                         const int *__restrict__ Kof, int P, int of_ran, int expanded, const int *__restrict__ appended) {
+    double *r = rep + (long long)k * 8;
+    r[0] = lam[0];
+    r[1] = sqrt(resid2[0]);
+    r[2] = expanded ? sqrt(rn2[0]) : 0.0;
+    r[3] = (double)(K[0] - (expanded && appended[0] ? 1 : 0));
+    r[4] = (double)flag[0];
+    int mn = 1 << 30, mx = 0;
+    if (of_ran)
+        for (int b = 0; b < P; ++b) {
+            mn = min(mn, Kof[b]);
+            mx = max(mx, Kof[b]);
+        }
+    r[5] = of_ran ? (double)mn : 0.0;
+    r[6] = of_ran ? (double)mx : 0.0;
+}
+
+static inline int fb(long long n) { return (int)std::min<long long>(152 * 8, (n + 255) / 256); }
+
+// ============================================================ Solve-OF
+template <typename real>
+static mof_status solve_of_impl(mof_problem *p, const mof_solver_params &prm, WS<real> &w, const real *u, real *s_out,
+                                Timer *tm, cudaStream_t st) {
+    const int P = p->nt - 1;
+    const long long ns = p->ns, N2 = 2 * ns;
+    const int Kof = w.Kof, ldU = w.of_ell + 1;
+    const double tol = prm.breakdown_tol > 0 ? prm.breakdown_tol : (sizeof(real) == 8 ? 1e-10 : 1e-6);
+    Krylov<real> kr;
+    kr.partial = w.partial;
+    const dim3 g2((p->nx + 31) / 32, (p->ny + 7) / 8, P);
+    const dim3 blk2(32, 8);
+    {
+        Scope sc(tm, "of_fields", st);
+        MOF_TRY(launch_of_fields<real>(p, u, prm.of_dr, w.ux, w.uy, w.ut, st));
+        k_of_rhs<real><<<dim3(fb(ns), P), 256, 0, st>>>(w.ux, w.uy, w.ut, w.bof, w.AtB, ns);
+    }
+    BasisRef<real> BV{w.Vof, N2, Kof, P, w.Kv_of, w.gkb_of};
+    BasisRef<real> BU{w.Uof, ns, ldU, P, w.Ku_of, w.gkb_of};
+    {
+        Scope sc(tm, "of_gkb", st);
+        kr.norm2(w.bof, ns, ns, P, w.bb_of, st);
+        k_of_activate<<<(P + 63) / 64, 64, 0, st>>>(w.bb_of, w.act_of, w.gkb_of, w.grow_of, w.Kv_of, w.Ku_of, w.beta1_of, P);
+        kr.norm2(w.AtB, N2, N2, P, w.nrm_of, st);
+        k_sqrt_into<<<(P + 63) / 64, 64, 0, st>>>(w.nrm_of, w.scale_of, P);
+        // u_1 = b / ||b||
+        kr.append(BU, w.Ku_of, w.bof, ns, w.bb_of, nullptr, 0.0, w.gkb_of, nullptr, nullptr, st);
+        for (int j = 0; j < w.of_ell && j < prm.of_ell; ++j) {
+            k_of_upsT<real><<<dim3(fb(ns), P), 256, 0, st>>>(w.ux, w.uy, w.Uof, ldU, j, w.Vof, Kof, w.beta_of, w.wv, ns, w.gkb_of);
+            kr.reorth(BV, w.wv, N2, w.coef_of, w.nrm_of, st);
+            if (j == 0) k_sqrt_into_if<<<(P + 63) / 64, 64, 0, st>>>(w.nrm_of, w.alpha1_of, P, w.gkb_of);
+            k_sqrt_into_if<<<(P + 63) / 64, 64, 0, st>>>(w.nrm_of, w.alpha_of, P, w.gkb_of);
+            kr.append(BV, w.Kv_of, w.wv, N2, w.nrm_of, j == 0 ? nullptr : w.alpha1_of, tol, w.gkb_of, nullptr, nullptr, st);
+            k_of_ups<real><<<dim3(fb(ns), P), 256, 0, st>>>(w.ux, w.uy, w.Vof, Kof, j, w.Uof, ldU, w.alpha_of, w.wu, ns, w.gkb_of);
+            kr.reorth(BU, w.wu, ns, w.coefU_of, w.nrm_of, st);
+            k_sqrt_into_if<<<(P + 63) / 64, 64, 0, st>>>(w.nrm_of, w.beta_of, P, w.gkb_of);
+            kr.append(BU, w.Ku_of, w.wu, ns, w.nrm_of, w.beta1_of, tol, w.gkb_of, nullptr, nullptr, st);
+        }
+    }
+    BasisRef<real> BA{w.Vof, N2, Kof, P, w.Kv_of, w.act_of};
+    {
+        Scope sc(tm, "of_gram", st);
+        for (int j = 0; j < prm.of_ell; ++j) {
+            k_of_normal_parts<real><<<g2, blk2, 0, st>>>(w.ux, w.uy, w.Vof + (long long)j * N2, (long long)Kof * N2, w.y1, w.y2,
+                                                         p->nx, p->ny, w.act_of);
+            DotVecs<real> xs{{w.y1, w.y2, w.AtB}, {N2, N2, N2}};
+            DotOuts o{};
+            o.o[0] = DotOut{w.GA + j, (long long)Kof * Kof, Kof, 0, 0, 1.0};
+            o.o[1] = DotOut{w.GL + j, (long long)Kof * Kof, Kof, 0, 0, 1.0};
+            o.o[2] = DotOut{w.gof, Kof, 1, 0, 0, 1.0};
+            kr.multidot(BA, 3, xs, o, st);
+        }
+    }
+    SmallArgs sa{};
+    sa.GA = w.GA;
+    sa.GL = w.GL;
+    sa.g = w.gof;
+    sa.bb = w.bb_of;
+    sa.K = w.Kv_of;
+    sa.active = w.act_of;
+    sa.ld = Kof;
+    sa.B = P;
+    sa.rule = MOF_RULE_GCV;
+    sa.lam = w.gam;
+    sa.z = w.zof;
+    sa.flag = w.flag_of;
+    sa.err = w.err;
+    BasisRef<real> BS{w.Vof, N2, Kof, P, w.Kv_of, nullptr};
+    for (int it = 0; it < prm.of_iters; ++it) {
+        {
+            Scope sc(tm, "of_small", st);
+            MOF_TRY(launch_small_solve(sa, st));
+        }
+        {
+            Scope sc(tm, "of_combine", st);
+            kr.combine(BS, w.zof, Kof, s_out, N2, st);
+        }
+        if (it == prm.of_iters - 1) break;
+        {
+            Scope sc(tm, "of_resid", st);
+            k_of_resid<real><<<g2, blk2, 0, st>>>(w.ux, w.uy, w.AtB, s_out, w.gam, w.wv, p->nx, p->ny, w.act_of);
+        }
+        {
+            Scope sc(tm, "of_reorth", st);
+            kr.reorth(BA, w.wv, N2, w.coef_of, w.nrm_of, st);
+            kr.append(BA, w.Kv_of, w.wv, N2, w.nrm_of, w.scale_of, tol, w.grow_of, w.app_of, w.vnew_of, st);
+        }
+        {
+            Scope sc(tm, "of_gram", st);
+            BasisRef<real> BN{w.Vof, N2, Kof, P, w.Kv_of, w.app_of};
+            k_of_normal_parts<real><<<g2, blk2, 0, st>>>(w.ux, w.uy, w.vnew_of, N2, w.y1, w.y2, p->nx, p->ny, w.app_of);
+            DotVecs<real> xs{{w.y1, w.y2, w.AtB}, {N2, N2, N2}};
+            DotOuts o{};
+            o.o[0] = DotOut{w.GA, (long long)Kof * Kof, Kof, 1, 1, 1.0};
+            o.o[1] = DotOut{w.GL, (long long)Kof * Kof, Kof, 1, 1, 1.0};
+            o.o[2] = DotOut{w.gof, Kof, 1, 0, 0, 1.0};
+            kr.multidot(BN, 3, xs, o, st);
+            k_sym_last<<<P, 64, 0, st>>>(w.GA, Kof, w.Kv_of, w.app_of);
+            k_sym_last<<<P, 64, 0, st>>>(w.GL, Kof, w.Kv_of, w.app_of);
+        }
+    }
+    MOF_LAUNCH_CHECK();
+    return MOF_OK;
+}
+
+// ============================================================ MMGKS-OF
+template <typename real>
+static mof_status solve_impl(mof_problem *p, const mof_solver_params &prm, int n_outer, const real *b_in, real *u_out,
+                             real *s_out, real *sr_out, mof_report *report, cudaStream_t st) {
+    Holder *h = holder(p);
+    WS<real> *&wp = ws_slot<real>(h);
+    MOF_TRY(ensure_ws<real>(p, prm, n_outer, wp));
+    WS<real> &w = *wp;
+    Timer *tm = p->timing ? &h->timer : nullptr;
+    if (tm) tm->reset();
+    const long long n = p->n, m = p->m, ns = p->ns;
+    const int P = p->nt - 1;
+    const int Kmax = w.Kmax;
+    const double tol = prm.breakdown_tol > 0 ? prm.breakdown_tol : (sizeof(real) == 8 ? 1e-10 : 1e-6);
+    Krylov<real> kr;
+    kr.partial = w.partial;
+    const size_t tg_smem = theta_gram_smem<real>(Kmax);
+    MOF_CUDA(cudaFuncSetAttribute(k_theta_gram<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tg_smem));
+
+    BasisRef<real> BV{w.V, n, Kmax, 1, w.K, nullptr};
+    BasisRef<real> BH{w.HV, m, Kmax, 1, w.K, nullptr};
+    BasisRef<real> BU{w.U, m, w.ell + 1, 1, w.KU, w.gkb};
+    {
+        Scope sc(tm, "init", st);
+        k_fill_int<<<1, 32, 0, st>>>(w.K, 1, 0);
+        k_fill_int<<<1, 32, 0, st>>>(w.KU, 1, 0);
+        k_fill_int<<<1, 32, 0, st>>>(w.grow, 1, 1);
+        k_fill_int<<<1, 32, 0, st>>>(w.gkb, 1, 1);
+        k_fill_int<<<1, 32, 0, st>>>(w.err, 1, 0);
+        k_fill_int<<<1, 32, 0, st>>>(w.flag, 1, 0);
+        k_fill<real><<<fb(n), 256, 0, st>>>(w.u, n, (real)0);
+        k_fill<real><<<fb(2 * P * ns), 256, 0, st>>>(w.s, 2 * P * ns, (real)0);
+        k_fill<real><<<fb(2 * P * ns), 256, 0, st>>>(w.sr, 2 * P * ns, (real)0);
+        k_copy<real><<<fb(m), 256, 0, st>>>(b_in, w.b, m);
+        MOF_TRY(launch_window_radius<real>(p, w.s, w.sr, w.radius, st));
+    }
+    // ---- GKB on H from b / ||b|| (Sec. 4.1.1), H V_l = U_{l+1} B_l
+    {
+        Scope sc(tm, "gkb", st);
+        kr.norm2(w.b, m, m, 1, w.bb, st);
+        k_sqrt_into<<<1, 1, 0, st>>>(w.bb, w.beta1, 1);
+        kr.append(BU, w.KU, w.b, m, w.bb, nullptr, 0.0, w.gkb, nullptr, nullptr, st);
+        for (int j = 0; j < prm.ell; ++j) {
+            MOF_TRY(launch_backproject<real>(p, w.U + (long long)j * m, w.r, st));
+            if (j > 0) k_axpy_dev<real><<<dim3(fb(n), 1), 256, 0, st>>>(w.r, n, w.V + (long long)(j - 1) * n, n, w.beta, n, w.gkb);
+            kr.reorth(BV, w.r, n, w.coef, w.nrm2, st);
+            if (j == 0) k_sqrt_into_if<<<1, 1, 0, st>>>(w.nrm2, w.alpha1, 1, w.gkb);
+            k_sqrt_into_if<<<1, 1, 0, st>>>(w.nrm2, w.alpha, 1, w.gkb);
+            kr.append(BV, w.K, w.r, n, w.nrm2, j == 0 ? nullptr : w.alpha1, tol, w.gkb, nullptr, nullptr, st);
+            MOF_TRY(launch_project<real>(p, w.V + (long long)j * n, w.uT, w.HV + (long long)j * m, st));
+            k_copy<real><<<fb(m), 256, 0, st>>>(w.HV + (long long)j * m, w.tm, m);
+            k_axpy_dev<real><<<dim3(fb(m), 1), 256, 0, st>>>(w.tm, m, w.U + (long long)j * m, m, w.alpha, m, w.gkb);
+            kr.reorth(BU, w.tm, m, w.coef, w.nrm2, st);
+            k_sqrt_into_if<<<1, 1, 0, st>>>(w.nrm2, w.beta, 1, w.gkb);
+            kr.append(BU, w.KU, w.tm, m, w.nrm2, w.beta1, tol, w.gkb, nullptr, nullptr, st);
+        }
+        // breakdown scale of the expansions: ||H^T b|| = alpha_1 beta_1
+        k_mul_into<<<1, 1, 0, st>>>(w.alpha1, w.beta1, w.scaleR, 1);
+        for (int j = 0; j < prm.ell; ++j) {
+            DotVecs<real> xs{{w.HV + (long long)j * m, w.b, nullptr}, {m, m, 0}};
+            DotOuts o{};
+            o.o[0] = DotOut{w.GH + j, 0, Kmax, 0, 0, 1.0};
+            o.o[1] = DotOut{w.gH, 0, 1, 0, 0, 1.0};
+            kr.multidot(BH, 2, xs, o, st);
+        }
+    }
+    SmallArgs sa{};
+    sa.GA = w.GH;
+    sa.GL = w.GT;
+    sa.g = w.gH;
+    sa.bb = w.bb;
+    sa.K = w.K;
+    sa.active = nullptr;
+    sa.ld = Kmax;
+    sa.B = 1;
+    sa.rule = prm.image_rule;
+    sa.target2 = (prm.eta * prm.noise_norm) * (prm.eta * prm.noise_norm);
+    sa.lam_fixed = prm.lam_fixed;
+    sa.lam = w.lam;
+    sa.z = w.z;
+    sa.flag = w.flag;
+    sa.err = w.err;
+    const real eps2 = (real)(prm.eps * prm.eps);
+    for (int k = 0; k < n_outer; ++k) {
+        const bool of_now = prm.tau > 0 && (k % prm.tau) == 0;
+        if (of_now) {
+            MOF_TRY(solve_of_impl<real>(p, prm, w, w.u, w.s, tm, st));
+            Scope sc(tm, "reverse_flow", st);
+            MOF_TRY(launch_window_radius<real>(p, w.s, nullptr, w.radius, st));
+            MOF_TRY(launch_reverse_flow<real>(p, w.s, w.radius, w.dest, w.sr, st));
+            MOF_TRY(launch_window_radius<real>(p, w.s, w.sr, w.radius, st));
+        }
+        {
+            Scope sc(tm, "theta_gram", st);
+            k_theta_gram<real><<<w.gram_ctas, TG_T, tg_smem, st>>>(w.V, n, Kmax, w.K, w.u, w.s, w.sr, eps2, p->nx, p->ny, p->nt,
+                                                                   w.gpart);
+            k_gram_reduce<<<8, 256, 0, st>>>(w.gpart, w.gram_ctas, Kmax, w.K, w.GT);
+        }
+        {
+            Scope sc(tm, "small_solve", st);
+            MOF_TRY(launch_small_solve(sa, st));
+        }
+        {
+            Scope sc(tm, "combine", st);
+            kr.combine(BV, w.z, Kmax, w.un, n, st);
+            kr.combine_minus(BH, w.z, Kmax, w.b, m, w.tm, m, w.nrm2b, st);  // H V z - b
+        }
+        const bool expand = k < n_outer - 1;
+        if (expand) {
+            {
+                Scope sc(tm, "backproject", st);
+                MOF_TRY(launch_backproject<real>(p, w.tm, w.tn, st));
+            }
+            {
+                Scope sc(tm, "reg_normal", st);
+                MOF_TRY(launch_reg_normal<real>(p, w.un, w.u, w.s, w.sr, w.radius, prm.eps, 1.0, w.lam, w.tn, w.q, w.r, st));
+            }
+            {
+                Scope sc(tm, "reorth", st);
+                kr.reorth(BV, w.r, n, w.coef, w.nrm2, st);
+                kr.append(BV, w.K, w.r, n, w.nrm2, w.scaleR, tol, w.grow, w.appended, w.vnew, st);
+            }
+            {
+                Scope sc(tm, "project", st);
+                MOF_TRY(launch_project<real>(p, w.vnew, w.uT, w.hvnew, st));
+                k_store_slot<real><<<fb(m), 256, 0, st>>>(w.HV, m, w.K, w.appended, w.hvnew);
+            }
+            {
+                Scope sc(tm, "gram_h", st);
+                BasisRef<real> BHn{w.HV, m, Kmax, 1, w.K, w.appended};
+                DotVecs<real> xs{{w.hvnew, w.b, nullptr}, {m, m, 0}};
+                DotOuts o{};
+                o.o[0] = DotOut{w.GH, 0, Kmax, 1, 1, 1.0};
+                o.o[1] = DotOut{w.gH, 0, 1, 0, 0, 1.0};
+                kr.multidot(BHn, 2, xs, o, st);
+                k_sym_last<<<1, 64, 0, st>>>(w.GH, Kmax, w.K, w.appended);
+            }
+        }
+        {
+            Scope sc(tm, "misc", st);
+            k_copy<real><<<fb(n), 256, 0, st>>>(w.un, w.u, n);
+            k_report<<<1, 1, 0, st>>>(w.report, k, w.lam, w.nrm2b, w.nrm2, w.K, w.flag, w.Kv_of, P, of_now ? 1 : 0,
+                                      expand ? 1 : 0, w.appended);
+        }
+    }
+    MOF_LAUNCH_CHECK();
+    if (u_out) MOF_CUDA(cudaMemcpyAsync(u_out, w.u, sizeof(real) * n, cudaMemcpyDeviceToDevice, st));
+    if (s_out) MOF_CUDA(cudaMemcpyAsync(s_out, w.s, sizeof(real) * 2 * P * ns, cudaMemcpyDeviceToDevice, st));
+    if (sr_out) MOF_CUDA(cudaMemcpyAsync(sr_out, w.sr, sizeof(real) * 2 * P * ns, cudaMemcpyDeviceToDevice, st));
+    std::vector<double> rep((size_t)n_outer * 8);
+    int err = 0;
+    MOF_CUDA(cudaMemcpyAsync(rep.data(), w.report, sizeof(double) * rep.size(), cudaMemcpyDeviceToHost, st));
+    MOF_CUDA(cudaMemcpyAsync(&err, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MOF_CUDA(cudaStreamSynchronize(st));
+    if (tm) tm->collect();
+    if (report)
+        for (int k = 0; k < n_outer; ++k) {
+            const double *r = &rep[(size_t)k * 8];
+            report[k].lambda = r[0];
+            report[k].resid = r[1];
+            report[k].rnorm = r[2];
+            report[k].basis = (int)r[3];
+            report[k].flag = (int)r[4];
+            report[k].of_basis_min = (int)r[5];
+            report[k].of_basis_max = (int)r[6];
+        }
+    if (err) return fail(MOF_ENUMERIC, "device reported a numerical failure (code %d): factorisation or non-finite value", err);
+    return MOF_OK;
+}
+
+template <typename real>
+static mof_status solve_of_entry(mof_problem *p, const mof_solver_params &prm, const real *u, real *s, cudaStream_t st) {
+    Holder *h = holder(p);
+    WS<real> *&wp = ws_slot<real>(h);
+    MOF_TRY(ensure_ws<real>(p, prm, 1, wp));
+    Timer *tm = p->timing ? &h->timer : nullptr;
+    if (tm) tm->reset();
+    k_fill_int<<<1, 32, 0, st>>>(wp->err, 1, 0);
+    MOF_TRY(solve_of_impl<real>(p, prm, *wp, u, s, tm, st));
+    int err = 0;
+    MOF_CUDA(cudaMemcpyAsync(&err, wp->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MOF_CUDA(cudaStreamSynchronize(st));
+    if (tm) tm->collect();
+    if (err) return fail(MOF_ENUMERIC, "device reported a numerical failure (code %d)", err);
+    return MOF_OK;
+}
+
+static mof_status check_params(const mof_problem *p, const mof_solver_params *prm, int n_outer) {
+    if (!p || !prm) return fail(MOF_EINVAL, "null problem or parameters");
+    if (n_outer < 1) return fail(MOF_EINVAL, "n_outer must be >= 1");
+    if (prm->ell < 1 || prm->of_ell < 1 || prm->of_iters < 1 || prm->tau < 0 || prm->of_dr < 1 || prm->of_dr > 64)
+        return fail(MOF_EINVAL, "invalid solver parameters");
+    if (prm->ell + n_outer > 64 || prm->of_ell + prm->of_iters > 64)
+        return fail(MOF_EUNSUPPORTED, "Krylov bases larger than 64 vectors are not supported (ell + n_outer = %d, of_ell + of_iters = %d)",
+                    prm->ell + n_outer, prm->of_ell + prm->of_iters);
+    if (!(prm->eps > 0) || !std::isfinite(prm->eps)) return fail(MOF_EINVAL, "eps must be finite and > 0");
+    if (prm->image_rule == MOF_RULE_DP && !(prm->noise_norm >= 0))
+        return fail(MOF_EINVAL, "the discrepancy principle needs noise_norm >= 0");
+    if (prm->image_rule == MOF_RULE_FIXED && !(prm->lam_fixed > 0)) return fail(MOF_EINVAL, "fixed rule needs lam_fixed > 0");
+    if (prm->image_rule < 0 || prm->image_rule > 2) return fail(MOF_EINVAL, "unknown image rule");
+    return MOF_OK;
+}
+
+}  // namespace mof
+
+using namespace mof;
+
+extern "C" {
+
+mof_status mof_solve_of(mof_problem *p, const mof_solver_params *prm, const void *u, void *s, void *stream) {
+    MOF_TRY(check_params(p, prm, 1));
+    if (!u || !s) return fail(MOF_EINVAL, "null array");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (p->precision == MOF_FP64) return solve_of_entry<double>(p, *prm, (const double *)u, (double *)s, st);
+    return solve_of_entry<float>(p, *prm, (const float *)u, (float *)s, st);
+}
+
+mof_status mof_solve(mof_problem *p, const mof_solver_params *prm, int n_outer, const void *b, void *u_out, void *s_out,
+                     void *sr_out, mof_report *report, void *stream) {
+    MOF_TRY(check_params(p, prm, n_outer));
+    if (!b || !u_out) return fail(MOF_EINVAL, "null b or u_out");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (p->precision == MOF_FP64)
+        return solve_impl<double>(p, *prm, n_outer, (const double *)b, (double *)u_out, (double *)s_out, (double *)sr_out,
+                                  report, st);
+    return solve_impl<float>(p, *prm, n_outer, (const float *)b, (float *)u_out, (float *)s_out, (float *)sr_out, report,
+                             st);
+}
+
+mof_status mof_solve_host(mof_problem *p, const mof_solver_params *prm, int n_outer, const void *b_host, void *u_host,
+                          void *s_host, void *sr_host, mof_report *report, void *stream) {
+    MOF_TRY(check_params(p, prm, n_outer));
+    if (!b_host || !u_host) return fail(MOF_EINVAL, "null b or u");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const size_t es = p->precision == MOF_FP64 ? 8 : 4;
+    Holder *h = holder(p);
+    if (!h->host_stage) MOF_CUDA(cudaMalloc(&h->host_stage, es * (p->m + p->n + 2 * p->nv) + 1024));
+    char *base = static_cast<char *>(h->host_stage);
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    void *db = base, *du = base + al(es * p->m), *ds = (char *)du + al(es * p->n), *dsr = (char *)ds + es * p->nv;
+    MOF_CUDA(cudaMemcpyAsync(db, b_host, es * p->m, cudaMemcpyHostToDevice, st));
+    MOF_TRY(mof_solve(p, prm, n_outer, db, du, s_host ? ds : nullptr, sr_host ? dsr : nullptr, report, stream));
+    MOF_CUDA(cudaMemcpyAsync(u_host, du, es * p->n, cudaMemcpyDeviceToHost, st));
+    if (s_host) MOF_CUDA(cudaMemcpyAsync(s_host, ds, es * p->nv, cudaMemcpyDeviceToHost, st));
+    if (sr_host) MOF_CUDA(cudaMemcpyAsync(sr_host, dsr, es * p->nv, cudaMemcpyDeviceToHost, st));
+    MOF_CUDA(cudaStreamSynchronize(st));
+    return MOF_OK;
+}
+
+mof_status mof_get_timing(const mof_problem *p, int cap, const char **names, double *ms, long long *launches, int *count) {
+    if (!p) return fail(MOF_EINVAL, "null problem");
+    const Holder *h = static_cast<const Holder *>(p->ws);
+    const int nc = h ? (int)h->timer.names.size() : 0;
+    if (count) *count = nc;
+    for (int i = 0; i < nc && i < cap; ++i) {
+        if (names) names[i] = h->timer.names[i].c_str();
+        if (ms) ms[i] = h->timer.ms[i];
+        if (launches) launches[i] = h->timer.count[i];
+    }
+    return MOF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,97 @@
+// Internal interfaces of the Krylov layer and the solver (krylov.cu,
+// small.cu, solver.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace mof {
+
+// ------------------------------------------------------ per-problem scratch
+// Small buffers of the stand-alone operator entry points, allocated on first
+// use and kept until mof_problem_destroy.
+enum ScratchKind { SCR_IMAGE = 0, SCR_RADIUS = 1, SCR_DEST = 2, SCR_FLOWROWS = 3, SCR_COUNT = 4 };
+mof_status apply_scratch(mof_problem *p, ScratchKind kind, void **out);
+void free_workspace(mof_problem *p);
+
+// ------------------------------------------------------------ Krylov bases
+template <typename real>
+struct BasisRef {
+    real *V;          // [B][Kmax][N]
+    long long N;      // vector length
+    int Kmax;
+    int B;            // number of independent problems
+    const int *K;     // device [B]: current basis size
+    const int *act;   // device [B] or null: problems with act[b] == 0 are skipped
+};
+
+// Up to three right-hand vectors of one batched multi-dot.
+template <typename real>
+struct DotVecs {
+    const real *x[3];
+    long long stride[3];  // between problems
+};
+// Output addressing of one dot result i (i < K[b]) of problem b:
+//   out[b*bstride + i*istride + col*jstride], col = K[b]-1 if last_col else 0.
+struct DotOut {
+    double *out;
+    long long bstride;
+    int istride;
+    int jstride;
+    int last_col;
+    double sign;
+};
+struct DotOuts {
+    DotOut o[3];
+};
+
+long long krylov_chunks(long long N);
+
+template <typename real>
+struct Krylov {
+    double *partial = nullptr;  // scratch [B][chunks][Kmax] (sized by the owner)
+    // out[b][j] = sign * <V[b][j], x[b]>, j < K[b]
+    void dots(const BasisRef<real> &B, const real *x, long long xstride, double *out, long long ostride, double sign,
+              cudaStream_t st) const;
+    // dots of every basis vector with nv (1..3) vectors in one pass over V
+    void multidot(const BasisRef<real> &B, int nv, const DotVecs<real> &xs, const DotOuts &outs, cudaStream_t st) const;
+    // out[b] = sum_j V[b][j] c[b][j]
+    void combine(const BasisRef<real> &B, const double *c, long long cstride, real *out, long long ostride,
+                 cudaStream_t st) const;
+    // out[b] = sum_j V[b][j] c[b][j] - x[b]; optionally ||out[b]||^2 -> nrm2_out[b]
+    void combine_minus(const BasisRef<real> &B, const double *c, long long cstride, const real *x, long long xstride,
+                       real *out, long long ostride, double *nrm2_out, cudaStream_t st) const;
+    // out[b] = x[b] - sum_j V[b][j] c[b][j]; optionally ||out[b]||^2 -> nrm2_out[b]
+    void subtract(const BasisRef<real> &B, const double *c, long long cstride, const real *x, long long xstride, real *out,
+                  long long ostride, double *nrm2_out, cudaStream_t st) const;
+    void norm2(const real *x, long long N, long long xstride, int nb, double *out, cudaStream_t st) const;
+    // x[b] <- (I - V V^T)^2 x[b] (classical Gram-Schmidt twice); ||x||^2 -> nrm2_out
+    void reorth(const BasisRef<real> &B, real *x, long long xstride, double *coef, double *nrm2_out, cudaStream_t st) const;
+    // V[b][K[b]] = x[b]/||x[b]||, K[b]++ unless ||x[b]|| <= tol*scale[b] (then grow[b] = 0);
+    // scale may be null (only ||x|| > 0 required); stage[b] (may be null) receives the new vector
+    void append(const BasisRef<real> &B, int *Kmut, const real *x, long long xstride, const double *nrm2,
+                const double *scale, double tol, int *grow, int *appended, real *stage, cudaStream_t st) const;
+};
+
+// ------------------------------------------------------ small FP64 solver
+// One projected problem per block: min ||A V z - b||^2 + lam ||L V z||^2
+// given G_A = (AV)^T(AV), G_L = (LV)^T(LV), g = (AV)^T b, bb = ||b||^2.
+struct SmallArgs {
+    const double *GA;      // [B][ld][ld]
+    const double *GL;      // [B][ld][ld]
+    const double *g;       // [B][ld]
+    const double *bb;      // [B]
+    const int *K;          // [B] problem dimension
+    const int *active;     // [B] (null = all active); inactive -> z = 0, lam = 0
+    int ld;                // leading dimension (Kmax)
+    int B;
+    int rule;              // MOF_RULE_*
+    double target2;        // DP: (eta delta)^2
+    double lam_fixed;
+    double *lam;           // [B] out
+    double *z;             // [B][ld] out
+    int *flag;             // [B] out: DP flag
+    int *err;              // error word (|= 1: factorisation failed, 2: non-finite)
+};
+mof_status launch_small_solve(const SmallArgs &a, cudaStream_t st);
+
+}  // namespace mof

@@ -1,0 +1,223 @@
+"""GPU parity of every operator of the hot path against the FP64 oracle.
+
+Inputs are seeded; the oracle receives exactly the values the GPU received
+(float32 inputs widened to float64). Bars: relative 2-norm error <= 1e-5 for
+the FP32 operators (the per-operator tolerance of the precision form), <= 1e-12
+for the FP64 build, bit-exact for the integer decisions (reverse-flow
+destinations). Sizes span several tiles with ragged tails, the 64x64x8
+workload and full 256x256 frames with 30 angles and 363 bins.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import ops as O
+from paper_2501_12497_gb300 import api, synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {api.MOF_FP32: 1e-5, api.MOF_FP64: 1e-12}
+DT = {api.MOF_FP32: (np.float32, torch.float32), api.MOF_FP64: (np.float64, torch.float64)}
+
+# (nx, ny, nt, na, nb): ragged tiles, the 64x64x8 workload, full-size frames
+SHAPES = [(37, 29, 3, 7, 45), (64, 64, 8, 16, 64), (256, 256, 3, 30, 363)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def rel(a, b):
+    return np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300)
+
+
+def make(shape, prec, seed=0, h=1.0, db=1.0):
+    nx, ny, nt, na, nb = shape
+    na_arr, ang = synth.shifted_angles(nt, na)
+    p = api.mof_problem_create(nx, ny, nt, nb, na_arr, ang, h, db, prec)
+    g = O.Geometry(nx, ny, nt, nb, na_arr, ang, h, db)
+    return p, g
+
+
+def dev(a, prec):
+    npdt, tdt = DT[prec]
+    return torch.tensor(np.ascontiguousarray(a, dtype=npdt), device="cuda").reshape(-1)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().double().numpy()
+
+
+def empty(n, prec):
+    return torch.full((n,), float("nan"), dtype=DT[prec][1], device="cuda")
+
+
+@pytest.mark.parametrize("prec", [api.MOF_FP32, api.MOF_FP64])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_project_and_backproject(shape, prec):
+    p, g = make(shape, prec)
+    nx, ny, nt = shape[:3]
+    u = synth.random_images(nt, ny, nx, seed=1)
+    b = np.random.default_rng(2).standard_normal(g.m)
+    ud, bd = dev(u, prec), dev(b, prec)
+    out_b, out_u = empty(p.m, prec), empty(p.n, prec)
+    api.mof_apply_A(p, ud, out_b)
+    api.mof_apply_AT(p, bd, out_u)
+    assert rel(host(out_b), O.project(g, host(ud))) <= TOL[prec]
+    assert rel(host(out_u), O.backproject(g, host(bd))) <= TOL[prec]
+
+
+def test_projector_general_pixel_and_bin_size():
+    """h != db: footprints span more than two bins in the backprojector."""
+    for prec in (api.MOF_FP32, api.MOF_FP64):
+        p, g = make((40, 33, 2, 9, 101), prec, h=1.7, db=0.6)
+        u = synth.random_images(2, 33, 40, seed=3)
+        b = np.random.default_rng(4).standard_normal(g.m)
+        ud, bd = dev(u, prec), dev(b, prec)
+        ob, ou = empty(p.m, prec), empty(p.n, prec)
+        api.mof_apply_A(p, ud, ob)
+        api.mof_apply_AT(p, bd, ou)
+        assert rel(host(ob), O.project(g, host(ud))) <= TOL[prec]
+        assert rel(host(ou), O.backproject(g, host(bd))) <= TOL[prec]
+
+
+def test_projector_adjoint_identity_fp32():
+    p, g = make((256, 256, 2, 30, 363), api.MOF_FP32)
+    u = dev(synth.random_images(2, 256, 256, seed=5), api.MOF_FP32)
+    b = dev(np.random.default_rng(6).standard_normal(g.m), api.MOF_FP32)
+    hb, hu = empty(p.m, api.MOF_FP32), empty(p.n, api.MOF_FP32)
+    api.mof_apply_A(p, u, hb)
+    api.mof_apply_AT(p, b, hu)
+    lhs = np.dot(host(hb), host(b))
+    rhs = np.dot(host(u), host(hu))
+    assert abs(lhs - rhs) <= 1e-5 * np.linalg.norm(host(hb)) * np.linalg.norm(host(b))
+
+
+@pytest.mark.parametrize("prec", [api.MOF_FP32, api.MOF_FP64])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_grad_and_transpose(shape, prec):
+    p, g = make(shape, prec)
+    nx, ny, nt = shape[:3]
+    u = dev(synth.random_images(nt, ny, nx, seed=7), prec)
+    gg = dev(np.random.default_rng(8).standard_normal(2 * p.n), prec)
+    og, ou = empty(2 * p.n, prec), empty(p.n, prec)
+    api.mof_apply_grad(p, u, og)
+    api.mof_apply_gradT(p, gg, ou)
+    assert rel(host(og), O.grad(host(u).reshape(nt, ny, nx))) <= TOL[prec]
+    assert rel(host(ou), O.gradT(host(gg).reshape(nt, 2, ny, nx))) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [api.MOF_FP32, api.MOF_FP64])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_flow_and_transpose(shape, prec):
+    p, g = make(shape, prec)
+    nx, ny, nt = shape[:3]
+    u = dev(synth.random_images(nt, ny, nx, seed=9), prec)
+    s = dev(synth.random_velocities(nt - 1, ny, nx, 2.5, seed=10), prec)
+    sr = dev(synth.random_velocities(nt - 1, ny, nx, 3.5, seed=11), prec)
+    r = dev(np.random.default_rng(12).standard_normal(2 * (nt - 1) * nx * ny), prec)
+    orr, ou = empty(r.numel(), prec), empty(p.n, prec)
+    api.mof_apply_flow(p, u, s, sr, orr)
+    api.mof_apply_flowT(p, r, s, sr, ou)
+    sh = (nt - 1, 2, ny, nx)
+    hs, hsr = host(s).reshape(sh), host(sr).reshape(sh)
+    assert rel(host(orr), O.flow(host(u).reshape(nt, ny, nx), hs, hsr)) <= TOL[prec]
+    assert rel(host(ou), O.flowT(host(r).reshape(2, nt - 1, ny, nx), hs, hsr)) <= TOL[prec]
+
+
+def test_flow_large_and_out_of_grid_velocities():
+    """Velocities that push samples far outside the frame (clipping) and a wide window."""
+    prec = api.MOF_FP32
+    shape = (48, 40, 3, 4, 40)
+    p, g = make(shape, prec)
+    nx, ny, nt = shape[:3]
+    rng = np.random.default_rng(13)
+    u = dev(synth.random_images(nt, ny, nx, seed=14), prec)
+    s = dev(rng.uniform(-9, 9, (nt - 1, 2, ny, nx)), prec)
+    sr = dev(rng.uniform(-1, 1, (nt - 1, 2, ny, nx)), prec)
+    r = dev(rng.standard_normal(2 * (nt - 1) * nx * ny), prec)
+    orr, ou = empty(r.numel(), prec), empty(p.n, prec)
+    api.mof_apply_flow(p, u, s, sr, orr)
+    api.mof_apply_flowT(p, r, s, sr, ou)
+    sh = (nt - 1, 2, ny, nx)
+    assert rel(host(orr), O.flow(host(u).reshape(nt, ny, nx), host(s).reshape(sh), host(sr).reshape(sh))) <= 1e-5
+    assert rel(host(ou), O.flowT(host(r).reshape(2, nt - 1, ny, nx), host(s).reshape(sh), host(sr).reshape(sh))) <= 1e-5
+
+
+@pytest.mark.parametrize("prec", [api.MOF_FP32, api.MOF_FP64])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_of_fields_flow_lin_and_vgrad(shape, prec):
+    p, g = make(shape, prec)
+    nx, ny, nt = shape[:3]
+    P = nt - 1
+    u = dev(synth.random_images(nt, ny, nx, seed=15), prec)
+    for dr in (1, 2):
+        ux, uy, ut = (empty(P * nx * ny, prec) for _ in range(3))
+        api.mof_of_fields(p, u, dr, ux, uy, ut)
+        rx, ry, rt = O.of_fields(host(u).reshape(nt, ny, nx), dr)
+        assert rel(host(ux), rx) <= TOL[prec] and rel(host(uy), ry) <= TOL[prec] and rel(host(ut), rt) <= TOL[prec]
+    s = dev(synth.random_velocities(P, ny, nx, 2.0, seed=16), prec)
+    r = dev(np.random.default_rng(17).standard_normal(P * nx * ny), prec)
+    lin, gs = empty(P * nx * ny, prec), empty(p.nv, prec)
+    api.mof_apply_flow_lin(p, ux, uy, ut, s, lin)
+    api.mof_apply_flow_linT(p, ux, uy, r, gs)
+    sh = (P, ny, nx)
+    hux, huy, hut = host(ux).reshape(sh), host(uy).reshape(sh), host(ut).reshape(sh)
+    assert rel(host(lin), O.flow_lin(hux, huy, hut, host(s).reshape(P, 2, ny, nx))) <= TOL[prec]
+    assert rel(host(gs), O.flow_linT(hux, huy, host(r).reshape(sh))) <= TOL[prec]
+    vg, vt = empty(2 * p.nv, prec), empty(p.nv, prec)
+    gsv = dev(np.random.default_rng(18).standard_normal(2 * p.nv), prec)
+    api.mof_apply_vgrad(p, s, vg)
+    api.mof_apply_vgradT(p, gsv, vt)
+    assert rel(host(vg), O.vgrad(host(s).reshape(P, 2, ny, nx))) <= TOL[prec]
+    assert rel(host(vt), O.vgradT(host(gsv).reshape(P, 2, 2, ny, nx))) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [api.MOF_FP32, api.MOF_FP64])
+def test_reverse_flow_bit_exact(prec):
+    """Destinations are integer decisions: identical to the oracle's, so the averaged
+    reverse velocities agree to rounding (FP32: the cast of an FP64 average)."""
+    shape = (53, 47, 4, 4, 40)
+    p, g = make(shape, prec)
+    nx, ny, nt = shape[:3]
+    rng = np.random.default_rng(19)
+    sv = synth.random_velocities(nt - 1, ny, nx, 3.0, seed=20)
+    # plant exact half-way positions and negative half-way positions
+    sv[0, 0, :5, :5] = 0.5
+    sv[0, 0, 5:10, :5] = -0.5
+    sv[1, 1, :7, :] = -1.5
+    s = dev(sv, prec)
+    sr = empty(p.nv, prec)
+    api.mof_reverse_flow(p, s, sr)
+    want = O.reverse_flow(host(s).reshape(nt - 1, 2, ny, nx))
+    got = host(sr).reshape(want.shape)
+    if prec == api.MOF_FP64:
+        np.testing.assert_array_equal(got, want)
+    else:
+        np.testing.assert_array_equal(got, want.astype(np.float32).astype(np.float64))
+
+
+@pytest.mark.parametrize("prec", [api.MOF_FP32, api.MOF_FP64])
+@pytest.mark.parametrize("shape", SHAPES[:2] + [(256, 256, 3, 30, 363)])
+def test_reg_normal(shape, prec):
+    """y = Theta^T W Theta x with W from uk (Alg. 1 weights), against the oracle's Theta."""
+    from oracle import solver as OS
+    p, g = make(shape, prec)
+    nx, ny, nt = shape[:3]
+    x = dev(synth.random_images(nt, ny, nx, seed=21), prec)
+    uk = dev(synth.random_images(nt, ny, nx, seed=22), prec)
+    s = dev(synth.random_velocities(nt - 1, ny, nx, 2.0, seed=23), prec)
+    sr = dev(synth.random_velocities(nt - 1, ny, nx, 2.0, seed=24), prec)
+    eps = 0.05
+    y = empty(p.n, prec)
+    api.mof_apply_reg_normal(p, x, uk, s, sr, eps, y)
+    sh = (nt - 1, 2, ny, nx)
+    th = OS.Theta((nt, ny, nx), host(s).reshape(sh), host(sr).reshape(sh))
+    nu = th(host(uk))
+    w = 1.0 / np.sqrt(nu * nu + eps * eps)
+    want = th.T(w * th(host(x)))
+    assert rel(host(y), want) <= 3 * TOL[prec]
