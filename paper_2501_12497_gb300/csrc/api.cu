@@ -63,7 +63,8 @@ static AngleParams angle_params(double theta, int frame, int nx, int ny, int nb,
     P.f0_c = -0.5 * (nb - 1) * db / (cc * h) + 0.5 * (nfast - 1) + 0.5 * (nstep - 1) * (ss / cc);
     P.df = -ss / cc;
     split12(P.df, P.df_hi, P.df_lo);
-    P.wstep = (float)(h / std::fabs(cc));
+    P.wstep_d = h / std::fabs(cc);
+    P.wstep = (float)P.wstep_d;
     // t(i, j) = (x_i c + y_j s)/db + (nb-1)/2
     P.tA = h * c / db;
     P.tB = h * s / db;
@@ -71,8 +72,10 @@ static AngleParams angle_params(double theta, int frame, int nx, int ny, int nb,
     split12(P.tA, P.tA_hi, P.tA_lo);
     split12(P.tB, P.tB_hi, P.tB_lo);
     const double mu = std::fmax(std::fabs(c), std::fabs(s));
-    P.rfoot = (float)(mu * h / db);
-    P.wfoot = (float)(h / mu);
+    P.rfoot_d = mu * h / db;
+    P.wfoot_d = h / mu;
+    P.rfoot = (float)P.rfoot_d;
+    P.wfoot = (float)P.wfoot_d;
     return P;
 }
 
@@ -228,12 +231,13 @@ mof_status mof_apply_flowT(mof_problem *p, const void *r, const void *s, const v
     if (!u || !s || !sr || !r) return fail(MOF_EINVAL, "null array");
     void *rad = nullptr;
     MOF_TRY(apply_scratch(p, SCR_RADIUS, &rad));
+    int *rs = (int *)rad, *rr = rs + (long long)(p->nt - 1) * tiles_count(p);
     if (p->precision == MOF_FP64) {
-        MOF_TRY(launch_window_radius<double>(p, CD(s), CD(sr), (int *)rad, S(stream)));
-        return launch_flowT<double>(p, CD(r), CD(s), CD(sr), (const int *)rad, D(u), S(stream));
+        MOF_TRY(launch_tile_radii<double>(p, CD(s), CD(sr), rs, rr, S(stream)));
+        return launch_flowT<double>(p, CD(r), CD(s), CD(sr), rs, rr, D(u), S(stream));
     }
-    MOF_TRY(launch_window_radius<float>(p, CF(s), CF(sr), (int *)rad, S(stream)));
-    return launch_flowT<float>(p, CF(r), CF(s), CF(sr), (const int *)rad, F(u), S(stream));
+    MOF_TRY(launch_tile_radii<float>(p, CF(s), CF(sr), rs, rr, S(stream)));
+    return launch_flowT<float>(p, CF(r), CF(s), CF(sr), rs, rr, F(u), S(stream));
 }
 
 mof_status mof_of_fields(mof_problem *p, const void *u, int dr, void *ux, void *uy, void *ut, void *stream) {
@@ -287,12 +291,8 @@ mof_status mof_reverse_flow(mof_problem *p, const void *s, void *sr, void *strea
     void *rad = nullptr, *dest = nullptr;
     MOF_TRY(apply_scratch(p, SCR_RADIUS, &rad));
     MOF_TRY(apply_scratch(p, SCR_DEST, &dest));
-    if (p->precision == MOF_FP64) {
-        MOF_TRY(launch_window_radius<double>(p, CD(s), nullptr, (int *)rad, S(stream)));
-        return launch_reverse_flow<double>(p, CD(s), (const int *)rad, (int *)dest, D(sr), S(stream));
-    }
-    MOF_TRY(launch_window_radius<float>(p, CF(s), nullptr, (int *)rad, S(stream)));
-    return launch_reverse_flow<float>(p, CF(s), (const int *)rad, (int *)dest, F(sr), S(stream));
+    if (p->precision == MOF_FP64) return launch_reverse_flow<double>(p, CD(s), (int *)rad, (int *)dest, D(sr), S(stream));
+    return launch_reverse_flow<float>(p, CF(s), (int *)rad, (int *)dest, F(sr), S(stream));
 }
 
 mof_status mof_apply_reg_normal(mof_problem *p, const void *x, const void *uk, const void *s, const void *sr, double eps,
@@ -304,14 +304,15 @@ mof_status mof_apply_reg_normal(mof_problem *p, const void *x, const void *uk, c
     void *rad = nullptr, *q = nullptr;
     MOF_TRY(apply_scratch(p, SCR_RADIUS, &rad));
     MOF_TRY(apply_scratch(p, SCR_FLOWROWS, &q));
+    int *rs = (int *)rad, *rr = rs + (long long)(p->nt - 1) * tiles_count(p);
     if (p->precision == MOF_FP64) {
-        MOF_TRY(launch_window_radius<double>(p, CD(s), CD(sr), (int *)rad, S(stream)));
-        return launch_reg_normal<double>(p, CD(x), CD(uk), CD(s), CD(sr), (const int *)rad, eps, 1.0, nullptr, nullptr,
-                                         D(q), D(y), S(stream));
+        MOF_TRY(launch_tile_radii<double>(p, CD(s), CD(sr), rs, rr, S(stream)));
+        return launch_reg_normal<double>(p, CD(x), CD(uk), CD(s), CD(sr), rs, rr, eps, 1.0, nullptr, nullptr, D(q), D(y),
+                                         S(stream));
     }
-    MOF_TRY(launch_window_radius<float>(p, CF(s), CF(sr), (int *)rad, S(stream)));
-    return launch_reg_normal<float>(p, CF(x), CF(uk), CF(s), CF(sr), (const int *)rad, eps, 1.0, nullptr, nullptr, F(q),
-                                    F(y), S(stream));
+    MOF_TRY(launch_tile_radii<float>(p, CF(s), CF(sr), rs, rr, S(stream)));
+    return launch_reg_normal<float>(p, CF(x), CF(uk), CF(s), CF(sr), rs, rr, eps, 1.0, nullptr, nullptr, F(q), F(y),
+                                    S(stream));
 }
 
 mof_status mof_set_timing(mof_problem *p, int enable) {

@@ -56,6 +56,7 @@ struct AngleParams {
     float wfoot;        // footprint height h / mu
     int frame;          // frame this angle belongs to
     int pad_;
+    double wstep_d, rfoot_d, wfoot_d;  // the same three in FP64 (FP64 kernels)
 };
 
 }  // namespace mof
@@ -83,18 +84,20 @@ template <typename real> mof_status launch_backproject(const mof_problem *p, con
 template <typename real> mof_status launch_grad(const mof_problem *p, int nf, const real *u, real *g, cudaStream_t st);
 template <typename real> mof_status launch_gradT(const mof_problem *p, int nf, const real *g, real *u, cudaStream_t st);
 template <typename real> mof_status launch_flow(const mof_problem *p, const real *u, const real *s, const real *sr, real *r, cudaStream_t st);
-template <typename real> mof_status launch_window_radius(const mof_problem *p, const real *s, const real *sr, int *d_radius, cudaStream_t st);
-template <typename real> mof_status launch_flowT(const mof_problem *p, const real *r, const real *s, const real *sr, const int *d_radius, real *u, cudaStream_t st);
+// Per-tile gather radii of the warp transposes (rad_* hold (nt-1) * tiles_count ints).
+int tiles_count(const mof_problem *p);
+template <typename real> mof_status launch_tile_radii(const mof_problem *p, const real *s, const real *sr, int *rad_s, int *rad_sr, cudaStream_t st);
+template <typename real> mof_status launch_flowT(const mof_problem *p, const real *r, const real *s, const real *sr, const int *rad_s, const int *rad_sr, real *u, cudaStream_t st);
 template <typename real> mof_status launch_of_fields(const mof_problem *p, const real *u, int dr, real *ux, real *uy, real *ut, cudaStream_t st);
 template <typename real> mof_status launch_flow_lin(const mof_problem *p, const real *ux, const real *uy, const real *ut, const real *s, real *r, cudaStream_t st);
 template <typename real> mof_status launch_flow_linT(const mof_problem *p, const real *ux, const real *uy, const real *r, real *gs, cudaStream_t st);
-template <typename real> mof_status launch_reverse_flow(const mof_problem *p, const real *s, const int *d_radius, int *dest_scratch, real *sr, cudaStream_t st);
+template <typename real> mof_status launch_reverse_flow(const mof_problem *p, const real *s, int *rad_scratch, int *dest_scratch, real *sr, cudaStream_t st);
 // Weighted regulariser normal operator: y = y_add + scale * Theta^T W Theta x,
 // W from uk; q_scratch holds 2*(nt-1)*ns weighted flow rows. lam_dev (may be
 // null) multiplies `scale` by *lam_dev.
 template <typename real> mof_status launch_reg_normal(const mof_problem *p, const real *x, const real *uk, const real *s, const real *sr,
-                                                      const int *d_radius, double eps, double scale, const double *lam_dev, const real *y_add,
-                                                      real *q_scratch, real *y, cudaStream_t st);
+                                                      const int *rad_s, const int *rad_sr, double eps, double scale, const double *lam_dev,
+                                                      const real *y_add, real *q_scratch, real *y, cudaStream_t st);
 
 // ----------------------------------------------------------- device helpers
 template <typename T>

@@ -6,11 +6,13 @@
 //   K7  App. C derivative fields u_x, u_y, u_t
 //   K8  Upsilon s + u_t, Upsilon^T r (Sec. 2.2)
 //
-// The transposes of the warp are computed as deterministic gathers: an output
-// pixel q collects the contributions of the sources p within a window of
-// radius R = floor(max |s|) + 1 around q (a source can only reach the four
-// pixels around r + s(r), and clipping only moves the sample towards r), in
-// a fixed order, so repeated runs are bit-identical.
+// The transposes of the warp (and the reverse flow) are computed as
+// deterministic gathers: an output pixel q collects the contributions of the
+// sources p within a square window around q, in a fixed order, so repeated
+// runs are bit-identical. The window radius is per 32x8 output tile: every
+// source records, in the tile of each pixel it reaches, the Chebyshev
+// distance to that pixel (atomic max), so a tile scans only as far as its
+// farthest actual arrival.
 #include "common.cuh"
 
 #include <cfloat>
@@ -147,89 +149,99 @@ mof_status launch_flow(const mof_problem *p, const real *u, const real *s, const
     return MOF_OK;
 }
 
-// Window radius for the transposes: R = floor(max |v|) + 1 over the given
-// fields (sr may be null), as an int written to *d_radius. A non-finite
-// velocity sets R = -1 (the gathers then treat the warp as the identity and
-// the solver reports MOF_ENUMERIC).
+// Per-tile gather radii of M(v)^T for nf velocity fields v[f] (each [2][ny][nx]):
+// rad[f][tile] = max over sources p and the pixels q of their bilinear
+// footprint, q in the tile, of |p - q|_inf. Launched with the gather tiling.
 template <typename real>
-__global__ void k_absmax(const real *__restrict__ a, long long n, unsigned *__restrict__ out) {
-    float m = 0.0f;
-    bool bad = false;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const real v = a[i];
-        if (!(v == v) || v > (real)FLT_MAX || v < -(real)FLT_MAX) bad = true;
-        else m = fmaxf(m, (float)fabs((double)v));
+__global__ void k_tile_radius(const real *__restrict__ v, int nx, int ny, int *__restrict__ rad, int tiles_x, int tiles) {
+    __shared__ int own;
+    const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, f = blockIdx.z;
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    if (tid == 0) own = 0;
+    __syncthreads();
+    if (x < nx && y < ny) {
+        const long long ns = (long long)nx * ny, i = (long long)y * nx + x;
+        const real *vf = v + 2LL * f * ns;
+        int x0, x1, y0, y1;
+        real wx, wy;
+        warp_axis(x, vf[i], nx, x0, x1, wx);
+        warp_axis(y, vf[ns + i], ny, y0, y1, wy);
+        const int qx[2] = {x0, x1}, qy[2] = {y0, y1};
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int d = max(abs(qx[a] - x), abs(qy[c] - y));
+                const int tx = qx[a] / TX, ty = qy[c] / TY;
+                if (tx == (int)blockIdx.x && ty == (int)blockIdx.y) atomicMax(&own, d);
+                else atomicMax(&rad[(long long)f * tiles + ty * tiles_x + tx], d);
+            }
     }
-    m = warp_maxf(m);
-    const unsigned badw = __any_sync(0xffffffffu, bad);
-    if ((threadIdx.x & 31) == 0) atomicMax(out, badw ? 0x7f800000u : __float_as_uint(m));
+    __syncthreads();
+    if (tid == 0) atomicMax(&rad[(long long)f * tiles + blockIdx.y * tiles_x + blockIdx.x], own);
 }
 
-__global__ void k_radius_finish(const unsigned *__restrict__ bits, int *__restrict__ radius, int cap) {
-    const unsigned b = bits[0];
-    if (b >= 0x7f800000u) { *radius = -1; return; }
-    const float m = __uint_as_float(b);
-    *radius = (int)fminf(floorf(m) + 1.0f, (float)cap);
+__global__ void k_zero_ints(int *p, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) p[i] = 0;
 }
 
-__global__ void k_zero_u32(unsigned *p) { *p = 0u; }
+int tiles_x(const mof_problem *p) { return (p->nx + TX - 1) / TX; }
+int tiles_count(const mof_problem *p) { return tiles_x(p) * ((p->ny + TY - 1) / TY); }
 
 template <typename real>
-mof_status launch_window_radius(const mof_problem *p, const real *s, const real *sr, int *d_radius, cudaStream_t st) {
-    // the int slot right after *d_radius holds the running max bits
-    unsigned *bits = reinterpret_cast<unsigned *>(d_radius + 1);
-    k_zero_u32<<<1, 1, 0, st>>>(bits);
+mof_status launch_tile_radii(const mof_problem *p, const real *s, const real *sr, int *rad_s, int *rad_sr, cudaStream_t st) {
+    const int np = p->nt - 1, tiles = tiles_count(p);
+    k_zero_ints<<<8, 256, 0, st>>>(rad_s, (long long)np * tiles);
     MOF_LAUNCH_CHECK();
-    const long long nv = p->nv;
-    const int blocks = (int)std::min<long long>(1184, (nv + 255) / 256);
-    k_absmax<real><<<blocks, 256, 0, st>>>(s, nv, bits);
+    k_tile_radius<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(s, p->nx, p->ny, rad_s, tiles_x(p), tiles);
     MOF_LAUNCH_CHECK();
     if (sr) {
-        k_absmax<real><<<blocks, 256, 0, st>>>(sr, nv, bits);
+        k_zero_ints<<<8, 256, 0, st>>>(rad_sr, (long long)np * tiles);
+        MOF_LAUNCH_CHECK();
+        k_tile_radius<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(sr, p->nx, p->ny, rad_sr, tiles_x(p), tiles);
         MOF_LAUNCH_CHECK();
     }
-    k_radius_finish<<<1, 1, 0, st>>>(bits, d_radius, std::max(p->nx, p->ny));
-    MOF_LAUNCH_CHECK();
     return MOF_OK;
 }
 
 // u = Mhat^T r (+ optional addend, times scale), one thread per pixel of a frame:
 //   u_t = [t<P] r0_t + [t>0] r1_{t-1} - [t<P] M(sr_t)^T r1_t - [t>0] M(s_{t-1})^T r0_{t-1}
 template <typename real>
-__device__ __forceinline__ real flowT_at(const real *__restrict__ r, const real *__restrict__ s,
-                                         const real *__restrict__ sr, int nx, int ny, int np, int t,
-                                         int x, int y, int R) {
+__device__ __forceinline__ real flowT_at(const real *__restrict__ r, const real *__restrict__ s, const real *__restrict__ sr,
+                                         int nx, int ny, int np, int t, int x, int y, const int *__restrict__ rad_s,
+                                         const int *__restrict__ rad_sr, int tiles, int tile) {
     const long long ns = (long long)nx * ny, i = (long long)y * nx + x;
-    const int Rw = R < 0 ? 0 : R;
     real v = 0;
     if (t < np) {
         const real *r1 = r + (np + t) * ns;
         const real *srp = sr + 2LL * t * ns;
         v += r[t * ns + i];
-        v -= R < 0 ? r1[i] : warpT_gather(r1, srp, srp + ns, nx, ny, x, y, Rw);
+        v -= warpT_gather(r1, srp, srp + ns, nx, ny, x, y, rad_sr[(long long)t * tiles + tile]);
     }
     if (t > 0) {
         const real *r0 = r + (long long)(t - 1) * ns;
         const real *sp = s + 2LL * (t - 1) * ns;
         v += r[(np + t - 1) * ns + i];
-        v -= R < 0 ? r0[i] : warpT_gather(r0, sp, sp + ns, nx, ny, x, y, Rw);
+        v -= warpT_gather(r0, sp, sp + ns, nx, ny, x, y, rad_s[(long long)(t - 1) * tiles + tile]);
     }
     return v;
 }
 
 template <typename real>
 __global__ void k_flowT(const real *__restrict__ r, const real *__restrict__ s, const real *__restrict__ sr,
-                        const int *__restrict__ radius, real *__restrict__ u, int nx, int ny, int np) {
+                        const int *__restrict__ rad_s, const int *__restrict__ rad_sr, real *__restrict__ u, int nx, int ny,
+                        int np, int tiles) {
     const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, t = blockIdx.z;
     if (x >= nx || y >= ny) return;
-    const int R = *radius;
-    u[(long long)t * nx * ny + (long long)y * nx + x] = flowT_at(r, s, sr, nx, ny, np, t, x, y, R);
+    const int tile = blockIdx.y * gridDim.x + blockIdx.x;
+    u[(long long)t * nx * ny + (long long)y * nx + x] = flowT_at(r, s, sr, nx, ny, np, t, x, y, rad_s, rad_sr, tiles, tile);
 }
 
 template <typename real>
-mof_status launch_flowT(const mof_problem *p, const real *r, const real *s, const real *sr, const int *d_radius, real *u,
-                        cudaStream_t st) {
-    k_flowT<real><<<grid2d(p->nx, p->ny, p->nt), dim3(TX, TY), 0, st>>>(r, s, sr, d_radius, u, p->nx, p->ny, p->nt - 1);
+mof_status launch_flowT(const mof_problem *p, const real *r, const real *s, const real *sr, const int *rad_s,
+                        const int *rad_sr, real *u, cudaStream_t st) {
+    k_flowT<real><<<grid2d(p->nx, p->ny, p->nt), dim3(TX, TY), 0, st>>>(r, s, sr, rad_s, rad_sr, u, p->nx, p->ny, p->nt - 1,
+                                                                      tiles_count(p));
     MOF_LAUNCH_CHECK();
     return MOF_OK;
 }
@@ -253,24 +265,36 @@ __device__ __forceinline__ int round_axis(int x, real v, int n) {
 }
 
 template <typename real>
-__global__ void k_rev_dest(const real *__restrict__ s, int *__restrict__ dest, int nx, int ny) {
+__global__ void k_rev_dest(const real *__restrict__ s, int *__restrict__ dest, int *__restrict__ rad, int nx, int ny,
+                           int tiles_x, int tiles) {
+    __shared__ int own;
     const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, p = blockIdx.z;
-    if (x >= nx || y >= ny) return;
-    const long long ns = (long long)nx * ny, i = (long long)y * nx + x;
-    const real *sp = s + 2LL * p * ns;
-    const int dx = round_axis(x, sp[i], nx), dy = round_axis(y, sp[ns + i], ny);
-    dest[p * ns + i] = dy * nx + dx;
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    if (tid == 0) own = 0;
+    __syncthreads();
+    if (x < nx && y < ny) {
+        const long long ns = (long long)nx * ny, i = (long long)y * nx + x;
+        const real *sp = s + 2LL * p * ns;
+        const int dx = round_axis(x, sp[i], nx), dy = round_axis(y, sp[ns + i], ny);
+        dest[p * ns + i] = dy * nx + dx;
+        const int d = max(abs(dx - x), abs(dy - y));
+        const int tx = dx / TX, ty = dy / TY;
+        if (tx == (int)blockIdx.x && ty == (int)blockIdx.y) atomicMax(&own, d);
+        else atomicMax(&rad[(long long)p * tiles + ty * tiles_x + tx], d);
+    }
+    __syncthreads();
+    if (tid == 0) atomicMax(&rad[(long long)p * tiles + blockIdx.y * tiles_x + blockIdx.x], own);
 }
 
 template <typename real>
-__global__ void k_rev_gather(const real *__restrict__ s, const int *__restrict__ dest, const int *__restrict__ radius,
-                             real *__restrict__ sr, int nx, int ny) {
+__global__ void k_rev_gather(const real *__restrict__ s, const int *__restrict__ dest, const int *__restrict__ rad,
+                             real *__restrict__ sr, int nx, int ny, int tiles) {
     const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, p = blockIdx.z;
     if (x >= nx || y >= ny) return;
     const long long ns = (long long)nx * ny, q = (long long)y * nx + x;
     const real *sx = s + 2LL * p * ns, *sy = sx + ns;
     const int *dp = dest + p * ns;
-    const int R = max(*radius, 0);
+    const int R = rad[(long long)p * tiles + blockIdx.y * gridDim.x + blockIdx.x];
     double ax = 0.0, ay = 0.0;
     int cnt = 0;
     // sources in row-major order, as the arrivals are accumulated in order of source
@@ -291,11 +315,13 @@ __global__ void k_rev_gather(const real *__restrict__ s, const int *__restrict__
 }
 
 template <typename real>
-mof_status launch_reverse_flow(const mof_problem *p, const real *s, const int *d_radius, int *dest, real *sr, cudaStream_t st) {
-    const int np = p->nt - 1;
-    k_rev_dest<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(s, dest, p->nx, p->ny);
+mof_status launch_reverse_flow(const mof_problem *p, const real *s, int *rad, int *dest, real *sr, cudaStream_t st) {
+    const int np = p->nt - 1, tiles = tiles_count(p);
+    k_zero_ints<<<8, 256, 0, st>>>(rad, (long long)np * tiles);
     MOF_LAUNCH_CHECK();
-    k_rev_gather<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(s, dest, d_radius, sr, p->nx, p->ny);
+    k_rev_dest<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(s, dest, rad, p->nx, p->ny, tiles_x(p), tiles);
+    MOF_LAUNCH_CHECK();
+    k_rev_gather<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(s, dest, rad, sr, p->nx, p->ny, tiles);
     MOF_LAUNCH_CHECK();
     return MOF_OK;
 }
@@ -402,9 +428,10 @@ __global__ void k_regn_flow_rows(const real *__restrict__ x, const real *__restr
 // Stage 2: y = y_add + scale * (Psi^T W_Psi Psi x + Mhat^T q).
 template <typename real>
 __global__ void k_regn_apply(const real *__restrict__ x, const real *__restrict__ uk, const real *__restrict__ s,
-                             const real *__restrict__ sr, const real *__restrict__ q, const int *__restrict__ radius,
-                             real eps2, double scale, const double *__restrict__ lam, const real *__restrict__ y_add,
-                             real *__restrict__ y, int nx, int ny, int np) {
+                             const real *__restrict__ sr, const real *__restrict__ q, const int *__restrict__ rad_s,
+                             const int *__restrict__ rad_sr, int tiles, real eps2, double scale,
+                             const double *__restrict__ lam, const real *__restrict__ y_add, real *__restrict__ y, int nx,
+                             int ny, int np) {
     const int xx = blockIdx.x * TX + threadIdx.x, yy = blockIdx.y * TY + threadIdx.y, t = blockIdx.z;
     if (xx >= nx || yy >= ny) return;
     const long long ns = (long long)nx * ny, i = (long long)yy * nx + xx;
@@ -423,7 +450,7 @@ __global__ void k_regn_apply(const real *__restrict__ x, const real *__restrict_
     if (xx < nx - 1) v -= wdx(i);
     if (yy > 0) v += wdy(i - nx);
     if (yy < ny - 1) v -= wdy(i);
-    if (np > 0) v += flowT_at(q, s, sr, nx, ny, np, t, xx, yy, *radius);
+    if (np > 0) v += flowT_at(q, s, sr, nx, ny, np, t, xx, yy, rad_s, rad_sr, tiles, blockIdx.y * gridDim.x + blockIdx.x);
     const double sc = lam ? scale * *lam : scale;
     const real out = (real)sc * v;
     y[t * ns + i] = y_add ? y_add[t * ns + i] + out : out;
@@ -431,16 +458,16 @@ __global__ void k_regn_apply(const real *__restrict__ x, const real *__restrict_
 
 template <typename real>
 mof_status launch_reg_normal(const mof_problem *p, const real *x, const real *uk, const real *s, const real *sr,
-                             const int *d_radius, double eps, double scale, const double *lam_dev, const real *y_add,
-                             real *q, real *y, cudaStream_t st) {
+                             const int *rad_s, const int *rad_sr, double eps, double scale, const double *lam_dev,
+                             const real *y_add, real *q, real *y, cudaStream_t st) {
     const int np = p->nt - 1;
     const real eps2 = (real)(eps * eps);
     if (np > 0) {
         k_regn_flow_rows<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(x, uk, s, sr, eps2, q, p->nx, p->ny, np);
         MOF_LAUNCH_CHECK();
     }
-    k_regn_apply<real><<<grid2d(p->nx, p->ny, p->nt), dim3(TX, TY), 0, st>>>(x, uk, s, sr, q, d_radius, eps2, scale, lam_dev,
-                                                                            y_add, y, p->nx, p->ny, np);
+    k_regn_apply<real><<<grid2d(p->nx, p->ny, p->nt), dim3(TX, TY), 0, st>>>(x, uk, s, sr, q, rad_s, rad_sr, tiles_count(p),
+                                                                            eps2, scale, lam_dev, y_add, y, p->nx, p->ny, np);
     MOF_LAUNCH_CHECK();
     return MOF_OK;
 }
@@ -449,18 +476,18 @@ mof_status launch_reg_normal(const mof_problem *p, const real *x, const real *uk
     template mof_status launch_grad<real>(const mof_problem *, int, const real *, real *, cudaStream_t);                      \
     template mof_status launch_gradT<real>(const mof_problem *, int, const real *, real *, cudaStream_t);                     \
     template mof_status launch_flow<real>(const mof_problem *, const real *, const real *, const real *, real *, cudaStream_t); \
-    template mof_status launch_window_radius<real>(const mof_problem *, const real *, const real *, int *, cudaStream_t);     \
-    template mof_status launch_flowT<real>(const mof_problem *, const real *, const real *, const real *, const int *, real *, \
-                                           cudaStream_t);                                                                     \
-    template mof_status launch_reverse_flow<real>(const mof_problem *, const real *, const int *, int *, real *, cudaStream_t); \
+    template mof_status launch_tile_radii<real>(const mof_problem *, const real *, const real *, int *, int *, cudaStream_t);  \
+    template mof_status launch_flowT<real>(const mof_problem *, const real *, const real *, const real *, const int *,         \
+                                           const int *, real *, cudaStream_t);                                                \
+    template mof_status launch_reverse_flow<real>(const mof_problem *, const real *, int *, int *, real *, cudaStream_t);     \
     template mof_status launch_of_fields<real>(const mof_problem *, const real *, int, real *, real *, real *, cudaStream_t);   \
     template mof_status launch_flow_lin<real>(const mof_problem *, const real *, const real *, const real *, const real *,     \
                                               real *, cudaStream_t);                                                          \
     template mof_status launch_flow_linT<real>(const mof_problem *, const real *, const real *, const real *, real *,          \
                                                cudaStream_t);                                                                 \
     template mof_status launch_reg_normal<real>(const mof_problem *, const real *, const real *, const real *, const real *,   \
-                                                const int *, double, double, const double *, const real *, real *, real *,    \
-                                                cudaStream_t);
+                                                const int *, const int *, double, double, const double *, const real *,       \
+                                                real *, real *, cudaStream_t);
 
 MOF_INST(float)
 MOF_INST(double)

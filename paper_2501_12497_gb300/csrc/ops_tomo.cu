@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(128) k_project(const real *__restrict__ u, con
             if (i0 + 1 >= 0 && i0 + 1 < nfast) acc = fma(w1, ldg(row + i0 + 1), acc);
         }
     }
-    b[(long long)a * nb + k] = acc * (real)P.wstep;
+    b[(long long)a * nb + k] = acc * (sizeof(real) == 8 ? (real)P.wstep_d : (real)P.wstep);
 }
 
 template <typename real>
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(BP_TX *BP_TY) k_backproject(const real *__rest
                     const double ff = floor(tt);
                     const int ib = (int)ff;
                     const double fr = tt - ff;
-                    const double rd = (double)P.rfoot, wf = (double)P.wfoot;
+                    const double rd = P.rfoot_d, wf = P.wfoot_d;
                     for (int m = 0; (double)m < rd; ++m) {
                         const double d0 = fr + m, d1 = 1.0 - fr + m;
                         const int k0 = ib - m, k1 = ib + 1 + m;

@@ -4,20 +4,29 @@
 // Given the Gram matrices G_A = (A V)^T (A V), G_L = (L V)^T (L V) and
 // g = (A V)^T b of the current basis (R_A^T R_A = G_A and R_L^T R_L = G_L for
 // the R factors of eq. (QR)), the block
-//   1. factors M = G_A + rho G_L = R^T R (Cholesky), rho = tr G_A / tr G_L;
-//   2. diagonalises C = R^-T G_A R^-1 = W diag(theta) W^T (parallel cyclic
-//      Jacobi), so that with X = R^-1 W:  X^T G_A X = diag(theta),
-//      X^T G_L X = diag(1 - theta)/rho  (the generalized singular values of
+//   1. factors M = G_A + rho G_L = R^T R (Cholesky, FP64), rho = tr G_A / tr G_L,
+//      and forms C = R^-T G_A R^-1 and h = R^-T g (FP64);
+//   2. diagonalises C: cyclic Jacobi sweeps in FP32 give approximate
+//      eigenvectors W; two Newton-Schulz steps make them orthonormal in FP64
+//      (W <- W (3I - W^T W)/2), and cyclic Jacobi sweeps in FP64 on W^T C W,
+//      which start near diagonal and converge quadratically, finish the
+//      decomposition to FP64 accuracy; with the eigenvalues theta_i in [0, 1]
+//      and eigenvectors W, X = R^-1 W satisfies X^T G_A X = diag(theta),
+//      X^T G_L X = diag(1 - theta)/rho (the generalized singular values of
 //      (R_A, R_L));
-//   3. evaluates, for any lam, the filter factors f_i = theta_i/(theta_i +
-//      (lam/rho)(1 - theta_i)), the projected residual
-//      ||R_A z - Q_A^T b||^2 = sum_i chat_i^2 (1 - f_i)^2 with
-//      chat_i^2 = (X^T g)_i^2 / theta_i, and trace(I - S) = sum_i (1 - f_i);
-//   4. picks lam: DP solves ||A V z - b||^2 = (eta delta)^2 on the bracket
-//      [1e-12, 1e12] rho by 256-way multisection in log10 lam; GCV minimises
-//      G = sum chat^2 (1-f)^2 / (sum (1-f))^2 on a 200-point log grid and
-//      refines around the grid minimum by repeated 256-point grids;
-//   5. returns z = X diag(1/(theta + (lam/rho)(1 - theta))) X^T g.
+//   3. with ghat = X^T g, chat_i^2 = ghat_i^2 / theta_i and the filter factors
+//      f_i = theta_i / (theta_i + mu (1 - theta_i)), mu = lam / rho, has
+//      ||R_A z - Q_A^T b||^2 = sum chat_i^2 (1 - f_i)^2 and
+//      trace(I - S) = sum (1 - f_i), with closed-form derivatives in lam;
+//   4. picks lam on the bracket 10^[log10 rho - 12, log10 rho + 12]:
+//      DP: the root of ||A V z - b||^2 = (eta delta)^2 (monotone in lam) by
+//      safeguarded Newton steps in log10 lam; GCV: the minimum of a 200-point
+//      log grid (ties to the smaller lam), refined inside its two grid
+//      neighbours by safeguarded Newton steps on dG/dlog10(lam) = 0, kept only
+//      if it improves on the grid value;
+//   5. returns z = X diag(1/(theta + mu (1 - theta))) ghat.
+// Each Jacobi round updates every 2x2 block (pair i rows, pair j columns) of
+// the matrix from its old values in one pass, so a round costs two barriers.
 #include "solver.cuh"
 
 #include <cfloat>
@@ -28,76 +37,149 @@ namespace {
 
 constexpr int ST = 256;
 constexpr int GRID_POINTS = 200;
+constexpr int NEWTON_MAX = 60;
 constexpr double BRACKET_DECADES = 12.0;
 constexpr double THETA_TINY = 1e-14;
-constexpr int JACOBI_MAX_SWEEPS = 40;
-constexpr int REFINE_ROUNDS = 7;
-constexpr int DP_ROUNDS = 8;
+constexpr int JACOBI32_MAX_SWEEPS = 12;
+constexpr int JACOBI64_MAX_SWEEPS = 10;
+constexpr double LN10 = 2.302585092994045684;
 
 struct Spec {
     int K;
-    double rho, bb, rho0sq;
+    double rho, rho0sq;
     const double *theta, *c2;
 };
 
-// sum_i chat_i^2 (1 - f_i)^2 and sum_i (1 - f_i) at lam = 10^t
-__device__ __forceinline__ void filters(const Spec &S, double t, double &num, double &den) {
-    const double mu = exp10(t) / S.rho;
-    num = 0.0;
-    den = 0.0;
-    for (int i = 0; i < S.K; ++i) {
-        const double th = S.theta[i];
-        const double d = th + mu * (1.0 - th);
-        const double omf = d > 0.0 ? mu * (1.0 - th) / d : 1.0;
-        num += S.c2[i] * omf * omf;
-        den += omf;
+// sums over i (lane-strided) of the lam-functions and their mu-derivatives:
+// s[0] = N = sum c2 g^2, s[1] = N', s[2] = N'', s[3] = D = sum g, s[4] = D', s[5] = D''
+// with g_i = mu a_i / d_i = 1 - f_i, a_i = 1 - theta_i, d_i = theta_i + mu a_i.
+__device__ __forceinline__ void lam_sums(const Spec &S, double mu, int i0, int step, double s[6]) {
+    for (int k = 0; k < 6; ++k) s[k] = 0.0;
+    for (int i = i0; i < S.K; i += step) {
+        const double th = S.theta[i], a = 1.0 - th, d = th + mu * a;
+        if (!(d > 0.0)) {
+            s[3] += 1.0;
+            continue;
+        }
+        const double inv = 1.0 / d;
+        const double g = mu * a * inv;
+        const double g1 = a * th * inv * inv;
+        const double g2 = -2.0 * a * g1 * inv;
+        const double c = S.c2[i];
+        s[0] += c * g * g;
+        s[1] += 2.0 * c * g * g1;
+        s[2] += 2.0 * c * (g1 * g1 + g * g2);
+        s[3] += g;
+        s[4] += g1;
+        s[5] += g2;
     }
 }
 
-__device__ __forceinline__ double gcv_at(const Spec &S, double t) {
-    double num, den;
-    filters(S, t, num, den);
-    const double g = num / (den * den);
+__device__ __forceinline__ void warp_lam_sums(const Spec &S, double t, double s[6]) {
+    const double mu = exp10(t) / S.rho;
+    lam_sums(S, mu, threadIdx.x & 31, 32, s);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) s[k] = warp_sum(s[k]);
+}
+
+__device__ __forceinline__ double gcv_of(const double s[6]) {
+    const double g = s[0] / (s[3] * s[3]);
     return g == g ? g : DBL_MAX;
 }
 
-__device__ __forceinline__ double dp_at(const Spec &S, double t, double target2) {
-    double num, den;
-    filters(S, t, num, den);
-    return num + S.rho0sq - target2;
+// first and second derivative of G = N / D^2 with respect to t = log10(lam)
+__device__ __forceinline__ void gcv_dt(const double s[6], double mu, double &d1, double &d2) {
+    const double N = s[0], N1 = s[1], N2 = s[2], D = s[3], D1 = s[4], D2 = s[5];
+    const double G1 = N1 / (D * D) - 2.0 * N * D1 / (D * D * D);
+    const double G2 =
+        N2 / (D * D) - 4.0 * N1 * D1 / (D * D * D) - 2.0 * N * D2 / (D * D * D) + 6.0 * N * D1 * D1 / (D * D * D * D);
+    d1 = G1 * mu * LN10;
+    d2 = (G2 * mu * mu + G1 * mu) * LN10 * LN10;
 }
 
-// block argmin of (v, i): smallest v, ties to the smallest i
-__device__ void block_argmin(double v, int i, double *sv, int *si, double &vbest, int &ibest) {
-    const int tid = threadIdx.x;
-    sv[tid] = v;
-    si[tid] = i;
+// round-robin tournament: player at position j in round r (positions 0..Kp-1)
+__device__ __forceinline__ int rr_player(int j, int r, int Kp) {
+    int v = j - 1 + r;
+    if (v >= Kp - 1) v -= Kp - 1;
+    return j == 0 ? 0 : 1 + v;
+}
+
+// Cyclic two-sided Jacobi sweeps on the symmetric Kp x Kp matrix A (padded
+// rows/columns beyond K are zero) with eigenvector accumulation W <- W J,
+// until a sweep applies no rotation (|a_pq| <= rel * sqrt(|a_pp a_qq|) or
+// |a_pq| <= rel_abs * max_i |a_ii|) or max_sweeps. All threads must call.
+template <typename T>
+__device__ void jacobi(T *A, int lda, T *W, int ldw, int K, int Kp, int max_sweeps, T rel, T rel_abs, T *rc, T *rs,
+                       double *red) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int half = Kp / 2;
+    double dm = 0.0;
+    for (int i = tid; i < K; i += ST) dm = fmax(dm, fabs((double)A[i * lda + i]));
+    for (int o = 16; o > 0; o >>= 1) dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+    if (lane == 0) red[wid] = dm;
     __syncthreads();
-    for (int s = ST / 2; s > 0; s >>= 1) {
-        if (tid < s) {
-            const double vo = sv[tid + s];
-            const int io = si[tid + s];
-            if (vo < sv[tid] || (vo == sv[tid] && io < si[tid])) {
-                sv[tid] = vo;
-                si[tid] = io;
+    dm = 0.0;
+    for (int w = 0; w < ST / 32; ++w) dm = fmax(dm, red[w]);
+    __syncthreads();
+    const T floor_abs = rel_abs * (T)dm;
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        int any_in_sweep = 0;
+        for (int round = 0; round < Kp - 1; ++round) {
+            int active = 0;
+            if (tid < half) {
+                const int p = rr_player(tid, round, Kp), q = rr_player(Kp - 1 - tid, round, Kp);
+                T c = 1, s = 0;
+                if (p < K && q < K) {
+                    const T apq = A[p * lda + q], app = A[p * lda + p], aqq = A[q * lda + q];
+                    if (fabs(apq) > rel * sqrt(fabs(app * aqq)) && fabs(apq) > floor_abs && fabs(apq) > (T)1e-300) {
+                        const T th = (aqq - app) / (2 * apq);
+                        const T t = (th >= 0 ? (T)1 : (T)-1) / (fabs(th) + sqrt(th * th + 1));
+                        c = 1 / sqrt(t * t + 1);
+                        s = t * c;
+                        active = 1;
+                    }
+                }
+                rc[tid] = c;
+                rs[tid] = s;
             }
+            if (!__syncthreads_or(active)) continue;
+            any_in_sweep = 1;
+            if (lane < half) {
+                const int pi = rr_player(lane, round, Kp), qi = rr_player(Kp - 1 - lane, round, Kp);
+                const T ci = rc[lane], si = rs[lane];
+                for (int j = wid; j < half; j += ST / 32) {
+                    const int pj = rr_player(j, round, Kp), qj = rr_player(Kp - 1 - j, round, Kp);
+                    const T cj = rc[j], sj = rs[j];
+                    const T a = A[pi * lda + pj], b = A[pi * lda + qj], c = A[qi * lda + pj], d = A[qi * lda + qj];
+                    const T a1 = ci * a - si * c, b1 = ci * b - si * d, c1 = si * a + ci * c, d1 = si * b + ci * d;
+                    A[pi * lda + pj] = cj * a1 - sj * b1;
+                    A[pi * lda + qj] = sj * a1 + cj * b1;
+                    A[qi * lda + pj] = cj * c1 - sj * d1;
+                    A[qi * lda + qj] = sj * c1 + cj * d1;
+                }
+                // W <- W J on the columns of pair `lane`
+                for (int r = wid; r < Kp; r += ST / 32) {
+                    const T wp = W[r * ldw + pi], wq = W[r * ldw + qi];
+                    W[r * ldw + pi] = ci * wp - si * wq;
+                    W[r * ldw + qi] = si * wp + ci * wq;
+                }
+            }
+            __syncthreads();
         }
-        __syncthreads();
+        if (!any_in_sweep) break;
     }
-    vbest = sv[0];
-    ibest = si[0];
-    __syncthreads();
 }
 
 }  // namespace
 
 __global__ void __launch_bounds__(ST) k_small_solve(SmallArgs a) {
     extern __shared__ double sm[];
-    __shared__ double s_rho, s_piv, s_rho0sq, s_lo, s_hi, s_t, s_va;
-    __shared__ int s_fail, s_flag, s_conv;
-    __shared__ double sv[ST];
-    __shared__ int si[ST];
-    const int b = blockIdx.x, tid = threadIdx.x;
+    __shared__ double s_rho, s_piv, s_rho0sq, s_t, s_vgrid;
+    __shared__ double s_red[ST / 32];
+    __shared__ int s_fail, s_flag, s_ig, s_idx[ST / 32];
+    __shared__ float rcf[33], rsf[33];
+    __shared__ double rcd[33], rsd[33];
+    const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int ld = a.ld;
     const int K = min(a.K[b], ld);
     double *z = a.z + (long long)b * ld;
@@ -109,40 +191,53 @@ __global__ void __launch_bounds__(ST) k_small_solve(SmallArgs a) {
         }
         return;
     }
-    const int Kp = K + (K & 1);  // padded to even for the round-robin Jacobi
-    const int lds = ld + 2;       // shared-memory leading dimension (>= Kp)
-    double *M = sm;               // Kp x Kp, later C
+    const int Kp = K + (K & 1);
+    const int lds = ld + 2;       // FP64 leading dimension (>= Kp)
+    const int ldf = ld + 3;       // FP32 leading dimension
+    double *M = sm;               // Cholesky factor R (upper), later X^T C X
     double *Ri = M + lds * lds;   // R^-1
-    double *T = Ri + lds * lds;   // G_A R^-1, later X
-    double *W = T + lds * lds;    // eigenvectors
-    double *theta = W + lds * lds;
-    double *gh = theta + (ld + 2);
-    double *c2 = gh + (ld + 2);
-    double *rc = c2 + (ld + 2);
-    double *rs = rc + (ld + 2);
-    int *perm = (int *)(rs + (ld + 2));
+    double *C = Ri + lds * lds;   // G_A, then C = R^-T G_A R^-1
+    double *T = C + lds * lds;    // scratch: G_A R^-1, Newton-Schulz products, C X
+    double *X = T + lds * lds;    // eigenvector estimate
+    double *E = X + lds * lds;    // G_L, then scratch
+    double *vec = E + lds * lds;  // vectors, lds each
+    double *theta = vec, *gh = vec + lds, *c2 = vec + 2 * lds, *h = vec + 3 * lds, *y = vec + 4 * lds;
+    float *Af = reinterpret_cast<float *>(T);  // FP32 Jacobi matrices alias T and E (free then)
+    float *Wf = reinterpret_cast<float *>(E);
     const double *GA = a.GA + (long long)b * ld * ld;
     const double *GL = a.GL + (long long)b * ld * ld;
     const double *g = a.g + (long long)b * ld;
 #define AT(P, i, j) P[(i) * lds + (j)]
+#define AF(P, i, j) P[(i) * ldf + (j)]
 
-    if (tid == 0) {
+    // ---------------------------------------------- 1. Cholesky, C, h (FP64)
+    for (int e = tid; e < K * K; e += ST) {
+        const int i = e / K, j = e - (e / K) * K;
+        AT(C, i, j) = GA[i * ld + j];
+        AT(E, i, j) = GL[i * ld + j];
+    }
+    for (int i = tid; i < K; i += ST) y[i] = g[i];
+    __syncthreads();
+    if (tid < 32) {
         double tA = 0.0, tL = 0.0;
-        for (int i = 0; i < K; ++i) {
-            tA += GA[i * ld + i];
-            tL += GL[i * ld + i];
+        for (int i = lane; i < K; i += 32) {
+            tA += AT(C, i, i);
+            tL += AT(E, i, i);
         }
-        s_rho = (tA > 0.0 && tL > 0.0) ? tA / tL : 1.0;
-        s_fail = 0;
+        tA = warp_sum(tA);
+        tL = warp_sum(tL);
+        if (lane == 0) {
+            s_rho = (tA > 0.0 && tL > 0.0) ? tA / tL : 1.0;
+            s_fail = 0;
+        }
     }
     __syncthreads();
     const double rho = s_rho;
     for (int e = tid; e < K * K; e += ST) {
-        const int i = e / K, j = e % K;
-        AT(M, i, j) = GA[i * ld + j] + rho * GL[i * ld + j];
+        const int i = e / K, j = e - (e / K) * K;
+        AT(M, i, j) = AT(C, i, j) + rho * AT(E, i, j);
     }
     __syncthreads();
-    // Cholesky, upper: M = R^T R, R stored in the upper triangle of M
     for (int j = 0; j < K; ++j) {
         if (tid == 0) {
             const double d = AT(M, j, j);
@@ -151,8 +246,8 @@ __global__ void __launch_bounds__(ST) k_small_solve(SmallArgs a) {
             AT(M, j, j) = s_piv;
         }
         __syncthreads();
-        const double piv = s_piv;
-        for (int k = j + 1 + tid; k < K; k += ST) AT(M, j, k) /= piv;
+        const double inv = 1.0 / s_piv;
+        for (int k = j + 1 + tid; k < K; k += ST) AT(M, j, k) *= inv;
         __syncthreads();
         const int rem = K - j - 1;
         for (int e = tid; e < rem * rem; e += ST) {
@@ -169,7 +264,6 @@ __global__ void __launch_bounds__(ST) k_small_solve(SmallArgs a) {
         }
         return;
     }
-    // R^-1 by back substitution, one column per thread
     for (int c = tid; c < K; c += ST) {
         for (int i = 0; i < K; ++i) AT(Ri, i, c) = 0.0;
         AT(Ri, c, c) = 1.0 / AT(M, c, c);
@@ -180,190 +274,227 @@ __global__ void __launch_bounds__(ST) k_small_solve(SmallArgs a) {
         }
     }
     __syncthreads();
-    // T = G_A R^-1
-    for (int e = tid; e < K * K; e += ST) {
-        const int i = e / K, j = e % K;
+    for (int e = tid; e < K * K; e += ST) {  // T = G_A R^-1
+        const int i = e / K, j = e - (e / K) * K;
         double s = 0.0;
-        for (int k = 0; k <= j; ++k) s += GA[i * ld + k] * AT(Ri, k, j);
+        for (int k = 0; k <= j; ++k) s += AT(C, i, k) * AT(Ri, k, j);
         AT(T, i, j) = s;
     }
-    __syncthreads();
-    // C = R^-T T (symmetric), into M; padded row/column zero
-    for (int e = tid; e < Kp * Kp; e += ST) {
-        const int i = e / Kp, j = e % Kp;
+    for (int i = tid; i < K; i += ST) {  // h = R^-T g
         double s = 0.0;
-        if (i < K && j < K)
-            for (int k = 0; k <= i; ++k) s += AT(Ri, k, i) * AT(T, k, j);
-        AT(M, i, j) = s;
-        AT(W, i, j) = (i == j) ? 1.0 : 0.0;
+        for (int k = 0; k <= i; ++k) s += AT(Ri, k, i) * y[k];
+        h[i] = s;
     }
     __syncthreads();
-    // symmetrise (rounding)
+    for (int e = tid; e < K * K; e += ST) {  // C = R^-T T (upper triangle, mirrored)
+        const int i = e / K, j = e - (e / K) * K;
+        if (i > j) continue;
+        double s = 0.0;
+        for (int k = 0; k <= i; ++k) s += AT(Ri, k, i) * AT(T, k, j);
+        AT(C, i, j) = s;
+        AT(C, j, i) = s;
+    }
+    __syncthreads();
+
+    // ---------------------------------------------- 2a. FP32 Jacobi on C
+    for (int e = tid; e < Kp * Kp; e += ST) {
+        const int i = e / Kp, j = e - (e / Kp) * Kp;
+        AF(Af, i, j) = (i < K && j < K) ? (float)AT(C, i, j) : 0.0f;
+        AF(Wf, i, j) = i == j ? 1.0f : 0.0f;
+    }
+    __syncthreads();
+    jacobi<float>(Af, ldf, Wf, ldf, K, Kp, JACOBI32_MAX_SWEEPS, 1e-6f, 1e-7f, rcf, rsf, s_red);
+
+    // ---------------------------------------------- 2b. FP64: orthonormalise, then Jacobi
     for (int e = tid; e < K * K; e += ST) {
-        const int i = e / K, j = e % K;
-        if (i < j) {
-            const double v = 0.5 * (AT(M, i, j) + AT(M, j, i));
-            AT(M, i, j) = v;
-            AT(M, j, i) = v;
-        }
+        const int i = e / K, j = e - (e / K) * K;
+        AT(X, i, j) = (double)AF(Wf, i, j);
     }
-    for (int i = tid; i < Kp; i += ST) perm[i] = i;
     __syncthreads();
-    // parallel cyclic Jacobi with round-robin pairing
-    const int half = Kp / 2;
-    for (int sweep = 0; sweep < JACOBI_MAX_SWEEPS; ++sweep) {
-        if (tid == 0) {
-            double off = 0.0, dia = 0.0;
-            for (int i = 0; i < K; ++i)
-                for (int j = 0; j < K; ++j) {
-                    const double v = AT(M, i, j);
-                    if (i == j) dia += v * v;
-                    else off += v * v;
-                }
-            s_conv = !(off > 1e-30 * dia);
+    for (int step = 0; step < 2; ++step) {  // Newton-Schulz: X <- X (3I - X^T X) / 2
+        for (int e = tid; e < K * K; e += ST) {
+            const int i = e / K, j = e - (e / K) * K;
+            if (i > j) continue;
+            double s = 0.0;
+            for (int k = 0; k < K; ++k) s += AT(X, k, i) * AT(X, k, j);
+            AT(E, i, j) = s;
+            AT(E, j, i) = s;
         }
         __syncthreads();
-        if (s_conv) break;
-        for (int round = 0; round < Kp - 1; ++round) {
-            if (tid < half) {
-                int p = perm[tid], q = perm[Kp - 1 - tid];
-                double c = 1.0, s = 0.0;
-                if (p < K && q < K) {
-                    const double apq = AT(M, p, q);
-                    if (apq != 0.0) {
-                        const double th = (AT(M, q, q) - AT(M, p, p)) / (2.0 * apq);
-                        const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-                        c = 1.0 / sqrt(t * t + 1.0);
-                        s = t * c;
-                    }
-                }
-                rc[tid] = c;
-                rs[tid] = s;
-            }
-            __syncthreads();
-            // columns: A <- A J, W <- W J
-            for (int e = tid; e < half * Kp; e += ST) {
-                const int pr = e / Kp, r = e % Kp;
-                const int p = perm[pr], q = perm[Kp - 1 - pr];
-                const double c = rc[pr], s = rs[pr];
-                if (s != 0.0) {
-                    const double ap = AT(M, r, p), aq = AT(M, r, q);
-                    AT(M, r, p) = c * ap - s * aq;
-                    AT(M, r, q) = s * ap + c * aq;
-                    const double wp = AT(W, r, p), wq = AT(W, r, q);
-                    AT(W, r, p) = c * wp - s * wq;
-                    AT(W, r, q) = s * wp + c * wq;
-                }
-            }
-            __syncthreads();
-            // rows: A <- J^T A
-            for (int e = tid; e < half * Kp; e += ST) {
-                const int pr = e / Kp, r = e % Kp;
-                const int p = perm[pr], q = perm[Kp - 1 - pr];
-                const double c = rc[pr], s = rs[pr];
-                if (s != 0.0) {
-                    const double ap = AT(M, p, r), aq = AT(M, q, r);
-                    AT(M, p, r) = c * ap - s * aq;
-                    AT(M, q, r) = s * ap + c * aq;
-                }
-            }
-            __syncthreads();
-            if (tid == 0) {  // rotate players 1..Kp-1
-                const int last = perm[Kp - 1];
-                for (int i = Kp - 1; i > 1; --i) perm[i] = perm[i - 1];
-                perm[1] = last;
-            }
-            __syncthreads();
+        for (int e = tid; e < K * K; e += ST) {
+            const int i = e / K, j = e - (e / K) * K;
+            double s = 0.0;
+            for (int k = 0; k < K; ++k) s += AT(X, i, k) * ((k == j ? 3.0 : 0.0) - AT(E, k, j));
+            AT(T, i, j) = 0.5 * s;
         }
+        __syncthreads();
+        for (int e = tid; e < K * K; e += ST) {
+            const int i = e / K, j = e - (e / K) * K;
+            AT(X, i, j) = AT(T, i, j);
+        }
+        __syncthreads();
     }
-    for (int i = tid; i < K; i += ST) theta[i] = fmin(fmax(AT(M, i, i), 0.0), 1.0);
-    __syncthreads();
-    // X = R^-1 W into T
-    for (int e = tid; e < K * K; e += ST) {
-        const int i = e / K, j = e % K;
+    for (int e = tid; e < K * K; e += ST) {  // T = C X
+        const int i = e / K, j = e - (e / K) * K;
         double s = 0.0;
-        for (int k = i; k < K; ++k) s += AT(Ri, i, k) * AT(W, k, j);
+        for (int k = 0; k < K; ++k) s += AT(C, i, k) * AT(X, k, j);
         AT(T, i, j) = s;
     }
     __syncthreads();
+    for (int e = tid; e < Kp * Kp; e += ST) {  // M = X^T C X (padded row/column zero, X padded by I)
+        const int i = e / Kp, j = e - (e / Kp) * Kp;
+        if (i > j) continue;
+        double s = 0.0;
+        if (j < K)
+            for (int k = 0; k < K; ++k) s += AT(X, k, i) * AT(T, k, j);
+        AT(M, i, j) = s;
+        AT(M, j, i) = s;
+        if (j == K) {
+            AT(X, i, j) = (i == j) ? 1.0 : 0.0;
+            AT(X, j, i) = (i == j) ? 1.0 : 0.0;
+        }
+    }
+    __syncthreads();
+    jacobi<double>(M, lds, X, lds, K, Kp, JACOBI64_MAX_SWEEPS, 1e-16, 1e-18, rcd, rsd, s_red);
     for (int i = tid; i < K; i += ST) {
         double s = 0.0;
-        for (int k = 0; k < K; ++k) s += AT(T, k, i) * g[k];
+        for (int k = 0; k < K; ++k) s += AT(X, k, i) * h[k];
+        theta[i] = fmin(fmax(AT(M, i, i), 0.0), 1.0);
         gh[i] = s;
         c2[i] = theta[i] > THETA_TINY ? s * s / theta[i] : 0.0;
     }
     __syncthreads();
-    if (tid == 0) {
+
+    // ---------------------------------------------- 3-4. lambda
+    if (tid < 32) {
         double kept = 0.0;
-        for (int i = 0; i < K; ++i) kept += c2[i];
-        s_rho0sq = a.bb[b] - kept;
-        s_lo = log10(rho) - BRACKET_DECADES;
-        s_hi = log10(rho) + BRACKET_DECADES;
-        s_flag = 0;
+        for (int i = lane; i < K; i += 32) kept += c2[i];
+        kept = warp_sum(kept);
+        if (lane == 0) {
+            s_rho0sq = a.bb[b] - kept;
+            s_flag = 0;
+        }
     }
     __syncthreads();
-    Spec S{K, rho, a.bb[b], s_rho0sq, theta, c2};
-    double t_sel;
-    if (a.rule == MOF_RULE_DP) {
-        double lo = s_lo, hi = s_hi;
-        if (tid == 0) {
-            if (dp_at(S, lo, a.target2) >= 0.0) s_flag = 1;
-            else if (dp_at(S, hi, a.target2) <= 0.0) s_flag = 2;
+    const Spec S{K, rho, s_rho0sq, theta, c2};
+    const double lo = log10(rho) - BRACKET_DECADES, hi = log10(rho) + BRACKET_DECADES;
+    if (a.rule == MOF_RULE_GCV) {
+        const double step = (hi - lo) / (GRID_POINTS - 1);
+        double vb = DBL_MAX;
+        int ib = tid;
+        if (tid < GRID_POINTS) {
+            double s[6];
+            lam_sums(S, exp10(lo + tid * step) / rho, 0, 1, s);
+            vb = gcv_of(s);
+        }
+        for (int o = 16; o > 0; o >>= 1) {  // argmin, ties to the smaller index
+            const double vo = __shfl_xor_sync(0xffffffffu, vb, o);
+            const int io = __shfl_xor_sync(0xffffffffu, ib, o);
+            if (vo < vb || (vo == vb && io < ib)) {
+                vb = vo;
+                ib = io;
+            }
+        }
+        if (lane == 0) {
+            s_red[wid] = vb;
+            s_idx[wid] = ib;
         }
         __syncthreads();
-        if (s_flag == 1) t_sel = lo;
-        else if (s_flag == 2) t_sel = hi;
-        else {
-            for (int r = 0; r < DP_ROUNDS; ++r) {
-                const double tj = lo + (tid + 1) * (hi - lo) / (ST + 1);
-                const double f = dp_at(S, tj, a.target2);
-                double vb;
-                int ib;
-                block_argmin(f > 0.0 ? 0.0 : 1.0, f > 0.0 ? tid : ST, sv, si, vb, ib);
-                const double nlo = ib == 0 ? lo : lo + ib * (hi - lo) / (ST + 1);
-                const double nhi = ib >= ST ? hi : lo + (ib + 1) * (hi - lo) / (ST + 1);
-                lo = nlo;
-                hi = nhi;
+        if (tid == 0) {
+            double bv = s_red[0];
+            int bi = s_idx[0];
+            for (int w = 1; w < ST / 32; ++w) {
+                if (s_red[w] < bv || (s_red[w] == bv && s_idx[w] < bi)) {
+                    bv = s_red[w];
+                    bi = s_idx[w];
+                }
             }
-            t_sel = 0.5 * (lo + hi);
+            s_vgrid = bv;
+            s_ig = bi;
         }
-    } else if (a.rule == MOF_RULE_GCV) {
-        const double lo = s_lo, hi = s_hi;
-        const double step = (hi - lo) / (GRID_POINTS - 1);
-        const double v = tid < GRID_POINTS ? gcv_at(S, lo + tid * step) : DBL_MAX;
-        double vgrid;
-        int ig;
-        block_argmin(v, tid, sv, si, vgrid, ig);
-        double a0 = lo + max(ig - 1, 0) * step, b0 = lo + min(ig + 1, GRID_POINTS - 1) * step;
-        double tbest = lo + ig * step, vbest = vgrid;
-        for (int r = 0; r < REFINE_ROUNDS; ++r) {
-            const double tj = a0 + tid * (b0 - a0) / (ST - 1);
-            double vr;
-            int ir;
-            block_argmin(gcv_at(S, tj), tid, sv, si, vr, ir);
-            const double ts = a0 + ir * (b0 - a0) / (ST - 1);
-            if (vr < vbest) {
-                vbest = vr;
-                tbest = ts;
+        __syncthreads();
+        if (wid == 0) {
+            // safeguarded Newton on dG/dt inside [t_{i-1}, t_{i+1}]
+            const int ig = s_ig;
+            double A0 = lo + max(ig - 1, 0) * step, B0 = lo + min(ig + 1, GRID_POINTS - 1) * step;
+            double t = lo + ig * step, s[6], d1, d2;
+            for (int it = 0; it < NEWTON_MAX; ++it) {
+                warp_lam_sums(S, t, s);
+                gcv_dt(s, exp10(t) / rho, d1, d2);
+                if (d1 > 0.0) B0 = t;
+                else if (d1 < 0.0) A0 = t;
+                else break;
+                double tn = (d2 > 0.0) ? t - d1 / d2 : 0.5 * (A0 + B0);
+                if (!(tn > A0 && tn < B0)) tn = 0.5 * (A0 + B0);
+                const double dt = fabs(tn - t);
+                t = tn;
+                if (dt <= 1e-14 * fmax(1.0, fabs(t)) || B0 - A0 <= 1e-14 * fmax(1.0, fabs(t))) break;
             }
-            const double na = a0 + max(ir - 1, 0) * (b0 - a0) / (ST - 1);
-            const double nb = a0 + min(ir + 1, ST - 1) * (b0 - a0) / (ST - 1);
-            a0 = na;
-            b0 = nb;
+            warp_lam_sums(S, t, s);
+            if (gcv_of(s) > s_vgrid) t = lo + ig * step;
+            if (lane == 0) s_t = t;
         }
-        t_sel = tbest;
+        __syncthreads();
+    } else if (a.rule == MOF_RULE_DP) {
+        if (wid == 0) {
+            double s[6], t;
+            warp_lam_sums(S, lo, s);
+            const double flo = s[0] + S.rho0sq - a.target2;
+            warp_lam_sums(S, hi, s);
+            const double fhi = s[0] + S.rho0sq - a.target2;
+            int flag = 0;
+            if (flo >= 0.0) {
+                flag = 1;
+                t = lo;
+            } else if (fhi <= 0.0) {
+                flag = 2;
+                t = hi;
+            } else {
+                // safeguarded Newton on F(t) = N(mu(t)) + rho0^2 - target^2 (increasing in t)
+                double A0 = lo, B0 = hi;
+                t = 0.5 * (lo + hi);
+                for (int it = 0; it < NEWTON_MAX; ++it) {
+                    warp_lam_sums(S, t, s);
+                    const double mu = exp10(t) / rho;
+                    const double F = s[0] + S.rho0sq - a.target2;
+                    const double F1 = s[1] * mu * LN10;
+                    if (F > 0.0) B0 = t;
+                    else A0 = t;
+                    double tn = F1 > 0.0 ? t - F / F1 : 0.5 * (A0 + B0);
+                    if (!(tn > A0 && tn < B0)) tn = 0.5 * (A0 + B0);
+                    const double dt = fabs(tn - t);
+                    t = tn;
+                    if (dt <= 1e-15 * fmax(1.0, fabs(t)) || B0 - A0 <= 1e-15 * fmax(1.0, fabs(t))) break;
+                }
+            }
+            if (lane == 0) {
+                s_t = t;
+                s_flag = flag;
+            }
+        }
+        __syncthreads();
     } else {
-        t_sel = log10(fmax(a.lam_fixed, 1e-300));
+        if (tid == 0) s_t = 0.0;
+        __syncthreads();
     }
-    const double lam = a.rule == MOF_RULE_FIXED ? a.lam_fixed : exp10(t_sel);
+    const double lam = a.rule == MOF_RULE_FIXED ? a.lam_fixed : exp10(s_t);
     const double mu = lam / rho;
-    // z = X diag(1/(theta + mu (1 - theta))) gh
+
+    // ---------------------------------------------- 5. z = R^-1 X y
+    for (int i = tid; i < K; i += ST) {
+        const double d = theta[i] + mu * (1.0 - theta[i]);
+        y[i] = d > 0.0 ? gh[i] / d : 0.0;
+    }
+    __syncthreads();
+    for (int i = tid; i < K; i += ST) {  // h = X y
+        double s = 0.0;
+        for (int k = 0; k < K; ++k) s += AT(X, i, k) * y[k];
+        h[i] = s;
+    }
+    __syncthreads();
     for (int i = tid; i < K; i += ST) {
         double s = 0.0;
-        for (int k = 0; k < K; ++k) {
-            const double d = theta[k] + mu * (1.0 - theta[k]);
-            if (d > 0.0) s += AT(T, i, k) * gh[k] / d;
-        }
+        for (int k = i; k < K; ++k) s += AT(Ri, i, k) * h[k];
         z[i] = s;
         if (!isfinite(s)) atomicOr(a.err, 2);
     }
@@ -372,12 +503,12 @@ __global__ void __launch_bounds__(ST) k_small_solve(SmallArgs a) {
         a.flag[b] = s_flag;
     }
 #undef AT
+#undef AF
 }
 
 mof_status launch_small_solve(const SmallArgs &a, cudaStream_t st) {
-    const int ld = a.ld;
-    const size_t lds = (size_t)ld + 2;
-    const size_t smem = sizeof(double) * (4 * lds * lds + 5 * lds) + sizeof(int) * lds;
+    const size_t lds = (size_t)a.ld + 2;
+    const size_t smem = sizeof(double) * (6 * lds * lds + 5 * lds);
     static size_t configured = 0;
     if (smem > 48 * 1024 && smem > configured) {
         MOF_CUDA(cudaFuncSetAttribute(k_small_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

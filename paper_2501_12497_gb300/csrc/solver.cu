@@ -104,7 +104,7 @@ struct WS {
     size_t bytes = 0;
     // ---- image step (one problem)
     real *V, *HV, *U, *u, *un, *r, *tm, *tn, *b, *q, *uT, *s, *sr, *vnew, *hvnew;
-    int *radius, *dest;
+    int *rad_s, *rad_sr, *rad_rev, *dest;
     double *GH, *GT, *gH, *z, *lam, *coef, *nrm2, *nrm2b, *scaleR, *alpha, *beta, *beta1, *alpha1, *bb, *gpart;
     int *K, *KU, *grow, *gkb, *flag, *err, *appended;
     double *report;  // [max_outer][8]
@@ -162,7 +162,7 @@ mof_status apply_scratch(mof_problem *p, ScratchKind kind, void **out) {
         size_t bytes = 0;
         switch (kind) {
             case SCR_IMAGE: bytes = es * p->n; break;
-            case SCR_RADIUS: bytes = 16; break;
+            case SCR_RADIUS: bytes = sizeof(int) * (2 * (size_t)(p->nt - 1) * tiles_count(p) + 16); break;
             case SCR_DEST: bytes = sizeof(int) * (p->nt - 1) * p->ns; break;
             case SCR_FLOWROWS: bytes = es * 2 * (p->nt - 1) * p->ns; break;
             default: return fail(MOF_EINVAL, "bad scratch kind");
@@ -221,7 +221,10 @@ static mof_status ensure_ws(mof_problem *p, const mof_solver_params &prm, int n_
         w->sr = a.take<real>(P * N2);
         w->vnew = a.take<real>(n);
         w->hvnew = a.take<real>(m);
-        w->radius = a.take<int>(4);
+        const long long tiles = (long long)tiles_count(p) * P;
+        w->rad_s = a.take<int>(tiles);
+        w->rad_sr = a.take<int>(tiles);
+        w->rad_rev = a.take<int>(tiles);
         w->dest = a.take<int>(P * ns);
         w->GH = a.take<double>((size_t)Kmax * Kmax);
         w->GT = a.take<double>((size_t)Kmax * Kmax);
@@ -769,7 +772,7 @@ static mof_status solve_impl(mof_problem *p, const mof_solver_params &prm, int n
         k_fill<real><<<fb(2 * P * ns), 256, 0, st>>>(w.s, 2 * P * ns, (real)0);
         k_fill<real><<<fb(2 * P * ns), 256, 0, st>>>(w.sr, 2 * P * ns, (real)0);
         k_copy<real><<<fb(m), 256, 0, st>>>(b_in, w.b, m);
-        MOF_TRY(launch_window_radius<real>(p, w.s, w.sr, w.radius, st));
+        MOF_TRY(launch_tile_radii<real>(p, w.s, w.sr, w.rad_s, w.rad_sr, st));
     }
     // ---- GKB on H from b / ||b|| (Sec. 4.1.1), H V_l = U_{l+1} B_l
     {
@@ -823,9 +826,8 @@ static mof_status solve_impl(mof_problem *p, const mof_solver_params &prm, int n
         if (of_now) {
             MOF_TRY(solve_of_impl<real>(p, prm, w, w.u, w.s, tm, st));
             Scope sc(tm, "reverse_flow", st);
-            MOF_TRY(launch_window_radius<real>(p, w.s, nullptr, w.radius, st));
-            MOF_TRY(launch_reverse_flow<real>(p, w.s, w.radius, w.dest, w.sr, st));
-            MOF_TRY(launch_window_radius<real>(p, w.s, w.sr, w.radius, st));
+            MOF_TRY(launch_reverse_flow<real>(p, w.s, w.rad_rev, w.dest, w.sr, st));
+            MOF_TRY(launch_tile_radii<real>(p, w.s, w.sr, w.rad_s, w.rad_sr, st));
         }
         {
             Scope sc(tm, "theta_gram", st);
@@ -850,7 +852,8 @@ static mof_status solve_impl(mof_problem *p, const mof_solver_params &prm, int n
             }
             {
                 Scope sc(tm, "reg_normal", st);
-                MOF_TRY(launch_reg_normal<real>(p, w.un, w.u, w.s, w.sr, w.radius, prm.eps, 1.0, w.lam, w.tn, w.q, w.r, st));
+                MOF_TRY(launch_reg_normal<real>(p, w.un, w.u, w.s, w.sr, w.rad_s, w.rad_sr, prm.eps, 1.0, w.lam, w.tn, w.q, w.r,
+                                                st));
             }
             {
                 Scope sc(tm, "reorth", st);
@@ -922,7 +925,7 @@ static mof_status solve_of_entry(mof_problem *p, const mof_solver_params &prm, c
     return MOF_OK;
 }
 
-static mof_status check_params(const mof_problem *p, const mof_solver_params *prm, int n_outer) {
+static mof_status check_params(const mof_problem *p, const mof_solver_params *prm, int n_outer, bool image_step = true) {
     if (!p || !prm) return fail(MOF_EINVAL, "null problem or parameters");
     if (n_outer < 1) return fail(MOF_EINVAL, "n_outer must be >= 1");
     if (prm->ell < 1 || prm->of_ell < 1 || prm->of_iters < 1 || prm->tau < 0 || prm->of_dr < 1 || prm->of_dr > 64)
@@ -931,6 +934,7 @@ static mof_status check_params(const mof_problem *p, const mof_solver_params *pr
         return fail(MOF_EUNSUPPORTED, "Krylov bases larger than 64 vectors are not supported (ell + n_outer = %d, of_ell + of_iters = %d)",
                     prm->ell + n_outer, prm->of_ell + prm->of_iters);
     if (!(prm->eps > 0) || !std::isfinite(prm->eps)) return fail(MOF_EINVAL, "eps must be finite and > 0");
+    if (!image_step) return MOF_OK;
     if (prm->image_rule == MOF_RULE_DP && !(prm->noise_norm >= 0))
         return fail(MOF_EINVAL, "the discrepancy principle needs noise_norm >= 0");
     if (prm->image_rule == MOF_RULE_FIXED && !(prm->lam_fixed > 0)) return fail(MOF_EINVAL, "fixed rule needs lam_fixed > 0");
@@ -945,7 +949,7 @@ using namespace mof;
 extern "C" {
 
 mof_status mof_solve_of(mof_problem *p, const mof_solver_params *prm, const void *u, void *s, void *stream) {
-    MOF_TRY(check_params(p, prm, 1));
+    MOF_TRY(check_params(p, prm, 1, false));
     if (!u || !s) return fail(MOF_EINVAL, "null array");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (p->precision == MOF_FP64) return solve_of_entry<double>(p, *prm, (const double *)u, (double *)s, st);
