@@ -1,0 +1,316 @@
+"""Benchmark of the MMGKS-OF hot path on GB300.
+
+One step = one complete MMGKS-OF solve (Alg. 1) of 30 outer iterations, each
+with a Solve-OF (Alg. 2, 20 GKS iterations on every one of the 31 frame
+pairs), on the 256x256x32 moving-ellipse workload (30 angles per frame
+rotating across frames, 363 bins, 1% noise): FP32 operators, FP64 Krylov
+bookkeeping and projected solves. The metric is outer solver iterations per
+second over the whole job (N GPUs x steps x 30 / time).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun with one process per GPU: every rank solves its own
+seeded problem of the same shape (independent replicas, no collective in the
+data path); rank 0 prints one JSON line with the max-over-ranks time.
+--impl reference times the FP64 CPU oracle on the host cores instead (the
+same workload and metric, a bounded sample per step, extrapolated).
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_OUTER = 30
+WORKLOAD = "ellipses256x256x32"
+CFG = dict(n=256, nt=32, na=30, nb=363)
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------ CPU oracle sample
+def oracle_outer_iteration_seconds(w):
+    """Time the oracle (as it stands) on a bounded sample of one outer iteration:
+    Solve-OF of one frame pair (the step the paper names as the bottleneck) on the
+    reconstruction's ground-truth frames, scaled by the number of pairs; the image
+    step's own cost is left out, so the figure flatters the oracle."""
+    import numpy as np
+    from oracle import ops, solver
+    prm = solver.Params(noise_norm=w.noise_norm)
+    ux, uy, ut = ops.of_fields(w.u_true[:2], prm.of_dr)
+    t0 = time.perf_counter()
+    solver.solve_of_pair(ux[0], uy[0], ut[0], prm)
+    dt = time.perf_counter() - t0
+    return dt * (w.nt - 1), dt
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2501_12497_gb300 import synth
+    w = synth.precision_form(0)
+    for _ in range(args.warmup):
+        oracle_outer_iteration_seconds(w)
+    tot = 0.0
+    sample = 0.0
+    for _ in range(args.steps):
+        est, dt = oracle_outer_iteration_seconds(w)
+        tot += est
+        sample += dt
+    value = args.steps / tot
+    line = {
+        "impl": "reference", "metric": "mmgks_of_outer_iterations_per_s", "value": value,
+        "unit": "outer_iters/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, **CFG, "n_outer": N_OUTER, "of_iters": 20, "ell": 10},
+        "cpu_baseline": {"value": value, "unit": "outer_iters/s", "cores": cpu_cores(), "kind": "oracle",
+                         "sample": "per step: Solve-OF of 1 of the 31 frame pairs (%.1f s measured), "
+                                   "x31 = one outer iteration; image step not counted" % (sample / args.steps)},
+        "e2e": {"value": value, "unit": "outer_iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------ clock sampling
+class Clocks:
+    def __init__(self, enabled):
+        self.proc = None
+        self.path = None
+        if not enabled:
+            return
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self, gpu_index):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9 or f[0] != str(gpu_index):
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ roofline models
+def reorth_bytes(nvec_list, N, pairs, es=4):
+    """Algorithmic bytes of the CGS2 reorthogonalisation (Solve-OF residual) over a solve:
+    two dot passes (read K basis vectors and x) and two update passes (read K vectors and x,
+    write x), K the basis size at each call, for every active pair."""
+    tot = 0
+    for K in nvec_list:
+        tot += pairs * es * N * (2 * (K + 1) + 2 * (K + 2))
+    return tot
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2501_12497_gb300 import api, synth
+    api.load()
+    dev = torch.device("cuda", local)
+    w = synth.precision_form(seed=rank)
+    p = api.mof_problem_create(w.nx, w.ny, w.nt, w.nb, w.na, w.angles, precision=api.MOF_FP32)
+    prm = api.mof_default_params(noise_norm=w.noise_norm)
+    stream = torch.cuda.current_stream(dev)
+    b = torch.tensor(w.b.astype(np.float32), device=dev)
+    u = torch.empty(p.n, dtype=torch.float32, device=dev)
+    s = torch.empty(p.nv, dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        api.mof_solve(p, prm, N_OUTER, b, u, s)
+    torch.cuda.synchronize()
+    api.mof_set_timing(p, 1)
+    clocks = Clocks(rank == 0)
+    launches0 = api.mof_kernel_launches()
+    per_step = []
+    class_ms = {}
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.fill_(1.0)  # evict L2 between timed steps
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rep = api.mof_solve(p, prm, N_OUTER, b, u, s)
+        e1.record(stream)
+        e1.synchronize()
+        per_step.append(e0.elapsed_time(e1))
+        for k, (ms, cnt) in api.mof_get_timing(p).items():
+            a = class_ms.setdefault(k, [0.0, 0])
+            a[0] += ms
+            a[1] += cnt
+    torch.cuda.synchronize()
+    launches = api.mof_kernel_launches() - launches0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop(local)
+    api.mof_set_timing(p, 0)
+    total_ms = sum(per_step)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = world * args.steps * N_OUTER / (total_ms / 1e3)
+
+    # end to end through the public host-buffer entry point: pinned host b in, u out
+    bh = torch.empty(p.m, dtype=torch.float32, pin_memory=True)
+    bh.copy_(torch.from_numpy(w.b.astype(np.float32)))
+    uh = torch.empty(p.n, dtype=torch.float32, pin_memory=True)
+    bhn, uhn = bh.numpy(), uh.numpy()
+    e2e_value = None
+    if args.e2e_steps > 0:
+        api.mof_solve_host(p, prm, N_OUTER, bhn, uhn)  # first call allocates the staging buffers
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            api.mof_solve_host(p, prm, N_OUTER, bhn, uhn)
+        e2e_s = time.perf_counter() - t0
+        te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e_value = world * args.e2e_steps * N_OUTER / float(te.item())
+
+    # quality of the result (RRE against the phantom) and the DP residual
+    rre = float(np.linalg.norm(u.cpu().numpy() - w.u_true.ravel()) / np.linalg.norm(w.u_true))
+
+    # roofline of the dominant HBM-bound unit: the CGS2 reorthogonalisation of the
+    # Solve-OF residuals (k_mdot + k_combine passes over the per-pair bases)
+    import json as _json
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = _json.load(open(pk))
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    N2 = 2 * CFG["n"] * CFG["n"]
+    pairs = CFG["nt"] - 1
+    # OF runs on outer iterations 1..29 (u^(0) = 0 gives u_t = 0 and no work at k = 0);
+    # GKS iteration it reorthogonalises against of_ell + it vectors (it = 0..18)
+    ks = [10 + it for it in range(19)] * (N_OUTER - 1)
+    bytes_total = reorth_bytes(ks, N2, pairs) * args.steps
+    ro_ms = class_ms.get("of_reorth", [float("nan"), 0])[0]
+    achieved = bytes_total / (ro_ms / 1e3) / 1e9 if ro_ms == ro_ms and ro_ms > 0 else None
+    dominant = max(class_ms.items(), key=lambda kv: kv[1][0])[0] if class_ms else None
+    roofline = {
+        "kernel": "of_reorth (CGS2 of the Solve-OF residuals: k_mdot, k_combine)",
+        "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+        "frac": (achieved / hbm_peak) if achieved else None, "traffic": None,
+        "peak_source": peak_src,
+        "share_of_step": ro_ms / total_ms if total_ms else None,
+        "largest_class": dominant,
+    }
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        est, dt = oracle_outer_iteration_seconds(w)
+        cpu = {"value": 1.0 / est, "unit": "outer_iters/s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": "Solve-OF of 1 of the 31 frame pairs (%.1f s), x31 = one outer iteration; "
+                         "image step not counted" % dt}
+    line = {
+        "metric": "mmgks_of_outer_iterations_per_s", "value": value, "unit": "outer_iters/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, **CFG, "n_outer": N_OUTER, "of_iters": 20, "of_ell": 10, "ell": 10,
+                   "precision": "FP32 operators, FP64 Krylov/projected solves", "parallelism": "replicas",
+                   "l2": "flushed between steps (512 MB write)", "rre": rre,
+                   "time_to_tolerance_s": total_ms / args.steps / 1e3},
+        "e2e": {"value": e2e_value, "unit": "outer_iters/s", "h2d_bytes_per_step": 4 * p.m,
+                "d2h_bytes_per_step": 4 * p.n + 64 * N_OUTER},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "roofline": roofline,
+        "kernel_classes_ms_per_step": {k: v[0] / args.steps for k, v in sorted(class_ms.items(), key=lambda kv: -kv[1][0])},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -203,6 +203,10 @@ mof_status mof_set_timing(mof_problem *p, int enable);
 mof_status mof_get_timing(const mof_problem *p, int cap, const char **names, double *ms,
                           long long *launches, int *count);
 
+/* Number of CUDA kernels this library has launched in the process so far
+ * (all threads, all problems); differences bracket a region of interest. */
+long long mof_kernel_launches(void);
+
 /* Text of the last error on the calling thread ("" if none). */
 const char *mof_last_error(void);
 

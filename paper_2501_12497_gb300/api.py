@@ -73,6 +73,7 @@ _SIGS = {
     "mof_get_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_void_p]),
     "mof_last_error": (ctypes.c_char_p, []),
+    "mof_kernel_launches": (ctypes.c_longlong, []),
 }
 
 
@@ -313,3 +314,8 @@ def mof_get_timing(p):
 def mof_last_error():
     load()
     return _lib.mof_last_error().decode()
+
+
+def mof_kernel_launches():
+    """Kernels launched by libmof in this process so far."""
+    return int(load().mof_kernel_launches())

@@ -7,11 +7,15 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
+#include <atomic>
 #include <new>
 
 namespace mof {
 
 static thread_local char g_err[512] = "";
+static std::atomic<long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void set_error(const char *fmt, ...) {
     va_list ap;
@@ -93,6 +97,8 @@ using namespace mof;
 extern "C" {
 
 const char *mof_last_error(void) { return g_err; }
+
+long long mof_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 void mof_default_params(mof_solver_params *p) {
     if (!p) return;

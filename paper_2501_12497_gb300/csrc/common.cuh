@@ -30,6 +30,9 @@ mof_status cuda_fail(cudaError_t e, const char *what, const char *file, int line
         if (s_ != MOF_OK) return s_;        \
     } while (0)
 
+// Kernel-launch counter (every launch site calls count_launch()).
+void count_launch();
+
 // Launch-error check after a kernel launch.
 #define MOF_LAUNCH_CHECK() MOF_CUDA(cudaGetLastError())
 

@@ -238,17 +238,17 @@ void Krylov<real>::multidot(const BasisRef<real> &B, int nv, const DotVecs<real>
                             cudaStream_t st) const {
     const int nc = (int)krylov_chunks(B.N);
     const dim3 grid(nc, B.B);
-    if (nv == 1) k_mdot<real, 1><<<grid, KT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, xs, partial, nc);
-    else if (nv == 2) k_mdot<real, 2><<<grid, KT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, xs, partial, nc);
-    else k_mdot<real, 3><<<grid, KT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, xs, partial, nc);
-    k_sum_chunks<<<B.B, 128, 0, st>>>(partial, nc, nv, B.Kmax, B.K, B.act, outs);
+    if (nv == 1) ::mof::count_launch(), k_mdot<real, 1><<<grid, KT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, xs, partial, nc);
+    else if (nv == 2) ::mof::count_launch(), k_mdot<real, 2><<<grid, KT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, xs, partial, nc);
+    else ::mof::count_launch(), k_mdot<real, 3><<<grid, KT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, xs, partial, nc);
+    ::mof::count_launch(), k_sum_chunks<<<B.B, 128, 0, st>>>(partial, nc, nv, B.Kmax, B.K, B.act, outs);
 }
 
 template <typename real>
 void Krylov<real>::combine(const BasisRef<real> &B, const double *c, long long cstride, real *out, long long ostride,
                            cudaStream_t st) const {
     const int nc = (int)krylov_chunks(B.N);
-    k_combine<real, 0><<<dim3(nc, B.B), KT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, c, cstride, nullptr, 0, out, ostride, nullptr,
+    ::mof::count_launch(), k_combine<real, 0><<<dim3(nc, B.B), KT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, c, cstride, nullptr, 0, out, ostride, nullptr,
                                                      nc);
 }
 
@@ -256,25 +256,25 @@ template <typename real>
 void Krylov<real>::combine_minus(const BasisRef<real> &B, const double *c, long long cstride, const real *x, long long xstride,
                                  real *out, long long ostride, double *nrm2_out, cudaStream_t st) const {
     const int nc = (int)krylov_chunks(B.N);
-    k_combine<real, 2><<<dim3(nc, B.B), KT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, c, cstride, x, xstride, out, ostride,
+    ::mof::count_launch(), k_combine<real, 2><<<dim3(nc, B.B), KT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, c, cstride, x, xstride, out, ostride,
                                                      nrm2_out ? partial : nullptr, nc);
-    if (nrm2_out) k_sum_scalar_chunks<<<(B.B + 63) / 64, 64, 0, st>>>(partial, nc, nrm2_out, B.B);
+    if (nrm2_out) ::mof::count_launch(), k_sum_scalar_chunks<<<(B.B + 63) / 64, 64, 0, st>>>(partial, nc, nrm2_out, B.B);
 }
 
 template <typename real>
 void Krylov<real>::subtract(const BasisRef<real> &B, const double *c, long long cstride, const real *x, long long xstride,
                             real *out, long long ostride, double *nrm2_out, cudaStream_t st) const {
     const int nc = (int)krylov_chunks(B.N);
-    k_combine<real, 1><<<dim3(nc, B.B), KT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, c, cstride, x, xstride, out, ostride,
+    ::mof::count_launch(), k_combine<real, 1><<<dim3(nc, B.B), KT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, c, cstride, x, xstride, out, ostride,
                                                      nrm2_out ? partial : nullptr, nc);
-    if (nrm2_out) k_sum_scalar_chunks<<<(B.B + 63) / 64, 64, 0, st>>>(partial, nc, nrm2_out, B.B);
+    if (nrm2_out) ::mof::count_launch(), k_sum_scalar_chunks<<<(B.B + 63) / 64, 64, 0, st>>>(partial, nc, nrm2_out, B.B);
 }
 
 template <typename real>
 void Krylov<real>::norm2(const real *x, long long N, long long xstride, int nb, double *out, cudaStream_t st) const {
     const int nc = (int)krylov_chunks(N);
-    k_norm2<real><<<dim3(nc, nb), KT, 0, st>>>(x, N, xstride, partial, nc);
-    k_sum_scalar_chunks<<<(nb + 63) / 64, 64, 0, st>>>(partial, nc, out, nb);
+    ::mof::count_launch(), k_norm2<real><<<dim3(nc, nb), KT, 0, st>>>(x, N, xstride, partial, nc);
+    ::mof::count_launch(), k_sum_scalar_chunks<<<(nb + 63) / 64, 64, 0, st>>>(partial, nc, out, nb);
 }
 
 template <typename real>
@@ -291,8 +291,8 @@ template <typename real>
 void Krylov<real>::append(const BasisRef<real> &B, int *Kmut, const real *x, long long xstride, const double *nrm2,
                           const double *scale, double tol, int *grow, int *appended, real *stage, cudaStream_t st) const {
     const int blocks = (int)std::min<long long>(1024, (B.N + KT - 1) / KT);
-    k_append<real><<<dim3(blocks, B.B), KT, 0, st>>>(B.V, B.N, B.Kmax, B.K, x, xstride, nrm2, scale, tol, grow, stage);
-    k_commit<<<(B.B + 63) / 64, 64, 0, st>>>(Kmut, B.Kmax, nrm2, scale, tol, grow, B.B, appended);
+    ::mof::count_launch(), k_append<real><<<dim3(blocks, B.B), KT, 0, st>>>(B.V, B.N, B.Kmax, B.K, x, xstride, nrm2, scale, tol, grow, stage);
+    ::mof::count_launch(), k_commit<<<(B.B + 63) / 64, 64, 0, st>>>(Kmut, B.Kmax, nrm2, scale, tol, grow, B.B, appended);
 }
 
 template struct Krylov<float>;

@@ -117,13 +117,13 @@ __global__ void k_gradT(const real *__restrict__ g, real *__restrict__ u, int nx
 
 template <typename real>
 mof_status launch_grad(const mof_problem *p, int nf, const real *u, real *g, cudaStream_t st) {
-    k_grad<real><<<grid2d(p->nx, p->ny, nf), dim3(TX, TY), 0, st>>>(u, g, p->nx, p->ny);
+    ::mof::count_launch(), k_grad<real><<<grid2d(p->nx, p->ny, nf), dim3(TX, TY), 0, st>>>(u, g, p->nx, p->ny);
     MOF_LAUNCH_CHECK();
     return MOF_OK;
 }
 template <typename real>
 mof_status launch_gradT(const mof_problem *p, int nf, const real *g, real *u, cudaStream_t st) {
-    k_gradT<real><<<grid2d(p->nx, p->ny, nf), dim3(TX, TY), 0, st>>>(g, u, p->nx, p->ny);
+    ::mof::count_launch(), k_gradT<real><<<grid2d(p->nx, p->ny, nf), dim3(TX, TY), 0, st>>>(g, u, p->nx, p->ny);
     MOF_LAUNCH_CHECK();
     return MOF_OK;
 }
@@ -144,7 +144,7 @@ __global__ void k_flow(const real *__restrict__ u, const real *__restrict__ s, c
 template <typename real>
 mof_status launch_flow(const mof_problem *p, const real *u, const real *s, const real *sr, real *r, cudaStream_t st) {
     const int np = p->nt - 1;
-    k_flow<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(u, s, sr, r, p->nx, p->ny, np);
+    ::mof::count_launch(), k_flow<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(u, s, sr, r, p->nx, p->ny, np);
     MOF_LAUNCH_CHECK();
     return MOF_OK;
 }
@@ -191,14 +191,14 @@ int tiles_count(const mof_problem *p) { return tiles_x(p) * ((p->ny + TY - 1) / 
 template <typename real>
 mof_status launch_tile_radii(const mof_problem *p, const real *s, const real *sr, int *rad_s, int *rad_sr, cudaStream_t st) {
     const int np = p->nt - 1, tiles = tiles_count(p);
-    k_zero_ints<<<8, 256, 0, st>>>(rad_s, (long long)np * tiles);
+    ::mof::count_launch(), k_zero_ints<<<8, 256, 0, st>>>(rad_s, (long long)np * tiles);
     MOF_LAUNCH_CHECK();
-    k_tile_radius<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(s, p->nx, p->ny, rad_s, tiles_x(p), tiles);
+    ::mof::count_launch(), k_tile_radius<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(s, p->nx, p->ny, rad_s, tiles_x(p), tiles);
     MOF_LAUNCH_CHECK();
     if (sr) {
-        k_zero_ints<<<8, 256, 0, st>>>(rad_sr, (long long)np * tiles);
+        ::mof::count_launch(), k_zero_ints<<<8, 256, 0, st>>>(rad_sr, (long long)np * tiles);
         MOF_LAUNCH_CHECK();
-        k_tile_radius<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(sr, p->nx, p->ny, rad_sr, tiles_x(p), tiles);
+        ::mof::count_launch(), k_tile_radius<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(sr, p->nx, p->ny, rad_sr, tiles_x(p), tiles);
         MOF_LAUNCH_CHECK();
     }
     return MOF_OK;
@@ -240,7 +240,7 @@ __global__ void k_flowT(const real *__restrict__ r, const real *__restrict__ s, 
 template <typename real>
 mof_status launch_flowT(const mof_problem *p, const real *r, const real *s, const real *sr, const int *rad_s,
                         const int *rad_sr, real *u, cudaStream_t st) {
-    k_flowT<real><<<grid2d(p->nx, p->ny, p->nt), dim3(TX, TY), 0, st>>>(r, s, sr, rad_s, rad_sr, u, p->nx, p->ny, p->nt - 1,
+    ::mof::count_launch(), k_flowT<real><<<grid2d(p->nx, p->ny, p->nt), dim3(TX, TY), 0, st>>>(r, s, sr, rad_s, rad_sr, u, p->nx, p->ny, p->nt - 1,
                                                                       tiles_count(p));
     MOF_LAUNCH_CHECK();
     return MOF_OK;
@@ -317,11 +317,11 @@ __global__ void k_rev_gather(const real *__restrict__ s, const int *__restrict__
 template <typename real>
 mof_status launch_reverse_flow(const mof_problem *p, const real *s, int *rad, int *dest, real *sr, cudaStream_t st) {
     const int np = p->nt - 1, tiles = tiles_count(p);
-    k_zero_ints<<<8, 256, 0, st>>>(rad, (long long)np * tiles);
+    ::mof::count_launch(), k_zero_ints<<<8, 256, 0, st>>>(rad, (long long)np * tiles);
     MOF_LAUNCH_CHECK();
-    k_rev_dest<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(s, dest, rad, p->nx, p->ny, tiles_x(p), tiles);
+    ::mof::count_launch(), k_rev_dest<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(s, dest, rad, p->nx, p->ny, tiles_x(p), tiles);
     MOF_LAUNCH_CHECK();
-    k_rev_gather<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(s, dest, rad, sr, p->nx, p->ny, tiles);
+    ::mof::count_launch(), k_rev_gather<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(s, dest, rad, sr, p->nx, p->ny, tiles);
     MOF_LAUNCH_CHECK();
     return MOF_OK;
 }
@@ -363,7 +363,7 @@ __global__ void k_of_fields(const real *__restrict__ u, int dr, real *__restrict
 
 template <typename real>
 mof_status launch_of_fields(const mof_problem *p, const real *u, int dr, real *ux, real *uy, real *ut, cudaStream_t st) {
-    k_of_fields<real><<<grid2d(p->nx, p->ny, p->nt - 1), dim3(TX, TY), 0, st>>>(u, dr, ux, uy, ut, p->nx, p->ny);
+    ::mof::count_launch(), k_of_fields<real><<<grid2d(p->nx, p->ny, p->nt - 1), dim3(TX, TY), 0, st>>>(u, dr, ux, uy, ut, p->nx, p->ny);
     MOF_LAUNCH_CHECK();
     return MOF_OK;
 }
@@ -394,14 +394,14 @@ template <typename real>
 mof_status launch_flow_lin(const mof_problem *p, const real *ux, const real *uy, const real *ut, const real *s, real *r,
                            cudaStream_t st) {
     const long long total = (long long)(p->nt - 1) * p->ns;
-    k_flow_lin<real><<<flat_blocks(total), 256, 0, st>>>(ux, uy, ut, s, r, p->ns, total);
+    ::mof::count_launch(), k_flow_lin<real><<<flat_blocks(total), 256, 0, st>>>(ux, uy, ut, s, r, p->ns, total);
     MOF_LAUNCH_CHECK();
     return MOF_OK;
 }
 template <typename real>
 mof_status launch_flow_linT(const mof_problem *p, const real *ux, const real *uy, const real *r, real *gs, cudaStream_t st) {
     const long long total = (long long)(p->nt - 1) * p->ns;
-    k_flow_linT<real><<<flat_blocks(total), 256, 0, st>>>(ux, uy, r, gs, p->ns, total);
+    ::mof::count_launch(), k_flow_linT<real><<<flat_blocks(total), 256, 0, st>>>(ux, uy, r, gs, p->ns, total);
     MOF_LAUNCH_CHECK();
     return MOF_OK;
 }
@@ -463,10 +463,10 @@ mof_status launch_reg_normal(const mof_problem *p, const real *x, const real *uk
     const int np = p->nt - 1;
     const real eps2 = (real)(eps * eps);
     if (np > 0) {
-        k_regn_flow_rows<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(x, uk, s, sr, eps2, q, p->nx, p->ny, np);
+        ::mof::count_launch(), k_regn_flow_rows<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(x, uk, s, sr, eps2, q, p->nx, p->ny, np);
         MOF_LAUNCH_CHECK();
     }
-    k_regn_apply<real><<<grid2d(p->nx, p->ny, p->nt), dim3(TX, TY), 0, st>>>(x, uk, s, sr, q, rad_s, rad_sr, tiles_count(p),
+    ::mof::count_launch(), k_regn_apply<real><<<grid2d(p->nx, p->ny, p->nt), dim3(TX, TY), 0, st>>>(x, uk, s, sr, q, rad_s, rad_sr, tiles_count(p),
                                                                             eps2, scale, lam_dev, y_add, y, p->nx, p->ny, np);
     MOF_LAUNCH_CHECK();
     return MOF_OK;

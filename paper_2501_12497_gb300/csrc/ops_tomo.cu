@@ -89,10 +89,10 @@ __global__ void __launch_bounds__(128) k_project(const real *__restrict__ u, con
 template <typename real>
 mof_status launch_project(const mof_problem *p, const real *u, real *uT, real *b, cudaStream_t st) {
     dim3 tb(32, 8), tg((p->nx + 31) / 32, (p->ny + 31) / 32, p->nt);
-    k_transpose<real><<<tg, tb, 0, st>>>(u, uT, p->nx, p->ny);
+    ::mof::count_launch(), k_transpose<real><<<tg, tb, 0, st>>>(u, uT, p->nx, p->ny);
     MOF_LAUNCH_CHECK();
     dim3 grid((p->nb + 127) / 128, p->A);
-    k_project<real><<<grid, 128, 0, st>>>(u, uT, b, p->d_ang, p->nx, p->ny, p->nb);
+    ::mof::count_launch(), k_project<real><<<grid, 128, 0, st>>>(u, uT, b, p->d_ang, p->nx, p->ny, p->nb);
     MOF_LAUNCH_CHECK();
     return MOF_OK;
 }
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(BP_TX *BP_TY) k_backproject(const real *__rest
 template <typename real>
 mof_status launch_backproject(const mof_problem *p, const real *b, real *u, cudaStream_t st) {
     dim3 grid((p->nx + BP_TX - 1) / BP_TX, (p->ny + BP_TY - 1) / BP_TY, p->nt);
-    k_backproject<real><<<grid, dim3(BP_TX, BP_TY), 0, st>>>(b, u, p->d_ang, p->d_aoff, p->nx, p->ny, p->nb);
+    ::mof::count_launch(), k_backproject<real><<<grid, dim3(BP_TX, BP_TY), 0, st>>>(b, u, p->d_ang, p->d_aoff, p->nx, p->ny, p->nb);
     MOF_LAUNCH_CHECK();
     return MOF_OK;
 }

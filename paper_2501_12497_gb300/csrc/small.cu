@@ -514,7 +514,7 @@ mof_status launch_small_solve(const SmallArgs &a, cudaStream_t st) {
         MOF_CUDA(cudaFuncSetAttribute(k_small_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         configured = smem;
     }
-    k_small_solve<<<a.B, ST, smem, st>>>(a);
+    ::mof::count_launch(), k_small_solve<<<a.B, ST, smem, st>>>(a);
     MOF_LAUNCH_CHECK();
     return MOF_OK;
 }

@@ -648,27 +648,27 @@ static mof_status solve_of_impl(mof_problem *p, const mof_solver_params &prm, WS
     {
         Scope sc(tm, "of_fields", st);
         MOF_TRY(launch_of_fields<real>(p, u, prm.of_dr, w.ux, w.uy, w.ut, st));
-        k_of_rhs<real><<<dim3(fb(ns), P), 256, 0, st>>>(w.ux, w.uy, w.ut, w.bof, w.AtB, ns);
+        ::mof::count_launch(), k_of_rhs<real><<<dim3(fb(ns), P), 256, 0, st>>>(w.ux, w.uy, w.ut, w.bof, w.AtB, ns);
     }
     BasisRef<real> BV{w.Vof, N2, Kof, P, w.Kv_of, w.gkb_of};
     BasisRef<real> BU{w.Uof, ns, ldU, P, w.Ku_of, w.gkb_of};
     {
         Scope sc(tm, "of_gkb", st);
         kr.norm2(w.bof, ns, ns, P, w.bb_of, st);
-        k_of_activate<<<(P + 63) / 64, 64, 0, st>>>(w.bb_of, w.act_of, w.gkb_of, w.grow_of, w.Kv_of, w.Ku_of, w.beta1_of, P);
+        ::mof::count_launch(), k_of_activate<<<(P + 63) / 64, 64, 0, st>>>(w.bb_of, w.act_of, w.gkb_of, w.grow_of, w.Kv_of, w.Ku_of, w.beta1_of, P);
         kr.norm2(w.AtB, N2, N2, P, w.nrm_of, st);
-        k_sqrt_into<<<(P + 63) / 64, 64, 0, st>>>(w.nrm_of, w.scale_of, P);
+        ::mof::count_launch(), k_sqrt_into<<<(P + 63) / 64, 64, 0, st>>>(w.nrm_of, w.scale_of, P);
         // u_1 = b / ||b||
         kr.append(BU, w.Ku_of, w.bof, ns, w.bb_of, nullptr, 0.0, w.gkb_of, nullptr, nullptr, st);
         for (int j = 0; j < w.of_ell && j < prm.of_ell; ++j) {
-            k_of_upsT<real><<<dim3(fb(ns), P), 256, 0, st>>>(w.ux, w.uy, w.Uof, ldU, j, w.Vof, Kof, w.beta_of, w.wv, ns, w.gkb_of);
+            ::mof::count_launch(), k_of_upsT<real><<<dim3(fb(ns), P), 256, 0, st>>>(w.ux, w.uy, w.Uof, ldU, j, w.Vof, Kof, w.beta_of, w.wv, ns, w.gkb_of);
             kr.reorth(BV, w.wv, N2, w.coef_of, w.nrm_of, st);
-            if (j == 0) k_sqrt_into_if<<<(P + 63) / 64, 64, 0, st>>>(w.nrm_of, w.alpha1_of, P, w.gkb_of);
-            k_sqrt_into_if<<<(P + 63) / 64, 64, 0, st>>>(w.nrm_of, w.alpha_of, P, w.gkb_of);
+            if (j == 0) ::mof::count_launch(), k_sqrt_into_if<<<(P + 63) / 64, 64, 0, st>>>(w.nrm_of, w.alpha1_of, P, w.gkb_of);
+            ::mof::count_launch(), k_sqrt_into_if<<<(P + 63) / 64, 64, 0, st>>>(w.nrm_of, w.alpha_of, P, w.gkb_of);
             kr.append(BV, w.Kv_of, w.wv, N2, w.nrm_of, j == 0 ? nullptr : w.alpha1_of, tol, w.gkb_of, nullptr, nullptr, st);
-            k_of_ups<real><<<dim3(fb(ns), P), 256, 0, st>>>(w.ux, w.uy, w.Vof, Kof, j, w.Uof, ldU, w.alpha_of, w.wu, ns, w.gkb_of);
+            ::mof::count_launch(), k_of_ups<real><<<dim3(fb(ns), P), 256, 0, st>>>(w.ux, w.uy, w.Vof, Kof, j, w.Uof, ldU, w.alpha_of, w.wu, ns, w.gkb_of);
             kr.reorth(BU, w.wu, ns, w.coefU_of, w.nrm_of, st);
-            k_sqrt_into_if<<<(P + 63) / 64, 64, 0, st>>>(w.nrm_of, w.beta_of, P, w.gkb_of);
+            ::mof::count_launch(), k_sqrt_into_if<<<(P + 63) / 64, 64, 0, st>>>(w.nrm_of, w.beta_of, P, w.gkb_of);
             kr.append(BU, w.Ku_of, w.wu, ns, w.nrm_of, w.beta1_of, tol, w.gkb_of, nullptr, nullptr, st);
         }
     }
@@ -676,7 +676,7 @@ static mof_status solve_of_impl(mof_problem *p, const mof_solver_params &prm, WS
     {
         Scope sc(tm, "of_gram", st);
         for (int j = 0; j < prm.of_ell; ++j) {
-            k_of_normal_parts<real><<<g2, blk2, 0, st>>>(w.ux, w.uy, w.Vof + (long long)j * N2, (long long)Kof * N2, w.y1, w.y2,
+            ::mof::count_launch(), k_of_normal_parts<real><<<g2, blk2, 0, st>>>(w.ux, w.uy, w.Vof + (long long)j * N2, (long long)Kof * N2, w.y1, w.y2,
                                                          p->nx, p->ny, w.act_of);
             DotVecs<real> xs{{w.y1, w.y2, w.AtB}, {N2, N2, N2}};
             DotOuts o{};
@@ -713,7 +713,7 @@ static mof_status solve_of_impl(mof_problem *p, const mof_solver_params &prm, WS
         if (it == prm.of_iters - 1) break;
         {
             Scope sc(tm, "of_resid", st);
-            k_of_resid<real><<<g2, blk2, 0, st>>>(w.ux, w.uy, w.AtB, s_out, w.gam, w.wv, p->nx, p->ny, w.act_of);
+            ::mof::count_launch(), k_of_resid<real><<<g2, blk2, 0, st>>>(w.ux, w.uy, w.AtB, s_out, w.gam, w.wv, p->nx, p->ny, w.act_of);
         }
         {
             Scope sc(tm, "of_reorth", st);
@@ -723,15 +723,15 @@ static mof_status solve_of_impl(mof_problem *p, const mof_solver_params &prm, WS
         {
             Scope sc(tm, "of_gram", st);
             BasisRef<real> BN{w.Vof, N2, Kof, P, w.Kv_of, w.app_of};
-            k_of_normal_parts<real><<<g2, blk2, 0, st>>>(w.ux, w.uy, w.vnew_of, N2, w.y1, w.y2, p->nx, p->ny, w.app_of);
+            ::mof::count_launch(), k_of_normal_parts<real><<<g2, blk2, 0, st>>>(w.ux, w.uy, w.vnew_of, N2, w.y1, w.y2, p->nx, p->ny, w.app_of);
             DotVecs<real> xs{{w.y1, w.y2, w.AtB}, {N2, N2, N2}};
             DotOuts o{};
             o.o[0] = DotOut{w.GA, (long long)Kof * Kof, Kof, 1, 1, 1.0};
             o.o[1] = DotOut{w.GL, (long long)Kof * Kof, Kof, 1, 1, 1.0};
             o.o[2] = DotOut{w.gof, Kof, 1, 0, 0, 1.0};
             kr.multidot(BN, 3, xs, o, st);
-            k_sym_last<<<P, 64, 0, st>>>(w.GA, Kof, w.Kv_of, w.app_of);
-            k_sym_last<<<P, 64, 0, st>>>(w.GL, Kof, w.Kv_of, w.app_of);
+            ::mof::count_launch(), k_sym_last<<<P, 64, 0, st>>>(w.GA, Kof, w.Kv_of, w.app_of);
+            ::mof::count_launch(), k_sym_last<<<P, 64, 0, st>>>(w.GL, Kof, w.Kv_of, w.app_of);
         }
     }
     MOF_LAUNCH_CHECK();
@@ -762,40 +762,40 @@ static mof_status solve_impl(mof_problem *p, const mof_solver_params &prm, int n
     BasisRef<real> BU{w.U, m, w.ell + 1, 1, w.KU, w.gkb};
     {
         Scope sc(tm, "init", st);
-        k_fill_int<<<1, 32, 0, st>>>(w.K, 1, 0);
-        k_fill_int<<<1, 32, 0, st>>>(w.KU, 1, 0);
-        k_fill_int<<<1, 32, 0, st>>>(w.grow, 1, 1);
-        k_fill_int<<<1, 32, 0, st>>>(w.gkb, 1, 1);
-        k_fill_int<<<1, 32, 0, st>>>(w.err, 1, 0);
-        k_fill_int<<<1, 32, 0, st>>>(w.flag, 1, 0);
-        k_fill<real><<<fb(n), 256, 0, st>>>(w.u, n, (real)0);
-        k_fill<real><<<fb(2 * P * ns), 256, 0, st>>>(w.s, 2 * P * ns, (real)0);
-        k_fill<real><<<fb(2 * P * ns), 256, 0, st>>>(w.sr, 2 * P * ns, (real)0);
-        k_copy<real><<<fb(m), 256, 0, st>>>(b_in, w.b, m);
+        ::mof::count_launch(), k_fill_int<<<1, 32, 0, st>>>(w.K, 1, 0);
+        ::mof::count_launch(), k_fill_int<<<1, 32, 0, st>>>(w.KU, 1, 0);
+        ::mof::count_launch(), k_fill_int<<<1, 32, 0, st>>>(w.grow, 1, 1);
+        ::mof::count_launch(), k_fill_int<<<1, 32, 0, st>>>(w.gkb, 1, 1);
+        ::mof::count_launch(), k_fill_int<<<1, 32, 0, st>>>(w.err, 1, 0);
+        ::mof::count_launch(), k_fill_int<<<1, 32, 0, st>>>(w.flag, 1, 0);
+        ::mof::count_launch(), k_fill<real><<<fb(n), 256, 0, st>>>(w.u, n, (real)0);
+        ::mof::count_launch(), k_fill<real><<<fb(2 * P * ns), 256, 0, st>>>(w.s, 2 * P * ns, (real)0);
+        ::mof::count_launch(), k_fill<real><<<fb(2 * P * ns), 256, 0, st>>>(w.sr, 2 * P * ns, (real)0);
+        ::mof::count_launch(), k_copy<real><<<fb(m), 256, 0, st>>>(b_in, w.b, m);
         MOF_TRY(launch_tile_radii<real>(p, w.s, w.sr, w.rad_s, w.rad_sr, st));
     }
     // ---- GKB on H from b / ||b|| (Sec. 4.1.1), H V_l = U_{l+1} B_l
     {
         Scope sc(tm, "gkb", st);
         kr.norm2(w.b, m, m, 1, w.bb, st);
-        k_sqrt_into<<<1, 1, 0, st>>>(w.bb, w.beta1, 1);
+        ::mof::count_launch(), k_sqrt_into<<<1, 1, 0, st>>>(w.bb, w.beta1, 1);
         kr.append(BU, w.KU, w.b, m, w.bb, nullptr, 0.0, w.gkb, nullptr, nullptr, st);
         for (int j = 0; j < prm.ell; ++j) {
             MOF_TRY(launch_backproject<real>(p, w.U + (long long)j * m, w.r, st));
-            if (j > 0) k_axpy_dev<real><<<dim3(fb(n), 1), 256, 0, st>>>(w.r, n, w.V + (long long)(j - 1) * n, n, w.beta, n, w.gkb);
+            if (j > 0) ::mof::count_launch(), k_axpy_dev<real><<<dim3(fb(n), 1), 256, 0, st>>>(w.r, n, w.V + (long long)(j - 1) * n, n, w.beta, n, w.gkb);
             kr.reorth(BV, w.r, n, w.coef, w.nrm2, st);
-            if (j == 0) k_sqrt_into_if<<<1, 1, 0, st>>>(w.nrm2, w.alpha1, 1, w.gkb);
-            k_sqrt_into_if<<<1, 1, 0, st>>>(w.nrm2, w.alpha, 1, w.gkb);
+            if (j == 0) ::mof::count_launch(), k_sqrt_into_if<<<1, 1, 0, st>>>(w.nrm2, w.alpha1, 1, w.gkb);
+            ::mof::count_launch(), k_sqrt_into_if<<<1, 1, 0, st>>>(w.nrm2, w.alpha, 1, w.gkb);
             kr.append(BV, w.K, w.r, n, w.nrm2, j == 0 ? nullptr : w.alpha1, tol, w.gkb, nullptr, nullptr, st);
             MOF_TRY(launch_project<real>(p, w.V + (long long)j * n, w.uT, w.HV + (long long)j * m, st));
-            k_copy<real><<<fb(m), 256, 0, st>>>(w.HV + (long long)j * m, w.tm, m);
-            k_axpy_dev<real><<<dim3(fb(m), 1), 256, 0, st>>>(w.tm, m, w.U + (long long)j * m, m, w.alpha, m, w.gkb);
+            ::mof::count_launch(), k_copy<real><<<fb(m), 256, 0, st>>>(w.HV + (long long)j * m, w.tm, m);
+            ::mof::count_launch(), k_axpy_dev<real><<<dim3(fb(m), 1), 256, 0, st>>>(w.tm, m, w.U + (long long)j * m, m, w.alpha, m, w.gkb);
             kr.reorth(BU, w.tm, m, w.coef, w.nrm2, st);
-            k_sqrt_into_if<<<1, 1, 0, st>>>(w.nrm2, w.beta, 1, w.gkb);
+            ::mof::count_launch(), k_sqrt_into_if<<<1, 1, 0, st>>>(w.nrm2, w.beta, 1, w.gkb);
             kr.append(BU, w.KU, w.tm, m, w.nrm2, w.beta1, tol, w.gkb, nullptr, nullptr, st);
         }
         // breakdown scale of the expansions: ||H^T b|| = alpha_1 beta_1
-        k_mul_into<<<1, 1, 0, st>>>(w.alpha1, w.beta1, w.scaleR, 1);
+        ::mof::count_launch(), k_mul_into<<<1, 1, 0, st>>>(w.alpha1, w.beta1, w.scaleR, 1);
         for (int j = 0; j < prm.ell; ++j) {
             DotVecs<real> xs{{w.HV + (long long)j * m, w.b, nullptr}, {m, m, 0}};
             DotOuts o{};
@@ -831,9 +831,9 @@ static mof_status solve_impl(mof_problem *p, const mof_solver_params &prm, int n
         }
         {
             Scope sc(tm, "theta_gram", st);
-            k_theta_gram<real><<<w.gram_ctas, TG_T, tg_smem, st>>>(w.V, n, Kmax, w.K, w.u, w.s, w.sr, eps2, p->nx, p->ny, p->nt,
+            ::mof::count_launch(), k_theta_gram<real><<<w.gram_ctas, TG_T, tg_smem, st>>>(w.V, n, Kmax, w.K, w.u, w.s, w.sr, eps2, p->nx, p->ny, p->nt,
                                                                    w.gpart);
-            k_gram_reduce<<<8, 256, 0, st>>>(w.gpart, w.gram_ctas, Kmax, w.K, w.GT);
+            ::mof::count_launch(), k_gram_reduce<<<8, 256, 0, st>>>(w.gpart, w.gram_ctas, Kmax, w.K, w.GT);
         }
         {
             Scope sc(tm, "small_solve", st);
@@ -863,7 +863,7 @@ static mof_status solve_impl(mof_problem *p, const mof_solver_params &prm, int n
             {
                 Scope sc(tm, "project", st);
                 MOF_TRY(launch_project<real>(p, w.vnew, w.uT, w.hvnew, st));
-                k_store_slot<real><<<fb(m), 256, 0, st>>>(w.HV, m, w.K, w.appended, w.hvnew);
+                ::mof::count_launch(), k_store_slot<real><<<fb(m), 256, 0, st>>>(w.HV, m, w.K, w.appended, w.hvnew);
             }
             {
                 Scope sc(tm, "gram_h", st);
@@ -873,13 +873,13 @@ static mof_status solve_impl(mof_problem *p, const mof_solver_params &prm, int n
                 o.o[0] = DotOut{w.GH, 0, Kmax, 1, 1, 1.0};
                 o.o[1] = DotOut{w.gH, 0, 1, 0, 0, 1.0};
                 kr.multidot(BHn, 2, xs, o, st);
-                k_sym_last<<<1, 64, 0, st>>>(w.GH, Kmax, w.K, w.appended);
+                ::mof::count_launch(), k_sym_last<<<1, 64, 0, st>>>(w.GH, Kmax, w.K, w.appended);
             }
         }
         {
             Scope sc(tm, "misc", st);
-            k_copy<real><<<fb(n), 256, 0, st>>>(w.un, w.u, n);
-            k_report<<<1, 1, 0, st>>>(w.report, k, w.lam, w.nrm2b, w.nrm2, w.K, w.flag, w.Kv_of, P, of_now ? 1 : 0,
+            ::mof::count_launch(), k_copy<real><<<fb(n), 256, 0, st>>>(w.un, w.u, n);
+            ::mof::count_launch(), k_report<<<1, 1, 0, st>>>(w.report, k, w.lam, w.nrm2b, w.nrm2, w.K, w.flag, w.Kv_of, P, of_now ? 1 : 0,
                                       expand ? 1 : 0, w.appended);
         }
     }
@@ -915,7 +915,7 @@ static mof_status solve_of_entry(mof_problem *p, const mof_solver_params &prm, c
     MOF_TRY(ensure_ws<real>(p, prm, 1, wp));
     Timer *tm = p->timing ? &h->timer : nullptr;
     if (tm) tm->reset();
-    k_fill_int<<<1, 32, 0, st>>>(wp->err, 1, 0);
+    ::mof::count_launch(), k_fill_int<<<1, 32, 0, st>>>(wp->err, 1, 0);
     MOF_TRY(solve_of_impl<real>(p, prm, *wp, u, s, tm, st));
     int err = 0;
     MOF_CUDA(cudaMemcpyAsync(&err, wp->err, sizeof(int), cudaMemcpyDeviceToHost, st));
