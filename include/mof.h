@@ -177,7 +177,8 @@ mof_status mof_apply_reg_normal(mof_problem *p, const void *x, const void *uk, c
 mof_status mof_solve_of(mof_problem *p, const mof_solver_params *prm, const void *u, void *s,
                         void *stream);
 
-/* MMGKS-OF (Alg. 1) for n_outer outer iterations from u^(0) = 0, s^(0) = 0.
+/* MMGKS-OF (Alg. 1) for n_outer outer iterations from u^(0) = 0, s^(0) = 0
+ * (ell + n_outer <= 60 and of_ell + of_iters <= 64; larger: MOF_EUNSUPPORTED).
  * b: m (device). u_out: n. s_out, sr_out: nv each, may be NULL (the flow
  * used by the last iteration). report: HOST array of n_outer records, may
  * be NULL. The library allocates its workspace (Krylov bases, Gram

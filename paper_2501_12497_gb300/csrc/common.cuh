@@ -30,8 +30,11 @@ mof_status cuda_fail(cudaError_t e, const char *what, const char *file, int line
         if (s_ != MOF_OK) return s_;        \
     } while (0)
 
-// Kernel-launch counter (every launch site calls count_launch()).
+// Kernel-launch counter (every launch site calls count_launch()); graph
+// replays add the number of kernel nodes they execute.
 void count_launch();
+void count_launches_add(long long k);
+long long launches_so_far();
 
 // Launch-error check after a kernel launch.
 #define MOF_LAUNCH_CHECK() MOF_CUDA(cudaGetLastError())

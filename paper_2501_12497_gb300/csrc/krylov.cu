@@ -14,10 +14,15 @@
 namespace mof {
 
 constexpr int KT = 256;                    // threads per block
-constexpr int KE = 8;                      // elements per thread per chunk
-constexpr int CHUNK = KT * KE;             // elements per chunk
+constexpr int KE = 8;                      // elements per thread per chunk (norms, scalar paths)
+constexpr int CHUNK = KT * KE;             // elements per chunk of the scalar kernels
+constexpr int DCH_BYTES = 16384;           // bytes of one staged right-hand chunk of the multi-dot
+template <typename real>
+constexpr int dch() { return DCH_BYTES / (int)sizeof(real); }  // elements per multi-dot chunk
 
 long long krylov_chunks(long long N) { return (N + CHUNK - 1) / CHUNK; }
+template <typename real>
+long long mdot_chunks(long long N) { return (N + dch<real>() - 1) / dch<real>(); }
 
 // block-wide sum of one value per thread into thread 0's return (FP64 across warps)
 template <typename acc_t>
@@ -34,59 +39,73 @@ __device__ __forceinline__ double block_sum_to_double(acc_t v, double *sh) {
     return r;
 }
 
-// partial[b][chunk][v][j] = sum_{i in chunk} V[b][j][i] * x_v[b][i], j < K[b], v < NV
-template <typename real, int NV>
+// partial[b][chunk][v][j] = sum_{i in chunk} V[b][j][i] * x_v[b][i], j < K[b], v < NV.
+// The NV right-hand chunks are staged in shared memory; warp w streams the
+// basis vectors j = w, w + 8, ... of the chunk (16-byte loads when VEC) and
+// reduces each dot once.
+template <typename real, int NV, bool VEC>
 __global__ void __launch_bounds__(KT) k_mdot(const real *__restrict__ V, long long N, int Kmax, const int *__restrict__ K,
                                              const int *__restrict__ act, DotVecs<real> xs, double *__restrict__ partial,
                                              int nchunk) {
-    __shared__ real sw[NV][KT / 32][32];
+    constexpr int DCH = dch<real>();
+    __shared__ __align__(16) real sx[NV][DCH];
     const int b = blockIdx.y, chunk = blockIdx.x;
     if (act && !act[b]) return;
     const int Kb = min(K[b], Kmax);
-    const long long i0 = (long long)chunk * CHUNK + threadIdx.x;
-    const real *Vb = V + (long long)b * Kmax * N;
-    real xv[NV][KE];
-#pragma unroll
-    for (int v = 0; v < NV; ++v)
-#pragma unroll
-        for (int e = 0; e < KE; ++e) {
-            const long long i = i0 + (long long)e * KT;
-            xv[v][e] = i < N ? xs.x[v][b * xs.stride[v] + i] : (real)0;
-        }
+    const long long c0 = (long long)chunk * DCH;
+    const int len = (int)min((long long)DCH, N - c0);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    for (int j0 = 0; j0 < Kb; j0 += 32) {
-        const int jn = min(32, Kb - j0);
-        for (int jj = 0; jj < jn; ++jj) {
-            const real *vj = Vb + (long long)(j0 + jj) * N;
-            real a[NV];
 #pragma unroll
-            for (int v = 0; v < NV; ++v) a[v] = 0;
+    for (int v = 0; v < NV; ++v) {
+        const real *xb = xs.x[v] + b * xs.stride[v] + c0;
+        for (int i = threadIdx.x; i < DCH; i += KT) sx[v][i] = i < len ? xb[i] : (real)0;
+    }
+    __syncthreads();
+    const real *Vb = V + (long long)b * Kmax * N + c0;
+    for (int j = w; j < Kb; j += KT / 32) {
+        const real *vj = Vb + (long long)j * N;
+        real a[NV];
 #pragma unroll
-            for (int e = 0; e < KE; ++e) {
-                const long long i = i0 + (long long)e * KT;
-                if (i < N) {
-                    const real vv = vj[i];
+        for (int v = 0; v < NV; ++v) a[v] = 0;
+        if constexpr (VEC) {
+            const float4 *v4 = reinterpret_cast<const float4 *>(vj);
+            const int n4 = len >> 2;
+            int i = l;
+#pragma unroll 1
+            for (; i + 96 < n4; i += 128) {
+                const float4 q0 = __ldcs(v4 + i), q1 = __ldcs(v4 + i + 32), q2 = __ldcs(v4 + i + 64), q3 = __ldcs(v4 + i + 96);
 #pragma unroll
-                    for (int v = 0; v < NV; ++v) a[v] += vv * xv[v][e];
+                for (int v = 0; v < NV; ++v) {
+                    const float4 *x4 = reinterpret_cast<const float4 *>(sx[v]);
+                    const float4 y0 = x4[i], y1 = x4[i + 32], y2 = x4[i + 64], y3 = x4[i + 96];
+                    a[v] += q0.x * y0.x + q0.y * y0.y + q0.z * y0.z + q0.w * y0.w;
+                    a[v] += q1.x * y1.x + q1.y * y1.y + q1.z * y1.z + q1.w * y1.w;
+                    a[v] += q2.x * y2.x + q2.y * y2.y + q2.z * y2.z + q2.w * y2.w;
+                    a[v] += q3.x * y3.x + q3.y * y3.y + q3.z * y3.z + q3.w * y3.w;
                 }
             }
+            for (; i < n4; i += 32) {
+                const float4 q = __ldcs(v4 + i);
 #pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                real t = a[v];
-                if constexpr (sizeof(real) == 4) t = warp_sumf(t);
-                else t = warp_sum(t);
-                if (l == 0) sw[v][w][jj] = t;
+                for (int v = 0; v < NV; ++v) {
+                    const float4 y = reinterpret_cast<const float4 *>(sx[v])[i];
+                    a[v] += q.x * y.x + q.y * y.y + q.z * y.z + q.w * y.w;
+                }
+            }
+        } else {
+            for (int i = l; i < len; i += 32) {
+                const real q = vj[i];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) a[v] += q * sx[v][i];
             }
         }
-        __syncthreads();
-        for (int e = threadIdx.x; e < NV * jn; e += KT) {
-            const int v = e / jn, jj = e % jn;
-            double s = 0.0;
 #pragma unroll
-            for (int ww = 0; ww < KT / 32; ++ww) s += (double)sw[v][ww][jj];
-            partial[(((long long)b * nchunk + chunk) * NV + v) * Kmax + j0 + jj] = s;
+        for (int v = 0; v < NV; ++v) {
+            real t = a[v];
+            if constexpr (sizeof(real) == 4) t = warp_sumf(t);
+            else t = warp_sum(t);
+            if (l == 0) partial[(((long long)b * nchunk + chunk) * NV + v) * Kmax + j] = (double)t;
         }
-        __syncthreads();
     }
 }
 
@@ -109,50 +128,69 @@ __global__ void k_sum_chunks(const double *__restrict__ partial, int nchunk, int
 }
 
 // out[b] = sum_j V[b][j] c[b][j] (mode 0), x[b] - sum_j V[b][j] c[b][j] (mode 1),
-// sum_j V[b][j] c[b][j] - x[b] (mode 2); optionally ||out[b]||^2 per chunk.
-template <typename real, int MODE>
-__global__ void __launch_bounds__(KT) k_combine(const real *__restrict__ V, long long N, int Kmax, const int *__restrict__ K,
+// sum_j V[b][j] c[b][j] - x[b] (mode 2); optionally ||out[b]||^2 per block.
+// One thread per 4 consecutive elements (16-byte loads when VEC), basis
+// vectors streamed four at a time.
+constexpr int CT = 256;
+template <typename real, int MODE, bool VEC>
+__global__ void __launch_bounds__(CT) k_combine(const real *__restrict__ V, long long N, int Kmax, const int *__restrict__ K,
                                                 const int *__restrict__ act, const double *__restrict__ c, long long cstride,
                                                 const real *__restrict__ x, long long xstride, real *__restrict__ out,
-                                                long long ostride, double *__restrict__ nrm_partial, int nchunk) {
+                                                long long ostride, double *__restrict__ nrm_partial, int nblk) {
     __shared__ real sc[64];
-    __shared__ double sh[KT / 32];
-    const int b = blockIdx.y, chunk = blockIdx.x;
+    __shared__ double sh[CT / 32];
+    const int b = blockIdx.y;
     if (act && !act[b]) return;
     const int Kb = min(K[b], Kmax);
-    const long long i0 = (long long)chunk * CHUNK + threadIdx.x;
+    for (int j = threadIdx.x; j < Kb; j += CT) sc[j] = (real)c[b * cstride + j];
+    __syncthreads();
+    const long long i4 = ((long long)blockIdx.x * CT + threadIdx.x) * 4;
     const real *Vb = V + (long long)b * Kmax * N;
-    real acc[KE];
+    real n2 = 0;
+    if (i4 < N) {
+        real acc[4] = {0, 0, 0, 0};
+        if (VEC && i4 + 3 < N) {
+            int j = 0;
+            for (; j + 3 < Kb; j += 4) {
+                const float4 q0 = __ldcs(reinterpret_cast<const float4 *>(Vb + (long long)j * N + i4));
+                const float4 q1 = __ldcs(reinterpret_cast<const float4 *>(Vb + (long long)(j + 1) * N + i4));
+                const float4 q2 = __ldcs(reinterpret_cast<const float4 *>(Vb + (long long)(j + 2) * N + i4));
+                const float4 q3 = __ldcs(reinterpret_cast<const float4 *>(Vb + (long long)(j + 3) * N + i4));
+                const real c0 = sc[j], c1 = sc[j + 1], c2 = sc[j + 2], c3 = sc[j + 3];
+                acc[0] += q0.x * c0 + q1.x * c1 + q2.x * c2 + q3.x * c3;
+                acc[1] += q0.y * c0 + q1.y * c1 + q2.y * c2 + q3.y * c3;
+                acc[2] += q0.z * c0 + q1.z * c1 + q2.z * c2 + q3.z * c3;
+                acc[3] += q0.w * c0 + q1.w * c1 + q2.w * c2 + q3.w * c3;
+            }
+            for (; j < Kb; ++j) {
+                const float4 q = __ldcs(reinterpret_cast<const float4 *>(Vb + (long long)j * N + i4));
+                const real cj = sc[j];
+                acc[0] += q.x * cj;
+                acc[1] += q.y * cj;
+                acc[2] += q.z * cj;
+                acc[3] += q.w * cj;
+            }
+        } else {
+            for (int j = 0; j < Kb; ++j) {
+                const real cj = sc[j];
 #pragma unroll
-    for (int e = 0; e < KE; ++e) acc[e] = 0;
-    for (int j0 = 0; j0 < Kb; j0 += 64) {
-        const int jn = min(64, Kb - j0);
-        __syncthreads();
-        if (threadIdx.x < jn) sc[threadIdx.x] = (real)c[b * cstride + j0 + threadIdx.x];
-        __syncthreads();
-        for (int jj = 0; jj < jn; ++jj) {
-            const real *vj = Vb + (long long)(j0 + jj) * N;
-            const real cj = sc[jj];
-#pragma unroll
-            for (int e = 0; e < KE; ++e) {
-                const long long i = i0 + (long long)e * KT;
-                if (i < N) acc[e] += vj[i] * cj;
+                for (int e = 0; e < 4; ++e)
+                    if (i4 + e < N) acc[e] += Vb[(long long)j * N + i4 + e] * cj;
             }
         }
-    }
-    real n2 = 0;
 #pragma unroll
-    for (int e = 0; e < KE; ++e) {
-        const long long i = i0 + (long long)e * KT;
-        if (i < N) {
-            const real v = MODE == 1 ? x[b * xstride + i] - acc[e] : (MODE == 2 ? acc[e] - x[b * xstride + i] : acc[e]);
-            out[b * ostride + i] = v;
-            n2 += v * v;
+        for (int e = 0; e < 4; ++e) {
+            const long long i = i4 + e;
+            if (i < N) {
+                const real v = MODE == 1 ? x[b * xstride + i] - acc[e] : (MODE == 2 ? acc[e] - x[b * xstride + i] : acc[e]);
+                out[b * ostride + i] = v;
+                n2 += v * v;
+            }
         }
     }
     if (nrm_partial) {
         const double s = block_sum_to_double(n2, sh);
-        if (threadIdx.x == 0) nrm_partial[(long long)b * nchunk + chunk] = s;
+        if (threadIdx.x == 0) nrm_partial[(long long)b * nblk + blockIdx.x] = s;
     }
 }
 
@@ -234,40 +272,71 @@ void Krylov<real>::dots(const BasisRef<real> &B, const real *x, long long xstrid
 }
 
 template <typename real>
+static bool vec_ok(const void *base, long long N, long long stride) {
+    return sizeof(real) == 4 && (N % 4) == 0 && (stride % 4) == 0 && (reinterpret_cast<uintptr_t>(base) % 16) == 0;
+}
+
+template <typename real>
 void Krylov<real>::multidot(const BasisRef<real> &B, int nv, const DotVecs<real> &xs, const DotOuts &outs,
                             cudaStream_t st) const {
-    const int nc = (int)krylov_chunks(B.N);
+    const int nc = (int)mdot_chunks<real>(B.N);
     const dim3 grid(nc, B.B);
-    if (nv == 1) ::mof::count_launch(), k_mdot<real, 1><<<grid, KT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, xs, partial, nc);
-    else if (nv == 2) ::mof::count_launch(), k_mdot<real, 2><<<grid, KT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, xs, partial, nc);
-    else ::mof::count_launch(), k_mdot<real, 3><<<grid, KT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, xs, partial, nc);
+    const bool vec = vec_ok<real>(B.V, B.N, (long long)B.Kmax * B.N);
+#define MDOT(NVv)                                                                                                       \
+    if (vec) ::mof::count_launch(), k_mdot<real, NVv, true><<<grid, KT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, xs, partial, nc); \
+    else ::mof::count_launch(), k_mdot<real, NVv, false><<<grid, KT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, xs, partial, nc);
+    if (nv == 1) {
+        MDOT(1)
+    } else if (nv == 2) {
+        MDOT(2)
+    } else {
+        MDOT(3)
+    }
+#undef MDOT
     ::mof::count_launch(), k_sum_chunks<<<B.B, 128, 0, st>>>(partial, nc, nv, B.Kmax, B.K, B.act, outs);
 }
 
 template <typename real>
 void Krylov<real>::combine(const BasisRef<real> &B, const double *c, long long cstride, real *out, long long ostride,
                            cudaStream_t st) const {
-    const int nc = (int)krylov_chunks(B.N);
-    ::mof::count_launch(), k_combine<real, 0><<<dim3(nc, B.B), KT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, c, cstride, nullptr, 0, out, ostride, nullptr,
-                                                     nc);
+    const int nb = (int)((B.N + 4LL * CT - 1) / (4LL * CT));
+    const bool vec = vec_ok<real>(B.V, B.N, (long long)B.Kmax * B.N) && (ostride % 4 == 0);
+    if (vec)
+        ::mof::count_launch(), k_combine<real, 0, true><<<dim3(nb, B.B), CT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, c, cstride,
+                                                                                   nullptr, 0, out, ostride, nullptr, nb);
+    else
+        ::mof::count_launch(), k_combine<real, 0, false><<<dim3(nb, B.B), CT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, c, cstride,
+                                                                                    nullptr, 0, out, ostride, nullptr, nb);
 }
 
 template <typename real>
 void Krylov<real>::combine_minus(const BasisRef<real> &B, const double *c, long long cstride, const real *x, long long xstride,
                                  real *out, long long ostride, double *nrm2_out, cudaStream_t st) const {
-    const int nc = (int)krylov_chunks(B.N);
-    ::mof::count_launch(), k_combine<real, 2><<<dim3(nc, B.B), KT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, c, cstride, x, xstride, out, ostride,
-                                                     nrm2_out ? partial : nullptr, nc);
-    if (nrm2_out) ::mof::count_launch(), k_sum_scalar_chunks<<<(B.B + 63) / 64, 64, 0, st>>>(partial, nc, nrm2_out, B.B);
+    const int nb = (int)((B.N + 4LL * CT - 1) / (4LL * CT));
+    const bool vec = vec_ok<real>(B.V, B.N, (long long)B.Kmax * B.N) && (ostride % 4 == 0);
+    double *np = nrm2_out ? partial : nullptr;
+    if (vec)
+        ::mof::count_launch(), k_combine<real, 2, true><<<dim3(nb, B.B), CT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, c, cstride, x,
+                                                                                   xstride, out, ostride, np, nb);
+    else
+        ::mof::count_launch(), k_combine<real, 2, false><<<dim3(nb, B.B), CT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, c, cstride, x,
+                                                                                    xstride, out, ostride, np, nb);
+    if (nrm2_out) ::mof::count_launch(), k_sum_scalar_chunks<<<(B.B + 63) / 64, 64, 0, st>>>(partial, nb, nrm2_out, B.B);
 }
 
 template <typename real>
 void Krylov<real>::subtract(const BasisRef<real> &B, const double *c, long long cstride, const real *x, long long xstride,
                             real *out, long long ostride, double *nrm2_out, cudaStream_t st) const {
-    const int nc = (int)krylov_chunks(B.N);
-    ::mof::count_launch(), k_combine<real, 1><<<dim3(nc, B.B), KT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, c, cstride, x, xstride, out, ostride,
-                                                     nrm2_out ? partial : nullptr, nc);
-    if (nrm2_out) ::mof::count_launch(), k_sum_scalar_chunks<<<(B.B + 63) / 64, 64, 0, st>>>(partial, nc, nrm2_out, B.B);
+    const int nb = (int)((B.N + 4LL * CT - 1) / (4LL * CT));
+    const bool vec = vec_ok<real>(B.V, B.N, (long long)B.Kmax * B.N) && (ostride % 4 == 0);
+    double *np = nrm2_out ? partial : nullptr;
+    if (vec)
+        ::mof::count_launch(), k_combine<real, 1, true><<<dim3(nb, B.B), CT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, c, cstride, x,
+                                                                                   xstride, out, ostride, np, nb);
+    else
+        ::mof::count_launch(), k_combine<real, 1, false><<<dim3(nb, B.B), CT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, c, cstride, x,
+                                                                                    xstride, out, ostride, np, nb);
+    if (nrm2_out) ::mof::count_launch(), k_sum_scalar_chunks<<<(B.B + 63) / 64, 64, 0, st>>>(partial, nb, nrm2_out, B.B);
 }
 
 template <typename real>

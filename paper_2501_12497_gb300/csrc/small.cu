@@ -13,7 +13,8 @@
 //      decomposition to FP64 accuracy; with the eigenvalues theta_i in [0, 1]
 //      and eigenvectors W, X = R^-1 W satisfies X^T G_A X = diag(theta),
 //      X^T G_L X = diag(1 - theta)/rho (the generalized singular values of
-//      (R_A, R_L));
+//      (R_A, R_L)); the FP64 sweeps rotate the one vector W^T h they need
+//      instead of accumulating W;
 //   3. with ghat = X^T g, chat_i^2 = ghat_i^2 / theta_i and the filter factors
 //      f_i = theta_i / (theta_i + mu (1 - theta_i)), mu = lam / rho, has
 //      ||R_A z - Q_A^T b||^2 = sum chat_i^2 (1 - f_i)^2 and
@@ -24,11 +25,13 @@
 //      log grid (ties to the smaller lam), refined inside its two grid
 //      neighbours by safeguarded Newton steps on dG/dlog10(lam) = 0, kept only
 //      if it improves on the grid value;
-//   5. returns z = X diag(1/(theta + mu (1 - theta))) ghat.
+//   5. returns z = R^-1 (C + mu (I - C))^-1 h, the solution of
+//      (G_A + lam G_L) z = g, by an FP64 Cholesky solve in the R basis.
 // Each Jacobi round updates every 2x2 block (pair i rows, pair j columns) of
 // the matrix from its old values in one pass, so a round costs two barriers.
 #include "solver.cuh"
 
+#include <atomic>
 #include <cfloat>
 
 namespace mof {
@@ -75,6 +78,19 @@ __device__ __forceinline__ void lam_sums(const Spec &S, double mu, int i0, int s
     }
 }
 
+// N = sum c2 g^2 and D = sum g only (the grid scan)
+__device__ __forceinline__ double gcv_plain(const Spec &S, double mu) {
+    double N = 0.0, D = 0.0;
+    for (int i = 0; i < S.K; ++i) {
+        const double th = S.theta[i], a = 1.0 - th, d = th + mu * a;
+        const double g = d > 0.0 ? mu * a / d : 1.0;
+        N += S.c2[i] * g * g;
+        D += g;
+    }
+    const double v = N / (D * D);
+    return v == v ? v : DBL_MAX;
+}
+
 __device__ __forceinline__ void warp_lam_sums(const Spec &S, double t, double s[6]) {
     const double mu = exp10(t) / S.rho;
     lam_sums(S, mu, threadIdx.x & 31, 32, s);
@@ -104,13 +120,35 @@ __device__ __forceinline__ int rr_player(int j, int r, int Kp) {
     return j == 0 ? 0 : 1 + v;
 }
 
+// Rotation (c, s) that zeroes a_pq of the 2x2 block [[a_pp, a_pq], [a_pq, a_qq]]:
+// t = tan(phi) from the classical formula, c = 1/sqrt(1 + t^2), s = t c. For
+// the FP64 sweeps the angle itself is computed in FP32 and c, s in FP64 from
+// it: the rotation stays orthogonal to FP64 accuracy, and an angle accurate
+// to FP32 still shrinks a_pq by ~1e-7 per visit once the matrix is near
+// diagonal (the quadratic phase these sweeps run in).
+__device__ __forceinline__ void rot_angle(float app, float aqq, float apq, float &c, float &s) {
+    const float th = (aqq - app) / (2.0f * apq);
+    const float t = (th >= 0.0f ? 1.0f : -1.0f) / (fabsf(th) + sqrtf(th * th + 1.0f));
+    c = rsqrtf(t * t + 1.0f);
+    s = t * c;
+}
+__device__ __forceinline__ void rot_angle(double app, double aqq, double apq, double &c, double &s) {
+    const float th = (float)(aqq - app) / (2.0f * (float)apq);
+    const double t = (double)((th >= 0.0f ? 1.0f : -1.0f) / (fabsf(th) + sqrtf(th * th + 1.0f)));
+    c = rsqrt(fma(t, t, 1.0));
+    s = t * c;
+}
+
 // Cyclic two-sided Jacobi sweeps on the symmetric Kp x Kp matrix A (padded
-// rows/columns beyond K are zero) with eigenvector accumulation W <- W J,
+// rows/columns beyond K are zero) with eigenvector accumulation W <- W J
+// (W may be null) and/or the rotations applied to one vector v <- J^T v (v may be null),
 // until a sweep applies no rotation (|a_pq| <= rel * sqrt(|a_pp a_qq|) or
-// |a_pq| <= rel_abs * max_i |a_ii|) or max_sweeps. All threads must call.
+// |a_pq| <= rel_abs * max_i |a_ii|) or max_sweeps. Every warp computes the
+// round's rotations itself (pair index = lane) and takes the others' by
+// shuffle; a barrier separates the pivot reads from the block updates and
+// another ends the round. All threads must call.
 template <typename T>
-__device__ void jacobi(T *A, int lda, T *W, int ldw, int K, int Kp, int max_sweeps, T rel, T rel_abs, T *rc, T *rs,
-                       double *red) {
+__device__ void jacobi(T *A, int lda, T *W, int ldw, T *v, int K, int Kp, int max_sweeps, T rel, T rel_abs, double *red) {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int half = Kp / 2;
     double dm = 0.0;
@@ -122,47 +160,42 @@ __device__ void jacobi(T *A, int lda, T *W, int ldw, int K, int Kp, int max_swee
     for (int w = 0; w < ST / 32; ++w) dm = fmax(dm, red[w]);
     __syncthreads();
     const T floor_abs = rel_abs * (T)dm;
+    const T tiny = (T)(sizeof(T) == 8 ? 1e-300 : 1e-30);
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         int any_in_sweep = 0;
         for (int round = 0; round < Kp - 1; ++round) {
-            int active = 0;
-            if (tid < half) {
-                const int p = rr_player(tid, round, Kp), q = rr_player(Kp - 1 - tid, round, Kp);
-                T c = 1, s = 0;
-                if (p < K && q < K) {
-                    const T apq = A[p * lda + q], app = A[p * lda + p], aqq = A[q * lda + q];
-                    if (fabs(apq) > rel * sqrt(fabs(app * aqq)) && fabs(apq) > floor_abs && fabs(apq) > (T)1e-300) {
-                        const T th = (aqq - app) / (2 * apq);
-                        const T t = (th >= 0 ? (T)1 : (T)-1) / (fabs(th) + sqrt(th * th + 1));
-                        c = 1 / sqrt(t * t + 1);
-                        s = t * c;
-                        active = 1;
-                    }
-                }
-                rc[tid] = c;
-                rs[tid] = s;
+            const int pl = rr_player(lane, round, Kp), ql = rr_player(Kp - 1 - lane, round, Kp);
+            T c = 1, s = 0;
+            if (lane < half && pl < K && ql < K) {
+                const T apq = A[pl * lda + ql], app = A[pl * lda + pl], aqq = A[ql * lda + ql];
+                if (fabs(apq) > rel * sqrt(fabs(app * aqq)) && fabs(apq) > floor_abs && fabs(apq) > tiny)
+                    rot_angle(app, aqq, apq, c, s);
             }
-            if (!__syncthreads_or(active)) continue;
+            if (!__any_sync(0xffffffffu, s != (T)0)) continue;  // identical decision in every warp
             any_in_sweep = 1;
-            if (lane < half) {
-                const int pi = rr_player(lane, round, Kp), qi = rr_player(Kp - 1 - lane, round, Kp);
-                const T ci = rc[lane], si = rs[lane];
-                for (int j = wid; j < half; j += ST / 32) {
-                    const int pj = rr_player(j, round, Kp), qj = rr_player(Kp - 1 - j, round, Kp);
-                    const T cj = rc[j], sj = rs[j];
-                    const T a = A[pi * lda + pj], b = A[pi * lda + qj], c = A[qi * lda + pj], d = A[qi * lda + qj];
-                    const T a1 = ci * a - si * c, b1 = ci * b - si * d, c1 = si * a + ci * c, d1 = si * b + ci * d;
-                    A[pi * lda + pj] = cj * a1 - sj * b1;
-                    A[pi * lda + qj] = sj * a1 + cj * b1;
-                    A[qi * lda + pj] = cj * c1 - sj * d1;
-                    A[qi * lda + qj] = sj * c1 + cj * d1;
+            __syncthreads();  // every warp has read this round's pivots before any block is rewritten
+            for (int j = wid; j < half; j += ST / 32) {
+                const int pj = rr_player(j, round, Kp), qj = rr_player(Kp - 1 - j, round, Kp);
+                const T cj = __shfl_sync(0xffffffffu, c, j), sj = __shfl_sync(0xffffffffu, s, j);
+                if (lane < half) {
+                    const T a = A[pl * lda + pj], b = A[pl * lda + qj], cc = A[ql * lda + pj], d = A[ql * lda + qj];
+                    const T a1 = c * a - s * cc, b1 = c * b - s * d, c1 = s * a + c * cc, d1 = s * b + c * d;
+                    A[pl * lda + pj] = cj * a1 - sj * b1;
+                    A[pl * lda + qj] = sj * a1 + cj * b1;
+                    A[ql * lda + pj] = cj * c1 - sj * d1;
+                    A[ql * lda + qj] = sj * c1 + cj * d1;
                 }
-                // W <- W J on the columns of pair `lane`
-                for (int r = wid; r < Kp; r += ST / 32) {
-                    const T wp = W[r * ldw + pi], wq = W[r * ldw + qi];
-                    W[r * ldw + pi] = ci * wp - si * wq;
-                    W[r * ldw + qi] = si * wp + ci * wq;
+            }
+            if (W && lane < half && s != (T)0)
+                for (int r = wid; r < Kp; r += ST / 32) {  // W <- W J on the columns of pair `lane`
+                    const T wp = W[r * ldw + pl], wq = W[r * ldw + ql];
+                    W[r * ldw + pl] = c * wp - s * wq;
+                    W[r * ldw + ql] = s * wp + c * wq;
                 }
+            if (v && wid == 0 && lane < half && s != (T)0) {  // v <- J^T v
+                const T vp = v[pl], vq = v[ql];
+                v[pl] = c * vp - s * vq;
+                v[ql] = s * vp + c * vq;
             }
             __syncthreads();
         }
@@ -177,8 +210,6 @@ __global__ void __launch_bounds__(ST) k_small_solve(SmallArgs a) {
     __shared__ double s_rho, s_piv, s_rho0sq, s_t, s_vgrid;
     __shared__ double s_red[ST / 32];
     __shared__ int s_fail, s_flag, s_ig, s_idx[ST / 32];
-    __shared__ float rcf[33], rsf[33];
-    __shared__ double rcd[33], rsd[33];
     const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int ld = a.ld;
     const int K = min(a.K[b], ld);
@@ -303,7 +334,7 @@ __global__ void __launch_bounds__(ST) k_small_solve(SmallArgs a) {
         AF(Wf, i, j) = i == j ? 1.0f : 0.0f;
     }
     __syncthreads();
-    jacobi<float>(Af, ldf, Wf, ldf, K, Kp, JACOBI32_MAX_SWEEPS, 1e-6f, 1e-7f, rcf, rsf, s_red);
+    jacobi<float>(Af, ldf, Wf, ldf, (float *)nullptr, K, Kp, JACOBI32_MAX_SWEEPS, 1e-6f, 1e-7f, s_red);
 
     // ---------------------------------------------- 2b. FP64: orthonormalise, then Jacobi
     for (int e = tid; e < K * K; e += ST) {
@@ -355,13 +386,17 @@ __global__ void __launch_bounds__(ST) k_small_solve(SmallArgs a) {
         }
     }
     __syncthreads();
-    jacobi<double>(M, lds, X, lds, K, Kp, JACOBI64_MAX_SWEEPS, 1e-16, 1e-18, rcd, rsd, s_red);
-    for (int i = tid; i < K; i += ST) {
+    for (int i = tid; i < Kp; i += ST) {  // gh = X^T h, then rotated along with M
         double s = 0.0;
-        for (int k = 0; k < K; ++k) s += AT(X, k, i) * h[k];
-        theta[i] = fmin(fmax(AT(M, i, i), 0.0), 1.0);
+        if (i < K)
+            for (int k = 0; k < K; ++k) s += AT(X, k, i) * h[k];
         gh[i] = s;
-        c2[i] = theta[i] > THETA_TINY ? s * s / theta[i] : 0.0;
+    }
+    __syncthreads();
+    jacobi<double>(M, lds, (double *)nullptr, lds, gh, K, Kp, JACOBI64_MAX_SWEEPS, 1e-16, 1e-18, s_red);
+    for (int i = tid; i < K; i += ST) {
+        theta[i] = fmin(fmax(AT(M, i, i), 0.0), 1.0);
+        c2[i] = theta[i] > THETA_TINY ? gh[i] * gh[i] / theta[i] : 0.0;
     }
     __syncthreads();
 
@@ -382,11 +417,7 @@ __global__ void __launch_bounds__(ST) k_small_solve(SmallArgs a) {
         const double step = (hi - lo) / (GRID_POINTS - 1);
         double vb = DBL_MAX;
         int ib = tid;
-        if (tid < GRID_POINTS) {
-            double s[6];
-            lam_sums(S, exp10(lo + tid * step) / rho, 0, 1, s);
-            vb = gcv_of(s);
-        }
+        if (tid < GRID_POINTS) vb = gcv_plain(S, exp10(lo + tid * step) / rho);
         for (int o = 16; o > 0; o >>= 1) {  // argmin, ties to the smaller index
             const double vo = __shfl_xor_sync(0xffffffffu, vb, o);
             const int io = __shfl_xor_sync(0xffffffffu, ib, o);
@@ -428,7 +459,7 @@ __global__ void __launch_bounds__(ST) k_small_solve(SmallArgs a) {
                 if (!(tn > A0 && tn < B0)) tn = 0.5 * (A0 + B0);
                 const double dt = fabs(tn - t);
                 t = tn;
-                if (dt <= 1e-14 * fmax(1.0, fabs(t)) || B0 - A0 <= 1e-14 * fmax(1.0, fabs(t))) break;
+                if (dt <= 1e-10 * fmax(1.0, fabs(t)) || B0 - A0 <= 1e-10 * fmax(1.0, fabs(t))) break;
             }
             warp_lam_sums(S, t, s);
             if (gcv_of(s) > s_vgrid) t = lo + ig * step;
@@ -480,23 +511,54 @@ __global__ void __launch_bounds__(ST) k_small_solve(SmallArgs a) {
     const double lam = a.rule == MOF_RULE_FIXED ? a.lam_fixed : exp10(s_t);
     const double mu = lam / rho;
 
-    // ---------------------------------------------- 5. z = R^-1 X y
-    for (int i = tid; i < K; i += ST) {
-        const double d = theta[i] + mu * (1.0 - theta[i]);
-        y[i] = d > 0.0 ? gh[i] / d : 0.0;
+    // ---------------------------------------------- 5. z = R^-1 (C + mu (I - C))^-1 h
+    // (G_A + lam G_L = R^T (C + mu (I - C)) R and g = R^T h)
+    for (int e = tid; e < K * K; e += ST) {
+        const int i = e / K, j = e - (e / K) * K;
+        AT(M, i, j) = (1.0 - mu) * AT(C, i, j) + (i == j ? mu : 0.0);
+    }
+    for (int i = tid; i < K; i += ST) y[i] = h[i];
+    __syncthreads();
+    for (int j = 0; j < K; ++j) {  // Cholesky, upper, in M
+        if (tid == 0) {
+            const double d = AT(M, j, j);
+            if (!(d > 0.0) || !isfinite(d)) s_fail = 1;
+            s_piv = d > 0.0 ? sqrt(d) : 1.0;
+            AT(M, j, j) = s_piv;
+        }
+        __syncthreads();
+        const double inv = 1.0 / s_piv;
+        for (int k = j + 1 + tid; k < K; k += ST) AT(M, j, k) *= inv;
+        __syncthreads();
+        const int rem = K - j - 1;
+        for (int e = tid; e < rem * rem; e += ST) {
+            const int k = j + 1 + e / rem, l = j + 1 + e % rem;
+            if (l >= k) AT(M, k, l) -= AT(M, j, k) * AT(M, j, l);
+        }
+        __syncthreads();
+    }
+    if (wid == 0) {  // forward (R^T w = h) and backward (R y = w) substitution, one warp
+        for (int i = 0; i < K; ++i) {
+            double s = 0.0;
+            for (int k = lane; k < i; k += 32) s += AT(M, k, i) * y[k];
+            s = warp_sum(s);
+            if (lane == 0) y[i] = (y[i] - s) / AT(M, i, i);
+            __syncwarp();
+        }
+        for (int i = K - 1; i >= 0; --i) {
+            double s = 0.0;
+            for (int k = i + 1 + lane; k < K; k += 32) s += AT(M, i, k) * y[k];
+            s = warp_sum(s);
+            if (lane == 0) y[i] = (y[i] - s) / AT(M, i, i);
+            __syncwarp();
+        }
     }
     __syncthreads();
-    for (int i = tid; i < K; i += ST) {  // h = X y
-        double s = 0.0;
-        for (int k = 0; k < K; ++k) s += AT(X, i, k) * y[k];
-        h[i] = s;
-    }
-    __syncthreads();
     for (int i = tid; i < K; i += ST) {
         double s = 0.0;
-        for (int k = i; k < K; ++k) s += AT(Ri, i, k) * h[k];
+        for (int k = i; k < K; ++k) s += AT(Ri, i, k) * y[k];
         z[i] = s;
-        if (!isfinite(s)) atomicOr(a.err, 2);
+        if (!isfinite(s) || s_fail) atomicOr(a.err, 2);
     }
     if (tid == 0) {
         a.lam[b] = lam;
@@ -506,14 +568,25 @@ __global__ void __launch_bounds__(ST) k_small_solve(SmallArgs a) {
 #undef AF
 }
 
-mof_status launch_small_solve(const SmallArgs &a, cudaStream_t st) {
-    const size_t lds = (size_t)a.ld + 2;
-    const size_t smem = sizeof(double) * (6 * lds * lds + 5 * lds);
-    static size_t configured = 0;
-    if (smem > 48 * 1024 && smem > configured) {
+static size_t small_smem(int ld) {
+    const size_t lds = (size_t)ld + 2;
+    return sizeof(double) * (6 * lds * lds + 5 * lds);
+}
+
+mof_status prepare_small_solve(int ld) {
+    // the limit only ever grows: smaller problems launched later still fit
+    static std::atomic<size_t> configured{48 * 1024};
+    const size_t smem = small_smem(ld);
+    size_t cur = configured.load();
+    while (smem > cur) {
         MOF_CUDA(cudaFuncSetAttribute(k_small_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        configured = smem;
+        if (configured.compare_exchange_weak(cur, smem)) break;
     }
+    return MOF_OK;
+}
+
+mof_status launch_small_solve(const SmallArgs &a, cudaStream_t st) {
+    const size_t smem = small_smem(a.ld);
     ::mof::count_launch(), k_small_solve<<<a.B, ST, smem, st>>>(a);
     MOF_LAUNCH_CHECK();
     return MOF_OK;

@@ -26,6 +26,10 @@ struct Timer {
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> pool;
     size_t used = 0;
+    // While a graph is being captured, scopes record external event nodes into
+    // the graph, with events owned by that graph (never reused elsewhere).
+    std::vector<Pending> *sink = nullptr;
+    std::vector<cudaEvent_t> *owned = nullptr;
 
     int cls(const char *name) {
         for (size_t i = 0; i < names.size(); ++i)
@@ -36,6 +40,12 @@ struct Timer {
         return (int)names.size() - 1;
     }
     cudaEvent_t ev() {
+        if (owned) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            owned->push_back(e);
+            return e;
+        }
         if (used == pool.size()) {
             cudaEvent_t e;
             cudaEventCreate(&e);
@@ -49,14 +59,17 @@ struct Timer {
         pending.clear();
         used = 0;
     }
-    void collect() {
-        for (auto &p : pending) {
+    void collect_list(const std::vector<Pending> &lst) {
+        for (auto &p : lst) {
             float t = 0.f;
             if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) {
                 ms[p.cls] += t;
                 count[p.cls] += 1;
             }
         }
+    }
+    void collect() {
+        collect_list(pending);
         pending.clear();
         used = 0;
     }
@@ -76,11 +89,18 @@ struct Scope {
         c = t->cls(name);
         cudaEvent_t a = t->ev();
         b = t->ev();
-        cudaEventRecord(a, st);
-        t->pending.push_back({c, a, b});
+        if (t->sink) {
+            cudaEventRecordWithFlags(a, st, cudaEventRecordExternal);
+            t->sink->push_back({c, a, b});
+        } else {
+            cudaEventRecord(a, st);
+            t->pending.push_back({c, a, b});
+        }
     }
     ~Scope() {
-        if (t) cudaEventRecord(b, st);
+        if (!t) return;
+        if (t->sink) cudaEventRecordWithFlags(b, st, cudaEventRecordExternal);
+        else cudaEventRecord(b, st);
     }
 };
 
@@ -114,7 +134,28 @@ struct WS {
         *beta1_of, *bb_of;
     int *Kv_of, *Ku_of, *grow_of, *gkb_of, *act_of, *app_of, *flag_of;
     double *partial;
+    int *iter;  // device index of the outer iteration (report slot)
     int gram_ctas = 0;
+    // one captured graph per outer-iteration variant: bit 0 Solve-OF, bit 1 expansion,
+    // bit 2 timing scopes present
+    struct IterGraph {
+        cudaGraphExec_t exec = nullptr;
+        long long kernels = 0;  // kernel nodes per replay
+        std::vector<Timer::Pending> ev;
+        std::vector<cudaEvent_t> owned;
+    };
+    IterGraph graphs[8];
+    mof_solver_params gkey{};
+    int gkey_n = -1;
+    cudaStream_t ss = nullptr;  // internal stream (graphs cannot be captured on the legacy stream)
+    cudaEvent_t join = nullptr;
+    void drop_graphs() {
+        for (auto &g : graphs) {
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+            for (auto e : g.owned) cudaEventDestroy(e);
+            g = IterGraph();
+        }
+    }
 };
 
 struct Holder {
@@ -139,6 +180,9 @@ static Holder *holder(mof_problem *p) {
 template <typename real>
 static void free_ws(WS<real> *w) {
     if (!w) return;
+    w->drop_graphs();
+    if (w->ss) cudaStreamDestroy(w->ss);
+    if (w->join) cudaEventDestroy(w->join);
     if (w->mem) cudaFree(w->mem);
     delete w;
 }
@@ -180,7 +224,7 @@ constexpr int TG_ROWS = 4 * TG_PIX;
 template <typename real>
 static size_t theta_gram_smem(int Kmax) {
     const int Ks = ((Kmax + 3) / 4) * 4 + 4;
-    return sizeof(real) * TG_ROWS * Ks + sizeof(double) * Kmax * Kmax;
+    return sizeof(real) * TG_ROWS * Ks;
 }
 
 template <typename real>
@@ -240,7 +284,7 @@ static mof_status ensure_ws(mof_problem *p, const mof_solver_params &prm, int n_
         w->beta1 = a.take<double>(1);
         w->alpha1 = a.take<double>(1);
         w->bb = a.take<double>(1);
-        w->gpart = a.take<double>((size_t)w->gram_ctas * Kmax * Kmax);
+        w->gpart = a.take<double>((size_t)w->gram_ctas * 4 * Kmax * Kmax);
         w->K = a.take<int>(1);
         w->KU = a.take<int>(1);
         w->grow = a.take<int>(1);
@@ -285,6 +329,7 @@ static mof_status ensure_ws(mof_problem *p, const mof_solver_params &prm, int n_
         w->app_of = a.take<int>(P);
         w->flag_of = a.take<int>(P);
         w->partial = a.take<double>((size_t)partial);
+        w->iter = a.take<int>(1);
         if (pass == 0) {
             w->bytes = a.off + 256;
             cudaError_t e = cudaMalloc(&w->mem, w->bytes);
@@ -294,6 +339,8 @@ static mof_status ensure_ws(mof_problem *p, const mof_solver_params &prm, int n_
                 return cuda_fail(e, "workspace allocation", __FILE__, __LINE__);
             }
             MOF_CUDA(cudaMemset(w->mem, 0, w->bytes));
+            MOF_CUDA(cudaStreamCreateWithFlags(&w->ss, cudaStreamNonBlocking));
+            MOF_CUDA(cudaEventCreateWithFlags(&w->join, cudaEventDisableTiming));
         }
     }
     const size_t sm = theta_gram_smem<real>(Kmax);
@@ -474,9 +521,10 @@ __global__ void k_of_rhs(const real *__restrict__ ux, const real *__restrict__ u
 // G = (P Theta V)^T (P Theta V), P^2 = diag(((Theta uk)^2 + eps^2)^(-1/2)), over the
 // first K columns of V. Each tile of TG_PIX pixels of one frame yields 4 rows per
 // pixel (Psi_x, Psi_y of the frame; Mbar and Mbar' rows of the pair starting at
-// the frame), written to shared memory scaled by P; the block then adds their
-// outer products to a per-block FP64 Gram (4x4 register blocks of the upper
-// triangle, FP32 within a tile for the FP32 path).
+// the frame), written to shared memory scaled by P. The block's threads own the
+// 4x4 blocks of the upper triangle of G (split over row groups of the tile),
+// accumulate a tile's rows in FP32 registers and carry the running sums across
+// tiles with Kahan compensation; per-block partials are reduced in FP64.
 template <typename real>
 __device__ __forceinline__ real bil_sample(const real *__restrict__ f, int nx, int x0, int x1, int y0, int y1, real wx, real wy) {
     const real a = f[(long long)y0 * nx + x0], b = f[(long long)y0 * nx + x1];
@@ -496,26 +544,48 @@ __device__ __forceinline__ void warp_axis_s(int x, real v, int n, int &i0, int &
     i1 = min(i0 + 1, n - 1);
 }
 
+// number of row groups the tile is split over: 4 while the 4x4 blocks of the
+// upper triangle fit in 64 threads, else 2 (<= 128 blocks, K <= 60)
+__host__ __device__ inline int tg_groups(int K) {
+    const int K4 = (K + 3) / 4;
+    return K4 * (K4 + 1) / 2 <= TG_T / 4 ? 4 : 2;
+}
+
 template <typename real>
 __global__ void __launch_bounds__(TG_T) k_theta_gram(const real *__restrict__ V, long long n, int Kmax, const int *__restrict__ Kp,
                                                      const real *__restrict__ uk, const real *__restrict__ s,
                                                      const real *__restrict__ sr, real eps2, int nx, int ny, int nt,
                                                      double *__restrict__ partial) {
-    extern __shared__ unsigned char smraw[];
+    extern __shared__ __align__(16) unsigned char smraw[];
     const int Ks = ((Kmax + 3) / 4) * 4 + 4;
     real *A = reinterpret_cast<real *>(smraw);
-    double *Gs = reinterpret_cast<double *>(smraw + sizeof(real) * TG_ROWS * Ks);
     const int K = min(Kp[0], Kmax);
     const int K4 = (K + 3) / 4;
     const int nblk = K4 * (K4 + 1) / 2;
+    const int G = tg_groups(K);
+    const int gsize = TG_T / G, rows_per_group = TG_ROWS / G;
     const int tid = threadIdx.x;
-    for (int e = tid; e < Kmax * Kmax; e += TG_T) Gs[e] = 0.0;
+    const int group = tid / gsize, blk = tid - group * gsize;
+    // this thread's 4x4 block (I, J), I <= J, row-major over the upper triangle
+    int I = 0, J = 0;
+    if (blk < nblk) {
+        int rem = blk;
+        while (rem >= K4 - I) {
+            rem -= K4 - I;
+            ++I;
+        }
+        J = I + rem;
+    }
+    real sum[4][4], comp[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) sum[a][c] = comp[a][c] = 0;
     const long long ns = (long long)nx * ny;
     const long long tpf = (ns + TG_PIX - 1) / TG_PIX;
     const long long ntiles = tpf * nt;
     const int np = nt - 1;
     const int q = tid & 3;
-    const int group = tid >> 6, gl = tid & 63;
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int t = (int)(tile / tpf);
         const long long pix = (tile % tpf) * TG_PIX + (tid >> 2);
@@ -556,54 +626,67 @@ __global__ void __launch_bounds__(TG_T) k_theta_gram(const real *__restrict__ V,
         }
         for (int j = K; j < K4 * 4; ++j) Arow[j] = 0;
         __syncthreads();
-        for (int blk = gl; blk < nblk; blk += 64) {
-            // blk -> (I, J), I <= J, row-major over the upper triangle
-            int I = 0, rem = blk;
-            while (rem >= K4 - I) {
-                rem -= K4 - I;
-                ++I;
-            }
-            const int J = I + rem;
+        if (blk < nblk) {
             real acc[4][4];
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
                 for (int c = 0; c < 4; ++c) acc[a][c] = 0;
-            for (int rr = 0; rr < 64; ++rr) {
-                const real *row = A + (group * 64 + rr) * Ks;
+            const real *rowp = A + (long long)group * rows_per_group * Ks;
+            for (int rr = 0; rr < rows_per_group; ++rr, rowp += Ks) {
                 real va[4], vb[4];
+                if constexpr (sizeof(real) == 4) {
+                    const float4 fa4 = *reinterpret_cast<const float4 *>(rowp + 4 * I);
+                    const float4 fb4 = *reinterpret_cast<const float4 *>(rowp + 4 * J);
+                    va[0] = fa4.x; va[1] = fa4.y; va[2] = fa4.z; va[3] = fa4.w;
+                    vb[0] = fb4.x; vb[1] = fb4.y; vb[2] = fb4.z; vb[3] = fb4.w;
+                } else {
 #pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    va[a] = row[4 * I + a];
-                    vb[a] = row[4 * J + a];
+                    for (int a = 0; a < 4; ++a) {
+                        va[a] = rowp[4 * I + a];
+                        vb[a] = rowp[4 * J + a];
+                    }
                 }
 #pragma unroll
                 for (int a = 0; a < 4; ++a)
 #pragma unroll
                     for (int c = 0; c < 4; ++c) acc[a][c] += va[a] * vb[c];
             }
+            // Kahan-compensated carry of the tile sums
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    const int i = 4 * I + a, jj = 4 * J + c;
-                    if (i < K && jj < K) atomicAdd(&Gs[i * Kmax + jj], (double)acc[a][c]);
+                    const real yv = acc[a][c] - comp[a][c];
+                    const real tv = sum[a][c] + yv;
+                    comp[a][c] = (tv - sum[a][c]) - yv;
+                    sum[a][c] = tv;
                 }
         }
         __syncthreads();
     }
-    double *out = partial + (long long)blockIdx.x * Kmax * Kmax;
-    for (int e = tid; e < Kmax * Kmax; e += TG_T) out[e] = Gs[e];
+    // partial[blockIdx.x * G + group][i][j] for this thread's block (upper triangle)
+    if (blk < nblk) {
+        double *out = partial + ((long long)blockIdx.x * G + group) * Kmax * Kmax;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int i = 4 * I + a, jj = 4 * J + c;
+                if (i < K && jj < K && i <= jj) out[i * Kmax + jj] = (double)sum[a][c] - (double)comp[a][c];
+            }
+    }
 }
 
-// G[i][j] = sum over blocks of the upper-triangle partials, mirrored
-__global__ void k_gram_reduce(const double *__restrict__ partial, int nparts, int Kmax, const int *__restrict__ Kp,
+// G[i][j] = sum over all block partials (upper triangle), mirrored
+__global__ void k_gram_reduce(const double *__restrict__ partial, int nblocks, int Kmax, const int *__restrict__ Kp,
                               double *__restrict__ G) {
     const int K = min(Kp[0], Kmax);
+    const int groups = tg_groups(K);
+    const int nparts = nblocks * groups;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < K * K; e += gridDim.x * blockDim.x) {
         const int i = e / K, j = e % K;
         if (i > j) continue;
-        // entries inside a 4x4 diagonal block were produced both ways; take i <= j
         double s = 0.0;
         for (int c = 0; c < nparts; ++c) s += partial[(long long)c * Kmax * Kmax + i * Kmax + j];
         G[i * Kmax + j] = s;
@@ -612,9 +695,12 @@ __global__ void k_gram_reduce(const double *__restrict__ partial, int nparts, in
 }
 
 // report[k] = {lam, resid, rnorm, basis, flag, of_min, of_max}
-__global__ void k_report(double *__restrict__ rep, int k, const double *__restrict__ lam, const double *__restrict__ resid2,
-                         const double *__restrict__ rn2, const int *__restrict__ K, const int *__restrict__ flag,
-                         const int *__restrict__ Kof, int P, int of_ran, int expanded, const int *__restrict__ appended) {
+__global__ void k_report(double *__restrict__ rep, int *__restrict__ iter, const double *__restrict__ lam,
+                         const double *__restrict__ resid2, const double *__restrict__ rn2, const int *__restrict__ K,
+                         const int *__restrict__ flag, const int *__restrict__ Kof, int P, int of_ran, int expanded,
+                         const int *__restrict__ appended) {
+    const int k = iter[0];
+    iter[0] = k + 1;
     double *r = rep + (long long)k * 8;
     r[0] = lam[0];
     r[1] = sqrt(resid2[0]);
@@ -741,11 +827,15 @@ static mof_status solve_of_impl(mof_problem *p, const mof_solver_params &prm, WS
 // ============================================================ MMGKS-OF
 template <typename real>
 static mof_status solve_impl(mof_problem *p, const mof_solver_params &prm, int n_outer, const real *b_in, real *u_out,
-                             real *s_out, real *sr_out, mof_report *report, cudaStream_t st) {
+                             real *s_out, real *sr_out, mof_report *report, cudaStream_t ust) {
     Holder *h = holder(p);
     WS<real> *&wp = ws_slot<real>(h);
     MOF_TRY(ensure_ws<real>(p, prm, n_outer, wp));
     WS<real> &w = *wp;
+    // all work runs on the problem's own stream, ordered after the caller's stream
+    const cudaStream_t st = w.ss;
+    MOF_CUDA(cudaEventRecord(w.join, ust));
+    MOF_CUDA(cudaStreamWaitEvent(st, w.join, 0));
     Timer *tm = p->timing ? &h->timer : nullptr;
     if (tm) tm->reset();
     const long long n = p->n, m = p->m, ns = p->ns;
@@ -768,6 +858,7 @@ static mof_status solve_impl(mof_problem *p, const mof_solver_params &prm, int n
         ::mof::count_launch(), k_fill_int<<<1, 32, 0, st>>>(w.gkb, 1, 1);
         ::mof::count_launch(), k_fill_int<<<1, 32, 0, st>>>(w.err, 1, 0);
         ::mof::count_launch(), k_fill_int<<<1, 32, 0, st>>>(w.flag, 1, 0);
+        ::mof::count_launch(), k_fill_int<<<1, 32, 0, st>>>(w.iter, 1, 0);
         ::mof::count_launch(), k_fill<real><<<fb(n), 256, 0, st>>>(w.u, n, (real)0);
         ::mof::count_launch(), k_fill<real><<<fb(2 * P * ns), 256, 0, st>>>(w.s, 2 * P * ns, (real)0);
         ::mof::count_launch(), k_fill<real><<<fb(2 * P * ns), 256, 0, st>>>(w.sr, 2 * P * ns, (real)0);
@@ -821,8 +912,9 @@ static mof_status solve_impl(mof_problem *p, const mof_solver_params &prm, int n
     sa.flag = w.flag;
     sa.err = w.err;
     const real eps2 = (real)(prm.eps * prm.eps);
-    for (int k = 0; k < n_outer; ++k) {
-        const bool of_now = prm.tau > 0 && (k % prm.tau) == 0;
+    // One outer iteration of Alg. 1 (k is tracked on the device); enqueued directly
+    // or captured once per variant into a CUDA graph and replayed.
+    auto iteration = [&](bool of_now, bool expand) -> mof_status {
         if (of_now) {
             MOF_TRY(solve_of_impl<real>(p, prm, w, w.u, w.s, tm, st));
             Scope sc(tm, "reverse_flow", st);
@@ -844,7 +936,6 @@ static mof_status solve_impl(mof_problem *p, const mof_solver_params &prm, int n
             kr.combine(BV, w.z, Kmax, w.un, n, st);
             kr.combine_minus(BH, w.z, Kmax, w.b, m, w.tm, m, w.nrm2b, st);  // H V z - b
         }
-        const bool expand = k < n_outer - 1;
         if (expand) {
             {
                 Scope sc(tm, "backproject", st);
@@ -879,8 +970,57 @@ static mof_status solve_impl(mof_problem *p, const mof_solver_params &prm, int n
         {
             Scope sc(tm, "misc", st);
             ::mof::count_launch(), k_copy<real><<<fb(n), 256, 0, st>>>(w.un, w.u, n);
-            ::mof::count_launch(), k_report<<<1, 1, 0, st>>>(w.report, k, w.lam, w.nrm2b, w.nrm2, w.K, w.flag, w.Kv_of, P, of_now ? 1 : 0,
-                                      expand ? 1 : 0, w.appended);
+            ::mof::count_launch(), k_report<<<1, 1, 0, st>>>(w.report, w.iter, w.lam, w.nrm2b, w.nrm2, w.K, w.flag, w.Kv_of, P,
+                                                             of_now ? 1 : 0, expand ? 1 : 0, w.appended);
+        }
+        MOF_LAUNCH_CHECK();
+        return MOF_OK;
+    };
+    if (std::memcmp(&w.gkey, &prm, sizeof(prm)) != 0 || w.gkey_n != n_outer) {
+        w.drop_graphs();
+        w.gkey = prm;
+        w.gkey_n = n_outer;
+    }
+    MOF_TRY(prepare_small_solve(Kmax));
+    MOF_TRY(prepare_small_solve(w.Kof));
+    for (int k = 0; k < n_outer; ++k) {
+        const bool of_now = prm.tau > 0 && (k % prm.tau) == 0;
+        const bool expand = k < n_outer - 1;
+        auto &G = w.graphs[(of_now ? 1 : 0) | (expand ? 2 : 0) | (tm ? 4 : 0)];
+        if (!G.exec) {
+            if (tm) {
+                tm->sink = &G.ev;
+                tm->owned = &G.owned;
+            }
+            const long long before = launches_so_far();
+            MOF_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            const mof_status cs = iteration(of_now, expand);
+            cudaGraph_t graph = nullptr;
+            const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+            G.kernels = launches_so_far() - before;
+            count_launches_add(-G.kernels);  // captured, not executed
+            if (tm) {
+                tm->sink = nullptr;
+                tm->owned = nullptr;
+            }
+            if (cs != MOF_OK || ce != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                w.drop_graphs();
+                if (cs != MOF_OK) return cs;
+                return cuda_fail(ce, "graph capture of an outer iteration", __FILE__, __LINE__);
+            }
+            const cudaError_t ie = cudaGraphInstantiate(&G.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ie != cudaSuccess) {
+                G.exec = nullptr;
+                return cuda_fail(ie, "graph instantiation", __FILE__, __LINE__);
+            }
+        }
+        MOF_CUDA(cudaGraphLaunch(G.exec, st));
+        count_launches_add(G.kernels);
+        if (tm) {
+            MOF_CUDA(cudaStreamSynchronize(st));
+            tm->collect_list(G.ev);
         }
     }
     MOF_LAUNCH_CHECK();
@@ -915,6 +1055,7 @@ static mof_status solve_of_entry(mof_problem *p, const mof_solver_params &prm, c
     MOF_TRY(ensure_ws<real>(p, prm, 1, wp));
     Timer *tm = p->timing ? &h->timer : nullptr;
     if (tm) tm->reset();
+    MOF_TRY(prepare_small_solve(wp->Kof));
     ::mof::count_launch(), k_fill_int<<<1, 32, 0, st>>>(wp->err, 1, 0);
     MOF_TRY(solve_of_impl<real>(p, prm, *wp, u, s, tm, st));
     int err = 0;
@@ -930,8 +1071,10 @@ static mof_status check_params(const mof_problem *p, const mof_solver_params *pr
     if (n_outer < 1) return fail(MOF_EINVAL, "n_outer must be >= 1");
     if (prm->ell < 1 || prm->of_ell < 1 || prm->of_iters < 1 || prm->tau < 0 || prm->of_dr < 1 || prm->of_dr > 64)
         return fail(MOF_EINVAL, "invalid solver parameters");
-    if (prm->ell + n_outer > 64 || prm->of_ell + prm->of_iters > 64)
-        return fail(MOF_EUNSUPPORTED, "Krylov bases larger than 64 vectors are not supported (ell + n_outer = %d, of_ell + of_iters = %d)",
+    if (prm->ell + n_outer > 60 || prm->of_ell + prm->of_iters > 64)
+        return fail(MOF_EUNSUPPORTED,
+                    "Krylov bases larger than 60 (image step) / 64 (Solve-OF) vectors are not supported "
+                    "(ell + n_outer = %d, of_ell + of_iters = %d)",
                     prm->ell + n_outer, prm->of_ell + prm->of_iters);
     if (!(prm->eps > 0) || !std::isfinite(prm->eps)) return fail(MOF_EINVAL, "eps must be finite and > 0");
     if (!image_step) return MOF_OK;

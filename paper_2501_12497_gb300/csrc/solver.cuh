@@ -93,5 +93,8 @@ struct SmallArgs {
     int *err;              // error word (|= 1: factorisation failed, 2: non-finite)
 };
 mof_status launch_small_solve(const SmallArgs &a, cudaStream_t st);
+// Raise the kernel's dynamic shared-memory limit for leading dimension ld
+// (done before any graph capture).
+mof_status prepare_small_solve(int ld);
 
 }  // namespace mof
