@@ -5,30 +5,40 @@
 // g = (A V)^T b of the current basis (R_A^T R_A = G_A and R_L^T R_L = G_L for
 // the R factors of eq. (QR)), the block
 //   1. factors M = G_A + rho G_L = R^T R (Cholesky, FP64), rho = tr G_A / tr G_L,
-//      and forms C = R^-T G_A R^-1 and h = R^-T g (FP64);
+//      and forms C = R^-T G_A R^-1 and h = R^-T g by two triangular solves;
 //   2. diagonalises C: cyclic Jacobi sweeps in FP32 give approximate
-//      eigenvectors W; two Newton-Schulz steps make them orthonormal in FP64
-//      (W <- W (3I - W^T W)/2), and cyclic Jacobi sweeps in FP64 on W^T C W,
-//      which start near diagonal and converge quadratically, finish the
-//      decomposition to FP64 accuracy; with the eigenvalues theta_i in [0, 1]
-//      and eigenvectors W, X = R^-1 W satisfies X^T G_A X = diag(theta),
+//      eigenvectors W; one third-order Newton-Schulz step makes them
+//      orthonormal in FP64 (W <- W (I - E/2 + 3E^2/8), E = W^T W - I), and
+//      cyclic Jacobi sweeps in FP64 on W^T C W, which start near diagonal,
+//      finish the decomposition to FP64 accuracy while rotating the one vector
+//      W^T h they need; with the eigenvalues theta_i in [0, 1] and the
+//      eigenvectors, X = R^-1 W satisfies X^T G_A X = diag(theta),
 //      X^T G_L X = diag(1 - theta)/rho (the generalized singular values of
-//      (R_A, R_L)); the FP64 sweeps rotate the one vector W^T h they need
-//      instead of accumulating W;
+//      (R_A, R_L));
 //   3. with ghat = X^T g, chat_i^2 = ghat_i^2 / theta_i and the filter factors
 //      f_i = theta_i / (theta_i + mu (1 - theta_i)), mu = lam / rho, has
 //      ||R_A z - Q_A^T b||^2 = sum chat_i^2 (1 - f_i)^2 and
 //      trace(I - S) = sum (1 - f_i), with closed-form derivatives in lam;
 //   4. picks lam on the bracket 10^[log10 rho - 12, log10 rho + 12]:
-//      DP: the root of ||A V z - b||^2 = (eta delta)^2 (monotone in lam) by
-//      safeguarded Newton steps in log10 lam; GCV: the minimum of a 200-point
-//      log grid (ties to the smaller lam), refined inside its two grid
-//      neighbours by safeguarded Newton steps on dG/dlog10(lam) = 0, kept only
-//      if it improves on the grid value;
+//      GCV: the minimum of a 200-point log grid (ties to the smaller lam),
+//      scanned in FP32 and decided in FP64 among the five points around the
+//      FP32 minimum, then refined between its two grid neighbours by
+//      safeguarded Newton steps on dG/dlog10(lam) = 0 (FP32 steps, then FP64
+//      steps), kept only if it improves on the grid value;
+//      DP: the root of ||A V z - b||^2 = (eta delta)^2 (monotone in lam); the
+//      bracket ends decide the no-root flags in FP64, an FP32 grid locates the
+//      sign change (its cell is confirmed in FP64), and safeguarded Newton
+//      steps in log10 lam (FP32, then FP64) converge to the root;
 //   5. returns z = R^-1 (C + mu (I - C))^-1 h, the solution of
 //      (G_A + lam G_L) z = g, by an FP64 Cholesky solve in the R basis.
-// Each Jacobi round updates every 2x2 block (pair i rows, pair j columns) of
-// the matrix from its old values in one pass, so a round costs two barriers.
+//
+// GB300 executes FP64 at about 2 fused multiply-adds per clock per SM, and a
+// warp's FP64 instruction costs the same with one lane active as with 32, so
+// the block does its FP64 arithmetic with full warps wherever the work is
+// parallel (triangular updates over all threads, symmetric products over the
+// upper triangle), keeps the serial parts (pivots, rotation angles,
+// substitutions, Newton steps) in one warp, and evaluates in FP32 what a
+// later FP64 step corrects (the Jacobi warm start, the lambda grids).
 #include "solver.cuh"
 
 #include <atomic>
@@ -39,78 +49,32 @@ namespace mof {
 namespace {
 
 constexpr int ST = 256;
+constexpr int NW = ST / 32;
 constexpr int GRID_POINTS = 200;
 constexpr int NEWTON_MAX = 60;
+constexpr int NEWTON32_MAX = 30;
+constexpr int NREF = 5;  // FP64 re-evaluated grid points around the FP32 minimum
 constexpr double BRACKET_DECADES = 12.0;
 constexpr double THETA_TINY = 1e-14;
 constexpr int JACOBI32_MAX_SWEEPS = 12;
 constexpr int JACOBI64_MAX_SWEEPS = 10;
 constexpr double LN10 = 2.302585092994045684;
 
-struct Spec {
-    int K;
-    double rho, rho0sq;
-    const double *theta, *c2;
-};
-
-// sums over i (lane-strided) of the lam-functions and their mu-derivatives:
-// s[0] = N = sum c2 g^2, s[1] = N', s[2] = N'', s[3] = D = sum g, s[4] = D', s[5] = D''
-// with g_i = mu a_i / d_i = 1 - f_i, a_i = 1 - theta_i, d_i = theta_i + mu a_i.
-__device__ __forceinline__ void lam_sums(const Spec &S, double mu, int i0, int step, double s[6]) {
-    for (int k = 0; k < 6; ++k) s[k] = 0.0;
-    for (int i = i0; i < S.K; i += step) {
-        const double th = S.theta[i], a = 1.0 - th, d = th + mu * a;
-        if (!(d > 0.0)) {
-            s[3] += 1.0;
-            continue;
-        }
-        const double inv = 1.0 / d;
-        const double g = mu * a * inv;
-        const double g1 = a * th * inv * inv;
-        const double g2 = -2.0 * a * g1 * inv;
-        const double c = S.c2[i];
-        s[0] += c * g * g;
-        s[1] += 2.0 * c * g * g1;
-        s[2] += 2.0 * c * (g1 * g1 + g * g2);
-        s[3] += g;
-        s[4] += g1;
-        s[5] += g2;
+// ------------------------------------------------------------ index helpers
+// The n(n+1)/2 pairs (r, c), r <= c < n, of an upper triangle enumerated as a
+// ceil(n/2) x (n+1) rectangle whose row q holds triangle rows q and n-1-q.
+__device__ __forceinline__ int tri_count(int n) { return ((n + 1) / 2) * (n + 1); }
+__device__ __forceinline__ bool tri_pair(int e, int n, int &r, int &c) {
+    const int q = e / (n + 1), x = e - q * (n + 1);
+    if (x < n - q) {
+        r = q;
+        c = q + x;
+        return true;
     }
-}
-
-// N = sum c2 g^2 and D = sum g only (the grid scan)
-__device__ __forceinline__ double gcv_plain(const Spec &S, double mu) {
-    double N = 0.0, D = 0.0;
-    for (int i = 0; i < S.K; ++i) {
-        const double th = S.theta[i], a = 1.0 - th, d = th + mu * a;
-        const double g = d > 0.0 ? mu * a / d : 1.0;
-        N += S.c2[i] * g * g;
-        D += g;
-    }
-    const double v = N / (D * D);
-    return v == v ? v : DBL_MAX;
-}
-
-__device__ __forceinline__ void warp_lam_sums(const Spec &S, double t, double s[6]) {
-    const double mu = exp10(t) / S.rho;
-    lam_sums(S, mu, threadIdx.x & 31, 32, s);
-#pragma unroll
-    for (int k = 0; k < 6; ++k) s[k] = warp_sum(s[k]);
-}
-
-__device__ __forceinline__ double gcv_of(const double s[6]) {
-    const double g = s[0] / (s[3] * s[3]);
-    return g == g ? g : DBL_MAX;
-}
-
-// first and second derivative of G = N / D^2 with respect to t = log10(lam)
-__device__ __forceinline__ void gcv_dt(const double s[6], double mu, double &d1, double &d2) {
-    const double N = s[0], N1 = s[1], N2 = s[2], D = s[3], D1 = s[4], D2 = s[5];
-    const double G1 = N1 / (D * D) - 2.0 * N * D1 / (D * D * D);
-    const double G2 =
-        N2 / (D * D) - 4.0 * N1 * D1 / (D * D * D) - 2.0 * N * D2 / (D * D * D) + 6.0 * N * D1 * D1 / (D * D * D * D);
-    d1 = G1 * mu * LN10;
-    d2 = (G2 * mu * mu + G1 * mu) * LN10 * LN10;
+    r = n - 1 - q;
+    if (r == q) return false;  // middle row of an odd n: already enumerated
+    c = r + (x - (n - q));
+    return true;
 }
 
 // round-robin tournament: player at position j in round r (positions 0..Kp-1)
@@ -120,96 +84,436 @@ __device__ __forceinline__ int rr_player(int j, int r, int Kp) {
     return j == 0 ? 0 : 1 + v;
 }
 
-// Rotation (c, s) that zeroes a_pq of the 2x2 block [[a_pp, a_pq], [a_pq, a_qq]]:
-// t = tan(phi) from the classical formula, c = 1/sqrt(1 + t^2), s = t c. For
-// the FP64 sweeps the angle itself is computed in FP32 and c, s in FP64 from
-// it: the rotation stays orthogonal to FP64 accuracy, and an angle accurate
-// to FP32 still shrinks a_pq by ~1e-7 per visit once the matrix is near
-// diagonal (the quadratic phase these sweeps run in).
-__device__ __forceinline__ void rot_angle(float app, float aqq, float apq, float &c, float &s) {
-    const float th = (aqq - app) / (2.0f * apq);
-    const float t = (th >= 0.0f ? 1.0f : -1.0f) / (fabsf(th) + sqrtf(th * th + 1.0f));
-    c = rsqrtf(t * t + 1.0f);
-    s = t * c;
+// ------------------------------------------------------------ reductions
+// Sums over the warp of two values, each returned to every lane; 5 FP64
+// additions per lane instead of 10.
+__device__ __forceinline__ void warp_sum2(double &a, double &b) {
+    const bool hi = (threadIdx.x & 16) != 0;
+    double y = (hi ? b : a) + __shfl_xor_sync(0xffffffffu, hi ? a : b, 16);
+    for (int o = 8; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+    a = __shfl_sync(0xffffffffu, y, 0);
+    b = __shfl_sync(0xffffffffu, y, 16);
 }
-__device__ __forceinline__ void rot_angle(double app, double aqq, double apq, double &c, double &s) {
-    const float th = (float)(aqq - app) / (2.0f * (float)apq);
-    const double t = (double)((th >= 0.0f ? 1.0f : -1.0f) / (fabsf(th) + sqrtf(th * th + 1.0f)));
-    c = rsqrt(fma(t, t, 1.0));
-    s = t * c;
+// Sums over the warp of six values with 8 FP64 additions per lane instead of
+// 30: each shuffle level halves the number of distinct partial sums a lane
+// carries; the totals end in lanes 0, 16, 8, 24, 4, 20 and are broadcast.
+__device__ __forceinline__ void warp_sum6(double s[6]) {
+    const int lane = threadIdx.x & 31;
+    const bool h = (lane & 16) != 0, g = (lane & 8) != 0, f = (lane & 4) != 0;
+    const double r0 = __shfl_xor_sync(0xffffffffu, h ? s[0] : s[1], 16);
+    const double r1 = __shfl_xor_sync(0xffffffffu, h ? s[2] : s[3], 16);
+    const double r2 = __shfl_xor_sync(0xffffffffu, h ? s[4] : s[5], 16);
+    const double a = (h ? s[1] : s[0]) + r0, b = (h ? s[3] : s[2]) + r1;
+    double c = (h ? s[5] : s[4]) + r2;
+    const double x = (g ? b : a) + __shfl_xor_sync(0xffffffffu, g ? a : b, 8);
+    c += __shfl_xor_sync(0xffffffffu, c, 8);
+    double y = (f ? c : x) + __shfl_xor_sync(0xffffffffu, f ? x : c, 4);
+    y += __shfl_xor_sync(0xffffffffu, y, 2);
+    y += __shfl_xor_sync(0xffffffffu, y, 1);
+    s[0] = __shfl_sync(0xffffffffu, y, 0);
+    s[1] = __shfl_sync(0xffffffffu, y, 16);
+    s[2] = __shfl_sync(0xffffffffu, y, 8);
+    s[3] = __shfl_sync(0xffffffffu, y, 24);
+    s[4] = __shfl_sync(0xffffffffu, y, 4);
+    s[5] = __shfl_sync(0xffffffffu, y, 20);
 }
 
-// Cyclic two-sided Jacobi sweeps on the symmetric Kp x Kp matrix A (padded
-// rows/columns beyond K are zero) with eigenvector accumulation W <- W J
-// (W may be null) and/or the rotations applied to one vector v <- J^T v (v may be null),
-// until a sweep applies no rotation (|a_pq| <= rel * sqrt(|a_pp a_qq|) or
-// |a_pq| <= rel_abs * max_i |a_ii|) or max_sweeps. Every warp computes the
-// round's rotations itself (pair index = lane) and takes the others' by
-// shuffle; a barrier separates the pivot reads from the block updates and
-// another ends the round. All threads must call.
-template <typename T>
-__device__ void jacobi(T *A, int lda, T *W, int ldw, T *v, int K, int Kp, int max_sweeps, T rel, T rel_abs, double *red) {
+// ------------------------------------------------------------ dense kernels
+// Upper Cholesky in place: on return row j of A holds R[j][j..K) with
+// A = R^T R (only the upper triangle of A is referenced) and
+// invd[j] = 1 / R[j][j]. One barrier per column: warp 0 factors the pivot
+// row, which it brought up to date itself in the previous column, while the
+// other warps finish the previous column's trailing update. A non-positive or
+// non-finite pivot sets *fail. All threads call; ends with a barrier.
+__device__ void chol_upper(double *A, int lds, int K, double *invd, int *fail) {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int half = Kp / 2;
-    double dm = 0.0;
-    for (int i = tid; i < K; i += ST) dm = fmax(dm, fabs((double)A[i * lda + i]));
-    for (int o = 16; o > 0; o >>= 1) dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
-    if (lane == 0) red[wid] = dm;
-    __syncthreads();
-    dm = 0.0;
-    for (int w = 0; w < ST / 32; ++w) dm = fmax(dm, red[w]);
-    __syncthreads();
-    const T floor_abs = rel_abs * (T)dm;
-    const T tiny = (T)(sizeof(T) == 8 ? 1e-300 : 1e-30);
-    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-        int any_in_sweep = 0;
-        for (int round = 0; round < Kp - 1; ++round) {
-            const int pl = rr_player(lane, round, Kp), ql = rr_player(Kp - 1 - lane, round, Kp);
-            T c = 1, s = 0;
-            if (lane < half && pl < K && ql < K) {
-                const T apq = A[pl * lda + ql], app = A[pl * lda + pl], aqq = A[ql * lda + ql];
-                if (fabs(apq) > rel * sqrt(fabs(app * aqq)) && fabs(apq) > floor_abs && fabs(apq) > tiny)
-                    rot_angle(app, aqq, apq, c, s);
+    for (int j = 0; j < K; ++j) {
+        if (wid == 0) {
+            const double d = A[j * lds + j];
+            const bool ok = d > 0.0 && isfinite(d);
+            const double rs = ok ? rsqrt(d) : 1.0;
+            for (int k = j + lane; k < K; k += 32) A[j * lds + k] = (k == j) ? d * rs : A[j * lds + k] * rs;
+            if (lane == 0) {
+                invd[j] = rs;
+                if (!ok) *fail = 1;
             }
-            if (!__any_sync(0xffffffffu, s != (T)0)) continue;  // identical decision in every warp
-            any_in_sweep = 1;
-            __syncthreads();  // every warp has read this round's pivots before any block is rewritten
-            for (int j = wid; j < half; j += ST / 32) {
-                const int pj = rr_player(j, round, Kp), qj = rr_player(Kp - 1 - j, round, Kp);
-                const T cj = __shfl_sync(0xffffffffu, c, j), sj = __shfl_sync(0xffffffffu, s, j);
-                if (lane < half) {
-                    const T a = A[pl * lda + pj], b = A[pl * lda + qj], cc = A[ql * lda + pj], d = A[ql * lda + qj];
-                    const T a1 = c * a - s * cc, b1 = c * b - s * d, c1 = s * a + c * cc, d1 = s * b + c * d;
-                    A[pl * lda + pj] = cj * a1 - sj * b1;
-                    A[pl * lda + qj] = sj * a1 + cj * b1;
-                    A[ql * lda + pj] = cj * c1 - sj * d1;
-                    A[ql * lda + qj] = sj * c1 + cj * d1;
+        }
+        __syncthreads();
+        if (wid == 0) {
+            const int k = j + 1;
+            if (k < K) {
+                const double ajk = A[j * lds + k];
+                for (int l = k + lane; l < K; l += 32) A[k * lds + l] -= ajk * A[j * lds + l];
+            }
+            __syncwarp();
+        } else {
+            const int n = K - j - 2;  // rows j+2 .. K-1
+            if (n > 0) {
+                const int cnt = tri_count(n);
+                for (int e = tid - 32; e < cnt; e += ST - 32) {
+                    int r, c;
+                    if (!tri_pair(e, n, r, c)) continue;
+                    const int k = j + 2 + r, l = j + 2 + c;
+                    A[k * lds + l] -= A[j * lds + k] * A[j * lds + l];
                 }
             }
-            if (W && lane < half && s != (T)0)
-                for (int r = wid; r < Kp; r += ST / 32) {  // W <- W J on the columns of pair `lane`
+        }
+    }
+    __syncthreads();
+}
+
+// Y <- R^-T Y for the K x nc block Y (row stride ldy): forward substitution
+// in column-oriented form with the division by R[i][i] deferred to the end,
+// so the update by row i needs U[i][k] = R[i][k] / R[i][i] (k > i) only. One
+// barrier per row; all threads call; ends with a barrier.
+__device__ void trsm_rt(const double *U, int ldu, const double *invd, double *Y, int ldy, int K, int nc) {
+    const int tid = threadIdx.x;
+    for (int i = 0; i + 1 < K; ++i) {
+        const int cnt = (K - 1 - i) * nc;
+        for (int e = tid; e < cnt; e += ST) {
+            const int k = i + 1 + e / nc, j = e - (e / nc) * nc;
+            Y[k * ldy + j] -= U[i * ldu + k] * Y[i * ldy + j];
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < K * nc; e += ST) {
+        const int i = e / nc, j = e - (e / nc) * nc;
+        Y[i * ldy + j] *= invd[i];
+    }
+    __syncthreads();
+}
+
+// Y <- Y R^-1 for the nr x K block Y: column-oriented solve of Z R = Y with
+// deferred scaling. One barrier per column; all threads call.
+__device__ void trsm_r(const double *U, int ldu, const double *invd, double *Y, int ldy, int nr, int K) {
+    const int tid = threadIdx.x;
+    for (int j = 0; j + 1 < K; ++j) {
+        const int w = K - 1 - j, cnt = nr * w;
+        for (int e = tid; e < cnt; e += ST) {
+            const int r = e / w, l = j + 1 + (e - (e / w) * w);
+            Y[r * ldy + l] -= Y[r * ldy + j] * U[j * ldu + l];
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < nr * K; e += ST) {
+        const int r = e / K, j = e - (e / K) * K;
+        Y[r * ldy + j] *= invd[j];
+    }
+    __syncthreads();
+}
+
+// O = op(A) op(B) for K x K operands (op = transpose when the flag is set).
+// With sym, only the upper triangle is computed and mirrored. Ends with a barrier.
+__device__ void gemm_kk(double *O, const double *A, bool tA, const double *B, bool tB, int K, int lds, bool sym) {
+    const int tid = threadIdx.x;
+    const int cnt = sym ? tri_count(K) : K * K;
+    for (int e = tid; e < cnt; e += ST) {
+        int i, j;
+        if (sym) {
+            if (!tri_pair(e, K, i, j)) continue;
+        } else {
+            i = e / K;
+            j = e - i * K;
+        }
+        double s = 0.0;
+        for (int k = 0; k < K; ++k) s += (tA ? A[k * lds + i] : A[i * lds + k]) * (tB ? B[j * lds + k] : B[k * lds + j]);
+        O[i * lds + j] = s;
+        if (sym) O[j * lds + i] = s;
+    }
+    __syncthreads();
+}
+
+// Triangular solve in one warp, column-oriented; lane k holds entries k and
+// k + 32 of the right-hand side (K <= 64). R is upper, given by its rows, and
+// invd = 1 / diag(R). forward = true solves R^T x = x, else R x = x.
+__device__ void warp_trsv(const double *R, int lds, const double *invd, double &x0, double &x1, int K, bool forward) {
+    const int lane = threadIdx.x & 31;
+    for (int s = 0; s < K; ++s) {
+        const int i = forward ? s : K - 1 - s;
+        const double own = (i >> 5) ? x1 : x0;
+        const double xi = __shfl_sync(0xffffffffu, own, i & 31) * invd[i];
+        if (lane == (i & 31)) {
+            if (i >> 5) x1 = xi;
+            else x0 = xi;
+        }
+        if (forward) {  // x_k -= R[i][k] x_i for k > i
+            if (lane > i && lane < K) x0 -= R[i * lds + lane] * xi;
+            if (lane + 32 > i && lane + 32 < K) x1 -= R[i * lds + lane + 32] * xi;
+        } else {  // x_k -= R[k][i] x_i for k < i
+            if (lane < i) x0 -= R[lane * lds + i] * xi;
+            if (lane + 32 < i) x1 -= R[(lane + 32) * lds + i] * xi;
+        }
+    }
+}
+
+// ------------------------------------------------------------ Jacobi
+// Rotation (c, s) that zeroes a_pq of [[a_pp, a_pq], [a_pq, a_qq]]: tan(phi)
+// by the classical formula in FP32, from the FP64 difference a_qq - a_pp.
+// For the FP64 sweeps the FP32 pair is renormalised in FP64 with the series
+// 1/sqrt(1 + d) = 1 - d/2 + 3d^2/8 (|d| < 1e-6), so the rotation is orthogonal
+// to FP64 accuracy; an angle accurate to FP32 still shrinks a_pq by ~1e-7 per
+// visit, which is what the FP64 sweeps (started near diagonal) need.
+__device__ __forceinline__ void rot_from(float th, float &c0, float &s0) {
+    const float t = (th >= 0.0f ? 1.0f : -1.0f) / (fabsf(th) + sqrtf(fmaf(th, th, 1.0f)));
+    c0 = rsqrtf(fmaf(t, t, 1.0f));
+    s0 = t * c0;
+}
+__device__ __forceinline__ void rot_angle(float app, float aqq, float apq, float &c, float &s) {
+    rot_from((aqq - app) / (2.0f * apq), c, s);
+}
+__device__ __forceinline__ void rot_angle(double app, double aqq, double apq, double &c, double &s) {
+    float c0, s0;
+    rot_from((float)(aqq - app) / (2.0f * (float)apq), c0, s0);
+    const double cd = c0, sd = s0;
+    const double dl = fma(cd, cd, sd * sd) - 1.0;
+    const double r = fma(dl, fma(0.375, dl, -0.5), 1.0);
+    c = cd * r;
+    s = sd * r;
+}
+
+template <typename T>
+struct JacobiShared {
+    T c[2][32], s[2][32];
+    int any[2];
+};
+
+// Cyclic two-sided Jacobi on the symmetric Kp x Kp matrix A (rows/columns
+// beyond K are zero padding) with eigenvector accumulation W <- W J (W may be
+// null) and the rotations applied to one vector v <- J^T v (v may be null).
+// Each round of the round-robin ordering rotates Kp/2 disjoint pairs: warp 0
+// decides and computes the rotations and rotates v, then all threads update
+// the 2x2 blocks (pair i rows, pair j columns) of the upper block triangle
+// from their old values and mirror them, and the rows of W. A pair rotates
+// while |a_pq| > rel sqrt(|a_pp a_qq|) and |a_pq| > rel_abs max_i |a_ii|; the
+// sweeps stop when a parallel scan after a sweep finds no such pair, or after
+// max_sweeps. The rotation buffers alternate between rounds, so a round costs
+// one barrier when it rotates nothing and two otherwise. All threads call.
+template <typename T>
+__device__ void jacobi(T *A, int lda, T *W, int ldw, T *v, int K, int Kp, int max_sweeps, float rel, float rel_abs,
+                       JacobiShared<T> &sh, float *redf) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int half = Kp / 2;
+    float dm = 0.0f;
+    for (int i = tid; i < K; i += ST) dm = fmaxf(dm, fabsf((float)A[i * lda + i]));
+    dm = warp_maxf(dm);
+    if (lane == 0) redf[wid] = dm;
+    __syncthreads();
+    dm = 0.0f;
+    for (int w = 0; w < NW; ++w) dm = fmaxf(dm, redf[w]);
+    const float floor_abs = rel_abs * dm;
+    int buf = 0;
+    const int nblk = tri_count(half);
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        for (int round = 0; round < Kp - 1; ++round, buf ^= 1) {
+            if (wid == 0) {
+                T c = 1, s = 0;
+                bool rot = false;
+                if (lane < half) {
+                    const int pl = rr_player(lane, round, Kp), ql = rr_player(Kp - 1 - lane, round, Kp);
+                    if (pl < K && ql < K) {
+                        const T apq = A[pl * lda + ql], app = A[pl * lda + pl], aqq = A[ql * lda + ql];
+                        const float fpq = fabsf((float)apq);
+                        rot = fpq > rel * sqrtf(fabsf((float)app * (float)aqq)) && fpq > floor_abs && fpq > 1e-35f;
+                        if (rot) rot_angle(app, aqq, apq, c, s);
+                        if (rot && v) {
+                            const T vp = v[pl], vq = v[ql];
+                            v[pl] = c * vp - s * vq;
+                            v[ql] = s * vp + c * vq;
+                        }
+                    }
+                    sh.c[buf][lane] = c;
+                    sh.s[buf][lane] = rot ? s : (T)0;
+                }
+                const int any = __any_sync(0xffffffffu, rot);
+                if (lane == 0) sh.any[buf] = any;
+            }
+            __syncthreads();
+            if (!sh.any[buf]) continue;
+            for (int e = tid; e < nblk; e += ST) {
+                int bi, bj;
+                if (!tri_pair(e, half, bi, bj)) continue;
+                const T ci = sh.c[buf][bi], si = sh.s[buf][bi], cj = sh.c[buf][bj], sj = sh.s[buf][bj];
+                if (si == (T)0 && sj == (T)0) continue;
+                const int pi = rr_player(bi, round, Kp), qi = rr_player(Kp - 1 - bi, round, Kp);
+                const int pj = rr_player(bj, round, Kp), qj = rr_player(Kp - 1 - bj, round, Kp);
+                const T a = A[pi * lda + pj], b = A[pi * lda + qj], cc = A[qi * lda + pj], d = A[qi * lda + qj];
+                const T a1 = ci * a - si * cc, b1 = ci * b - si * d, c1 = si * a + ci * cc, d1 = si * b + ci * d;
+                const T na = cj * a1 - sj * b1, nb = sj * a1 + cj * b1, nd = sj * c1 + cj * d1;
+                const T nc = (bi == bj) ? nb : cj * c1 - sj * d1;  // exact symmetry of a diagonal block
+                A[pi * lda + pj] = na;
+                A[pi * lda + qj] = nb;
+                A[qi * lda + pj] = nc;
+                A[qi * lda + qj] = nd;
+                if (bi != bj) {
+                    A[pj * lda + pi] = na;
+                    A[qj * lda + pi] = nb;
+                    A[pj * lda + qi] = nc;
+                    A[qj * lda + qi] = nd;
+                }
+            }
+            if (W) {
+                for (int e = tid; e < Kp * half; e += ST) {  // W <- W J on the columns of each pair
+                    const int r = e / half, j = e - (e / half) * half;
+                    const T s = sh.s[buf][j];
+                    if (s == (T)0) continue;
+                    const T c = sh.c[buf][j];
+                    const int pl = rr_player(j, round, Kp), ql = rr_player(Kp - 1 - j, round, Kp);
                     const T wp = W[r * ldw + pl], wq = W[r * ldw + ql];
                     W[r * ldw + pl] = c * wp - s * wq;
                     W[r * ldw + ql] = s * wp + c * wq;
                 }
-            if (v && wid == 0 && lane < half && s != (T)0) {  // v <- J^T v
-                const T vp = v[pl], vq = v[ql];
-                v[pl] = c * vp - s * vq;
-                v[ql] = s * vp + c * vq;
             }
             __syncthreads();
         }
-        if (!any_in_sweep) break;
+        // does any pair still exceed the rotation threshold?
+        int more = 0;
+        for (int e = tid; e < K * K; e += ST) {
+            const int p = e / K, q = e - (e / K) * K;
+            if (q <= p) continue;
+            const float fpq = fabsf((float)A[p * lda + q]);
+            if (fpq > rel * sqrtf(fabsf((float)A[p * lda + p] * (float)A[q * lda + q])) && fpq > floor_abs &&
+                fpq > 1e-35f)
+                more = 1;
+        }
+        if (!__syncthreads_or(more)) break;
     }
+}
+
+// ------------------------------------------------------------ lambda functions
+struct Spec {
+    int K;
+    double rho, rho0sq;
+    const double *theta, *c2;
+};
+// FP32 copies of theta, 1 - theta and c2 (scaled by 1 / sum c2) for the scans
+struct SpecF {
+    int K;
+    const float *th, *a, *c2;
+};
+
+// per-lane terms (lanes stride over i) of the lam-functions and their
+// mu-derivatives: s[0] = N = sum c2 g^2, s[1] = N', s[2] = N'', s[3] = D = sum g,
+// s[4] = D', s[5] = D'' with g_i = mu a_i / d_i = 1 - f_i, a_i = 1 - theta_i,
+// d_i = theta_i + mu a_i.
+template <typename R, typename SP>
+__device__ __forceinline__ void lam_terms6(const SP &S, R mu, R s[6]) {
+    for (int k = 0; k < 6; ++k) s[k] = R(0);
+    for (int i = threadIdx.x & 31; i < S.K; i += 32) {
+        R th, a, c;
+        if constexpr (sizeof(R) == 8) {
+            th = S.theta[i];
+            a = 1.0 - th;
+            c = S.c2[i];
+        } else {
+            th = S.th[i];
+            a = S.a[i];
+            c = S.c2[i];
+        }
+        const R d = th + mu * a;
+        if (!(d > R(0))) {
+            s[3] += R(1);
+            continue;
+        }
+        const R inv = R(1) / d;
+        const R g = mu * a * inv, g1 = a * th * inv * inv, g2 = R(-2) * a * g1 * inv;
+        s[0] += c * g * g;
+        s[1] += R(2) * c * g * g1;
+        s[2] += R(2) * c * (g1 * g1 + g * g2);
+        s[3] += g;
+        s[4] += g1;
+        s[5] += g2;
+    }
+}
+// N and N' only (DP)
+template <typename R, typename SP>
+__device__ __forceinline__ void lam_terms_n(const SP &S, R mu, R &N, R &N1) {
+    N = R(0);
+    N1 = R(0);
+    for (int i = threadIdx.x & 31; i < S.K; i += 32) {
+        R th, a, c;
+        if constexpr (sizeof(R) == 8) {
+            th = S.theta[i];
+            a = 1.0 - th;
+            c = S.c2[i];
+        } else {
+            th = S.th[i];
+            a = S.a[i];
+            c = S.c2[i];
+        }
+        const R d = th + mu * a;
+        if (!(d > R(0))) continue;
+        const R inv = R(1) / d;
+        const R g = mu * a * inv, g1 = a * th * inv * inv;
+        N += c * g * g;
+        N1 += R(2) * c * g * g1;
+    }
+}
+// N and D only (GCV values)
+__device__ __forceinline__ void lam_terms_nd(const Spec &S, double mu, double &N, double &D) {
+    N = 0.0;
+    D = 0.0;
+    for (int i = threadIdx.x & 31; i < S.K; i += 32) {
+        const double th = S.theta[i], a = 1.0 - th, d = th + mu * a;
+        const double g = d > 0.0 ? mu * a / d : 1.0;
+        N += S.c2[i] * g * g;
+        D += g;
+    }
+}
+__device__ __forceinline__ double gcv_value(double N, double D) {
+    const double g = N / (D * D);
+    return g == g ? g : DBL_MAX;
+}
+// one thread's FP32 grid value: GCV (N / D^2) or the DP function N - delta
+__device__ __forceinline__ void grid_nd(const SpecF &S, float mu, float &N, float &D) {
+    N = 0.0f;
+    D = 0.0f;
+    for (int i = 0; i < S.K; ++i) {
+        const float ai = S.a[i], d = fmaf(mu, ai, S.th[i]);
+        const float gg = d > 0.0f ? __fdividef(mu * ai, d) : 1.0f;
+        N = fmaf(S.c2[i] * gg, gg, N);
+        D += gg;
+    }
+}
+template <typename R>
+__device__ __forceinline__ R warp_sum_t(R v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// first and second derivative of G = N / D^2 with respect to t = log10(lam)
+template <typename R>
+__device__ __forceinline__ void gcv_dt(const R s[6], R mu, R &d1, R &d2) {
+    const R N = s[0], N1 = s[1], N2 = s[2], D = s[3], D1 = s[4], D2 = s[5];
+    const R iD = R(1) / D, iD2 = iD * iD;
+    const R G1 = N1 * iD2 - R(2) * N * D1 * iD2 * iD;
+    const R G2 = N2 * iD2 - R(4) * N1 * D1 * iD2 * iD - R(2) * N * D2 * iD2 * iD + R(6) * N * D1 * D1 * iD2 * iD2;
+    const R ln10 = R(LN10);
+    d1 = G1 * mu * ln10;
+    d2 = (G2 * mu * mu + G1 * mu) * ln10 * ln10;
+}
+
+// safeguarded Newton step for a root of an increasing function f (f1 = f')
+// inside [A, B], which the sign of f shrinks
+template <typename R>
+__device__ __forceinline__ R newton_step(R t, R f, R f1, R &A, R &B) {
+    if (f > R(0)) B = t;
+    else if (f < R(0)) A = t;
+    R tn = (f1 > R(0)) ? t - f / f1 : R(0.5) * (A + B);
+    if (!(tn > A && tn < B)) tn = R(0.5) * (A + B);
+    return tn;
 }
 
 }  // namespace
 
 __global__ void __launch_bounds__(ST) k_small_solve(SmallArgs a) {
     extern __shared__ double sm[];
-    __shared__ double s_rho, s_piv, s_rho0sq, s_t, s_vgrid;
-    __shared__ double s_red[ST / 32];
-    __shared__ int s_fail, s_flag, s_ig, s_idx[ST / 32];
+    __shared__ double s_rho, s_rho0sq, s_t, s_scale;
+    __shared__ double s_refv[NREF];
+    __shared__ int s_refi[NREF];
+    __shared__ float s_redf[NW], s_redv[NW];
+    __shared__ int s_fail, s_flag, s_idx[NW], s_end[4];
+    __shared__ JacobiShared<float> jf;
+    __shared__ JacobiShared<double> jd;
     const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int ld = a.ld;
     const int K = min(a.K[b], ld);
@@ -223,70 +527,51 @@ __global__ void __launch_bounds__(ST) k_small_solve(SmallArgs a) {
         return;
     }
     const int Kp = K + (K & 1);
-    const int lds = ld + 2;       // FP64 leading dimension (>= Kp)
-    const int ldf = ld + 3;       // FP32 leading dimension
-    double *M = sm;               // Cholesky factor R (upper), later X^T C X
-    double *Ri = M + lds * lds;   // R^-1
-    double *C = Ri + lds * lds;   // G_A, then C = R^-T G_A R^-1
-    double *T = C + lds * lds;    // scratch: G_A R^-1, Newton-Schulz products, C X
-    double *X = T + lds * lds;    // eigenvector estimate
-    double *E = X + lds * lds;    // G_L, then scratch
-    double *vec = E + lds * lds;  // vectors, lds each
-    double *theta = vec, *gh = vec + lds, *c2 = vec + 2 * lds, *h = vec + 3 * lds, *y = vec + 4 * lds;
-    float *Af = reinterpret_cast<float *>(T);  // FP32 Jacobi matrices alias T and E (free then)
-    float *Wf = reinterpret_cast<float *>(E);
+    const int lds = (ld + 1) | 1;  // FP64 leading dimension: odd, >= Kp and >= K + 1
+    const int ldf = ld + 3;        // FP32 leading dimension
+    double *Rm = sm;               // Cholesky rows of M = G_A + rho G_L (kept for z)
+    double *Cm = Rm + lds * lds;   // [G_A | g] -> [R^-T G_A | h] -> C = R^-T G_A R^-1 (kept for z)
+    double *Um = Cm + lds * lds;   // R rows over their diagonal; then X^T C X; then C + mu (I - C)
+    double *Xm = Um + lds * lds;   // eigenvector estimate
+    double *Tm = Xm + lds * lds;   // scratch (FP32 Jacobi matrix first)
+    double *Em = Tm + lds * lds;   // scratch (FP32 eigenvectors first)
+    double *vec = Em + lds * lds;
+    double *theta = vec, *gh = vec + lds, *c2 = vec + 2 * lds, *invd = vec + 3 * lds, *hv = vec + 4 * lds;
+    float *fvec = reinterpret_cast<float *>(vec + 5 * lds);  // 3 x lds floats within 2 x lds doubles
+    float *thf = fvec, *af = fvec + lds, *c2f = fvec + 2 * lds;
+    float *Af = reinterpret_cast<float *>(Tm);
+    float *Wf = reinterpret_cast<float *>(Em);
     const double *GA = a.GA + (long long)b * ld * ld;
     const double *GL = a.GL + (long long)b * ld * ld;
     const double *g = a.g + (long long)b * ld;
 #define AT(P, i, j) P[(i) * lds + (j)]
 #define AF(P, i, j) P[(i) * ldf + (j)]
 
-    // ---------------------------------------------- 1. Cholesky, C, h (FP64)
-    for (int e = tid; e < K * K; e += ST) {
-        const int i = e / K, j = e - (e / K) * K;
-        AT(C, i, j) = GA[i * ld + j];
-        AT(E, i, j) = GL[i * ld + j];
-    }
-    for (int i = tid; i < K; i += ST) y[i] = g[i];
-    __syncthreads();
-    if (tid < 32) {
+    // ---------------------------------------------- 1. Cholesky of M, C and h (FP64)
+    if (wid == 0) {
         double tA = 0.0, tL = 0.0;
         for (int i = lane; i < K; i += 32) {
-            tA += AT(C, i, i);
-            tL += AT(E, i, i);
+            tA += GA[i * ld + i];
+            tL += GL[i * ld + i];
         }
-        tA = warp_sum(tA);
-        tL = warp_sum(tL);
+        warp_sum2(tA, tL);
         if (lane == 0) {
             s_rho = (tA > 0.0 && tL > 0.0) ? tA / tL : 1.0;
             s_fail = 0;
+            s_flag = 0;
         }
     }
     __syncthreads();
     const double rho = s_rho;
     for (int e = tid; e < K * K; e += ST) {
         const int i = e / K, j = e - (e / K) * K;
-        AT(M, i, j) = AT(C, i, j) + rho * AT(E, i, j);
+        const double ga = GA[i * ld + j];
+        AT(Cm, i, j) = ga;
+        AT(Rm, i, j) = ga + rho * GL[i * ld + j];
     }
+    for (int i = tid; i < K; i += ST) AT(Cm, i, K) = g[i];
     __syncthreads();
-    for (int j = 0; j < K; ++j) {
-        if (tid == 0) {
-            const double d = AT(M, j, j);
-            if (!(d > 0.0) || !isfinite(d)) s_fail = 1;
-            s_piv = d > 0.0 ? sqrt(d) : 1.0;
-            AT(M, j, j) = s_piv;
-        }
-        __syncthreads();
-        const double inv = 1.0 / s_piv;
-        for (int k = j + 1 + tid; k < K; k += ST) AT(M, j, k) *= inv;
-        __syncthreads();
-        const int rem = K - j - 1;
-        for (int e = tid; e < rem * rem; e += ST) {
-            const int k = j + 1 + e / rem, l = j + 1 + e % rem;
-            if (l >= k) AT(M, k, l) -= AT(M, j, k) * AT(M, j, l);
-        }
-        __syncthreads();
-    }
+    chol_upper(Rm, lds, K, invd, &s_fail);
     if (s_fail) {
         if (tid == 0) {
             atomicOr(a.err, 1);
@@ -295,287 +580,302 @@ __global__ void __launch_bounds__(ST) k_small_solve(SmallArgs a) {
         }
         return;
     }
-    for (int c = tid; c < K; c += ST) {
-        for (int i = 0; i < K; ++i) AT(Ri, i, c) = 0.0;
-        AT(Ri, c, c) = 1.0 / AT(M, c, c);
-        for (int i = c - 1; i >= 0; --i) {
-            double s = 0.0;
-            for (int k = i + 1; k <= c; ++k) s += AT(M, i, k) * AT(Ri, k, c);
-            AT(Ri, i, c) = -s / AT(M, i, i);
-        }
-    }
-    __syncthreads();
-    for (int e = tid; e < K * K; e += ST) {  // T = G_A R^-1
-        const int i = e / K, j = e - (e / K) * K;
-        double s = 0.0;
-        for (int k = 0; k <= j; ++k) s += AT(C, i, k) * AT(Ri, k, j);
-        AT(T, i, j) = s;
-    }
-    for (int i = tid; i < K; i += ST) {  // h = R^-T g
-        double s = 0.0;
-        for (int k = 0; k <= i; ++k) s += AT(Ri, k, i) * y[k];
-        h[i] = s;
-    }
-    __syncthreads();
-    for (int e = tid; e < K * K; e += ST) {  // C = R^-T T (upper triangle, mirrored)
-        const int i = e / K, j = e - (e / K) * K;
-        if (i > j) continue;
-        double s = 0.0;
-        for (int k = 0; k <= i; ++k) s += AT(Ri, k, i) * AT(T, k, j);
-        AT(C, i, j) = s;
-        AT(C, j, i) = s;
-    }
-    __syncthreads();
-
-    // ---------------------------------------------- 2a. FP32 Jacobi on C
-    for (int e = tid; e < Kp * Kp; e += ST) {
-        const int i = e / Kp, j = e - (e / Kp) * Kp;
-        AF(Af, i, j) = (i < K && j < K) ? (float)AT(C, i, j) : 0.0f;
-        AF(Wf, i, j) = i == j ? 1.0f : 0.0f;
-    }
-    __syncthreads();
-    jacobi<float>(Af, ldf, Wf, ldf, (float *)nullptr, K, Kp, JACOBI32_MAX_SWEEPS, 1e-6f, 1e-7f, s_red);
-
-    // ---------------------------------------------- 2b. FP64: orthonormalise, then Jacobi
     for (int e = tid; e < K * K; e += ST) {
+        const int i = e / K, k = e - (e / K) * K;
+        if (k > i) AT(Um, i, k) = AT(Rm, i, k) * invd[i];
+    }
+    __syncthreads();
+    trsm_rt(Um, lds, invd, Cm, lds, K, K + 1);  // [G_A | g] <- R^-T [G_A | g]
+    for (int i = tid; i < K; i += ST) hv[i] = AT(Cm, i, K);
+    trsm_r(Um, lds, invd, Cm, lds, K, K);  // C = (R^-T G_A) R^-1
+    for (int e = tid; e < K * K; e += ST) {  // exact symmetry
         const int i = e / K, j = e - (e / K) * K;
-        AT(X, i, j) = (double)AF(Wf, i, j);
-    }
-    __syncthreads();
-    for (int step = 0; step < 2; ++step) {  // Newton-Schulz: X <- X (3I - X^T X) / 2
-        for (int e = tid; e < K * K; e += ST) {
-            const int i = e / K, j = e - (e / K) * K;
-            if (i > j) continue;
-            double s = 0.0;
-            for (int k = 0; k < K; ++k) s += AT(X, k, i) * AT(X, k, j);
-            AT(E, i, j) = s;
-            AT(E, j, i) = s;
+        if (j > i) {
+            const double s = 0.5 * (AT(Cm, i, j) + AT(Cm, j, i));
+            AT(Cm, i, j) = s;
+            AT(Cm, j, i) = s;
         }
-        __syncthreads();
-        for (int e = tid; e < K * K; e += ST) {
-            const int i = e / K, j = e - (e / K) * K;
-            double s = 0.0;
-            for (int k = 0; k < K; ++k) s += AT(X, i, k) * ((k == j ? 3.0 : 0.0) - AT(E, k, j));
-            AT(T, i, j) = 0.5 * s;
-        }
-        __syncthreads();
-        for (int e = tid; e < K * K; e += ST) {
-            const int i = e / K, j = e - (e / K) * K;
-            AT(X, i, j) = AT(T, i, j);
-        }
-        __syncthreads();
-    }
-    for (int e = tid; e < K * K; e += ST) {  // T = C X
-        const int i = e / K, j = e - (e / K) * K;
-        double s = 0.0;
-        for (int k = 0; k < K; ++k) s += AT(C, i, k) * AT(X, k, j);
-        AT(T, i, j) = s;
-    }
-    __syncthreads();
-    for (int e = tid; e < Kp * Kp; e += ST) {  // M = X^T C X (padded row/column zero, X padded by I)
-        const int i = e / Kp, j = e - (e / Kp) * Kp;
-        if (i > j) continue;
-        double s = 0.0;
-        if (j < K)
-            for (int k = 0; k < K; ++k) s += AT(X, k, i) * AT(T, k, j);
-        AT(M, i, j) = s;
-        AT(M, j, i) = s;
-        if (j == K) {
-            AT(X, i, j) = (i == j) ? 1.0 : 0.0;
-            AT(X, j, i) = (i == j) ? 1.0 : 0.0;
-        }
-    }
-    __syncthreads();
-    for (int i = tid; i < Kp; i += ST) {  // gh = X^T h, then rotated along with M
-        double s = 0.0;
-        if (i < K)
-            for (int k = 0; k < K; ++k) s += AT(X, k, i) * h[k];
-        gh[i] = s;
-    }
-    __syncthreads();
-    jacobi<double>(M, lds, (double *)nullptr, lds, gh, K, Kp, JACOBI64_MAX_SWEEPS, 1e-16, 1e-18, s_red);
-    for (int i = tid; i < K; i += ST) {
-        theta[i] = fmin(fmax(AT(M, i, i), 0.0), 1.0);
-        c2[i] = theta[i] > THETA_TINY ? gh[i] * gh[i] / theta[i] : 0.0;
     }
     __syncthreads();
 
-    // ---------------------------------------------- 3-4. lambda
-    if (tid < 32) {
-        double kept = 0.0;
-        for (int i = lane; i < K; i += 32) kept += c2[i];
-        kept = warp_sum(kept);
-        if (lane == 0) {
-            s_rho0sq = a.bb[b] - kept;
-            s_flag = 0;
+    double lam = a.lam_fixed;
+    if (a.rule != MOF_RULE_FIXED) {
+        // ------------------------------------------ 2a. FP32 Jacobi on C
+        for (int e = tid; e < Kp * Kp; e += ST) {
+            const int i = e / Kp, j = e - (e / Kp) * Kp;
+            AF(Af, i, j) = (i < K && j < K) ? (float)AT(Cm, i, j) : 0.0f;
+            AF(Wf, i, j) = i == j ? 1.0f : 0.0f;
         }
-    }
-    __syncthreads();
-    const Spec S{K, rho, s_rho0sq, theta, c2};
-    const double lo = log10(rho) - BRACKET_DECADES, hi = log10(rho) + BRACKET_DECADES;
-    if (a.rule == MOF_RULE_GCV) {
+        __syncthreads();
+        jacobi<float>(Af, ldf, Wf, ldf, (float *)nullptr, K, Kp, JACOBI32_MAX_SWEEPS, 1e-6f, 1e-7f, jf, s_redf);
+
+        // ------------------------------------------ 2b. FP64: orthonormalise, congruence
+        for (int e = tid; e < K * K; e += ST) {
+            const int i = e / K, j = e - (e / K) * K;
+            AT(Xm, i, j) = (double)AF(Wf, i, j);
+        }
+        __syncthreads();
+        gemm_kk(Tm, Xm, true, Xm, false, K, lds, true);  // X0^T X0 (the FP32 matrix is done with)
+        for (int i = tid; i < K; i += ST) AT(Tm, i, i) -= 1.0;  // E = X0^T X0 - I
+        __syncthreads();
+        gemm_kk(Em, Tm, false, Tm, false, K, lds, true);  // E^2 (the FP32 eigenvectors are in Xm)
+        for (int e = tid; e < K * K; e += ST) {           // P = I - E/2 + 3 E^2/8
+            const int i = e / K, j = e - (e / K) * K;
+            AT(Em, i, j) = (i == j ? 1.0 : 0.0) - 0.5 * AT(Tm, i, j) + 0.375 * AT(Em, i, j);
+        }
+        __syncthreads();
+        gemm_kk(Tm, Xm, false, Em, false, K, lds, false);  // X = X0 P
+        for (int e = tid; e < K * K; e += ST) {
+            const int i = e / K, j = e - (e / K) * K;
+            AT(Xm, i, j) = AT(Tm, i, j);
+        }
+        __syncthreads();
+        gemm_kk(Tm, Cm, false, Xm, false, K, lds, false);  // T = C X
+        gemm_kk(Um, Xm, true, Tm, false, K, lds, true);    // X^T C X
+        for (int i = tid; i < Kp; i += ST) {               // gh = X^T h; zero padding of an odd size
+            double s = 0.0;
+            if (i < K)
+                for (int k = 0; k < K; ++k) s += AT(Xm, k, i) * hv[k];
+            gh[i] = s;
+            if (K & 1) {
+                AT(Um, i, K) = 0.0;
+                AT(Um, K, i) = 0.0;
+            }
+        }
+        __syncthreads();
+
+        // ------------------------------------------ 2c. FP64 Jacobi polish
+        jacobi<double>(Um, lds, (double *)nullptr, lds, gh, K, Kp, JACOBI64_MAX_SWEEPS, 1e-16f, 1e-18f, jd, s_redf);
+        for (int i = tid; i < K; i += ST) {
+            theta[i] = fmin(fmax(AT(Um, i, i), 0.0), 1.0);
+            c2[i] = theta[i] > THETA_TINY ? gh[i] * gh[i] / theta[i] : 0.0;
+        }
+        __syncthreads();
+
+        // ------------------------------------------ 3-4. lambda
+        if (wid == 0) {
+            double kept = 0.0, unused = 0.0;
+            for (int i = lane; i < K; i += 32) kept += c2[i];
+            warp_sum2(kept, unused);
+            if (lane == 0) {
+                s_rho0sq = a.bb[b] - kept;
+                s_scale = kept > 0.0 ? 1.0 / kept : 1.0;
+            }
+        }
+        __syncthreads();
+        for (int i = tid; i < K; i += ST) {
+            thf[i] = (float)theta[i];
+            af[i] = (float)(1.0 - theta[i]);
+            c2f[i] = (float)(c2[i] * s_scale);
+        }
+        __syncthreads();
+        const Spec S{K, rho, s_rho0sq, theta, c2};
+        const SpecF SF{K, thf, af, c2f};
+        const double lrho = log10(rho);
+        const double lo = lrho - BRACKET_DECADES, hi = lrho + BRACKET_DECADES;
         const double step = (hi - lo) / (GRID_POINTS - 1);
-        double vb = DBL_MAX;
-        int ib = tid;
-        if (tid < GRID_POINTS) vb = gcv_plain(S, exp10(lo + tid * step) / rho);
-        for (int o = 16; o > 0; o >>= 1) {  // argmin, ties to the smaller index
-            const double vo = __shfl_xor_sync(0xffffffffu, vb, o);
-            const int io = __shfl_xor_sync(0xffffffffu, ib, o);
-            if (vo < vb || (vo == vb && io < ib)) {
-                vb = vo;
-                ib = io;
+        if (a.rule == MOF_RULE_GCV) {
+            // FP32 scan of the grid, argmin with ties to the smaller index
+            float vb = FLT_MAX;
+            int ib = tid;
+            if (tid < GRID_POINTS) {
+                float N, D;
+                grid_nd(SF, exp10f((float)(-BRACKET_DECADES + tid * step)), N, D);
+                vb = __fdividef(N, D * D);
+                if (!(vb == vb)) vb = FLT_MAX;
             }
-        }
-        if (lane == 0) {
-            s_red[wid] = vb;
-            s_idx[wid] = ib;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            double bv = s_red[0];
-            int bi = s_idx[0];
-            for (int w = 1; w < ST / 32; ++w) {
-                if (s_red[w] < bv || (s_red[w] == bv && s_idx[w] < bi)) {
-                    bv = s_red[w];
-                    bi = s_idx[w];
-                }
-            }
-            s_vgrid = bv;
-            s_ig = bi;
-        }
-        __syncthreads();
-        if (wid == 0) {
-            // safeguarded Newton on dG/dt inside [t_{i-1}, t_{i+1}]
-            const int ig = s_ig;
-            double A0 = lo + max(ig - 1, 0) * step, B0 = lo + min(ig + 1, GRID_POINTS - 1) * step;
-            double t = lo + ig * step, s[6], d1, d2;
-            for (int it = 0; it < NEWTON_MAX; ++it) {
-                warp_lam_sums(S, t, s);
-                gcv_dt(s, exp10(t) / rho, d1, d2);
-                if (d1 > 0.0) B0 = t;
-                else if (d1 < 0.0) A0 = t;
-                else break;
-                double tn = (d2 > 0.0) ? t - d1 / d2 : 0.5 * (A0 + B0);
-                if (!(tn > A0 && tn < B0)) tn = 0.5 * (A0 + B0);
-                const double dt = fabs(tn - t);
-                t = tn;
-                if (dt <= 1e-10 * fmax(1.0, fabs(t)) || B0 - A0 <= 1e-10 * fmax(1.0, fabs(t))) break;
-            }
-            warp_lam_sums(S, t, s);
-            if (gcv_of(s) > s_vgrid) t = lo + ig * step;
-            if (lane == 0) s_t = t;
-        }
-        __syncthreads();
-    } else if (a.rule == MOF_RULE_DP) {
-        if (wid == 0) {
-            double s[6], t;
-            warp_lam_sums(S, lo, s);
-            const double flo = s[0] + S.rho0sq - a.target2;
-            warp_lam_sums(S, hi, s);
-            const double fhi = s[0] + S.rho0sq - a.target2;
-            int flag = 0;
-            if (flo >= 0.0) {
-                flag = 1;
-                t = lo;
-            } else if (fhi <= 0.0) {
-                flag = 2;
-                t = hi;
-            } else {
-                // safeguarded Newton on F(t) = N(mu(t)) + rho0^2 - target^2 (increasing in t)
-                double A0 = lo, B0 = hi;
-                t = 0.5 * (lo + hi);
-                for (int it = 0; it < NEWTON_MAX; ++it) {
-                    warp_lam_sums(S, t, s);
-                    const double mu = exp10(t) / rho;
-                    const double F = s[0] + S.rho0sq - a.target2;
-                    const double F1 = s[1] * mu * LN10;
-                    if (F > 0.0) B0 = t;
-                    else A0 = t;
-                    double tn = F1 > 0.0 ? t - F / F1 : 0.5 * (A0 + B0);
-                    if (!(tn > A0 && tn < B0)) tn = 0.5 * (A0 + B0);
-                    const double dt = fabs(tn - t);
-                    t = tn;
-                    if (dt <= 1e-15 * fmax(1.0, fabs(t)) || B0 - A0 <= 1e-15 * fmax(1.0, fabs(t))) break;
+            for (int o = 16; o > 0; o >>= 1) {
+                const float vo = __shfl_xor_sync(0xffffffffu, vb, o);
+                const int io = __shfl_xor_sync(0xffffffffu, ib, o);
+                if (vo < vb || (vo == vb && io < ib)) {
+                    vb = vo;
+                    ib = io;
                 }
             }
             if (lane == 0) {
-                s_t = t;
-                s_flag = flag;
+                s_redv[wid] = vb;
+                s_idx[wid] = ib;
             }
+            __syncthreads();
+            int i32 = s_idx[0];
+            {
+                float bv = s_redv[0];
+                for (int w = 1; w < NW; ++w)
+                    if (s_redv[w] < bv || (s_redv[w] == bv && s_idx[w] < i32)) {
+                        bv = s_redv[w];
+                        i32 = s_idx[w];
+                    }
+            }
+            // FP64 values of the grid points around the FP32 minimum decide it
+            if (wid < NREF) {
+                const int idx = min(max(i32 - NREF / 2 + wid, 0), GRID_POINTS - 1);
+                double N, D;
+                lam_terms_nd(S, exp10(lo + idx * step) / rho, N, D);
+                warp_sum2(N, D);
+                if (lane == 0) {
+                    s_refv[wid] = gcv_value(N, D);
+                    s_refi[wid] = idx;
+                }
+            }
+            __syncthreads();
+            if (wid == 0) {
+                double bv = s_refv[0];
+                int ig = s_refi[0];
+                for (int w = 1; w < NREF; ++w)
+                    if (s_refv[w] < bv || (s_refv[w] == bv && s_refi[w] < ig)) {
+                        bv = s_refv[w];
+                        ig = s_refi[w];
+                    }
+                // safeguarded Newton on dG/dt = 0 inside [t_{i-1}, t_{i+1}]: FP32 steps
+                // (in t - log10 rho) to a starting point, then FP64 steps on the full cell pair
+                const double A0 = lo + max(ig - 1, 0) * step, B0 = lo + min(ig + 1, GRID_POINTS - 1) * step;
+                float tf = (float)(ig * step - BRACKET_DECADES);
+                float Af0 = (float)(A0 - lrho), Bf0 = (float)(B0 - lrho);
+                for (int it = 0; it < NEWTON32_MAX; ++it) {
+                    float s[6], d1, d2;
+                    const float mu = exp10f(tf);
+                    lam_terms6<float>(SF, mu, s);
+                    for (int k = 0; k < 6; ++k) s[k] = warp_sum_t(s[k]);
+                    gcv_dt<float>(s, mu, d1, d2);
+                    if (d1 == 0.0f || !(d1 == d1)) break;
+                    const float tn = newton_step<float>(tf, d1, d2, Af0, Bf0);
+                    const float dt = fabsf(tn - tf);
+                    tf = tn;
+                    if (dt <= 1e-6f || Bf0 - Af0 <= 1e-6f) break;
+                }
+                double t = lrho + (double)tf, A1 = A0, B1 = B0;
+                if (!(t > A1 && t < B1)) t = lo + ig * step;
+                for (int it = 0; it < NEWTON_MAX; ++it) {
+                    double s6[6], d1, d2;
+                    const double mu = exp10(t) / rho;
+                    lam_terms6<double>(S, mu, s6);
+                    warp_sum6(s6);
+                    gcv_dt<double>(s6, mu, d1, d2);
+                    if (d1 == 0.0) break;
+                    const double tn = newton_step<double>(t, d1, d2, A1, B1);
+                    const double dt = fabs(tn - t);
+                    t = tn;
+                    if (dt <= 1e-10 * fmax(1.0, fabs(t)) || B1 - A1 <= 1e-10 * fmax(1.0, fabs(t))) break;
+                }
+                double N, D;
+                lam_terms_nd(S, exp10(t) / rho, N, D);
+                warp_sum2(N, D);
+                if (gcv_value(N, D) > bv) t = lo + ig * step;
+                if (lane == 0) s_t = t;
+            }
+            __syncthreads();
+        } else {  // DP on F(t) = N(mu(t)) + rho0^2 - (eta delta)^2, increasing in t
+            if (wid < 2) {  // the bracket ends, in FP64
+                double N, N1;
+                lam_terms_n<double>(S, exp10(wid ? hi : lo) / rho, N, N1);
+                warp_sum2(N, N1);
+                const double F = N + S.rho0sq - a.target2;
+                if (lane == 0) s_end[wid] = wid ? (F <= 0.0) : (F >= 0.0);
+            }
+            __syncthreads();
+            const int flag = s_end[0] ? 1 : (s_end[1] ? 2 : 0);
+            if (flag == 0) {
+                const float delta = (float)((a.target2 - S.rho0sq) * s_scale);
+                // FP32 grid: the first point with F >= 0
+                int first = GRID_POINTS;
+                if (tid < GRID_POINTS) {
+                    float N, D;
+                    grid_nd(SF, exp10f((float)(-BRACKET_DECADES + tid * step)), N, D);
+                    if (N - delta >= 0.0f) first = tid;
+                }
+                for (int o = 16; o > 0; o >>= 1) first = min(first, __shfl_xor_sync(0xffffffffu, first, o));
+                if (lane == 0) s_idx[wid] = first;
+                __syncthreads();
+                int k = GRID_POINTS;
+                for (int w = 0; w < NW; ++w) k = min(k, s_idx[w]);
+                // the sign change within (t_{k-2}, t_{k+1}), confirmed in FP64
+                const double A1 = lo + max(k - 2, 0) * step, B1 = lo + min(k + 1, GRID_POINTS - 1) * step;
+                if (wid < 2) {
+                    double N, N1;
+                    lam_terms_n<double>(S, exp10(wid ? B1 : A1) / rho, N, N1);
+                    warp_sum2(N, N1);
+                    const double F = N + S.rho0sq - a.target2;
+                    if (lane == 0) s_end[2 + wid] = wid ? (F > 0.0) : (F < 0.0);
+                }
+                __syncthreads();
+                if (wid == 0) {
+                    const bool cell = s_end[2] && s_end[3];
+                    double A0 = cell ? A1 : lo, B0 = cell ? B1 : hi;
+                    float tf = (float)(0.5 * (A0 + B0) - lrho), Af0 = (float)(A0 - lrho), Bf0 = (float)(B0 - lrho);
+                    for (int it = 0; it < NEWTON32_MAX; ++it) {
+                        float N, N1;
+                        const float mu = exp10f(tf);
+                        lam_terms_n<float>(SF, mu, N, N1);
+                        N = warp_sum_t(N);
+                        N1 = warp_sum_t(N1);
+                        const float tn = newton_step<float>(tf, N - delta, N1 * mu * (float)LN10, Af0, Bf0);
+                        const float dt = fabsf(tn - tf);
+                        tf = tn;
+                        if (dt <= 1e-6f || Bf0 - Af0 <= 1e-6f) break;
+                    }
+                    double t = lrho + (double)tf;
+                    if (!(t > A0 && t < B0)) t = 0.5 * (A0 + B0);
+                    for (int it = 0; it < NEWTON_MAX; ++it) {
+                        const double mu = exp10(t) / rho;
+                        double N, N1;
+                        lam_terms_n<double>(S, mu, N, N1);
+                        warp_sum2(N, N1);
+                        const double tn = newton_step<double>(t, N + S.rho0sq - a.target2, N1 * mu * LN10, A0, B0);
+                        const double dt = fabs(tn - t);
+                        t = tn;
+                        if (dt <= 1e-15 * fmax(1.0, fabs(t)) || B0 - A0 <= 1e-15 * fmax(1.0, fabs(t))) break;
+                    }
+                    if (lane == 0) s_t = t;
+                }
+            } else if (tid == 0) {
+                s_t = flag == 1 ? lo : hi;
+            }
+            if (tid == 0) s_flag = flag;
+            __syncthreads();
         }
-        __syncthreads();
-    } else {
-        if (tid == 0) s_t = 0.0;
-        __syncthreads();
+        lam = exp10(s_t);
     }
-    const double lam = a.rule == MOF_RULE_FIXED ? a.lam_fixed : exp10(s_t);
     const double mu = lam / rho;
 
     // ---------------------------------------------- 5. z = R^-1 (C + mu (I - C))^-1 h
     // (G_A + lam G_L = R^T (C + mu (I - C)) R and g = R^T h)
     for (int e = tid; e < K * K; e += ST) {
         const int i = e / K, j = e - (e / K) * K;
-        AT(M, i, j) = (1.0 - mu) * AT(C, i, j) + (i == j ? mu : 0.0);
-    }
-    for (int i = tid; i < K; i += ST) y[i] = h[i];
-    __syncthreads();
-    for (int j = 0; j < K; ++j) {  // Cholesky, upper, in M
-        if (tid == 0) {
-            const double d = AT(M, j, j);
-            if (!(d > 0.0) || !isfinite(d)) s_fail = 1;
-            s_piv = d > 0.0 ? sqrt(d) : 1.0;
-            AT(M, j, j) = s_piv;
-        }
-        __syncthreads();
-        const double inv = 1.0 / s_piv;
-        for (int k = j + 1 + tid; k < K; k += ST) AT(M, j, k) *= inv;
-        __syncthreads();
-        const int rem = K - j - 1;
-        for (int e = tid; e < rem * rem; e += ST) {
-            const int k = j + 1 + e / rem, l = j + 1 + e % rem;
-            if (l >= k) AT(M, k, l) -= AT(M, j, k) * AT(M, j, l);
-        }
-        __syncthreads();
-    }
-    if (wid == 0) {  // forward (R^T w = h) and backward (R y = w) substitution, one warp
-        for (int i = 0; i < K; ++i) {
-            double s = 0.0;
-            for (int k = lane; k < i; k += 32) s += AT(M, k, i) * y[k];
-            s = warp_sum(s);
-            if (lane == 0) y[i] = (y[i] - s) / AT(M, i, i);
-            __syncwarp();
-        }
-        for (int i = K - 1; i >= 0; --i) {
-            double s = 0.0;
-            for (int k = i + 1 + lane; k < K; k += 32) s += AT(M, i, k) * y[k];
-            s = warp_sum(s);
-            if (lane == 0) y[i] = (y[i] - s) / AT(M, i, i);
-            __syncwarp();
-        }
+        if (j >= i) AT(Um, i, j) = (1.0 - mu) * AT(Cm, i, j) + (i == j ? mu : 0.0);
     }
     __syncthreads();
-    for (int i = tid; i < K; i += ST) {
-        double s = 0.0;
-        for (int k = i; k < K; ++k) s += AT(Ri, i, k) * y[k];
-        z[i] = s;
-        if (!isfinite(s) || s_fail) atomicOr(a.err, 2);
-    }
-    if (tid == 0) {
-        a.lam[b] = lam;
-        a.flag[b] = s_flag;
+    double *invs = gh;  // 1 / diagonal of the Cholesky factor of C + mu (I - C)
+    chol_upper(Um, lds, K, invs, &s_fail);
+    if (wid == 0) {
+        double x0 = lane < K ? hv[lane] : 0.0, x1 = lane + 32 < K ? hv[lane + 32] : 0.0;
+        warp_trsv(Um, lds, invs, x0, x1, K, true);   // Rs^T w = h
+        warp_trsv(Um, lds, invs, x0, x1, K, false);  // Rs y = w
+        warp_trsv(Rm, lds, invd, x0, x1, K, false);  // R z = y
+        const bool bad = (lane < K && !isfinite(x0)) || (lane + 32 < K && !isfinite(x1));
+        if (lane < K) z[lane] = x0;
+        if (lane + 32 < K) z[lane + 32] = x1;
+        if (__any_sync(0xffffffffu, bad) || s_fail) {
+            if (lane == 0) atomicOr(a.err, 2);
+        }
+        if (lane == 0) {
+            a.lam[b] = lam;
+            a.flag[b] = s_flag;
+        }
     }
 #undef AT
 #undef AF
 }
 
 static size_t small_smem(int ld) {
-    const size_t lds = (size_t)ld + 2;
-    return sizeof(double) * (6 * lds * lds + 5 * lds);
+    const size_t lds = (size_t)((ld + 1) | 1);
+    return sizeof(double) * (6 * lds * lds + 7 * lds);
 }
 
 mof_status prepare_small_solve(int ld) {
-    // the limit only ever grows: smaller problems launched later still fit
-    static std::atomic<size_t> configured{48 * 1024};
+    // the limit only ever grows: smaller problems launched later still fit (set
+    // from the first call on: static and dynamic shared memory together exceed
+    // the default 48 KB before the dynamic part alone does)
+    static std::atomic<size_t> configured{0};
     const size_t smem = small_smem(ld);
     size_t cur = configured.load();
     while (smem > cur) {
