@@ -59,6 +59,7 @@ _SIGS = {
     "mof_apply_gradT": (ctypes.c_int, [ctypes.c_void_p] * 4),
     "mof_apply_flow": (ctypes.c_int, [ctypes.c_void_p] * 6),
     "mof_apply_flowT": (ctypes.c_int, [ctypes.c_void_p] * 6),
+    "mof_apply_flowT_noalloc": (ctypes.c_int, [ctypes.c_void_p] * 6),
     "mof_of_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 4),
     "mof_apply_flow_lin": (ctypes.c_int, [ctypes.c_void_p] * 7),
     "mof_apply_flow_linT": (ctypes.c_int, [ctypes.c_void_p] * 6),
@@ -211,6 +212,12 @@ def mof_apply_flowT(p, r, sv, sr, u, stream=None):
     s = _sizes(p)
     _check(_lib.mof_apply_flowT(p.handle, _ptr(p, r, s["flow"], "r"), _ptr(p, sv, s["nv"], "s"),
                                 _ptr(p, sr, s["nv"], "sr"), _ptr(p, u, s["n"], "u"), _stream(stream)))
+
+
+def mof_apply_flowT_noalloc(p, r, sv, sr, u, stream=None):
+    s = _sizes(p)
+    _check(_lib.mof_apply_flowT_noalloc(p.handle, _ptr(p, r, s["flow"], "r"), _ptr(p, sv, s["nv"], "s"),
+                                        _ptr(p, sr, s["nv"], "sr"), _ptr(p, u, s["n"], "u"), _stream(stream)))
 
 
 def mof_of_fields(p, u, dr, ux, uy, ut, stream=None):

@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstring>
 #include <atomic>
+#include <mutex>
 #include <new>
 
 namespace mof {
@@ -240,6 +241,52 @@ mof_status mof_apply_flowT(mof_problem *p, const void *r, const void *s, const v
     void *rad = nullptr;
     MOF_TRY(apply_scratch(p, SCR_RADIUS, &rad));
     int *rs = (int *)rad, *rr = rs + (long long)(p->nt - 1) * tiles_count(p);
+    if (p->precision == MOF_FP64) {
+        MOF_TRY(launch_tile_radii<double>(p, CD(s), CD(sr), rs, rr, S(stream)));
+        return launch_flowT<double>(p, CD(r), CD(s), CD(sr), rs, rr, D(u), S(stream));
+    }
+    MOF_TRY(launch_tile_radii<float>(p, CF(s), CF(sr), rs, rr, S(stream)));
+    return launch_flowT<float>(p, CF(r), CF(s), CF(sr), rs, rr, F(u), S(stream));
+}
+
+// Allocation-free Mhat^T: the tile radii live in a fixed device array
+// instead of the problem's lazily allocated workspace (include/mof.h states
+// the size limit, the one-time set-up and the concurrency rule).
+static __device__ __align__(256) int g_flowT_noalloc_radii[MOF_FLOWT_NOALLOC_MAX_RADII];
+
+static mof_status flowT_noalloc_scratch(const mof_problem *p, int **out) {
+    constexpr int MAX_DEVICES = 64;
+    static std::mutex mu;
+    static int *addr[MAX_DEVICES] = {};
+    if (p->device < 0 || p->device >= MAX_DEVICES)
+        return fail(MOF_EUNSUPPORTED, "device ordinal %d is outside the supported range", p->device);
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[p->device]) {  // one-time set-up on this device
+        int cur = -1;
+        MOF_CUDA(cudaGetDevice(&cur));
+        if (cur != p->device)
+            return fail(MOF_EINVAL, "first call on device %d made with device %d current", p->device, cur);
+        void *a = nullptr;
+        MOF_CUDA(cudaGetSymbolAddress(&a, g_flowT_noalloc_radii));
+        addr[p->device] = static_cast<int *>(a);
+    }
+    *out = addr[p->device];
+    return MOF_OK;
+}
+
+mof_status mof_apply_flowT_noalloc(mof_problem *p, const void *r, const void *s, const void *sr, void *u, void *stream) {
+    g_err[0] = 0;
+    MOF_TRY(check_problem(p));
+    if (!u || !s || !sr || !r) return fail(MOF_EINVAL, "null array");
+    const long long need = 2LL * (p->nt - 1) * tiles_count(p);
+    if (need > MOF_FLOWT_NOALLOC_MAX_RADII)
+        return fail(MOF_EUNSUPPORTED,
+                    "mof_apply_flowT_noalloc: the problem needs %lld tile radii, more than the fixed %d "
+                    "(use mof_apply_flowT)",
+                    need, MOF_FLOWT_NOALLOC_MAX_RADII);
+    int *rad = nullptr;
+    MOF_TRY(flowT_noalloc_scratch(p, &rad));
+    int *rs = rad, *rr = rad + (long long)(p->nt - 1) * tiles_count(p);
     if (p->precision == MOF_FP64) {
         MOF_TRY(launch_tile_radii<double>(p, CD(s), CD(sr), rs, rr, S(stream)));
         return launch_flowT<double>(p, CD(r), CD(s), CD(sr), rs, rr, D(u), S(stream));
