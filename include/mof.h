@@ -83,6 +83,10 @@ typedef struct {
     double noise_norm;     /* delta = ||e||, required by MOF_RULE_DP */
     double lam_fixed;      /* lambda for MOF_RULE_FIXED */
     double breakdown_tol;  /* <= 0: 1e-10 (FP64) / 1e-6 (FP32) relative breakdown threshold */
+    int of_streams;        /* execution only: the GKS iterations of Solve-OF run the frame pairs in
+                              this many groups on separate streams, so that one group's small
+                              FP64 solves overlap another group's bandwidth-bound kernels; the
+                              result does not depend on it. 0 = automatic; at most 16 */
 } mof_solver_params;
 
 /* One record per outer iteration k of mof_solve (host struct). */

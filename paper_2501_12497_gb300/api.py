@@ -36,7 +36,7 @@ class mof_solver_params(ctypes.Structure):
     _fields_ = [("ell", ctypes.c_int), ("tau", ctypes.c_int), ("of_iters", ctypes.c_int),
                 ("of_ell", ctypes.c_int), ("of_dr", ctypes.c_int), ("image_rule", ctypes.c_int),
                 ("eps", ctypes.c_double), ("eta", ctypes.c_double), ("noise_norm", ctypes.c_double),
-                ("lam_fixed", ctypes.c_double), ("breakdown_tol", ctypes.c_double)]
+                ("lam_fixed", ctypes.c_double), ("breakdown_tol", ctypes.c_double), ("of_streams", ctypes.c_int)]
 
 
 class mof_report(ctypes.Structure):

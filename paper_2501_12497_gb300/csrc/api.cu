@@ -116,6 +116,7 @@ void mof_default_params(mof_solver_params *p) {
     p->noise_norm = -1.0;
     p->lam_fixed = 0.0;
     p->breakdown_tol = 0.0;
+    p->of_streams = 0;
 }
 
 mof_status mof_problem_create(const mof_geometry *g, int precision, mof_problem **out) {

@@ -11,6 +11,9 @@
 #include "common.cuh"
 #include "solver.cuh"
 
+#include <atomic>
+#include <type_traits>
+
 namespace mof {
 
 constexpr int KT = 256;                    // threads per block
@@ -110,18 +113,23 @@ __global__ void __launch_bounds__(KT) k_mdot(const real *__restrict__ V, long lo
 }
 
 // out_v[b*bstride + i*istride + col*jstride] = sign * sum_chunk partial[b][chunk][v][i], i < K[b];
-// col = K[b] - 1 when last_col, else 0.
-__global__ void k_sum_chunks(const double *__restrict__ partial, int nchunk, int NV, int Kmax, const int *__restrict__ K,
-                             const int *__restrict__ act, DotOuts outs) {
-    const int b = blockIdx.x;
+// col = K[b] - 1 when last_col, else 0. One warp per output (lanes stride
+// over the chunks, then a fixed tree), blockIdx.y = problem.
+constexpr int SUMT = 256;
+__global__ void __launch_bounds__(SUMT) k_sum_chunks(const double *__restrict__ partial, int nchunk, int NV, int Kmax,
+                                                     const int *__restrict__ K, const int *__restrict__ act, DotOuts outs) {
+    const int b = blockIdx.y;
     if (act && !act[b]) return;
     const int Kb = min(K[b], Kmax);
-    for (int e = threadIdx.x; e < NV * Kb; e += blockDim.x) {
-        const int v = e / Kb, i = e % Kb;
-        const DotOut &o = outs.o[v];
-        if (!o.out) continue;
-        double s = 0.0;
-        for (int c = 0; c < nchunk; ++c) s += partial[(((long long)b * nchunk + c) * NV + v) * Kmax + i];
+    const int e = blockIdx.x * (SUMT / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (e >= NV * Kb) return;
+    const int v = e / Kb, i = e - (e / Kb) * Kb;
+    const DotOut &o = outs.o[v];
+    if (!o.out) return;
+    double s = 0.0;
+    for (int c = lane; c < nchunk; c += 32) s += partial[(((long long)b * nchunk + c) * NV + v) * Kmax + i];
+    s = warp_sum(s);
+    if (lane == 0) {
         const long long col = o.last_col ? (long long)(Kb - 1) : 0;
         o.out[b * o.bstride + (long long)i * o.istride + col * o.jstride] = o.sign * s;
     }
@@ -194,6 +202,135 @@ __global__ void __launch_bounds__(CT) k_combine(const real *__restrict__ V, long
     }
 }
 
+// ------------------------------------------------------------ fused CGS2 middle pass
+// x'[b] = x[b] - V[b] c[b] and the chunk partials of V[b]^T x'[b] in one pass
+// over V: a CTA owns one 1 KB chunk of every basis vector of its problem and
+// of x, brought into shared memory by 1D bulk copies (TMA) that complete on
+// an mbarrier; it forms x' for the chunk, writes it, and takes the dots from
+// the same staged tile. Classical Gram-Schmidt twice then reads V three times
+// instead of four. Products in the storage precision, summed per chunk in a
+// fixed order (deterministic), chunks combined in FP64 by k_sum_chunks.
+constexpr int SDT = 64;        // threads per CTA
+constexpr int SD_BYTES = 1024; // bytes of one vector's chunk (small tiles: many CTAs per SM keep copies in flight)
+template <typename real>
+constexpr int sdch() { return SD_BYTES / (int)sizeof(real); }
+constexpr long long MBAR_MAX_POLLS = 1LL << 22;
+
+long long subdot_chunks(long long N, int elem_bytes) { return (N * elem_bytes + SD_BYTES - 1) / SD_BYTES; }
+long long krylov_partial_doubles(long long N, int Kmax) {
+    // multi-dot (<= 3 right-hand sides), norms and combines; fused pass, whose fixed-size
+    // chunks hold the fewest elements (so are the most numerous) for FP64
+    const long long a = krylov_chunks(N) * 3 * Kmax, b = subdot_chunks(N, 8) * Kmax;
+    return a > b ? a : b;
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+// poll the mbarrier phase with a bound; false when the bound ran out
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned phase) {
+    for (long long it = 0; it < MBAR_MAX_POLLS; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(phase)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+template <typename real>
+__global__ void __launch_bounds__(SDT) k_sub_dot(const real *__restrict__ V, long long N, int Kmax, const int *__restrict__ K,
+                                                 const int *__restrict__ act, const double *__restrict__ c, long long cstride,
+                                                 const real *x, long long xstride, real *out, long long ostride,
+                                                 double *__restrict__ partial, int nchunk, int *__restrict__ err) {
+    constexpr int CH = sdch<real>();
+    constexpr int EPT = CH / SDT;  // elements per thread: 4 (FP32) or 2 (FP64), 16 bytes
+    using vec_t = typename std::conditional<sizeof(real) == 4, float4, double2>::type;
+    extern __shared__ __align__(128) unsigned char sd_smem[];
+    real *sx = reinterpret_cast<real *>(sd_smem);  // [CH]
+    real *sV = sx + CH;                            // [Kmax][CH]
+    __shared__ real sc[64];
+    __shared__ __align__(8) unsigned long long bar;
+    const int b = blockIdx.y, chunk = blockIdx.x, tid = threadIdx.x;
+    if (act && !act[b]) return;
+    const int Kb = min(K[b], Kmax);
+    const long long c0 = (long long)chunk * CH;
+    const int len = (int)min((long long)CH, N - c0);
+    const unsigned bar_a = smem_u32(&bar);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int j = tid; j < Kb; j += SDT) sc[j] = (real)c[b * cstride + j];
+    __syncthreads();
+    if (tid == 0) {
+        const unsigned bytes = (unsigned)len * (unsigned)sizeof(real);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a), "r"(bytes * (unsigned)(Kb + 1))
+                     : "memory");
+        bulk_g2s(sx, x + b * xstride + c0, bytes, bar_a);
+        const real *Vb = V + (long long)b * Kmax * N + c0;
+        for (int j = 0; j < Kb; ++j) bulk_g2s(sV + (long long)j * CH, Vb + (long long)j * N, bytes, bar_a);
+    }
+    if (!mbar_wait(bar_a, 0)) {
+        if (tid == 0 && err) atomicOr(err, 4);
+        mbar_wait(bar_a, 0);  // do not leave while copies may still land
+        return;
+    }
+    // x' = x - V c on this thread's EPT consecutive elements
+    const int i0 = tid * EPT;
+    real acc[EPT];
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) acc[e] = 0;
+    for (int j = 0; j < Kb; ++j) {
+        const vec_t q = *reinterpret_cast<const vec_t *>(sV + (long long)j * CH + i0);
+        const real cj = sc[j];
+        const real *qq = reinterpret_cast<const real *>(&q);
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) acc[e] += qq[e] * cj;
+    }
+    {
+        vec_t xv = *reinterpret_cast<const vec_t *>(sx + i0);
+        real *xx = reinterpret_cast<real *>(&xv);
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) xx[e] = (i0 + e < len) ? xx[e] - acc[e] : (real)0;
+        *reinterpret_cast<vec_t *>(sx + i0) = xv;
+        real *ob = out + b * ostride + c0;
+        if (i0 + EPT <= len) {
+            *reinterpret_cast<vec_t *>(ob + i0) = xv;
+        } else {
+#pragma unroll
+            for (int e = 0; e < EPT; ++e)
+                if (i0 + e < len) ob[i0 + e] = xx[e];
+        }
+    }
+    __syncthreads();
+    // partial dots V_j^T x' of the chunk: warp w takes j = w, w + 4, ...
+    const int w = tid >> 5, l = tid & 31;
+    for (int j = w; j < Kb; j += SDT / 32) {
+        real a = 0;
+#pragma unroll
+        for (int q = 0; q < CH / (32 * EPT); ++q) {
+            const int i = (q * 32 + l) * EPT;
+            const vec_t v = *reinterpret_cast<const vec_t *>(sV + (long long)j * CH + i);
+            const vec_t y = *reinterpret_cast<const vec_t *>(sx + i);
+            const real *vv = reinterpret_cast<const real *>(&v);
+            const real *yy = reinterpret_cast<const real *>(&y);
+#pragma unroll
+            for (int e = 0; e < EPT; ++e)
+                if (i + e < len) a += vv[e] * yy[e];
+        }
+        if constexpr (sizeof(real) == 4) a = warp_sumf(a);
+        else a = warp_sum(a);
+        if (l == 0) partial[((long long)b * nchunk + chunk) * Kmax + j] = (double)a;
+    }
+}
+
 // ||x[b]||^2 per chunk
 template <typename real>
 __global__ void __launch_bounds__(KT) k_norm2(const real *__restrict__ x, long long N, long long xstride,
@@ -214,12 +351,14 @@ __global__ void __launch_bounds__(KT) k_norm2(const real *__restrict__ x, long l
     if (threadIdx.x == 0) partial[(long long)b * nchunk + chunk] = s;
 }
 
+// out[b] = sum_chunk partial[b][chunk], one warp per problem
 __global__ void k_sum_scalar_chunks(const double *__restrict__ partial, int nchunk, double *__restrict__ out, int B) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blockIdx.x, lane = threadIdx.x;
     if (b >= B) return;
     double s = 0.0;
-    for (int c = 0; c < nchunk; ++c) s += partial[(long long)b * nchunk + c];
-    out[b] = s;
+    for (int c = lane; c < nchunk; c += 32) s += partial[(long long)b * nchunk + c];
+    s = warp_sum(s);
+    if (lane == 0) out[b] = s;
 }
 
 // Append x[b] / ||x[b]|| as vector K[b] when ||x[b]|| > tol * scale[b] and the
@@ -231,32 +370,39 @@ __device__ __forceinline__ bool append_ok(int grow, int Kb, int Kmax, double nrm
     return grow && Kb < Kmax && (nr > tol * sc) && (nr > 0.0) && isfinite(nr);
 }
 
+// The per-problem decision and scale of an append, once per problem (FP64):
+// slot[b] = K[b] and inv[b] = 1/||x[b]|| when the vector is appended (then
+// K[b] += 1), slot[b] = -1 and grow[b] = 0 otherwise; appended[b] (may be
+// null) records which. k_append's threads then do no FP64 arithmetic.
 template <typename real>
-__global__ void __launch_bounds__(KT) k_append(real *__restrict__ V, long long N, int Kmax, const int *__restrict__ K,
-                                               const real *__restrict__ x, long long xstride, const double *__restrict__ nrm2,
-                                               const double *__restrict__ scale, double tol, const int *__restrict__ grow,
+__global__ void k_append_prep(int *__restrict__ K, int Kmax, const double *__restrict__ nrm2, const double *__restrict__ scale,
+                              double tol, int *__restrict__ grow, int B, int *__restrict__ slot, real *__restrict__ inv,
+                              int *__restrict__ appended) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const int Kb = K[b];
+    const bool ok = append_ok(grow[b], Kb, Kmax, nrm2[b], scale, b, tol);
+    slot[b] = ok ? Kb : -1;
+    inv[b] = ok ? (real)(1.0 / sqrt(nrm2[b])) : (real)0;
+    if (ok) K[b] = Kb + 1;
+    else grow[b] = 0;
+    if (appended) appended[b] = ok;
+}
+
+template <typename real>
+__global__ void __launch_bounds__(KT) k_append(real *__restrict__ V, long long N, int Kmax, const int *__restrict__ slot,
+                                               const real *__restrict__ inv, const real *__restrict__ x, long long xstride,
                                                real *__restrict__ stage) {
     const int b = blockIdx.y;
-    const int Kb = K[b];
-    if (!append_ok(grow[b], Kb, Kmax, nrm2[b], scale, b, tol)) return;
-    const real inv = (real)(1.0 / sqrt(nrm2[b]));
-    real *vd = V + ((long long)b * Kmax + Kb) * N;
+    const int sl = slot[b];
+    if (sl < 0) return;
+    const real iv = inv[b];
+    real *vd = V + ((long long)b * Kmax + sl) * N;
     for (long long i = blockIdx.x * (long long)KT + threadIdx.x; i < N; i += (long long)gridDim.x * KT) {
-        const real v = x[b * xstride + i] * inv;
+        const real v = x[b * xstride + i] * iv;
         vd[i] = v;
         if (stage) stage[b * N + i] = v;
     }
-}
-
-// Commit the append: K[b] += 1 where k_append wrote, else clear grow[b].
-__global__ void k_commit(int *__restrict__ K, int Kmax, const double *__restrict__ nrm2, const double *__restrict__ scale,
-                         double tol, int *__restrict__ grow, int B, int *__restrict__ appended) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= B) return;
-    const int ok = append_ok(grow[b], K[b], Kmax, nrm2[b], scale, b, tol);
-    if (ok) K[b] += 1;
-    else grow[b] = 0;
-    if (appended) appended[b] = ok;
 }
 
 // ------------------------------------------------------------ host launchers
@@ -293,7 +439,7 @@ void Krylov<real>::multidot(const BasisRef<real> &B, int nv, const DotVecs<real>
         MDOT(3)
     }
 #undef MDOT
-    ::mof::count_launch(), k_sum_chunks<<<B.B, 128, 0, st>>>(partial, nc, nv, B.Kmax, B.K, B.act, outs);
+    ::mof::count_launch(), k_sum_chunks<<<dim3((nv * B.Kmax + SUMT / 32 - 1) / (SUMT / 32), B.B), SUMT, 0, st>>>(partial, nc, nv, B.Kmax, B.K, B.act, outs);
 }
 
 template <typename real>
@@ -321,7 +467,7 @@ void Krylov<real>::combine_minus(const BasisRef<real> &B, const double *c, long 
     else
         ::mof::count_launch(), k_combine<real, 2, false><<<dim3(nb, B.B), CT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, c, cstride, x,
                                                                                     xstride, out, ostride, np, nb);
-    if (nrm2_out) ::mof::count_launch(), k_sum_scalar_chunks<<<(B.B + 63) / 64, 64, 0, st>>>(partial, nb, nrm2_out, B.B);
+    if (nrm2_out) ::mof::count_launch(), k_sum_scalar_chunks<<<B.B, 32, 0, st>>>(partial, nb, nrm2_out, B.B);
 }
 
 template <typename real>
@@ -336,14 +482,38 @@ void Krylov<real>::subtract(const BasisRef<real> &B, const double *c, long long 
     else
         ::mof::count_launch(), k_combine<real, 1, false><<<dim3(nb, B.B), CT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, c, cstride, x,
                                                                                     xstride, out, ostride, np, nb);
-    if (nrm2_out) ::mof::count_launch(), k_sum_scalar_chunks<<<(B.B + 63) / 64, 64, 0, st>>>(partial, nb, nrm2_out, B.B);
+    if (nrm2_out) ::mof::count_launch(), k_sum_scalar_chunks<<<B.B, 32, 0, st>>>(partial, nb, nrm2_out, B.B);
 }
 
 template <typename real>
 void Krylov<real>::norm2(const real *x, long long N, long long xstride, int nb, double *out, cudaStream_t st) const {
     const int nc = (int)krylov_chunks(N);
     ::mof::count_launch(), k_norm2<real><<<dim3(nc, nb), KT, 0, st>>>(x, N, xstride, partial, nc);
-    ::mof::count_launch(), k_sum_scalar_chunks<<<(nb + 63) / 64, 64, 0, st>>>(partial, nc, out, nb);
+    ::mof::count_launch(), k_sum_scalar_chunks<<<nb, 32, 0, st>>>(partial, nc, out, nb);
+}
+
+template <typename real>
+bool Krylov<real>::sub_dot(const BasisRef<real> &B, const double *c, long long cstride, real *x, long long xstride,
+                           double *out, cudaStream_t st) const {
+    const long long es = sizeof(real);
+    const bool ok = B.Kmax <= 64 && (B.N * es) % 16 == 0 && (xstride * es) % 16 == 0 &&
+                    (reinterpret_cast<uintptr_t>(B.V) % 16) == 0 && (reinterpret_cast<uintptr_t>(x) % 16) == 0;
+    if (!ok) return false;
+    static std::atomic<bool> configured{false};
+    if (!configured.load()) {  // the largest tile this instantiation can need (65 chunks)
+        if (cudaFuncSetAttribute(k_sub_dot<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65 * SD_BYTES) != cudaSuccess)
+            return false;
+        configured.store(true);
+    }
+    const int nc = (int)subdot_chunks(B.N, (int)es);
+    const size_t smem = (size_t)(B.Kmax + 1) * SD_BYTES;
+    ::mof::count_launch(), k_sub_dot<real><<<dim3(nc, B.B), SDT, smem, st>>>(B.V, B.N, B.Kmax, B.K, B.act, c, cstride, x, xstride,
+                                                                         x, xstride, partial, nc, err);
+    DotOuts o{};
+    o.o[0] = DotOut{out, B.Kmax, 1, 0, 0, 1.0};
+    ::mof::count_launch(), k_sum_chunks<<<dim3((B.Kmax + SUMT / 32 - 1) / (SUMT / 32), B.B), SUMT, 0, st>>>(partial, nc, 1, B.Kmax,
+                                                                                                          B.K, B.act, o);
+    return true;
 }
 
 template <typename real>
@@ -351,17 +521,22 @@ void Krylov<real>::reorth(const BasisRef<real> &B, real *x, long long xstride, d
                           cudaStream_t st) const {
     // classical Gram-Schmidt against V, twice (CGS2); coef is [B][Kmax] scratch
     dots(B, x, xstride, coef, B.Kmax, 1.0, st);
-    subtract(B, coef, B.Kmax, x, xstride, x, xstride, nullptr, st);
-    dots(B, x, xstride, coef, B.Kmax, 1.0, st);
+    if (!sub_dot(B, coef, B.Kmax, x, xstride, coef, st)) {
+        subtract(B, coef, B.Kmax, x, xstride, x, xstride, nullptr, st);
+        dots(B, x, xstride, coef, B.Kmax, 1.0, st);
+    }
     subtract(B, coef, B.Kmax, x, xstride, x, xstride, nrm2_out, st);
 }
 
 template <typename real>
 void Krylov<real>::append(const BasisRef<real> &B, int *Kmut, const real *x, long long xstride, const double *nrm2,
                           const double *scale, double tol, int *grow, int *appended, real *stage, cudaStream_t st) const {
+    int *slot = reinterpret_cast<int *>(aux);
+    real *inv = reinterpret_cast<real *>(aux + B.B);
+    ::mof::count_launch(), k_append_prep<real><<<(B.B + 63) / 64, 64, 0, st>>>(Kmut, B.Kmax, nrm2, scale, tol, grow, B.B, slot, inv,
+                                                                              appended);
     const int blocks = (int)std::min<long long>(1024, (B.N + KT - 1) / KT);
-    ::mof::count_launch(), k_append<real><<<dim3(blocks, B.B), KT, 0, st>>>(B.V, B.N, B.Kmax, B.K, x, xstride, nrm2, scale, tol, grow, stage);
-    ::mof::count_launch(), k_commit<<<(B.B + 63) / 64, 64, 0, st>>>(Kmut, B.Kmax, nrm2, scale, tol, grow, B.B, appended);
+    ::mof::count_launch(), k_append<real><<<dim3(blocks, B.B), KT, 0, st>>>(B.V, B.N, B.Kmax, slot, inv, x, xstride, stage);
 }
 
 template struct Krylov<float>;

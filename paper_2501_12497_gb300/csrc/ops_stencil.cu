@@ -433,6 +433,9 @@ __global__ void k_regn_apply(const real *__restrict__ x, const real *__restrict_
                              const double *__restrict__ lam, const real *__restrict__ y_add, real *__restrict__ y, int nx,
                              int ny, int np) {
     const int xx = blockIdx.x * TX + threadIdx.x, yy = blockIdx.y * TY + threadIdx.y, t = blockIdx.z;
+    __shared__ real s_sc;  // scale * lam once per block (FP64 kept out of the threads)
+    if (threadIdx.x == 0 && threadIdx.y == 0) s_sc = (real)(lam ? scale * *lam : scale);
+    __syncthreads();
     if (xx >= nx || yy >= ny) return;
     const long long ns = (long long)nx * ny, i = (long long)yy * nx + xx;
     const real *f = x + t * ns, *k = uk + t * ns;
@@ -451,8 +454,7 @@ __global__ void k_regn_apply(const real *__restrict__ x, const real *__restrict_
     if (yy > 0) v += wdy(i - nx);
     if (yy < ny - 1) v -= wdy(i);
     if (np > 0) v += flowT_at(q, s, sr, nx, ny, np, t, xx, yy, rad_s, rad_sr, tiles, blockIdx.y * gridDim.x + blockIdx.x);
-    const double sc = lam ? scale * *lam : scale;
-    const real out = (real)sc * v;
+    const real out = s_sc * v;
     y[t * ns + i] = y_add ? y_add[t * ns + i] + out : out;
 }
 

@@ -117,6 +117,9 @@ struct Arena {
     }
 };
 
+constexpr int MAX_OF_STREAMS = 16;
+constexpr int AUTO_OF_STREAMS = 4;
+
 template <typename real>
 struct WS {
     int Kmax = 0, Kof = 0, of_ell = 0, ell = 0, max_outer = 0;
@@ -134,6 +137,7 @@ struct WS {
         *beta1_of, *bb_of;
     int *Kv_of, *Ku_of, *grow_of, *gkb_of, *act_of, *app_of, *flag_of;
     double *partial;
+    double *kaux;  // Krylov append scratch, 2 per problem
     int *iter;  // device index of the outer iteration (report slot)
     int gram_ctas = 0;
     // one captured graph per outer-iteration variant: bit 0 Solve-OF, bit 1 expansion,
@@ -149,6 +153,9 @@ struct WS {
     int gkey_n = -1;
     cudaStream_t ss = nullptr;  // internal stream (graphs cannot be captured on the legacy stream)
     cudaEvent_t join = nullptr;
+    // Solve-OF pair groups: one stream each, forked from and joined to ss
+    cudaStream_t gs[MAX_OF_STREAMS] = {};
+    cudaEvent_t gfork = nullptr, gdone[MAX_OF_STREAMS] = {};
     void drop_graphs() {
         for (auto &g : graphs) {
             if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -183,6 +190,11 @@ static void free_ws(WS<real> *w) {
     w->drop_graphs();
     if (w->ss) cudaStreamDestroy(w->ss);
     if (w->join) cudaEventDestroy(w->join);
+    for (int g = 0; g < MAX_OF_STREAMS; ++g) {
+        if (w->gs[g]) cudaStreamDestroy(w->gs[g]);
+        if (w->gdone[g]) cudaEventDestroy(w->gdone[g]);
+    }
+    if (w->gfork) cudaEventDestroy(w->gfork);
     if (w->mem) cudaFree(w->mem);
     delete w;
 }
@@ -244,8 +256,7 @@ static mof_status ensure_ws(mof_problem *p, const mof_solver_params &prm, int n_
     int dev_sms = 152;
     cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, p->device);
     w->gram_ctas = 2 * dev_sms;
-    const long long chunks_n = krylov_chunks(std::max(n, m)), chunks_of = krylov_chunks(N2);
-    const long long partial = std::max(chunks_n * 3 * Kmax, P * chunks_of * 3 * (long long)Kof);
+    const long long partial = std::max(krylov_partial_doubles(std::max(n, m), Kmax), P * krylov_partial_doubles(N2, Kof));
     for (int pass = 0; pass < 2; ++pass) {
         Arena a;
         a.base = w->mem;
@@ -329,6 +340,7 @@ static mof_status ensure_ws(mof_problem *p, const mof_solver_params &prm, int n_
         w->app_of = a.take<int>(P);
         w->flag_of = a.take<int>(P);
         w->partial = a.take<double>((size_t)partial);
+        w->kaux = a.take<double>(2 * (size_t)std::max<long long>(P, 1) + 8);
         w->iter = a.take<int>(1);
         if (pass == 0) {
             w->bytes = a.off + 256;
@@ -341,6 +353,11 @@ static mof_status ensure_ws(mof_problem *p, const mof_solver_params &prm, int n_
             MOF_CUDA(cudaMemset(w->mem, 0, w->bytes));
             MOF_CUDA(cudaStreamCreateWithFlags(&w->ss, cudaStreamNonBlocking));
             MOF_CUDA(cudaEventCreateWithFlags(&w->join, cudaEventDisableTiming));
+            MOF_CUDA(cudaEventCreateWithFlags(&w->gfork, cudaEventDisableTiming));
+            for (int g = 0; g < MAX_OF_STREAMS; ++g) {
+                MOF_CUDA(cudaStreamCreateWithFlags(&w->gs[g], cudaStreamNonBlocking));
+                MOF_CUDA(cudaEventCreateWithFlags(&w->gdone[g], cudaEventDisableTiming));
+            }
         }
     }
     const size_t sm = theta_gram_smem<real>(Kmax);
@@ -349,6 +366,18 @@ static mof_status ensure_ws(mof_problem *p, const mof_solver_params &prm, int n_
 }
 
 // ============================================================ small kernels
+// Per-problem FP64 scalar converted to the storage type once per block and
+// shared: GB300 issues FP64 (conversions included) at a small fraction of
+// the FP32 rate, so bandwidth-bound kernels keep FP64 out of their threads.
+// Call once per kernel, before any thread-dependent return.
+template <typename real>
+__device__ __forceinline__ real block_scalar(const double *p) {
+    __shared__ real v;
+    if (threadIdx.x == 0 && threadIdx.y == 0) v = (real)*p;
+    __syncthreads();
+    return v;
+}
+
 template <typename real>
 __global__ void k_fill(real *x, long long n, real v) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) x[i] = v;
@@ -370,7 +399,7 @@ __global__ void k_axpy_dev(real *__restrict__ x, long long xstride, const real *
                            const double *__restrict__ coef, long long N, const int *__restrict__ act) {
     const int b = blockIdx.y;
     if (act && !act[b]) return;
-    const real c = (real)coef[b];
+    const real c = block_scalar<real>(coef + b);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
         x[b * xstride + i] -= c * y[b * ystride + i];
 }
@@ -428,7 +457,7 @@ __global__ void k_of_upsT(const real *__restrict__ ux, const real *__restrict__ 
     if (!act[b]) return;
     const real *uj = U + ((long long)b * ldU + j) * ns;
     const real *vp = j > 0 ? V + ((long long)b * ldV + j - 1) * 2 * ns : nullptr;
-    const real bj = j > 0 ? (real)beta[b] : (real)0;
+    const real bj = j > 0 ? block_scalar<real>(beta + b) : (real)0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ns; i += (long long)gridDim.x * blockDim.x) {
         const real r = uj[i];
         real o0 = ux[b * ns + i] * r, o1 = uy[b * ns + i] * r;
@@ -449,7 +478,7 @@ __global__ void k_of_ups(const real *__restrict__ ux, const real *__restrict__ u
     if (!act[b]) return;
     const real *vj = V + ((long long)b * ldV + j) * 2 * ns;
     const real *uj = U + ((long long)b * ldU + j) * ns;
-    const real aj = (real)alpha[b];
+    const real aj = block_scalar<real>(alpha + b);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ns; i += (long long)gridDim.x * blockDim.x)
         out[b * ns + i] = ux[b * ns + i] * vj[i] + uy[b * ns + i] * vj[ns + i] - aj * uj[i];
 }
@@ -493,13 +522,13 @@ __global__ void k_of_resid(const real *__restrict__ ux, const real *__restrict__
                            const int *__restrict__ act) {
     const int b = blockIdx.z;
     if (!act[b]) return;
+    const real g = block_scalar<real>(gam + b);
     const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
     if (x >= nx || y >= ny) return;
     const long long ns = (long long)nx * ny, i = (long long)y * nx + x;
     const real *v = s + b * 2 * ns;
     const real ax = ux[b * ns + i], ay = uy[b * ns + i];
     const real a = ax * v[i] + ay * v[ns + i];
-    const real g = (real)gam[b];
     r[b * 2 * ns + i] = ax * a - AtB[b * 2 * ns + i] + g * lap_at(v, nx, ny, x, y);
     r[b * 2 * ns + ns + i] = ay * a - AtB[b * 2 * ns + ns + i] + g * lap_at(v + ns, nx, ny, x, y);
 }
@@ -729,6 +758,8 @@ static mof_status solve_of_impl(mof_problem *p, const mof_solver_params &prm, WS
     const double tol = prm.breakdown_tol > 0 ? prm.breakdown_tol : (sizeof(real) == 8 ? 1e-10 : 1e-6);
     Krylov<real> kr;
     kr.partial = w.partial;
+    kr.err = w.err;
+    kr.aux = w.kaux;
     const dim3 g2((p->nx + 31) / 32, (p->ny + 7) / 8, P);
     const dim3 blk2(32, 8);
     {
@@ -772,54 +803,80 @@ static mof_status solve_of_impl(mof_problem *p, const mof_solver_params &prm, WS
             kr.multidot(BA, 3, xs, o, st);
         }
     }
-    SmallArgs sa{};
-    sa.GA = w.GA;
-    sa.GL = w.GL;
-    sa.g = w.gof;
-    sa.bb = w.bb_of;
-    sa.K = w.Kv_of;
-    sa.active = w.act_of;
-    sa.ld = Kof;
-    sa.B = P;
-    sa.rule = MOF_RULE_GCV;
-    sa.lam = w.gam;
-    sa.z = w.zof;
-    sa.flag = w.flag_of;
-    sa.err = w.err;
-    BasisRef<real> BS{w.Vof, N2, Kof, P, w.Kv_of, nullptr};
-    for (int it = 0; it < prm.of_iters; ++it) {
-        {
-            Scope sc(tm, "of_small", st);
-            MOF_TRY(launch_small_solve(sa, st));
+    // GKS iterations. The pairs are split into groups, each iterating on its own
+    // stream: a group's small FP64 solves occupy one SM per pair and are latency
+    // bound, so they run while the other groups' bandwidth-bound kernels use the
+    // rest of the GPU. Every kernel works per pair, so the grouping does not
+    // change the result.
+    const int G = std::max(1, std::min(prm.of_streams > 0 ? prm.of_streams : AUTO_OF_STREAMS, P));
+    const long long part_pair = krylov_partial_doubles(N2, Kof);
+    MOF_CUDA(cudaEventRecord(w.gfork, st));
+    for (int gi = 0; gi < G; ++gi) {
+        const int b0 = (int)((long long)gi * P / G), nb = (int)((long long)(gi + 1) * P / G) - b0;
+        const cudaStream_t gst = w.gs[gi];
+        MOF_CUDA(cudaStreamWaitEvent(gst, w.gfork, 0));
+        Krylov<real> kg;
+        kg.partial = w.partial + b0 * part_pair;
+        kg.err = w.err;
+        kg.aux = w.kaux + 2LL * b0;
+        const long long KK = (long long)Kof * Kof;
+        real *Vg = w.Vof + (long long)b0 * Kof * N2, *sg = s_out + (long long)b0 * N2, *wvg = w.wv + (long long)b0 * N2;
+        real *vng = w.vnew_of + (long long)b0 * N2, *y1g = w.y1 + (long long)b0 * N2, *y2g = w.y2 + (long long)b0 * N2;
+        const real *uxg = w.ux + (long long)b0 * ns, *uyg = w.uy + (long long)b0 * ns, *AtBg = w.AtB + (long long)b0 * N2;
+        int *Kvg = w.Kv_of + b0, *actg = w.act_of + b0, *appg = w.app_of + b0;
+        SmallArgs sa{};
+        sa.GA = w.GA + b0 * KK;
+        sa.GL = w.GL + b0 * KK;
+        sa.g = w.gof + (long long)b0 * Kof;
+        sa.bb = w.bb_of + b0;
+        sa.K = Kvg;
+        sa.active = actg;
+        sa.ld = Kof;
+        sa.B = nb;
+        sa.rule = MOF_RULE_GCV;
+        sa.lam = w.gam + b0;
+        sa.z = w.zof + (long long)b0 * Kof;
+        sa.flag = w.flag_of + b0;
+        sa.err = w.err;
+        const dim3 gg((p->nx + 31) / 32, (p->ny + 7) / 8, nb);
+        BasisRef<real> BS{Vg, N2, Kof, nb, Kvg, nullptr};
+        BasisRef<real> BAg{Vg, N2, Kof, nb, Kvg, actg};
+        BasisRef<real> BNg{Vg, N2, Kof, nb, Kvg, appg};
+        for (int it = 0; it < prm.of_iters; ++it) {
+            {
+                Scope sc(tm, "of_small", gst);
+                MOF_TRY(launch_small_solve(sa, gst));
+            }
+            {
+                Scope sc(tm, "of_combine", gst);
+                kg.combine(BS, sa.z, Kof, sg, N2, gst);
+            }
+            if (it == prm.of_iters - 1) break;
+            {
+                Scope sc(tm, "of_resid", gst);
+                ::mof::count_launch(), k_of_resid<real><<<gg, blk2, 0, gst>>>(uxg, uyg, AtBg, sg, sa.lam, wvg, p->nx, p->ny, actg);
+            }
+            {
+                Scope sc(tm, "of_reorth", gst);
+                kg.reorth(BAg, wvg, N2, w.coef_of + (long long)b0 * Kof, w.nrm_of + b0, gst);
+                kg.append(BAg, Kvg, wvg, N2, w.nrm_of + b0, w.scale_of + b0, tol, w.grow_of + b0, appg, vng, gst);
+            }
+            {
+                Scope sc(tm, "of_gram", gst);
+                ::mof::count_launch(), k_of_normal_parts<real><<<gg, blk2, 0, gst>>>(uxg, uyg, vng, N2, y1g, y2g, p->nx, p->ny, appg);
+                DotVecs<real> xs{{y1g, y2g, AtBg}, {N2, N2, N2}};
+                DotOuts o{};
+                o.o[0] = DotOut{w.GA + b0 * KK, KK, Kof, 1, 1, 1.0};
+                o.o[1] = DotOut{w.GL + b0 * KK, KK, Kof, 1, 1, 1.0};
+                o.o[2] = DotOut{w.gof + (long long)b0 * Kof, Kof, 1, 0, 0, 1.0};
+                kg.multidot(BNg, 3, xs, o, gst);
+                ::mof::count_launch(), k_sym_last<<<nb, 64, 0, gst>>>(w.GA + b0 * KK, Kof, Kvg, appg);
+                ::mof::count_launch(), k_sym_last<<<nb, 64, 0, gst>>>(w.GL + b0 * KK, Kof, Kvg, appg);
+            }
         }
-        {
-            Scope sc(tm, "of_combine", st);
-            kr.combine(BS, w.zof, Kof, s_out, N2, st);
-        }
-        if (it == prm.of_iters - 1) break;
-        {
-            Scope sc(tm, "of_resid", st);
-            ::mof::count_launch(), k_of_resid<real><<<g2, blk2, 0, st>>>(w.ux, w.uy, w.AtB, s_out, w.gam, w.wv, p->nx, p->ny, w.act_of);
-        }
-        {
-            Scope sc(tm, "of_reorth", st);
-            kr.reorth(BA, w.wv, N2, w.coef_of, w.nrm_of, st);
-            kr.append(BA, w.Kv_of, w.wv, N2, w.nrm_of, w.scale_of, tol, w.grow_of, w.app_of, w.vnew_of, st);
-        }
-        {
-            Scope sc(tm, "of_gram", st);
-            BasisRef<real> BN{w.Vof, N2, Kof, P, w.Kv_of, w.app_of};
-            ::mof::count_launch(), k_of_normal_parts<real><<<g2, blk2, 0, st>>>(w.ux, w.uy, w.vnew_of, N2, w.y1, w.y2, p->nx, p->ny, w.app_of);
-            DotVecs<real> xs{{w.y1, w.y2, w.AtB}, {N2, N2, N2}};
-            DotOuts o{};
-            o.o[0] = DotOut{w.GA, (long long)Kof * Kof, Kof, 1, 1, 1.0};
-            o.o[1] = DotOut{w.GL, (long long)Kof * Kof, Kof, 1, 1, 1.0};
-            o.o[2] = DotOut{w.gof, Kof, 1, 0, 0, 1.0};
-            kr.multidot(BN, 3, xs, o, st);
-            ::mof::count_launch(), k_sym_last<<<P, 64, 0, st>>>(w.GA, Kof, w.Kv_of, w.app_of);
-            ::mof::count_launch(), k_sym_last<<<P, 64, 0, st>>>(w.GL, Kof, w.Kv_of, w.app_of);
-        }
+        MOF_CUDA(cudaEventRecord(w.gdone[gi], gst));
     }
+    for (int gi = 0; gi < G; ++gi) MOF_CUDA(cudaStreamWaitEvent(st, w.gdone[gi], 0));
     MOF_LAUNCH_CHECK();
     return MOF_OK;
 }
@@ -844,6 +901,8 @@ static mof_status solve_impl(mof_problem *p, const mof_solver_params &prm, int n
     const double tol = prm.breakdown_tol > 0 ? prm.breakdown_tol : (sizeof(real) == 8 ? 1e-10 : 1e-6);
     Krylov<real> kr;
     kr.partial = w.partial;
+    kr.err = w.err;
+    kr.aux = w.kaux;
     const size_t tg_smem = theta_gram_smem<real>(Kmax);
     MOF_CUDA(cudaFuncSetAttribute(k_theta_gram<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tg_smem));
 
@@ -1044,6 +1103,7 @@ static mof_status solve_impl(mof_problem *p, const mof_solver_params &prm, int n
             report[k].of_basis_min = (int)r[5];
             report[k].of_basis_max = (int)r[6];
         }
+    if (err & 4) return fail(MOF_ETIMEOUT, "a bounded device wait ran out (code %d)", err);
     if (err) return fail(MOF_ENUMERIC, "device reported a numerical failure (code %d): factorisation or non-finite value", err);
     return MOF_OK;
 }
@@ -1062,6 +1122,7 @@ static mof_status solve_of_entry(mof_problem *p, const mof_solver_params &prm, c
     MOF_CUDA(cudaMemcpyAsync(&err, wp->err, sizeof(int), cudaMemcpyDeviceToHost, st));
     MOF_CUDA(cudaStreamSynchronize(st));
     if (tm) tm->collect();
+    if (err & 4) return fail(MOF_ETIMEOUT, "a bounded device wait ran out (code %d)", err);
     if (err) return fail(MOF_ENUMERIC, "device reported a numerical failure (code %d)", err);
     return MOF_OK;
 }
@@ -1069,7 +1130,8 @@ static mof_status solve_of_entry(mof_problem *p, const mof_solver_params &prm, c
 static mof_status check_params(const mof_problem *p, const mof_solver_params *prm, int n_outer, bool image_step = true) {
     if (!p || !prm) return fail(MOF_EINVAL, "null problem or parameters");
     if (n_outer < 1) return fail(MOF_EINVAL, "n_outer must be >= 1");
-    if (prm->ell < 1 || prm->of_ell < 1 || prm->of_iters < 1 || prm->tau < 0 || prm->of_dr < 1 || prm->of_dr > 64)
+    if (prm->ell < 1 || prm->of_ell < 1 || prm->of_iters < 1 || prm->tau < 0 || prm->of_dr < 1 || prm->of_dr > 64 ||
+        prm->of_streams < 0 || prm->of_streams > MAX_OF_STREAMS)
         return fail(MOF_EINVAL, "invalid solver parameters");
     if (prm->ell + n_outer > 60 || prm->of_ell + prm->of_iters > 64)
         return fail(MOF_EUNSUPPORTED,

@@ -45,10 +45,14 @@ struct DotOuts {
 };
 
 long long krylov_chunks(long long N);
+// doubles of Krylov::partial needed per problem of length N and basis capacity Kmax
+long long krylov_partial_doubles(long long N, int Kmax);
 
 template <typename real>
 struct Krylov {
-    double *partial = nullptr;  // scratch [B][chunks][Kmax] (sized by the owner)
+    double *partial = nullptr;  // scratch [B][chunks][Kmax] (sized by the owner: krylov_partial_doubles)
+    int *err = nullptr;         // device error word (|= 4: a bounded wait ran out), may be null
+    double *aux = nullptr;      // scratch [2][B] of append (slot, 1/||x||), sized by the owner
     // out[b][j] = sign * <V[b][j], x[b]>, j < K[b]
     void dots(const BasisRef<real> &B, const real *x, long long xstride, double *out, long long ostride, double sign,
               cudaStream_t st) const;
@@ -66,6 +70,10 @@ struct Krylov {
     void norm2(const real *x, long long N, long long xstride, int nb, double *out, cudaStream_t st) const;
     // x[b] <- (I - V V^T)^2 x[b] (classical Gram-Schmidt twice); ||x||^2 -> nrm2_out
     void reorth(const BasisRef<real> &B, real *x, long long xstride, double *coef, double *nrm2_out, cudaStream_t st) const;
+    // x[b] <- x[b] - V[b] c[b] and out[b] = V[b]^T x[b] in one pass over V (false: not
+    // applicable to this layout, nothing enqueued)
+    bool sub_dot(const BasisRef<real> &B, const double *c, long long cstride, real *x, long long xstride, double *out,
+                 cudaStream_t st) const;
     // V[b][K[b]] = x[b]/||x[b]||, K[b]++ unless ||x[b]|| <= tol*scale[b] (then grow[b] = 0);
     // scale may be null (only ||x|| > 0 required); stage[b] (may be null) receives the new vector
     void append(const BasisRef<real> &B, int *Kmut, const real *x, long long xstride, const double *nrm2,
