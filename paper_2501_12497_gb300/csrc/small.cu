@@ -379,6 +379,80 @@ __device__ void jacobi(T *A, int lda, T *W, int ldw, T *v, int K, int Kp, int ma
     }
 }
 
+// FP32 one-sided (Hestenes) Jacobi in the registers of one warp, K <= 32:
+// lane i holds column i of the symmetric positive semi-definite C and of the
+// accumulated rotation V; in each round of the round-robin ordering a lane
+// takes its partner's columns by shuffles, both lanes of a pair compute the
+// same rotation from the same numbers (the two column norms and their dot
+// product), and each updates its own columns (lower index p:
+// c x_p - s x_q, higher q: s x_p + c x_q). At convergence the columns of C V
+// are orthogonal, so V diagonalises C^2 and therefore C. The warm start needs
+// eigenvectors to FP32 accuracy only; V is written to X (FP64, K x K).
+// Called by warp 0 only.
+__device__ void jacobi1_warp(const double *C, int lds, int K, double *X, int max_sweeps, float tol) {
+    const int lane = threadIdx.x & 31;
+    float a[32], v[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        a[k] = (lane < K && k < K) ? (float)C[k * lds + lane] : 0.0f;
+        v[k] = (k == lane && lane < K) ? 1.0f : 0.0f;
+    }
+    const int Kp = K + (K & 1);
+    // pairs whose dot product is below floor_g (set by ||C||_F^2, invariant under the
+    // rotations) are left alone: their directions carry eigenvalues too small for FP32
+    // to resolve, and the FP64 stage handles them
+    float f2 = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) f2 = fmaf(a[k], a[k], f2);
+    f2 = warp_sumf(f2);
+    const float floor_g = 1e-14f * f2;
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        bool any = false;
+        for (int round = 0; round < Kp - 1; ++round) {
+            // position of this lane's column in the round, and its partner's column
+            int pos = 0;
+            if (lane > 0 && lane < Kp) {
+                pos = (lane - 1 - round) % (Kp - 1);
+                if (pos < 0) pos += Kp - 1;
+                pos += 1;
+            }
+            const int partner = lane < Kp ? rr_player(Kp - 1 - pos, round, Kp) : lane;
+            const int src = partner < 32 ? partner : lane;
+            float pa[32];
+            float g = 0.0f, nrm = 0.0f, pn = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+                pa[k] = __shfl_sync(0xffffffffu, a[k], src);
+                g = fmaf(a[k], pa[k], g);
+                nrm = fmaf(a[k], a[k], nrm);
+                pn = fmaf(pa[k], pa[k], pn);
+            }
+            const bool low = lane < partner;
+            const float alpha = low ? nrm : pn, beta = low ? pn : nrm;  // norms^2 of the lower, higher column
+            const bool rot = lane < K && partner < K && fabsf(g) > tol * sqrtf(alpha * beta) && fabsf(g) > floor_g &&
+                             fabsf(g) > 1e-30f;
+            float c = 1.0f, sp = 0.0f;  // own' = c own + sp partner
+            if (rot) {
+                const float zeta = (beta - alpha) / (2.0f * g);
+                const float t = (zeta >= 0.0f ? 1.0f : -1.0f) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.0f)));
+                c = rsqrtf(fmaf(t, t, 1.0f));
+                sp = low ? -t * c : t * c;
+                any = true;
+            }
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+                const float pv = __shfl_sync(0xffffffffu, v[k], src);
+                a[k] = fmaf(sp, pa[k], c * a[k]);
+                v[k] = fmaf(sp, pv, c * v[k]);
+            }
+        }
+        if (!__any_sync(0xffffffffu, any)) break;
+    }
+#pragma unroll
+    for (int k = 0; k < 32; ++k)
+        if (lane < K && k < K) X[k * lds + lane] = (double)v[k];
+}
+
 // ------------------------------------------------------------ lambda functions
 struct Spec {
     int K;
@@ -505,7 +579,7 @@ __device__ __forceinline__ R newton_step(R t, R f, R f1, R &A, R &B) {
 
 }  // namespace
 
-__global__ void __launch_bounds__(ST) k_small_solve(SmallArgs a) {
+__global__ void __launch_bounds__(ST, 1) k_small_solve(SmallArgs a) {
     extern __shared__ double sm[];
     __shared__ double s_rho, s_rho0sq, s_t, s_scale;
     __shared__ double s_refv[NREF];
@@ -601,20 +675,25 @@ __global__ void __launch_bounds__(ST) k_small_solve(SmallArgs a) {
     double lam = a.lam_fixed;
     if (a.rule != MOF_RULE_FIXED) {
         // ------------------------------------------ 2a. FP32 Jacobi on C
-        for (int e = tid; e < Kp * Kp; e += ST) {
-            const int i = e / Kp, j = e - (e / Kp) * Kp;
-            AF(Af, i, j) = (i < K && j < K) ? (float)AT(Cm, i, j) : 0.0f;
-            AF(Wf, i, j) = i == j ? 1.0f : 0.0f;
+        if (K <= 32) {  // one warp, registers only
+            if (wid == 0) jacobi1_warp(Cm, lds, K, Xm, JACOBI32_MAX_SWEEPS, 1e-6f);
+            __syncthreads();
+        } else {
+            for (int e = tid; e < Kp * Kp; e += ST) {
+                const int i = e / Kp, j = e - (e / Kp) * Kp;
+                AF(Af, i, j) = (i < K && j < K) ? (float)AT(Cm, i, j) : 0.0f;
+                AF(Wf, i, j) = i == j ? 1.0f : 0.0f;
+            }
+            __syncthreads();
+            jacobi<float>(Af, ldf, Wf, ldf, (float *)nullptr, K, Kp, JACOBI32_MAX_SWEEPS, 1e-6f, 1e-7f, jf, s_redf);
+            for (int e = tid; e < K * K; e += ST) {
+                const int i = e / K, j = e - (e / K) * K;
+                AT(Xm, i, j) = (double)AF(Wf, i, j);
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        jacobi<float>(Af, ldf, Wf, ldf, (float *)nullptr, K, Kp, JACOBI32_MAX_SWEEPS, 1e-6f, 1e-7f, jf, s_redf);
 
         // ------------------------------------------ 2b. FP64: orthonormalise, congruence
-        for (int e = tid; e < K * K; e += ST) {
-            const int i = e / K, j = e - (e / K) * K;
-            AT(Xm, i, j) = (double)AF(Wf, i, j);
-        }
-        __syncthreads();
         gemm_kk(Tm, Xm, true, Xm, false, K, lds, true);  // X0^T X0 (the FP32 matrix is done with)
         for (int i = tid; i < K; i += ST) AT(Tm, i, i) -= 1.0;  // E = X0^T X0 - I
         __syncthreads();

@@ -756,58 +756,17 @@ static mof_status solve_of_impl(mof_problem *p, const mof_solver_params &prm, WS
     const long long ns = p->ns, N2 = 2 * ns;
     const int Kof = w.Kof, ldU = w.of_ell + 1;
     const double tol = prm.breakdown_tol > 0 ? prm.breakdown_tol : (sizeof(real) == 8 ? 1e-10 : 1e-6);
-    Krylov<real> kr;
-    kr.partial = w.partial;
-    kr.err = w.err;
-    kr.aux = w.kaux;
-    const dim3 g2((p->nx + 31) / 32, (p->ny + 7) / 8, P);
     const dim3 blk2(32, 8);
     {
         Scope sc(tm, "of_fields", st);
         MOF_TRY(launch_of_fields<real>(p, u, prm.of_dr, w.ux, w.uy, w.ut, st));
         ::mof::count_launch(), k_of_rhs<real><<<dim3(fb(ns), P), 256, 0, st>>>(w.ux, w.uy, w.ut, w.bof, w.AtB, ns);
     }
-    BasisRef<real> BV{w.Vof, N2, Kof, P, w.Kv_of, w.gkb_of};
-    BasisRef<real> BU{w.Uof, ns, ldU, P, w.Ku_of, w.gkb_of};
-    {
-        Scope sc(tm, "of_gkb", st);
-        kr.norm2(w.bof, ns, ns, P, w.bb_of, st);
-        ::mof::count_launch(), k_of_activate<<<(P + 63) / 64, 64, 0, st>>>(w.bb_of, w.act_of, w.gkb_of, w.grow_of, w.Kv_of, w.Ku_of, w.beta1_of, P);
-        kr.norm2(w.AtB, N2, N2, P, w.nrm_of, st);
-        ::mof::count_launch(), k_sqrt_into<<<(P + 63) / 64, 64, 0, st>>>(w.nrm_of, w.scale_of, P);
-        // u_1 = b / ||b||
-        kr.append(BU, w.Ku_of, w.bof, ns, w.bb_of, nullptr, 0.0, w.gkb_of, nullptr, nullptr, st);
-        for (int j = 0; j < w.of_ell && j < prm.of_ell; ++j) {
-            ::mof::count_launch(), k_of_upsT<real><<<dim3(fb(ns), P), 256, 0, st>>>(w.ux, w.uy, w.Uof, ldU, j, w.Vof, Kof, w.beta_of, w.wv, ns, w.gkb_of);
-            kr.reorth(BV, w.wv, N2, w.coef_of, w.nrm_of, st);
-            if (j == 0) ::mof::count_launch(), k_sqrt_into_if<<<(P + 63) / 64, 64, 0, st>>>(w.nrm_of, w.alpha1_of, P, w.gkb_of);
-            ::mof::count_launch(), k_sqrt_into_if<<<(P + 63) / 64, 64, 0, st>>>(w.nrm_of, w.alpha_of, P, w.gkb_of);
-            kr.append(BV, w.Kv_of, w.wv, N2, w.nrm_of, j == 0 ? nullptr : w.alpha1_of, tol, w.gkb_of, nullptr, nullptr, st);
-            ::mof::count_launch(), k_of_ups<real><<<dim3(fb(ns), P), 256, 0, st>>>(w.ux, w.uy, w.Vof, Kof, j, w.Uof, ldU, w.alpha_of, w.wu, ns, w.gkb_of);
-            kr.reorth(BU, w.wu, ns, w.coefU_of, w.nrm_of, st);
-            ::mof::count_launch(), k_sqrt_into_if<<<(P + 63) / 64, 64, 0, st>>>(w.nrm_of, w.beta_of, P, w.gkb_of);
-            kr.append(BU, w.Ku_of, w.wu, ns, w.nrm_of, w.beta1_of, tol, w.gkb_of, nullptr, nullptr, st);
-        }
-    }
-    BasisRef<real> BA{w.Vof, N2, Kof, P, w.Kv_of, w.act_of};
-    {
-        Scope sc(tm, "of_gram", st);
-        for (int j = 0; j < prm.of_ell; ++j) {
-            ::mof::count_launch(), k_of_normal_parts<real><<<g2, blk2, 0, st>>>(w.ux, w.uy, w.Vof + (long long)j * N2, (long long)Kof * N2, w.y1, w.y2,
-                                                         p->nx, p->ny, w.act_of);
-            DotVecs<real> xs{{w.y1, w.y2, w.AtB}, {N2, N2, N2}};
-            DotOuts o{};
-            o.o[0] = DotOut{w.GA + j, (long long)Kof * Kof, Kof, 0, 0, 1.0};
-            o.o[1] = DotOut{w.GL + j, (long long)Kof * Kof, Kof, 0, 0, 1.0};
-            o.o[2] = DotOut{w.gof, Kof, 1, 0, 0, 1.0};
-            kr.multidot(BA, 3, xs, o, st);
-        }
-    }
-    // GKS iterations. The pairs are split into groups, each iterating on its own
-    // stream: a group's small FP64 solves occupy one SM per pair and are latency
-    // bound, so they run while the other groups' bandwidth-bound kernels use the
-    // rest of the GPU. Every kernel works per pair, so the grouping does not
-    // change the result.
+    // The pairs are split into groups, each running its whole Solve-OF (GKB start,
+    // initial Gram columns, GKS iterations) on its own stream: a group's small
+    // FP64 solves occupy one SM per pair and are latency bound, and its GKB steps
+    // are short launches, so the groups fill the GPU together. Every kernel works
+    // per pair, so the grouping does not change the result.
     const int G = std::max(1, std::min(prm.of_streams > 0 ? prm.of_streams : AUTO_OF_STREAMS, P));
     const long long part_pair = krylov_partial_doubles(N2, Kof);
     MOF_CUDA(cudaEventRecord(w.gfork, st));
@@ -822,8 +781,49 @@ static mof_status solve_of_impl(mof_problem *p, const mof_solver_params &prm, WS
         const long long KK = (long long)Kof * Kof;
         real *Vg = w.Vof + (long long)b0 * Kof * N2, *sg = s_out + (long long)b0 * N2, *wvg = w.wv + (long long)b0 * N2;
         real *vng = w.vnew_of + (long long)b0 * N2, *y1g = w.y1 + (long long)b0 * N2, *y2g = w.y2 + (long long)b0 * N2;
+        real *Ug = w.Uof + (long long)b0 * ldU * ns, *wug = w.wu + (long long)b0 * ns;
         const real *uxg = w.ux + (long long)b0 * ns, *uyg = w.uy + (long long)b0 * ns, *AtBg = w.AtB + (long long)b0 * N2;
-        int *Kvg = w.Kv_of + b0, *actg = w.act_of + b0, *appg = w.app_of + b0;
+        const real *bofg = w.bof + (long long)b0 * ns;
+        int *Kvg = w.Kv_of + b0, *Kug = w.Ku_of + b0, *actg = w.act_of + b0, *appg = w.app_of + b0, *gkbg = w.gkb_of + b0;
+        double *nrmg = w.nrm_of + b0, *bbg = w.bb_of + b0;
+        const int pb = (nb + 63) / 64;
+        BasisRef<real> BV{Vg, N2, Kof, nb, Kvg, gkbg};
+        BasisRef<real> BU{Ug, ns, ldU, nb, Kug, gkbg};
+        {
+            Scope sc(tm, "of_gkb", gst);
+            kg.norm2(bofg, ns, ns, nb, bbg, gst);
+            ::mof::count_launch(), k_of_activate<<<pb, 64, 0, gst>>>(bbg, actg, gkbg, w.grow_of + b0, Kvg, Kug, w.beta1_of + b0, nb);
+            kg.norm2(AtBg, N2, N2, nb, nrmg, gst);
+            ::mof::count_launch(), k_sqrt_into<<<pb, 64, 0, gst>>>(nrmg, w.scale_of + b0, nb);
+            // u_1 = b / ||b||
+            kg.append(BU, Kug, bofg, ns, bbg, nullptr, 0.0, gkbg, nullptr, nullptr, gst);
+            for (int j = 0; j < w.of_ell && j < prm.of_ell; ++j) {
+                ::mof::count_launch(), k_of_upsT<real><<<dim3(fb(ns), nb), 256, 0, gst>>>(uxg, uyg, Ug, ldU, j, Vg, Kof, w.beta_of + b0, wvg, ns, gkbg);
+                kg.reorth(BV, wvg, N2, w.coef_of + (long long)b0 * Kof, nrmg, gst);
+                if (j == 0) ::mof::count_launch(), k_sqrt_into_if<<<pb, 64, 0, gst>>>(nrmg, w.alpha1_of + b0, nb, gkbg);
+                ::mof::count_launch(), k_sqrt_into_if<<<pb, 64, 0, gst>>>(nrmg, w.alpha_of + b0, nb, gkbg);
+                kg.append(BV, Kvg, wvg, N2, nrmg, j == 0 ? nullptr : w.alpha1_of + b0, tol, gkbg, nullptr, nullptr, gst);
+                ::mof::count_launch(), k_of_ups<real><<<dim3(fb(ns), nb), 256, 0, gst>>>(uxg, uyg, Vg, Kof, j, Ug, ldU, w.alpha_of + b0, wug, ns, gkbg);
+                kg.reorth(BU, wug, ns, w.coefU_of + (long long)b0 * ldU, nrmg, gst);
+                ::mof::count_launch(), k_sqrt_into_if<<<pb, 64, 0, gst>>>(nrmg, w.beta_of + b0, nb, gkbg);
+                kg.append(BU, Kug, wug, ns, nrmg, w.beta1_of + b0, tol, gkbg, nullptr, nullptr, gst);
+            }
+        }
+        const dim3 gg((p->nx + 31) / 32, (p->ny + 7) / 8, nb);
+        BasisRef<real> BAg{Vg, N2, Kof, nb, Kvg, actg};
+        {
+            Scope sc(tm, "of_gram", gst);
+            for (int j = 0; j < prm.of_ell; ++j) {
+                ::mof::count_launch(), k_of_normal_parts<real><<<gg, blk2, 0, gst>>>(uxg, uyg, Vg + (long long)j * N2, (long long)Kof * N2, y1g, y2g,
+                                                              p->nx, p->ny, actg);
+                DotVecs<real> xs{{y1g, y2g, AtBg}, {N2, N2, N2}};
+                DotOuts o{};
+                o.o[0] = DotOut{w.GA + b0 * KK + j, KK, Kof, 0, 0, 1.0};
+                o.o[1] = DotOut{w.GL + b0 * KK + j, KK, Kof, 0, 0, 1.0};
+                o.o[2] = DotOut{w.gof + (long long)b0 * Kof, Kof, 1, 0, 0, 1.0};
+                kg.multidot(BAg, 3, xs, o, gst);
+            }
+        }
         SmallArgs sa{};
         sa.GA = w.GA + b0 * KK;
         sa.GL = w.GL + b0 * KK;
@@ -838,9 +838,7 @@ static mof_status solve_of_impl(mof_problem *p, const mof_solver_params &prm, WS
         sa.z = w.zof + (long long)b0 * Kof;
         sa.flag = w.flag_of + b0;
         sa.err = w.err;
-        const dim3 gg((p->nx + 31) / 32, (p->ny + 7) / 8, nb);
         BasisRef<real> BS{Vg, N2, Kof, nb, Kvg, nullptr};
-        BasisRef<real> BAg{Vg, N2, Kof, nb, Kvg, actg};
         BasisRef<real> BNg{Vg, N2, Kof, nb, Kvg, appg};
         for (int it = 0; it < prm.of_iters; ++it) {
             {
