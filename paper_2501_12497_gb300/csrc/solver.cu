@@ -9,6 +9,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <string>
 #include <vector>
 
@@ -235,8 +236,10 @@ constexpr int TG_ROWS = 4 * TG_PIX;
 
 template <typename real>
 static size_t theta_gram_smem(int Kmax) {
-    const int Ks = ((Kmax + 3) / 4) * 4 + 4;
-    return sizeof(real) * TG_ROWS * Ks;
+    // the row tile, reused at the end for the FP64 group sums ([groups][blocks][16] <= [256][16])
+    const size_t tile = sizeof(real) * (size_t)(((Kmax + 3) / 4) * 4) * (TG_ROWS + 4);
+    const size_t red = sizeof(double) * 256 * 16;
+    return tile > red ? tile : red;
 }
 
 template <typename real>
@@ -295,7 +298,7 @@ static mof_status ensure_ws(mof_problem *p, const mof_solver_params &prm, int n_
         w->beta1 = a.take<double>(1);
         w->alpha1 = a.take<double>(1);
         w->bb = a.take<double>(1);
-        w->gpart = a.take<double>((size_t)w->gram_ctas * 4 * Kmax * Kmax);
+        w->gpart = a.take<double>((size_t)w->gram_ctas * Kmax * Kmax);
         w->K = a.take<int>(1);
         w->KU = a.take<int>(1);
         w->grow = a.take<int>(1);
@@ -548,18 +551,19 @@ __global__ void k_of_rhs(const real *__restrict__ ux, const real *__restrict__ u
 
 // ------------------------------------------------------ weighted Theta Gram
 // G = (P Theta V)^T (P Theta V), P^2 = diag(((Theta uk)^2 + eps^2)^(-1/2)), over the
-// first K columns of V. Each tile of TG_PIX pixels of one frame yields 4 rows per
-// pixel (Psi_x, Psi_y of the frame; Mbar and Mbar' rows of the pair starting at
-// the frame), written to shared memory scaled by P. The block's threads own the
-// 4x4 blocks of the upper triangle of G (split over row groups of the tile),
-// accumulate a tile's rows in FP32 registers and carry the running sums across
-// tiles with Kahan compensation; per-block partials are reduced in FP64.
-template <typename real>
-__device__ __forceinline__ real bil_sample(const real *__restrict__ f, int nx, int x0, int x1, int y0, int y1, real wx, real wy) {
-    const real a = f[(long long)y0 * nx + x0], b = f[(long long)y0 * nx + x1];
-    const real c = f[(long long)y1 * nx + x0], d = f[(long long)y1 * nx + x1];
-    return (1 - wy) * ((1 - wx) * a + wx * b) + wy * ((1 - wx) * c + wx * d);
-}
+// first K columns of V. A tile of TG_PIX consecutive pixels of one frame yields
+// 4 rows per pixel (Psi_x, Psi_y of the frame; Mbar and Mbar' rows of the pair
+// starting at the frame), one row per thread: the thread's offsets and
+// bilinear weights are computed once per tile, its rows of the K basis vectors
+// are generated four vectors at a time (loads of four vectors in flight) and
+// stored scaled by P, column-major in shared memory (conflict-free stores).
+// The (4x4 block of the upper triangle, row group) pairs are spread over all
+// threads; each accumulates outer products of four rows at a time from
+// 128-bit shared loads in FP32 registers and carries the running sums across
+// tiles with Kahan compensation. At the end the row groups are combined in
+// FP64 in shared memory, and the per-CTA partials by k_gram_reduce.
+constexpr int TG_S = TG_ROWS + 4;  // column stride of the shared row tile
+constexpr int TG_MAXG = 8;         // row groups per 4x4 block at most
 
 template <typename real>
 __device__ __forceinline__ void warp_axis_s(int x, real v, int n, int &i0, int &i1, real &w) {
@@ -573,11 +577,18 @@ __device__ __forceinline__ void warp_axis_s(int x, real v, int n, int &i0, int &
     i1 = min(i0 + 1, n - 1);
 }
 
-// number of row groups the tile is split over: 4 while the 4x4 blocks of the
-// upper triangle fit in 64 threads, else 2 (<= 128 blocks, K <= 60)
-__host__ __device__ inline int tg_groups(int K) {
-    const int K4 = (K + 3) / 4;
-    return K4 * (K4 + 1) / 2 <= TG_T / 4 ? 4 : 2;
+// four consecutive values from 16-byte aligned shared memory
+template <typename real>
+struct Quad {
+    real x, y, z, w;
+};
+__device__ __forceinline__ Quad<float> load_quad(const float *p) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ Quad<double> load_quad(const double *p) {
+    const double2 a = *reinterpret_cast<const double2 *>(p), b = *reinterpret_cast<const double2 *>(p + 2);
+    return {a.x, a.y, b.x, b.y};
 }
 
 template <typename real>
@@ -586,18 +597,20 @@ __global__ void __launch_bounds__(TG_T) k_theta_gram(const real *__restrict__ V,
                                                      const real *__restrict__ sr, real eps2, int nx, int ny, int nt,
                                                      double *__restrict__ partial) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int Ks = ((Kmax + 3) / 4) * 4 + 4;
-    real *A = reinterpret_cast<real *>(smraw);
+    real *As = reinterpret_cast<real *>(smraw);  // [K4 * 4][TG_S], column j = basis vector j
     const int K = min(Kp[0], Kmax);
     const int K4 = (K + 3) / 4;
     const int nblk = K4 * (K4 + 1) / 2;
-    const int G = tg_groups(K);
-    const int gsize = TG_T / G, rows_per_group = TG_ROWS / G;
+    const int nb1 = max(nblk, 1);
+    const int RG = max(1, min(TG_MAXG, TG_T / nb1));
     const int tid = threadIdx.x;
-    const int group = tid / gsize, blk = tid - group * gsize;
-    // this thread's 4x4 block (I, J), I <= J, row-major over the upper triangle
+    const int g = tid / nb1, blk = tid - g * nb1;
+    const bool acc_on = g < RG && blk < nblk;
+    // rows of group g: [r0, r1), multiples of 4
+    const int rpg = ((TG_ROWS / RG + 3) / 4) * 4;
+    const int r0 = min(g * rpg, TG_ROWS), r1 = min(r0 + rpg, TG_ROWS);
     int I = 0, J = 0;
-    if (blk < nblk) {
+    if (acc_on) {
         int rem = blk;
         while (rem >= K4 - I) {
             rem -= K4 - I;
@@ -610,78 +623,90 @@ __global__ void __launch_bounds__(TG_T) k_theta_gram(const real *__restrict__ V,
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int c = 0; c < 4; ++c) sum[a][c] = comp[a][c] = 0;
-    const long long ns = (long long)nx * ny;
-    const long long tpf = (ns + TG_PIX - 1) / TG_PIX;
-    const long long ntiles = tpf * nt;
+    const int ns = nx * ny;
+    const int tpf = (ns + TG_PIX - 1) / TG_PIX;
+    const int ntiles = tpf * nt;
     const int np = nt - 1;
     const int q = tid & 3;
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int t = (int)(tile / tpf);
-        const long long pix = (tile % tpf) * TG_PIX + (tid >> 2);
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int t = tile / tpf;
+        const int pix = (tile - t * tpf) * TG_PIX + (tid >> 2);
         const bool inpix = pix < ns;
-        const int x = inpix ? (int)(pix % nx) : 0, y = inpix ? (int)(pix / nx) : 0;
+        const int y = inpix ? pix / nx : 0, x = inpix ? pix - y * nx : 0;
         bool valid = inpix && (q < 2 || t < np);
         if (q == 0 && x >= nx - 1) valid = false;
         if (q == 1 && y >= ny - 1) valid = false;
-        int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
-        real wx = 0, wy = 0;
-        long long fa = 0, fb = 0;  // frame offsets: row = v[fa + i] - interp(v[fb + .])
-        if (valid && q >= 2) {
-            const real *sv = (q == 2 ? s : sr) + 2LL * t * ns;
-            warp_axis_s(x, sv[pix], nx, x0, x1, wx);
-            warp_axis_s(y, sv[ns + pix], ny, y0, y1, wy);
-            fa = (q == 2 ? t : t + 1) * ns;
-            fb = (q == 2 ? t + 1 : t) * ns;
+        // row value = f[oc] - (w00 f[o00] + w01 f[o01] + w10 f[o10] + w11 f[o11]) within one basis vector
+        int oc = 0, o00 = 0, o01 = 0, o10 = 0, o11 = 0;
+        real w00 = 0, w01 = 0, w10 = 0, w11 = 0;
+        if (valid) {
+            const int base = t * ns + pix;
+            if (q == 0) {
+                oc = base + 1;
+                o00 = o01 = o10 = o11 = base;
+                w00 = 1;
+            } else if (q == 1) {
+                oc = base + nx;
+                o00 = o01 = o10 = o11 = base;
+                w00 = 1;
+            } else {
+                const real *sv = (q == 2 ? s : sr) + 2LL * t * ns;
+                int x0, x1, y0, y1;
+                real wx, wy;
+                warp_axis_s(x, sv[pix], nx, x0, x1, wx);
+                warp_axis_s(y, sv[ns + pix], ny, y0, y1, wy);
+                const int fa = (q == 2 ? t : t + 1) * ns, fb = (q == 2 ? t + 1 : t) * ns;
+                oc = fa + pix;
+                o00 = fb + y0 * nx + x0;
+                o01 = fb + y0 * nx + x1;
+                o10 = fb + y1 * nx + x0;
+                o11 = fb + y1 * nx + x1;
+                w00 = (1 - wx) * (1 - wy);
+                w01 = wx * (1 - wy);
+                w10 = (1 - wx) * wy;
+                w11 = wx * wy;
+            }
         }
         real sw = 0;
         if (valid) {
-            real nu;
-            const real *f = uk;
-            if (q == 0) nu = f[t * ns + pix + 1] - f[t * ns + pix];
-            else if (q == 1) nu = f[t * ns + pix + nx] - f[t * ns + pix];
-            else nu = f[fa + pix] - bil_sample(f + fb, nx, x0, x1, y0, y1, wx, wy);
+            const real nu = uk[oc] - (w00 * uk[o00] + w01 * uk[o01] + w10 * uk[o10] + w11 * uk[o11]);
             sw = (real)1 / sqrt(sqrt(nu * nu + eps2));
         }
-        real *Arow = A + tid * Ks;
-        for (int j = 0; j < K; ++j) {
-            real val = 0;
-            if (valid) {
-                const real *f = V + (long long)j * n;
-                if (q == 0) val = f[t * ns + pix + 1] - f[t * ns + pix];
-                else if (q == 1) val = f[t * ns + pix + nx] - f[t * ns + pix];
-                else val = f[fa + pix] - bil_sample(f + fb, nx, x0, x1, y0, y1, wx, wy);
+        const real *f = V;
+        for (int j = 0; j < K4 * 4; j += 4, f += 4 * n) {
+            real val[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                val[u] = 0;
+                if (valid && j + u < K) {
+                    const real *fu = f + (long long)u * n;
+                    val[u] = fu[oc] - (w00 * fu[o00] + w01 * fu[o01] + w10 * fu[o10] + w11 * fu[o11]);
+                }
             }
-            Arow[j] = sw * val;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) As[(j + u) * TG_S + tid] = sw * val[u];
         }
-        for (int j = K; j < K4 * 4; ++j) Arow[j] = 0;
         __syncthreads();
-        if (blk < nblk) {
+        if (acc_on) {
             real acc[4][4];
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
                 for (int c = 0; c < 4; ++c) acc[a][c] = 0;
-            const real *rowp = A + (long long)group * rows_per_group * Ks;
-            for (int rr = 0; rr < rows_per_group; ++rr, rowp += Ks) {
-                real va[4], vb[4];
-                if constexpr (sizeof(real) == 4) {
-                    const float4 fa4 = *reinterpret_cast<const float4 *>(rowp + 4 * I);
-                    const float4 fb4 = *reinterpret_cast<const float4 *>(rowp + 4 * J);
-                    va[0] = fa4.x; va[1] = fa4.y; va[2] = fa4.z; va[3] = fa4.w;
-                    vb[0] = fb4.x; vb[1] = fb4.y; vb[2] = fb4.z; vb[3] = fb4.w;
-                } else {
+            const real *pa = As + 4 * I * TG_S, *pb = As + 4 * J * TG_S;
+            for (int r = r0; r < r1; r += 4) {
+                Quad<real> va[4], vb[4];
 #pragma unroll
-                    for (int a = 0; a < 4; ++a) {
-                        va[a] = rowp[4 * I + a];
-                        vb[a] = rowp[4 * J + a];
-                    }
+                for (int a = 0; a < 4; ++a) {
+                    va[a] = load_quad(pa + a * TG_S + r);
+                    vb[a] = load_quad(pb + a * TG_S + r);
                 }
 #pragma unroll
                 for (int a = 0; a < 4; ++a)
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) acc[a][c] += va[a] * vb[c];
+                    for (int c = 0; c < 4; ++c)
+                        acc[a][c] += va[a].x * vb[c].x + va[a].y * vb[c].y + va[a].z * vb[c].z + va[a].w * vb[c].w;
             }
-            // Kahan-compensated carry of the tile sums
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -694,25 +719,34 @@ __global__ void __launch_bounds__(TG_T) k_theta_gram(const real *__restrict__ V,
         }
         __syncthreads();
     }
-    // partial[blockIdx.x * G + group][i][j] for this thread's block (upper triangle)
-    if (blk < nblk) {
-        double *out = partial + ((long long)blockIdx.x * G + group) * Kmax * Kmax;
+    // combine the row groups in FP64 (the tile buffer is free now), one partial per CTA
+    double *red = reinterpret_cast<double *>(smraw);  // [RG][nblk][16]
+    if (acc_on) {
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int i = 4 * I + a, jj = 4 * J + c;
-                if (i < K && jj < K && i <= jj) out[i * Kmax + jj] = (double)sum[a][c] - (double)comp[a][c];
-            }
+            for (int c = 0; c < 4; ++c) red[((long long)g * nblk + blk) * 16 + a * 4 + c] = (double)sum[a][c] - (double)comp[a][c];
+    }
+    __syncthreads();
+    double *out = partial + (long long)blockIdx.x * Kmax * Kmax;
+    for (int e = tid; e < nblk * 16; e += TG_T) {
+        const int b = e >> 4, el = e & 15;
+        int bi = 0, rem = b;
+        while (rem >= K4 - bi) {
+            rem -= K4 - bi;
+            ++bi;
+        }
+        const int i = 4 * bi + (el >> 2), jj = 4 * (bi + rem) + (el & 3);
+        double v = 0.0;
+        for (int gg = 0; gg < RG; ++gg) v += red[((long long)gg * nblk + b) * 16 + el];
+        if (i < K && jj < K && i <= jj) out[i * Kmax + jj] = v;
     }
 }
 
-// G[i][j] = sum over all block partials (upper triangle), mirrored
-__global__ void k_gram_reduce(const double *__restrict__ partial, int nblocks, int Kmax, const int *__restrict__ Kp,
+// G[i][j] = sum over the per-CTA partials (upper triangle), mirrored
+__global__ void k_gram_reduce(const double *__restrict__ partial, int nparts, int Kmax, const int *__restrict__ Kp,
                               double *__restrict__ G) {
     const int K = min(Kp[0], Kmax);
-    const int groups = tg_groups(K);
-    const int nparts = nblocks * groups;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < K * K; e += gridDim.x * blockDim.x) {
         const int i = e / K, j = e % K;
         if (i > j) continue;
