@@ -156,14 +156,15 @@ class Clocks:
 # ------------------------------------------------------------ roofline models
 def reorth_bytes(nvec_list, N, pairs, es=4):
     """Algorithmic bytes of the CGS2 reorthogonalisation and append of the Solve-OF
-    residuals over a solve, at the minimum a streaming implementation needs (the bases
-    do not fit on chip): c1 = V^T x reads K basis vectors and x; x' = x - V c1 together
-    with c2 = V^T x' reads K vectors and x and writes x'; x'' = x' - V c2 reads K vectors
-    and x' and writes x''; the append reads x'' and writes the new basis vector. That is
-    3K + 7 vectors of N values, K the basis size at each call, for every active pair."""
+    residuals over a solve. The first projection's coefficients come from the FP64
+    Gram matrices (V^T r = (G_A + gamma G_L) z - g), so the basis is streamed twice:
+    x' = x - V c1 together with c2 = V^T x' reads K basis vectors and x and writes x';
+    x'' = x' - V c2 reads K vectors and x' and writes x''; the append reads x'' and
+    writes the new basis vector. That is 2K + 6 vectors of N values, K the basis
+    size at each call, for every active pair."""
     tot = 0
     for K in nvec_list:
-        tot += pairs * es * N * (3 * K + 7)
+        tot += pairs * es * N * (2 * K + 6)
     return tot
 
 
@@ -277,11 +278,11 @@ def run_ours(args):
     step1_ms = sum(v[0] for v in class_ms.values())
     dominant = max(class_ms.items(), key=lambda kv: kv[1][0])[0] if class_ms else None
     roofline = {
-        "kernel": "of_reorth (CGS2 + append of the Solve-OF residuals: k_mdot, k_sub_dot, k_combine, k_append)",
+        "kernel": "of_reorth (CGS2 + append of the Solve-OF residuals: k_of_proj_gram, k_sub_dot, k_combine, k_append)",
         "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
         "frac": (achieved / hbm_peak) if achieved else None, "traffic": None,
         "peak_source": peak_src,
-        "bytes_model": "3K+7 vectors of 2*n*n FP32 per pair and GKS iteration",
+        "bytes_model": "2K+6 vectors of 2*n*n FP32 per pair and GKS iteration",
         "measured": "class time from one instrumented single-stream step after the timed region",
         "share_of_single_stream_step": ro_ms / step1_ms if step1_ms else None,
         "largest_class_single_stream": dominant,

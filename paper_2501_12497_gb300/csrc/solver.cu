@@ -242,6 +242,15 @@ static size_t theta_gram_smem(int Kmax) {
     return tile > red ? tile : red;
 }
 
+// doubles of Krylov scratch per frame pair of Solve-OF: the Krylov kernels' chunk
+// partials, and the per-CTA partials of the Gram columns (of_ell columns at once)
+static long long of_partial_per_pair(const mof_problem *p, int Kof, int of_ell) {
+    const long long ns = p->ns;
+    const long long gram_chunks = (ns + 511) / 512;  // chunks of the FP64 Gram kernel (the smaller)
+    const long long gram = (long long)std::min(of_ell, Kof) * gram_chunks * (2LL * Kof + 1);
+    return std::max(krylov_partial_doubles(2 * ns, Kof), gram);
+}
+
 template <typename real>
 static mof_status ensure_ws(mof_problem *p, const mof_solver_params &prm, int n_outer, WS<real> *&w) {
     const int Kmax = prm.ell + n_outer;
@@ -259,7 +268,7 @@ static mof_status ensure_ws(mof_problem *p, const mof_solver_params &prm, int n_
     int dev_sms = 152;
     cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, p->device);
     w->gram_ctas = 2 * dev_sms;
-    const long long partial = std::max(krylov_partial_doubles(std::max(n, m), Kmax), P * krylov_partial_doubles(N2, Kof));
+    const long long partial = std::max(krylov_partial_doubles(std::max(n, m), Kmax), P * of_partial_per_pair(p, Kof, prm.of_ell));
     for (int pass = 0; pass < 2; ++pass) {
         Arena a;
         a.base = w->mem;
@@ -536,6 +545,192 @@ __global__ void k_of_resid(const real *__restrict__ ux, const real *__restrict__
     r[b * 2 * ns + ns + i] = ay * a - AtB[b * 2 * ns + ns + i] + g * lap_at(v + ns, nx, ny, x, y);
 }
 
+// First CGS projection of the GKS residual from the Gram matrices: with
+// r = (Ups^T Ups + gamma (L(+)L)^T (L(+)L)) V z - Ups^T b, V^T r = (G_A + gamma G_L) z - g
+// exactly, so the coefficients need no pass over V. One warp per pair.
+__global__ void k_of_proj_gram(const double *__restrict__ GA, const double *__restrict__ GL, const double *__restrict__ g,
+                               const double *__restrict__ z, const double *__restrict__ gam, const int *__restrict__ K,
+                               const int *__restrict__ act, int ld, double *__restrict__ c) {
+    const int b = blockIdx.x, lane = threadIdx.x;
+    if (!act[b]) return;
+    const int Kb = min(K[b], ld);
+    const double *A = GA + (long long)b * ld * ld, *L = GL + (long long)b * ld * ld, *zb = z + (long long)b * ld;
+    const double gm = gam[b];
+    for (int i = lane; i < Kb; i += 32) {
+        double sa = 0.0, sl = 0.0;
+        for (int k = 0; k < Kb; ++k) {
+            sa += A[i * ld + k] * zb[k];
+            sl += L[i * ld + k] * zb[k];
+        }
+        c[(long long)b * ld + i] = sa + gm * sl - g[(long long)b * ld + i];
+    }
+}
+
+// Gram columns of Solve-OF computed from V with the operators applied on the
+// fly: for column j and every i <= j,
+//   G_A[i][j] = (Ups v_i)^T (Ups v_j),  G_L[i][j] = (L v_i)^T (L v_j),  g[j] = (Ups v_j)^T b,
+// with Ups v = u_x v_x + u_y v_y pointwise and L the forward differences in x
+// and y of both velocity components (no boundary row), b = -u_t. Column j is
+// blockIdx.z (mode 0: the first columns, j < K) or K - 1 (mode 1: the vector
+// appended last, where appended). A CTA owns a chunk of OFC pixels of one pair:
+// it stages column j's five rows per pixel and u_x, u_y in shared memory, and
+// its warps stream the basis vectors i = w, w + 8, ... over the chunk, forming
+// their rows on the fly (coalesced loads), with FP32 sums per chunk in the
+// storage precision; k_of_gram_reduce adds the chunks in FP64.
+constexpr int OFG_T = 256;
+template <typename real>
+constexpr int ofc() { return 4096 / (int)sizeof(real); }  // pixels per chunk: 1024 (FP32), 512 (FP64)
+
+template <typename real>
+__device__ __forceinline__ void of_rows(const real *__restrict__ v, long long ns, int nx, int ny, int p, real ux, real uy,
+                                        real &a, real l[4]) {
+    const int y = p / nx, x = p - y * nx;
+    const real vx = v[p], vy = v[ns + p];
+    a = ux * vx + uy * vy;
+    const bool hx = x < nx - 1, hy = y < ny - 1;
+    l[0] = hx ? v[p + 1] - vx : (real)0;
+    l[1] = hy ? v[p + nx] - vx : (real)0;
+    l[2] = hx ? v[ns + p + 1] - vy : (real)0;
+    l[3] = hy ? v[ns + p + nx] - vy : (real)0;
+}
+
+template <typename real>
+__device__ __forceinline__ real warp_sum_r(real v) {
+    if constexpr (sizeof(real) == 4) return warp_sumf(v);
+    else return warp_sum(v);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(OFG_T) k_of_gram_cols(const real *__restrict__ V, int Kmax, const int *__restrict__ K,
+                                                        const int *__restrict__ act, int mode, const real *__restrict__ ux,
+                                                        const real *__restrict__ uy, const real *__restrict__ bof, int nx,
+                                                        int ny, double *__restrict__ partial) {
+    constexpr int OFC = ofc<real>();
+    __shared__ __align__(16) real s_a[OFC], s_l[4][OFC], s_ux[OFC], s_uy[OFC], s_hx[OFC], s_hy[OFC];
+    __shared__ real s_red[OFG_T / 32];
+    const int b = blockIdx.y, chunk = blockIdx.x, nchunk = gridDim.x;
+    if (!act[b]) return;
+    const int Kb = min(K[b], Kmax);
+    const int j = mode == 0 ? (int)blockIdx.z : Kb - 1;
+    if (j < 0 || j >= Kb) return;
+    const long long ns = (long long)nx * ny, N2 = 2 * ns;
+    const int c0 = chunk * OFC;
+    const int len = (int)min((long long)OFC, ns - c0);
+    const real *Vb = V + (long long)b * Kmax * N2;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    double *out = partial + (((long long)b * gridDim.z + blockIdx.z) * nchunk + chunk) * (2 * Kmax + 1);
+    // stage column j's rows, the fields and the boundary masks; g_j on the way
+    real gs = 0;
+    for (int q = tid; q < OFC; q += OFG_T) {
+        real a = 0, l[4] = {0, 0, 0, 0}, fx = 0, fy = 0, mx = 0, my = 0;
+        if (q < len) {
+            const int p = c0 + q;
+            const int y = p / nx, x = p - y * nx;
+            fx = ux[b * ns + p];
+            fy = uy[b * ns + p];
+            mx = x < nx - 1 ? (real)1 : (real)0;
+            my = y < ny - 1 ? (real)1 : (real)0;
+            of_rows(Vb + (long long)j * N2, ns, nx, ny, p, fx, fy, a, l);
+            gs += a * bof[b * ns + p];
+        }
+        s_a[q] = a;
+        s_l[0][q] = l[0];
+        s_l[1][q] = l[1];
+        s_l[2][q] = l[2];
+        s_l[3][q] = l[3];
+        s_ux[q] = fx;
+        s_uy[q] = fy;
+        s_hx[q] = mx;
+        s_hy[q] = my;
+    }
+    gs = warp_sum_r(gs);
+    if (lane == 0) s_red[wid] = gs;
+    __syncthreads();
+    if (tid == 0) {
+        double dg = 0.0;
+        for (int w = 0; w < OFG_T / 32; ++w) dg += (double)s_red[w];
+        out[2 * Kmax] = dg;
+    }
+    // 4 pixels per lane with 128-bit loads where the layout allows it (FP32, aligned
+    // rows, a full chunk); masked rows (x = nx-1 or y = ny-1) read in-bounds neighbours
+    // that the masks zero
+    const bool quad = sizeof(real) == 4 && (nx % 4) == 0 && len == OFC;
+    for (int i = wid; i <= j; i += OFG_T / 32) {
+        const real *vi = Vb + (long long)i * N2 + c0;
+        real ga = 0, gl = 0;
+        if (quad) {
+            const float *vf = reinterpret_cast<const float *>(vi);
+            for (int q = lane * 4; q < OFC; q += 128) {
+                const bool last_row = c0 + q + nx >= ns;  // this quad's y = ny-1
+                const float4 X = *reinterpret_cast<const float4 *>(vf + q);
+                const float4 Y = *reinterpret_cast<const float4 *>(vf + ns + q);
+                const float4 Xn = last_row ? X : *reinterpret_cast<const float4 *>(vf + q + nx);
+                const float4 Yn = last_row ? Y : *reinterpret_cast<const float4 *>(vf + ns + q + nx);
+                const bool row_end = ((c0 + q + 4) % nx) == 0;
+                const float x4 = row_end ? X.w : vf[q + 4], y4 = row_end ? Y.w : vf[ns + q + 4];
+                const float xs[5] = {X.x, X.y, X.z, X.w, x4}, ys[5] = {Y.x, Y.y, Y.z, Y.w, y4};
+                const float xn[4] = {Xn.x, Xn.y, Xn.z, Xn.w}, yn[4] = {Yn.x, Yn.y, Yn.z, Yn.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int qq = q + e;
+                    const float hx = s_hx[qq], hy = s_hy[qq];
+                    const float ai = s_ux[qq] * xs[e] + s_uy[qq] * ys[e];
+                    const float l0 = hx * (xs[e + 1] - xs[e]), l1 = hy * (xn[e] - xs[e]);
+                    const float l2 = hx * (ys[e + 1] - ys[e]), l3 = hy * (yn[e] - ys[e]);
+                    ga += ai * s_a[qq];
+                    gl += l0 * s_l[0][qq] + l1 * s_l[1][qq] + l2 * s_l[2][qq] + l3 * s_l[3][qq];
+                }
+            }
+        } else {
+            for (int q = lane; q < len; q += 32) {
+                const real hx = s_hx[q], hy = s_hy[q];
+                const real vx = vi[q], vy = vi[ns + q];
+                const real ai = s_ux[q] * vx + s_uy[q] * vy;
+                const real l0 = hx != 0 ? vi[q + 1] - vx : (real)0, l1 = hy != 0 ? vi[q + nx] - vx : (real)0;
+                const real l2 = hx != 0 ? vi[ns + q + 1] - vy : (real)0, l3 = hy != 0 ? vi[ns + q + nx] - vy : (real)0;
+                ga += ai * s_a[q];
+                gl += l0 * s_l[0][q] + l1 * s_l[1][q] + l2 * s_l[2][q] + l3 * s_l[3][q];
+            }
+        }
+        ga = warp_sum_r(ga);
+        gl = warp_sum_r(gl);
+        if (lane == 0) {
+            out[2 * i] = (double)ga;
+            out[2 * i + 1] = (double)gl;
+        }
+    }
+}
+
+// Sum the CTA partials of k_of_gram_cols in FP64 (one warp per output) and write
+// G_A[b][i][j] = G_A[b][j][i], G_L likewise, g[b][j].
+__global__ void k_of_gram_reduce(const double *__restrict__ partial, int nctas, int Kmax, const int *__restrict__ K,
+                                 const int *__restrict__ act, int mode, double *__restrict__ GA, double *__restrict__ GL,
+                                 double *__restrict__ g) {
+    const int b = blockIdx.y;
+    if (!act[b]) return;
+    const int Kb = min(K[b], Kmax);
+    const int j = mode == 0 ? (int)blockIdx.z : Kb - 1;
+    if (j < 0 || j >= Kb) return;
+    const int o = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    const int nout = 2 * (j + 1) + 1;
+    if (o >= nout) return;
+    const int slot = o == nout - 1 ? 2 * Kmax : o;
+    const double *src = partial + ((long long)b * gridDim.z + blockIdx.z) * nctas * (2 * Kmax + 1) + slot;
+    double sum = 0.0;
+    for (int c = lane; c < nctas; c += 32) sum += src[(long long)c * (2 * Kmax + 1)];
+    sum = warp_sum(sum);
+    if (lane != 0) return;
+    const long long KK = (long long)Kmax * Kmax;
+    if (o == nout - 1) {
+        g[(long long)b * Kmax + j] = sum;
+        return;
+    }
+    const int i = o >> 1;
+    double *G = (o & 1) ? GL : GA;
+    G[b * KK + (long long)i * Kmax + j] = sum;
+    G[b * KK + (long long)j * Kmax + i] = sum;
+}
+
 // AtB = Upsilon^T b with b = -u_t, and bof = -u_t
 template <typename real>
 __global__ void k_of_rhs(const real *__restrict__ ux, const real *__restrict__ uy, const real *__restrict__ ut,
@@ -802,7 +997,7 @@ static mof_status solve_of_impl(mof_problem *p, const mof_solver_params &prm, WS
     // are short launches, so the groups fill the GPU together. Every kernel works
     // per pair, so the grouping does not change the result.
     const int G = std::max(1, std::min(prm.of_streams > 0 ? prm.of_streams : AUTO_OF_STREAMS, P));
-    const long long part_pair = krylov_partial_doubles(N2, Kof);
+    const long long part_pair = of_partial_per_pair(p, Kof, w.of_ell);
     MOF_CUDA(cudaEventRecord(w.gfork, st));
     for (int gi = 0; gi < G; ++gi) {
         const int b0 = (int)((long long)gi * P / G), nb = (int)((long long)(gi + 1) * P / G) - b0;
@@ -814,7 +1009,6 @@ static mof_status solve_of_impl(mof_problem *p, const mof_solver_params &prm, WS
         kg.aux = w.kaux + 2LL * b0;
         const long long KK = (long long)Kof * Kof;
         real *Vg = w.Vof + (long long)b0 * Kof * N2, *sg = s_out + (long long)b0 * N2, *wvg = w.wv + (long long)b0 * N2;
-        real *vng = w.vnew_of + (long long)b0 * N2, *y1g = w.y1 + (long long)b0 * N2, *y2g = w.y2 + (long long)b0 * N2;
         real *Ug = w.Uof + (long long)b0 * ldU * ns, *wug = w.wu + (long long)b0 * ns;
         const real *uxg = w.ux + (long long)b0 * ns, *uyg = w.uy + (long long)b0 * ns, *AtBg = w.AtB + (long long)b0 * N2;
         const real *bofg = w.bof + (long long)b0 * ns;
@@ -845,18 +1039,17 @@ static mof_status solve_of_impl(mof_problem *p, const mof_solver_params &prm, WS
         }
         const dim3 gg((p->nx + 31) / 32, (p->ny + 7) / 8, nb);
         BasisRef<real> BAg{Vg, N2, Kof, nb, Kvg, actg};
+        const int gram_ctas = (int)((ns + ofc<real>() - 1) / ofc<real>());
+        const int gram_red = (2 * Kof + 1 + 7) / 8;
+        const real *bofg2 = w.bof + (long long)b0 * ns;
         {
             Scope sc(tm, "of_gram", gst);
-            for (int j = 0; j < prm.of_ell; ++j) {
-                ::mof::count_launch(), k_of_normal_parts<real><<<gg, blk2, 0, gst>>>(uxg, uyg, Vg + (long long)j * N2, (long long)Kof * N2, y1g, y2g,
-                                                              p->nx, p->ny, actg);
-                DotVecs<real> xs{{y1g, y2g, AtBg}, {N2, N2, N2}};
-                DotOuts o{};
-                o.o[0] = DotOut{w.GA + b0 * KK + j, KK, Kof, 0, 0, 1.0};
-                o.o[1] = DotOut{w.GL + b0 * KK + j, KK, Kof, 0, 0, 1.0};
-                o.o[2] = DotOut{w.gof + (long long)b0 * Kof, Kof, 1, 0, 0, 1.0};
-                kg.multidot(BAg, 3, xs, o, gst);
-            }
+            const int ncol = std::min(prm.of_ell, Kof);
+            ::mof::count_launch(), k_of_gram_cols<real><<<dim3(gram_ctas, nb, ncol), OFG_T, 0, gst>>>(Vg, Kof, Kvg, actg, 0, uxg, uyg, bofg2,
+                                                                                                   p->nx, p->ny, kg.partial);
+            ::mof::count_launch(), k_of_gram_reduce<<<dim3(gram_red, nb, ncol), 256, 0, gst>>>(kg.partial, gram_ctas, Kof, Kvg, actg, 0,
+                                                                                             w.GA + b0 * KK, w.GL + b0 * KK,
+                                                                                             w.gof + (long long)b0 * Kof);
         }
         SmallArgs sa{};
         sa.GA = w.GA + b0 * KK;
@@ -873,7 +1066,6 @@ static mof_status solve_of_impl(mof_problem *p, const mof_solver_params &prm, WS
         sa.flag = w.flag_of + b0;
         sa.err = w.err;
         BasisRef<real> BS{Vg, N2, Kof, nb, Kvg, nullptr};
-        BasisRef<real> BNg{Vg, N2, Kof, nb, Kvg, appg};
         for (int it = 0; it < prm.of_iters; ++it) {
             {
                 Scope sc(tm, "of_small", gst);
@@ -890,20 +1082,24 @@ static mof_status solve_of_impl(mof_problem *p, const mof_solver_params &prm, WS
             }
             {
                 Scope sc(tm, "of_reorth", gst);
-                kg.reorth(BAg, wvg, N2, w.coef_of + (long long)b0 * Kof, w.nrm_of + b0, gst);
-                kg.append(BAg, Kvg, wvg, N2, w.nrm_of + b0, w.scale_of + b0, tol, w.grow_of + b0, appg, vng, gst);
+                // CGS2: the first projection's coefficients from the Grams, the second by
+                // dot products (fused with the first update); then the second update
+                double *cg = w.coef_of + (long long)b0 * Kof;
+                ::mof::count_launch(), k_of_proj_gram<<<nb, 32, 0, gst>>>(sa.GA, sa.GL, sa.g, sa.z, sa.lam, Kvg, actg, Kof, cg);
+                if (!kg.sub_dot(BAg, cg, Kof, wvg, N2, cg, gst)) {
+                    kg.subtract(BAg, cg, Kof, wvg, N2, wvg, N2, nullptr, gst);
+                    kg.dots(BAg, wvg, N2, cg, Kof, 1.0, gst);
+                }
+                kg.subtract(BAg, cg, Kof, wvg, N2, wvg, N2, w.nrm_of + b0, gst);
+                kg.append(BAg, Kvg, wvg, N2, w.nrm_of + b0, w.scale_of + b0, tol, w.grow_of + b0, appg, nullptr, gst);
             }
             {
                 Scope sc(tm, "of_gram", gst);
-                ::mof::count_launch(), k_of_normal_parts<real><<<gg, blk2, 0, gst>>>(uxg, uyg, vng, N2, y1g, y2g, p->nx, p->ny, appg);
-                DotVecs<real> xs{{y1g, y2g, AtBg}, {N2, N2, N2}};
-                DotOuts o{};
-                o.o[0] = DotOut{w.GA + b0 * KK, KK, Kof, 1, 1, 1.0};
-                o.o[1] = DotOut{w.GL + b0 * KK, KK, Kof, 1, 1, 1.0};
-                o.o[2] = DotOut{w.gof + (long long)b0 * Kof, Kof, 1, 0, 0, 1.0};
-                kg.multidot(BNg, 3, xs, o, gst);
-                ::mof::count_launch(), k_sym_last<<<nb, 64, 0, gst>>>(w.GA + b0 * KK, Kof, Kvg, appg);
-                ::mof::count_launch(), k_sym_last<<<nb, 64, 0, gst>>>(w.GL + b0 * KK, Kof, Kvg, appg);
+                ::mof::count_launch(), k_of_gram_cols<real><<<dim3(gram_ctas, nb, 1), OFG_T, 0, gst>>>(Vg, Kof, Kvg, appg, 1, uxg, uyg, bofg2,
+                                                                                                    p->nx, p->ny, kg.partial);
+                ::mof::count_launch(), k_of_gram_reduce<<<dim3(gram_red, nb, 1), 256, 0, gst>>>(kg.partial, gram_ctas, Kof, Kvg, appg, 1,
+                                                                                              w.GA + b0 * KK, w.GL + b0 * KK,
+                                                                                              w.gof + (long long)b0 * Kof);
             }
         }
         MOF_CUDA(cudaEventRecord(w.gdone[gi], gst));
