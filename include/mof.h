@@ -140,6 +140,20 @@ mof_status mof_apply_flow(mof_problem *p, const void *u, const void *s, const vo
 mof_status mof_apply_flowT(mof_problem *p, const void *r, const void *s, const void *sr,
                            void *u, void *stream);
 
+/* Vector-Jacobian product of the flow residual r = Mhat(s, s') u (mof_apply_flow,
+ * Sec. 2.3) with respect to the velocities: for a cotangent gr (layout of r),
+ *   gs[t]  = -gr[0][t] * grad_s  B(u_{t+1}; x + s_t),
+ *   gsr[t] = -gr[1][t] * grad_s' B(u_t;     x + sr_t),
+ * with B the clipped bilinear sample: on the forward pass's cell,
+ * dB/dsx = (1-wy)(f01-f00) + wy(f11-f10), dB/dsy = (1-wx)(f10-f00) + wx(f11-f01),
+ * zero along an axis where the sample point is clipped (x + s < 0 or
+ * x + s >= n-1), the derivative from the right where x + s is an integer.
+ * u: n; s, sr: nv; gr: 2 (nt-1) ns; gs, gsr: nv (outputs). The image VJP of r
+ * is mof_apply_flowT; the projector's is mof_apply_AT. Used as the backward
+ * pass of the differentiable operators of the binding. */
+mof_status mof_apply_flow_ds(mof_problem *p, const void *u, const void *s, const void *sr, const void *gr,
+                             void *gs, void *gsr, void *stream);
+
 /* App. C derivative fields of every pair (u_p, u_{p+1}), box half-width dr,
  * image flipped about its edges:  ux = box-averaged central x-difference of
  * u_p, uy likewise in y, ut = box average of u_{p+1} - u_p. u: n; outputs (nt-1)*nx*ny. */

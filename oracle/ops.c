@@ -359,3 +359,55 @@ void orc_reverse_flow(int nx, int ny, int nt, const double *s, double *sr)
     }
     free(cnt);
 }
+
+/* Velocity derivative of the bilinear sample B(v; X, Y) at the clipped point
+ * X = clamp(x + sx, 0, nx-1), Y = clamp(y + sy, 0, ny-1) of warp_taps: on the
+ * cell (floor X, floor Y) the interpolant is bilinear, so
+ *   dB/dsx = (1 - fy) (v01 - v00) + fy (v11 - v10),
+ *   dB/dsy = (1 - fx) (v10 - v00) + fx (v11 - v01),
+ * taken on the cell floor(X) (the right derivative where x + sx is an integer),
+ * and zero along an axis where the clamp holds the sample point (x + sx < 0 or
+ * x + sx >= nx - 1: there the sample does not move with sx). */
+static void warp_grad(int nx, int ny, int x, int y, double sx, double sy, const double *v, double *gx, double *gy)
+{
+    const double Xu = x + sx, Yu = y + sy;
+    const double X = clampd(Xu, 0.0, nx - 1.0), Y = clampd(Yu, 0.0, ny - 1.0);
+    const int x0 = (int)floor(X), y0 = (int)floor(Y);
+    const int x1 = x0 + 1 < nx ? x0 + 1 : nx - 1;
+    const int y1 = y0 + 1 < ny ? y0 + 1 : ny - 1;
+    const double fx = X - x0, fy = Y - y0;
+    const double v00 = v[(size_t)y0 * nx + x0], v01 = v[(size_t)y0 * nx + x1];
+    const double v10 = v[(size_t)y1 * nx + x0], v11 = v[(size_t)y1 * nx + x1];
+    *gx = (Xu >= 0.0 && Xu < nx - 1.0) ? (1 - fy) * (v01 - v00) + fy * (v11 - v10) : 0.0;
+    *gy = (Yu >= 0.0 && Yu < ny - 1.0) ? (1 - fx) * (v10 - v00) + fx * (v11 - v01) : 0.0;
+}
+
+/* Vector-Jacobian product of r = Mhat(s, s') u (orc_flow) with respect to the
+ * velocities, for a cotangent gr[2][nt-1][ny][nx]: since
+ * r[0][p] = u_p - B(u_{p+1}; x + s_p) and r[1][p] = u_{p+1} - B(u_p; x + sr_p),
+ *   gs[p]  = -gr[0][p] * grad B(u_{p+1}; x + s_p)   (components x, y),
+ *   gsr[p] = -gr[1][p] * grad B(u_p;     x + sr_p).
+ * Layouts of s: gs, gsr [nt-1][2][ny][nx]. */
+void orc_flow_ds(int nx, int ny, int nt, const double *u, const double *s, const double *sr, const double *gr,
+                 double *gs, double *gsr)
+{
+    const size_t ns = (size_t)nx * ny;
+    const int np = nt - 1;
+    for (int p = 0; p < np; ++p) {
+        const double *u0 = u + p * ns, *u1 = u + (p + 1) * ns;
+        const double *sp = s + (size_t)(2 * p) * ns, *srp = sr + (size_t)(2 * p) * ns;
+        const double *g0 = gr + (size_t)p * ns, *g1 = gr + (size_t)(np + p) * ns;
+        double *os = gs + (size_t)(2 * p) * ns, *osr = gsr + (size_t)(2 * p) * ns;
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const size_t i = (size_t)y * nx + x;
+                double gx, gy;
+                warp_grad(nx, ny, x, y, sp[i], sp[ns + i], u1, &gx, &gy);
+                os[i] = -g0[i] * gx;
+                os[ns + i] = -g0[i] * gy;
+                warp_grad(nx, ny, x, y, srp[i], srp[ns + i], u0, &gx, &gy);
+                osr[i] = -g1[i] * gx;
+                osr[ns + i] = -g1[i] * gy;
+            }
+    }
+}

@@ -37,9 +37,10 @@ def _load():
         lib.orc_flow_lin.argtypes = [i, i, i, _D, _D, _D, _D, _D]
         lib.orc_flow_linT.argtypes = [i, i, i, _D, _D, _D, _D]
         lib.orc_reverse_flow.argtypes = [i, i, i, _D, _D]
+        lib.orc_flow_ds.argtypes = [i, i, i, _D, _D, _D, _D, _D, _D]
         for f in ("orc_project", "orc_backproject", "orc_grad", "orc_gradT", "orc_warp",
                   "orc_warpT", "orc_flow", "orc_flowT", "orc_of_fields", "orc_flow_lin",
-                  "orc_flow_linT", "orc_reverse_flow"):
+                  "orc_flow_linT", "orc_reverse_flow", "orc_flow_ds"):
             getattr(lib, f).restype = None
         _lib = lib
     return _lib
@@ -159,6 +160,17 @@ def flowT(r, s, sr):
     u = np.empty((npairs + 1, ny, nx))
     _load().orc_flowT(nx, ny, npairs + 1, _d(r), _d(s), _d(sr), _d(u))
     return u
+
+
+def flow_ds(u, s, sr, gr):
+    """Velocity VJP of Mhat(s, s') u for the cotangent gr (2, nt-1, ny, nx):
+    (gs, gsr), each (nt-1, 2, ny, nx)."""
+    u, s, sr, gr = _c64(u), _c64(s), _c64(sr), _c64(gr)
+    nt, ny, nx = u.shape
+    gs = np.empty((nt - 1, 2, ny, nx))
+    gsr = np.empty((nt - 1, 2, ny, nx))
+    _load().orc_flow_ds(nx, ny, nt, _d(u), _d(s), _d(sr), _d(gr), _d(gs), _d(gsr))
+    return gs, gsr
 
 
 def of_fields(u, dr=1):

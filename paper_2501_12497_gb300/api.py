@@ -60,6 +60,7 @@ _SIGS = {
     "mof_apply_flow": (ctypes.c_int, [ctypes.c_void_p] * 6),
     "mof_apply_flowT": (ctypes.c_int, [ctypes.c_void_p] * 6),
     "mof_apply_flowT_noalloc": (ctypes.c_int, [ctypes.c_void_p] * 6),
+    "mof_apply_flow_ds": (ctypes.c_int, [ctypes.c_void_p] * 8),
     "mof_of_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 4),
     "mof_apply_flow_lin": (ctypes.c_int, [ctypes.c_void_p] * 7),
     "mof_apply_flow_linT": (ctypes.c_int, [ctypes.c_void_p] * 6),
@@ -218,6 +219,13 @@ def mof_apply_flowT_noalloc(p, r, sv, sr, u, stream=None):
     s = _sizes(p)
     _check(_lib.mof_apply_flowT_noalloc(p.handle, _ptr(p, r, s["flow"], "r"), _ptr(p, sv, s["nv"], "s"),
                                         _ptr(p, sr, s["nv"], "sr"), _ptr(p, u, s["n"], "u"), _stream(stream)))
+
+
+def mof_apply_flow_ds(p, u, sv, sr, gr, gs, gsr, stream=None):
+    s = _sizes(p)
+    _check(_lib.mof_apply_flow_ds(p.handle, _ptr(p, u, s["n"], "u"), _ptr(p, sv, s["nv"], "s"), _ptr(p, sr, s["nv"], "sr"),
+                                  _ptr(p, gr, s["flow"], "gr"), _ptr(p, gs, s["nv"], "gs"), _ptr(p, gsr, s["nv"], "gsr"),
+                                  _stream(stream)))
 
 
 def mof_of_fields(p, u, dr, ux, uy, ut, stream=None):

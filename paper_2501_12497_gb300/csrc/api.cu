@@ -250,6 +250,15 @@ mof_status mof_apply_flowT(mof_problem *p, const void *r, const void *s, const v
     return launch_flowT<float>(p, CF(r), CF(s), CF(sr), rs, rr, F(u), S(stream));
 }
 
+mof_status mof_apply_flow_ds(mof_problem *p, const void *u, const void *s, const void *sr, const void *gr, void *gs,
+                             void *gsr, void *stream) {
+    g_err[0] = 0;
+    MOF_TRY(check_problem(p));
+    if (!u || !s || !sr || !gr || !gs || !gsr) return fail(MOF_EINVAL, "null array");
+    return DISPATCH(p, launch_flow_ds<float>(p, CF(u), CF(s), CF(sr), CF(gr), F(gs), F(gsr), S(stream)),
+                    launch_flow_ds<double>(p, CD(u), CD(s), CD(sr), CD(gr), D(gs), D(gsr), S(stream)));
+}
+
 // Allocation-free Mhat^T: the tile radii live in a fixed device array
 // instead of the problem's lazily allocated workspace (include/mof.h states
 // the size limit, the one-time set-up and the concurrency rule).

@@ -90,6 +90,8 @@ template <typename real> mof_status launch_backproject(const mof_problem *p, con
 template <typename real> mof_status launch_grad(const mof_problem *p, int nf, const real *u, real *g, cudaStream_t st);
 template <typename real> mof_status launch_gradT(const mof_problem *p, int nf, const real *g, real *u, cudaStream_t st);
 template <typename real> mof_status launch_flow(const mof_problem *p, const real *u, const real *s, const real *sr, real *r, cudaStream_t st);
+// Velocity VJP of Mhat(s, s') u: gs, gsr = (d r / d s)^T gr, (d r / d s')^T gr.
+template <typename real> mof_status launch_flow_ds(const mof_problem *p, const real *u, const real *s, const real *sr, const real *gr, real *gs, real *gsr, cudaStream_t st);
 // Per-tile gather radii of the warp transposes (rad_* hold (nt-1) * tiles_count ints).
 int tiles_count(const mof_problem *p);
 template <typename real> mof_status launch_tile_radii(const mof_problem *p, const real *s, const real *sr, int *rad_s, int *rad_sr, cudaStream_t st);

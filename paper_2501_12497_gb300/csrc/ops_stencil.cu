@@ -246,6 +246,60 @@ mof_status launch_flowT(const mof_problem *p, const real *r, const real *s, cons
     return MOF_OK;
 }
 
+// ============================================================ K12 velocity VJP of Mhat
+// Derivative of the bilinear sample B(f; x + v) with respect to the displacement,
+// on the cell the forward pass uses: dB/dvx = (1 - wy)(f01 - f00) + wy (f11 - f10),
+// dB/dvy = (1 - wx)(f10 - f00) + wx (f11 - f01), and zero along an axis where
+// the sample point is clipped (x + v < 0 or x + v >= n - 1: the sample does not
+// move there). At an integer x + v this is the derivative from the right.
+template <typename real>
+__device__ __forceinline__ bool axis_moves(int x, real v, int n) {
+    if (!(v == v)) return false;
+    const real vc = v > (real)16777216 ? (real)16777216 : (v < (real)-16777216 ? (real)-16777216 : v);
+    const int I = x + (int)floor(vc);
+    return I >= 0 && I < n - 1;
+}
+
+template <typename real>
+__device__ __forceinline__ void bilinear_grad(const real *__restrict__ f, int nx, int ny, int x, int y, real vx, real vy,
+                                              real &gx, real &gy) {
+    int x0, x1, y0, y1;
+    real wx, wy;
+    warp_axis(x, vx, nx, x0, x1, wx);
+    warp_axis(y, vy, ny, y0, y1, wy);
+    const real a = ldg(f + (long long)y0 * nx + x0), b = ldg(f + (long long)y0 * nx + x1);
+    const real c = ldg(f + (long long)y1 * nx + x0), d = ldg(f + (long long)y1 * nx + x1);
+    gx = axis_moves(x, vx, nx) ? (1 - wy) * (b - a) + wy * (d - c) : (real)0;
+    gy = axis_moves(y, vy, ny) ? (1 - wx) * (c - a) + wx * (d - b) : (real)0;
+}
+
+// gs[t] = -gr[0][t] grad B(u_{t+1}; x + s_t), gsr[t] = -gr[1][t] grad B(u_t; x + sr_t):
+// the vector-Jacobian product of r = Mhat(s, s') u with respect to s and s'.
+template <typename real>
+__global__ void k_flow_ds(const real *__restrict__ u, const real *__restrict__ s, const real *__restrict__ sr,
+                          const real *__restrict__ gr, real *__restrict__ gs, real *__restrict__ gsr, int nx, int ny, int np) {
+    const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, t = blockIdx.z;
+    if (x >= nx || y >= ny) return;
+    const long long ns = (long long)nx * ny, i = (long long)y * nx + x;
+    const real g0 = gr[t * ns + i], g1 = gr[(np + t) * ns + i];
+    real gx, gy;
+    bilinear_grad(u + (t + 1) * ns, nx, ny, x, y, s[2 * t * ns + i], s[(2 * t + 1) * ns + i], gx, gy);
+    gs[2 * t * ns + i] = -g0 * gx;
+    gs[(2 * t + 1) * ns + i] = -g0 * gy;
+    bilinear_grad(u + t * ns, nx, ny, x, y, sr[2 * t * ns + i], sr[(2 * t + 1) * ns + i], gx, gy);
+    gsr[2 * t * ns + i] = -g1 * gx;
+    gsr[(2 * t + 1) * ns + i] = -g1 * gy;
+}
+
+template <typename real>
+mof_status launch_flow_ds(const mof_problem *p, const real *u, const real *s, const real *sr, const real *gr, real *gs,
+                          real *gsr, cudaStream_t st) {
+    ::mof::count_launch(), k_flow_ds<real><<<grid2d(p->nx, p->ny, p->nt - 1), dim3(TX, TY), 0, st>>>(u, s, sr, gr, gs, gsr, p->nx,
+                                                                                                   p->ny, p->nt - 1);
+    MOF_LAUNCH_CHECK();
+    return MOF_OK;
+}
+
 // ============================================================ K6 reverse flow
 // Destination of each source pixel, round half away from zero of r + s(r),
 // clipped. With v = fv + fr (fv = floor(v), fr in [0,1) exact) and
@@ -479,6 +533,8 @@ mof_status launch_reg_normal(const mof_problem *p, const real *x, const real *uk
     template mof_status launch_gradT<real>(const mof_problem *, int, const real *, real *, cudaStream_t);                     \
     template mof_status launch_flow<real>(const mof_problem *, const real *, const real *, const real *, real *, cudaStream_t); \
     template mof_status launch_tile_radii<real>(const mof_problem *, const real *, const real *, int *, int *, cudaStream_t);  \
+    template mof_status launch_flow_ds<real>(const mof_problem *, const real *, const real *, const real *, const real *,      \
+                                             real *, real *, cudaStream_t);                                                   \
     template mof_status launch_flowT<real>(const mof_problem *, const real *, const real *, const real *, const int *,         \
                                            const int *, real *, cudaStream_t);                                                \
     template mof_status launch_reverse_flow<real>(const mof_problem *, const real *, int *, int *, real *, cudaStream_t);     \

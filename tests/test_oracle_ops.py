@@ -322,3 +322,60 @@ def test_reverse_flow_rounding_and_averaging():
     s2 = np.zeros((1, 2, 1, 3))
     s2[0, 0, 0] = [-0.5, 0.0, 0.0]   # round(-0.5) = -1 -> clipped to 0
     np.testing.assert_allclose(ops.reverse_flow(s2)[0, 0, 0], [0.5, 0.0, 0.0])
+
+
+def _smooth_velocities(npairs, ny, nx, seed, vmax=2.5):
+    """Velocities whose sample points x + s keep 0.02 away from every integer and
+    from the clamp, so a central difference of step 1e-6 never crosses a kink."""
+    rng = np.random.default_rng(seed)
+    s = rng.uniform(-vmax, vmax, size=(npairs, 2, ny, nx))
+    frac = s - np.floor(s)
+    s = np.where(frac < 0.02, s + 0.02, s)
+    s = np.where(frac > 0.98, s - 0.02, s)
+    return s
+
+
+def test_flow_velocity_vjp_matches_central_differences():
+    """The velocity VJP of Mhat(s, s')u against FP64 central differences of
+    <gr, Mhat(s, s')u> along random directions (step 1e-6), sample points both
+    inside the grid and clipped at its edges (zero derivative there)."""
+    nt, ny, nx = 4, 13, 17
+    u = synth.random_images(nt, ny, nx, seed=31)
+    s = _smooth_velocities(nt - 1, ny, nx, seed=32)
+    sr = _smooth_velocities(nt - 1, ny, nx, seed=33)
+    rng = np.random.default_rng(34)
+    gr = rng.standard_normal((2, nt - 1, ny, nx))
+    gs, gsr = ops.flow_ds(u, s, sr, gr)
+    loss = lambda s_, sr_: float(np.sum(gr * ops.flow(u, s_, sr_)))
+    h = 1e-6
+    for k in range(6):
+        ds = rng.standard_normal(s.shape)
+        dsr = rng.standard_normal(sr.shape)
+        fd = (loss(s + h * ds, sr + h * dsr) - loss(s - h * ds, sr - h * dsr)) / (2 * h)
+        an = float(np.sum(gs * ds) + np.sum(gsr * dsr))
+        assert abs(fd - an) <= 1e-7 * max(1.0, abs(an)), (k, fd, an)
+
+
+def test_flow_velocity_vjp_is_zero_where_the_sample_is_clipped():
+    nt, ny, nx = 3, 8, 9
+    u = synth.random_images(nt, ny, nx, seed=35)
+    s = np.full((nt - 1, 2, ny, nx), 50.0)  # every sample point beyond the far edge
+    sr = np.full((nt - 1, 2, ny, nx), -50.0)  # and beyond the near edge
+    gr = np.ones((2, nt - 1, ny, nx))
+    gs, gsr = ops.flow_ds(u, s, sr, gr)
+    assert np.all(gs == 0) and np.all(gsr == 0)
+
+
+def test_flow_velocity_vjp_of_a_linear_image_is_its_slope():
+    """For u = a x + b y + c every interior bilinear sample moves with slope (a, b),
+    so gs = -gr (a, b) wherever the sample point is not clipped."""
+    nt, ny, nx = 2, 10, 12
+    a, b = 0.7, -1.3
+    yy, xx = np.mgrid[0:ny, 0:nx]
+    u = np.stack([a * xx + b * yy + 0.5] * nt).astype(float)
+    s = np.full((1, 2, ny, nx), 0.37)
+    gr = np.ones((2, 1, ny, nx))
+    gs, _ = ops.flow_ds(u, s, s, gr)
+    inside = (xx + 0.37 < nx - 1) & (yy + 0.37 < ny - 1)
+    np.testing.assert_allclose(gs[0, 0][inside], -a, atol=1e-12)
+    np.testing.assert_allclose(gs[0, 1][inside], -b, atol=1e-12)
