@@ -213,6 +213,32 @@ mof_status mof_solve_host(mof_problem *p, const mof_solver_params *prm, int n_ou
                           const void *b_host, void *u_host, void *s_host, void *sr_host,
                           mof_report *report, void *stream);
 
+/* Batched MMGKS-OF (Alg. 1) over `count` independent problems, each created
+ * on its own and of any size and precision: problems[i] with params[i] (its
+ * own noise level), device arrays b[i] (m_i) -> u_out[i] (n_i), s_out[i]
+ * (nv_i; s_out or any entry may be NULL), reports[i] (HOST, n_outer records;
+ * reports or any entry may be NULL). Each problem's outer iterations run on
+ * the problem's own streams, enqueued outer iteration by outer iteration
+ * across the batch, so the GPU works on many problems at once; every problem's
+ * result is the one mof_solve gives it (bit for bit). A problem may appear
+ * only once. Argument errors are returned before anything is enqueued;
+ * otherwise the call returns after all problems finished, with the first
+ * problem's error (its batch index in mof_last_error). */
+mof_status mof_solve_batch(mof_problem *const *problems, int count, const mof_solver_params *params, int n_outer,
+                           const void *const *b, void *const *u_out, void *const *s_out,
+                           mof_report *const *reports, void *stream);
+
+/* Autotuner of the execution parameter of_streams (the number of frame-pair
+ * groups Solve-OF runs on separate streams): times n_probe outer iterations of
+ * the batch (mof_solve_batch; count = 1 tunes a single problem) for each
+ * candidate in {1, 2, 4, 8} (at most the number of frame pairs), each after an
+ * untimed run that captures its graphs, and writes the fastest into every
+ * params[i].of_streams (and its time in milliseconds into *best_ms, may be
+ * NULL). u_scratch[i] (n_i, device) receives the probes' images. The result of
+ * a solve does not depend on of_streams, so tuning changes speed only. */
+mof_status mof_autotune(mof_problem *const *problems, int count, mof_solver_params *params, int n_probe,
+                        const void *const *b, void *const *u_scratch, double *best_ms, void *stream);
+
 /* Per-kernel-class device time of the last mof_solve when timing was
  * enabled with mof_set_timing(p, 1): fills up to `cap` entries of names
  * (static strings), milliseconds and launch counts; returns the number of

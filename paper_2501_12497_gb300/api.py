@@ -71,6 +71,8 @@ _SIGS = {
     "mof_solve_of": (ctypes.c_int, [ctypes.c_void_p] * 5),
     "mof_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 6),
     "mof_solve_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 6),
+    "mof_solve_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 5),
+    "mof_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 4),
     "mof_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "mof_get_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_void_p]),
@@ -309,6 +311,48 @@ def mof_solve_host(p, params, n_outer, b_host, u_host, s_host=None, sr_host=None
                                _host_ptr(p, u_host, s["n"], "u"), _host_ptr(p, s_host, s["nv"], "s", True),
                                _host_ptr(p, sr_host, s["nv"], "sr", True), rep, _stream(stream)))
     return _reports(rep)
+
+
+def _ptr_array(items):
+    arr = (ctypes.c_void_p * len(items))()
+    for i, v in enumerate(items):
+        arr[i] = v
+    return arr
+
+
+def mof_solve_batch(problems, params, n_outer, bs, us, ss=None, stream=None):
+    """Batched solve: lists of problems, params (one each), device b and u (and
+    optionally s) tensors. Returns one report list per problem."""
+    count = len(problems)
+    if not (len(params) == len(bs) == len(us) == count) or (ss is not None and len(ss) != count):
+        raise ValueError("batch lists must have one entry per problem")
+    sz = [_sizes(p) for p in problems]
+    pa = (mof_solver_params * count)(*params)
+    reps = [(mof_report * n_outer)() for _ in range(count)]
+    rp = _ptr_array([ctypes.cast(r, ctypes.c_void_p).value for r in reps])
+    handles = _ptr_array([p.handle.value for p in problems])
+    bp = _ptr_array([_ptr(p, b, z["m"], "b").value for p, b, z in zip(problems, bs, sz)])
+    up = _ptr_array([_ptr(p, u, z["n"], "u").value for p, u, z in zip(problems, us, sz)])
+    sp = None if ss is None else _ptr_array([_ptr(p, s_, z["nv"], "s").value for p, s_, z in zip(problems, ss, sz)])
+    _check(_lib.mof_solve_batch(handles, count, pa, int(n_outer), bp, up, sp, rp, _stream(stream)))
+    return [[{"lambda": r.lambda_, "resid": r.resid, "rnorm": r.rnorm, "basis": r.basis, "flag": r.flag,
+              "of_basis_min": r.of_basis_min, "of_basis_max": r.of_basis_max} for r in rep] for rep in reps]
+
+
+def mof_autotune(problems, params, n_probe, bs, us, stream=None):
+    """Tunes of_streams for the batch in place (params is a list of mof_solver_params);
+    returns the chosen value and the probe time in ms."""
+    count = len(problems)
+    sz = [_sizes(p) for p in problems]
+    pa = (mof_solver_params * count)(*params)
+    handles = _ptr_array([p.handle.value for p in problems])
+    bp = _ptr_array([_ptr(p, b, z["m"], "b").value for p, b, z in zip(problems, bs, sz)])
+    up = _ptr_array([_ptr(p, u, z["n"], "u").value for p, u, z in zip(problems, us, sz)])
+    ms = ctypes.c_double()
+    _check(_lib.mof_autotune(handles, count, pa, int(n_probe), bp, up, ctypes.byref(ms), _stream(stream)))
+    for i in range(count):
+        params[i].of_streams = pa[i].of_streams
+    return pa[0].of_streams, ms.value
 
 
 def mof_set_timing(p, enable):

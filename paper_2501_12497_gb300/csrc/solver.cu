@@ -8,6 +8,7 @@
 #include "solver.cuh"
 
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <type_traits>
 #include <string>
@@ -1110,28 +1111,64 @@ static mof_status solve_of_impl(mof_problem *p, const mof_solver_params &prm, WS
 }
 
 // ============================================================ MMGKS-OF
+// One MMGKS-OF solve (Alg. 1) as phases, so that several problems can be
+// interleaved on their own streams (mof_solve_batch): begin() enqueues the set-up
+// and the GKB start, step(k) outer iteration k (captured once per variant into a
+// CUDA graph and replayed), end() the copies of the results, result() reads the
+// report and the device error word after the stream has finished. Every
+// data-dependent decision is taken on the device, so nothing synchronises the
+// host before end().
 template <typename real>
-static mof_status solve_impl(mof_problem *p, const mof_solver_params &prm, int n_outer, const real *b_in, real *u_out,
-                             real *s_out, real *sr_out, mof_report *report, cudaStream_t ust) {
+struct SolveRun {
+    mof_problem *p = nullptr;
+    mof_solver_params prm{};
+    int n_outer = 0;
+    const real *b_in = nullptr;
+    real *u_out = nullptr, *s_out = nullptr, *sr_out = nullptr;
+    mof_report *report = nullptr;
+    WS<real> *wp = nullptr;
+    Timer *tm = nullptr;
+    cudaStream_t st = nullptr;
+    long long n = 0, m = 0, ns = 0;
+    int P = 0, Kmax = 0;
+    double tol = 0;
+    Krylov<real> kr;
+    size_t tg_smem = 0;
+    SmallArgs sa{};
+    real eps2 = 0;
+    std::vector<double> rep;
+    int err = 0;
+
+    mof_status begin(cudaStream_t ust);
+    mof_status iteration(bool of_now, bool expand);
+    mof_status step(int k);
+    mof_status end();
+    mof_status result();
+};
+
+template <typename real>
+mof_status SolveRun<real>::begin(cudaStream_t ust) {
     Holder *h = holder(p);
-    WS<real> *&wp = ws_slot<real>(h);
-    MOF_TRY(ensure_ws<real>(p, prm, n_outer, wp));
+    WS<real> *&slot = ws_slot<real>(h);
+    MOF_TRY(ensure_ws<real>(p, prm, n_outer, slot));
+    wp = slot;
     WS<real> &w = *wp;
     // all work runs on the problem's own stream, ordered after the caller's stream
-    const cudaStream_t st = w.ss;
+    st = w.ss;
     MOF_CUDA(cudaEventRecord(w.join, ust));
     MOF_CUDA(cudaStreamWaitEvent(st, w.join, 0));
-    Timer *tm = p->timing ? &h->timer : nullptr;
+    tm = p->timing ? &h->timer : nullptr;
     if (tm) tm->reset();
-    const long long n = p->n, m = p->m, ns = p->ns;
-    const int P = p->nt - 1;
-    const int Kmax = w.Kmax;
-    const double tol = prm.breakdown_tol > 0 ? prm.breakdown_tol : (sizeof(real) == 8 ? 1e-10 : 1e-6);
-    Krylov<real> kr;
+    n = p->n;
+    m = p->m;
+    ns = p->ns;
+    P = p->nt - 1;
+    Kmax = w.Kmax;
+    tol = prm.breakdown_tol > 0 ? prm.breakdown_tol : (sizeof(real) == 8 ? 1e-10 : 1e-6);
     kr.partial = w.partial;
     kr.err = w.err;
     kr.aux = w.kaux;
-    const size_t tg_smem = theta_gram_smem<real>(Kmax);
+    tg_smem = theta_gram_smem<real>(Kmax);
     MOF_CUDA(cudaFuncSetAttribute(k_theta_gram<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tg_smem));
 
     BasisRef<real> BV{w.V, n, Kmax, 1, w.K, nullptr};
@@ -1182,7 +1219,7 @@ static mof_status solve_impl(mof_problem *p, const mof_solver_params &prm, int n
             kr.multidot(BH, 2, xs, o, st);
         }
     }
-    SmallArgs sa{};
+    sa = SmallArgs{};
     sa.GA = w.GH;
     sa.GL = w.GT;
     sa.g = w.gH;
@@ -1198,10 +1235,23 @@ static mof_status solve_impl(mof_problem *p, const mof_solver_params &prm, int n
     sa.z = w.z;
     sa.flag = w.flag;
     sa.err = w.err;
-    const real eps2 = (real)(prm.eps * prm.eps);
-    // One outer iteration of Alg. 1 (k is tracked on the device); enqueued directly
-    // or captured once per variant into a CUDA graph and replayed.
-    auto iteration = [&](bool of_now, bool expand) -> mof_status {
+    eps2 = (real)(prm.eps * prm.eps);
+    if (std::memcmp(&w.gkey, &prm, sizeof(prm)) != 0 || w.gkey_n != n_outer) {
+        w.drop_graphs();
+        w.gkey = prm;
+        w.gkey_n = n_outer;
+    }
+    MOF_TRY(prepare_small_solve(Kmax));
+    MOF_TRY(prepare_small_solve(w.Kof));
+    return MOF_OK;
+}
+
+// One outer iteration of Alg. 1 (k is tracked on the device).
+template <typename real>
+mof_status SolveRun<real>::iteration(bool of_now, bool expand) {
+    WS<real> &w = *wp;
+    BasisRef<real> BV{w.V, n, Kmax, 1, w.K, nullptr};
+    BasisRef<real> BH{w.HV, m, Kmax, 1, w.K, nullptr};
         if (of_now) {
             MOF_TRY(solve_of_impl<real>(p, prm, w, w.u, w.s, tm, st));
             Scope sc(tm, "reverse_flow", st);
@@ -1262,62 +1312,68 @@ static mof_status solve_impl(mof_problem *p, const mof_solver_params &prm, int n
         }
         MOF_LAUNCH_CHECK();
         return MOF_OK;
-    };
-    if (std::memcmp(&w.gkey, &prm, sizeof(prm)) != 0 || w.gkey_n != n_outer) {
-        w.drop_graphs();
-        w.gkey = prm;
-        w.gkey_n = n_outer;
-    }
-    MOF_TRY(prepare_small_solve(Kmax));
-    MOF_TRY(prepare_small_solve(w.Kof));
-    for (int k = 0; k < n_outer; ++k) {
-        const bool of_now = prm.tau > 0 && (k % prm.tau) == 0;
-        const bool expand = k < n_outer - 1;
-        auto &G = w.graphs[(of_now ? 1 : 0) | (expand ? 2 : 0) | (tm ? 4 : 0)];
-        if (!G.exec) {
-            if (tm) {
-                tm->sink = &G.ev;
-                tm->owned = &G.owned;
-            }
-            const long long before = launches_so_far();
-            MOF_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-            const mof_status cs = iteration(of_now, expand);
-            cudaGraph_t graph = nullptr;
-            const cudaError_t ce = cudaStreamEndCapture(st, &graph);
-            G.kernels = launches_so_far() - before;
-            count_launches_add(-G.kernels);  // captured, not executed
-            if (tm) {
-                tm->sink = nullptr;
-                tm->owned = nullptr;
-            }
-            if (cs != MOF_OK || ce != cudaSuccess) {
-                if (graph) cudaGraphDestroy(graph);
-                w.drop_graphs();
-                if (cs != MOF_OK) return cs;
-                return cuda_fail(ce, "graph capture of an outer iteration", __FILE__, __LINE__);
-            }
-            const cudaError_t ie = cudaGraphInstantiate(&G.exec, graph, 0);
-            cudaGraphDestroy(graph);
-            if (ie != cudaSuccess) {
-                G.exec = nullptr;
-                return cuda_fail(ie, "graph instantiation", __FILE__, __LINE__);
-            }
-        }
-        MOF_CUDA(cudaGraphLaunch(G.exec, st));
-        count_launches_add(G.kernels);
+}
+
+template <typename real>
+mof_status SolveRun<real>::step(int k) {
+    WS<real> &w = *wp;
+    const bool of_now = prm.tau > 0 && (k % prm.tau) == 0;
+    const bool expand = k < n_outer - 1;
+    auto &G = w.graphs[(of_now ? 1 : 0) | (expand ? 2 : 0) | (tm ? 4 : 0)];
+    if (!G.exec) {
         if (tm) {
-            MOF_CUDA(cudaStreamSynchronize(st));
-            tm->collect_list(G.ev);
+            tm->sink = &G.ev;
+            tm->owned = &G.owned;
+        }
+        const long long before = launches_so_far();
+        MOF_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        const mof_status cs = iteration(of_now, expand);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+        G.kernels = launches_so_far() - before;
+        count_launches_add(-G.kernels);  // captured, not executed
+        if (tm) {
+            tm->sink = nullptr;
+            tm->owned = nullptr;
+        }
+        if (cs != MOF_OK || ce != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            w.drop_graphs();
+            if (cs != MOF_OK) return cs;
+            return cuda_fail(ce, "graph capture of an outer iteration", __FILE__, __LINE__);
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&G.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) {
+            G.exec = nullptr;
+            return cuda_fail(ie, "graph instantiation", __FILE__, __LINE__);
         }
     }
+    MOF_CUDA(cudaGraphLaunch(G.exec, st));
+    count_launches_add(G.kernels);
+    if (tm) {
+        MOF_CUDA(cudaStreamSynchronize(st));
+        tm->collect_list(G.ev);
+    }
+    return MOF_OK;
+}
+
+template <typename real>
+mof_status SolveRun<real>::end() {
+    WS<real> &w = *wp;
     MOF_LAUNCH_CHECK();
     if (u_out) MOF_CUDA(cudaMemcpyAsync(u_out, w.u, sizeof(real) * n, cudaMemcpyDeviceToDevice, st));
     if (s_out) MOF_CUDA(cudaMemcpyAsync(s_out, w.s, sizeof(real) * 2 * P * ns, cudaMemcpyDeviceToDevice, st));
     if (sr_out) MOF_CUDA(cudaMemcpyAsync(sr_out, w.sr, sizeof(real) * 2 * P * ns, cudaMemcpyDeviceToDevice, st));
-    std::vector<double> rep((size_t)n_outer * 8);
-    int err = 0;
+    rep.assign((size_t)n_outer * 8, 0.0);
+    err = 0;
     MOF_CUDA(cudaMemcpyAsync(rep.data(), w.report, sizeof(double) * rep.size(), cudaMemcpyDeviceToHost, st));
     MOF_CUDA(cudaMemcpyAsync(&err, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    return MOF_OK;
+}
+
+template <typename real>
+mof_status SolveRun<real>::result() {
     MOF_CUDA(cudaStreamSynchronize(st));
     if (tm) tm->collect();
     if (report)
@@ -1334,6 +1390,24 @@ static mof_status solve_impl(mof_problem *p, const mof_solver_params &prm, int n
     if (err & 4) return fail(MOF_ETIMEOUT, "a bounded device wait ran out (code %d)", err);
     if (err) return fail(MOF_ENUMERIC, "device reported a numerical failure (code %d): factorisation or non-finite value", err);
     return MOF_OK;
+}
+
+template <typename real>
+static mof_status solve_impl(mof_problem *p, const mof_solver_params &prm, int n_outer, const real *b_in, real *u_out,
+                             real *s_out, real *sr_out, mof_report *report, cudaStream_t ust) {
+    SolveRun<real> run;
+    run.p = p;
+    run.prm = prm;
+    run.n_outer = n_outer;
+    run.b_in = b_in;
+    run.u_out = u_out;
+    run.s_out = s_out;
+    run.sr_out = sr_out;
+    run.report = report;
+    MOF_TRY(run.begin(ust));
+    for (int k = 0; k < n_outer; ++k) MOF_TRY(run.step(k));
+    MOF_TRY(run.end());
+    return run.result();
 }
 
 template <typename real>
@@ -1399,6 +1473,123 @@ mof_status mof_solve(mof_problem *p, const mof_solver_params *prm, int n_outer, 
                                   report, st);
     return solve_impl<float>(p, *prm, n_outer, (const float *)b, (float *)u_out, (float *)s_out, (float *)sr_out, report,
                              st);
+}
+
+// One problem of a batch in either precision.
+struct AnyRun {
+    int fp64 = 0;
+    SolveRun<float> f;
+    SolveRun<double> d;
+    mof_status begin(cudaStream_t st) { return fp64 ? d.begin(st) : f.begin(st); }
+    mof_status step(int k) { return fp64 ? d.step(k) : f.step(k); }
+    mof_status end() { return fp64 ? d.end() : f.end(); }
+    mof_status result() { return fp64 ? d.result() : f.result(); }
+};
+
+static mof_status check_batch(mof_problem *const *ps, int count, const mof_solver_params *prm, int n_outer,
+                              const void *const *b, void *const *u_out) {
+    if (!ps || !prm || !b || !u_out) return fail(MOF_EINVAL, "null batch array");
+    if (count < 1) return fail(MOF_EINVAL, "batch count must be >= 1");
+    for (int i = 0; i < count; ++i) {
+        if (!ps[i] || !b[i] || !u_out[i]) return fail(MOF_EINVAL, "null problem, b or u_out at batch index %d", i);
+        for (int j = 0; j < i; ++j)
+            if (ps[j] == ps[i]) return fail(MOF_EINVAL, "problem at batch index %d repeats index %d", i, j);
+        const mof_status st = check_params(ps[i], &prm[i], n_outer);
+        if (st != MOF_OK) return st;
+    }
+    return MOF_OK;
+}
+
+// Enqueue every problem's solve, interleaved outer iteration by outer iteration on
+// the problems' own streams, then wait for all of them.
+static mof_status batch_run(mof_problem *const *ps, int count, const mof_solver_params *prm, int n_outer,
+                            const void *const *b, void *const *u_out, void *const *s_out, mof_report *const *reports,
+                            cudaStream_t st) {
+    std::vector<AnyRun> runs((size_t)count);
+    for (int i = 0; i < count; ++i) {
+        AnyRun &r = runs[i];
+        r.fp64 = ps[i]->precision == MOF_FP64;
+        void *so = s_out ? s_out[i] : nullptr;
+        mof_report *rep = reports ? reports[i] : nullptr;
+        if (r.fp64) {
+            r.d.p = ps[i];
+            r.d.prm = prm[i];
+            r.d.n_outer = n_outer;
+            r.d.b_in = (const double *)b[i];
+            r.d.u_out = (double *)u_out[i];
+            r.d.s_out = (double *)so;
+            r.d.report = rep;
+        } else {
+            r.f.p = ps[i];
+            r.f.prm = prm[i];
+            r.f.n_outer = n_outer;
+            r.f.b_in = (const float *)b[i];
+            r.f.u_out = (float *)u_out[i];
+            r.f.s_out = (float *)so;
+            r.f.report = rep;
+        }
+        MOF_TRY(r.begin(st));
+    }
+    for (int k = 0; k < n_outer; ++k)
+        for (auto &r : runs) MOF_TRY(r.step(k));
+    for (auto &r : runs) MOF_TRY(r.end());
+    mof_status first = MOF_OK;
+    for (int i = 0; i < count; ++i) {
+        const mof_status rs = runs[i].result();
+        if (rs != MOF_OK && first == MOF_OK) {
+            char msg[512];
+            std::snprintf(msg, sizeof(msg), "%s", mof_last_error());
+            first = fail(rs, "batch index %d: %s", i, msg);
+        }
+    }
+    return first;
+}
+
+mof_status mof_solve_batch(mof_problem *const *problems, int count, const mof_solver_params *params, int n_outer,
+                           const void *const *b, void *const *u_out, void *const *s_out, mof_report *const *reports,
+                           void *stream) {
+    MOF_TRY(check_batch(problems, count, params, n_outer, b, u_out));
+    return batch_run(problems, count, params, n_outer, b, u_out, s_out, reports, reinterpret_cast<cudaStream_t>(stream));
+}
+
+mof_status mof_autotune(mof_problem *const *problems, int count, mof_solver_params *params, int n_probe,
+                        const void *const *b, void *const *u_scratch, double *best_ms, void *stream) {
+    if (n_probe < 1) return fail(MOF_EINVAL, "n_probe must be >= 1");
+    MOF_TRY(check_batch(problems, count, params, n_probe, b, u_scratch));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int maxp = 1;
+    for (int i = 0; i < count; ++i) maxp = std::max(maxp, problems[i]->nt - 1);
+    std::vector<mof_solver_params> trial(params, params + count);
+    cudaEvent_t e0, e1;
+    MOF_CUDA(cudaEventCreate(&e0));
+    MOF_CUDA(cudaEventCreate(&e1));
+    int best = -1;
+    float best_t = 0.0f;
+    mof_status out = MOF_OK;
+    for (int g : {1, 2, 4, 8}) {
+        if (g > maxp && g != 1) continue;
+        for (auto &t : trial) t.of_streams = g;
+        // the first run captures the graphs of this configuration; the second is timed
+        out = batch_run(problems, count, trial.data(), n_probe, b, u_scratch, nullptr, nullptr, st);
+        if (out != MOF_OK) break;
+        if (cudaEventRecord(e0, st) != cudaSuccess) break;
+        out = batch_run(problems, count, trial.data(), n_probe, b, u_scratch, nullptr, nullptr, st);
+        if (out != MOF_OK) break;
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float t = 0.0f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (best < 0 || t < best_t) {
+            best = g;
+            best_t = t;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (out != MOF_OK) return out;
+    for (int i = 0; i < count; ++i) params[i].of_streams = best;
+    if (best_ms) *best_ms = best_t;
+    return MOF_OK;
 }
 
 mof_status mof_solve_host(mof_problem *p, const mof_solver_params *prm, int n_outer, const void *b_host, void *u_host,

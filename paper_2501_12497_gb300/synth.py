@@ -209,6 +209,21 @@ def differentiation_form(seed=0):
     return moving_disks(256, 32, 16, 256, radii=(32.0, 48.0), seed=seed, name="disks256x256x32")
 
 
+def batch_form(count=48, seed=0, sizes=(128, 192, 256, 384, 512), nt_range=(8, 40), na_range=(10, 45)):
+    """Independent problems of uneven size: for each, seeded n from `sizes`, T and
+    angles per frame uniform in the given ranges, ceil(sqrt(2) n) bins, and the
+    moving-ellipse generator (rigid motion up to 2 px/frame, 1% noise)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.choice(sizes))
+        nt = int(rng.integers(nt_range[0], nt_range[1] + 1))
+        na = int(rng.integers(na_range[0], na_range[1] + 1))
+        nb = int(math.ceil(math.sqrt(2) * n))
+        out.append(moving_ellipses(n, nt, na, nb, seed=1000 * seed + i, name="batch%d_%dx%dx%d" % (i, n, n, nt)))
+    return out
+
+
 # ------------------------------------------------------- generic random inputs
 
 def random_images(nt, ny, nx, seed=0, smooth=2):
