@@ -41,6 +41,10 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["ellipses256x256x32", "batch48", "ellipses1024x1024x64"],
+                    default="ellipses256x256x32",
+                    help="the 256x256x32 ellipse problem (default), 48 uneven problems batched, "
+                         "or the 1024x1024x64 problem")
     ap.add_argument("--of-streams", type=int, default=0,
                     help="frame-pair groups of Solve-OF on separate streams (0 = library default)")
     return ap.parse_args()
@@ -320,10 +324,113 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batch(args):
+    """48 independent problems of uneven size (n in {128..512}, T in [8, 40], 10-45
+    angles, ceil(sqrt(2) n) bins): the batched solve (mof_solve_batch, of_streams
+    chosen by mof_autotune) against the same problems solved one after another with
+    mof_solve. Metric: outer iterations per second summed over the problems."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2501_12497_gb300 import api, synth
+    api.load()
+    ws = synth.batch_form(count=48, seed=0)
+    probs, params, bs, us = [], [], [], []
+    for w in ws:
+        p = api.mof_problem_create(w.nx, w.ny, w.nt, w.nb, w.na, w.angles, precision=api.MOF_FP32)
+        probs.append(p)
+        params.append(api.mof_default_params(noise_norm=w.noise_norm))
+        bs.append(torch.tensor(w.b.astype(np.float32), device="cuda"))
+        us.append(torch.empty(p.n, dtype=torch.float32, device="cuda"))
+    g, _ = api.mof_autotune(probs, params, 2, bs, us)
+    for _ in range(args.warmup):
+        api.mof_solve_batch(probs, params, N_OUTER, bs, us)
+    torch.cuda.synchronize()
+    clocks = Clocks(True)
+    l0 = api.mof_kernel_launches()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        api.mof_solve_batch(probs, params, N_OUTER, bs, us)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    launches = api.mof_kernel_launches() - l0
+    clk = clocks.stop(0)
+    # the plain form: one problem after another
+    for p, prm, b, u in zip(probs, params, bs, us):
+        api.mof_solve(p, prm, N_OUTER, b, u)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for p, prm, b, u in zip(probs, params, bs, us):
+        api.mof_solve(p, prm, N_OUTER, b, u)
+    torch.cuda.synchronize()
+    ts = time.perf_counter() - t0
+    units = len(probs) * N_OUTER
+    line = {
+        "metric": "mmgks_of_outer_iterations_per_s", "value": args.steps * units / tb, "unit": "outer_iters/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tb / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "batch48", "problems": len(probs), "pixels_total": int(sum(w.nx * w.ny * w.nt for w in ws)),
+                   "n_outer": N_OUTER, "of_streams": g, "timing": "host wall clock around synchronised batches"},
+        "sequential": {"value": units / ts, "ms_per_step": 1e3 * ts, "form": "mof_solve per problem, one after another"},
+        "speedup_vs_sequential": ts / (tb / args.steps),
+        "gpu_launches": launches, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_large(args):
+    """The 1024x1024x64 problem (90 angles, 1448 bins, 20 ellipses, 0.5% noise), 30
+    outer iterations; inputs resident, L2 flushed before each step."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2501_12497_gb300 import api, synth
+    api.load()
+    w = synth.large_form(0)
+    p = api.mof_problem_create(w.nx, w.ny, w.nt, w.nb, w.na, w.angles, precision=api.MOF_FP32)
+    prm = api.mof_default_params(noise_norm=w.noise_norm, of_streams=args.of_streams)
+    b = torch.tensor(w.b.astype(np.float32), device="cuda")
+    u = torch.empty(p.n, dtype=torch.float32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        api.mof_solve(p, prm, N_OUTER, b, u)
+    torch.cuda.synchronize()
+    clocks = Clocks(True)
+    l0 = api.mof_kernel_launches()
+    ms = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        rep = api.mof_solve(p, prm, N_OUTER, b, u)
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    launches = api.mof_kernel_launches() - l0
+    clk = clocks.stop(0)
+    rre = float(np.linalg.norm(u.cpu().numpy() - w.u_true.ravel()) / np.linalg.norm(w.u_true))
+    tot = sum(ms)
+    line = {
+        "metric": "mmgks_of_outer_iterations_per_s", "value": args.steps * N_OUTER / (tot / 1e3), "unit": "outer_iters/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "ellipses1024x1024x64", "n": 1024, "nt": 64, "na": 90, "nb": 1448, "n_outer": N_OUTER,
+                   "rre": rre, "basis_last": rep[-1]["basis"], "l2": "flushed between steps (512 MB write)"},
+        "gpu_launches": launches, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch48":
+        run_batch(args)
+    elif args.workload == "ellipses1024x1024x64":
+        run_large(args)
     else:
         run_ours(args)
 

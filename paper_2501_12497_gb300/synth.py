@@ -101,7 +101,7 @@ def raster(e_list, nx, ny, h=1.0, ss=4):
     return img.reshape(ny, ss, nx, ss).mean(axis=(1, 3))
 
 
-def _make(name, nx, ny, nt, na, nb, ellipses, noise_rel, seed, h=1.0, db=1.0):
+def _make(name, nx, ny, nt, na, nb, ellipses, noise_rel, seed, h=1.0, db=1.0, ss=4):
     na_arr, angles = shifted_angles(nt, na)
     sig = (np.arange(nb) - 0.5 * (nb - 1)) * db
     u_true = np.empty((nt, ny, nx))
@@ -110,7 +110,7 @@ def _make(name, nx, ny, nt, na, nb, ellipses, noise_rel, seed, h=1.0, db=1.0):
     aoff = 0
     for t in range(nt):
         ets = [e.at(t) for e in ellipses]
-        u_true[t] = raster(ets, nx, ny, h)
+        u_true[t] = raster(ets, nx, ny, h, ss)
         th = angles[aoff:aoff + na_arr[t]]
         blk = np.zeros((na_arr[t], nb))
         for et in ets:
@@ -158,7 +158,7 @@ def moving_disks(n=64, nt=8, na=16, nb=64, radii=(8.0, 12.0), rhos=(1.0, 0.6), s
 
 
 def moving_ellipses(n=256, nt=32, na=30, nb=363, n_ell=6, axes=(8.0, 40.0), rho=(0.2, 1.0),
-                    speed=(0.5, 2.0), rot_deg=2.0, noise=0.01, seed=0, name=None):
+                    speed=(0.5, 2.0), rot_deg=2.0, noise=0.01, seed=0, name=None, ss=4):
     """Seeded ellipses, each in rigid motion: translation of U(speed) px/frame and
     rotation of U(-rot_deg, rot_deg) degrees/frame about its own centre."""
     rng = np.random.default_rng(seed)
@@ -182,7 +182,7 @@ def moving_ellipses(n=256, nt=32, na=30, nb=363, n_ell=6, axes=(8.0, 40.0), rho=
                 break
         else:
             raise RuntimeError("could not place ellipse")
-    return _make(name or "ellipses%dx%dx%d" % (n, n, nt), n, n, nt, na, nb, ell, noise, seed)
+    return _make(name or "ellipses%dx%dx%d" % (n, n, nt), n, n, nt, na, nb, ell, noise, seed, ss=ss)
 
 
 # The workloads of the method's benchmark configurations.
@@ -212,7 +212,8 @@ def differentiation_form(seed=0):
 def batch_form(count=48, seed=0, sizes=(128, 192, 256, 384, 512), nt_range=(8, 40), na_range=(10, 45)):
     """Independent problems of uneven size: for each, seeded n from `sizes`, T and
     angles per frame uniform in the given ranges, ceil(sqrt(2) n) bins, and the
-    moving-ellipse generator (rigid motion up to 2 px/frame, 1% noise)."""
+    moving-ellipse generator (rigid motion up to 2 px/frame, 1% noise; the phantom
+    raster at one sample per pixel)."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(count):
@@ -220,8 +221,15 @@ def batch_form(count=48, seed=0, sizes=(128, 192, 256, 384, 512), nt_range=(8, 4
         nt = int(rng.integers(nt_range[0], nt_range[1] + 1))
         na = int(rng.integers(na_range[0], na_range[1] + 1))
         nb = int(math.ceil(math.sqrt(2) * n))
-        out.append(moving_ellipses(n, nt, na, nb, seed=1000 * seed + i, name="batch%d_%dx%dx%d" % (i, n, n, nt)))
+        out.append(moving_ellipses(n, nt, na, nb, seed=1000 * seed + i, name="batch%d_%dx%dx%d" % (i, n, n, nt), ss=1))
     return out
+
+
+def large_form(seed=0):
+    """1024x1024 frames, T=64, 90 angles/frame, 1448 bins, 20 ellipses in rigid motion
+    (up to 3 px/frame), 0.5% noise; the phantom raster at one sample per pixel."""
+    return moving_ellipses(1024, 64, 90, 1448, n_ell=20, speed=(0.5, 3.0), noise=0.005, seed=seed,
+                           name="ellipses1024x1024x64", ss=1)
 
 
 # ------------------------------------------------------- generic random inputs
