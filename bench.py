@@ -41,7 +41,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["ellipses256x256x32", "batch48", "ellipses1024x1024x64"],
+    ap.add_argument("--no-class-step", action="store_true",
+                    help="skip the instrumented single-stream step (no class times, no roofline); for profiling runs")
+    ap.add_argument("--workload", choices=["ellipses256x256x32", "batch48", "ellipses1024x1024x64", "operators"],
                     default="ellipses256x256x32",
                     help="the 256x256x32 ellipse problem (default), 48 uneven problems batched, "
                          "or the 1024x1024x64 problem")
@@ -229,15 +231,17 @@ def run_ours(args):
     # per-kernel-class device time from one extra, instrumented step with the frame-pair
     # groups of Solve-OF on a single stream, so that no two classes overlap in time
     # (the timed steps above run them on several streams, uninstrumented)
-    prm1 = api.mof_default_params(noise_norm=w.noise_norm, of_streams=1)
-    api.mof_solve(p, prm1, N_OUTER, b, u, s)
-    flush.fill_(1.0)
-    torch.cuda.synchronize()
-    api.mof_set_timing(p, 1)
-    api.mof_solve(p, prm1, N_OUTER, b, u, s)
-    class_ms = {k: [ms, cnt] for k, (ms, cnt) in api.mof_get_timing(p).items()}
-    api.mof_set_timing(p, 0)
-    torch.cuda.synchronize()
+    class_ms = {}
+    if not args.no_class_step:
+        prm1 = api.mof_default_params(noise_norm=w.noise_norm, of_streams=1)
+        api.mof_solve(p, prm1, N_OUTER, b, u, s)
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        api.mof_set_timing(p, 1)
+        api.mof_solve(p, prm1, N_OUTER, b, u, s)
+        class_ms = {k: [ms, cnt] for k, (ms, cnt) in api.mof_get_timing(p).items()}
+        api.mof_set_timing(p, 0)
+        torch.cuda.synchronize()
 
     # end to end through the public host-buffer entry point: pinned host b in, u out
     bh = torch.empty(p.m, dtype=torch.float32, pin_memory=True)
@@ -423,6 +427,85 @@ def run_large(args):
     print(json.dumps(line), flush=True)
 
 
+def run_operators(args):
+    """Every operator of the C ABI applied alone at the 256x256x32 sizes (30 angles, 363
+    bins), L2 flushed before each application, CUDA events around it; achieved GB/s =
+    algorithmic bytes (minimum FP32 traffic of one application) / time, against the
+    measured copy peak. The projector pair is reported against HBM too, although it
+    is bound by FP32 and L1 work (about 36 flop per byte)."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2501_12497_gb300 import api, synth
+    api.load()
+    w = synth.precision_form(0)
+    p = api.mof_problem_create(w.nx, w.ny, w.nt, w.nb, w.na, w.angles, precision=api.MOF_FP32)
+    n, m, ns, P = p.n, p.m, p.nx * p.ny, p.nt - 1
+    dev = "cuda"
+    f32 = lambda a: torch.tensor(np.asarray(a, dtype=np.float32), device=dev).reshape(-1)
+    u = f32(w.u_true)
+    b = f32(w.b)
+    s = f32(synth.random_velocities(P, p.ny, p.nx, vmax=2.0, seed=1))
+    sr = torch.empty_like(s)
+    api.mof_reverse_flow(p, s, sr)
+    flow = torch.empty(2 * P * ns, device=dev)
+    grad = torch.empty(2 * n, device=dev)
+    img = torch.empty(n, device=dev)
+    sino = torch.empty(m, device=dev)
+    ux, uy, ut = (torch.empty(P * ns, device=dev) for _ in range(3))
+    api.mof_of_fields(p, u, 1, ux, uy, ut)
+    pr = torch.empty(P * ns, device=dev)
+    vel = torch.empty(p.nv, device=dev)
+    vel2 = torch.empty(p.nv, device=dev)
+    vg = torch.empty(2 * p.nv, device=dev)
+    r2 = torch.randn(2 * P * ns, device=dev)
+    ops = [
+        ("H (k_project)", 4 * (n + m), lambda: api.mof_apply_A(p, u, sino)),
+        ("H^T (k_backproject)", 4 * (n + m), lambda: api.mof_apply_AT(p, b, img)),
+        ("Psi (k_grad)", 12 * n, lambda: api.mof_apply_grad(p, u, grad)),
+        ("Psi^T (k_gradT)", 12 * n, lambda: api.mof_apply_gradT(p, grad, img)),
+        ("Mhat (k_flow)", 4 * n + 24 * P * ns, lambda: api.mof_apply_flow(p, u, s, sr, flow)),
+        ("Mhat^T (k_flowT + radii)", 4 * n + 24 * P * ns, lambda: api.mof_apply_flowT(p, r2, s, sr, img)),
+        ("Theta^T W Theta (k_regn_*)", 12 * n + 16 * P * ns, lambda: api.mof_apply_reg_normal(p, u, u, s, sr, 1e-3, img)),
+        ("reverse flow (k_rev_*)", 16 * P * ns, lambda: api.mof_reverse_flow(p, s, sr)),
+        ("App. C fields (k_of_fields)", 4 * n + 12 * P * ns, lambda: api.mof_of_fields(p, u, 1, ux, uy, ut)),
+        ("Upsilon s + u_t (k_flow_lin)", 24 * P * ns, lambda: api.mof_apply_flow_lin(p, ux, uy, ut, s, pr)),
+        ("Upsilon^T r (k_flow_linT)", 20 * P * ns, lambda: api.mof_apply_flow_linT(p, ux, uy, pr, vel)),
+        ("(L+L) s (k_grad)", 24 * P * ns, lambda: api.mof_apply_vgrad(p, s, vg)),
+        ("(L+L)^T g (k_gradT)", 24 * P * ns, lambda: api.mof_apply_vgradT(p, vg, vel)),
+        ("velocity VJP (k_flow_ds)", 4 * n + 40 * P * ns, lambda: api.mof_apply_flow_ds(p, u, s, sr, r2, vel, vel2)),
+    ]
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = json.load(open(pk))
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
+    reps = max(args.steps, 5)
+    out = {}
+    for name, nbytes, fn in ops:
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(reps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        us = 1e3 * tot / reps
+        gbs = nbytes / (us * 1e-6) / 1e9
+        out[name] = {"us": round(us, 2), "algorithmic_MB": round(nbytes / 1e6, 2), "GB_s": round(gbs, 1),
+                     "frac_of_measured_peak": round(gbs / peak, 3)}
+    line = {"metric": "operator_applications", "unit": "GB/s", "config": {"workload": "ellipses256x256x32 operators",
+            "l2": "flushed before each application", "reps": reps, "peak_gbs": peak}, "operators": out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -431,6 +514,8 @@ def main():
         run_batch(args)
     elif args.workload == "ellipses1024x1024x64":
         run_large(args)
+    elif args.workload == "operators":
+        run_operators(args)
     else:
         run_ours(args)
 

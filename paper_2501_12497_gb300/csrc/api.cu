@@ -83,6 +83,12 @@ static AngleParams angle_params(double theta, int frame, int nx, int ny, int nb,
     P.wfoot_d = h / mu;
     P.rfoot = (float)P.rfoot_d;
     P.wfoot = (float)P.wfoot_d;
+    P.inv_rfoot = (float)(1.0 / P.rfoot_d);
+    const double fci = std::floor(P.f0_c);
+    P.f0c_i = (int)std::fmax(std::fmin(fci, 1e9), -1e9);
+    P.f0c_f = (float)(P.f0_c - fci);
+    split12(P.f0_k, P.f0k_hi, P.f0k_lo);
+    P.df_f = (float)P.df;
     return P;
 }
 

@@ -63,6 +63,12 @@ struct AngleParams {
     int frame;          // frame this angle belongs to
     int pad_;
     double wstep_d, rfoot_d, wfoot_d;  // the same three in FP64 (FP64 kernels)
+    // FP32 ray set-up without FP64: f0(k) = f0c_i + f0c_f + k (f0k_hi + f0k_lo),
+    // f0k_hi with 12 significant bits (k * f0k_hi exact for k < 4096)
+    int f0c_i;
+    float f0c_f, f0k_hi, f0k_lo;
+    float inv_rfoot;    // 1 / rfoot
+    float df_f;         // df rounded to FP32 (step-range bounds only)
 };
 
 }  // namespace mof

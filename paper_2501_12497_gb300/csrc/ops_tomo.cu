@@ -46,33 +46,55 @@ __global__ void __launch_bounds__(128) k_project(const real *__restrict__ u, con
     const int rows = P.rows;
     const real *img = rows ? u + P.frame * ns : uT + P.frame * ns;
     const int nfast = rows ? nx : ny, nstep = rows ? ny : nx;
-    const double f0 = (double)k * P.f0_k + P.f0_c;  // fractional fast index at step 0
-    // steps whose crossing lies in (-1, nfast); one step of margin each side
-    int jlo = 0, jhi = nstep - 1;
-    if (P.df != 0.0) {
-        double ja = (-1.0 - f0) / P.df, jb = ((double)nfast - f0) / P.df;
-        double lo = fmin(ja, jb), hi = fmax(ja, jb);
-        lo = fmax(lo, -1.0);
-        hi = fmin(hi, (double)nstep);
-        jlo = max(0, (int)floor(lo) - 1);
-        jhi = min(nstep - 1, (int)ceil(hi) + 1);
-    } else if (!(f0 > -1.0 && f0 < (double)nfast)) {
-        jhi = -1;
-    }
     real acc = 0;
     if constexpr (sizeof(real) == 4) {
-        const double fl0 = floor(f0);
-        const int ibase = (int)fmax(fmin(fl0, 1e9), -1e9);
-        const float fbase = (float)(f0 - fl0);
+        // f(k, j) = f0(k) + j df, in FP32 with split steps (the base in FP64 when nb >= 4096):
+        // the base f0(k) = f0c_i + f0c_f + k (f0k_hi + f0k_lo) and each step j df are
+        // evaluated as an integer part plus a fraction accurate to ~1e-7
+        int ib;
+        float fb;
+        if (nb < 4096) {
+            affine_frac(P.f0c_i, P.f0c_f, P.f0k_hi, P.f0k_lo, k, ib, fb);
+        } else {  // k * f0k_hi would not be exact: the base in FP64
+            const double f0d = (double)k * P.f0_k + P.f0_c, fl0 = floor(f0d);
+            ib = (int)fmax(fmin(fl0, 1e9), -1e9);
+            fb = (float)(f0d - fl0);
+        }
+        // steps whose crossing can lie in (-1, nfast), with two steps of margin each side
+        // (the taps are bounds-checked, so extra steps add nothing)
+        int jlo = 0, jhi = nstep - 1;
+        const float f0 = (float)ib + fb;
+        if (P.df_f != 0.0f) {
+            const float ja = (-1.0f - f0) / P.df_f, jb = ((float)nfast - f0) / P.df_f;
+            const float lo = fmaxf(fminf(ja, jb), -1.0f), hi = fminf(fmaxf(ja, jb), (float)nstep);
+            jlo = max(0, (int)floorf(lo) - 2);
+            jhi = min(nstep - 1, (int)ceilf(hi) + 2);
+        } else if (!(f0 > -1.0f && f0 < (float)nfast)) {
+            jhi = -1;
+        }
+#pragma unroll 4
         for (int j = jlo; j <= jhi; ++j) {
             int i0;
             float w1;
-            affine_frac(ibase, fbase, P.df_hi, P.df_lo, j, i0, w1);
+            affine_frac(ib, fb, P.df_hi, P.df_lo, j, i0, w1);
             const real *row = img + (long long)j * nfast;
             if (i0 >= 0 && i0 < nfast) acc = fmaf(1.0f - w1, ldg(row + i0), acc);
             if (i0 + 1 >= 0 && i0 + 1 < nfast) acc = fmaf(w1, ldg(row + i0 + 1), acc);
         }
+        b[(long long)a * nb + k] = acc * P.wstep;
     } else {
+        const double f0 = (double)k * P.f0_k + P.f0_c;  // fractional fast index at step 0
+        int jlo = 0, jhi = nstep - 1;
+        if (P.df != 0.0) {
+            double ja = (-1.0 - f0) / P.df, jb = ((double)nfast - f0) / P.df;
+            double lo = fmin(ja, jb), hi = fmax(ja, jb);
+            lo = fmax(lo, -1.0);
+            hi = fmin(hi, (double)nstep);
+            jlo = max(0, (int)floor(lo) - 1);
+            jhi = min(nstep - 1, (int)ceil(hi) + 1);
+        } else if (!(f0 > -1.0 && f0 < (double)nfast)) {
+            jhi = -1;
+        }
         for (int j = jlo; j <= jhi; ++j) {
             const double f = fma((double)j, P.df, f0);
             const double fl = floor(f);
@@ -82,8 +104,8 @@ __global__ void __launch_bounds__(128) k_project(const real *__restrict__ u, con
             if (i0 >= 0 && i0 < nfast) acc = fma(1.0 - w1, ldg(row + i0), acc);
             if (i0 + 1 >= 0 && i0 + 1 < nfast) acc = fma(w1, ldg(row + i0 + 1), acc);
         }
+        b[(long long)a * nb + k] = acc * (real)P.wstep_d;
     }
-    b[(long long)a * nb + k] = acc * (sizeof(real) == 8 ? (real)P.wstep_d : (real)P.wstep);
 }
 
 template <typename real>
@@ -109,8 +131,11 @@ template <typename real>
 __global__ void __launch_bounds__(BP_TX *BP_TY) k_backproject(const real *__restrict__ b, real *__restrict__ u,
                                                               const AngleParams *__restrict__ ang,
                                                               const int *__restrict__ aoff, int nx, int ny, int nb) {
+    // per angle of the chunk: the bin coordinate at the tile origin (integer + fraction,
+    // from FP64) and the constants of the footprint, shared by the block's pixels
     __shared__ int s_ib[BP_CHUNK];
-    __shared__ float s_fb[BP_CHUNK];
+    __shared__ float s_fb[BP_CHUNK], s_tAh[BP_CHUNK], s_tAl[BP_CHUNK], s_tBh[BP_CHUNK], s_tBl[BP_CHUNK];
+    __shared__ float s_r[BP_CHUNK], s_ir[BP_CHUNK], s_wf[BP_CHUNK];
     __shared__ double s_tb[BP_CHUNK];
     const int t = blockIdx.z;
     const int x0 = blockIdx.x * BP_TX, y0 = blockIdx.y * BP_TY;
@@ -129,29 +154,42 @@ __global__ void __launch_bounds__(BP_TX *BP_TY) k_backproject(const real *__rest
             s_ib[tid] = (int)fmax(fmin(fl, 1e9), -1e9);
             s_fb[tid] = (float)(tb - fl);
             s_tb[tid] = tb;
+            s_tAh[tid] = P.tA_hi;
+            s_tAl[tid] = P.tA_lo;
+            s_tBh[tid] = P.tB_hi;
+            s_tBl[tid] = P.tB_lo;
+            s_r[tid] = P.rfoot;
+            s_ir[tid] = P.inv_rfoot;
+            s_wf[tid] = P.wfoot;
         }
         __syncthreads();
         if (x < nx && y < ny) {
             for (int q = 0; q < cn; ++q) {
-                const AngleParams &P = ang[ac + q];
                 const real *row = b + (long long)(ac + q) * nb;
-                const float r = P.rfoot;
                 if constexpr (sizeof(real) == 4) {
-                    // bin coordinate t = ib + fr of this pixel
-                    const float pa = (float)di * P.tA_hi, pb = (float)dj * P.tB_hi;  // exact
+                    // bin coordinate t = ib + fr of this pixel (split-step, exact products)
+                    const float pa = (float)di * s_tAh[q], pb = (float)dj * s_tBh[q];
                     const float pfa = floorf(pa), pfb = floorf(pb);
-                    float fr = s_fb[q] + (pa - pfa) + (pb - pfb) + fmaf((float)di, P.tA_lo, (float)dj * P.tB_lo);
+                    float fr = s_fb[q] + (pa - pfa) + (pb - pfb) + fmaf((float)di, s_tAl[q], (float)dj * s_tBl[q]);
                     const float ff = floorf(fr);
                     const int ib = s_ib[q] + (int)pfa + (int)pfb + (int)ff;
                     fr -= ff;
-                    // bins k with |k - t| < r: k = ib - m (distance fr + m) and ib + 1 + m (1 - fr + m)
-                    for (int m = 0; (float)m < r; ++m) {
-                        const float d0 = fr + (float)m, d1 = 1.0f - fr + (float)m;
-                        const int k0 = ib - m, k1 = ib + 1 + m;
-                        if (d0 < r && k0 >= 0 && k0 < nb) acc = fmaf(P.wfoot * (1.0f - d0 / r), ldg(row + k0), acc);
-                        if (d1 < r && k1 >= 0 && k1 < nb) acc = fmaf(P.wfoot * (1.0f - d1 / r), ldg(row + k1), acc);
+                    const float r = s_r[q], ir = s_ir[q], wf = s_wf[q];
+                    if (r <= 1.0f) {  // at most the two bins around t
+                        const float d1 = 1.0f - fr;
+                        if (fr < r && ib >= 0 && ib < nb) acc = fmaf(wf * (1.0f - fr * ir), ldg(row + ib), acc);
+                        if (d1 < r && ib + 1 >= 0 && ib + 1 < nb) acc = fmaf(wf * (1.0f - d1 * ir), ldg(row + ib + 1), acc);
+                    } else {
+                        // bins k with |k - t| < r: k = ib - m (distance fr + m) and ib + 1 + m (1 - fr + m)
+                        for (int m = 0; (float)m < r; ++m) {
+                            const float d0 = fr + (float)m, d1 = 1.0f - fr + (float)m;
+                            const int k0 = ib - m, k1 = ib + 1 + m;
+                            if (d0 < r && k0 >= 0 && k0 < nb) acc = fmaf(wf * (1.0f - d0 * ir), ldg(row + k0), acc);
+                            if (d1 < r && k1 >= 0 && k1 < nb) acc = fmaf(wf * (1.0f - d1 * ir), ldg(row + k1), acc);
+                        }
                     }
                 } else {
+                    const AngleParams &P = ang[ac + q];
                     const double tt = s_tb[q] + (double)di * P.tA + (double)dj * P.tB;
                     const double ff = floor(tt);
                     const int ib = (int)ff;

@@ -238,7 +238,7 @@ constexpr int TG_ROWS = 4 * TG_PIX;
 template <typename real>
 static size_t theta_gram_smem(int Kmax) {
     // the row tile, reused at the end for the FP64 group sums ([groups][blocks][16] <= [256][16])
-    const size_t tile = sizeof(real) * (size_t)(((Kmax + 3) / 4) * 4) * (TG_ROWS + 4);
+    const size_t tile = sizeof(real) * ((size_t)(((Kmax + 3) / 4) * 4) * (TG_ROWS + 4) + 4 * (size_t)((Kmax + 3) / 4));
     const size_t red = sizeof(double) * 256 * 16;
     return tile > red ? tile : red;
 }
@@ -759,6 +759,10 @@ __global__ void k_of_rhs(const real *__restrict__ ux, const real *__restrict__ u
 // tiles with Kahan compensation. At the end the row groups are combined in
 // FP64 in shared memory, and the per-CTA partials by k_gram_reduce.
 constexpr int TG_S = TG_ROWS + 4;  // column stride of the shared row tile
+// column j starts at j * TG_S + 4 * (j / 4): the skew of four floats per group of
+// four columns puts the 128-bit reads of the eight column groups a warp's 4x4
+// blocks touch on eight different bank quads
+__host__ __device__ constexpr int tg_col(int j) { return j * TG_S + 4 * (j / 4); }
 constexpr int TG_MAXG = 8;         // row groups per 4x4 block at most
 
 template <typename real>
@@ -880,7 +884,7 @@ __global__ void __launch_bounds__(TG_T) k_theta_gram(const real *__restrict__ V,
                 }
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) As[(j + u) * TG_S + tid] = sw * val[u];
+            for (int u = 0; u < 4; ++u) As[tg_col(j + u) + tid] = sw * val[u];
         }
         __syncthreads();
         if (acc_on) {
@@ -889,7 +893,7 @@ __global__ void __launch_bounds__(TG_T) k_theta_gram(const real *__restrict__ V,
             for (int a = 0; a < 4; ++a)
 #pragma unroll
                 for (int c = 0; c < 4; ++c) acc[a][c] = 0;
-            const real *pa = As + 4 * I * TG_S, *pb = As + 4 * J * TG_S;
+            const real *pa = As + tg_col(4 * I), *pb = As + tg_col(4 * J);
             for (int r = r0; r < r1; r += 4) {
                 Quad<real> va[4], vb[4];
 #pragma unroll
