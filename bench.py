@@ -59,6 +59,22 @@ def dist_env():
     return rank, world, local
 
 
+# ------------------------------------------------------------ ranks
+def max_over_ranks(value, world, device="cpu"):
+    """The largest value over the ranks of the process group (the slowest rank's time)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, steps, n_outer, total_ms):
+    """Whole-job throughput: outer iterations of all ranks per second of the slowest rank."""
+    return world * steps * n_outer / (total_ms / 1e3)
+
+
 # ------------------------------------------------------------ CPU oracle sample
 def oracle_outer_iteration_seconds(w):
     """Time the oracle (as it stands) on a bounded sample of one outer iteration:
@@ -221,12 +237,8 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     clk = clocks.stop(local)
-    total_ms = sum(per_step)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = world * args.steps * N_OUTER / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(per_step), world, dev)
+    value = job_value(world, args.steps, N_OUTER, total_ms)
 
     # per-kernel-class device time from one extra, instrumented step with the frame-pair
     # groups of Solve-OF on a single stream, so that no two classes overlap in time
@@ -257,11 +269,8 @@ def run_ours(args):
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             api.mof_solve_host(p, prm, N_OUTER, bhn, uhn)
-        e2e_s = time.perf_counter() - t0
-        te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e_value = world * args.e2e_steps * N_OUTER / float(te.item())
+        e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+        e2e_value = job_value(world, args.e2e_steps, N_OUTER, 1e3 * e2e_s)
 
     # quality of the result (RRE against the phantom) and the DP residual
     rre = float(np.linalg.norm(u.cpu().numpy() - w.u_true.ravel()) / np.linalg.norm(w.u_true))
