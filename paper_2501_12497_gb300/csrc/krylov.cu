@@ -521,8 +521,20 @@ void Krylov<real>::reorth(const BasisRef<real> &B, real *x, long long xstride, d
                           cudaStream_t st) const {
     // classical Gram-Schmidt against V, twice (CGS2); coef is [B][Kmax] scratch
     dots(B, x, xstride, coef, B.Kmax, 1.0, st);
-    if (!sub_dot(B, coef, B.Kmax, x, xstride, coef, st)) {
-        subtract(B, coef, B.Kmax, x, xstride, x, xstride, nullptr, st);
+    reorth_second(B, x, xstride, coef, coef, nrm2_out, st);
+}
+
+template <typename real>
+void Krylov<real>::reorth_second(const BasisRef<real> &B, real *x, long long xstride, const double *c1, double *coef,
+                                 double *nrm2_out, cudaStream_t st) const {
+    // the first projection's coefficients are given (c1; null: zero), the second are
+    // taken by dot products, fused with the first update where the layout allows
+    if (c1) {
+        if (!sub_dot(B, c1, B.Kmax, x, xstride, coef, st)) {
+            subtract(B, c1, B.Kmax, x, xstride, x, xstride, nullptr, st);
+            dots(B, x, xstride, coef, B.Kmax, 1.0, st);
+        }
+    } else {
         dots(B, x, xstride, coef, B.Kmax, 1.0, st);
     }
     subtract(B, coef, B.Kmax, x, xstride, x, xstride, nrm2_out, st);

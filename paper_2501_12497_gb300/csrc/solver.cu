@@ -130,7 +130,7 @@ struct WS {
     // ---- image step (one problem)
     real *V, *HV, *U, *u, *un, *r, *tm, *tn, *b, *q, *uT, *s, *sr, *vnew, *hvnew;
     int *rad_s, *rad_sr, *rad_rev, *dest;
-    double *GH, *GT, *gH, *z, *lam, *coef, *nrm2, *nrm2b, *scaleR, *alpha, *beta, *beta1, *alpha1, *bb, *gpart;
+    double *GH, *GT, *gH, *z, *lam, *coef, *c1, *nrm2, *nrm2b, *scaleR, *alpha, *beta, *beta1, *alpha1, *bb, *gpart;
     int *K, *KU, *grow, *gkb, *flag, *err, *appended;
     double *report;  // [max_outer][8]
     // ---- Solve-OF (P pairs)
@@ -300,6 +300,7 @@ static mof_status ensure_ws(mof_problem *p, const mof_solver_params &prm, int n_
         w->z = a.take<double>(Kmax);
         w->lam = a.take<double>(1);
         w->coef = a.take<double>(Kmax + 8);
+        w->c1 = a.take<double>(Kmax + 8);
         w->nrm2 = a.take<double>(1);
         w->nrm2b = a.take<double>(1);
         w->scaleR = a.take<double>(1);
@@ -553,7 +554,7 @@ __global__ void k_of_proj_gram(const double *__restrict__ GA, const double *__re
                                const double *__restrict__ z, const double *__restrict__ gam, const int *__restrict__ K,
                                const int *__restrict__ act, int ld, double *__restrict__ c) {
     const int b = blockIdx.x, lane = threadIdx.x;
-    if (!act[b]) return;
+    if (act && !act[b]) return;
     const int Kb = min(K[b], ld);
     const double *A = GA + (long long)b * ld * ld, *L = GL + (long long)b * ld * ld, *zb = z + (long long)b * ld;
     const double gm = gam[b];
@@ -1032,12 +1033,12 @@ static mof_status solve_of_impl(mof_problem *p, const mof_solver_params &prm, WS
             kg.append(BU, Kug, bofg, ns, bbg, nullptr, 0.0, gkbg, nullptr, nullptr, gst);
             for (int j = 0; j < w.of_ell && j < prm.of_ell; ++j) {
                 ::mof::count_launch(), k_of_upsT<real><<<dim3(fb(ns), nb), 256, 0, gst>>>(uxg, uyg, Ug, ldU, j, Vg, Kof, w.beta_of + b0, wvg, ns, gkbg);
-                kg.reorth(BV, wvg, N2, w.coef_of + (long long)b0 * Kof, nrmg, gst);
+                kg.reorth_second(BV, wvg, N2, nullptr, w.coef_of + (long long)b0 * Kof, nrmg, gst);  // V^T x = 0 by the recurrence
                 if (j == 0) ::mof::count_launch(), k_sqrt_into_if<<<pb, 64, 0, gst>>>(nrmg, w.alpha1_of + b0, nb, gkbg);
                 ::mof::count_launch(), k_sqrt_into_if<<<pb, 64, 0, gst>>>(nrmg, w.alpha_of + b0, nb, gkbg);
                 kg.append(BV, Kvg, wvg, N2, nrmg, j == 0 ? nullptr : w.alpha1_of + b0, tol, gkbg, nullptr, nullptr, gst);
                 ::mof::count_launch(), k_of_ups<real><<<dim3(fb(ns), nb), 256, 0, gst>>>(uxg, uyg, Vg, Kof, j, Ug, ldU, w.alpha_of + b0, wug, ns, gkbg);
-                kg.reorth(BU, wug, ns, w.coefU_of + (long long)b0 * ldU, nrmg, gst);
+                kg.reorth_second(BU, wug, ns, nullptr, w.coefU_of + (long long)b0 * ldU, nrmg, gst);
                 ::mof::count_launch(), k_sqrt_into_if<<<pb, 64, 0, gst>>>(nrmg, w.beta_of + b0, nb, gkbg);
                 kg.append(BU, Kug, wug, ns, nrmg, w.beta1_of + b0, tol, gkbg, nullptr, nullptr, gst);
             }
@@ -1091,11 +1092,7 @@ static mof_status solve_of_impl(mof_problem *p, const mof_solver_params &prm, WS
                 // dot products (fused with the first update); then the second update
                 double *cg = w.coef_of + (long long)b0 * Kof;
                 ::mof::count_launch(), k_of_proj_gram<<<nb, 32, 0, gst>>>(sa.GA, sa.GL, sa.g, sa.z, sa.lam, Kvg, actg, Kof, cg);
-                if (!kg.sub_dot(BAg, cg, Kof, wvg, N2, cg, gst)) {
-                    kg.subtract(BAg, cg, Kof, wvg, N2, wvg, N2, nullptr, gst);
-                    kg.dots(BAg, wvg, N2, cg, Kof, 1.0, gst);
-                }
-                kg.subtract(BAg, cg, Kof, wvg, N2, wvg, N2, w.nrm_of + b0, gst);
+                kg.reorth_second(BAg, wvg, N2, cg, cg, w.nrm_of + b0, gst);
                 kg.append(BAg, Kvg, wvg, N2, w.nrm_of + b0, w.scale_of + b0, tol, w.grow_of + b0, appg, nullptr, gst);
             }
             {
@@ -1202,14 +1199,14 @@ mof_status SolveRun<real>::begin(cudaStream_t ust) {
         for (int j = 0; j < prm.ell; ++j) {
             MOF_TRY(launch_backproject<real>(p, w.U + (long long)j * m, w.r, st));
             if (j > 0) ::mof::count_launch(), k_axpy_dev<real><<<dim3(fb(n), 1), 256, 0, st>>>(w.r, n, w.V + (long long)(j - 1) * n, n, w.beta, n, w.gkb);
-            kr.reorth(BV, w.r, n, w.coef, w.nrm2, st);
+            kr.reorth_second(BV, w.r, n, nullptr, w.coef, w.nrm2, st);  // V^T x = 0 by the recurrence
             if (j == 0) ::mof::count_launch(), k_sqrt_into_if<<<1, 1, 0, st>>>(w.nrm2, w.alpha1, 1, w.gkb);
             ::mof::count_launch(), k_sqrt_into_if<<<1, 1, 0, st>>>(w.nrm2, w.alpha, 1, w.gkb);
             kr.append(BV, w.K, w.r, n, w.nrm2, j == 0 ? nullptr : w.alpha1, tol, w.gkb, nullptr, nullptr, st);
             MOF_TRY(launch_project<real>(p, w.V + (long long)j * n, w.uT, w.HV + (long long)j * m, st));
             ::mof::count_launch(), k_copy<real><<<fb(m), 256, 0, st>>>(w.HV + (long long)j * m, w.tm, m);
             ::mof::count_launch(), k_axpy_dev<real><<<dim3(fb(m), 1), 256, 0, st>>>(w.tm, m, w.U + (long long)j * m, m, w.alpha, m, w.gkb);
-            kr.reorth(BU, w.tm, m, w.coef, w.nrm2, st);
+            kr.reorth_second(BU, w.tm, m, nullptr, w.coef, w.nrm2, st);
             ::mof::count_launch(), k_sqrt_into_if<<<1, 1, 0, st>>>(w.nrm2, w.beta, 1, w.gkb);
             kr.append(BU, w.KU, w.tm, m, w.nrm2, w.beta1, tol, w.gkb, nullptr, nullptr, st);
         }
@@ -1289,7 +1286,9 @@ mof_status SolveRun<real>::iteration(bool of_now, bool expand) {
             }
             {
                 Scope sc(tm, "reorth", st);
-                kr.reorth(BV, w.r, n, w.coef, w.nrm2, st);
+                // V^T r = (G_H + lam G_Theta) z - g_H exactly: the first projection from the Grams
+                ::mof::count_launch(), k_of_proj_gram<<<1, 32, 0, st>>>(w.GH, w.GT, w.gH, w.z, w.lam, w.K, nullptr, Kmax, w.c1);
+                kr.reorth_second(BV, w.r, n, w.c1, w.coef, w.nrm2, st);
                 kr.append(BV, w.K, w.r, n, w.nrm2, w.scaleR, tol, w.grow, w.appended, w.vnew, st);
             }
             {

@@ -70,6 +70,11 @@ struct Krylov {
     void norm2(const real *x, long long N, long long xstride, int nb, double *out, cudaStream_t st) const;
     // x[b] <- (I - V V^T)^2 x[b] (classical Gram-Schmidt twice); ||x||^2 -> nrm2_out
     void reorth(const BasisRef<real> &B, real *x, long long xstride, double *coef, double *nrm2_out, cudaStream_t st) const;
+    // the same with the first projection's coefficients V^T x supplied by the caller from an
+    // exact identity (c1 [B][Kmax]; null when they are zero, as for a Golub-Kahan residual),
+    // so that only the second projection streams V for its dot products
+    void reorth_second(const BasisRef<real> &B, real *x, long long xstride, const double *c1, double *coef,
+                       double *nrm2_out, cudaStream_t st) const;
     // x[b] <- x[b] - V[b] c[b] and out[b] = V[b]^T x[b] in one pass over V (false: not
     // applicable to this layout, nothing enqueued)
     bool sub_dot(const BasisRef<real> &B, const double *c, long long cstride, real *x, long long xstride, double *out,
