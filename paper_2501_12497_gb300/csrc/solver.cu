@@ -158,6 +158,9 @@ struct WS {
     // Solve-OF pair groups: one stream each, forked from and joined to ss
     cudaStream_t gs[MAX_OF_STREAMS] = {};
     cudaEvent_t gfork = nullptr, gdone[MAX_OF_STREAMS] = {};
+    // side stream of the image step (the Psi rows of the weighted Gram beside Solve-OF)
+    cudaStream_t side = nullptr;
+    cudaEvent_t side_fork = nullptr, side_done = nullptr;
     void drop_graphs() {
         for (auto &g : graphs) {
             if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -197,6 +200,9 @@ static void free_ws(WS<real> *w) {
         if (w->gdone[g]) cudaEventDestroy(w->gdone[g]);
     }
     if (w->gfork) cudaEventDestroy(w->gfork);
+    if (w->side) cudaStreamDestroy(w->side);
+    if (w->side_fork) cudaEventDestroy(w->side_fork);
+    if (w->side_done) cudaEventDestroy(w->side_done);
     if (w->mem) cudaFree(w->mem);
     delete w;
 }
@@ -309,7 +315,7 @@ static mof_status ensure_ws(mof_problem *p, const mof_solver_params &prm, int n_
         w->beta1 = a.take<double>(1);
         w->alpha1 = a.take<double>(1);
         w->bb = a.take<double>(1);
-        w->gpart = a.take<double>((size_t)w->gram_ctas * Kmax * Kmax);
+        w->gpart = a.take<double>((size_t)2 * w->gram_ctas * Kmax * Kmax);
         w->K = a.take<int>(1);
         w->KU = a.take<int>(1);
         w->grow = a.take<int>(1);
@@ -368,6 +374,9 @@ static mof_status ensure_ws(mof_problem *p, const mof_solver_params &prm, int n_
             MOF_CUDA(cudaStreamCreateWithFlags(&w->ss, cudaStreamNonBlocking));
             MOF_CUDA(cudaEventCreateWithFlags(&w->join, cudaEventDisableTiming));
             MOF_CUDA(cudaEventCreateWithFlags(&w->gfork, cudaEventDisableTiming));
+            MOF_CUDA(cudaStreamCreateWithFlags(&w->side, cudaStreamNonBlocking));
+            MOF_CUDA(cudaEventCreateWithFlags(&w->side_fork, cudaEventDisableTiming));
+            MOF_CUDA(cudaEventCreateWithFlags(&w->side_done, cudaEventDisableTiming));
             for (int g = 0; g < MAX_OF_STREAMS; ++g) {
                 MOF_CUDA(cudaStreamCreateWithFlags(&w->gs[g], cudaStreamNonBlocking));
                 MOF_CUDA(cudaEventCreateWithFlags(&w->gdone[g], cudaEventDisableTiming));
@@ -796,7 +805,7 @@ template <typename real>
 __global__ void __launch_bounds__(TG_T) k_theta_gram(const real *__restrict__ V, long long n, int Kmax, const int *__restrict__ Kp,
                                                      const real *__restrict__ uk, const real *__restrict__ s,
                                                      const real *__restrict__ sr, real eps2, int nx, int ny, int nt,
-                                                     double *__restrict__ partial) {
+                                                     int rows, double *__restrict__ partial) {
     extern __shared__ __align__(16) unsigned char smraw[];
     real *As = reinterpret_cast<real *>(smraw);  // [K4 * 4][TG_S], column j = basis vector j
     const int K = min(Kp[0], Kmax);
@@ -824,14 +833,18 @@ __global__ void __launch_bounds__(TG_T) k_theta_gram(const real *__restrict__ V,
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int c = 0; c < 4; ++c) sum[a][c] = comp[a][c] = 0;
+    // rows: 0 = all four rows per pixel (64 pixels per tile), 1 = the Psi rows only,
+    // 2 = the Mhat rows only (128 pixels per tile)
     const int ns = nx * ny;
-    const int tpf = (ns + TG_PIX - 1) / TG_PIX;
-    const int ntiles = tpf * nt;
+    const int ppt = rows == 0 ? TG_PIX : 2 * TG_PIX;
+    const int tpf = (ns + ppt - 1) / ppt;
     const int np = nt - 1;
-    const int q = tid & 3;
+    const int ntiles = tpf * (rows == 2 ? np : nt);
+    const int q = rows == 0 ? (tid & 3) : (tid & 1) + (rows == 2 ? 2 : 0);
+    const int pid = rows == 0 ? (tid >> 2) : (tid >> 1);
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int t = tile / tpf;
-        const int pix = (tile - t * tpf) * TG_PIX + (tid >> 2);
+        const int pix = (tile - t * tpf) * ppt + pid;
         const bool inpix = pix < ns;
         const int y = inpix ? pix / nx : 0, x = inpix ? pix - y * nx : 0;
         bool valid = inpix && (q < 2 || t < np);
@@ -1253,7 +1266,22 @@ mof_status SolveRun<real>::iteration(bool of_now, bool expand) {
     WS<real> &w = *wp;
     BasisRef<real> BV{w.V, n, Kmax, 1, w.K, nullptr};
     BasisRef<real> BH{w.HV, m, Kmax, 1, w.K, nullptr};
+        // The weighted Gram of Theta = [Psi; Mhat] in two parts: the Psi rows depend on the
+        // basis and u_k only, so they are accumulated on a side stream while Solve-OF runs;
+        // the Mhat rows follow the new flow. The reduction adds both sets of partials.
+        double *gpart_psi = w.gpart, *gpart_m = w.gpart + (long long)w.gram_ctas * Kmax * Kmax;
+        const cudaStream_t pst = of_now ? w.side : st;
         if (of_now) {
+            MOF_CUDA(cudaEventRecord(w.side_fork, st));
+            MOF_CUDA(cudaStreamWaitEvent(w.side, w.side_fork, 0));
+        }
+        {
+            Scope sc(tm, "theta_gram", pst);
+            ::mof::count_launch(), k_theta_gram<real><<<w.gram_ctas, TG_T, tg_smem, pst>>>(w.V, n, Kmax, w.K, w.u, w.s, w.sr, eps2, p->nx,
+                                                                                      p->ny, p->nt, 1, gpart_psi);
+        }
+        if (of_now) {
+            MOF_CUDA(cudaEventRecord(w.side_done, w.side));
             MOF_TRY(solve_of_impl<real>(p, prm, w, w.u, w.s, tm, st));
             Scope sc(tm, "reverse_flow", st);
             MOF_TRY(launch_reverse_flow<real>(p, w.s, w.rad_rev, w.dest, w.sr, st));
@@ -1261,9 +1289,10 @@ mof_status SolveRun<real>::iteration(bool of_now, bool expand) {
         }
         {
             Scope sc(tm, "theta_gram", st);
-            ::mof::count_launch(), k_theta_gram<real><<<w.gram_ctas, TG_T, tg_smem, st>>>(w.V, n, Kmax, w.K, w.u, w.s, w.sr, eps2, p->nx, p->ny, p->nt,
-                                                                   w.gpart);
-            ::mof::count_launch(), k_gram_reduce<<<8, 256, 0, st>>>(w.gpart, w.gram_ctas, Kmax, w.K, w.GT);
+            ::mof::count_launch(), k_theta_gram<real><<<w.gram_ctas, TG_T, tg_smem, st>>>(w.V, n, Kmax, w.K, w.u, w.s, w.sr, eps2, p->nx,
+                                                                                     p->ny, p->nt, 2, gpart_m);
+            if (of_now) MOF_CUDA(cudaStreamWaitEvent(st, w.side_done, 0));
+            ::mof::count_launch(), k_gram_reduce<<<8, 256, 0, st>>>(w.gpart, 2 * w.gram_ctas, Kmax, w.K, w.GT);
         }
         {
             Scope sc(tm, "small_solve", st);
