@@ -6,11 +6,13 @@
 // the R factors of eq. (QR)), the block
 //   1. factors M = G_A + rho G_L = R^T R (Cholesky, FP64), rho = tr G_A / tr G_L,
 //      and forms C = R^-T G_A R^-1 and h = R^-T g by two triangular solves;
-//   2. diagonalises C: cyclic Jacobi sweeps in FP32 give approximate
+//   2. diagonalises C: cyclic one-sided Jacobi sweeps in FP32 (four warps,
+//      each holding a quarter of every column) give approximate
 //      eigenvectors W; one third-order Newton-Schulz step makes them
 //      orthonormal in FP64 (W <- W (I - E/2 + 3E^2/8), E = W^T W - I), and
 //      cyclic Jacobi sweeps in FP64 on W^T C W, which start near diagonal,
-//      finish the decomposition to FP64 accuracy while rotating the one vector
+//      finish the decomposition (usually in one sweep: the sweeps stop once no
+//      off-diagonal entry exceeds 1e-12 max|c_ii|) while rotating the one vector
 //      W^T h they need; with the eigenvalues theta_i in [0, 1] and the
 //      eigenvectors, X = R^-1 W satisfies X^T G_A X = diag(theta),
 //      X^T G_L X = diag(1 - theta)/rho (the generalized singular values of
@@ -24,7 +26,11 @@
 //      scanned in FP32 and decided in FP64 among the five points around the
 //      FP32 minimum, then refined between its two grid neighbours by
 //      safeguarded Newton steps on dG/dlog10(lam) = 0 (FP32 steps, then FP64
-//      steps), kept only if it improves on the grid value;
+//      steps, which stop after a Newton step below 1e-6 -- the next would be
+//      below ~1e-12 -- or once the derivative is at its rounding level), kept
+//      only if it improves on the grid value; where the five FP64 values agree
+//      to 1e-13 the neighbourhood is flat to rounding (the plateau G takes
+//      as lam -> 0 when every theta_i > 0) and the grid point stands;
 //      DP: the root of ||A V z - b||^2 = (eta delta)^2 (monotone in lam); the
 //      bracket ends decide the no-root flags in FP64, an FP32 grid locates the
 //      sign change (its cell is confirmed in FP64), and safeguarded Newton
@@ -58,6 +64,8 @@ constexpr double BRACKET_DECADES = 12.0;
 constexpr double THETA_TINY = 1e-14;
 constexpr int JACOBI32_MAX_SWEEPS = 12;
 constexpr int JACOBI64_MAX_SWEEPS = 10;
+constexpr int JW = 4;  // warps of the FP32 one-sided Jacobi
+constexpr int RW = 32 / JW;
 constexpr double LN10 = 2.302585092994045684;
 
 // ------------------------------------------------------------ index helpers
@@ -379,23 +387,42 @@ __device__ void jacobi(T *A, int lda, T *W, int ldw, T *v, int K, int Kp, int ma
     }
 }
 
-// FP32 one-sided (Hestenes) Jacobi in the registers of one warp, K <= 32:
-// lane i holds column i of the symmetric positive semi-definite C and of the
-// accumulated rotation V; in each round of the round-robin ordering a lane
-// takes its partner's columns by shuffles, both lanes of a pair compute the
-// same rotation from the same numbers (the two column norms and their dot
-// product), and each updates its own columns (lower index p:
-// c x_p - s x_q, higher q: s x_p + c x_q). At convergence the columns of C V
-// are orthogonal, so V diagonalises C^2 and therefore C. The warm start needs
-// eigenvectors to FP32 accuracy only; V is written to X (FP64, K x K).
-// Called by warp 0 only.
-__device__ void jacobi1_warp(const double *C, int lds, int K, double *X, int max_sweeps, float tol) {
-    const int lane = threadIdx.x & 31;
-    float a[32], v[32];
+__device__ __forceinline__ void jw_bar() { asm volatile("bar.sync 1, %0;" ::"r"(JW * 32) : "memory"); }
+
+// The partner of column l in round r of the round-robin ordering of Kp
+// (even, <= 32) columns; columns l >= Kp pair with themselves.
+__device__ __forceinline__ int rr_partner(int l, int r, int Kp) {
+    if (l >= Kp) return l;
+    int pos = 0;
+    if (l > 0) {
+        pos = (l - 1 - r) % (Kp - 1);
+        if (pos < 0) pos += Kp - 1;
+        pos += 1;
+    }
+    return rr_player(Kp - 1 - pos, r, Kp);
+}
+
+// FP32 one-sided (Hestenes) Jacobi in registers, K <= 32, by warps 0..JW-1:
+// lane i of every warp holds column i of the symmetric positive semi-definite
+// C and of the accumulated rotation V, warp w the rows [w RW, (w + 1) RW). In
+// each round of the round-robin ordering (partners from the table ptab) a lane
+// takes its partner's entries by shuffles; the warps' partial dot products and
+// squared norms are summed through shared memory in a fixed order (one named
+// barrier per round, the buffer alternating between rounds), so every warp,
+// and both lanes of a pair, take the same rotation from the same numbers, and
+// each lane updates its own column (lower index p: c x_p - s x_q, higher q:
+// s x_p + c x_q). At convergence the columns of C V are orthogonal, so V
+// diagonalises C^2 and therefore C. The warm start needs eigenvectors to FP32
+// accuracy only; V is written to X (FP64, K x K).
+__device__ void jacobi1_warps(const double *C, int lds, int K, double *X, int max_sweeps, float tol,
+                              float2 (*xch)[JW][32], const unsigned char (*ptab)[32]) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float a[RW], v[RW];
 #pragma unroll
-    for (int k = 0; k < 32; ++k) {
-        a[k] = (lane < K && k < K) ? (float)C[k * lds + lane] : 0.0f;
-        v[k] = (k == lane && lane < K) ? 1.0f : 0.0f;
+    for (int r = 0; r < RW; ++r) {
+        const int k = w * RW + r;
+        a[r] = (lane < K && k < K) ? (float)C[k * lds + lane] : 0.0f;
+        v[r] = (k == lane && lane < K) ? 1.0f : 0.0f;
     }
     const int Kp = K + (K & 1);
     // pairs whose dot product is below floor_g (set by ||C||_F^2, invariant under the
@@ -403,54 +430,66 @@ __device__ void jacobi1_warp(const double *C, int lds, int K, double *X, int max
     // to resolve, and the FP64 stage handles them
     float f2 = 0.0f;
 #pragma unroll
-    for (int k = 0; k < 32; ++k) f2 = fmaf(a[k], a[k], f2);
+    for (int r = 0; r < RW; ++r) f2 = fmaf(a[r], a[r], f2);
     f2 = warp_sumf(f2);
-    const float floor_g = 1e-14f * f2;
+    xch[1][w][lane] = make_float2(f2, 0.0f);
+    jw_bar();
+    float f2t = 0.0f;
+    for (int u = 0; u < JW; ++u) f2t += xch[1][u][lane].x;
+    const float floor_g = 1e-14f * f2t, tol2 = tol * tol;
+    int buf = 0;
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         bool any = false;
-        for (int round = 0; round < Kp - 1; ++round) {
-            // position of this lane's column in the round, and its partner's column
-            int pos = 0;
-            if (lane > 0 && lane < Kp) {
-                pos = (lane - 1 - round) % (Kp - 1);
-                if (pos < 0) pos += Kp - 1;
-                pos += 1;
-            }
-            const int partner = lane < Kp ? rr_player(Kp - 1 - pos, round, Kp) : lane;
+        for (int round = 0; round < Kp - 1; ++round, buf ^= 1) {
+            const int partner = ptab[round][lane];
             const int src = partner < 32 ? partner : lane;
-            float pa[32];
-            float g = 0.0f, nrm = 0.0f, pn = 0.0f;
+            float pa[RW];
+            float g = 0.0f, nrm = 0.0f;
 #pragma unroll
-            for (int k = 0; k < 32; ++k) {
-                pa[k] = __shfl_sync(0xffffffffu, a[k], src);
-                g = fmaf(a[k], pa[k], g);
-                nrm = fmaf(a[k], a[k], nrm);
-                pn = fmaf(pa[k], pa[k], pn);
+            for (int r = 0; r < RW; ++r) {
+                pa[r] = __shfl_sync(0xffffffffu, a[r], src);
+                g = fmaf(a[r], pa[r], g);
+                nrm = fmaf(a[r], a[r], nrm);
             }
+            xch[buf][w][lane] = make_float2(g, nrm);
+            jw_bar();
+            g = 0.0f;
+            nrm = 0.0f;
+#pragma unroll
+            for (int u = 0; u < JW; ++u) {
+                const float2 t = xch[buf][u][lane];
+                g += t.x;
+                nrm += t.y;
+            }
+            const float pn = __shfl_sync(0xffffffffu, nrm, src);
             const bool low = lane < partner;
             const float alpha = low ? nrm : pn, beta = low ? pn : nrm;  // norms^2 of the lower, higher column
-            const bool rot = lane < K && partner < K && fabsf(g) > tol * sqrtf(alpha * beta) && fabsf(g) > floor_g &&
+            const bool rot = lane < K && partner < K && g * g > tol2 * (alpha * beta) && fabsf(g) > floor_g &&
                              fabsf(g) > 1e-30f;
             float c = 1.0f, sp = 0.0f;  // own' = c own + sp partner
             if (rot) {
-                const float zeta = (beta - alpha) / (2.0f * g);
-                const float t = (zeta >= 0.0f ? 1.0f : -1.0f) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.0f)));
+                // tangent of the rotation angle: 2 g sign(d) / (|d| + sqrt(d^2 + 4 g^2)), d = beta - alpha
+                const float dd = beta - alpha, g2 = 2.0f * g;
+                const float r2 = fmaf(dd, dd, g2 * g2);
+                const float t = __fdividef(dd >= 0.0f ? g2 : -g2, fabsf(dd) + r2 * rsqrtf(r2));
                 c = rsqrtf(fmaf(t, t, 1.0f));
                 sp = low ? -t * c : t * c;
                 any = true;
             }
 #pragma unroll
-            for (int k = 0; k < 32; ++k) {
-                const float pv = __shfl_sync(0xffffffffu, v[k], src);
-                a[k] = fmaf(sp, pa[k], c * a[k]);
-                v[k] = fmaf(sp, pv, c * v[k]);
+            for (int r = 0; r < RW; ++r) {
+                const float pv = __shfl_sync(0xffffffffu, v[r], src);
+                a[r] = fmaf(sp, pa[r], c * a[r]);
+                v[r] = fmaf(sp, pv, c * v[r]);
             }
         }
-        if (!__any_sync(0xffffffffu, any)) break;
+        if (!__any_sync(0xffffffffu, any)) break;  // the same decision in every warp
     }
 #pragma unroll
-    for (int k = 0; k < 32; ++k)
-        if (lane < K && k < K) X[k * lds + lane] = (double)v[k];
+    for (int r = 0; r < RW; ++r) {
+        const int k = w * RW + r;
+        if (lane < K && k < K) X[k * lds + lane] = (double)v[r];
+    }
 }
 
 // ------------------------------------------------------------ lambda functions
@@ -566,6 +605,14 @@ __device__ __forceinline__ void gcv_dt(const R s[6], R mu, R &d1, R &d2) {
     d2 = (G2 * mu * mu + G1 * mu) * ln10 * ln10;
 }
 
+// size of the two terms whose difference is dG/dt: |dG/dt| below a small
+// multiple of it is rounding noise
+template <typename R>
+__device__ __forceinline__ R gcv_dt_scale(const R s[6], R mu) {
+    const R iD = R(1) / s[3];
+    return (fabs(s[1]) + fabs(R(2) * s[0] * s[4] * iD)) * iD * iD * mu * R(LN10);
+}
+
 // safeguarded Newton step for a root of an increasing function f (f1 = f')
 // inside [A, B], which the sign of f shrinks
 template <typename R>
@@ -588,6 +635,8 @@ __global__ void __launch_bounds__(ST, 1) k_small_solve(SmallArgs a) {
     __shared__ int s_fail, s_flag, s_idx[NW], s_end[4];
     __shared__ JacobiShared<float> jf;
     __shared__ JacobiShared<double> jd;
+    __shared__ float2 s_xch[2][JW][32];
+    __shared__ unsigned char s_ptab[31][32];
     const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int ld = a.ld;
     const int K = min(a.K[b], ld);
@@ -601,6 +650,8 @@ __global__ void __launch_bounds__(ST, 1) k_small_solve(SmallArgs a) {
         return;
     }
     const int Kp = K + (K & 1);
+    if (Kp <= 32)  // partners of the FP32 Jacobi rounds
+        for (int e = tid; e < (Kp - 1) * 32; e += ST) s_ptab[e >> 5][e & 31] = (unsigned char)rr_partner(e & 31, e >> 5, Kp);
     const int lds = (ld + 1) | 1;  // FP64 leading dimension: odd, >= Kp and >= K + 1
     const int ldf = ld + 3;        // FP32 leading dimension
     double *Rm = sm;               // Cholesky rows of M = G_A + rho G_L (kept for z)
@@ -675,8 +726,8 @@ __global__ void __launch_bounds__(ST, 1) k_small_solve(SmallArgs a) {
     double lam = a.lam_fixed;
     if (a.rule != MOF_RULE_FIXED) {
         // ------------------------------------------ 2a. FP32 Jacobi on C
-        if (K <= 32) {  // one warp, registers only
-            if (wid == 0) jacobi1_warp(Cm, lds, K, Xm, JACOBI32_MAX_SWEEPS, 1e-6f);
+        if (K <= 32) {  // registers only
+            if (wid < JW) jacobi1_warps(Cm, lds, K, Xm, JACOBI32_MAX_SWEEPS, 1e-6f, s_xch, s_ptab);
             __syncthreads();
         } else {
             for (int e = tid; e < Kp * Kp; e += ST) {
@@ -724,7 +775,7 @@ __global__ void __launch_bounds__(ST, 1) k_small_solve(SmallArgs a) {
         __syncthreads();
 
         // ------------------------------------------ 2c. FP64 Jacobi polish
-        jacobi<double>(Um, lds, (double *)nullptr, lds, gh, K, Kp, JACOBI64_MAX_SWEEPS, 1e-16f, 1e-18f, jd, s_redf);
+        jacobi<double>(Um, lds, (double *)nullptr, lds, gh, K, Kp, JACOBI64_MAX_SWEEPS, 1e-16f, 1e-12f, jd, s_redf);
         for (int i = tid; i < K; i += ST) {
             theta[i] = fmin(fmax(AT(Um, i, i), 0.0), 1.0);
             c2[i] = theta[i] > THETA_TINY ? gh[i] * gh[i] / theta[i] : 0.0;
@@ -798,25 +849,29 @@ __global__ void __launch_bounds__(ST, 1) k_small_solve(SmallArgs a) {
             }
             __syncthreads();
             if (wid == 0) {
-                double bv = s_refv[0];
+                double bv = s_refv[0], vmax = s_refv[0];
                 int ig = s_refi[0];
-                for (int w = 1; w < NREF; ++w)
+                for (int w = 1; w < NREF; ++w) {
                     if (s_refv[w] < bv || (s_refv[w] == bv && s_refi[w] < ig)) {
                         bv = s_refv[w];
                         ig = s_refi[w];
                     }
+                    vmax = fmax(vmax, s_refv[w]);
+                }
+                const bool flat = vmax - bv <= 1e-13 * bv;
                 // safeguarded Newton on dG/dt = 0 inside [t_{i-1}, t_{i+1}]: FP32 steps
                 // (in t - log10 rho) to a starting point, then FP64 steps on the full cell pair
                 const double A0 = lo + max(ig - 1, 0) * step, B0 = lo + min(ig + 1, GRID_POINTS - 1) * step;
                 float tf = (float)(ig * step - BRACKET_DECADES);
                 float Af0 = (float)(A0 - lrho), Bf0 = (float)(B0 - lrho);
-                for (int it = 0; it < NEWTON32_MAX; ++it) {
+                for (int it = 0; it < (flat ? 0 : NEWTON32_MAX); ++it) {
                     float s[6], d1, d2;
                     const float mu = exp10f(tf);
                     lam_terms6<float>(SF, mu, s);
                     for (int k = 0; k < 6; ++k) s[k] = warp_sum_t(s[k]);
                     gcv_dt<float>(s, mu, d1, d2);
                     if (d1 == 0.0f || !(d1 == d1)) break;
+                    if (fabsf(d1) <= 1e-5f * gcv_dt_scale<float>(s, mu)) break;  // at the rounding level
                     const float tn = newton_step<float>(tf, d1, d2, Af0, Bf0);
                     const float dt = fabsf(tn - tf);
                     tf = tn;
@@ -824,22 +879,29 @@ __global__ void __launch_bounds__(ST, 1) k_small_solve(SmallArgs a) {
                 }
                 double t = lrho + (double)tf, A1 = A0, B1 = B0;
                 if (!(t > A1 && t < B1)) t = lo + ig * step;
-                for (int it = 0; it < NEWTON_MAX; ++it) {
+                for (int it = 0; it < (flat ? 0 : NEWTON_MAX); ++it) {
                     double s6[6], d1, d2;
                     const double mu = exp10(t) / rho;
                     lam_terms6<double>(S, mu, s6);
                     warp_sum6(s6);
                     gcv_dt<double>(s6, mu, d1, d2);
                     if (d1 == 0.0) break;
+                    if (fabs(d1) <= 1e-12 * gcv_dt_scale<double>(s6, mu)) break;  // at the rounding level
+                    const bool pure = d2 > 0.0 && t - d1 / d2 > A1 && t - d1 / d2 < B1;
                     const double tn = newton_step<double>(t, d1, d2, A1, B1);
                     const double dt = fabs(tn - t);
                     t = tn;
                     if (dt <= 1e-10 * fmax(1.0, fabs(t)) || B1 - A1 <= 1e-10 * fmax(1.0, fabs(t))) break;
+                    if (pure && dt <= 1e-6 * fmax(1.0, fabs(t))) break;  // quadratic: the next step is ~1e-12
                 }
-                double N, D;
-                lam_terms_nd(S, exp10(t) / rho, N, D);
-                warp_sum2(N, D);
-                if (gcv_value(N, D) > bv) t = lo + ig * step;
+                if (flat) {
+                    t = lo + ig * step;
+                } else {
+                    double N, D;
+                    lam_terms_nd(S, exp10(t) / rho, N, D);
+                    warp_sum2(N, D);
+                    if (gcv_value(N, D) > bv) t = lo + ig * step;
+                }
                 if (lane == 0) s_t = t;
             }
             __syncthreads();
