@@ -577,33 +577,21 @@ __global__ void k_of_proj_gram(const double *__restrict__ GA, const double *__re
     }
 }
 
-// Gram columns of Solve-OF computed from V with the operators applied on the
-// fly: for column j and every i <= j,
-//   G_A[i][j] = (Ups v_i)^T (Ups v_j),  G_L[i][j] = (L v_i)^T (L v_j),  g[j] = (Ups v_j)^T b,
+// Gram columns of Solve-OF: for column j and every i <= j,
+//   G_A[i][j] = (Ups v_i)^T (Ups v_j) = v_i^T (Ups^T Ups v_j),
+//   G_L[i][j] = (L v_i)^T (L v_j) = v_i^T (L^T L v_j),   g[j] = (Ups v_j)^T b,
 // with Ups v = u_x v_x + u_y v_y pointwise and L the forward differences in x
-// and y of both velocity components (no boundary row), b = -u_t. Column j is
-// blockIdx.z (mode 0: the first columns, j < K) or K - 1 (mode 1: the vector
-// appended last, where appended). A CTA owns a chunk of OFC pixels of one pair:
-// it stages column j's five rows per pixel and u_x, u_y in shared memory, and
-// its warps stream the basis vectors i = w, w + 8, ... over the chunk, forming
-// their rows on the fly (coalesced loads), with FP32 sums per chunk in the
-// storage precision; k_of_gram_reduce adds the chunks in FP64.
+// and y of both velocity components (no boundary row), so L^T L is the graph
+// Laplacian of each component with free boundary. Column j is blockIdx.z (mode
+// 0: the first columns, j < K) or K - 1 (mode 1: the vector appended last,
+// where appended). A CTA owns a chunk of OFC pixels of one pair: it stages
+// Ups^T Ups v_j and L^T L v_j (both components) in shared memory, and its warps
+// stream the basis vectors i = w, w + 8, ... over the chunk with plain
+// coalesced loads, taking two dot products per vector, with sums per chunk in
+// the storage precision; k_of_gram_reduce adds the chunks in FP64.
 constexpr int OFG_T = 256;
 template <typename real>
 constexpr int ofc() { return 4096 / (int)sizeof(real); }  // pixels per chunk: 1024 (FP32), 512 (FP64)
-
-template <typename real>
-__device__ __forceinline__ void of_rows(const real *__restrict__ v, long long ns, int nx, int ny, int p, real ux, real uy,
-                                        real &a, real l[4]) {
-    const int y = p / nx, x = p - y * nx;
-    const real vx = v[p], vy = v[ns + p];
-    a = ux * vx + uy * vy;
-    const bool hx = x < nx - 1, hy = y < ny - 1;
-    l[0] = hx ? v[p + 1] - vx : (real)0;
-    l[1] = hy ? v[p + nx] - vx : (real)0;
-    l[2] = hx ? v[ns + p + 1] - vy : (real)0;
-    l[3] = hy ? v[ns + p + nx] - vy : (real)0;
-}
 
 template <typename real>
 __device__ __forceinline__ real warp_sum_r(real v) {
@@ -617,7 +605,7 @@ __global__ void __launch_bounds__(OFG_T) k_of_gram_cols(const real *__restrict__
                                                         const real *__restrict__ uy, const real *__restrict__ bof, int nx,
                                                         int ny, double *__restrict__ partial) {
     constexpr int OFC = ofc<real>();
-    __shared__ __align__(16) real s_a[OFC], s_l[4][OFC], s_ux[OFC], s_uy[OFC], s_hx[OFC], s_hy[OFC];
+    __shared__ __align__(16) real s_y[4][OFC];  // (Ups^T Ups v_j)_x, _y, (L^T L v_j)_x, _y
     __shared__ real s_red[OFG_T / 32];
     const int b = blockIdx.y, chunk = blockIdx.x, nchunk = gridDim.x;
     if (!act[b]) return;
@@ -630,29 +618,26 @@ __global__ void __launch_bounds__(OFG_T) k_of_gram_cols(const real *__restrict__
     const real *Vb = V + (long long)b * Kmax * N2;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     double *out = partial + (((long long)b * gridDim.z + blockIdx.z) * nchunk + chunk) * (2 * Kmax + 1);
-    // stage column j's rows, the fields and the boundary masks; g_j on the way
+    // stage the normal-equation parts of column j; g_j on the way
+    const real *vj = Vb + (long long)j * N2;
     real gs = 0;
     for (int q = tid; q < OFC; q += OFG_T) {
-        real a = 0, l[4] = {0, 0, 0, 0}, fx = 0, fy = 0, mx = 0, my = 0;
+        real y0 = 0, y1 = 0, l0 = 0, l1 = 0;
         if (q < len) {
             const int p = c0 + q;
             const int y = p / nx, x = p - y * nx;
-            fx = ux[b * ns + p];
-            fy = uy[b * ns + p];
-            mx = x < nx - 1 ? (real)1 : (real)0;
-            my = y < ny - 1 ? (real)1 : (real)0;
-            of_rows(Vb + (long long)j * N2, ns, nx, ny, p, fx, fy, a, l);
+            const real fx = ux[b * ns + p], fy = uy[b * ns + p];
+            const real a = fx * vj[p] + fy * vj[ns + p];
+            y0 = fx * a;
+            y1 = fy * a;
+            l0 = lap_at(vj, nx, ny, x, y);
+            l1 = lap_at(vj + ns, nx, ny, x, y);
             gs += a * bof[b * ns + p];
         }
-        s_a[q] = a;
-        s_l[0][q] = l[0];
-        s_l[1][q] = l[1];
-        s_l[2][q] = l[2];
-        s_l[3][q] = l[3];
-        s_ux[q] = fx;
-        s_uy[q] = fy;
-        s_hx[q] = mx;
-        s_hy[q] = my;
+        s_y[0][q] = y0;
+        s_y[1][q] = y1;
+        s_y[2][q] = l0;
+        s_y[3][q] = l1;
     }
     gs = warp_sum_r(gs);
     if (lane == 0) s_red[wid] = gs;
@@ -662,45 +647,29 @@ __global__ void __launch_bounds__(OFG_T) k_of_gram_cols(const real *__restrict__
         for (int w = 0; w < OFG_T / 32; ++w) dg += (double)s_red[w];
         out[2 * Kmax] = dg;
     }
-    // 4 pixels per lane with 128-bit loads where the layout allows it (FP32, aligned
-    // rows, a full chunk); masked rows (x = nx-1 or y = ny-1) read in-bounds neighbours
-    // that the masks zero
-    const bool quad = sizeof(real) == 4 && (nx % 4) == 0 && len == OFC;
+    // 4 pixels per lane with 16-byte loads where the layout allows it (FP32, a full
+    // chunk, both components 16-byte aligned)
+    const bool quad = sizeof(real) == 4 && (ns % 4) == 0 && len == OFC;
     for (int i = wid; i <= j; i += OFG_T / 32) {
         const real *vi = Vb + (long long)i * N2 + c0;
         real ga = 0, gl = 0;
         if (quad) {
-            const float *vf = reinterpret_cast<const float *>(vi);
-            for (int q = lane * 4; q < OFC; q += 128) {
-                const bool last_row = c0 + q + nx >= ns;  // this quad's y = ny-1
-                const float4 X = *reinterpret_cast<const float4 *>(vf + q);
-                const float4 Y = *reinterpret_cast<const float4 *>(vf + ns + q);
-                const float4 Xn = last_row ? X : *reinterpret_cast<const float4 *>(vf + q + nx);
-                const float4 Yn = last_row ? Y : *reinterpret_cast<const float4 *>(vf + ns + q + nx);
-                const bool row_end = ((c0 + q + 4) % nx) == 0;
-                const float x4 = row_end ? X.w : vf[q + 4], y4 = row_end ? Y.w : vf[ns + q + 4];
-                const float xs[5] = {X.x, X.y, X.z, X.w, x4}, ys[5] = {Y.x, Y.y, Y.z, Y.w, y4};
-                const float xn[4] = {Xn.x, Xn.y, Xn.z, Xn.w}, yn[4] = {Yn.x, Yn.y, Yn.z, Yn.w};
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int qq = q + e;
-                    const float hx = s_hx[qq], hy = s_hy[qq];
-                    const float ai = s_ux[qq] * xs[e] + s_uy[qq] * ys[e];
-                    const float l0 = hx * (xs[e + 1] - xs[e]), l1 = hy * (xn[e] - xs[e]);
-                    const float l2 = hx * (ys[e + 1] - ys[e]), l3 = hy * (yn[e] - ys[e]);
-                    ga += ai * s_a[qq];
-                    gl += l0 * s_l[0][qq] + l1 * s_l[1][qq] + l2 * s_l[2][qq] + l3 * s_l[3][qq];
-                }
+            const float4 *X4 = reinterpret_cast<const float4 *>(vi);
+            const float4 *Y4 = reinterpret_cast<const float4 *>(vi + ns);
+            const float4 *A0 = reinterpret_cast<const float4 *>(s_y[0]), *A1 = reinterpret_cast<const float4 *>(s_y[1]);
+            const float4 *L0 = reinterpret_cast<const float4 *>(s_y[2]), *L1 = reinterpret_cast<const float4 *>(s_y[3]);
+#pragma unroll 2
+            for (int q = lane; q < OFC / 4; q += 32) {
+                const float4 X = __ldcs(X4 + q), Y = __ldcs(Y4 + q);
+                const float4 a0 = A0[q], a1 = A1[q], l0 = L0[q], l1 = L1[q];
+                ga += X.x * a0.x + X.y * a0.y + X.z * a0.z + X.w * a0.w + Y.x * a1.x + Y.y * a1.y + Y.z * a1.z + Y.w * a1.w;
+                gl += X.x * l0.x + X.y * l0.y + X.z * l0.z + X.w * l0.w + Y.x * l1.x + Y.y * l1.y + Y.z * l1.z + Y.w * l1.w;
             }
         } else {
             for (int q = lane; q < len; q += 32) {
-                const real hx = s_hx[q], hy = s_hy[q];
                 const real vx = vi[q], vy = vi[ns + q];
-                const real ai = s_ux[q] * vx + s_uy[q] * vy;
-                const real l0 = hx != 0 ? vi[q + 1] - vx : (real)0, l1 = hy != 0 ? vi[q + nx] - vx : (real)0;
-                const real l2 = hx != 0 ? vi[ns + q + 1] - vy : (real)0, l3 = hy != 0 ? vi[ns + q + nx] - vy : (real)0;
-                ga += ai * s_a[q];
-                gl += l0 * s_l[0][q] + l1 * s_l[1][q] + l2 * s_l[2][q] + l3 * s_l[3][q];
+                ga += vx * s_y[0][q] + vy * s_y[1][q];
+                gl += vx * s_y[2][q] + vy * s_y[3][q];
             }
         }
         ga = warp_sum_r(ga);
