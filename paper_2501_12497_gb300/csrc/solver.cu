@@ -119,8 +119,8 @@ struct Arena {
     }
 };
 
-constexpr int MAX_OF_STREAMS = 16;
-constexpr int AUTO_OF_STREAMS = 4;
+constexpr int MAX_OF_STREAMS = 32;
+constexpr int AUTO_OF_STREAMS = 32;
 
 template <typename real>
 struct WS {
@@ -567,11 +567,14 @@ __global__ void k_of_proj_gram(const double *__restrict__ GA, const double *__re
     const int Kb = min(K[b], ld);
     const double *A = GA + (long long)b * ld * ld, *L = GL + (long long)b * ld * ld, *zb = z + (long long)b * ld;
     const double gm = gam[b];
+    // the Grams are stored symmetric: row i is read as column i, lanes over i (coalesced)
     for (int i = lane; i < Kb; i += 32) {
         double sa = 0.0, sl = 0.0;
+#pragma unroll 4
         for (int k = 0; k < Kb; ++k) {
-            sa += A[i * ld + k] * zb[k];
-            sl += L[i * ld + k] * zb[k];
+            const double zk = zb[k];
+            sa += A[k * ld + i] * zk;
+            sl += L[k * ld + i] * zk;
         }
         c[(long long)b * ld + i] = sa + gm * sl - g[(long long)b * ld + i];
     }
@@ -1567,7 +1570,7 @@ mof_status mof_autotune(mof_problem *const *problems, int count, mof_solver_para
     int best = -1;
     float best_t = 0.0f;
     mof_status out = MOF_OK;
-    for (int g : {1, 2, 4, 8}) {
+    for (int g : {1, 2, 4, 8, 16, 32}) {
         if (g > maxp && g != 1) continue;
         for (auto &t : trial) t.of_streams = g;
         // the first run captures the graphs of this configuration; the second is timed

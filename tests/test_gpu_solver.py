@@ -179,17 +179,18 @@ def test_full_size_precision_form_properties():
 
 @pytest.mark.parametrize("prec", [api.MOF_FP32, api.MOF_FP64])
 def test_solve_of_stream_groups_do_not_change_the_result(prec):
-    """Solve-OF run as 1, 3 (uneven) and 7 groups of frame pairs on separate streams:
-    every kernel works per pair, so the velocities agree bit for bit."""
+    """Solve-OF run as 1, 3 (uneven), 7 (one pair each) and 32 (more groups than
+    pairs: one pair each) groups of frame pairs on separate streams: every kernel
+    works per pair, so the velocities agree bit for bit."""
     w = synth.moving_disks(40, 8, 8, 40, radii=(5.0, 8.0), seed=6)
     p = problem(w, prec)
     u = torch.tensor(w.u_true.astype(npdt(prec)), device="cuda").reshape(-1)
     out = []
-    for g in (1, 3, 7):
+    for g in (1, 3, 7, 32):
         s = torch.empty(p.nv, dtype=tdt(prec), device="cuda")
         api.mof_solve_of(p, api.mof_default_params(of_ell=5, of_iters=6, of_streams=g), u, s)
         out.append(s.cpu())
-    assert torch.equal(out[0], out[1]) and torch.equal(out[0], out[2])
+    assert all(torch.equal(out[0], o) for o in out[1:])
 
 
 def test_mmgks_of_stream_groups_do_not_change_the_result():
