@@ -248,7 +248,7 @@ template <typename real>
 __global__ void __launch_bounds__(SDT) k_sub_dot(const real *__restrict__ V, long long N, int Kmax, const int *__restrict__ K,
                                                  const int *__restrict__ act, const double *__restrict__ c, long long cstride,
                                                  const real *x, long long xstride, real *out, long long ostride,
-                                                 double *__restrict__ partial, int nchunk, int *__restrict__ err) {
+                                                 double *__restrict__ partial, int nchunk, int *__restrict__ err, int kcap) {
     constexpr int CH = sdch<real>();
     constexpr int EPT = CH / SDT;  // elements per thread: 4 (FP32) or 2 (FP64), 16 bytes
     using vec_t = typename std::conditional<sizeof(real) == 4, float4, double2>::type;
@@ -259,7 +259,11 @@ __global__ void __launch_bounds__(SDT) k_sub_dot(const real *__restrict__ V, lon
     __shared__ __align__(8) unsigned long long bar;
     const int b = blockIdx.y, chunk = blockIdx.x, tid = threadIdx.x;
     if (act && !act[b]) return;
-    const int Kb = min(K[b], Kmax);
+    int Kb = min(K[b], Kmax);
+    if (Kb > kcap) {  // the tile holds kcap vectors: a caller's bound was wrong
+        if (tid == 0 && err) atomicOr(err, 8);
+        Kb = kcap;
+    }
     const long long c0 = (long long)chunk * CH;
     const int len = (int)min((long long)CH, N - c0);
     const unsigned bar_a = smem_u32(&bar);
@@ -494,7 +498,7 @@ void Krylov<real>::norm2(const real *x, long long N, long long xstride, int nb, 
 
 template <typename real>
 bool Krylov<real>::sub_dot(const BasisRef<real> &B, const double *c, long long cstride, real *x, long long xstride,
-                           double *out, cudaStream_t st) const {
+                           double *out, cudaStream_t st, int kcap) const {
     const long long es = sizeof(real);
     const bool ok = B.Kmax <= 64 && (B.N * es) % 16 == 0 && (xstride * es) % 16 == 0 &&
                     (reinterpret_cast<uintptr_t>(B.V) % 16) == 0 && (reinterpret_cast<uintptr_t>(x) % 16) == 0;
@@ -506,9 +510,10 @@ bool Krylov<real>::sub_dot(const BasisRef<real> &B, const double *c, long long c
         configured.store(true);
     }
     const int nc = (int)subdot_chunks(B.N, (int)es);
-    const size_t smem = (size_t)(B.Kmax + 1) * SD_BYTES;
+    const int kc = kcap > 0 ? std::min(kcap, B.Kmax) : B.Kmax;  // vectors the tile holds
+    const size_t smem = (size_t)(kc + 1) * SD_BYTES;
     ::mof::count_launch(), k_sub_dot<real><<<dim3(nc, B.B), SDT, smem, st>>>(B.V, B.N, B.Kmax, B.K, B.act, c, cstride, x, xstride,
-                                                                         x, xstride, partial, nc, err);
+                                                                         x, xstride, partial, nc, err, kc);
     DotOuts o{};
     o.o[0] = DotOut{out, B.Kmax, 1, 0, 0, 1.0};
     ::mof::count_launch(), k_sum_chunks<<<dim3((B.Kmax + SUMT / 32 - 1) / (SUMT / 32), B.B), SUMT, 0, st>>>(partial, nc, 1, B.Kmax,
@@ -526,11 +531,11 @@ void Krylov<real>::reorth(const BasisRef<real> &B, real *x, long long xstride, d
 
 template <typename real>
 void Krylov<real>::reorth_second(const BasisRef<real> &B, real *x, long long xstride, const double *c1, double *coef,
-                                 double *nrm2_out, cudaStream_t st) const {
+                                 double *nrm2_out, cudaStream_t st, int kcap) const {
     // the first projection's coefficients are given (c1; null: zero), the second are
     // taken by dot products, fused with the first update where the layout allows
     if (c1) {
-        if (!sub_dot(B, c1, B.Kmax, x, xstride, coef, st)) {
+        if (!sub_dot(B, c1, B.Kmax, x, xstride, coef, st, kcap)) {
             subtract(B, c1, B.Kmax, x, xstride, x, xstride, nullptr, st);
             dots(B, x, xstride, coef, B.Kmax, 1.0, st);
         }

@@ -1077,7 +1077,8 @@ static mof_status solve_of_impl(mof_problem *p, const mof_solver_params &prm, WS
                 // dot products (fused with the first update); then the second update
                 double *cg = w.coef_of + (long long)b0 * Kof;
                 ::mof::count_launch(), k_of_proj_gram<<<nb, 32, 0, gst>>>(sa.GA, sa.GL, sa.g, sa.z, sa.lam, Kvg, actg, Kof, cg);
-                kg.reorth_second(BAg, wvg, N2, cg, cg, w.nrm_of + b0, gst);
+                // at GKS iteration it the basis holds at most of_ell + it vectors (one append per iteration)
+                kg.reorth_second(BAg, wvg, N2, cg, cg, w.nrm_of + b0, gst, std::min(Kof, prm.of_ell + it));
                 kg.append(BAg, Kvg, wvg, N2, w.nrm_of + b0, w.scale_of + b0, tol, w.grow_of + b0, appg, nullptr, gst);
             }
             {
@@ -1392,6 +1393,7 @@ mof_status SolveRun<real>::result() {
             report[k].of_basis_max = (int)r[6];
         }
     if (err & 4) return fail(MOF_ETIMEOUT, "a bounded device wait ran out (code %d)", err);
+    if (err & 8) return fail(MOF_ENUMERIC, "a basis exceeded an internal size bound (code %d)", err);
     if (err) return fail(MOF_ENUMERIC, "device reported a numerical failure (code %d): factorisation or non-finite value", err);
     return MOF_OK;
 }
@@ -1429,6 +1431,7 @@ static mof_status solve_of_entry(mof_problem *p, const mof_solver_params &prm, c
     MOF_CUDA(cudaStreamSynchronize(st));
     if (tm) tm->collect();
     if (err & 4) return fail(MOF_ETIMEOUT, "a bounded device wait ran out (code %d)", err);
+    if (err & 8) return fail(MOF_ENUMERIC, "a basis exceeded an internal size bound (code %d)", err);
     if (err) return fail(MOF_ENUMERIC, "device reported a numerical failure (code %d)", err);
     return MOF_OK;
 }

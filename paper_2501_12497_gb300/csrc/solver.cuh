@@ -73,12 +73,14 @@ struct Krylov {
     // the same with the first projection's coefficients V^T x supplied by the caller from an
     // exact identity (c1 [B][Kmax]; null when they are zero, as for a Golub-Kahan residual),
     // so that only the second projection streams V for its dot products
+    // kcap (> 0): a bound on every K[b] known to the caller, which sizes the fused pass's
+    // shared-memory tile (a larger K[b] sets bit 8 of err)
     void reorth_second(const BasisRef<real> &B, real *x, long long xstride, const double *c1, double *coef,
-                       double *nrm2_out, cudaStream_t st) const;
+                       double *nrm2_out, cudaStream_t st, int kcap = 0) const;
     // x[b] <- x[b] - V[b] c[b] and out[b] = V[b]^T x[b] in one pass over V (false: not
     // applicable to this layout, nothing enqueued)
     bool sub_dot(const BasisRef<real> &B, const double *c, long long cstride, real *x, long long xstride, double *out,
-                 cudaStream_t st) const;
+                 cudaStream_t st, int kcap = 0) const;
     // V[b][K[b]] = x[b]/||x[b]||, K[b]++ unless ||x[b]|| <= tol*scale[b] (then grow[b] = 0);
     // scale may be null (only ||x|| > 0 required); stage[b] (may be null) receives the new vector
     void append(const BasisRef<real> &B, int *Kmut, const real *x, long long xstride, const double *nrm2,
