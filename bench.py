@@ -43,10 +43,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-class-step", action="store_true",
                     help="skip the instrumented single-stream step (no class times, no roofline); for profiling runs")
-    ap.add_argument("--workload", choices=["ellipses256x256x32", "batch48", "ellipses1024x1024x64", "operators"],
+    ap.add_argument("--workload", choices=["ellipses256x256x32", "batch48", "ellipses1024x1024x64", "operators",
+                                           "solve_of"],
                     default="ellipses256x256x32",
                     help="the 256x256x32 ellipse problem (default), 48 uneven problems batched, "
-                         "or the 1024x1024x64 problem")
+                         "the 1024x1024x64 problem, every operator alone, or Solve-OF alone "
+                         "(one call per step on the 256x256x32 frames)")
     ap.add_argument("--of-streams", type=int, default=0,
                     help="frame-pair groups of Solve-OF on separate streams (0 = library default)")
     return ap.parse_args()
@@ -515,6 +517,45 @@ def run_operators(args):
     print(json.dumps(line), flush=True)
 
 
+def run_solve_of(args):
+    """Solve-OF (Alg. 2) alone: one mof_solve_of call per step on the true frames of the
+    256x256x32 ellipse workload (31 frame pairs, of_ell 10, 20 GKS iterations), inputs
+    resident, L2 flushed before each call, CUDA events around it."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2501_12497_gb300 import api, synth
+    api.load()
+    w = synth.precision_form(0)
+    p = api.mof_problem_create(w.nx, w.ny, w.nt, w.nb, w.na, w.angles, precision=api.MOF_FP32)
+    prm = api.mof_default_params(of_streams=args.of_streams)
+    u = torch.tensor(w.u_true.astype(np.float32), device="cuda").reshape(-1)
+    s = torch.empty(p.nv, dtype=torch.float32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        api.mof_solve_of(p, prm, u, s)
+    torch.cuda.synchronize()
+    l0 = api.mof_kernel_launches()
+    ms = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        api.mof_solve_of(p, prm, u, s)
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    tot = sum(ms)
+    line = {"metric": "solve_of_calls_per_s", "value": args.steps / (tot / 1e3), "unit": "calls/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps, "higher_is_better": True,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "solve_of ellipses256x256x32", "pairs": p.nt - 1, "of_ell": 10, "of_iters": 20,
+                       "of_streams": args.of_streams or "auto", "l2": "flushed before each call"},
+            "gpu_launches": api.mof_kernel_launches() - l0}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -525,6 +566,8 @@ def main():
         run_large(args)
     elif args.workload == "operators":
         run_operators(args)
+    elif args.workload == "solve_of":
+        run_solve_of(args)
     else:
         run_ours(args)
 

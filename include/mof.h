@@ -87,7 +87,7 @@ typedef struct {
                               this many groups on separate streams, so that one group's small
                               FP64 solves overlap another group's bandwidth-bound kernels; the
                               result does not depend on it. 0 = automatic: one group per pair,
-                              up to 32 groups; at most 32 */
+                              up to 64 groups; at most 64 */
 } mof_solver_params;
 
 /* One record per outer iteration k of mof_solve (host struct). */
@@ -232,7 +232,7 @@ mof_status mof_solve_batch(mof_problem *const *problems, int count, const mof_so
 /* Autotuner of the execution parameter of_streams (the number of frame-pair
  * groups Solve-OF runs on separate streams): times n_probe outer iterations of
  * the batch (mof_solve_batch; count = 1 tunes a single problem) for each
- * candidate in {1, 2, 4, 8, 16, 32} (at most the number of frame pairs), each after an
+ * candidate in {1, 2, 4, 8, 16, 32, 64} (at most the number of frame pairs), each after an
  * untimed run that captures its graphs, and writes the fastest into every
  * params[i].of_streams (and its time in milliseconds into *best_ms, may be
  * NULL). u_scratch[i] (n_i, device) receives the probes' images. The result of

@@ -119,8 +119,8 @@ struct Arena {
     }
 };
 
-constexpr int MAX_OF_STREAMS = 32;
-constexpr int AUTO_OF_STREAMS = 32;
+constexpr int MAX_OF_STREAMS = 64;
+constexpr int AUTO_OF_STREAMS = 64;
 
 template <typename real>
 struct WS {
@@ -153,6 +153,9 @@ struct WS {
     IterGraph graphs[8];
     mof_solver_params gkey{};
     int gkey_n = -1;
+    // the stand-alone Solve-OF (mof_solve_of), captured once per parameter set
+    IterGraph ofgraph;
+    mof_solver_params ofkey{};
     cudaStream_t ss = nullptr;  // internal stream (graphs cannot be captured on the legacy stream)
     cudaEvent_t join = nullptr;
     // Solve-OF pair groups: one stream each, forked from and joined to ss
@@ -167,6 +170,11 @@ struct WS {
             for (auto e : g.owned) cudaEventDestroy(e);
             g = IterGraph();
         }
+        drop_of_graph();
+    }
+    void drop_of_graph() {
+        if (ofgraph.exec) cudaGraphExecDestroy(ofgraph.exec);
+        ofgraph = IterGraph();
     }
 };
 
@@ -1417,17 +1425,55 @@ static mof_status solve_impl(mof_problem *p, const mof_solver_params &prm, int n
 }
 
 template <typename real>
-static mof_status solve_of_entry(mof_problem *p, const mof_solver_params &prm, const real *u, real *s, cudaStream_t st) {
+static mof_status solve_of_entry(mof_problem *p, const mof_solver_params &prm, const real *u, real *s, cudaStream_t ust) {
     Holder *h = holder(p);
     WS<real> *&wp = ws_slot<real>(h);
     MOF_TRY(ensure_ws<real>(p, prm, 1, wp));
+    WS<real> &w = *wp;
     Timer *tm = p->timing ? &h->timer : nullptr;
     if (tm) tm->reset();
-    MOF_TRY(prepare_small_solve(wp->Kof));
-    ::mof::count_launch(), k_fill_int<<<1, 32, 0, st>>>(wp->err, 1, 0);
-    MOF_TRY(solve_of_impl<real>(p, prm, *wp, u, s, tm, st));
+    MOF_TRY(prepare_small_solve(w.Kof));
+    // all work on the problem's own stream, ordered after the caller's stream
+    const cudaStream_t st = w.ss;
+    MOF_CUDA(cudaEventRecord(w.join, ust));
+    MOF_CUDA(cudaStreamWaitEvent(st, w.join, 0));
+    const long long nimg = p->n, nvel = (long long)(p->nt - 1) * 2 * p->ns;
+    if (tm) {  // timed calls run eagerly (the scopes record events around each class)
+        ::mof::count_launch(), k_fill_int<<<1, 32, 0, st>>>(w.err, 1, 0);
+        MOF_TRY(solve_of_impl<real>(p, prm, w, u, s, tm, st));
+    } else {
+        // one captured graph per parameter set, over workspace copies of u and s (fixed
+        // addresses), replayed: the Solve-OF launches thousands of short kernels
+        if (w.ofgraph.exec && std::memcmp(&w.ofkey, &prm, sizeof(prm)) != 0) w.drop_of_graph();
+        if (!w.ofgraph.exec) {
+            const long long before = launches_so_far();
+            MOF_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            ::mof::count_launch(), k_fill_int<<<1, 32, 0, st>>>(w.err, 1, 0);
+            const mof_status cs = solve_of_impl<real>(p, prm, w, w.u, w.s, nullptr, st);
+            cudaGraph_t graph = nullptr;
+            const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+            w.ofgraph.kernels = launches_so_far() - before;
+            count_launches_add(-w.ofgraph.kernels);  // captured, not executed
+            if (cs != MOF_OK || ce != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                if (cs != MOF_OK) return cs;
+                return cuda_fail(ce, "graph capture of Solve-OF", __FILE__, __LINE__);
+            }
+            const cudaError_t ie = cudaGraphInstantiate(&w.ofgraph.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ie != cudaSuccess) {
+                w.ofgraph.exec = nullptr;
+                return cuda_fail(ie, "graph instantiation", __FILE__, __LINE__);
+            }
+            w.ofkey = prm;
+        }
+        MOF_CUDA(cudaMemcpyAsync(w.u, u, sizeof(real) * nimg, cudaMemcpyDeviceToDevice, st));
+        MOF_CUDA(cudaGraphLaunch(w.ofgraph.exec, st));
+        count_launches_add(w.ofgraph.kernels);
+        MOF_CUDA(cudaMemcpyAsync(s, w.s, sizeof(real) * nvel, cudaMemcpyDeviceToDevice, st));
+    }
     int err = 0;
-    MOF_CUDA(cudaMemcpyAsync(&err, wp->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MOF_CUDA(cudaMemcpyAsync(&err, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     MOF_CUDA(cudaStreamSynchronize(st));
     if (tm) tm->collect();
     if (err & 4) return fail(MOF_ETIMEOUT, "a bounded device wait ran out (code %d)", err);
@@ -1573,7 +1619,7 @@ mof_status mof_autotune(mof_problem *const *problems, int count, mof_solver_para
     int best = -1;
     float best_t = 0.0f;
     mof_status out = MOF_OK;
-    for (int g : {1, 2, 4, 8, 16, 32}) {
+    for (int g : {1, 2, 4, 8, 16, 32, 64}) {
         if (g > maxp && g != 1) continue;
         for (auto &t : trial) t.of_streams = g;
         // the first run captures the graphs of this configuration; the second is timed
