@@ -393,6 +393,38 @@ __global__ void k_append_prep(int *__restrict__ K, int Kmax, const double *__res
     if (appended) appended[b] = ok;
 }
 
+// The same with ||x[b]||^2 summed here from the per-block partials of the update
+// that formed x (one warp per problem, lanes over the partials, then a fixed tree:
+// the order of k_sum_scalar_chunks), written to nrm2_out, and sqrt(||x[b]||^2)
+// written to sq1[b] and sq2[b] (each may be null) for problems still growing
+// (grow[b] as it was on entry).
+template <typename real>
+__global__ void k_append_prep_sum(int *__restrict__ K, int Kmax, const double *__restrict__ parts, int nparts,
+                                  double *__restrict__ nrm2_out, const double *__restrict__ scale, double tol,
+                                  int *__restrict__ grow, int B, int *__restrict__ slot, real *__restrict__ inv,
+                                  int *__restrict__ appended, double *__restrict__ sq1, double *__restrict__ sq2) {
+    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (b >= B) return;
+    double s = 0.0;
+    for (int c = lane; c < nparts; c += 32) s += parts[(long long)b * nparts + c];
+    s = warp_sum(s);
+    if (lane != 0) return;
+    nrm2_out[b] = s;
+    const int g = grow[b];
+    if (g) {
+        const double r = sqrt(s);
+        if (sq1) sq1[b] = r;
+        if (sq2) sq2[b] = r;
+    }
+    const int Kb = K[b];
+    const bool ok = append_ok(g, Kb, Kmax, s, scale, b, tol);
+    slot[b] = ok ? Kb : -1;
+    inv[b] = ok ? (real)(1.0 / sqrt(s)) : (real)0;
+    if (ok) K[b] = Kb + 1;
+    else grow[b] = 0;
+    if (appended) appended[b] = ok;
+}
+
 template <typename real>
 __global__ void __launch_bounds__(KT) k_append(real *__restrict__ V, long long N, int Kmax, const int *__restrict__ slot,
                                                const real *__restrict__ inv, const real *__restrict__ x, long long xstride,
@@ -490,6 +522,20 @@ void Krylov<real>::subtract(const BasisRef<real> &B, const double *c, long long 
 }
 
 template <typename real>
+int Krylov<real>::subtract_parts(const BasisRef<real> &B, const double *c, long long cstride, const real *x, long long xstride,
+                                 real *out, long long ostride, cudaStream_t st) const {
+    const int nb = (int)((B.N + 4LL * CT - 1) / (4LL * CT));
+    const bool vec = vec_ok<real>(B.V, B.N, (long long)B.Kmax * B.N) && (ostride % 4 == 0);
+    if (vec)
+        ::mof::count_launch(), k_combine<real, 1, true><<<dim3(nb, B.B), CT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, c, cstride, x,
+                                                                                   xstride, out, ostride, partial, nb);
+    else
+        ::mof::count_launch(), k_combine<real, 1, false><<<dim3(nb, B.B), CT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, c, cstride, x,
+                                                                                    xstride, out, ostride, partial, nb);
+    return nb;
+}
+
+template <typename real>
 void Krylov<real>::norm2(const real *x, long long N, long long xstride, int nb, double *out, cudaStream_t st) const {
     const int nc = (int)krylov_chunks(N);
     ::mof::count_launch(), k_norm2<real><<<dim3(nc, nb), KT, 0, st>>>(x, N, xstride, partial, nc);
@@ -543,6 +589,32 @@ void Krylov<real>::reorth_second(const BasisRef<real> &B, real *x, long long xst
         dots(B, x, xstride, coef, B.Kmax, 1.0, st);
     }
     subtract(B, coef, B.Kmax, x, xstride, x, xstride, nrm2_out, st);
+}
+
+template <typename real>
+int Krylov<real>::reorth_second_parts(const BasisRef<real> &B, real *x, long long xstride, const double *c1, double *coef,
+                                      cudaStream_t st, int kcap) const {
+    if (c1) {
+        if (!sub_dot(B, c1, B.Kmax, x, xstride, coef, st, kcap)) {
+            subtract(B, c1, B.Kmax, x, xstride, x, xstride, nullptr, st);
+            dots(B, x, xstride, coef, B.Kmax, 1.0, st);
+        }
+    } else {
+        dots(B, x, xstride, coef, B.Kmax, 1.0, st);
+    }
+    return subtract_parts(B, coef, B.Kmax, x, xstride, x, xstride, st);
+}
+
+template <typename real>
+void Krylov<real>::append_parts(const BasisRef<real> &B, int *Kmut, const real *x, long long xstride, int nparts,
+                                double *nrm2_out, const double *scale, double tol, int *grow, int *appended, real *stage,
+                                double *sq1, double *sq2, cudaStream_t st) const {
+    int *slot = reinterpret_cast<int *>(aux);
+    real *inv = reinterpret_cast<real *>(aux + B.B);
+    ::mof::count_launch(), k_append_prep_sum<real><<<(B.B + 1) / 2, 64, 0, st>>>(Kmut, B.Kmax, partial, nparts, nrm2_out, scale, tol,
+                                                                                grow, B.B, slot, inv, appended, sq1, sq2);
+    const int blocks = (int)std::min<long long>(1024, (B.N + KT - 1) / KT);
+    ::mof::count_launch(), k_append<real><<<dim3(blocks, B.B), KT, 0, st>>>(B.V, B.N, B.Kmax, slot, inv, x, xstride, stage);
 }
 
 template <typename real>

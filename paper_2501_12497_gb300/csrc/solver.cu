@@ -1026,14 +1026,14 @@ static mof_status solve_of_impl(mof_problem *p, const mof_solver_params &prm, WS
             kg.append(BU, Kug, bofg, ns, bbg, nullptr, 0.0, gkbg, nullptr, nullptr, gst);
             for (int j = 0; j < w.of_ell && j < prm.of_ell; ++j) {
                 ::mof::count_launch(), k_of_upsT<real><<<dim3(fb(ns), nb), 256, 0, gst>>>(uxg, uyg, Ug, ldU, j, Vg, Kof, w.beta_of + b0, wvg, ns, gkbg);
-                kg.reorth_second(BV, wvg, N2, nullptr, w.coef_of + (long long)b0 * Kof, nrmg, gst);  // V^T x = 0 by the recurrence
-                if (j == 0) ::mof::count_launch(), k_sqrt_into_if<<<pb, 64, 0, gst>>>(nrmg, w.alpha1_of + b0, nb, gkbg);
-                ::mof::count_launch(), k_sqrt_into_if<<<pb, 64, 0, gst>>>(nrmg, w.alpha_of + b0, nb, gkbg);
-                kg.append(BV, Kvg, wvg, N2, nrmg, j == 0 ? nullptr : w.alpha1_of + b0, tol, gkbg, nullptr, nullptr, gst);
+                // V^T x = 0 by the recurrence; alpha (and alpha_1) = ||x|| with the append
+                const int nv = kg.reorth_second_parts(BV, wvg, N2, nullptr, w.coef_of + (long long)b0 * Kof, gst);
+                kg.append_parts(BV, Kvg, wvg, N2, nv, nrmg, j == 0 ? nullptr : w.alpha1_of + b0, tol, gkbg, nullptr, nullptr,
+                                w.alpha_of + b0, j == 0 ? w.alpha1_of + b0 : nullptr, gst);
                 ::mof::count_launch(), k_of_ups<real><<<dim3(fb(ns), nb), 256, 0, gst>>>(uxg, uyg, Vg, Kof, j, Ug, ldU, w.alpha_of + b0, wug, ns, gkbg);
-                kg.reorth_second(BU, wug, ns, nullptr, w.coefU_of + (long long)b0 * ldU, nrmg, gst);
-                ::mof::count_launch(), k_sqrt_into_if<<<pb, 64, 0, gst>>>(nrmg, w.beta_of + b0, nb, gkbg);
-                kg.append(BU, Kug, wug, ns, nrmg, w.beta1_of + b0, tol, gkbg, nullptr, nullptr, gst);
+                const int nu = kg.reorth_second_parts(BU, wug, ns, nullptr, w.coefU_of + (long long)b0 * ldU, gst);
+                kg.append_parts(BU, Kug, wug, ns, nu, nrmg, w.beta1_of + b0, tol, gkbg, nullptr, nullptr, w.beta_of + b0, nullptr,
+                                gst);
             }
         }
         const dim3 gg((p->nx + 31) / 32, (p->ny + 7) / 8, nb);
@@ -1086,8 +1086,9 @@ static mof_status solve_of_impl(mof_problem *p, const mof_solver_params &prm, WS
                 double *cg = w.coef_of + (long long)b0 * Kof;
                 ::mof::count_launch(), k_of_proj_gram<<<nb, 32, 0, gst>>>(sa.GA, sa.GL, sa.g, sa.z, sa.lam, Kvg, actg, Kof, cg);
                 // at GKS iteration it the basis holds at most of_ell + it vectors (one append per iteration)
-                kg.reorth_second(BAg, wvg, N2, cg, cg, w.nrm_of + b0, gst, std::min(Kof, prm.of_ell + it));
-                kg.append(BAg, Kvg, wvg, N2, w.nrm_of + b0, w.scale_of + b0, tol, w.grow_of + b0, appg, nullptr, gst);
+                const int np = kg.reorth_second_parts(BAg, wvg, N2, cg, cg, gst, std::min(Kof, prm.of_ell + it));
+                kg.append_parts(BAg, Kvg, wvg, N2, np, w.nrm_of + b0, w.scale_of + b0, tol, w.grow_of + b0, appg, nullptr, nullptr,
+                                nullptr, gst);
             }
             {
                 Scope sc(tm, "of_gram", gst);

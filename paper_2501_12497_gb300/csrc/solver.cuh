@@ -81,6 +81,18 @@ struct Krylov {
     // applicable to this layout, nothing enqueued)
     bool sub_dot(const BasisRef<real> &B, const double *c, long long cstride, real *x, long long xstride, double *out,
                  cudaStream_t st, int kcap = 0) const;
+    // x[b] <- x[b] - V[b] c[b], the per-block partials of ||x[b]||^2 left in partial;
+    // returns their number per problem (for append_parts)
+    int subtract_parts(const BasisRef<real> &B, const double *c, long long cstride, const real *x, long long xstride,
+                       real *out, long long ostride, cudaStream_t st) const;
+    // reorth_second with the final norm left as partials (returns their number per problem)
+    int reorth_second_parts(const BasisRef<real> &B, real *x, long long xstride, const double *c1, double *coef,
+                            cudaStream_t st, int kcap = 0) const;
+    // append with ||x||^2 summed from the nparts partials of the preceding update (written to
+    // nrm2_out), and sqrt(||x||^2) written to sq1 / sq2 (may be null) for problems still growing
+    void append_parts(const BasisRef<real> &B, int *Kmut, const real *x, long long xstride, int nparts, double *nrm2_out,
+                      const double *scale, double tol, int *grow, int *appended, real *stage, double *sq1, double *sq2,
+                      cudaStream_t st) const;
     // V[b][K[b]] = x[b]/||x[b]||, K[b]++ unless ||x[b]|| <= tol*scale[b] (then grow[b] = 0);
     // scale may be null (only ||x|| > 0 required); stage[b] (may be null) receives the new vector
     void append(const BasisRef<real> &B, int *Kmut, const real *x, long long xstride, const double *nrm2,
