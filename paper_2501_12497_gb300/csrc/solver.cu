@@ -248,6 +248,12 @@ mof_status apply_scratch(mof_problem *p, ScratchKind kind, void **out) {
 constexpr int TG_T = 256;      // theta-gram block
 constexpr int TG_PIX = 64;     // pixels per theta-gram tile
 constexpr int TG_ROWS = 4 * TG_PIX;
+// theta-gram CTAs per SM of the persistent grid: three in FP32 (registers bounded so that
+// three are resident), two in FP64 (unbounded registers)
+template <typename real>
+constexpr int tg_ctas_per_sm() { return sizeof(real) == 4 ? 3 : 2; }
+template <typename real>
+constexpr int tg_min_blocks() { return sizeof(real) == 4 ? 3 : 1; }
 
 template <typename real>
 static size_t theta_gram_smem(int Kmax) {
@@ -282,7 +288,7 @@ static mof_status ensure_ws(mof_problem *p, const mof_solver_params &prm, int n_
     const long long n = p->n, m = p->m, ns = p->ns, P = p->nt - 1, N2 = 2 * ns;
     int dev_sms = 152;
     cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, p->device);
-    w->gram_ctas = 2 * dev_sms;
+    w->gram_ctas = tg_ctas_per_sm<real>() * dev_sms;
     const long long partial = std::max(krylov_partial_doubles(std::max(n, m), Kmax), P * of_partial_per_pair(p, Kof, prm.of_ell));
     for (int pass = 0; pass < 2; ++pass) {
         Arena a;
@@ -782,7 +788,7 @@ __device__ __forceinline__ Quad<double> load_quad(const double *p) {
 }
 
 template <typename real>
-__global__ void __launch_bounds__(TG_T) k_theta_gram(const real *__restrict__ V, long long n, int Kmax, const int *__restrict__ Kp,
+__global__ void __launch_bounds__(TG_T, tg_min_blocks<real>()) k_theta_gram(const real *__restrict__ V, long long n, int Kmax, const int *__restrict__ Kp,
                                                      const real *__restrict__ uk, const real *__restrict__ s,
                                                      const real *__restrict__ sr, real eps2, int nx, int ny, int nt,
                                                      int rows, double *__restrict__ partial) {
