@@ -251,9 +251,9 @@ constexpr int TG_ROWS = 4 * TG_PIX;
 // theta-gram CTAs per SM of the persistent grid: three in FP32 (registers bounded so that
 // three are resident), two in FP64 (unbounded registers)
 template <typename real>
-constexpr int tg_ctas_per_sm() { return sizeof(real) == 4 ? 3 : 2; }
+constexpr int tg_ctas_per_sm() { return sizeof(real) == 4 ? 4 : 2; }
 template <typename real>
-constexpr int tg_min_blocks() { return sizeof(real) == 4 ? 3 : 1; }
+constexpr int tg_min_blocks() { return sizeof(real) == 4 ? 4 : 1; }
 
 template <typename real>
 static size_t theta_gram_smem(int Kmax) {
