@@ -802,8 +802,8 @@ __global__ void __launch_bounds__(TG_T, tg_min_blocks<real>()) k_theta_gram(cons
     const int tid = threadIdx.x;
     const int g = tid / nb1, blk = tid - g * nb1;
     const bool acc_on = g < RG && blk < nblk;
-    // rows of group g: [r0, r1), multiples of 4
-    const int rpg = ((TG_ROWS / RG + 3) / 4) * 4;
+    // rows of group g: [r0, r1), r0 a multiple of 4; the RG groups cover all TG_ROWS rows
+    const int rpg = (((TG_ROWS + RG - 1) / RG + 3) / 4) * 4;
     const int r0 = min(g * rpg, TG_ROWS), r1 = min(r0 + rpg, TG_ROWS);
     int I = 0, J = 0;
     if (acc_on) {

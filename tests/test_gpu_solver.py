@@ -200,3 +200,34 @@ def test_mmgks_of_stream_groups_do_not_change_the_result():
     b = _gpu_solve(w, api.MOF_FP32, 4, of_streams=4, **kw)
     np.testing.assert_array_equal(a[0], b[0])
     np.testing.assert_array_equal(a[1], b[1])
+
+
+@pytest.mark.parametrize("prec,tol", [(api.MOF_FP64, 1e-7), (api.MOF_FP32, 1e-3)])
+def test_solve_of_basis_beyond_32_matches_oracle(prec, tol):
+    """Solve-OF with of_ell = 20 and 15 GKS iterations: the basis grows to 34 vectors, past
+    the 32 the small solver keeps in registers (its shared-memory Jacobi path runs)."""
+    w = synth.moving_disks(48, 4, 8, 48, radii=(6.0, 9.0), seed=8)
+    p = problem(w, prec)
+    u = w.u_true.astype(npdt(prec))
+    ud = torch.tensor(u, device="cuda").reshape(-1)
+    s = torch.empty(p.nv, dtype=tdt(prec), device="cuda")
+    api.mof_solve_of(p, api.mof_default_params(of_ell=20, of_iters=15), ud, s)
+    want = OS.solve_of(u.astype(np.float64), OS.Params(of_ell=20, of_iters=15))
+    got = s.cpu().double().numpy().reshape(want.shape)
+    assert rel(got, want) <= tol, rel(got, want)
+
+
+def test_mmgks_of_fp64_image_basis_beyond_32_matches_oracle():
+    """MMGKS-OF with ell = 26 and 8 outer iterations: the image-step basis grows from 26 to
+    33 vectors, through the sizes where the weighted Theta Gram splits its 4x4 blocks into
+    row groups that do not divide a tile evenly (K = 29..32), and past the 32 of the small
+    solver's register path. 40x40x3 frames, 20 angles, 58 bins: enough data rows that
+    33 Golub-Kahan vectors stay well conditioned (rounding-level perturbations move the
+    oracle's own result by ~1e-9)."""
+    w = synth.moving_disks(40, 3, 20, 58, radii=(5.0, 8.0), seed=9)
+    kw = dict(ell=26, of_ell=3, of_iters=3)
+    ores = _oracle_solve(w, 8, **kw)
+    u, s, rep = _gpu_solve(w, api.MOF_FP64, 8, **kw)
+    assert max(r["basis"] for r in rep) > 32
+    assert rel(u, ores.u) <= 1e-7, rel(u, ores.u)
+    assert rel(s, ores.s) <= 1e-6, rel(s, ores.s)
