@@ -943,17 +943,24 @@ __global__ void __launch_bounds__(TG_T, tg_min_blocks<real>()) k_theta_gram(cons
     }
 }
 
-// G[i][j] = sum over the per-CTA partials (upper triangle), mirrored
+// G[i][j] = sum over the per-CTA partials (upper triangle), mirrored. One warp per
+// entry: lanes stride over the partials, then a fixed tree (deterministic); warps
+// stride over the K^2 entries.
 __global__ void k_gram_reduce(const double *__restrict__ partial, int nparts, int Kmax, const int *__restrict__ Kp,
                               double *__restrict__ G) {
     const int K = min(Kp[0], Kmax);
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < K * K; e += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int e = w0; e < K * K; e += nw) {
         const int i = e / K, j = e % K;
         if (i > j) continue;
         double s = 0.0;
-        for (int c = 0; c < nparts; ++c) s += partial[(long long)c * Kmax * Kmax + i * Kmax + j];
-        G[i * Kmax + j] = s;
-        G[j * Kmax + i] = s;
+        for (int c = lane; c < nparts; c += 32) s += partial[(long long)c * Kmax * Kmax + i * Kmax + j];
+        s = warp_sum(s);
+        if (lane == 0) {
+            G[i * Kmax + j] = s;
+            G[j * Kmax + i] = s;
+        }
     }
 }
 
@@ -1280,7 +1287,7 @@ mof_status SolveRun<real>::iteration(bool of_now, bool expand) {
             ::mof::count_launch(), k_theta_gram<real><<<w.gram_ctas, TG_T, tg_smem, st>>>(w.V, n, Kmax, w.K, w.u, w.s, w.sr, eps2, p->nx,
                                                                                      p->ny, p->nt, 2, gpart_m);
             if (of_now) MOF_CUDA(cudaStreamWaitEvent(st, w.side_done, 0));
-            ::mof::count_launch(), k_gram_reduce<<<8, 256, 0, st>>>(w.gpart, 2 * w.gram_ctas, Kmax, w.K, w.GT);
+            ::mof::count_launch(), k_gram_reduce<<<152, 256, 0, st>>>(w.gpart, 2 * w.gram_ctas, Kmax, w.K, w.GT);
         }
         {
             Scope sc(tm, "small_solve", st);
