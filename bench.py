@@ -178,18 +178,17 @@ class Clocks:
 
 
 # ------------------------------------------------------------ roofline models
-def reorth_bytes(nvec_list, N, pairs, es=4):
-    """Algorithmic bytes of the CGS2 reorthogonalisation and append of the Solve-OF
-    residuals over a solve. The first projection's coefficients come from the FP64
-    Gram matrices (V^T r = (G_A + gamma G_L) z - g), so the basis is streamed twice:
-    x' = x - V c1 together with c2 = V^T x' reads K basis vectors and x and writes x';
-    x'' = x' - V c2 reads K vectors and x' and writes x''; the append reads x'' and
-    writes the new basis vector. That is 2K + 6 vectors of N values, K the basis
-    size at each call, for every active pair."""
-    tot = 0
-    for K in nvec_list:
-        tot += pairs * es * N * (2 * K + 6)
-    return tot
+def subdot_bytes(nvec_list, N, pairs, es=4):
+    """Algorithmic bytes of the fused CGS pass (k_sub_dot) over a solve: x - V c1 and
+    V^T (x - V c1) read the K basis vectors and x and write x once, K + 2 vectors of N
+    values, K the basis size at each call, for every active pair."""
+    return sum(pairs * es * N * (K + 2) for K in nvec_list)
+
+
+# DRAM bytes over algorithmic bytes of one k_sub_dot launch (31 pairs, K = 22) in the
+# committed ncu capture (profiles/k_sub_dot_and_k_of_gram_cols_ellipses256x256x32.md):
+# 391.5 MB of traffic for 390.1 MB of algorithmic bytes
+SUBDOT_TRAFFIC_RATIO = 391.5 / 390.1
 
 
 def run_ours(args):
@@ -277,8 +276,8 @@ def run_ours(args):
     # quality of the result (RRE against the phantom) and the DP residual
     rre = float(np.linalg.norm(u.cpu().numpy() - w.u_true.ravel()) / np.linalg.norm(w.u_true))
 
-    # roofline of the dominant HBM-bound unit: the CGS2 reorthogonalisation of the
-    # Solve-OF residuals (k_mdot + k_combine passes over the per-pair bases)
+    # roofline of the dominant HBM-bound kernel: the fused CGS2 pass over the per-pair
+    # Solve-OF bases (k_sub_dot)
     import json as _json
     peaks = {}
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -291,19 +290,25 @@ def run_ours(args):
     # OF runs on outer iterations 1..29 (u^(0) = 0 gives u_t = 0 and no work at k = 0);
     # GKS iteration it reorthogonalises against of_ell + it vectors (it = 0..18)
     ks = [10 + it for it in range(19)] * (N_OUTER - 1)
-    bytes_total = reorth_bytes(ks, N2, pairs)
-    ro_ms = class_ms.get("of_reorth", [float("nan"), 0])[0]
-    achieved = bytes_total / (ro_ms / 1e3) / 1e9 if ro_ms == ro_ms and ro_ms > 0 else None
+    bytes_total = subdot_bytes(ks, N2, pairs)
+    sd_ms, sd_cnt = class_ms.get("of_subdot", [float("nan"), 0])
+    achieved = bytes_total / (sd_ms / 1e3) / 1e9 if sd_ms == sd_ms and sd_ms > 0 else None
     step1_ms = sum(v[0] for v in class_ms.values())
     dominant = max(class_ms.items(), key=lambda kv: kv[1][0])[0] if class_ms else None
+    n_subdot = len(ks)  # one launch per GKS iteration for all pairs in the single-stream step
     roofline = {
-        "kernel": "of_reorth (CGS2 + append of the Solve-OF residuals: k_of_proj_gram, k_sub_dot, k_combine, k_append)",
+        "kernel": "k_sub_dot (fused CGS2 pass of the Solve-OF residuals, with its chunk reduction)",
         "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-        "frac": (achieved / hbm_peak) if achieved else None, "traffic": None,
+        "frac": (achieved / hbm_peak) if achieved else None,
+        "traffic": SUBDOT_TRAFFIC_RATIO * bytes_total / n_subdot,
+        "traffic_source": "ncu capture of one launch (31 pairs, K = 22): DRAM read + write = 1.004 x algorithmic; "
+                          "scaled to the average launch by the vectors it streams",
+        "algorithmic_bytes_per_launch": bytes_total / n_subdot,
         "peak_source": peak_src,
-        "bytes_model": "2K+6 vectors of 2*n*n FP32 per pair and GKS iteration",
-        "measured": "class time from one instrumented single-stream step after the timed region",
-        "share_of_single_stream_step": ro_ms / step1_ms if step1_ms else None,
+        "bytes_model": "K+2 vectors of 2*n*n FP32 per pair and GKS iteration",
+        "measured": "class time from one instrumented single-stream step after the timed region "
+                    "(the timed steps run every pair on its own stream inside CUDA graphs)",
+        "share_of_single_stream_step": sd_ms / step1_ms if step1_ms else None,
         "largest_class_single_stream": dominant,
     }
     if rank != 0:

@@ -1093,13 +1093,27 @@ static mof_status solve_of_impl(mof_problem *p, const mof_solver_params &prm, WS
                 ::mof::count_launch(), k_of_resid<real><<<gg, blk2, 0, gst>>>(uxg, uyg, AtBg, sg, sa.lam, wvg, p->nx, p->ny, actg);
             }
             {
-                Scope sc(tm, "of_reorth", gst);
                 // CGS2: the first projection's coefficients from the Grams, the second by
-                // dot products (fused with the first update); then the second update
+                // dot products (fused with the first update); then the second update. The
+                // fused pass has a timing class of its own.
                 double *cg = w.coef_of + (long long)b0 * Kof;
-                ::mof::count_launch(), k_of_proj_gram<<<nb, 32, 0, gst>>>(sa.GA, sa.GL, sa.g, sa.z, sa.lam, Kvg, actg, Kof, cg);
+                {
+                    Scope sc(tm, "of_reorth", gst);
+                    ::mof::count_launch(), k_of_proj_gram<<<nb, 32, 0, gst>>>(sa.GA, sa.GL, sa.g, sa.z, sa.lam, Kvg, actg, Kof, cg);
+                }
                 // at GKS iteration it the basis holds at most of_ell + it vectors (one append per iteration)
-                const int np = kg.reorth_second_parts(BAg, wvg, N2, cg, cg, gst, std::min(Kof, prm.of_ell + it));
+                const int kcap = std::min(Kof, prm.of_ell + it);
+                bool fused;
+                {
+                    Scope sc(tm, "of_subdot", gst);
+                    fused = kg.sub_dot(BAg, cg, Kof, wvg, N2, cg, gst, kcap);
+                }
+                Scope sc(tm, "of_reorth", gst);
+                if (!fused) {
+                    kg.subtract(BAg, cg, Kof, wvg, N2, wvg, N2, nullptr, gst);
+                    kg.dots(BAg, wvg, N2, cg, Kof, 1.0, gst);
+                }
+                const int np = kg.subtract_parts(BAg, cg, Kof, wvg, N2, wvg, N2, gst);
                 kg.append_parts(BAg, Kvg, wvg, N2, np, w.nrm_of + b0, w.scale_of + b0, tol, w.grow_of + b0, appg, nullptr, nullptr,
                                 nullptr, gst);
             }
