@@ -231,3 +231,21 @@ def test_mmgks_of_fp64_image_basis_beyond_32_matches_oracle():
     assert max(r["basis"] for r in rep) > 32
     assert rel(u, ores.u) <= 1e-7, rel(u, ores.u)
     assert rel(s, ores.s) <= 1e-6, rel(s, ores.s)
+
+
+def test_solve_of_graph_replay_matches_eager_run():
+    """mof_solve_of captures its Solve-OF into a graph (over workspace copies of u and s)
+    and replays it; with timing on it runs eagerly. Both give the same velocities bit for
+    bit, across calls with different input and output buffers and a parameter change."""
+    w = synth.moving_disks(40, 4, 8, 40, radii=(5.0, 8.0), seed=10)
+    p = problem(w, api.MOF_FP32)
+    outs = []
+    for timing, of_iters in ((0, 5), (0, 5), (1, 5), (0, 6), (1, 6)):
+        api.mof_set_timing(p, timing)
+        u = torch.tensor(w.u_true.astype(np.float32), device="cuda").reshape(-1).clone()
+        s = torch.full((p.nv,), float("nan"), dtype=torch.float32, device="cuda")
+        api.mof_solve_of(p, api.mof_default_params(of_ell=4, of_iters=of_iters), u, s)
+        outs.append(s.cpu())
+    api.mof_set_timing(p, 0)
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+    assert torch.equal(outs[3], outs[4]) and not torch.equal(outs[0], outs[3])
