@@ -226,3 +226,43 @@ def reverse_flow(s):
     sr = np.empty_like(s)
     _load().orc_reverse_flow(nx, ny, npairs + 1, _d(s), _d(sr))
     return sr
+
+
+# ------------------------------------------------------------ rescaling for Solve-OF
+# Sec. 4.1.5 ("Rescaling Large Images for Optical Flow Computation") and Sec. 5 (frames
+# downsampled by a factor of 2 or 4 before Solve-OF, velocities upscaled afterwards). The
+# paper names neither operator; the readings: the frames are averaged over a x a blocks,
+# and the coarse velocity field is interpolated bilinearly at the fine pixel centres
+# (coarse coordinate (x + 1/2)/a - 1/2, clamped to the coarse grid) and multiplied by a,
+# since a coarse pixel is a fine pixels wide.
+
+def downsample(u, a):
+    """Block mean over a x a pixels of every frame: (nt, ny, nx) -> (nt, ny/a, nx/a);
+    ny and nx must be multiples of a."""
+    u = np.asarray(u, dtype=np.float64)
+    nt, ny, nx = u.shape
+    if ny % a or nx % a:
+        raise ValueError("frame size must be a multiple of the factor")
+    return u.reshape(nt, ny // a, a, nx // a, a).mean(axis=(2, 4))
+
+
+def upsample_velocity(sc, a):
+    """Coarse velocities (npairs, 2, nyc, nxc) in coarse pixels -> fine velocities
+    (npairs, 2, a nyc, a nxc) in fine pixels: bilinear interpolation at the fine pixel
+    centres, clamped to the coarse grid, times a."""
+    sc = np.asarray(sc, dtype=np.float64)
+    npairs, two, nyc, nxc = sc.shape
+    ny, nx = a * nyc, a * nxc
+
+    def axis(n_fine, n_coarse):
+        X = np.clip((np.arange(n_fine) + 0.5) / a - 0.5, 0.0, n_coarse - 1.0)
+        i0 = np.floor(X).astype(int)
+        i1 = np.minimum(i0 + 1, n_coarse - 1)
+        return i0, i1, X - i0
+
+    y0, y1, wy = axis(ny, nyc)
+    x0, x1, wx = axis(nx, nxc)
+    wy, wx = wy[:, None], wx[None, :]
+    out = (sc[:, :, y0][:, :, :, x0] * (1 - wy) * (1 - wx) + sc[:, :, y0][:, :, :, x1] * (1 - wy) * wx
+           + sc[:, :, y1][:, :, :, x0] * wy * (1 - wx) + sc[:, :, y1][:, :, :, x1] * wy * wx)
+    return a * out

@@ -52,6 +52,7 @@ class Params:
     """Parameters of Alg. 1 and Alg. 2 (defaults: Sec. 5 where stated)."""
     ell: int = 10            # initial GKB subspace dimension (Sec. 5)
     tau: int = 1             # OF update period (Sec. 4.1.5); 0 = never update s
+    of_scale: int = 1        # Solve-OF on frames downsampled by this factor (Sec. 4.1.5, Sec. 5)
     of_iters: int = 20       # MMGKS iterations per Solve-OF call (Sec. 5)
     of_ell: int = 10         # GKB start of Solve-OF
     of_dr: int = 1           # box half-width of App. C
@@ -386,7 +387,11 @@ def mmgks_of(geom: ops.Geometry, b, prm: Params, n_outer, u0=None, s_init=None, 
     for k in range(n_outer):
         rec = {"k": k}
         if prm.tau > 0 and k % prm.tau == 0:
-            s = solve_of(u.reshape(shape), prm, pool)
+            if prm.of_scale > 1:  # on downsampled frames, velocities upscaled (Sec. 4.1.5)
+                s = ops.upsample_velocity(solve_of(ops.downsample(u.reshape(shape), prm.of_scale), prm, pool),
+                                          prm.of_scale)
+            else:
+                s = solve_of(u.reshape(shape), prm, pool)
             sr = ops.reverse_flow(s)
         th = Theta(shape, s, sr)
         nu = th(u)

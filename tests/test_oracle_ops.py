@@ -379,3 +379,53 @@ def test_flow_velocity_vjp_of_a_linear_image_is_its_slope():
     inside = (xx + 0.37 < nx - 1) & (yy + 0.37 < ny - 1)
     np.testing.assert_allclose(gs[0, 0][inside], -a, atol=1e-12)
     np.testing.assert_allclose(gs[0, 1][inside], -b, atol=1e-12)
+
+
+# ------------------------------------------------------------ rescaling for Solve-OF
+@pytest.mark.parametrize("a", [2, 4])
+def test_downsample_block_means_of_constants_and_ramps(a):
+    """Block means: a constant stays constant; a linear ramp c0 + cx x + cy y goes to the
+    ramp at the block centres, c0 + cx (a X + (a-1)/2) + cy (a Y + (a-1)/2); the total
+    mass is kept (sum of the coarse frame times a^2)."""
+    nt, ny, nx = 2, 4 * a, 3 * a
+    assert np.allclose(ops.downsample(np.full((nt, ny, nx), 3.25), a), 3.25, rtol=0, atol=1e-15)
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    u = np.stack([1.5 + 0.25 * x - 0.75 * y, -2.0 + 1.0 * x + 0.5 * y])
+    Y, X = np.mgrid[0:ny // a, 0:nx // a].astype(float)
+    cx, cy = a * X + (a - 1) / 2, a * Y + (a - 1) / 2
+    want = np.stack([1.5 + 0.25 * cx - 0.75 * cy, -2.0 + 1.0 * cx + 0.5 * cy])
+    assert np.allclose(ops.downsample(u, a), want, rtol=0, atol=1e-13)
+    r = np.random.default_rng(0).standard_normal((nt, ny, nx))
+    assert np.allclose(ops.downsample(r, a).sum(axis=(1, 2)) * a * a, r.sum(axis=(1, 2)), rtol=1e-13, atol=1e-12)
+    with pytest.raises(ValueError):
+        ops.downsample(np.zeros((1, 4 * a + 1, 4 * a)), a)
+
+
+@pytest.mark.parametrize("a", [2, 4])
+def test_upsample_velocity_constants_ramps_and_clamping(a):
+    """Velocities in coarse pixels become fine pixels (times a). A constant field c gives
+    a c everywhere; the coarse ramp s_x = X gives a * clamp((x + 1/2)/a - 1/2, 0, nxc - 1)
+    (bilinear interpolation is exact on linear fields, the clamp holds the border)."""
+    npairs, nyc, nxc = 2, 3, 5
+    c = np.zeros((npairs, 2, nyc, nxc))
+    c[:, 0] = 0.7
+    c[:, 1] = -1.3
+    f = ops.upsample_velocity(c, a)
+    assert f.shape == (npairs, 2, a * nyc, a * nxc)
+    assert np.allclose(f[:, 0], a * 0.7, rtol=0, atol=1e-14) and np.allclose(f[:, 1], -a * 1.3, rtol=0, atol=1e-14)
+    Yc, Xc = np.mgrid[0:nyc, 0:nxc].astype(float)
+    ramp = np.zeros((1, 2, nyc, nxc))
+    ramp[0, 0] = Xc
+    ramp[0, 1] = 2.0 * Yc - Xc
+    f = ops.upsample_velocity(ramp, a)
+    xs = np.clip((np.arange(a * nxc) + 0.5) / a - 0.5, 0, nxc - 1)
+    ys = np.clip((np.arange(a * nyc) + 0.5) / a - 0.5, 0, nyc - 1)
+    assert np.allclose(f[0, 0], a * np.broadcast_to(xs[None, :], (a * nyc, a * nxc)), rtol=0, atol=1e-13)
+    assert np.allclose(f[0, 1], a * (2.0 * ys[:, None] - xs[None, :]), rtol=0, atol=1e-13)
+
+
+def test_rescaling_by_one_is_the_identity():
+    r = np.random.default_rng(1).standard_normal((3, 6, 8))
+    s = np.random.default_rng(2).standard_normal((2, 2, 6, 8))
+    assert np.array_equal(ops.downsample(r, 1), r)
+    assert np.allclose(ops.upsample_velocity(s, 1), s, rtol=0, atol=0)
