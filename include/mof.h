@@ -88,6 +88,10 @@ typedef struct {
                               FP64 solves overlap another group's bandwidth-bound kernels; the
                               result does not depend on it. 0 = automatic: one group per pair,
                               up to 64 groups; at most 64 */
+    int of_scale;          /* Solve-OF on frames downsampled by this factor a (Sec. 4.1.5, Sec. 5:
+                              a = 2 or 4 to reach frames under 50x50): a x a block means, the
+                              velocities interpolated bilinearly back to the full grid and
+                              multiplied by a. 1 = full resolution; a must divide nx and ny */
 } mof_solver_params;
 
 /* One record per outer iteration k of mof_solve (host struct). */
@@ -160,6 +164,18 @@ mof_status mof_apply_flow_ds(mof_problem *p, const void *u, const void *s, const
  * u_p, uy likewise in y, ut = box average of u_{p+1} - u_p. u: n; outputs (nt-1)*nx*ny. */
 mof_status mof_of_fields(mof_problem *p, const void *u, int dr, void *ux, void *uy, void *ut,
                          void *stream);
+
+/* Rescaling for Solve-OF (Sec. 4.1.5: Solve-OF on smaller frames, velocities upscaled; the
+ * paper does not name the operators):
+ * uc = the a x a block means of every frame of u. a >= 1 must divide nx and ny.
+ * u: n values, uc: nt * (ny/a) * (nx/a) values (the same layout at the coarse size). */
+mof_status mof_downsample(mof_problem *p, int a, const void *u, void *uc, void *stream);
+
+/* s = a * (bilinear interpolation of the coarse velocities sc at the fine pixel centres),
+ * the coarse coordinate of fine pixel x being (x + 1/2)/a - 1/2 clamped to the coarse grid
+ * (so that velocities in coarse pixels become fine pixels). a as for mof_downsample.
+ * sc: (nt-1) * 2 * (ny/a) * (nx/a) values, s: nv values. */
+mof_status mof_upsample_velocity(mof_problem *p, int a, const void *sc, void *s, void *stream);
 
 /* r = Upsilon s + u_t per pair (Sec. 2.2: the pointwise row [u_x u_y]).
  * s: nv, r: (nt-1)*nx*ny. */

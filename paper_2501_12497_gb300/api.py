@@ -36,7 +36,8 @@ class mof_solver_params(ctypes.Structure):
     _fields_ = [("ell", ctypes.c_int), ("tau", ctypes.c_int), ("of_iters", ctypes.c_int),
                 ("of_ell", ctypes.c_int), ("of_dr", ctypes.c_int), ("image_rule", ctypes.c_int),
                 ("eps", ctypes.c_double), ("eta", ctypes.c_double), ("noise_norm", ctypes.c_double),
-                ("lam_fixed", ctypes.c_double), ("breakdown_tol", ctypes.c_double), ("of_streams", ctypes.c_int)]
+                ("lam_fixed", ctypes.c_double), ("breakdown_tol", ctypes.c_double), ("of_streams", ctypes.c_int),
+                ("of_scale", ctypes.c_int)]
 
 
 class mof_report(ctypes.Structure):
@@ -62,6 +63,8 @@ _SIGS = {
     "mof_apply_flowT_noalloc": (ctypes.c_int, [ctypes.c_void_p] * 6),
     "mof_apply_flow_ds": (ctypes.c_int, [ctypes.c_void_p] * 8),
     "mof_of_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 4),
+    "mof_downsample": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 3),
+    "mof_upsample_velocity": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 3),
     "mof_apply_flow_lin": (ctypes.c_int, [ctypes.c_void_p] * 7),
     "mof_apply_flow_linT": (ctypes.c_int, [ctypes.c_void_p] * 6),
     "mof_apply_vgrad": (ctypes.c_int, [ctypes.c_void_p] * 4),
@@ -234,6 +237,22 @@ def mof_of_fields(p, u, dr, ux, uy, ut, stream=None):
     s = _sizes(p)
     _check(_lib.mof_of_fields(p.handle, _ptr(p, u, s["n"], "u"), int(dr), _ptr(p, ux, s["pairs"], "ux"),
                               _ptr(p, uy, s["pairs"], "uy"), _ptr(p, ut, s["pairs"], "ut"), _stream(stream)))
+
+
+def mof_downsample(p, a, u, uc, stream=None):
+    """uc = a x a block means of the frames of u (uc has nt * (ny/a) * (nx/a) values)."""
+    s = _sizes(p)
+    a = int(a)
+    nc = p.nt * (p.ny // a) * (p.nx // a) if a >= 1 else 0
+    _check(_lib.mof_downsample(p.handle, a, _ptr(p, u, s["n"], "u"), _ptr(p, uc, nc, "uc"), _stream(stream)))
+
+
+def mof_upsample_velocity(p, a, sc, sv, stream=None):
+    """sv = a * bilinear interpolation of the coarse velocities sc at the fine pixel centres."""
+    s = _sizes(p)
+    a = int(a)
+    nc = (p.nt - 1) * 2 * (p.ny // a) * (p.nx // a) if a >= 1 else 0
+    _check(_lib.mof_upsample_velocity(p.handle, a, _ptr(p, sc, nc, "sc"), _ptr(p, sv, s["nv"], "s"), _stream(stream)))
 
 
 def mof_apply_flow_lin(p, ux, uy, ut, sv, r, stream=None):

@@ -123,6 +123,7 @@ void mof_default_params(mof_solver_params *p) {
     p->lam_fixed = 0.0;
     p->breakdown_tol = 0.0;
     p->of_streams = 0;
+    p->of_scale = 1;
 }
 
 mof_status mof_problem_create(const mof_geometry *g, int precision, mof_problem **out) {
@@ -318,6 +319,26 @@ mof_status mof_of_fields(mof_problem *p, const void *u, int dr, void *ux, void *
     if (dr < 1 || dr > 64) return fail(MOF_EINVAL, "dr must be in [1, 64] (got %d)", dr);
     return DISPATCH(p, launch_of_fields<float>(p, CF(u), dr, F(ux), F(uy), F(ut), S(stream)),
                     launch_of_fields<double>(p, CD(u), dr, D(ux), D(uy), D(ut), S(stream)));
+}
+
+mof_status mof_downsample(mof_problem *p, int a, const void *u, void *uc, void *stream) {
+    g_err[0] = 0;
+    MOF_TRY(check_problem(p));
+    if (!u || !uc) return fail(MOF_EINVAL, "null array");
+    if (a < 1 || p->nx % a || p->ny % a)
+        return fail(MOF_EINVAL, "the factor must be >= 1 and divide nx and ny (got %d for %d x %d)", a, p->nx, p->ny);
+    return DISPATCH(p, launch_downsample<float>(p, a, CF(u), F(uc), S(stream)),
+                    launch_downsample<double>(p, a, CD(u), D(uc), S(stream)));
+}
+
+mof_status mof_upsample_velocity(mof_problem *p, int a, const void *sc, void *s, void *stream) {
+    g_err[0] = 0;
+    MOF_TRY(check_problem(p));
+    if (!sc || !s) return fail(MOF_EINVAL, "null array");
+    if (a < 1 || p->nx % a || p->ny % a)
+        return fail(MOF_EINVAL, "the factor must be >= 1 and divide nx and ny (got %d for %d x %d)", a, p->nx, p->ny);
+    return DISPATCH(p, launch_upsample_velocity<float>(p, a, CF(sc), F(s), S(stream)),
+                    launch_upsample_velocity<double>(p, a, CD(sc), D(s), S(stream)));
 }
 
 mof_status mof_apply_flow_lin(mof_problem *p, const void *ux, const void *uy, const void *ut, const void *s, void *r,

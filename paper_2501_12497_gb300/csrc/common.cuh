@@ -103,6 +103,10 @@ int tiles_count(const mof_problem *p);
 template <typename real> mof_status launch_tile_radii(const mof_problem *p, const real *s, const real *sr, int *rad_s, int *rad_sr, cudaStream_t st);
 template <typename real> mof_status launch_flowT(const mof_problem *p, const real *r, const real *s, const real *sr, const int *rad_s, const int *rad_sr, real *u, cudaStream_t st);
 template <typename real> mof_status launch_of_fields(const mof_problem *p, const real *u, int dr, real *ux, real *uy, real *ut, cudaStream_t st);
+// Rescaling for Solve-OF (Sec. 4.1.5): uc = a x a block means of every frame of u;
+// s = a * bilinear interpolation of the coarse velocities sc at the fine pixel centres.
+template <typename real> mof_status launch_downsample(const mof_problem *p, int a, const real *u, real *uc, cudaStream_t st);
+template <typename real> mof_status launch_upsample_velocity(const mof_problem *p, int a, const real *sc, real *s, cudaStream_t st);
 template <typename real> mof_status launch_flow_lin(const mof_problem *p, const real *ux, const real *uy, const real *ut, const real *s, real *r, cudaStream_t st);
 template <typename real> mof_status launch_flow_linT(const mof_problem *p, const real *ux, const real *uy, const real *r, real *gs, cudaStream_t st);
 template <typename real> mof_status launch_reverse_flow(const mof_problem *p, const real *s, int *rad_scratch, int *dest_scratch, real *sr, cudaStream_t st);

@@ -15,6 +15,8 @@
 // farthest actual arrival.
 #include "common.cuh"
 
+#include <algorithm>
+
 #include <cfloat>
 
 namespace mof {
@@ -549,5 +551,81 @@ mof_status launch_reg_normal(const mof_problem *p, const real *x, const real *uk
 
 MOF_INST(float)
 MOF_INST(double)
+
+
+// ------------------------------------------------------------ rescaling for Solve-OF
+// Sec. 4.1.5 / Sec. 5: Solve-OF on frames downsampled by a factor a, the velocities
+// upscaled to the full grid. Block means of a x a pixels (one thread per coarse pixel,
+// summed row by row, scaled by 1/a^2); the velocity field interpolated bilinearly at
+// the fine pixel centres, coarse coordinate (x + 1/2)/a - 1/2 clamped to the coarse
+// grid, times a (one thread per fine value).
+template <typename real>
+__global__ void k_downsample(const real *__restrict__ u, real *__restrict__ uc, int nx, int ny, int nt, int a) {
+    const int nxc = nx / a, nyc = ny / a;
+    const long long nc = (long long)nt * nxc * nyc;
+    const real inv = (real)1 / (real)(a * a);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nc; i += (long long)gridDim.x * blockDim.x) {
+        const int X = (int)(i % nxc);
+        const long long r = i / nxc;
+        const int Y = (int)(r % nyc), t = (int)(r / nyc);
+        const real *src = u + ((long long)t * ny + (long long)Y * a) * nx + (long long)X * a;
+        real sum = 0;
+        for (int dy = 0; dy < a; ++dy)
+            for (int dx = 0; dx < a; ++dx) sum += src[(long long)dy * nx + dx];
+        uc[i] = sum * inv;
+    }
+}
+
+template <typename real>
+__device__ __forceinline__ void up_axis(int x, int a, int nc, int &i0, int &i1, real &w) {
+    real X = ((real)x + (real)0.5) / (real)a - (real)0.5;
+    X = X < (real)0 ? (real)0 : (X > (real)(nc - 1) ? (real)(nc - 1) : X);
+    i0 = (int)floor(X);
+    i1 = min(i0 + 1, nc - 1);
+    w = X - (real)i0;
+}
+
+template <typename real>
+__global__ void k_upsample_vel(const real *__restrict__ sc, real *__restrict__ s, int nx, int ny, int nplanes, int a) {
+    const int nxc = nx / a, nyc = ny / a;
+    const long long nf = (long long)nplanes * nx * ny;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nf; i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx);
+        const long long r = i / nx;
+        const int y = (int)(r % ny), pl = (int)(r / ny);
+        int x0, x1, y0, y1;
+        real wx, wy;
+        up_axis<real>(x, a, nxc, x0, x1, wx);
+        up_axis<real>(y, a, nyc, y0, y1, wy);
+        const real *c = sc + (long long)pl * nxc * nyc;
+        const real v = c[y0 * nxc + x0] * ((real)1 - wx) * ((real)1 - wy) + c[y0 * nxc + x1] * wx * ((real)1 - wy) +
+                       c[y1 * nxc + x0] * ((real)1 - wx) * wy + c[y1 * nxc + x1] * wx * wy;
+        s[i] = (real)a * v;
+    }
+}
+
+template <typename real>
+mof_status launch_downsample(const mof_problem *p, int a, const real *u, real *uc, cudaStream_t st) {
+    const long long nc = (long long)p->nt * (p->nx / a) * (p->ny / a);
+    const int blocks = (int)std::min<long long>(152 * 16, (nc + 255) / 256);
+    if (nc > 0) ::mof::count_launch(), k_downsample<real><<<blocks, 256, 0, st>>>(u, uc, p->nx, p->ny, p->nt, a);
+    MOF_LAUNCH_CHECK();
+    return MOF_OK;
+}
+
+template <typename real>
+mof_status launch_upsample_velocity(const mof_problem *p, int a, const real *sc, real *s, cudaStream_t st) {
+    const int nplanes = 2 * (p->nt - 1);
+    const long long nf = (long long)nplanes * p->nx * p->ny;
+    const int blocks = (int)std::min<long long>(152 * 16, (nf + 255) / 256);
+    if (nf > 0) ::mof::count_launch(), k_upsample_vel<real><<<blocks, 256, 0, st>>>(sc, s, p->nx, p->ny, nplanes, a);
+    MOF_LAUNCH_CHECK();
+    return MOF_OK;
+}
+
+template mof_status launch_downsample<float>(const mof_problem *, int, const float *, float *, cudaStream_t);
+template mof_status launch_downsample<double>(const mof_problem *, int, const double *, double *, cudaStream_t);
+template mof_status launch_upsample_velocity<float>(const mof_problem *, int, const float *, float *, cudaStream_t);
+template mof_status launch_upsample_velocity<double>(const mof_problem *, int, const double *, double *, cudaStream_t);
 
 }  // namespace mof

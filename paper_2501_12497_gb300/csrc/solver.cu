@@ -184,6 +184,10 @@ struct Holder {
     WS<double> *w64 = nullptr;
     void *host_stage = nullptr;  // device staging of mof_solve_host: b | u | s | sr
     Timer timer;
+    // Solve-OF on downsampled frames (of_scale > 1): an internal problem of the coarse size,
+    // with its own workspace
+    mof_problem *coarse = nullptr;
+    int coarse_scale = 0;
 };
 
 template <typename real>
@@ -223,6 +227,7 @@ void free_workspace(mof_problem *p) {
     if (h->host_stage) cudaFree(h->host_stage);
     free_ws(h->w32);
     free_ws(h->w64);
+    if (h->coarse) mof_problem_destroy(h->coarse);
     delete h;
     p->ws = nullptr;
 }
@@ -1133,6 +1138,60 @@ static mof_status solve_of_impl(mof_problem *p, const mof_solver_params &prm, WS
     return MOF_OK;
 }
 
+// ------------------------------------------------------------ Solve-OF on rescaled frames
+// Sec. 4.1.5 / Sec. 5: with of_scale = a > 1 Solve-OF runs on the frames' a x a block means
+// and the velocities are interpolated back to the full grid (times a). The coarse problem
+// (geometry of the coarse frames; its projector is never used) and its workspace are
+// created on first use, which callers make before any graph capture.
+template <typename real>
+static mof_status ensure_coarse(mof_problem *p, const mof_solver_params &prm, mof_problem **pc_out, WS<real> **wc_out) {
+    const int a = prm.of_scale;
+    Holder *h = holder(p);
+    if (!h->coarse || h->coarse_scale != a) {
+        if (h->coarse) {
+            mof_problem_destroy(h->coarse);
+            h->coarse = nullptr;
+        }
+        std::vector<int> na(p->nt, 1);
+        std::vector<double> ang(p->nt, 0.0);
+        mof_geometry g{p->nx / a, p->ny / a, p->nt, 1, na.data(), ang.data(), 1.0, 1.0};
+        MOF_TRY(mof_problem_create(&g, p->precision, &h->coarse));
+        h->coarse_scale = a;
+    }
+    WS<real> *&wc = ws_slot<real>(holder(h->coarse));
+    MOF_TRY(ensure_ws<real>(h->coarse, prm, 1, wc));
+    *pc_out = h->coarse;
+    *wc_out = wc;
+    return MOF_OK;
+}
+
+// err |= the coarse solve's error word, which is then cleared
+__global__ void k_merge_err(int *__restrict__ err, int *__restrict__ cerr) {
+    if (threadIdx.x == 0) {
+        err[0] |= cerr[0];
+        cerr[0] = 0;
+    }
+}
+
+template <typename real>
+static mof_status of_step(mof_problem *p, const mof_solver_params &prm, WS<real> &w, const real *u, real *s_out, Timer *tm,
+                          cudaStream_t st) {
+    if (prm.of_scale <= 1) return solve_of_impl<real>(p, prm, w, u, s_out, tm, st);
+    mof_problem *pc = nullptr;
+    WS<real> *wc = nullptr;
+    MOF_TRY(ensure_coarse<real>(p, prm, &pc, &wc));  // already in place: nothing is allocated here
+    {
+        Scope sc(tm, "of_fields", st);
+        MOF_TRY(launch_downsample<real>(p, prm.of_scale, u, wc->u, st));
+    }
+    MOF_TRY(solve_of_impl<real>(pc, prm, *wc, wc->u, wc->s, tm, st));
+    Scope sc(tm, "of_fields", st);
+    MOF_TRY(launch_upsample_velocity<real>(p, prm.of_scale, wc->s, s_out, st));
+    ::mof::count_launch(), k_merge_err<<<1, 32, 0, st>>>(w.err, wc->err);
+    MOF_LAUNCH_CHECK();
+    return MOF_OK;
+}
+
 // ============================================================ MMGKS-OF
 // One MMGKS-OF solve (Alg. 1) as phases, so that several problems can be
 // interleaved on their own streams (mof_solve_batch): begin() enqueues the set-up
@@ -1266,6 +1325,11 @@ mof_status SolveRun<real>::begin(cudaStream_t ust) {
     }
     MOF_TRY(prepare_small_solve(Kmax));
     MOF_TRY(prepare_small_solve(w.Kof));
+    if (prm.of_scale > 1) {
+        mof_problem *pc;
+        WS<real> *wc;
+        MOF_TRY(ensure_coarse<real>(p, prm, &pc, &wc));
+    }
     return MOF_OK;
 }
 
@@ -1291,7 +1355,7 @@ mof_status SolveRun<real>::iteration(bool of_now, bool expand) {
         }
         if (of_now) {
             MOF_CUDA(cudaEventRecord(w.side_done, w.side));
-            MOF_TRY(solve_of_impl<real>(p, prm, w, w.u, w.s, tm, st));
+            MOF_TRY(of_step<real>(p, prm, w, w.u, w.s, tm, st));
             Scope sc(tm, "reverse_flow", st);
             MOF_TRY(launch_reverse_flow<real>(p, w.s, w.rad_rev, w.dest, w.sr, st));
             MOF_TRY(launch_tile_radii<real>(p, w.s, w.sr, w.rad_s, w.rad_sr, st));
@@ -1348,7 +1412,10 @@ mof_status SolveRun<real>::iteration(bool of_now, bool expand) {
         {
             Scope sc(tm, "misc", st);
             ::mof::count_launch(), k_copy<real><<<fb(n), 256, 0, st>>>(w.un, w.u, n);
-            ::mof::count_launch(), k_report<<<1, 1, 0, st>>>(w.report, w.iter, w.lam, w.nrm2b, w.nrm2, w.K, w.flag, w.Kv_of, P,
+            // the Solve-OF basis sizes live in the coarse workspace when Solve-OF runs downsampled
+            const int *kof = w.Kv_of;
+            if (prm.of_scale > 1 && holder(p)->coarse) kof = ws_slot<real>(holder(holder(p)->coarse))->Kv_of;
+            ::mof::count_launch(), k_report<<<1, 1, 0, st>>>(w.report, w.iter, w.lam, w.nrm2b, w.nrm2, w.K, w.flag, kof, P,
                                                              of_now ? 1 : 0, expand ? 1 : 0, w.appended);
         }
         MOF_LAUNCH_CHECK();
@@ -1461,6 +1528,11 @@ static mof_status solve_of_entry(mof_problem *p, const mof_solver_params &prm, c
     Timer *tm = p->timing ? &h->timer : nullptr;
     if (tm) tm->reset();
     MOF_TRY(prepare_small_solve(w.Kof));
+    if (prm.of_scale > 1) {
+        mof_problem *pc;
+        WS<real> *wc;
+        MOF_TRY(ensure_coarse<real>(p, prm, &pc, &wc));
+    }
     // all work on the problem's own stream, ordered after the caller's stream
     const cudaStream_t st = w.ss;
     MOF_CUDA(cudaEventRecord(w.join, ust));
@@ -1468,7 +1540,7 @@ static mof_status solve_of_entry(mof_problem *p, const mof_solver_params &prm, c
     const long long nimg = p->n, nvel = (long long)(p->nt - 1) * 2 * p->ns;
     if (tm) {  // timed calls run eagerly (the scopes record events around each class)
         ::mof::count_launch(), k_fill_int<<<1, 32, 0, st>>>(w.err, 1, 0);
-        MOF_TRY(solve_of_impl<real>(p, prm, w, u, s, tm, st));
+        MOF_TRY(of_step<real>(p, prm, w, u, s, tm, st));
     } else {
         // one captured graph per parameter set, over workspace copies of u and s (fixed
         // addresses), replayed: the Solve-OF launches thousands of short kernels
@@ -1477,7 +1549,7 @@ static mof_status solve_of_entry(mof_problem *p, const mof_solver_params &prm, c
             const long long before = launches_so_far();
             MOF_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
             ::mof::count_launch(), k_fill_int<<<1, 32, 0, st>>>(w.err, 1, 0);
-            const mof_status cs = solve_of_impl<real>(p, prm, w, w.u, w.s, nullptr, st);
+            const mof_status cs = of_step<real>(p, prm, w, w.u, w.s, nullptr, st);
             cudaGraph_t graph = nullptr;
             const cudaError_t ce = cudaStreamEndCapture(st, &graph);
             w.ofgraph.kernels = launches_so_far() - before;
@@ -1522,6 +1594,10 @@ static mof_status check_params(const mof_problem *p, const mof_solver_params *pr
                     "(ell + n_outer = %d, of_ell + of_iters = %d)",
                     prm->ell + n_outer, prm->of_ell + prm->of_iters);
     if (!(prm->eps > 0) || !std::isfinite(prm->eps)) return fail(MOF_EINVAL, "eps must be finite and > 0");
+    if (prm->of_scale < 1 || p->nx % prm->of_scale || p->ny % prm->of_scale || p->nx / prm->of_scale < 2 ||
+        p->ny / prm->of_scale < 2)
+        return fail(MOF_EINVAL, "of_scale must be >= 1, divide nx and ny and leave frames of at least 2x2 (got %d for %d x %d)",
+                    prm->of_scale, p->nx, p->ny);
     if (!image_step) return MOF_OK;
     if (prm->image_rule == MOF_RULE_DP && !(prm->noise_norm >= 0))
         return fail(MOF_EINVAL, "the discrepancy principle needs noise_norm >= 0");

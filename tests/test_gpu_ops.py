@@ -221,3 +221,29 @@ def test_reg_normal(shape, prec):
     w = 1.0 / np.sqrt(nu * nu + eps * eps)
     want = th.T(w * th(host(x)))
     assert rel(host(y), want) <= 3 * TOL[prec]
+
+
+# ------------------------------------------------------------ rescaling for Solve-OF
+@pytest.mark.parametrize("prec,tol", [(api.MOF_FP32, 1e-6), (api.MOF_FP64, 1e-14)])
+@pytest.mark.parametrize("a", [2, 4, 8])
+def test_downsample_and_upsample_velocity_match_oracle(prec, tol, a):
+    """Block means of the frames and the bilinear velocity upscaling (Sec. 4.1.5) against
+    the oracle, on 96x56 frames (several thread blocks, a ragged last block)."""
+    nx, ny, nt = 96, 56, 5
+    p, g = make((nx, ny, nt, 3, 20), prec)
+    u = synth.random_images(nt, ny, nx, seed=3)
+    uc = empty(nt * (ny // a) * (nx // a), prec)
+    api.mof_downsample(p, a, dev(u, prec), uc)
+    assert rel(host(uc), O.downsample(u.astype(DT[prec][0]), a)) <= tol
+    sc = synth.random_velocities(nt - 1, ny // a, nx // a, vmax=2.0, seed=4)
+    s = empty(p.nv, prec)
+    api.mof_upsample_velocity(p, a, dev(sc, prec), s)
+    assert rel(host(s), O.upsample_velocity(sc.astype(DT[prec][0]), a)) <= tol
+
+
+def test_rescaling_rejects_factors_that_do_not_divide_the_frame():
+    p, _ = make((48, 40, 3, 3, 20), api.MOF_FP32)
+    u = torch.zeros(p.n, device="cuda")
+    with pytest.raises(api.MofError) as e:
+        api.mof_downsample(p, 3, u, torch.zeros(p.nt * 13 * 16, device="cuda"))
+    assert e.value.status == api.MOF_EINVAL

@@ -249,3 +249,41 @@ def test_solve_of_graph_replay_matches_eager_run():
     api.mof_set_timing(p, 0)
     assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
     assert torch.equal(outs[3], outs[4]) and not torch.equal(outs[0], outs[3])
+
+
+@pytest.mark.parametrize("prec,tol", [(api.MOF_FP64, 1e-7), (api.MOF_FP32, 1e-3)])
+def test_solve_of_on_downsampled_frames_matches_oracle(prec, tol):
+    """Solve-OF with of_scale = 2 (Sec. 4.1.5): on the 2x2 block means of the frames, the
+    velocities upscaled bilinearly and doubled, against the oracle's composition."""
+    w = synth.moving_disks(48, 4, 8, 48, radii=(6.0, 9.0), seed=11)
+    p = problem(w, prec)
+    u = w.u_true.astype(npdt(prec))
+    s = torch.empty(p.nv, dtype=tdt(prec), device="cuda")
+    api.mof_solve_of(p, api.mof_default_params(of_ell=6, of_iters=8, of_scale=2), torch.tensor(u, device="cuda").reshape(-1), s)
+    oprm = OS.Params(of_ell=6, of_iters=8)
+    want = O.upsample_velocity(OS.solve_of(O.downsample(u.astype(np.float64), 2), oprm), 2)
+    got = s.cpu().double().numpy().reshape(want.shape)
+    assert rel(got, want) <= tol, rel(got, want)
+
+
+def test_mmgks_of_fp64_with_downsampled_solve_of_and_tau_matches_oracle():
+    """MMGKS-OF with Solve-OF on frames downsampled by 2, every second outer iteration
+    (tau = 2), on the 64x64x8 two-disk workload."""
+    w = synth.plain_fp64(0)
+    kw = dict(of_scale=2, tau=2)
+    ores = _oracle_solve(w, 6, **kw)
+    u, s, rep = _gpu_solve(w, api.MOF_FP64, 6, **kw)
+    assert rel(u, ores.u) <= 1e-6, rel(u, ores.u)
+    assert rel(s, ores.s) <= 1e-5, rel(s, ores.s)
+    # Solve-OF ran on the even outer iterations from k = 2 on (at k = 0 the image is zero)
+    assert [r["of_basis_max"] > 0 for r in rep] == [k > 0 and k % 2 == 0 for k in range(6)]
+
+
+def test_of_scale_must_divide_the_frames():
+    w = synth.moving_disks(40, 3, 8, 40, radii=(5.0, 8.0), seed=12)
+    p = problem(w, api.MOF_FP32)
+    u = torch.zeros(p.n, device="cuda")
+    s = torch.empty(p.nv, device="cuda")
+    with pytest.raises(api.MofError) as e:
+        api.mof_solve_of(p, api.mof_default_params(of_scale=3), u, s)
+    assert e.value.status == api.MOF_EINVAL
