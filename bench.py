@@ -51,6 +51,10 @@ def parse():
                          "(one call per step on the 256x256x32 frames)")
     ap.add_argument("--of-streams", type=int, default=0,
                     help="frame-pair groups of Solve-OF on separate streams (0 = library default)")
+    ap.add_argument("--of-scale", type=int, default=1,
+                    help="Solve-OF on frames downsampled by this factor (the paper's experiments: 2 or 4)")
+    ap.add_argument("--tau", type=int, default=1,
+                    help="Solve-OF every tau outer iterations (the paper's experiments: 20)")
     return ap.parse_args()
 
 
@@ -210,7 +214,8 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     w = synth.precision_form(seed=rank)
     p = api.mof_problem_create(w.nx, w.ny, w.nt, w.nb, w.na, w.angles, precision=api.MOF_FP32)
-    prm = api.mof_default_params(noise_norm=w.noise_norm, of_streams=args.of_streams)
+    prm = api.mof_default_params(noise_norm=w.noise_norm, of_streams=args.of_streams, of_scale=args.of_scale,
+                                 tau=args.tau)
     stream = torch.cuda.current_stream(dev)
     b = torch.tensor(w.b.astype(np.float32), device=dev)
     u = torch.empty(p.n, dtype=torch.float32, device=dev)
@@ -246,7 +251,7 @@ def run_ours(args):
     # (the timed steps above run them on several streams, uninstrumented)
     class_ms = {}
     if not args.no_class_step:
-        prm1 = api.mof_default_params(noise_norm=w.noise_norm, of_streams=1)
+        prm1 = api.mof_default_params(noise_norm=w.noise_norm, of_streams=1, of_scale=args.of_scale, tau=args.tau)
         api.mof_solve(p, prm1, N_OUTER, b, u, s)
         flush.fill_(1.0)
         torch.cuda.synchronize()
@@ -285,11 +290,11 @@ def run_ours(args):
         peaks = _json.load(open(pk))
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    N2 = 2 * CFG["n"] * CFG["n"]
+    N2 = 2 * (CFG["n"] // args.of_scale) ** 2
     pairs = CFG["nt"] - 1
-    # OF runs on outer iterations 1..29 (u^(0) = 0 gives u_t = 0 and no work at k = 0);
-    # GKS iteration it reorthogonalises against of_ell + it vectors (it = 0..18)
-    ks = [10 + it for it in range(19)] * (N_OUTER - 1)
+    # OF runs on outer iterations k = 1..29 with k % tau == 0 (u^(0) = 0 gives u_t = 0 and no
+    # work at k = 0); GKS iteration it reorthogonalises against of_ell + it vectors (it = 0..18)
+    ks = [10 + it for it in range(19)] * sum(1 for k in range(1, N_OUTER) if k % args.tau == 0)
     bytes_total = subdot_bytes(ks, N2, pairs)
     sd_ms, sd_cnt = class_ms.get("of_subdot", [float("nan"), 0])
     achieved = bytes_total / (sd_ms / 1e3) / 1e9 if sd_ms == sd_ms and sd_ms > 0 else None
@@ -329,7 +334,7 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, **CFG, "n_outer": N_OUTER, "of_iters": 20, "of_ell": 10, "ell": 10,
                    "precision": "FP32 operators, FP64 Krylov/projected solves", "parallelism": "replicas",
                    "l2": "flushed between steps (512 MB write)", "rre": rre,
-                   "of_streams": args.of_streams or "auto",
+                   "of_streams": args.of_streams or "auto", "of_scale": args.of_scale, "tau": args.tau,
                    "time_to_tolerance_s": total_ms / args.steps / 1e3},
         "e2e": {"value": e2e_value, "unit": "outer_iters/s", "h2d_bytes_per_step": 4 * p.m,
                 "d2h_bytes_per_step": 4 * p.n + 64 * N_OUTER},
@@ -410,7 +415,8 @@ def run_large(args):
     api.load()
     w = synth.large_form(0)
     p = api.mof_problem_create(w.nx, w.ny, w.nt, w.nb, w.na, w.angles, precision=api.MOF_FP32)
-    prm = api.mof_default_params(noise_norm=w.noise_norm, of_streams=args.of_streams)
+    prm = api.mof_default_params(noise_norm=w.noise_norm, of_streams=args.of_streams, of_scale=args.of_scale,
+                                 tau=args.tau)
     b = torch.tensor(w.b.astype(np.float32), device="cuda")
     u = torch.empty(p.n, dtype=torch.float32, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -534,7 +540,7 @@ def run_solve_of(args):
     api.load()
     w = synth.precision_form(0)
     p = api.mof_problem_create(w.nx, w.ny, w.nt, w.nb, w.na, w.angles, precision=api.MOF_FP32)
-    prm = api.mof_default_params(of_streams=args.of_streams)
+    prm = api.mof_default_params(of_streams=args.of_streams, of_scale=args.of_scale)
     u = torch.tensor(w.u_true.astype(np.float32), device="cuda").reshape(-1)
     s = torch.empty(p.nv, dtype=torch.float32, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -556,7 +562,7 @@ def run_solve_of(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps, "higher_is_better": True,
             "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": "solve_of ellipses256x256x32", "pairs": p.nt - 1, "of_ell": 10, "of_iters": 20,
-                       "of_streams": args.of_streams or "auto", "l2": "flushed before each call"},
+                       "of_streams": args.of_streams or "auto", "of_scale": args.of_scale, "l2": "flushed before each call"},
             "gpu_launches": api.mof_kernel_launches() - l0}
     print(json.dumps(line), flush=True)
 
