@@ -53,6 +53,7 @@ class Params:
     ell: int = 10            # initial GKB subspace dimension (Sec. 5)
     tau: int = 1             # OF update period (Sec. 4.1.5); 0 = never update s
     of_scale: int = 1        # Solve-OF on frames downsampled by this factor (Sec. 4.1.5, Sec. 5)
+    temporal_tv: int = 0     # 1: Theta also holds the temporal differences L_t (D1-OF, Table 2)
     of_iters: int = 20       # MMGKS iterations per Solve-OF call (Sec. 5)
     of_ell: int = 10         # GKB start of Solve-OF
     of_dr: int = 1           # box half-width of App. C
@@ -326,23 +327,47 @@ def solve_of(u, prm: Params, pool=None):
 
 # ---------------------------------------------------------------- MMGKS-OF
 
-class Theta:
-    """Theta = [Psi; Mhat(s, s')] (Sec. 4.1.1) for fixed velocities."""
+def time_diff(x):
+    """L_t of Table 2 (AnisoTV, eq. (L) along time): forward differences between
+    consecutive frames, (nt, ny, nx) -> (nt-1, ny, nx), no boundary row."""
+    return x[1:] - x[:-1]
 
-    def __init__(self, shape, s, sr):
+
+def time_diffT(r):
+    """The transpose of time_diff: (nt-1, ny, nx) -> (nt, ny, nx)."""
+    out = np.zeros((r.shape[0] + 1,) + r.shape[1:])
+    out[1:] += r
+    out[:-1] -= r
+    return out
+
+
+class Theta:
+    """Theta = [Psi; Mhat(s, s')] (Sec. 4.1.1) for fixed velocities; with temporal,
+    Theta = [Psi; L_t; Mhat(s, s')], the AnisoTV-OF regulariser (D1-OF of Table 2:
+    spatial and temporal first differences plus the motion term, all in the l1 norm)."""
+
+    def __init__(self, shape, s, sr, temporal=False):
         self.shape = shape  # (nt, ny, nx)
         self.s, self.sr = s, sr
+        self.temporal = bool(temporal)
 
     def __call__(self, x):
         x = x.reshape(self.shape)
-        return np.concatenate([ops.grad(x).ravel(), ops.flow(x, self.s, self.sr).ravel()])
+        parts = [ops.grad(x).ravel()]
+        if self.temporal:
+            parts.append(time_diff(x).ravel())
+        parts.append(ops.flow(x, self.s, self.sr).ravel())
+        return np.concatenate(parts)
 
     def T(self, y):
         nt, ny, nx = self.shape
-        npsi = 2 * nt * ny * nx
+        npsi, nlt = 2 * nt * ny * nx, ((nt - 1) * ny * nx if self.temporal else 0)
         g = y[:npsi].reshape(nt, 2, ny, nx)
-        r = y[npsi:].reshape(2, nt - 1, ny, nx)
-        return (ops.gradT(g) + ops.flowT(r, self.s, self.sr)).ravel()
+        out = ops.gradT(g)
+        if self.temporal:
+            out = out + time_diffT(y[npsi:npsi + nlt].reshape(nt - 1, ny, nx))
+        r = y[npsi + nlt:].reshape(2, nt - 1, ny, nx)
+        return (out + ops.flowT(r, self.s, self.sr)).ravel()
 
 
 @dataclass
@@ -393,7 +418,7 @@ def mmgks_of(geom: ops.Geometry, b, prm: Params, n_outer, u0=None, s_init=None, 
             else:
                 s = solve_of(u.reshape(shape), prm, pool)
             sr = ops.reverse_flow(s)
-        th = Theta(shape, s, sr)
+        th = Theta(shape, s, sr, prm.temporal_tv)
         nu = th(u)
         w = 1.0 / np.sqrt(nu * nu + eps2)
         P = np.sqrt(w)

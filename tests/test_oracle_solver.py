@@ -262,3 +262,58 @@ def test_theta_adjoint_identity():
     x = rng.standard_normal(np.prod(shape))
     y = rng.standard_normal(th(x).size)
     assert abs(np.dot(th(x), y) - np.dot(x, th.T(y))) < 1e-11
+
+
+# ------------------------------------------------------------ D1-OF (AnisoTV-OF, Table 2)
+def test_time_differences_closed_forms():
+    """L_t of Table 2 (forward differences between frames, no boundary row): zero on a
+    sequence constant in time, the slope b on u_t = a + b t, and the transpose spreads
+    r_t to frames t+1 (+) and t (-)."""
+    rng = np.random.default_rng(3)
+    a = rng.standard_normal((5, 7))
+    const = np.broadcast_to(a, (4, 5, 7))
+    assert np.all(solver.time_diff(const) == 0)
+    ramp = a[None] + 0.75 * np.arange(4)[:, None, None]
+    assert np.allclose(solver.time_diff(ramp), 0.75, rtol=0, atol=1e-14)
+    r = np.zeros((3, 5, 7))
+    r[1, 2, 3] = 1.0
+    t = solver.time_diffT(r)
+    assert t[2, 2, 3] == 1.0 and t[1, 2, 3] == -1.0 and np.count_nonzero(t) == 2
+
+
+def test_theta_with_time_differences_adjoint_identity():
+    rng = np.random.default_rng(10)
+    shape = (4, 6, 7)
+    s = synth.random_velocities(3, 6, 7, 2.0, seed=2)
+    th = solver.Theta(shape, s, ops.reverse_flow(s), temporal=True)
+    x = rng.standard_normal(np.prod(shape))
+    y = rng.standard_normal(th(x).size)
+    assert th(x).size == (2 * 4 + 3 + 2 * 3) * 6 * 7
+    assert abs(np.dot(th(x), y) - np.dot(x, th.T(y))) < 1e-11
+
+
+def test_d1_of_mm_step_full_subspace_equals_dense_normal_equations():
+    """D1-OF: with V spanning R^n, one MMGKS step solves (H^T H + lam Theta^T P^2 Theta) u =
+    H^T b with Theta = [Psi; L_t; Mhat], L_t assembled here from its definition."""
+    g, b = _tiny_problem()
+    n = g.n
+    shape = (g.nt, g.ny, g.nx)
+    s = synth.random_velocities(g.nt - 1, g.ny, g.nx, 1.5, seed=6)
+    prm = solver.Params(ell=n, tau=0, image_rule=solver.RULE_FIXED, lam_fixed=0.05, eps=0.1, temporal_tv=1)
+    Hd = _dense_of(lambda x: ops.project(g, x), n, shape)
+    sr = ops.reverse_flow(s)
+    Tm = _dense_of(solver.Theta(shape, s, sr), n, shape)  # [Psi; Mhat]
+    npsi = 2 * n
+    Lt = np.zeros(((g.nt - 1) * g.ny * g.nx, n))  # row (t, p): u[t+1, p] - u[t, p]
+    ns = g.ny * g.nx
+    for t in range(g.nt - 1):
+        for q in range(ns):
+            Lt[t * ns + q, (t + 1) * ns + q] = 1.0
+            Lt[t * ns + q, t * ns + q] = -1.0
+    Th = np.vstack([Tm[:npsi], Lt, Tm[npsi:]])
+    u = np.zeros(n)
+    for n_outer in (1, 2):
+        res = solver.mmgks_of(g, b, prm, n_outer, s_init=s)
+        w = 1.0 / np.sqrt((Th @ u) ** 2 + prm.eps ** 2)
+        u = np.linalg.solve(Hd.T @ Hd + prm.lam_fixed * Th.T @ (w[:, None] * Th), Hd.T @ b)
+        np.testing.assert_allclose(res.u.ravel(), u, rtol=1e-8, atol=1e-10)
