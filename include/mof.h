@@ -92,6 +92,9 @@ typedef struct {
                               a = 2 or 4 to reach frames under 50x50): a x a block means, the
                               velocities interpolated bilinearly back to the full grid and
                               multiplied by a. 1 = full resolution; a must divide nx and ny */
+    int temporal_tv;       /* 1: D1-OF (AnisoTV-OF, Table 2): Theta = [Psi; L_t; Mhat] with L_t the
+                              forward differences between consecutive frames, all rows in the
+                              same l1 norm; 0 (default): M-OF, Theta = [Psi; Mhat] */
 } mof_solver_params;
 
 /* One record per outer iteration k of mof_solve (host struct). */

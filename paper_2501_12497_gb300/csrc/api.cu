@@ -124,6 +124,7 @@ void mof_default_params(mof_solver_params *p) {
     p->breakdown_tol = 0.0;
     p->of_streams = 0;
     p->of_scale = 1;
+    p->temporal_tv = 0;
 }
 
 mof_status mof_problem_create(const mof_geometry *g, int precision, mof_problem **out) {
@@ -399,11 +400,11 @@ mof_status mof_apply_reg_normal(mof_problem *p, const void *x, const void *uk, c
     int *rs = (int *)rad, *rr = rs + (long long)(p->nt - 1) * tiles_count(p);
     if (p->precision == MOF_FP64) {
         MOF_TRY(launch_tile_radii<double>(p, CD(s), CD(sr), rs, rr, S(stream)));
-        return launch_reg_normal<double>(p, CD(x), CD(uk), CD(s), CD(sr), rs, rr, eps, 1.0, nullptr, nullptr, D(q), D(y),
+        return launch_reg_normal<double>(p, 0, CD(x), CD(uk), CD(s), CD(sr), rs, rr, eps, 1.0, nullptr, nullptr, D(q), D(y),
                                          S(stream));
     }
     MOF_TRY(launch_tile_radii<float>(p, CF(s), CF(sr), rs, rr, S(stream)));
-    return launch_reg_normal<float>(p, CF(x), CF(uk), CF(s), CF(sr), rs, rr, eps, 1.0, nullptr, nullptr, F(q), F(y),
+    return launch_reg_normal<float>(p, 0, CF(x), CF(uk), CF(s), CF(sr), rs, rr, eps, 1.0, nullptr, nullptr, F(q), F(y),
                                     S(stream));
 }
 

@@ -113,7 +113,8 @@ template <typename real> mof_status launch_reverse_flow(const mof_problem *p, co
 // Weighted regulariser normal operator: y = y_add + scale * Theta^T W Theta x,
 // W from uk; q_scratch holds 2*(nt-1)*ns weighted flow rows. lam_dev (may be
 // null) multiplies `scale` by *lam_dev.
-template <typename real> mof_status launch_reg_normal(const mof_problem *p, const real *x, const real *uk, const real *s, const real *sr,
+// temporal: 1 adds L_t^T w_t L_t x (the temporal differences of D1-OF), 0 is M-OF
+template <typename real> mof_status launch_reg_normal(const mof_problem *p, int temporal, const real *x, const real *uk, const real *s, const real *sr,
                                                       const int *rad_s, const int *rad_sr, double eps, double scale, const double *lam_dev,
                                                       const real *y_add, real *q_scratch, real *y, cudaStream_t st);
 

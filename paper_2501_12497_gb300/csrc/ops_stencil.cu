@@ -487,7 +487,7 @@ __global__ void k_regn_apply(const real *__restrict__ x, const real *__restrict_
                              const real *__restrict__ sr, const real *__restrict__ q, const int *__restrict__ rad_s,
                              const int *__restrict__ rad_sr, int tiles, real eps2, double scale,
                              const double *__restrict__ lam, const real *__restrict__ y_add, real *__restrict__ y, int nx,
-                             int ny, int np) {
+                             int ny, int np, int temporal) {
     const int xx = blockIdx.x * TX + threadIdx.x, yy = blockIdx.y * TY + threadIdx.y, t = blockIdx.z;
     __shared__ real s_sc;  // scale * lam once per block (FP64 kept out of the threads)
     if (threadIdx.x == 0 && threadIdx.y == 0) s_sc = (real)(lam ? scale * *lam : scale);
@@ -509,13 +509,21 @@ __global__ void k_regn_apply(const real *__restrict__ x, const real *__restrict_
     if (xx < nx - 1) v -= wdx(i);
     if (yy > 0) v += wdy(i - nx);
     if (yy < ny - 1) v -= wdy(i);
+    if (temporal) {  // L_t^T w_t L_t x: the weighted differences to the previous and next frame
+        auto wdt = [&](const real *fa, const real *ka) -> real {
+            const real g = fa[i + ns] - fa[i], gk = ka[i + ns] - ka[i];
+            return g / sqrt(gk * gk + eps2);
+        };
+        if (t > 0) v += wdt(f - ns, k - ns);
+        if (t < np) v -= wdt(f, k);
+    }
     if (np > 0) v += flowT_at(q, s, sr, nx, ny, np, t, xx, yy, rad_s, rad_sr, tiles, blockIdx.y * gridDim.x + blockIdx.x);
     const real out = s_sc * v;
     y[t * ns + i] = y_add ? y_add[t * ns + i] + out : out;
 }
 
 template <typename real>
-mof_status launch_reg_normal(const mof_problem *p, const real *x, const real *uk, const real *s, const real *sr,
+mof_status launch_reg_normal(const mof_problem *p, int temporal, const real *x, const real *uk, const real *s, const real *sr,
                              const int *rad_s, const int *rad_sr, double eps, double scale, const double *lam_dev,
                              const real *y_add, real *q, real *y, cudaStream_t st) {
     const int np = p->nt - 1;
@@ -525,7 +533,7 @@ mof_status launch_reg_normal(const mof_problem *p, const real *x, const real *uk
         MOF_LAUNCH_CHECK();
     }
     ::mof::count_launch(), k_regn_apply<real><<<grid2d(p->nx, p->ny, p->nt), dim3(TX, TY), 0, st>>>(x, uk, s, sr, q, rad_s, rad_sr, tiles_count(p),
-                                                                            eps2, scale, lam_dev, y_add, y, p->nx, p->ny, np);
+                                                                            eps2, scale, lam_dev, y_add, y, p->nx, p->ny, np, temporal);
     MOF_LAUNCH_CHECK();
     return MOF_OK;
 }
@@ -545,7 +553,7 @@ mof_status launch_reg_normal(const mof_problem *p, const real *x, const real *uk
                                               real *, cudaStream_t);                                                          \
     template mof_status launch_flow_linT<real>(const mof_problem *, const real *, const real *, const real *, real *,          \
                                                cudaStream_t);                                                                 \
-    template mof_status launch_reg_normal<real>(const mof_problem *, const real *, const real *, const real *, const real *,   \
+    template mof_status launch_reg_normal<real>(const mof_problem *, int, const real *, const real *, const real *, const real *,   \
                                                 const int *, const int *, double, double, const double *, const real *,       \
                                                 real *, real *, cudaStream_t);
 

@@ -334,7 +334,7 @@ static mof_status ensure_ws(mof_problem *p, const mof_solver_params &prm, int n_
         w->beta1 = a.take<double>(1);
         w->alpha1 = a.take<double>(1);
         w->bb = a.take<double>(1);
-        w->gpart = a.take<double>((size_t)2 * w->gram_ctas * Kmax * Kmax);
+        w->gpart = a.take<double>((size_t)3 * w->gram_ctas * Kmax * Kmax);  // Psi, Mhat, L_t partial sets
         w->K = a.take<int>(1);
         w->KU = a.take<int>(1);
         w->grow = a.take<int>(1);
@@ -825,14 +825,15 @@ __global__ void __launch_bounds__(TG_T, tg_min_blocks<real>()) k_theta_gram(cons
 #pragma unroll
         for (int c = 0; c < 4; ++c) sum[a][c] = comp[a][c] = 0;
     // rows: 0 = all four rows per pixel (64 pixels per tile), 1 = the Psi rows only,
-    // 2 = the Mhat rows only (128 pixels per tile)
+    // 2 = the Mhat rows only (128 pixels per tile), 3 = the temporal differences L_t of
+    // D1-OF only (one row per pixel, 256 pixels per tile; q = 4)
     const int ns = nx * ny;
-    const int ppt = rows == 0 ? TG_PIX : 2 * TG_PIX;
+    const int ppt = rows == 0 ? TG_PIX : (rows == 3 ? 4 * TG_PIX : 2 * TG_PIX);
     const int tpf = (ns + ppt - 1) / ppt;
     const int np = nt - 1;
-    const int ntiles = tpf * (rows == 2 ? np : nt);
-    const int q = rows == 0 ? (tid & 3) : (tid & 1) + (rows == 2 ? 2 : 0);
-    const int pid = rows == 0 ? (tid >> 2) : (tid >> 1);
+    const int ntiles = tpf * (rows >= 2 ? np : nt);
+    const int q = rows == 0 ? (tid & 3) : (rows == 3 ? 4 : (tid & 1) + (rows == 2 ? 2 : 0));
+    const int pid = rows == 0 ? (tid >> 2) : (rows == 3 ? tid : (tid >> 1));
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int t = tile / tpf;
         const int pix = (tile - t * tpf) * ppt + pid;
@@ -852,6 +853,10 @@ __global__ void __launch_bounds__(TG_T, tg_min_blocks<real>()) k_theta_gram(cons
                 w00 = 1;
             } else if (q == 1) {
                 oc = base + nx;
+                o00 = o01 = o10 = o11 = base;
+                w00 = 1;
+            } else if (q == 4) {  // u(t+1) - u(t) at the pixel (t < nt - 1)
+                oc = base + ns;
                 o00 = o01 = o10 = o11 = base;
                 w00 = 1;
             } else {
@@ -1339,10 +1344,13 @@ mof_status SolveRun<real>::iteration(bool of_now, bool expand) {
     WS<real> &w = *wp;
     BasisRef<real> BV{w.V, n, Kmax, 1, w.K, nullptr};
     BasisRef<real> BH{w.HV, m, Kmax, 1, w.K, nullptr};
-        // The weighted Gram of Theta = [Psi; Mhat] in two parts: the Psi rows depend on the
-        // basis and u_k only, so they are accumulated on a side stream while Solve-OF runs;
-        // the Mhat rows follow the new flow. The reduction adds both sets of partials.
-        double *gpart_psi = w.gpart, *gpart_m = w.gpart + (long long)w.gram_ctas * Kmax * Kmax;
+        // The weighted Gram of Theta = [Psi; (L_t;) Mhat] in parts: the Psi rows (and the
+        // temporal differences of D1-OF) depend on the basis and u_k only, so they are
+        // accumulated on a side stream while Solve-OF runs; the Mhat rows follow the new
+        // flow. The reduction adds all sets of partials.
+        const long long gsz = (long long)w.gram_ctas * Kmax * Kmax;
+        double *gpart_psi = w.gpart, *gpart_m = w.gpart + gsz, *gpart_t = w.gpart + 2 * gsz;
+        const int nsets = prm.temporal_tv ? 3 : 2;
         const cudaStream_t pst = of_now ? w.side : st;
         if (of_now) {
             MOF_CUDA(cudaEventRecord(w.side_fork, st));
@@ -1352,6 +1360,9 @@ mof_status SolveRun<real>::iteration(bool of_now, bool expand) {
             Scope sc(tm, "theta_gram", pst);
             ::mof::count_launch(), k_theta_gram<real><<<w.gram_ctas, TG_T, tg_smem, pst>>>(w.V, n, Kmax, w.K, w.u, w.s, w.sr, eps2, p->nx,
                                                                                       p->ny, p->nt, 1, gpart_psi);
+            if (prm.temporal_tv)
+                ::mof::count_launch(), k_theta_gram<real><<<w.gram_ctas, TG_T, tg_smem, pst>>>(w.V, n, Kmax, w.K, w.u, w.s, w.sr, eps2,
+                                                                                          p->nx, p->ny, p->nt, 3, gpart_t);
         }
         if (of_now) {
             MOF_CUDA(cudaEventRecord(w.side_done, w.side));
@@ -1365,7 +1376,7 @@ mof_status SolveRun<real>::iteration(bool of_now, bool expand) {
             ::mof::count_launch(), k_theta_gram<real><<<w.gram_ctas, TG_T, tg_smem, st>>>(w.V, n, Kmax, w.K, w.u, w.s, w.sr, eps2, p->nx,
                                                                                      p->ny, p->nt, 2, gpart_m);
             if (of_now) MOF_CUDA(cudaStreamWaitEvent(st, w.side_done, 0));
-            ::mof::count_launch(), k_gram_reduce<<<152, 256, 0, st>>>(w.gpart, 2 * w.gram_ctas, Kmax, w.K, w.GT);
+            ::mof::count_launch(), k_gram_reduce<<<152, 256, 0, st>>>(w.gpart, nsets * w.gram_ctas, Kmax, w.K, w.GT);
         }
         {
             Scope sc(tm, "small_solve", st);
@@ -1383,7 +1394,7 @@ mof_status SolveRun<real>::iteration(bool of_now, bool expand) {
             }
             {
                 Scope sc(tm, "reg_normal", st);
-                MOF_TRY(launch_reg_normal<real>(p, w.un, w.u, w.s, w.sr, w.rad_s, w.rad_sr, prm.eps, 1.0, w.lam, w.tn, w.q, w.r,
+                MOF_TRY(launch_reg_normal<real>(p, prm.temporal_tv, w.un, w.u, w.s, w.sr, w.rad_s, w.rad_sr, prm.eps, 1.0, w.lam, w.tn, w.q, w.r,
                                                 st));
             }
             {
@@ -1594,6 +1605,7 @@ static mof_status check_params(const mof_problem *p, const mof_solver_params *pr
                     "(ell + n_outer = %d, of_ell + of_iters = %d)",
                     prm->ell + n_outer, prm->of_ell + prm->of_iters);
     if (!(prm->eps > 0) || !std::isfinite(prm->eps)) return fail(MOF_EINVAL, "eps must be finite and > 0");
+    if (prm->temporal_tv != 0 && prm->temporal_tv != 1) return fail(MOF_EINVAL, "temporal_tv must be 0 or 1");
     if (prm->of_scale < 1 || p->nx % prm->of_scale || p->ny % prm->of_scale || p->nx / prm->of_scale < 2 ||
         p->ny / prm->of_scale < 2)
         return fail(MOF_EINVAL, "of_scale must be >= 1, divide nx and ny and leave frames of at least 2x2 (got %d for %d x %d)",

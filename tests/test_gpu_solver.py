@@ -287,3 +287,24 @@ def test_of_scale_must_divide_the_frames():
     with pytest.raises(api.MofError) as e:
         api.mof_solve_of(p, api.mof_default_params(of_scale=3), u, s)
     assert e.value.status == api.MOF_EINVAL
+
+
+def test_mmgks_of_fp64_d1_of_matches_oracle():
+    """D1-OF (AnisoTV-OF, Table 2: Theta = [Psi; L_t; Mhat]) on the 64x64x8 two-disk workload,
+    6 outer iterations: the temporal rows enter the weighted Theta Gram (their own launch
+    beside Solve-OF) and the fused Theta^T W Theta of the residual."""
+    w = synth.plain_fp64(0)
+    ores = _oracle_solve(w, 6, temporal_tv=1)
+    u, s, rep = _gpu_solve(w, api.MOF_FP64, 6, temporal_tv=1)
+    assert rel(u, ores.u) <= 1e-6, rel(u, ores.u)
+    assert rel(s, ores.s) <= 1e-5, rel(s, ores.s)
+    base, _, _ = _gpu_solve(w, api.MOF_FP64, 6)
+    assert rel(u, base) > 1e-4  # the temporal rows change the result
+
+
+def test_mmgks_of_fp32_d1_of_precision_form_small():
+    w = synth.precision_form_small(0)
+    ores = _oracle_solve(w, 4, of_iters=10, temporal_tv=1)
+    u, s, rep = _gpu_solve(w, api.MOF_FP32, 4, of_iters=10, temporal_tv=1)
+    assert rel(u, ores.u) <= 1e-4, rel(u, ores.u)
+    assert rel(s, ores.s) <= 1e-3, rel(s, ores.s)
