@@ -55,6 +55,8 @@ def parse():
                     help="Solve-OF on frames downsampled by this factor (the paper's experiments: 2 or 4)")
     ap.add_argument("--tau", type=int, default=1,
                     help="Solve-OF every tau outer iterations (the paper's experiments: 20)")
+    ap.add_argument("--temporal-tv", type=int, default=0, choices=[0, 1],
+                    help="1: the D1-OF regulariser (temporal differences added to Theta)")
     return ap.parse_args()
 
 
@@ -215,7 +217,7 @@ def run_ours(args):
     w = synth.precision_form(seed=rank)
     p = api.mof_problem_create(w.nx, w.ny, w.nt, w.nb, w.na, w.angles, precision=api.MOF_FP32)
     prm = api.mof_default_params(noise_norm=w.noise_norm, of_streams=args.of_streams, of_scale=args.of_scale,
-                                 tau=args.tau)
+                                 tau=args.tau, temporal_tv=args.temporal_tv)
     stream = torch.cuda.current_stream(dev)
     b = torch.tensor(w.b.astype(np.float32), device=dev)
     u = torch.empty(p.n, dtype=torch.float32, device=dev)
@@ -251,7 +253,8 @@ def run_ours(args):
     # (the timed steps above run them on several streams, uninstrumented)
     class_ms = {}
     if not args.no_class_step:
-        prm1 = api.mof_default_params(noise_norm=w.noise_norm, of_streams=1, of_scale=args.of_scale, tau=args.tau)
+        prm1 = api.mof_default_params(noise_norm=w.noise_norm, of_streams=1, of_scale=args.of_scale, tau=args.tau,
+                                      temporal_tv=args.temporal_tv)
         api.mof_solve(p, prm1, N_OUTER, b, u, s)
         flush.fill_(1.0)
         torch.cuda.synchronize()
@@ -335,6 +338,7 @@ def run_ours(args):
                    "precision": "FP32 operators, FP64 Krylov/projected solves", "parallelism": "replicas",
                    "l2": "flushed between steps (512 MB write)", "rre": rre,
                    "of_streams": args.of_streams or "auto", "of_scale": args.of_scale, "tau": args.tau,
+                   "regulariser": "D1-OF" if args.temporal_tv else "M-OF",
                    "time_to_tolerance_s": total_ms / args.steps / 1e3},
         "e2e": {"value": e2e_value, "unit": "outer_iters/s", "h2d_bytes_per_step": 4 * p.m,
                 "d2h_bytes_per_step": 4 * p.n + 64 * N_OUTER},
@@ -416,7 +420,7 @@ def run_large(args):
     w = synth.large_form(0)
     p = api.mof_problem_create(w.nx, w.ny, w.nt, w.nb, w.na, w.angles, precision=api.MOF_FP32)
     prm = api.mof_default_params(noise_norm=w.noise_norm, of_streams=args.of_streams, of_scale=args.of_scale,
-                                 tau=args.tau)
+                                 tau=args.tau, temporal_tv=args.temporal_tv)
     b = torch.tensor(w.b.astype(np.float32), device="cuda")
     u = torch.empty(p.n, dtype=torch.float32, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
