@@ -266,3 +266,58 @@ def upsample_velocity(sc, a):
     out = (sc[:, :, y0][:, :, :, x0] * (1 - wy) * (1 - wx) + sc[:, :, y0][:, :, :, x1] * (1 - wy) * wx
            + sc[:, :, y1][:, :, :, x0] * wy * (1 - wx) + sc[:, :, y1][:, :, :, x1] * wy * wx)
     return a * out
+
+
+# ------------------------------------------------------------ rounding-and-clipping M(s)
+# Sec. 3, item 1 (eq. (m_matrix)): the velocity components are rounded to the nearest
+# integers and the source coordinates clipped to the image, so M(s) selects one pixel per
+# row. Reading: halves round away from zero (the rule of the reverse-flow remark).
+
+def _round_half_away(s):
+    return np.sign(s) * np.floor(np.abs(s) + 0.5)
+
+
+def warp_round(v, sx, sy):
+    """M(s) v for one frame (ny, nx) with rounding and clipping."""
+    v = np.asarray(v, dtype=np.float64)
+    ny, nx = v.shape
+    y, x = np.mgrid[0:ny, 0:nx]
+    X = np.clip(x + _round_half_away(np.asarray(sx, dtype=np.float64)).astype(int), 0, nx - 1)
+    Y = np.clip(y + _round_half_away(np.asarray(sy, dtype=np.float64)).astype(int), 0, ny - 1)
+    return v[Y, X]
+
+
+def warpT_round(r, sx, sy):
+    """M(s)^T r for one frame with rounding and clipping (each row's entry scattered back)."""
+    r = np.asarray(r, dtype=np.float64)
+    ny, nx = r.shape
+    y, x = np.mgrid[0:ny, 0:nx]
+    X = np.clip(x + _round_half_away(np.asarray(sx, dtype=np.float64)).astype(int), 0, nx - 1)
+    Y = np.clip(y + _round_half_away(np.asarray(sy, dtype=np.float64)).astype(int), 0, ny - 1)
+    out = np.zeros((ny, nx))
+    np.add.at(out, (Y, X), r)
+    return out
+
+
+def flow_round(u, s, sr):
+    """Mhat(s, s') u with the rounding-and-clipping M: rows u_p - M(s_p) u_{p+1} and
+    u_{p+1} - M(s'_p) u_p -> (2, nt-1, ny, nx)."""
+    u = np.asarray(u, dtype=np.float64)
+    nt = u.shape[0]
+    r = np.empty((2, nt - 1) + u.shape[1:])
+    for p in range(nt - 1):
+        r[0, p] = u[p] - warp_round(u[p + 1], s[p, 0], s[p, 1])
+        r[1, p] = u[p + 1] - warp_round(u[p], sr[p, 0], sr[p, 1])
+    return r
+
+
+def flowT_round(r, s, sr):
+    """The transpose of flow_round -> (nt, ny, nx)."""
+    npairs = r.shape[1]
+    u = np.zeros((npairs + 1,) + r.shape[2:])
+    for p in range(npairs):
+        u[p] += r[0, p]
+        u[p + 1] -= warpT_round(r[0, p], s[p, 0], s[p, 1])
+        u[p + 1] += r[1, p]
+        u[p] -= warpT_round(r[1, p], sr[p, 0], sr[p, 1])
+    return u

@@ -54,6 +54,7 @@ class Params:
     tau: int = 1             # OF update period (Sec. 4.1.5); 0 = never update s
     of_scale: int = 1        # Solve-OF on frames downsampled by this factor (Sec. 4.1.5, Sec. 5)
     temporal_tv: int = 0     # 1: Theta also holds the temporal differences L_t (D1-OF, Table 2)
+    warp_round: int = 0      # 1: M(s) by rounding and clipping (Sec. 3, item 1); 0: bilinear (item 2)
     of_iters: int = 20       # MMGKS iterations per Solve-OF call (Sec. 5)
     of_ell: int = 10         # GKB start of Solve-OF
     of_dr: int = 1           # box half-width of App. C
@@ -346,17 +347,19 @@ class Theta:
     Theta = [Psi; L_t; Mhat(s, s')], the AnisoTV-OF regulariser (D1-OF of Table 2:
     spatial and temporal first differences plus the motion term, all in the l1 norm)."""
 
-    def __init__(self, shape, s, sr, temporal=False):
+    def __init__(self, shape, s, sr, temporal=False, warp_round=False):
         self.shape = shape  # (nt, ny, nx)
         self.s, self.sr = s, sr
         self.temporal = bool(temporal)
+        self.flow = ops.flow_round if warp_round else ops.flow
+        self.flowT = ops.flowT_round if warp_round else ops.flowT
 
     def __call__(self, x):
         x = x.reshape(self.shape)
         parts = [ops.grad(x).ravel()]
         if self.temporal:
             parts.append(time_diff(x).ravel())
-        parts.append(ops.flow(x, self.s, self.sr).ravel())
+        parts.append(self.flow(x, self.s, self.sr).ravel())
         return np.concatenate(parts)
 
     def T(self, y):
@@ -367,7 +370,7 @@ class Theta:
         if self.temporal:
             out = out + time_diffT(y[npsi:npsi + nlt].reshape(nt - 1, ny, nx))
         r = y[npsi + nlt:].reshape(2, nt - 1, ny, nx)
-        return (out + ops.flowT(r, self.s, self.sr)).ravel()
+        return (out + self.flowT(r, self.s, self.sr)).ravel()
 
 
 @dataclass
@@ -418,7 +421,7 @@ def mmgks_of(geom: ops.Geometry, b, prm: Params, n_outer, u0=None, s_init=None, 
             else:
                 s = solve_of(u.reshape(shape), prm, pool)
             sr = ops.reverse_flow(s)
-        th = Theta(shape, s, sr, prm.temporal_tv)
+        th = Theta(shape, s, sr, prm.temporal_tv, prm.warp_round)
         nu = th(u)
         w = 1.0 / np.sqrt(nu * nu + eps2)
         P = np.sqrt(w)

@@ -429,3 +429,39 @@ def test_rescaling_by_one_is_the_identity():
     s = np.random.default_rng(2).standard_normal((2, 2, 6, 8))
     assert np.array_equal(ops.downsample(r, 1), r)
     assert np.allclose(ops.upsample_velocity(s, 1), s, rtol=0, atol=0)
+
+
+# ------------------------------------------------------------ rounding-and-clipping M(s)
+def test_round_warp_equals_bilinear_warp_on_integer_velocities():
+    """Where every velocity is an integer the two encodings of M(s) (Sec. 3, items 1 and 2)
+    are the same matrix: the rounding warp against the compiled bilinear oracle, including
+    clipped samples."""
+    rng = np.random.default_rng(4)
+    ny, nx = 9, 13
+    v = rng.standard_normal((ny, nx))
+    sx = rng.integers(-4, 5, (ny, nx)).astype(float)
+    sy = rng.integers(-4, 5, (ny, nx)).astype(float)
+    assert np.allclose(ops.warp_round(v, sx, sy), ops.warp(v, sx, sy), rtol=0, atol=1e-15)
+    r = rng.standard_normal((ny, nx))
+    assert np.allclose(ops.warpT_round(r, sx, sy), ops.warpT(r, sx, sy), rtol=0, atol=1e-14)
+
+
+def test_round_warp_halves_go_away_from_zero_and_rows_select_one_pixel():
+    ny, nx = 5, 7
+    v = np.arange(ny * nx, dtype=float).reshape(ny, nx)
+    z = np.zeros((ny, nx))
+    assert np.array_equal(ops.warp_round(v, z + 0.5, z), ops.warp_round(v, z + 1.0, z))
+    assert np.array_equal(ops.warp_round(v, z - 0.5, z), ops.warp_round(v, z - 1.0, z))
+    assert np.array_equal(ops.warp_round(v, z + 0.49, z - 0.49), v)
+    out = ops.warp_round(v, z + 2.3, z - 1.7)  # every value is some pixel of v
+    assert set(out.ravel()) <= set(v.ravel())
+
+
+def test_round_flow_adjoint_identity():
+    rng = np.random.default_rng(5)
+    nt, ny, nx = 4, 8, 9
+    s = synth.random_velocities(nt - 1, ny, nx, 2.5, seed=6)
+    sr = ops.reverse_flow(s)
+    u = rng.standard_normal((nt, ny, nx))
+    r = rng.standard_normal((2, nt - 1, ny, nx))
+    assert abs(np.sum(ops.flow_round(u, s, sr) * r) - np.sum(u * ops.flowT_round(r, s, sr))) < 1e-11
