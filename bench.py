@@ -57,6 +57,8 @@ def parse():
                     help="Solve-OF every tau outer iterations (the paper's experiments: 20)")
     ap.add_argument("--temporal-tv", type=int, default=0, choices=[0, 1],
                     help="1: the D1-OF regulariser (temporal differences added to Theta)")
+    ap.add_argument("--warp", default="bilinear", choices=["bilinear", "round"],
+                    help="encoding of the warp M(s) (Sec. 3): bilinear interpolation or rounding and clipping")
     return ap.parse_args()
 
 
@@ -216,6 +218,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     w = synth.precision_form(seed=rank)
     p = api.mof_problem_create(w.nx, w.ny, w.nt, w.nb, w.na, w.angles, precision=api.MOF_FP32)
+    api.mof_set_warp(p, 1 if args.warp == "round" else 0)
     prm = api.mof_default_params(noise_norm=w.noise_norm, of_streams=args.of_streams, of_scale=args.of_scale,
                                  tau=args.tau, temporal_tv=args.temporal_tv)
     stream = torch.cuda.current_stream(dev)
@@ -338,7 +341,7 @@ def run_ours(args):
                    "precision": "FP32 operators, FP64 Krylov/projected solves", "parallelism": "replicas",
                    "l2": "flushed between steps (512 MB write)", "rre": rre,
                    "of_streams": args.of_streams or "auto", "of_scale": args.of_scale, "tau": args.tau,
-                   "regulariser": "D1-OF" if args.temporal_tv else "M-OF",
+                   "regulariser": "D1-OF" if args.temporal_tv else "M-OF", "warp": args.warp,
                    "time_to_tolerance_s": total_ms / args.steps / 1e3},
         "e2e": {"value": e2e_value, "unit": "outer_iters/s", "h2d_bytes_per_step": 4 * p.m,
                 "d2h_bytes_per_step": 4 * p.n + 64 * N_OUTER},
@@ -419,6 +422,7 @@ def run_large(args):
     api.load()
     w = synth.large_form(0)
     p = api.mof_problem_create(w.nx, w.ny, w.nt, w.nb, w.na, w.angles, precision=api.MOF_FP32)
+    api.mof_set_warp(p, 1 if args.warp == "round" else 0)
     prm = api.mof_default_params(noise_norm=w.noise_norm, of_streams=args.of_streams, of_scale=args.of_scale,
                                  tau=args.tau, temporal_tv=args.temporal_tv)
     b = torch.tensor(w.b.astype(np.float32), device="cuda")
@@ -447,7 +451,8 @@ def run_large(args):
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": "ellipses1024x1024x64", "n": 1024, "nt": 64, "na": 90, "nb": 1448, "n_outer": N_OUTER,
-                   "rre": rre, "basis_last": rep[-1]["basis"], "l2": "flushed between steps (512 MB write)"},
+                   "rre": rre, "basis_last": rep[-1]["basis"], "l2": "flushed between steps (512 MB write)",
+                   "warp": args.warp},
         "gpu_launches": launches, "clocks": clk,
     }
     print(json.dumps(line), flush=True)

@@ -137,10 +137,19 @@ mof_status mof_apply_grad(mof_problem *p, const void *u, void *g, void *stream);
 /* u = Psi^T g (exact transpose; padded zero rows ignore g there). */
 mof_status mof_apply_gradT(mof_problem *p, const void *g, void *u, void *stream);
 
+/* Encoding of the warp M(s) (Sec. 3, the two constructions of the motion
+ * operator) used by every operator and solve on p from now on: mode 0
+ * (default), bilinear interpolation at r + s(r) clipped to the image; mode 1,
+ * rounding and clipping, M(s) picks the one pixel clamp(r + round(s(r))),
+ * halves rounded away from zero. In mode 1 the velocity VJP
+ * (mof_apply_flow_ds) is zero. Returns MOF_EINVAL for any other mode. */
+mof_status mof_set_warp(mof_problem *p, int mode);
+
 /* r = Mhat(s, s') u (Sec. 3, bilinear-warp encoding of M(s); Sec. 4:
  * Mhat = [Mbar; Mbar']):  r[0][p] = u_p - M(s_p) u_{p+1},
  * r[1][p] = u_{p+1} - M(sr_p) u_p. M(s) samples its argument at r + s(r),
- * clipped to the image, with bilinear weights. u: n, s, sr: nv, r: 2*(nt-1)*nx*ny. */
+ * clipped to the image, with bilinear weights (or by rounding, see
+ * mof_set_warp). u: n, s, sr: nv, r: 2*(nt-1)*nx*ny. */
 mof_status mof_apply_flow(mof_problem *p, const void *u, const void *s, const void *sr,
                           void *r, void *stream);
 

@@ -77,6 +77,7 @@ _SIGS = {
     "mof_solve_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 5),
     "mof_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 4),
     "mof_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "mof_set_warp": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "mof_get_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_void_p]),
     "mof_last_error": (ctypes.c_char_p, []),
@@ -376,6 +377,11 @@ def mof_autotune(problems, params, n_probe, bs, us, stream=None):
 
 def mof_set_timing(p, enable):
     _check(_lib.mof_set_timing(p.handle, 1 if enable else 0))
+
+
+def mof_set_warp(p, mode):
+    """M(s) encoding for every later operator and solve on p: 0 bilinear, 1 rounding and clipping."""
+    _check(_lib.mof_set_warp(p.handle, int(mode)))
 
 
 def mof_get_timing(p):

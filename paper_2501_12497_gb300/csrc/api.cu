@@ -235,6 +235,13 @@ mof_status mof_apply_gradT(mof_problem *p, const void *g, void *u, void *stream)
                     launch_gradT<double>(p, p->nt, CD(g), D(u), S(stream)));
 }
 
+mof_status mof_set_warp(mof_problem *p, int mode) {
+    MOF_TRY(check_problem(p));
+    if (mode != 0 && mode != 1) return fail(MOF_EINVAL, "unknown warp mode %d (0 bilinear, 1 rounding)", mode);
+    p->warp_mode = mode;
+    return MOF_OK;
+}
+
 mof_status mof_apply_flow(mof_problem *p, const void *u, const void *s, const void *sr, void *r, void *stream) {
     g_err[0] = 0;
     MOF_TRY(check_problem(p));

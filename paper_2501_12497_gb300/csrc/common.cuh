@@ -85,6 +85,7 @@ struct mof_problem {
     void *ws = nullptr;                 // solver workspace (solver.cu)
     int timing = 0;
     void *timer = nullptr;              // kernel-class timer (solver.cu)
+    int warp_mode = 0;                  // M(s): 0 bilinear, 1 rounding and clipping (Sec. 3)
 };
 
 namespace mof {

@@ -27,16 +27,19 @@ constexpr int TX = 32, TY = 8;
 
 inline dim3 grid2d(int nx, int ny, int nz) { return dim3((nx + TX - 1) / TX, (ny + TY - 1) / TY, nz); }
 
-// Sample coordinate of M(s) along one axis: X = clamp(x + v, 0, n - 1),
-// i0 = floor(X), i1 = min(i0 + 1, n - 1), w = X - i0. The fraction is taken
-// from v itself (v - floor(v) is exact), so the weights do not lose bits to
-// the magnitude of x.
+// Sample coordinate of M(s) along one axis (Sec. 3). wm = 0, bilinear: X =
+// clamp(x + v, 0, n - 1), i0 = floor(X), i1 = min(i0 + 1, n - 1), w = X - i0;
+// the fraction is taken from v itself (v - floor(v) is exact), so the weights
+// do not lose bits to the magnitude of x. wm = 1, rounding and clipping: i0 =
+// clamp(x + round(v), 0, n - 1) with halves rounded away from zero, w = 0.
 template <typename real>
-__device__ __forceinline__ void warp_axis(int x, real v, int n, int &i0, int &i1, real &w) {
+__device__ __forceinline__ void warp_axis(int x, real v, int n, int &i0, int &i1, real &w, int wm) {
     const real vc = v > (real)16777216 ? (real)16777216 : (v < (real)-16777216 ? (real)-16777216 : v);
     const real fv = floor(vc);
     const int I = x + (int)fv;
-    if (I < 0) {
+    if (wm) {
+        i0 = min(max(x + (int)round(vc), 0), n - 1); w = 0;
+    } else if (I < 0) {
         i0 = 0; w = 0;
     } else if (I >= n - 1) {
         i0 = n - 1; w = 0;
@@ -48,11 +51,11 @@ __device__ __forceinline__ void warp_axis(int x, real v, int n, int &i0, int &i1
 }
 
 template <typename real>
-__device__ __forceinline__ real bilinear(const real *__restrict__ f, int nx, int ny, int x, int y, real vx, real vy) {
+__device__ __forceinline__ real bilinear(const real *__restrict__ f, int nx, int ny, int x, int y, real vx, real vy, int wm) {
     int x0, x1, y0, y1;
     real wx, wy;
-    warp_axis(x, vx, nx, x0, x1, wx);
-    warp_axis(y, vy, ny, y0, y1, wy);
+    warp_axis(x, vx, nx, x0, x1, wx, wm);
+    warp_axis(y, vy, ny, y0, y1, wy, wm);
     const real a = ldg(f + (long long)y0 * nx + x0), b = ldg(f + (long long)y0 * nx + x1);
     const real c = ldg(f + (long long)y1 * nx + x0), d = ldg(f + (long long)y1 * nx + x1);
     const real top = (1 - wx) * a + wx * b, bot = (1 - wx) * c + wx * d;
@@ -62,11 +65,11 @@ __device__ __forceinline__ real bilinear(const real *__restrict__ f, int nx, int
 // Weight with which the source pixel (px, py), sampling at r + s(r), reaches
 // the pixel (qx, qy): the transposed bilinear weight.
 template <typename real>
-__device__ __forceinline__ real warp_weight_to(int px, int py, real vx, real vy, int nx, int ny, int qx, int qy) {
+__device__ __forceinline__ real warp_weight_to(int px, int py, real vx, real vy, int nx, int ny, int qx, int qy, int wm) {
     int x0, x1, y0, y1;
     real wx, wy;
-    warp_axis(px, vx, nx, x0, x1, wx);
-    warp_axis(py, vy, ny, y0, y1, wy);
+    warp_axis(px, vx, nx, x0, x1, wx, wm);
+    warp_axis(py, vy, ny, y0, y1, wy, wm);
     const real ax = (qx == x0 ? 1 - wx : (real)0) + (qx == x1 ? wx : (real)0);
     const real ay = (qy == y0 ? 1 - wy : (real)0) + (qy == y1 ? wy : (real)0);
     return ax * ay;
@@ -75,14 +78,14 @@ __device__ __forceinline__ real warp_weight_to(int px, int py, real vx, real vy,
 // (M(v)^T r)(q) by a gather over the window of radius R around q.
 template <typename real>
 __device__ __forceinline__ real warpT_gather(const real *__restrict__ r, const real *__restrict__ vx,
-                                             const real *__restrict__ vy, int nx, int ny, int qx, int qy, int R) {
+                                             const real *__restrict__ vy, int nx, int ny, int qx, int qy, int R, int wm) {
     real acc = 0;
     const int ylo = max(0, qy - R), yhi = min(ny - 1, qy + R);
     const int xlo = max(0, qx - R), xhi = min(nx - 1, qx + R);
     for (int py = ylo; py <= yhi; ++py) {
         for (int px = xlo; px <= xhi; ++px) {
             const long long i = (long long)py * nx + px;
-            const real w = warp_weight_to(px, py, ldg(vx + i), ldg(vy + i), nx, ny, qx, qy);
+            const real w = warp_weight_to(px, py, ldg(vx + i), ldg(vy + i), nx, ny, qx, qy, wm);
             if (w != (real)0) acc += w * ldg(r + i);
         }
     }
@@ -133,20 +136,20 @@ mof_status launch_gradT(const mof_problem *p, int nf, const real *g, real *u, cu
 // ================================================================= K4 Mhat
 template <typename real>
 __global__ void k_flow(const real *__restrict__ u, const real *__restrict__ s, const real *__restrict__ sr,
-                       real *__restrict__ r, int nx, int ny, int np) {
+                       real *__restrict__ r, int nx, int ny, int np, int wm) {
     const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, p = blockIdx.z;
     if (x >= nx || y >= ny) return;
     const long long ns = (long long)nx * ny, i = (long long)y * nx + x;
     const real *u0 = u + p * ns, *u1 = u0 + ns;
     const real *sp = s + 2LL * p * ns, *srp = sr + 2LL * p * ns;
-    r[p * ns + i] = u0[i] - bilinear(u1, nx, ny, x, y, sp[i], sp[ns + i]);
-    r[(np + p) * ns + i] = u1[i] - bilinear(u0, nx, ny, x, y, srp[i], srp[ns + i]);
+    r[p * ns + i] = u0[i] - bilinear(u1, nx, ny, x, y, sp[i], sp[ns + i], wm);
+    r[(np + p) * ns + i] = u1[i] - bilinear(u0, nx, ny, x, y, srp[i], srp[ns + i], wm);
 }
 
 template <typename real>
 mof_status launch_flow(const mof_problem *p, const real *u, const real *s, const real *sr, real *r, cudaStream_t st) {
     const int np = p->nt - 1;
-    ::mof::count_launch(), k_flow<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(u, s, sr, r, p->nx, p->ny, np);
+    ::mof::count_launch(), k_flow<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(u, s, sr, r, p->nx, p->ny, np, p->warp_mode);
     MOF_LAUNCH_CHECK();
     return MOF_OK;
 }
@@ -155,7 +158,7 @@ mof_status launch_flow(const mof_problem *p, const real *u, const real *s, const
 // rad[f][tile] = max over sources p and the pixels q of their bilinear
 // footprint, q in the tile, of |p - q|_inf. Launched with the gather tiling.
 template <typename real>
-__global__ void k_tile_radius(const real *__restrict__ v, int nx, int ny, int *__restrict__ rad, int tiles_x, int tiles) {
+__global__ void k_tile_radius(const real *__restrict__ v, int nx, int ny, int *__restrict__ rad, int tiles_x, int tiles, int wm) {
     __shared__ int own;
     const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, f = blockIdx.z;
     const int tid = threadIdx.y * TX + threadIdx.x;
@@ -166,8 +169,8 @@ __global__ void k_tile_radius(const real *__restrict__ v, int nx, int ny, int *_
         const real *vf = v + 2LL * f * ns;
         int x0, x1, y0, y1;
         real wx, wy;
-        warp_axis(x, vf[i], nx, x0, x1, wx);
-        warp_axis(y, vf[ns + i], ny, y0, y1, wy);
+        warp_axis(x, vf[i], nx, x0, x1, wx, wm);
+        warp_axis(y, vf[ns + i], ny, y0, y1, wy, wm);
         const int qx[2] = {x0, x1}, qy[2] = {y0, y1};
 #pragma unroll
         for (int a = 0; a < 2; ++a)
@@ -195,12 +198,12 @@ mof_status launch_tile_radii(const mof_problem *p, const real *s, const real *sr
     const int np = p->nt - 1, tiles = tiles_count(p);
     ::mof::count_launch(), k_zero_ints<<<8, 256, 0, st>>>(rad_s, (long long)np * tiles);
     MOF_LAUNCH_CHECK();
-    ::mof::count_launch(), k_tile_radius<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(s, p->nx, p->ny, rad_s, tiles_x(p), tiles);
+    ::mof::count_launch(), k_tile_radius<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(s, p->nx, p->ny, rad_s, tiles_x(p), tiles, p->warp_mode);
     MOF_LAUNCH_CHECK();
     if (sr) {
         ::mof::count_launch(), k_zero_ints<<<8, 256, 0, st>>>(rad_sr, (long long)np * tiles);
         MOF_LAUNCH_CHECK();
-        ::mof::count_launch(), k_tile_radius<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(sr, p->nx, p->ny, rad_sr, tiles_x(p), tiles);
+        ::mof::count_launch(), k_tile_radius<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(sr, p->nx, p->ny, rad_sr, tiles_x(p), tiles, p->warp_mode);
         MOF_LAUNCH_CHECK();
     }
     return MOF_OK;
@@ -211,20 +214,20 @@ mof_status launch_tile_radii(const mof_problem *p, const real *s, const real *sr
 template <typename real>
 __device__ __forceinline__ real flowT_at(const real *__restrict__ r, const real *__restrict__ s, const real *__restrict__ sr,
                                          int nx, int ny, int np, int t, int x, int y, const int *__restrict__ rad_s,
-                                         const int *__restrict__ rad_sr, int tiles, int tile) {
+                                         const int *__restrict__ rad_sr, int tiles, int tile, int wm) {
     const long long ns = (long long)nx * ny, i = (long long)y * nx + x;
     real v = 0;
     if (t < np) {
         const real *r1 = r + (np + t) * ns;
         const real *srp = sr + 2LL * t * ns;
         v += r[t * ns + i];
-        v -= warpT_gather(r1, srp, srp + ns, nx, ny, x, y, rad_sr[(long long)t * tiles + tile]);
+        v -= warpT_gather(r1, srp, srp + ns, nx, ny, x, y, rad_sr[(long long)t * tiles + tile], wm);
     }
     if (t > 0) {
         const real *r0 = r + (long long)(t - 1) * ns;
         const real *sp = s + 2LL * (t - 1) * ns;
         v += r[(np + t - 1) * ns + i];
-        v -= warpT_gather(r0, sp, sp + ns, nx, ny, x, y, rad_s[(long long)(t - 1) * tiles + tile]);
+        v -= warpT_gather(r0, sp, sp + ns, nx, ny, x, y, rad_s[(long long)(t - 1) * tiles + tile], wm);
     }
     return v;
 }
@@ -232,18 +235,18 @@ __device__ __forceinline__ real flowT_at(const real *__restrict__ r, const real 
 template <typename real>
 __global__ void k_flowT(const real *__restrict__ r, const real *__restrict__ s, const real *__restrict__ sr,
                         const int *__restrict__ rad_s, const int *__restrict__ rad_sr, real *__restrict__ u, int nx, int ny,
-                        int np, int tiles) {
+                        int np, int tiles, int wm) {
     const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, t = blockIdx.z;
     if (x >= nx || y >= ny) return;
     const int tile = blockIdx.y * gridDim.x + blockIdx.x;
-    u[(long long)t * nx * ny + (long long)y * nx + x] = flowT_at(r, s, sr, nx, ny, np, t, x, y, rad_s, rad_sr, tiles, tile);
+    u[(long long)t * nx * ny + (long long)y * nx + x] = flowT_at(r, s, sr, nx, ny, np, t, x, y, rad_s, rad_sr, tiles, tile, wm);
 }
 
 template <typename real>
 mof_status launch_flowT(const mof_problem *p, const real *r, const real *s, const real *sr, const int *rad_s,
                         const int *rad_sr, real *u, cudaStream_t st) {
     ::mof::count_launch(), k_flowT<real><<<grid2d(p->nx, p->ny, p->nt), dim3(TX, TY), 0, st>>>(r, s, sr, rad_s, rad_sr, u, p->nx, p->ny, p->nt - 1,
-                                                                      tiles_count(p));
+                                                                      tiles_count(p), p->warp_mode);
     MOF_LAUNCH_CHECK();
     return MOF_OK;
 }
@@ -267,8 +270,8 @@ __device__ __forceinline__ void bilinear_grad(const real *__restrict__ f, int nx
                                               real &gx, real &gy) {
     int x0, x1, y0, y1;
     real wx, wy;
-    warp_axis(x, vx, nx, x0, x1, wx);
-    warp_axis(y, vy, ny, y0, y1, wy);
+    warp_axis(x, vx, nx, x0, x1, wx, 0);
+    warp_axis(y, vy, ny, y0, y1, wy, 0);
     const real a = ldg(f + (long long)y0 * nx + x0), b = ldg(f + (long long)y0 * nx + x1);
     const real c = ldg(f + (long long)y1 * nx + x0), d = ldg(f + (long long)y1 * nx + x1);
     gx = axis_moves(x, vx, nx) ? (1 - wy) * (b - a) + wy * (d - c) : (real)0;
@@ -277,12 +280,20 @@ __device__ __forceinline__ void bilinear_grad(const real *__restrict__ f, int nx
 
 // gs[t] = -gr[0][t] grad B(u_{t+1}; x + s_t), gsr[t] = -gr[1][t] grad B(u_t; x + sr_t):
 // the vector-Jacobian product of r = Mhat(s, s') u with respect to s and s'.
+// With the rounding-and-clipping M(s) (wm = 1) the rows are piecewise constant
+// in s and the product is zero.
 template <typename real>
 __global__ void k_flow_ds(const real *__restrict__ u, const real *__restrict__ s, const real *__restrict__ sr,
-                          const real *__restrict__ gr, real *__restrict__ gs, real *__restrict__ gsr, int nx, int ny, int np) {
+                          const real *__restrict__ gr, real *__restrict__ gs, real *__restrict__ gsr, int nx, int ny, int np,
+                          int wm) {
     const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, t = blockIdx.z;
     if (x >= nx || y >= ny) return;
     const long long ns = (long long)nx * ny, i = (long long)y * nx + x;
+    if (wm) {
+        gs[2 * t * ns + i] = gs[(2 * t + 1) * ns + i] = 0;
+        gsr[2 * t * ns + i] = gsr[(2 * t + 1) * ns + i] = 0;
+        return;
+    }
     const real g0 = gr[t * ns + i], g1 = gr[(np + t) * ns + i];
     real gx, gy;
     bilinear_grad(u + (t + 1) * ns, nx, ny, x, y, s[2 * t * ns + i], s[(2 * t + 1) * ns + i], gx, gy);
@@ -297,7 +308,7 @@ template <typename real>
 mof_status launch_flow_ds(const mof_problem *p, const real *u, const real *s, const real *sr, const real *gr, real *gs,
                           real *gsr, cudaStream_t st) {
     ::mof::count_launch(), k_flow_ds<real><<<grid2d(p->nx, p->ny, p->nt - 1), dim3(TX, TY), 0, st>>>(u, s, sr, gr, gs, gsr, p->nx,
-                                                                                                   p->ny, p->nt - 1);
+                                                                                                   p->ny, p->nt - 1, p->warp_mode);
     MOF_LAUNCH_CHECK();
     return MOF_OK;
 }
@@ -466,17 +477,18 @@ mof_status launch_flow_linT(const mof_problem *p, const real *ux, const real *uy
 // Stage 1: q = W_M (Mhat x), W_M = ((Mhat uk)^2 + eps^2)^(-1/2), per flow row.
 template <typename real>
 __global__ void k_regn_flow_rows(const real *__restrict__ x, const real *__restrict__ uk, const real *__restrict__ s,
-                                 const real *__restrict__ sr, real eps2, real *__restrict__ q, int nx, int ny, int np) {
+                                 const real *__restrict__ sr, real eps2, real *__restrict__ q, int nx, int ny, int np,
+                                 int wm) {
     const int xx = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, p = blockIdx.z;
     if (xx >= nx || y >= ny) return;
     const long long ns = (long long)nx * ny, i = (long long)y * nx + xx;
     const real *sp = s + 2LL * p * ns, *srp = sr + 2LL * p * ns;
     const real svx = sp[i], svy = sp[ns + i], rvx = srp[i], rvy = srp[ns + i];
     const real *x0 = x + p * ns, *x1 = x0 + ns, *k0 = uk + p * ns, *k1 = k0 + ns;
-    const real fx = x0[i] - bilinear(x1, nx, ny, xx, y, svx, svy);
-    const real fk = k0[i] - bilinear(k1, nx, ny, xx, y, svx, svy);
-    const real bx = x1[i] - bilinear(x0, nx, ny, xx, y, rvx, rvy);
-    const real bk = k1[i] - bilinear(k0, nx, ny, xx, y, rvx, rvy);
+    const real fx = x0[i] - bilinear(x1, nx, ny, xx, y, svx, svy, wm);
+    const real fk = k0[i] - bilinear(k1, nx, ny, xx, y, svx, svy, wm);
+    const real bx = x1[i] - bilinear(x0, nx, ny, xx, y, rvx, rvy, wm);
+    const real bk = k1[i] - bilinear(k0, nx, ny, xx, y, rvx, rvy, wm);
     q[p * ns + i] = fx / sqrt(fk * fk + eps2);
     q[(np + p) * ns + i] = bx / sqrt(bk * bk + eps2);
 }
@@ -487,7 +499,7 @@ __global__ void k_regn_apply(const real *__restrict__ x, const real *__restrict_
                              const real *__restrict__ sr, const real *__restrict__ q, const int *__restrict__ rad_s,
                              const int *__restrict__ rad_sr, int tiles, real eps2, double scale,
                              const double *__restrict__ lam, const real *__restrict__ y_add, real *__restrict__ y, int nx,
-                             int ny, int np, int temporal) {
+                             int ny, int np, int temporal, int wm) {
     const int xx = blockIdx.x * TX + threadIdx.x, yy = blockIdx.y * TY + threadIdx.y, t = blockIdx.z;
     __shared__ real s_sc;  // scale * lam once per block (FP64 kept out of the threads)
     if (threadIdx.x == 0 && threadIdx.y == 0) s_sc = (real)(lam ? scale * *lam : scale);
@@ -517,7 +529,7 @@ __global__ void k_regn_apply(const real *__restrict__ x, const real *__restrict_
         if (t > 0) v += wdt(f - ns, k - ns);
         if (t < np) v -= wdt(f, k);
     }
-    if (np > 0) v += flowT_at(q, s, sr, nx, ny, np, t, xx, yy, rad_s, rad_sr, tiles, blockIdx.y * gridDim.x + blockIdx.x);
+    if (np > 0) v += flowT_at(q, s, sr, nx, ny, np, t, xx, yy, rad_s, rad_sr, tiles, blockIdx.y * gridDim.x + blockIdx.x, wm);
     const real out = s_sc * v;
     y[t * ns + i] = y_add ? y_add[t * ns + i] + out : out;
 }
@@ -529,11 +541,12 @@ mof_status launch_reg_normal(const mof_problem *p, int temporal, const real *x, 
     const int np = p->nt - 1;
     const real eps2 = (real)(eps * eps);
     if (np > 0) {
-        ::mof::count_launch(), k_regn_flow_rows<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(x, uk, s, sr, eps2, q, p->nx, p->ny, np);
+        ::mof::count_launch(), k_regn_flow_rows<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(x, uk, s, sr, eps2, q, p->nx, p->ny, np, p->warp_mode);
         MOF_LAUNCH_CHECK();
     }
     ::mof::count_launch(), k_regn_apply<real><<<grid2d(p->nx, p->ny, p->nt), dim3(TX, TY), 0, st>>>(x, uk, s, sr, q, rad_s, rad_sr, tiles_count(p),
-                                                                            eps2, scale, lam_dev, y_add, y, p->nx, p->ny, np, temporal);
+                                                                            eps2, scale, lam_dev, y_add, y, p->nx, p->ny, np, temporal,
+                                                                            p->warp_mode);
     MOF_LAUNCH_CHECK();
     return MOF_OK;
 }

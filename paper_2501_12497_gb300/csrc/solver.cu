@@ -153,6 +153,7 @@ struct WS {
     IterGraph graphs[8];
     mof_solver_params gkey{};
     int gkey_n = -1;
+    int gkey_wm = 0;                   // M(s) mode the graphs were captured with
     // the stand-alone Solve-OF (mof_solve_of), captured once per parameter set
     IterGraph ofgraph;
     mof_solver_params ofkey{};
@@ -767,11 +768,12 @@ __host__ __device__ constexpr int tg_col(int j) { return j * TG_S + 4 * (j / 4);
 constexpr int TG_MAXG = 8;         // row groups per 4x4 block at most
 
 template <typename real>
-__device__ __forceinline__ void warp_axis_s(int x, real v, int n, int &i0, int &i1, real &w) {
+__device__ __forceinline__ void warp_axis_s(int x, real v, int n, int &i0, int &i1, real &w, int wm) {
     const real vc = v > (real)16777216 ? (real)16777216 : (v < (real)-16777216 ? (real)-16777216 : v);
     const real fv = floor(vc);
     const int I = x + (int)fv;
-    if (I < 0) { i0 = 0; w = 0; }
+    if (wm) { i0 = min(max(x + (int)round(vc), 0), n - 1); w = 0; }  // rounding and clipping
+    else if (I < 0) { i0 = 0; w = 0; }
     else if (I >= n - 1) { i0 = n - 1; w = 0; }
     else { i0 = I; w = vc - fv; }
     if (!(v == v)) { i0 = x; w = 0; }
@@ -796,7 +798,7 @@ template <typename real>
 __global__ void __launch_bounds__(TG_T, tg_min_blocks<real>()) k_theta_gram(const real *__restrict__ V, long long n, int Kmax, const int *__restrict__ Kp,
                                                      const real *__restrict__ uk, const real *__restrict__ s,
                                                      const real *__restrict__ sr, real eps2, int nx, int ny, int nt,
-                                                     int rows, double *__restrict__ partial) {
+                                                     int rows, int wm, double *__restrict__ partial) {
     extern __shared__ __align__(16) unsigned char smraw[];
     real *As = reinterpret_cast<real *>(smraw);  // [K4 * 4][TG_S], column j = basis vector j
     const int K = min(Kp[0], Kmax);
@@ -863,8 +865,8 @@ __global__ void __launch_bounds__(TG_T, tg_min_blocks<real>()) k_theta_gram(cons
                 const real *sv = (q == 2 ? s : sr) + 2LL * t * ns;
                 int x0, x1, y0, y1;
                 real wx, wy;
-                warp_axis_s(x, sv[pix], nx, x0, x1, wx);
-                warp_axis_s(y, sv[ns + pix], ny, y0, y1, wy);
+                warp_axis_s(x, sv[pix], nx, x0, x1, wx, wm);
+                warp_axis_s(y, sv[ns + pix], ny, y0, y1, wy, wm);
                 const int fa = (q == 2 ? t : t + 1) * ns, fb = (q == 2 ? t + 1 : t) * ns;
                 oc = fa + pix;
                 o00 = fb + y0 * nx + x0;
@@ -1323,10 +1325,11 @@ mof_status SolveRun<real>::begin(cudaStream_t ust) {
     sa.flag = w.flag;
     sa.err = w.err;
     eps2 = (real)(prm.eps * prm.eps);
-    if (std::memcmp(&w.gkey, &prm, sizeof(prm)) != 0 || w.gkey_n != n_outer) {
+    if (std::memcmp(&w.gkey, &prm, sizeof(prm)) != 0 || w.gkey_n != n_outer || w.gkey_wm != p->warp_mode) {
         w.drop_graphs();
         w.gkey = prm;
         w.gkey_n = n_outer;
+        w.gkey_wm = p->warp_mode;
     }
     MOF_TRY(prepare_small_solve(Kmax));
     MOF_TRY(prepare_small_solve(w.Kof));
@@ -1359,10 +1362,10 @@ mof_status SolveRun<real>::iteration(bool of_now, bool expand) {
         {
             Scope sc(tm, "theta_gram", pst);
             ::mof::count_launch(), k_theta_gram<real><<<w.gram_ctas, TG_T, tg_smem, pst>>>(w.V, n, Kmax, w.K, w.u, w.s, w.sr, eps2, p->nx,
-                                                                                      p->ny, p->nt, 1, gpart_psi);
+                                                                                      p->ny, p->nt, 1, p->warp_mode, gpart_psi);
             if (prm.temporal_tv)
                 ::mof::count_launch(), k_theta_gram<real><<<w.gram_ctas, TG_T, tg_smem, pst>>>(w.V, n, Kmax, w.K, w.u, w.s, w.sr, eps2,
-                                                                                          p->nx, p->ny, p->nt, 3, gpart_t);
+                                                                                          p->nx, p->ny, p->nt, 3, p->warp_mode, gpart_t);
         }
         if (of_now) {
             MOF_CUDA(cudaEventRecord(w.side_done, w.side));
@@ -1374,7 +1377,7 @@ mof_status SolveRun<real>::iteration(bool of_now, bool expand) {
         {
             Scope sc(tm, "theta_gram", st);
             ::mof::count_launch(), k_theta_gram<real><<<w.gram_ctas, TG_T, tg_smem, st>>>(w.V, n, Kmax, w.K, w.u, w.s, w.sr, eps2, p->nx,
-                                                                                     p->ny, p->nt, 2, gpart_m);
+                                                                                     p->ny, p->nt, 2, p->warp_mode, gpart_m);
             if (of_now) MOF_CUDA(cudaStreamWaitEvent(st, w.side_done, 0));
             ::mof::count_launch(), k_gram_reduce<<<152, 256, 0, st>>>(w.gpart, nsets * w.gram_ctas, Kmax, w.K, w.GT);
         }

@@ -223,6 +223,82 @@ def test_reg_normal(shape, prec):
     assert rel(host(y), want) <= 3 * TOL[prec]
 
 
+# ------------------------------------------------ rounding-and-clipping M(s)
+def _round_velocities(nt, ny, nx, seed):
+    """Velocities with planted exact halves (the tie rule), integers and far out-of-grid values."""
+    rng = np.random.default_rng(seed)
+    v = rng.uniform(-4.0, 4.0, (nt - 1, 2, ny, nx))
+    v[0, 0, :3, :] = 0.5
+    v[0, 1, 3:6, :] = -0.5
+    v[-1, 0, :, :2] = 1.5
+    v[-1, 1, :, 2:4] = -2.5
+    v[0, :, -2:, :] = np.round(v[0, :, -2:, :])
+    v[-1, 0, -1, :] = 40.0
+    v[-1, 1, -2, :] = -40.0
+    return v
+
+
+@pytest.mark.parametrize("prec", [api.MOF_FP32, api.MOF_FP64])
+@pytest.mark.parametrize("shape", SHAPES[:2] + [(256, 256, 3, 30, 363)])
+def test_round_warp_flow_transpose_and_vjp(shape, prec):
+    """Mhat with the rounding-and-clipping M(s) (Sec. 3): forward rows bit-exact against the
+    oracle (one subtraction of a picked pixel), the transpose to rounding, the velocity VJP
+    zero; setting the mode back restores the bilinear rows."""
+    p, g = make(shape, prec)
+    nx, ny, nt = shape[:3]
+    u = dev(synth.random_images(nt, ny, nx, seed=41), prec)
+    s = dev(_round_velocities(nt, ny, nx, 42), prec)
+    sr = dev(_round_velocities(nt, ny, nx, 43), prec)
+    r = dev(np.random.default_rng(44).standard_normal(2 * (nt - 1) * nx * ny), prec)
+    sh = (nt - 1, 2, ny, nx)
+    hs, hsr, hu = host(s).reshape(sh), host(sr).reshape(sh), host(u).reshape(nt, ny, nx)
+    api.mof_set_warp(p, 1)
+    orr, ou = empty(r.numel(), prec), empty(p.n, prec)
+    api.mof_apply_flow(p, u, s, sr, orr)
+    api.mof_apply_flowT(p, r, s, sr, ou)
+    want = O.flow_round(hu, hs, hsr)
+    if prec == api.MOF_FP64:
+        np.testing.assert_array_equal(host(orr), want.ravel())
+    else:
+        np.testing.assert_array_equal(host(orr), want.astype(np.float32).astype(np.float64).ravel())
+    assert rel(host(ou), O.flowT_round(host(r).reshape(2, nt - 1, ny, nx), hs, hsr)) <= TOL[prec]
+    gs, gsr = empty(p.nv, prec), empty(p.nv, prec)
+    api.mof_apply_flow_ds(p, u, s, sr, r, gs, gsr)
+    assert not host(gs).any() and not host(gsr).any()
+    api.mof_set_warp(p, 0)
+    api.mof_apply_flow(p, u, s, sr, orr)
+    assert rel(host(orr), O.flow(hu, hs, hsr)) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [api.MOF_FP32, api.MOF_FP64])
+def test_round_warp_reg_normal(prec):
+    """Theta^T W Theta x with the rounding M(s) against the oracle's Theta(warp_round=True)."""
+    from oracle import solver as OS
+    shape = (64, 64, 8, 16, 64)
+    p, g = make(shape, prec)
+    nx, ny, nt = shape[:3]
+    x = dev(synth.random_images(nt, ny, nx, seed=45), prec)
+    uk = dev(synth.random_images(nt, ny, nx, seed=46), prec)
+    s = dev(_round_velocities(nt, ny, nx, 47), prec)
+    sr = dev(_round_velocities(nt, ny, nx, 48), prec)
+    eps = 0.05
+    y = empty(p.n, prec)
+    api.mof_set_warp(p, 1)
+    api.mof_apply_reg_normal(p, x, uk, s, sr, eps, y)
+    sh = (nt - 1, 2, ny, nx)
+    th = OS.Theta((nt, ny, nx), host(s).reshape(sh), host(sr).reshape(sh), warp_round=True)
+    nu = th(host(uk))
+    want = th.T(th(host(x)) / np.sqrt(nu * nu + eps * eps))
+    assert rel(host(y), want) <= 3 * TOL[prec]
+
+
+def test_set_warp_rejects_unknown_modes():
+    p, g = make(SHAPES[0], api.MOF_FP32)
+    for mode in (-1, 2):
+        with pytest.raises(api.MofError):
+            api.mof_set_warp(p, mode)
+
+
 # ------------------------------------------------------------ rescaling for Solve-OF
 @pytest.mark.parametrize("prec,tol", [(api.MOF_FP32, 1e-6), (api.MOF_FP64, 1e-14)])
 @pytest.mark.parametrize("a", [2, 4, 8])

@@ -302,6 +302,33 @@ def test_mmgks_of_fp64_d1_of_matches_oracle():
     assert rel(u, base) > 1e-4  # the temporal rows change the result
 
 
+def test_mmgks_of_fp64_round_warp_matches_oracle():
+    """MMGKS-OF with the rounding-and-clipping M(s) (Sec. 3) in Mhat, in the weighted Theta
+    Gram and in Theta^T W Theta, 64x64x8 two-disk workload, 5 outer iterations."""
+    w = synth.plain_fp64(0)
+    ores = _oracle_solve(w, 5, warp_round=1)
+    p = problem(w, api.MOF_FP64)
+    api.mof_set_warp(p, 1)
+    prm = api.mof_default_params(noise_norm=w.noise_norm)
+    b = torch.tensor(w.b, device="cuda")
+    u = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    s = torch.empty(p.nv, dtype=torch.float64, device="cuda")
+    rep = api.mof_solve(p, prm, 5, b, u, s)
+    u, s = u.cpu().numpy(), s.cpu().numpy()
+    assert rel(u, ores.u) <= 1e-6, rel(u, ores.u)
+    assert rel(s, ores.s) <= 1e-5, rel(s, ores.s)
+    for r, o in zip(rep, ores.report):
+        assert r["flag"] == o["flag"] and r["basis"] == o["basis"]
+    # the same problem handle back in bilinear mode (graphs captured again) gives the
+    # bilinear solve, which differs from the rounding one
+    api.mof_set_warp(p, 0)
+    u2 = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    api.mof_solve(p, prm, 5, b, u2)
+    base, _, _ = _gpu_solve(w, api.MOF_FP64, 5)
+    np.testing.assert_array_equal(u2.cpu().numpy(), base)
+    assert rel(u, base) > 1e-4
+
+
 def test_mmgks_of_fp32_d1_of_precision_form_small():
     w = synth.precision_form_small(0)
     ores = _oracle_solve(w, 4, of_iters=10, temporal_tv=1)
