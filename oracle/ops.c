@@ -22,8 +22,12 @@
  * H is the Joseph line integral along each ray, blockdiag over frames
  * (Sec. 2.1, the block-diagonal H).
  *
+ * Fan beam (orc_project_fan): the same Joseph rule along the lines from a point
+ * source through the bins of a flat detector (fan_line below).
+ *
  * Parity pins: tests/test_oracle_ops.py (adjoint identities, theta=0/90 column
- * and row sums, analytic disk chords, bilinear = scipy map_coordinates, exact
+ * and row sums, analytic disk chords (parallel and fan), the far-source limit,
+ * the fan magnification, bilinear = scipy map_coordinates, exact
  * integer shifts, zero residual on constants and translated linear images,
  * box stencils = scipy correlate, hand-checked reverse-flow cases).
  */
@@ -122,6 +126,68 @@ void orc_backproject(int nx, int ny, int nt, int nb, const int *na, const double
             for (int k = 0; k < nb; ++k) {
                 const double sigma = (k - 0.5 * (nb - 1)) * db;
                 joseph_ray(nx, ny, h, ang[aoff + a], sigma, ut, b[boff + (size_t)a * nb + k], 1);
+            }
+        }
+        aoff += na[t];
+        boff += (size_t)na[t] * nb;
+    }
+}
+
+/* --------------------------------------------------------- fan-beam projector */
+
+/* 2D fan beam with a flat detector (Sec. 5.1, the experiments' geometry). The
+ * view at angle theta looks along e = (-sin theta, cos theta), the direction
+ * of the parallel rays of the same angle: the source is the point S = -rs e,
+ * the detector the line through rd e perpendicular to e, and bin k its point
+ * D_k = rd e + sigma_k (cos theta, sin theta). The ray of bin k is the line
+ * through S and D_k; with the unit normal n of D_k - S it is the set
+ * {x n_x + y n_y = S . n}, which the parallel-beam Joseph rule integrates. */
+static void fan_line(double theta, double sigma, double rs, double rd, double *phi, double *p)
+{
+    const double ex = -sin(theta), ey = cos(theta);
+    const double sx = -rs * ex, sy = -rs * ey;
+    const double dx = rd * ex + sigma * cos(theta), dy = rd * ey + sigma * sin(theta);
+    const double vx = dx - sx, vy = dy - sy;
+    const double len = hypot(vx, vy);
+    const double nx = vy / len, ny = -vx / len;
+    *phi = atan2(ny, nx);
+    *p = sx * nx + sy * ny;
+}
+
+/* b = H u for the fan beam (block-diagonal over frames). */
+void orc_project_fan(int nx, int ny, int nt, int nb, const int *na, const double *ang,
+                     double h, double db, double rs, double rd, const double *u, double *b)
+{
+    size_t aoff = 0;
+    size_t boff = 0;
+    for (int t = 0; t < nt; ++t) {
+        const double *ut = u + (size_t)t * nx * ny;
+        for (int a = 0; a < na[t]; ++a) {
+            for (int k = 0; k < nb; ++k) {
+                double phi, p;
+                fan_line(ang[aoff + a], (k - 0.5 * (nb - 1)) * db, rs, rd, &phi, &p);
+                b[boff + (size_t)a * nb + k] = joseph_ray(nx, ny, h, phi, p, (double *)ut, 0.0, 0);
+            }
+        }
+        aoff += na[t];
+        boff += (size_t)na[t] * nb;
+    }
+}
+
+/* u = H^T b for the fan beam: the same ray entries, scattered. */
+void orc_backproject_fan(int nx, int ny, int nt, int nb, const int *na, const double *ang,
+                         double h, double db, double rs, double rd, const double *b, double *u)
+{
+    memset(u, 0, sizeof(double) * (size_t)nx * ny * nt);
+    size_t aoff = 0;
+    size_t boff = 0;
+    for (int t = 0; t < nt; ++t) {
+        double *ut = u + (size_t)t * nx * ny;
+        for (int a = 0; a < na[t]; ++a) {
+            for (int k = 0; k < nb; ++k) {
+                double phi, p;
+                fan_line(ang[aoff + a], (k - 0.5 * (nb - 1)) * db, rs, rd, &phi, &p);
+                joseph_ray(nx, ny, h, phi, p, ut, b[boff + (size_t)a * nb + k], 1);
             }
         }
         aoff += na[t];

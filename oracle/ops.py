@@ -27,6 +27,8 @@ def _load():
         i, d = ctypes.c_int, ctypes.c_double
         lib.orc_project.argtypes = [i, i, i, i, _I, _D, d, d, _D, _D]
         lib.orc_backproject.argtypes = [i, i, i, i, _I, _D, d, d, _D, _D]
+        lib.orc_project_fan.argtypes = [i, i, i, i, _I, _D, d, d, d, d, _D, _D]
+        lib.orc_backproject_fan.argtypes = [i, i, i, i, _I, _D, d, d, d, d, _D, _D]
         lib.orc_grad.argtypes = [i, i, i, _D, _D]
         lib.orc_gradT.argtypes = [i, i, i, _D, _D]
         lib.orc_warp.argtypes = [i, i, _D, _D, _D, _D]
@@ -38,7 +40,7 @@ def _load():
         lib.orc_flow_linT.argtypes = [i, i, i, _D, _D, _D, _D]
         lib.orc_reverse_flow.argtypes = [i, i, i, _D, _D]
         lib.orc_flow_ds.argtypes = [i, i, i, _D, _D, _D, _D, _D, _D]
-        for f in ("orc_project", "orc_backproject", "orc_grad", "orc_gradT", "orc_warp",
+        for f in ("orc_project", "orc_backproject", "orc_project_fan", "orc_backproject_fan", "orc_grad", "orc_gradT", "orc_warp",
                   "orc_warpT", "orc_flow", "orc_flowT", "orc_of_fields", "orc_flow_lin",
                   "orc_flow_linT", "orc_reverse_flow", "orc_flow_ds"):
             getattr(lib, f).restype = None
@@ -56,9 +58,12 @@ def _c64(a):
 
 @dataclass
 class Geometry:
-    """2D parallel-beam geometry of an image sequence (Sec. 2.1: H = blockdiag(H^1..H^nt)).
+    """2D parallel-beam or fan-beam geometry of an image sequence (Sec. 2.1:
+    H = blockdiag(H^1..H^nt)).
 
     angles: radians, concatenated over frames (na[t] entries for frame t).
+    fan: None for parallel beams, else (rs, rd): the source at distance rs from the
+    centre of rotation and a flat detector at distance rd on the other side (Sec. 5.1).
     """
     nx: int
     ny: int
@@ -68,6 +73,7 @@ class Geometry:
     angles: np.ndarray
     h: float = 1.0
     db: float = 1.0
+    fan: tuple = None
 
     def __post_init__(self):
         self.na = np.ascontiguousarray(self.na, dtype=np.int32)
@@ -92,6 +98,10 @@ def project(g: Geometry, u):
     """b = H u (Joseph ray-driven line integrals)."""
     u = _c64(u).reshape(g.nt, g.ny, g.nx)
     b = np.empty(g.m)
+    if g.fan is not None:
+        _load().orc_project_fan(g.nx, g.ny, g.nt, g.nb, g.na.ctypes.data_as(_I), _d(g.angles), g.h, g.db,
+                                float(g.fan[0]), float(g.fan[1]), _d(u), _d(b))
+        return b
     _load().orc_project(g.nx, g.ny, g.nt, g.nb, g.na.ctypes.data_as(_I), _d(g.angles), g.h, g.db,
                         _d(u), _d(b))
     return b
@@ -101,6 +111,10 @@ def backproject(g: Geometry, b):
     """u = H^T b (scatter of the same ray entries)."""
     b = _c64(b).reshape(g.m)
     u = np.empty((g.nt, g.ny, g.nx))
+    if g.fan is not None:
+        _load().orc_backproject_fan(g.nx, g.ny, g.nt, g.nb, g.na.ctypes.data_as(_I), _d(g.angles), g.h,
+                                    g.db, float(g.fan[0]), float(g.fan[1]), _d(b), _d(u))
+        return u
     _load().orc_backproject(g.nx, g.ny, g.nt, g.nb, g.na.ctypes.data_as(_I), _d(g.angles), g.h,
                             g.db, _d(b), _d(u))
     return u

@@ -13,6 +13,12 @@ angle theta and bin k is {x cos(theta) + y sin(theta) = sigma_k}; the angles
 of frame t are theta_{t,a} = (a*180/na + t*180/(na*nt)) degrees, i.e. each
 frame's fan of na equispaced angles is shifted by 180/(na*nt) degrees from the
 previous frame's (the "shifted intervals" scheme of Sec. 5.1.1).
+
+Fan-beam workloads (fan = (rs, rd)) put a point source at distance rs from the
+centre, opposite a flat detector at distance rd, for the view of angle theta
+on the line along (-sin theta, cos theta); the bins lie on the detector at
+sigma_k along (cos theta, sin theta), and each ray is the line from the source
+through its bin. Their data are the same analytic chords along those lines.
 """
 from dataclasses import dataclass, field
 import math
@@ -54,6 +60,7 @@ class Workload:
     b: np.ndarray           # (m,) noisy data
     noise_norm: float       # delta = ||b - b_clean||
     ellipses: list = field(default_factory=list)
+    fan: tuple = None       # (rs, rd) for a fan beam, None for parallel rays
 
     @property
     def m(self):
@@ -86,6 +93,18 @@ def ellipse_radon(e, theta, sigma):
     return np.where(q > 0, rho * 2.0 * a * b * np.sqrt(np.maximum(q, 0.0)) / a2, 0.0)
 
 
+def fan_rays(theta, sigma, rs, rd):
+    """Normal form (angle, offset) of the fan-beam rays: the line through the source
+    -rs (-sin, cos) and the detector point rd (-sin, cos) + sigma (cos, sin)."""
+    c, s = np.cos(theta), np.sin(theta)
+    sx, sy = rs * s, -rs * c
+    vx = -rd * s + sigma * c - sx
+    vy = rd * c + sigma * s - sy
+    ln = np.hypot(vx, vy)
+    nx, ny = vy / ln, -vx / ln
+    return np.arctan2(ny, nx), sx * nx + sy * ny
+
+
 def raster(e_list, nx, ny, h=1.0, ss=4):
     """Area-averaged raster (ss x ss sub-samples per pixel) of a sum of ellipses."""
     off = (np.arange(ss) + 0.5) / ss - 0.5
@@ -101,7 +120,7 @@ def raster(e_list, nx, ny, h=1.0, ss=4):
     return img.reshape(ny, ss, nx, ss).mean(axis=(1, 3))
 
 
-def _make(name, nx, ny, nt, na, nb, ellipses, noise_rel, seed, h=1.0, db=1.0, ss=4):
+def _make(name, nx, ny, nt, na, nb, ellipses, noise_rel, seed, h=1.0, db=1.0, ss=4, fan=None):
     na_arr, angles = shifted_angles(nt, na)
     sig = (np.arange(nb) - 0.5 * (nb - 1)) * db
     u_true = np.empty((nt, ny, nx))
@@ -113,8 +132,12 @@ def _make(name, nx, ny, nt, na, nb, ellipses, noise_rel, seed, h=1.0, db=1.0, ss
         u_true[t] = raster(ets, nx, ny, h, ss)
         th = angles[aoff:aoff + na_arr[t]]
         blk = np.zeros((na_arr[t], nb))
+        if fan is None:
+            phi, off_ = th[:, None], sig[None, :]
+        else:
+            phi, off_ = fan_rays(th[:, None], sig[None, :], fan[0], fan[1])
         for et in ets:
-            blk += ellipse_radon(et, th[:, None], sig[None, :])
+            blk += ellipse_radon(et, phi, off_)
         b_clean[off:off + blk.size] = blk.ravel()
         off += blk.size
         aoff += na_arr[t]
@@ -123,7 +146,7 @@ def _make(name, nx, ny, nt, na, nb, ellipses, noise_rel, seed, h=1.0, db=1.0, ss
     e = noise_rel * np.linalg.norm(b_clean) / math.sqrt(m) * rng.standard_normal(m)
     return Workload(name=name, nx=nx, ny=ny, nt=nt, nb=nb, na=na_arr, angles=angles, h=h, db=db,
                     u_true=u_true, b_clean=b_clean, b=b_clean + e,
-                    noise_norm=float(np.linalg.norm(e)), ellipses=ellipses)
+                    noise_norm=float(np.linalg.norm(e)), ellipses=ellipses, fan=fan)
 
 
 def _inside(e, nt, R):
@@ -136,7 +159,7 @@ def _inside(e, nt, R):
 
 
 def moving_disks(n=64, nt=8, na=16, nb=64, radii=(8.0, 12.0), rhos=(1.0, 0.6), speed=1.0,
-                 noise=0.01, seed=0, name=None):
+                 noise=0.01, seed=0, name=None, db=1.0, fan=None):
     """Uniform disks translating `speed` px/frame in fixed seeded directions, kept
     inside the inscribed circle of the grid for every frame."""
     rng = np.random.default_rng(seed)
@@ -154,11 +177,11 @@ def moving_disks(n=64, nt=8, na=16, nb=64, radii=(8.0, 12.0), rhos=(1.0, 0.6), s
                 break
         else:
             raise RuntimeError("could not place disk")
-    return _make(name or "disks%dx%dx%d" % (n, n, nt), n, n, nt, na, nb, ell, noise, seed)
+    return _make(name or "disks%dx%dx%d" % (n, n, nt), n, n, nt, na, nb, ell, noise, seed, db=db, fan=fan)
 
 
 def moving_ellipses(n=256, nt=32, na=30, nb=363, n_ell=6, axes=(8.0, 40.0), rho=(0.2, 1.0),
-                    speed=(0.5, 2.0), rot_deg=2.0, noise=0.01, seed=0, name=None, ss=4):
+                    speed=(0.5, 2.0), rot_deg=2.0, noise=0.01, seed=0, name=None, ss=4, db=1.0, fan=None):
     """Seeded ellipses, each in rigid motion: translation of U(speed) px/frame and
     rotation of U(-rot_deg, rot_deg) degrees/frame about its own centre."""
     rng = np.random.default_rng(seed)
@@ -182,7 +205,7 @@ def moving_ellipses(n=256, nt=32, na=30, nb=363, n_ell=6, axes=(8.0, 40.0), rho=
                 break
         else:
             raise RuntimeError("could not place ellipse")
-    return _make(name or "ellipses%dx%dx%d" % (n, n, nt), n, n, nt, na, nb, ell, noise, seed, ss=ss)
+    return _make(name or "ellipses%dx%dx%d" % (n, n, nt), n, n, nt, na, nb, ell, noise, seed, ss=ss, db=db, fan=fan)
 
 
 # The workloads of the method's benchmark configurations.
@@ -207,6 +230,19 @@ def differentiation_form(seed=0):
     """The two-disk generator at 256x256, T=32 (radii 32/48 px, 1 px/frame), 16 angles,
     256 bins."""
     return moving_disks(256, 32, 16, 256, radii=(32.0, 48.0), seed=seed, name="disks256x256x32")
+
+
+def fan_form(seed=0):
+    """The 256x256x32 moving-ellipse workload in a fan beam: source 512 px from the
+    centre, flat detector 256 px beyond it (magnification 1.5), 363 bins of 1.6 px
+    covering the magnified field of view, 30 views per frame over 180 degrees."""
+    return moving_ellipses(256, 32, 30, 363, seed=seed, name="fan_ellipses256x256x32", db=1.6, fan=(512.0, 256.0))
+
+
+def fan_form_small(seed=0):
+    """The 64x64x8 two-disk workload in a fan beam (source 128 px, detector 64 px
+    beyond the centre, 100 bins of 1.5 px, 16 views per frame): FP64 parity size."""
+    return moving_disks(64, 8, 16, 100, seed=seed, name="fan_disks64x64x8", db=1.5, fan=(128.0, 64.0))
 
 
 def batch_form(count=48, seed=0, sizes=(128, 192, 256, 384, 512), nt_range=(8, 40), na_range=(10, 45)):

@@ -92,6 +92,89 @@ def test_projector_converges_to_disk_chords():
     assert errs[1] < 0.75 * errs[0] and errs[2] < 0.75 * errs[1]
 
 
+# ------------------------------------------------------- fan-beam H, H^T
+def _fan_source_and_bins(theta, nb, db, rs, rd):
+    """Source S and detector points D_k of one view, written from the geometry: the view
+    looks along e = (-sin, cos), S = -rs e, D_k = rd e + sigma_k (cos, sin)."""
+    e = np.array([-np.sin(theta), np.cos(theta)])
+    f = np.array([np.cos(theta), np.sin(theta)])
+    sig = (np.arange(nb) - 0.5 * (nb - 1)) * db
+    return -rs * e, rd * e[None, :] + sig[:, None] * f[None, :]
+
+
+def test_fan_projector_adjoint_identity():
+    g = geom(23, 19, 2, 41, 5, seed=11)
+    g.fan = (40.0, 25.0)
+    rng = np.random.default_rng(12)
+    u = rng.standard_normal((2, 19, 23))
+    b = rng.standard_normal(g.m)
+    lhs = ops.project(g, u) @ b
+    rhs = np.sum(u * ops.backproject(g, b))
+    assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1.0)
+
+
+def test_fan_projector_converges_to_disk_chords():
+    """H (fan beam) applied to the raster of an off-centre disk tends to the exact chord
+    2 rho sqrt(r^2 - d^2), d the distance of the disk centre from the line through the
+    source and the bin (cross product), as the grid is refined. Views include fans that
+    straddle 45 degrees (rays of one view stepping along both axes)."""
+    cx, cy, r, rho = 4.1, -2.7, 8.0, 0.8
+    e = (cx, cy, r, r, 0.0, rho)
+    ang = np.deg2rad(np.array([0.0, 40.0, 45.0, 131.0, 222.0, 300.0]))
+    rs, rd = 60.0, 30.0
+    errs = []
+    for h in (1.0, 0.5, 0.25):
+        n = int(round(32 / h))
+        nb = int(round(1.6 * n))
+        db = 1.5 * h
+        g = ops.Geometry(n, n, 1, nb, [len(ang)], ang, h, db, fan=(rs, rd))
+        img = synth.raster([e], n, n, h)
+        exact = []
+        for th in ang:
+            S, D = _fan_source_and_bins(th, nb, db, rs, rd)
+            v = D - S
+            w = np.array([cx, cy]) - S
+            d = np.abs(v[:, 0] * w[1] - v[:, 1] * w[0]) / np.hypot(v[:, 0], v[:, 1])
+            exact.append(np.where(d < r, 2 * rho * np.sqrt(np.maximum(r * r - d * d, 0.0)), 0.0))
+        errs.append(rel(ops.project(g, img[None]), np.concatenate(exact)))
+    assert errs[0] < 0.03 and errs[2] < 0.01, errs
+    assert errs[1] < 0.75 * errs[0] and errs[2] < 0.75 * errs[1], errs
+
+
+def test_fan_projector_far_source_is_parallel():
+    """A source a million image widths away with the detector through the centre gives
+    the parallel-beam projector of the same angles."""
+    g = geom(21, 17, 2, 35, 4, seed=13)
+    rng = np.random.default_rng(14)
+    u = rng.standard_normal((2, 17, 21))
+    par = ops.project(g, u)
+    g.fan = (2e7, 0.0)
+    assert rel(ops.project(g, u), par) < 1e-5
+
+
+@pytest.mark.parametrize("pix", [(16, 16), (26, 9), (5, 27)])
+def test_fan_projector_point_lands_at_its_magnified_position(pix):
+    """A single pixel projects to a footprint centred on the detector coordinate of the
+    ray through its centre: sigma = sdd ((p - S) . f) / ((p - S) . e) (central projection
+    from the source onto the detector line)."""
+    n, nb, db, rs, rd = 33, 121, 0.5, 50.0, 20.0
+    ang = np.deg2rad(np.array([0.0, 33.0, 90.0, 160.0]))
+    g = ops.Geometry(n, n, 1, nb, [len(ang)], ang, 1.0, db, fan=(rs, rd))
+    u = np.zeros((1, n, n))
+    i, j = pix
+    u[0, j, i] = 1.0
+    b = ops.project(g, u).reshape(len(ang), nb)
+    p = np.array([i - 0.5 * (n - 1), j - 0.5 * (n - 1)])
+    for a, th in enumerate(ang):
+        e = np.array([-np.sin(th), np.cos(th)])
+        f = np.array([np.cos(th), np.sin(th)])
+        q = p + rs * e
+        sigma = (rs + rd) * (q @ f) / (q @ e)
+        t = sigma / db + 0.5 * (nb - 1)
+        cen = np.sum(np.arange(nb) * b[a]) / np.sum(b[a])
+        assert abs(cen - t) < 0.05, (a, cen, t)
+
+
 # ---------------------------------------------------------------- Psi, Psi^T
 
 def test_grad_zero_on_constants_and_constant_on_ramps():
