@@ -57,6 +57,9 @@ def parse():
                     help="Solve-OF every tau outer iterations (the paper's experiments: 20)")
     ap.add_argument("--temporal-tv", type=int, default=0, choices=[0, 1],
                     help="1: the D1-OF regulariser (temporal differences added to Theta)")
+    ap.add_argument("--geometry", default="parallel", choices=["parallel", "fan"],
+                    help="fan: the same workload in a flat fan beam (source 512 px, detector 256 px beyond "
+                         "the centre, 363 bins of 1.6 px)")
     ap.add_argument("--warp", default="bilinear", choices=["bilinear", "round"],
                     help="encoding of the warp M(s) (Sec. 3): bilinear interpolation or rounding and clipping")
     return ap.parse_args()
@@ -216,8 +219,8 @@ def run_ours(args):
     from paper_2501_12497_gb300 import api, synth
     api.load()
     dev = torch.device("cuda", local)
-    w = synth.precision_form(seed=rank)
-    p = api.mof_problem_create(w.nx, w.ny, w.nt, w.nb, w.na, w.angles, precision=api.MOF_FP32)
+    w = synth.fan_form(seed=rank) if args.geometry == "fan" else synth.precision_form(seed=rank)
+    p = api.mof_problem_create(w.nx, w.ny, w.nt, w.nb, w.na, w.angles, w.h, w.db, precision=api.MOF_FP32, fan=w.fan)
     api.mof_set_warp(p, 1 if args.warp == "round" else 0)
     prm = api.mof_default_params(noise_norm=w.noise_norm, of_streams=args.of_streams, of_scale=args.of_scale,
                                  tau=args.tau, temporal_tv=args.temporal_tv)
@@ -337,7 +340,8 @@ def run_ours(args):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, **CFG, "n_outer": N_OUTER, "of_iters": 20, "of_ell": 10, "ell": 10,
+        "config": {"workload": w.name, **CFG, "n_outer": N_OUTER, "of_iters": 20, "of_ell": 10, "ell": 10,
+                   "geometry": "fan (source 512, detector 256, bin 1.6)" if w.fan else "parallel",
                    "precision": "FP32 operators, FP64 Krylov/projected solves", "parallelism": "replicas",
                    "l2": "flushed between steps (512 MB write)", "rre": rre,
                    "of_streams": args.of_streams or "auto", "of_scale": args.of_scale, "tau": args.tau,

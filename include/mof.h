@@ -117,6 +117,22 @@ void mof_default_params(mof_solver_params *p);
 mof_status mof_problem_create(const mof_geometry *g, int precision, mof_problem **out);
 void mof_problem_destroy(mof_problem *p);
 
+/* Create a fan-beam problem (Sec. 5.1: the experiments' 2D flat fan-beam
+ * geometry): for the view at angle theta the source is the point
+ * -source_distance (-sin theta, cos theta) and the detector the line at
+ * detector_distance on the other side of the centre, perpendicular to
+ * (-sin theta, cos theta); bin k is its point at sigma_k = (k - (nb-1)/2)
+ * bin_size along (cos theta, sin theta), and its ray the line from the source
+ * through that point. mof_apply_A integrates each ray by the same Joseph rule
+ * as the parallel rays (its own direction, step h / max(|cos|, |sin|));
+ * mof_apply_AT is its exact transpose (pixel-driven gather). Every other
+ * entry point is unchanged. Distances are in the units of pixel_size.
+ * Returns MOF_EINVAL unless source_distance exceeds half the frame diagonal
+ * plus two pixels and detector_distance >= 0; holds a ray table of 32 (FP32)
+ * or 40 (FP64) bytes per data value on the device. */
+mof_status mof_problem_create_fan(const mof_geometry *g, double source_distance, double detector_distance,
+                                  int precision, mof_problem **out);
+
 /* Sizes: n = nx*ny*nt pixels, m = nb * sum(na) data values,
  * nv = (nt-1)*2*nx*ny values of one velocity field. Any pointer may be NULL. */
 mof_status mof_problem_sizes(const mof_problem *p, long long *n, long long *m, long long *nv);

@@ -52,6 +52,8 @@ LIB_PATH = _build.LIB_PATH
 _SIGS = {
     "mof_default_params": (None, [ctypes.c_void_p]),
     "mof_problem_create": (ctypes.c_int, [ctypes.POINTER(mof_geometry), ctypes.c_int, ctypes.c_void_p]),
+    "mof_problem_create_fan": (ctypes.c_int, [ctypes.POINTER(mof_geometry), ctypes.c_double, ctypes.c_double,
+                                              ctypes.c_int, ctypes.c_void_p]),
     "mof_problem_destroy": (None, [ctypes.c_void_p]),
     "mof_problem_sizes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "mof_apply_A": (ctypes.c_int, [ctypes.c_void_p] * 4),
@@ -152,13 +154,18 @@ def mof_default_params(**over):
     return p
 
 
-def mof_problem_create(nx, ny, nt, nb, na, angles, pixel_size=1.0, bin_size=1.0, precision=MOF_FP32):
+def mof_problem_create(nx, ny, nt, nb, na, angles, pixel_size=1.0, bin_size=1.0, precision=MOF_FP32, fan=None):
+    """A parallel-beam problem, or with fan = (source_distance, detector_distance) a
+    fan-beam problem (mof_problem_create_fan)."""
     load()
     na_arr = np.ascontiguousarray(na, dtype=np.int32)
     ang = np.ascontiguousarray(angles, dtype=np.float64)
     g = mof_geometry(nx, ny, nt, nb, na_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                      ang.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), pixel_size, bin_size)
     h = ctypes.c_void_p()
+    if fan is not None:
+        _check(_lib.mof_problem_create_fan(ctypes.byref(g), float(fan[0]), float(fan[1]), precision, ctypes.byref(h)))
+        return Problem(h.value, nx, ny, nt, nb, precision)
     _check(_lib.mof_problem_create(ctypes.byref(g), precision, ctypes.byref(h)))
     return Problem(h.value, nx, ny, nt, nb, precision)
 

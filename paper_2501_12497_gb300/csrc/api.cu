@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <new>
@@ -90,6 +91,67 @@ static AngleParams angle_params(double theta, int frame, int nx, int ny, int nb,
     split12(P.f0_k, P.f0k_hi, P.f0k_lo);
     P.df_f = (float)P.df;
     return P;
+}
+
+// Fan-beam ray tables. Bin k sits at sigma_k on the detector; its ray leaves the
+// source at the angle gamma_k = atan(sigma_k / (rs + rd)) from the central ray, so
+// in the normal form {x cos(phi) + y sin(phi) = p} of the parallel rays it has
+// phi = theta - gamma_k and p = rs sin(gamma_k) (the source lies on it). From there
+// the Joseph march is set up as for a parallel ray of that angle and offset.
+template <typename real>
+static void fan_ray(double theta, double gamma, double poff, int nx, int ny, double h, FanRay<real> &R) {
+    const double phi = theta - gamma, c = std::cos(phi), s = std::sin(phi);
+    const int rows = std::fabs(c) >= std::fabs(s);
+    const double cc = rows ? c : s, ss = rows ? s : c;
+    const int nfast = rows ? nx : ny, nstep = rows ? ny : nx;
+    const double f0 = poff / (cc * h) + 0.5 * (nfast - 1) + 0.5 * (nstep - 1) * (ss / cc);
+    const double df = -ss / cc;
+    // steps whose crossing can lie in (-1, nfast), two steps of margin each side
+    int jlo = 0, jhi = nstep - 1;
+    if (df != 0.0) {
+        const double ja = (-1.0 - f0) / df, jb = ((double)nfast - f0) / df;
+        const double lo = std::fmax(std::fmin(ja, jb), -1.0), hi = std::fmin(std::fmax(ja, jb), (double)nstep);
+        if (hi < lo) {
+            jhi = -1;
+        } else {
+            jlo = std::max(0, (int)std::floor(lo) - 2);
+            jhi = std::min(nstep - 1, (int)std::ceil(hi) + 2);
+        }
+    } else if (!(f0 > -1.0 && f0 < (double)nfast)) {
+        jhi = -1;
+    }
+    R.rows = rows;
+    R.jlo = jlo;
+    R.jhi = jhi;
+    if constexpr (sizeof(real) == 4) {
+        const double fl = std::floor(f0);
+        R.ib = (int)std::fmax(std::fmin(fl, 1e9), -1e9);
+        R.fb = (float)(f0 - fl);
+        split12(df, R.df_hi, R.df_lo);
+        R.wstep = (float)(h / std::fabs(cc));
+    } else {
+        R.f0 = f0;
+        R.df = df;
+        R.wstep = h / std::fabs(cc);
+        R.pad_ = 0;
+    }
+}
+
+template <typename real>
+static cudaError_t upload_fan_rays(mof_problem *p, const double *angles) {
+    const int nb = p->nb;
+    std::vector<double> gam(nb), poff(nb);
+    for (int k = 0; k < nb; ++k) {
+        const double sig = (k - 0.5 * (nb - 1)) * p->db;
+        gam[k] = std::atan2(sig, p->rs + p->rd);
+        poff[k] = p->rs * std::sin(gam[k]);
+    }
+    std::vector<FanRay<real>> rays((size_t)p->A * nb);
+    for (int a = 0; a < p->A; ++a)
+        for (int k = 0; k < nb; ++k) fan_ray<real>(angles[a], gam[k], poff[k], p->nx, p->ny, p->h, rays[(size_t)a * nb + k]);
+    cudaError_t e = cudaMalloc(&p->d_fanray, sizeof(FanRay<real>) * rays.size());
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_fanray, rays.data(), sizeof(FanRay<real>) * rays.size(), cudaMemcpyHostToDevice);
+    return e;
 }
 
 static mof_status check_problem(const mof_problem *p) {
@@ -179,9 +241,47 @@ mof_status mof_problem_create(const mof_geometry *g, int precision, mof_problem 
     return MOF_OK;
 }
 
+mof_status mof_problem_create_fan(const mof_geometry *g, double source_distance, double detector_distance,
+                                  int precision, mof_problem **out) {
+    if (!g || !out) return fail(MOF_EINVAL, "null geometry or output pointer");
+    *out = nullptr;
+    const double half_diag = 0.5 * std::hypot((double)g->nx, (double)g->ny) * g->pixel_size;
+    if (!(source_distance > half_diag + 2.0 * g->pixel_size) || !std::isfinite(source_distance))
+        return fail(MOF_EINVAL, "source_distance %g must exceed half the frame diagonal plus two pixels (%g)",
+                    source_distance, half_diag + 2.0 * g->pixel_size);
+    if (!(detector_distance >= 0.0) || !std::isfinite(detector_distance))
+        return fail(MOF_EINVAL, "detector_distance must be finite and >= 0");
+    mof_problem *p = nullptr;
+    MOF_TRY(mof_problem_create(g, precision, &p));
+    p->fan = 1;
+    p->rs = source_distance;
+    p->rd = detector_distance;
+    p->fan_scale = (float)((source_distance + detector_distance) / g->bin_size);
+    std::vector<FanView> views(p->A);
+    const double cx = 0.5 * (g->nx - 1) * g->pixel_size, cy = 0.5 * (g->ny - 1) * g->pixel_size;
+    for (int a = 0; a < p->A; ++a) {
+        const double th = g->angles[a], ex = -std::sin(th), ey = std::cos(th);
+        // q = p - S, S = -rs e, p = (x h - cx, y h - cy)
+        views[a] = FanView{(float)(-cx + source_distance * ex), (float)(-cy + source_distance * ey), (float)ex, (float)ey,
+                           (float)std::cos(th), (float)std::sin(th)};
+    }
+    cudaError_t e = precision == MOF_FP64 ? upload_fan_rays<double>(p, g->angles) : upload_fan_rays<float>(p, g->angles);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_fanview, sizeof(FanView) * p->A);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_fanview, views.data(), sizeof(FanView) * p->A, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        mof_status st = cuda_fail(e, "mof_problem_create_fan", __FILE__, __LINE__);
+        mof_problem_destroy(p);
+        return st;
+    }
+    *out = p;
+    return MOF_OK;
+}
+
 void mof_problem_destroy(mof_problem *p) {
     if (!p) return;
     free_workspace(p);
+    if (p->d_fanray) cudaFree(p->d_fanray);
+    if (p->d_fanview) cudaFree(p->d_fanview);
     if (p->d_ang) cudaFree(p->d_ang);
     if (p->d_aoff) cudaFree(p->d_aoff);
     delete p;

@@ -71,6 +71,30 @@ struct AngleParams {
     float df_f;         // df rounded to FP32 (step-range bounds only)
 };
 
+// Fan beam (flat detector): one Joseph march per ray (view a, bin k), stored per
+// ray because the rays of one view are not parallel. The crossing of step j is
+// f(j) = f0 + j df along the fast axis (x when rows = 1, else y), each step
+// weighted wstep = h / max(|cos|, |sin|) of the ray; steps jlo..jhi are the
+// ones whose crossing can touch the frame (both kernels use the same range).
+template <typename real> struct FanRay;
+template <> struct FanRay<float> {
+    int ib;              // floor(f0)
+    float fb;            // f0 - floor(f0)
+    float df_hi, df_lo;  // df split, df_hi with 12 significant bits
+    float wstep;
+    int rows, jlo, jhi;
+};
+template <> struct FanRay<double> {
+    double f0, df, wstep;
+    int rows, jlo, jhi, pad_;
+};
+// Per view, for the pixel-driven transpose: q = p - S = (x h + qx0, y h + qy0) is the
+// pixel centre seen from the source; its bin coordinate is
+// scale (q . f) / (q . e) + (nb - 1)/2, e the central ray direction, f the detector axis.
+struct FanView {
+    float qx0, qy0, ex, ey, fx, fy;
+};
+
 }  // namespace mof
 
 struct mof_problem {
@@ -86,6 +110,11 @@ struct mof_problem {
     int timing = 0;
     void *timer = nullptr;              // kernel-class timer (solver.cu)
     int warp_mode = 0;                  // M(s): 0 bilinear, 1 rounding and clipping (Sec. 3)
+    int fan = 0;                        // 1: fan beam with a flat detector
+    double rs = 0, rd = 0;              // source and detector distances from the centre
+    float fan_scale = 0;                // (rs + rd) / db
+    void *d_fanray = nullptr;           // device FanRay<real>[A * nb] (fan only)
+    mof::FanView *d_fanview = nullptr;  // device [A] (fan only)
 };
 
 namespace mof {

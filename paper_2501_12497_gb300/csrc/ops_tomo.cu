@@ -8,6 +8,12 @@
 // two linear-interpolation taps per step, weight h/mu), K2 from the pixel
 // side (the <= 2 bins within mu*h of p_ij), so <H u, b> = <u, H^T b> holds to
 // rounding.
+//
+// Fan beam (flat detector, the geometry of the paper's experiments, Sec. 5.1):
+// every ray is the line from the source through its bin, integrated by the
+// same Joseph rule with its own direction (k_project_fan); the transpose
+// (k_backproject_fan) visits, per pixel and view, the bins whose rays can
+// cross the pixel's two Joseph segments and re-evaluates the forward entry.
 #include "common.cuh"
 
 namespace mof {
@@ -108,11 +114,51 @@ __global__ void __launch_bounds__(128) k_project(const real *__restrict__ u, con
     }
 }
 
+// ---------------------------------------------------------- K1 fan beam
+// One thread per ray (view a = blockIdx.y, bin k); the march of the parallel
+// kernel with the ray's own start, step and range from the ray table.
+template <typename real>
+__global__ void __launch_bounds__(128) k_project_fan(const real *__restrict__ u, const real *__restrict__ uT,
+                                                     real *__restrict__ b, const FanRay<real> *__restrict__ rays,
+                                                     const AngleParams *__restrict__ ang, int nx, int ny, int nb) {
+    const int a = blockIdx.y;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nb) return;
+    const long long ns = (long long)nx * ny;
+    const FanRay<real> R = rays[(long long)a * nb + k];
+    const int frame = ang[a].frame;
+    const real *img = R.rows ? u + frame * ns : uT + frame * ns;
+    const int nfast = R.rows ? nx : ny;
+    real acc = 0;
+    for (int j = R.jlo; j <= R.jhi; ++j) {
+        int i0;
+        real w1;
+        if constexpr (sizeof(real) == 4) {
+            affine_frac(R.ib, R.fb, R.df_hi, R.df_lo, j, i0, w1);
+        } else {
+            const double f = fma((double)j, R.df, R.f0), fl = floor(f);
+            i0 = (int)fl;
+            w1 = f - fl;
+        }
+        const real *row = img + (long long)j * nfast;
+        if (i0 >= 0 && i0 < nfast) acc = fma((real)1 - w1, ldg(row + i0), acc);
+        if (i0 + 1 >= 0 && i0 + 1 < nfast) acc = fma(w1, ldg(row + i0 + 1), acc);
+    }
+    b[(long long)a * nb + k] = acc * R.wstep;
+}
+
 template <typename real>
 mof_status launch_project(const mof_problem *p, const real *u, real *uT, real *b, cudaStream_t st) {
     dim3 tb(32, 8), tg((p->nx + 31) / 32, (p->ny + 31) / 32, p->nt);
     ::mof::count_launch(), k_transpose<real><<<tg, tb, 0, st>>>(u, uT, p->nx, p->ny);
     MOF_LAUNCH_CHECK();
+    if (p->fan) {
+        dim3 grid((p->nb + 127) / 128, p->A);
+        ::mof::count_launch(), k_project_fan<real><<<grid, 128, 0, st>>>(u, uT, b, static_cast<const FanRay<real> *>(p->d_fanray),
+                                                                        p->d_ang, p->nx, p->ny, p->nb);
+        MOF_LAUNCH_CHECK();
+        return MOF_OK;
+    }
     dim3 grid((p->nb + 127) / 128, p->A);
     ::mof::count_launch(), k_project<real><<<grid, 128, 0, st>>>(u, uT, b, p->d_ang, p->nx, p->ny, p->nb);
     MOF_LAUNCH_CHECK();
@@ -208,9 +254,69 @@ __global__ void __launch_bounds__(BP_TX *BP_TY) k_backproject(const real *__rest
     if (x < nx && y < ny) u[(long long)t * nx * ny + (long long)y * nx + x] = acc;
 }
 
+// ---------------------------------------------------------- K2 fan beam
+// One thread per pixel. A ray steps over rows (or columns) and gives the pixel
+// a weight only at the step of the pixel's row (column), when its crossing
+// there is less than one pixel away; so the rays that reach the pixel are
+// those crossing the open segments of half-length h through its centre along
+// x and along y. Seen from the source, those segments cover the bins between
+// the central projections of their four end points (widened by one bin for
+// the FP32 evaluation); for each such bin the forward entry is re-evaluated
+// with the forward's own arithmetic.
+template <typename real>
+__global__ void __launch_bounds__(BP_TX *BP_TY) k_backproject_fan(const real *__restrict__ b, real *__restrict__ u,
+                                                                  const FanRay<real> *__restrict__ rays,
+                                                                  const FanView *__restrict__ views,
+                                                                  const int *__restrict__ aoff, int nx, int ny, int nb,
+                                                                  float h, float scale) {
+    const int t = blockIdx.z;
+    const int x = blockIdx.x * BP_TX + threadIdx.x, y = blockIdx.y * BP_TY + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    const float toff = 0.5f * (float)(nb - 1);
+    real acc = 0;
+    for (int a = aoff[t]; a < aoff[t + 1]; ++a) {
+        const FanView V = views[a];
+        const float qx = fmaf((float)x, h, V.qx0), qy = fmaf((float)y, h, V.qy0);
+        const float num = qx * V.fx + qy * V.fy, den = qx * V.ex + qy * V.ey;
+        const float nxp = h * V.fx, dxp = h * V.ex, nyp = h * V.fy, dyp = h * V.ey;
+        const float t0 = (num + nxp) / (den + dxp), t1 = (num - nxp) / (den - dxp);
+        const float t2 = (num + nyp) / (den + dyp), t3 = (num - nyp) / (den - dyp);
+        const float tlo = fminf(fminf(t0, t1), fminf(t2, t3)), thi = fmaxf(fmaxf(t0, t1), fmaxf(t2, t3));
+        // clamped in floating point before the conversion (a non-finite bound gives no bins)
+        const int klo = (int)fminf(fmaxf(floorf(fmaf(tlo, scale, toff)) - 1.0f, 0.0f), (float)nb);
+        const int khi = (int)fminf(fmaxf(ceilf(fmaf(thi, scale, toff)) + 1.0f, -1.0f), (float)(nb - 1));
+        const FanRay<real> *ra = rays + (long long)a * nb;
+        const real *row = b + (long long)a * nb;
+        for (int k = klo; k <= khi; ++k) {
+            const FanRay<real> R = ra[k];
+            const int j = R.rows ? y : x, fast = R.rows ? x : y;
+            if (j < R.jlo || j > R.jhi) continue;
+            int i0;
+            real w1;
+            if constexpr (sizeof(real) == 4) {
+                affine_frac(R.ib, R.fb, R.df_hi, R.df_lo, j, i0, w1);
+            } else {
+                const double f = fma((double)j, R.df, R.f0), fl = floor(f);
+                i0 = (int)fl;
+                w1 = f - fl;
+            }
+            const real w = i0 == fast ? (real)1 - w1 : (i0 + 1 == fast ? w1 : (real)0);
+            if (w != (real)0) acc = fma(w * R.wstep, ldg(row + k), acc);
+        }
+    }
+    u[(long long)t * nx * ny + (long long)y * nx + x] = acc;
+}
+
 template <typename real>
 mof_status launch_backproject(const mof_problem *p, const real *b, real *u, cudaStream_t st) {
     dim3 grid((p->nx + BP_TX - 1) / BP_TX, (p->ny + BP_TY - 1) / BP_TY, p->nt);
+    if (p->fan) {
+        ::mof::count_launch(), k_backproject_fan<real><<<grid, dim3(BP_TX, BP_TY), 0, st>>>(
+            b, u, static_cast<const FanRay<real> *>(p->d_fanray), p->d_fanview, p->d_aoff, p->nx, p->ny, p->nb,
+            (float)p->h, p->fan_scale);
+        MOF_LAUNCH_CHECK();
+        return MOF_OK;
+    }
     ::mof::count_launch(), k_backproject<real><<<grid, dim3(BP_TX, BP_TY), 0, st>>>(b, u, p->d_ang, p->d_aoff, p->nx, p->ny, p->nb);
     MOF_LAUNCH_CHECK();
     return MOF_OK;

@@ -97,6 +97,59 @@ def test_projector_adjoint_identity_fp32():
     assert abs(lhs - rhs) <= 1e-5 * np.linalg.norm(host(hb)) * np.linalg.norm(host(b))
 
 
+# ------------------------------------------------------------ fan beam
+# (nx, ny, nt, na, nb, db, rs, rd): ragged tiles with a wide fan and a detector through
+# the centre, the 64x64x8 fan workload, full-size frames of the 256x256x32 fan workload
+FAN = [(37, 29, 3, 7, 61, 1.1, 30.0, 0.0), (64, 64, 8, 16, 100, 1.5, 128.0, 64.0),
+       (256, 256, 2, 30, 363, 1.6, 512.0, 256.0)]
+
+
+def make_fan(case, prec, seed=0):
+    nx, ny, nt, na, nb, db, rs, rd = case
+    na_arr, ang = synth.shifted_angles(nt, na)
+    ang = ang + np.deg2rad(7.0) * seed
+    p = api.mof_problem_create(nx, ny, nt, nb, na_arr, ang, 1.0, db, prec, fan=(rs, rd))
+    g = O.Geometry(nx, ny, nt, nb, na_arr, ang, 1.0, db, fan=(rs, rd))
+    return p, g
+
+
+@pytest.mark.parametrize("prec", [api.MOF_FP32, api.MOF_FP64])
+@pytest.mark.parametrize("case", FAN)
+def test_fan_project_and_backproject(case, prec):
+    """Fan-beam H and H^T (flat detector, Sec. 5.1) against the oracle's rays through the
+    source; the views include fans that straddle 45 degrees."""
+    p, g = make_fan(case, prec)
+    nx, ny, nt = case[:3]
+    u = synth.random_images(nt, ny, nx, seed=31)
+    b = np.random.default_rng(32).standard_normal(g.m)
+    ud, bd = dev(u, prec), dev(b, prec)
+    out_b, out_u = empty(p.m, prec), empty(p.n, prec)
+    api.mof_apply_A(p, ud, out_b)
+    api.mof_apply_AT(p, bd, out_u)
+    assert rel(host(out_b), O.project(g, host(ud))) <= TOL[prec]
+    assert rel(host(out_u), O.backproject(g, host(bd))) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec,tol", [(api.MOF_FP32, 1e-5), (api.MOF_FP64, 1e-13)])
+def test_fan_projector_adjoint_identity(prec, tol):
+    p, g = make_fan(FAN[2], prec, seed=1)
+    nx, ny, nt = FAN[2][:3]
+    u = dev(synth.random_images(nt, ny, nx, seed=33), prec)
+    b = dev(np.random.default_rng(34).standard_normal(g.m), prec)
+    hb, hu = empty(p.m, prec), empty(p.n, prec)
+    api.mof_apply_A(p, u, hb)
+    api.mof_apply_AT(p, b, hu)
+    lhs, rhs = np.dot(host(hb), host(b)), np.dot(host(u), host(hu))
+    assert abs(lhs - rhs) <= tol * np.linalg.norm(host(hb)) * np.linalg.norm(host(b))
+
+
+def test_fan_rejects_a_source_inside_the_field():
+    na_arr, ang = synth.shifted_angles(2, 4)
+    for rs, rd in ((20.0, 5.0), (60.0, -1.0), (float("inf"), 1.0)):
+        with pytest.raises(api.MofError):
+            api.mof_problem_create(32, 32, 2, 64, na_arr, ang, 1.0, 1.0, api.MOF_FP32, fan=(rs, rd))
+
+
 @pytest.mark.parametrize("prec", [api.MOF_FP32, api.MOF_FP64])
 @pytest.mark.parametrize("shape", SHAPES)
 def test_grad_and_transpose(shape, prec):

@@ -329,6 +329,26 @@ def test_mmgks_of_fp64_round_warp_matches_oracle():
     assert rel(u, base) > 1e-4
 
 
+def test_mmgks_of_fp64_fan_beam_matches_oracle():
+    """MMGKS-OF on fan-beam data (flat detector, Sec. 5.1: source 128 px, detector 64 px
+    beyond the centre, 100 bins) of the 64x64x8 two-disk workload, 5 outer iterations."""
+    w = synth.fan_form_small(0)
+    g = O.Geometry(w.nx, w.ny, w.nt, w.nb, w.na, w.angles, w.h, w.db, fan=w.fan)
+    ores = OS.mmgks_of(g, w.b, OS.Params(noise_norm=w.noise_norm), 5)
+    p = api.mof_problem_create(w.nx, w.ny, w.nt, w.nb, w.na, w.angles, w.h, w.db, api.MOF_FP64, fan=w.fan)
+    prm = api.mof_default_params(noise_norm=w.noise_norm)
+    b = torch.tensor(w.b, device="cuda")
+    u = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    s = torch.empty(p.nv, dtype=torch.float64, device="cuda")
+    rep = api.mof_solve(p, prm, 5, b, u, s)
+    u, s = u.cpu().numpy(), s.cpu().numpy()
+    assert rel(u, ores.u) <= 1e-6, rel(u, ores.u)
+    assert rel(s, ores.s) <= 1e-5, rel(s, ores.s)
+    for r, o in zip(rep, ores.report):
+        assert r["flag"] == o["flag"] and r["basis"] == o["basis"]
+    assert rel(u, w.u_true.ravel()) < 0.5
+
+
 def test_mmgks_of_fp32_d1_of_precision_form_small():
     w = synth.precision_form_small(0)
     ores = _oracle_solve(w, 4, of_iters=10, temporal_tv=1)
