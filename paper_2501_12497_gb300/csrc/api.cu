@@ -120,16 +120,17 @@ static void fan_ray(double theta, double gamma, double poff, int nx, int ny, dou
     } else if (!(f0 > -1.0 && f0 < (double)nfast)) {
         jhi = -1;
     }
-    R.rows = rows;
-    R.jlo = jlo;
-    R.jhi = jhi;
     if constexpr (sizeof(real) == 4) {
+        (void)jlo;
+        (void)jhi;
         const double fl = std::floor(f0);
-        R.ib = (int)std::fmax(std::fmin(fl, 1e9), -1e9);
+        R.ibr = 2 * (int)std::fmax(std::fmin(fl, 5e8), -5e8) + rows;
         R.fb = (float)(f0 - fl);
         split12(df, R.df_hi, R.df_lo);
-        R.wstep = (float)(h / std::fabs(cc));
     } else {
+        R.rows = rows;
+        R.jlo = jlo;
+        R.jhi = jhi;
         R.f0 = f0;
         R.df = df;
         R.wstep = h / std::fabs(cc);

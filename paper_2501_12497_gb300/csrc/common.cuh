@@ -74,15 +74,14 @@ struct AngleParams {
 // Fan beam (flat detector): one Joseph march per ray (view a, bin k), stored per
 // ray because the rays of one view are not parallel. The crossing of step j is
 // f(j) = f0 + j df along the fast axis (x when rows = 1, else y), each step
-// weighted wstep = h / max(|cos|, |sin|) of the ray; steps jlo..jhi are the
-// ones whose crossing can touch the frame (both kernels use the same range).
+// weighted h / max(|cos|, |sin|) = h sqrt(1 + df^2) for the ray. Steps whose
+// crossing lies beyond (-1, nfast) by a margin touch no pixel, so the forward
+// march may skip them and the transpose needs no step range.
 template <typename real> struct FanRay;
-template <> struct FanRay<float> {
-    int ib;              // floor(f0)
+template <> struct __align__(16) FanRay<float> {
+    int ibr;             // 2 floor(f0) + rows
     float fb;            // f0 - floor(f0)
     float df_hi, df_lo;  // df split, df_hi with 12 significant bits
-    float wstep;
-    int rows, jlo, jhi;
 };
 template <> struct FanRay<double> {
     double f0, df, wstep;

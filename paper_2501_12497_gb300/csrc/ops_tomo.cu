@@ -116,35 +116,58 @@ __global__ void __launch_bounds__(128) k_project(const real *__restrict__ u, con
 
 // ---------------------------------------------------------- K1 fan beam
 // One thread per ray (view a = blockIdx.y, bin k); the march of the parallel
-// kernel with the ray's own start, step and range from the ray table.
+// kernel with the ray's own start and step from the ray table.
 template <typename real>
 __global__ void __launch_bounds__(128) k_project_fan(const real *__restrict__ u, const real *__restrict__ uT,
                                                      real *__restrict__ b, const FanRay<real> *__restrict__ rays,
-                                                     const AngleParams *__restrict__ ang, int nx, int ny, int nb) {
+                                                     const AngleParams *__restrict__ ang, int nx, int ny, int nb, real h) {
     const int a = blockIdx.y;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nb) return;
     const long long ns = (long long)nx * ny;
     const FanRay<real> R = rays[(long long)a * nb + k];
     const int frame = ang[a].frame;
-    const real *img = R.rows ? u + frame * ns : uT + frame * ns;
-    const int nfast = R.rows ? nx : ny;
-    real acc = 0;
-    for (int j = R.jlo; j <= R.jhi; ++j) {
-        int i0;
-        real w1;
-        if constexpr (sizeof(real) == 4) {
-            affine_frac(R.ib, R.fb, R.df_hi, R.df_lo, j, i0, w1);
-        } else {
-            const double f = fma((double)j, R.df, R.f0), fl = floor(f);
-            i0 = (int)fl;
-            w1 = f - fl;
+    real acc = 0, wstep;
+    if constexpr (sizeof(real) == 4) {
+        const int rows = R.ibr & 1, ib = R.ibr >> 1;
+        const float *img = rows ? u + frame * ns : uT + frame * ns;
+        const int nfast = rows ? nx : ny, nstep = rows ? ny : nx;
+        const float df = R.df_hi + R.df_lo;
+        wstep = h * sqrtf(fmaf(df, df, 1.0f));
+        // steps whose crossing can lie in (-1, nfast), two steps of margin each side
+        int jlo = 0, jhi = nstep - 1;
+        const float f0 = (float)ib + R.fb;
+        if (df != 0.0f) {
+            const float ja = (-1.0f - f0) / df, jb = ((float)nfast - f0) / df;
+            const float lo = fmaxf(fminf(ja, jb), -1.0f), hi = fminf(fmaxf(ja, jb), (float)nstep);
+            jlo = max(0, (int)floorf(lo) - 2);
+            jhi = min(nstep - 1, (int)ceilf(hi) + 2);
+        } else if (!(f0 > -1.0f && f0 < (float)nfast)) {
+            jhi = -1;
         }
-        const real *row = img + (long long)j * nfast;
-        if (i0 >= 0 && i0 < nfast) acc = fma((real)1 - w1, ldg(row + i0), acc);
-        if (i0 + 1 >= 0 && i0 + 1 < nfast) acc = fma(w1, ldg(row + i0 + 1), acc);
+#pragma unroll 4
+        for (int j = jlo; j <= jhi; ++j) {
+            int i0;
+            float w1;
+            affine_frac(ib, R.fb, R.df_hi, R.df_lo, j, i0, w1);
+            const float *row = img + (long long)j * nfast;
+            if (i0 >= 0 && i0 < nfast) acc = fmaf(1.0f - w1, ldg(row + i0), acc);
+            if (i0 + 1 >= 0 && i0 + 1 < nfast) acc = fmaf(w1, ldg(row + i0 + 1), acc);
+        }
+    } else {
+        const double *img = R.rows ? u + frame * ns : uT + frame * ns;
+        const int nfast = R.rows ? nx : ny;
+        wstep = R.wstep;
+        for (int j = R.jlo; j <= R.jhi; ++j) {
+            const double f = fma((double)j, R.df, R.f0), fl = floor(f);
+            const int i0 = (int)fl;
+            const double w1 = f - fl;
+            const double *row = img + (long long)j * nfast;
+            if (i0 >= 0 && i0 < nfast) acc = fma(1.0 - w1, ldg(row + i0), acc);
+            if (i0 + 1 >= 0 && i0 + 1 < nfast) acc = fma(w1, ldg(row + i0 + 1), acc);
+        }
     }
-    b[(long long)a * nb + k] = acc * R.wstep;
+    b[(long long)a * nb + k] = acc * wstep;
 }
 
 template <typename real>
@@ -155,7 +178,7 @@ mof_status launch_project(const mof_problem *p, const real *u, real *uT, real *b
     if (p->fan) {
         dim3 grid((p->nb + 127) / 128, p->A);
         ::mof::count_launch(), k_project_fan<real><<<grid, 128, 0, st>>>(u, uT, b, static_cast<const FanRay<real> *>(p->d_fanray),
-                                                                        p->d_ang, p->nx, p->ny, p->nb);
+                                                                        p->d_ang, p->nx, p->ny, p->nb, (real)p->h);
         MOF_LAUNCH_CHECK();
         return MOF_OK;
     }
@@ -260,9 +283,13 @@ __global__ void __launch_bounds__(BP_TX *BP_TY) k_backproject(const real *__rest
 // there is less than one pixel away; so the rays that reach the pixel are
 // those crossing the open segments of half-length h through its centre along
 // x and along y. Seen from the source, those segments cover the bins between
-// the central projections of their four end points (widened by one bin for
-// the FP32 evaluation); for each such bin the forward entry is re-evaluated
-// with the forward's own arithmetic.
+// the central projections of their four end points (widened by FAN_PAD bins
+// for the FP32 evaluation of the bounds); for each such bin the forward entry
+// is re-evaluated with the forward's own arithmetic. Steps the forward march
+// skips have crossings more than a pixel outside the frame, so they cannot
+// reach a pixel and need no test here.
+constexpr float FAN_PAD = 0.02f;
+
 template <typename real>
 __global__ void __launch_bounds__(BP_TX *BP_TY) k_backproject_fan(const real *__restrict__ b, real *__restrict__ u,
                                                                   const FanRay<real> *__restrict__ rays,
@@ -279,29 +306,35 @@ __global__ void __launch_bounds__(BP_TX *BP_TY) k_backproject_fan(const real *__
         const float qx = fmaf((float)x, h, V.qx0), qy = fmaf((float)y, h, V.qy0);
         const float num = qx * V.fx + qy * V.fy, den = qx * V.ex + qy * V.ey;
         const float nxp = h * V.fx, dxp = h * V.ex, nyp = h * V.fy, dyp = h * V.ey;
-        const float t0 = (num + nxp) / (den + dxp), t1 = (num - nxp) / (den - dxp);
-        const float t2 = (num + nyp) / (den + dyp), t3 = (num - nyp) / (den - dyp);
+        const float t0 = __fdividef(num + nxp, den + dxp), t1 = __fdividef(num - nxp, den - dxp);
+        const float t2 = __fdividef(num + nyp, den + dyp), t3 = __fdividef(num - nyp, den - dyp);
         const float tlo = fminf(fminf(t0, t1), fminf(t2, t3)), thi = fmaxf(fmaxf(t0, t1), fmaxf(t2, t3));
         // clamped in floating point before the conversion (a non-finite bound gives no bins)
-        const int klo = (int)fminf(fmaxf(floorf(fmaf(tlo, scale, toff)) - 1.0f, 0.0f), (float)nb);
-        const int khi = (int)fminf(fmaxf(ceilf(fmaf(thi, scale, toff)) + 1.0f, -1.0f), (float)(nb - 1));
+        const int klo = (int)fminf(fmaxf(ceilf(fmaf(tlo, scale, toff - FAN_PAD)), 0.0f), (float)nb);
+        const int khi = (int)fminf(fmaxf(floorf(fmaf(thi, scale, toff + FAN_PAD)), -1.0f), (float)(nb - 1));
         const FanRay<real> *ra = rays + (long long)a * nb;
         const real *row = b + (long long)a * nb;
         for (int k = klo; k <= khi; ++k) {
             const FanRay<real> R = ra[k];
-            const int j = R.rows ? y : x, fast = R.rows ? x : y;
-            if (j < R.jlo || j > R.jhi) continue;
-            int i0;
-            real w1;
+            int i0, fast;
+            real w1, wstep;
             if constexpr (sizeof(real) == 4) {
-                affine_frac(R.ib, R.fb, R.df_hi, R.df_lo, j, i0, w1);
+                const int rows = R.ibr & 1;
+                const int j = rows ? y : x;
+                fast = rows ? x : y;
+                affine_frac(R.ibr >> 1, R.fb, R.df_hi, R.df_lo, j, i0, w1);
+                const float df = R.df_hi + R.df_lo;
+                wstep = h * sqrtf(fmaf(df, df, 1.0f));
             } else {
+                const int j = R.rows ? y : x;
+                fast = R.rows ? x : y;
                 const double f = fma((double)j, R.df, R.f0), fl = floor(f);
                 i0 = (int)fl;
                 w1 = f - fl;
+                wstep = R.wstep;
             }
             const real w = i0 == fast ? (real)1 - w1 : (i0 + 1 == fast ? w1 : (real)0);
-            if (w != (real)0) acc = fma(w * R.wstep, ldg(row + k), acc);
+            if (w != (real)0) acc = fma(w * wstep, ldg(row + k), acc);
         }
     }
     u[(long long)t * nx * ny + (long long)y * nx + x] = acc;
