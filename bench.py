@@ -495,9 +495,15 @@ def run_operators(args):
     vel2 = torch.empty(p.nv, device=dev)
     vg = torch.empty(2 * p.nv, device=dev)
     r2 = torch.randn(2 * P * ns, device=dev)
+    wf = synth.fan_form(0)
+    pf = api.mof_problem_create(wf.nx, wf.ny, wf.nt, wf.nb, wf.na, wf.angles, wf.h, wf.db, precision=api.MOF_FP32,
+                                fan=wf.fan)
+    bf = f32(wf.b)
     ops = [
         ("H (k_project)", 4 * (n + m), lambda: api.mof_apply_A(p, u, sino)),
         ("H^T (k_backproject)", 4 * (n + m), lambda: api.mof_apply_AT(p, b, img)),
+        ("fan H (k_project_fan)", 4 * (n + m) + 16 * m, lambda: api.mof_apply_A(pf, u, sino)),
+        ("fan H^T (k_backproject_fan)", 4 * (n + m) + 16 * m, lambda: api.mof_apply_AT(pf, bf, img)),
         ("Psi (k_grad)", 12 * n, lambda: api.mof_apply_grad(p, u, grad)),
         ("Psi^T (k_gradT)", 12 * n, lambda: api.mof_apply_gradT(p, grad, img)),
         ("Mhat (k_flow)", 4 * n + 24 * P * ns, lambda: api.mof_apply_flow(p, u, s, sr, flow)),
