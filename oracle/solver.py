@@ -17,12 +17,14 @@ least squares) as single steps:
 * Residual of the normal equations (eq. after (minKryov2)), reorthogonalised
   against V twice, normalised and appended (eq. (enlargeMM-GKS)).
 * Solve-OF (Alg. 2) with p = q = 2: the same machinery with constant weights,
-  A = Upsilon(u(t)), b = -u_t, L = blockdiag(L, L), lam = gamma by GCV.
+  A = Upsilon(u(t)), b = -u_t, L = blockdiag(L, L), lam = gamma by GCV; with
+  p = q = 1 (the stand-alone optical-flow choice the paper mentions in Sec.
+  4.1.2) the MM-GKS of App. A with IRLS weights on both terms.
 * MMGKS-OF (Alg. 1): Solve-OF on every pair, reverse flow by the remark of
   Sec. 3, Theta = [Psi; Mhat], IRLS weights w = (nu^2 + eps^2)^(-1/2)
   (P = w^(1/2)), one MMGKS step.
 
-Readings of ambiguous passages (all listed in the design doc): GCV denominator is
+Readings of ambiguous passages: GCV denominator is
 the squared trace of the projected (I - influence) matrix; DP/GCV search
 bracket [1e-12, 1e12] * ||R_A||_F^2 / ||R_L||_F^2 in log10; DP by 100
 bisection steps; GCV by a 200-point log grid refined by 60 golden-section
@@ -64,6 +66,7 @@ class Params:
     image_rule: str = RULE_DP
     lam_fixed: float = 0.0    # used when image_rule == "fixed"
     breakdown_tol: float = 1e-10
+    of_pq: int = 2            # Solve-OF norms: 2 (p = q = 2, Sec. 5) or 1 (p = q = 1 by MM-GKS, App. A)
 
 
 # ------------------------------------------------------------------ helpers
@@ -282,8 +285,52 @@ def gks(A, AT, Lop, LTop, b, ell, iters, tol=1e-10):
     return x, info
 
 
+def mm_gks(A, AT, Lop, LTop, b, ell, iters, eps, tol=1e-10, lam_fixed=None):
+    """MM-GKS (App. A) for min ||A x - b||_1 + lam ||L x||_1, both norms smoothed to
+    sum_i sqrt(t_i^2 + eps^2): at iteration k the weights w = ((.)^2 + eps^2)^(-1/2) of the
+    fidelity residual A x^(k) - b and of L x^(k) (x^(0) = 0) define the quadratic majorant
+    ||W_f^(1/2) (A x - b)||^2 + lam ||W_L^(1/2) L x||^2, minimised over range(V) with lam by
+    GCV (or lam_fixed); the majorant's normal-equation residual at the new x,
+    A^T W_f (A x - b) + lam L^T W_L L x, is orthogonalised, normalised and appended.
+    The weights rescale that residual from one iteration to the next, so the growth of
+    the subspace ends when the orthogonalised residual is at most tol times its norm
+    before the orthogonalisation (the direction is already in range(V)).
+
+    Returns (x, info) like gks."""
+    V, _, _ = gkb(A, AT, b, ell, tol)
+    info = {"gamma": [], "k": V.shape[1], "V": V}
+    if V.shape[1] == 0:
+        return np.zeros(AT(b).size), info
+    AV = np.column_stack([A(V[:, j]) for j in range(V.shape[1])])
+    LV = np.column_stack([Lop(V[:, j]) for j in range(V.shape[1])])
+    x = np.zeros(V.shape[0])
+    grow = True
+    for k in range(iters):
+        wf = 1.0 / np.sqrt((A(x) - b) ** 2 + eps * eps)
+        wl = 1.0 / np.sqrt(Lop(x) ** 2 + eps * eps)
+        sf, sl = np.sqrt(wf), np.sqrt(wl)
+        pp = ProjectedProblem(sf[:, None] * AV, sl[:, None] * LV, sf * b)
+        lam = lam_fixed if lam_fixed is not None else choose_lambda_gcv(pp)[0]
+        z = pp.solve(lam)
+        x = V @ z
+        info["gamma"].append(lam)
+        if k == iters - 1 or not grow:
+            continue
+        r = AT(wf * (AV @ z - b)) + lam * LTop(wl * (LV @ z))
+        Vn, _ = expand(V, r, np.linalg.norm(r), tol)
+        if Vn is None:
+            grow = False
+            continue
+        V = Vn
+        AV = np.column_stack([AV, A(V[:, -1])])
+        LV = np.column_stack([LV, Lop(V[:, -1])])
+    info["k"], info["V"] = V.shape[1], V
+    return x, info
+
+
 def solve_of_pair(ux, uy, ut, prm: Params):
-    """Alg. 2 for one pair: min ||Upsilon s + u_t||^2 + gamma ||(L (+) L) s||^2 (p = q = 2).
+    """Alg. 2 for one pair: min ||Upsilon s + u_t||_p^p + gamma ||(L (+) L) s||_q^q with
+    p = q = 2 (GKS) or, when prm.of_pq == 1, p = q = 1 (MM-GKS).
 
     ux, uy, ut: (ny, nx) fields of App. C. Returns (s (2, ny, nx), info).
     """
@@ -306,7 +353,10 @@ def solve_of_pair(ux, uy, ut, prm: Params):
     def LTop(g):
         return ops.vgradT(g.reshape(1, 2, 2, ny, nx)).ravel()
 
-    s, info = gks(A, AT, Lop, LTop, b, prm.of_ell, prm.of_iters, prm.breakdown_tol)
+    if prm.of_pq == 1:
+        s, info = mm_gks(A, AT, Lop, LTop, b, prm.of_ell, prm.of_iters, prm.eps, prm.breakdown_tol)
+    else:
+        s, info = gks(A, AT, Lop, LTop, b, prm.of_ell, prm.of_iters, prm.breakdown_tol)
     return s.reshape(2, ny, nx), info
 
 

@@ -184,6 +184,84 @@ def test_solve_of_zero_time_derivative_gives_zero_velocity():
     assert np.all(s == 0) and info["k"] == 0
 
 
+# ------------------------------------------------ MM-GKS, p = q = 1 (App. A)
+def _l1_problem(seed=5, m=30, n=18):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((m, n)) @ np.diag(np.logspace(0, -1.5, n))
+    L = np.diff(np.eye(n), axis=0)
+    x0 = np.cumsum(rng.standard_normal(n) * (rng.uniform(size=n) < 0.3))
+    b = A @ x0 + 0.05 * rng.standard_normal(m) + 0.8 * (rng.uniform(size=m) < 0.1)
+    return A, L, b
+
+
+def _smoothed_l1(A, L, b, lam, eps, x):
+    return np.sum(np.sqrt((A @ x - b) ** 2 + eps * eps)) + lam * np.sum(np.sqrt((L @ x) ** 2 + eps * eps))
+
+
+def test_mm_gks_with_a_huge_eps_is_gks():
+    """With eps far above every residual the IRLS weights are one constant for both terms,
+    so the majorant is the p = q = 2 problem scaled and MM-GKS reproduces GKS (same GCV lam)."""
+    rng = np.random.default_rng(1)
+    n = 12
+    A = rng.standard_normal((18, n)) @ np.diag(np.logspace(0, -2, n))
+    L = np.diff(np.eye(n), axis=0)
+    b = A @ (0.3 * np.cumsum(rng.standard_normal(n))) + 0.05 * rng.standard_normal(18)
+    ops_ = (lambda v: A @ v, lambda y: A.T @ y, lambda v: L @ v, lambda g: L.T @ g)
+    x2, i2 = solver.gks(*ops_, b, 3, 9)
+    x1, i1 = solver.mm_gks(*ops_, b, 3, 9, eps=1e9)
+    assert 1e-4 < i2["gamma"][-1] < 1.0  # interior GCV minimum at the end
+    # (the first GCV functions are flat near their minima: lam to 1e-4)
+    np.testing.assert_allclose(i1["gamma"], i2["gamma"], rtol=1e-4)
+    assert i1["k"] == i2["k"]
+    np.testing.assert_allclose(x1, x2, rtol=1e-6, atol=1e-8 * np.linalg.norm(x2))
+
+
+def test_mm_gks_fixed_lambda_decreases_the_smoothed_l1_objective():
+    """MM: each iterate minimises a quadratic majorant of the smoothed l1 objective over a
+    subspace that holds the previous iterate, so the objective never increases."""
+    A, L, b = _l1_problem()
+    lam, eps = 0.7, 0.05
+    vals = []
+    for it in range(1, 25):
+        x, _ = solver.mm_gks(lambda v: A @ v, lambda y: A.T @ y, lambda v: L @ v, lambda g: L.T @ g, b, 3, it,
+                             eps=eps, lam_fixed=lam)
+        vals.append(_smoothed_l1(A, L, b, lam, eps, x))
+    assert all(vals[i + 1] <= vals[i] * (1 + 1e-12) for i in range(len(vals) - 1)), vals
+    assert vals[-1] < 0.9 * vals[0]
+
+
+def test_mm_gks_reaches_the_smoothed_l1_minimiser():
+    """Once the subspace is the whole space the iteration is IRLS, whose limit is the
+    minimiser of the smoothed l1 objective; scipy's BFGS on the same objective agrees."""
+    from scipy.optimize import minimize
+    A, L, b = _l1_problem()
+    lam, eps = 0.7, 0.05
+    x, info = solver.mm_gks(lambda v: A @ v, lambda y: A.T @ y, lambda v: L @ v, lambda g: L.T @ g, b, 3, 400,
+                            eps=eps, lam_fixed=lam)
+    assert info["k"] == A.shape[1]
+
+    def grad(v):
+        rf, rl = A @ v - b, L @ v
+        return A.T @ (rf / np.sqrt(rf * rf + eps * eps)) + lam * L.T @ (rl / np.sqrt(rl * rl + eps * eps))
+
+    ref = minimize(lambda v: _smoothed_l1(A, L, b, lam, eps, v), np.zeros(A.shape[1]), jac=grad, method="BFGS",
+                   options={"gtol": 1e-12, "maxiter": 10000})
+    assert np.linalg.norm(grad(x)) < 1e-7
+    np.testing.assert_allclose(x, ref.x, atol=1e-6 * np.linalg.norm(ref.x))
+
+
+def test_solve_of_pq1_runs_mm_gks_on_the_flow_problem():
+    """Solve-OF with p = q = 1: the MM-GKS iterate of the pair problem; with a huge eps it
+    equals the p = q = 2 Solve-OF."""
+    w = synth.moving_disks(16, 2, 8, 16, radii=(3.0, 5.0), seed=4)
+    ux, uy, ut = ops.of_fields(w.u_true, 1)
+    s2, _ = solver.solve_of_pair(ux[0], uy[0], ut[0], solver.Params(of_ell=6, of_iters=8))
+    s1, i1 = solver.solve_of_pair(ux[0], uy[0], ut[0], solver.Params(of_ell=6, of_iters=8, of_pq=1, eps=1e9))
+    np.testing.assert_allclose(s1, s2, rtol=1e-5, atol=1e-7 * np.abs(s2).max())
+    s1, i1 = solver.solve_of_pair(ux[0], uy[0], ut[0], solver.Params(of_ell=6, of_iters=8, of_pq=1))
+    assert i1["k"] == 13 and np.linalg.norm(s1 - s2) > 1e-3 * np.linalg.norm(s2)
+
+
 def _tiny_problem(seed=0, nx=4, ny=4, nt=2, na=6, nb=8):
     rng = np.random.default_rng(seed)
     na_arr, ang = synth.shifted_angles(nt, na)
