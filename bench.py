@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--geometry", default="parallel", choices=["parallel", "fan"],
                     help="fan: the same workload in a flat fan beam (source 512 px, detector 256 px beyond "
                          "the centre, 363 bins of 1.6 px)")
+    ap.add_argument("--of-pq", type=int, default=2, choices=[1, 2],
+                    help="norms of Solve-OF: 2 (p = q = 2, the paper's experiments) or 1 (p = q = 1 by MM-GKS)")
     ap.add_argument("--warp", default="bilinear", choices=["bilinear", "round"],
                     help="encoding of the warp M(s) (Sec. 3): bilinear interpolation or rounding and clipping")
     return ap.parse_args()
@@ -223,7 +225,7 @@ def run_ours(args):
     p = api.mof_problem_create(w.nx, w.ny, w.nt, w.nb, w.na, w.angles, w.h, w.db, precision=api.MOF_FP32, fan=w.fan)
     api.mof_set_warp(p, 1 if args.warp == "round" else 0)
     prm = api.mof_default_params(noise_norm=w.noise_norm, of_streams=args.of_streams, of_scale=args.of_scale,
-                                 tau=args.tau, temporal_tv=args.temporal_tv)
+                                 tau=args.tau, temporal_tv=args.temporal_tv, of_pq=args.of_pq)
     stream = torch.cuda.current_stream(dev)
     b = torch.tensor(w.b.astype(np.float32), device=dev)
     u = torch.empty(p.n, dtype=torch.float32, device=dev)
@@ -260,7 +262,7 @@ def run_ours(args):
     class_ms = {}
     if not args.no_class_step:
         prm1 = api.mof_default_params(noise_norm=w.noise_norm, of_streams=1, of_scale=args.of_scale, tau=args.tau,
-                                      temporal_tv=args.temporal_tv)
+                                      temporal_tv=args.temporal_tv, of_pq=args.of_pq)
         api.mof_solve(p, prm1, N_OUTER, b, u, s)
         flush.fill_(1.0)
         torch.cuda.synchronize()
@@ -346,6 +348,7 @@ def run_ours(args):
                    "l2": "flushed between steps (512 MB write)", "rre": rre,
                    "of_streams": args.of_streams or "auto", "of_scale": args.of_scale, "tau": args.tau,
                    "regulariser": "D1-OF" if args.temporal_tv else "M-OF", "warp": args.warp,
+                   "of_pq": args.of_pq,
                    "time_to_tolerance_s": total_ms / args.steps / 1e3},
         "e2e": {"value": e2e_value, "unit": "outer_iters/s", "h2d_bytes_per_step": 4 * p.m,
                 "d2h_bytes_per_step": 4 * p.n + 64 * N_OUTER},
@@ -428,7 +431,7 @@ def run_large(args):
     p = api.mof_problem_create(w.nx, w.ny, w.nt, w.nb, w.na, w.angles, precision=api.MOF_FP32)
     api.mof_set_warp(p, 1 if args.warp == "round" else 0)
     prm = api.mof_default_params(noise_norm=w.noise_norm, of_streams=args.of_streams, of_scale=args.of_scale,
-                                 tau=args.tau, temporal_tv=args.temporal_tv)
+                                 tau=args.tau, temporal_tv=args.temporal_tv, of_pq=args.of_pq)
     b = torch.tensor(w.b.astype(np.float32), device="cuda")
     u = torch.empty(p.n, dtype=torch.float32, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -559,7 +562,7 @@ def run_solve_of(args):
     api.load()
     w = synth.precision_form(0)
     p = api.mof_problem_create(w.nx, w.ny, w.nt, w.nb, w.na, w.angles, precision=api.MOF_FP32)
-    prm = api.mof_default_params(of_streams=args.of_streams, of_scale=args.of_scale)
+    prm = api.mof_default_params(of_streams=args.of_streams, of_scale=args.of_scale, of_pq=args.of_pq)
     u = torch.tensor(w.u_true.astype(np.float32), device="cuda").reshape(-1)
     s = torch.empty(p.nv, dtype=torch.float32, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -581,6 +584,7 @@ def run_solve_of(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps, "higher_is_better": True,
             "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": "solve_of ellipses256x256x32", "pairs": p.nt - 1, "of_ell": 10, "of_iters": 20,
+                       "of_pq": args.of_pq,
                        "of_streams": args.of_streams or "auto", "of_scale": args.of_scale, "l2": "flushed before each call"},
             "gpu_launches": api.mof_kernel_launches() - l0}
     print(json.dumps(line), flush=True)

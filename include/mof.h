@@ -95,6 +95,12 @@ typedef struct {
     int temporal_tv;       /* 1: D1-OF (AnisoTV-OF, Table 2): Theta = [Psi; L_t; Mhat] with L_t the
                               forward differences between consecutive frames, all rows in the
                               same l1 norm; 0 (default): M-OF, Theta = [Psi; Mhat] */
+    int of_pq;             /* norms of Solve-OF (Sec. 4.1.2): 2 (default, the paper's experiments)
+                              p = q = 2 by GKS; 1: p = q = 1 by MM-GKS (App. A) with IRLS weights
+                              ((.)^2 + eps^2)^(-1/2) on the flow residual and on (L+L) s, recomputed
+                              from the current velocity (zero at the start) every iteration; the
+                              subspace stops growing when the orthogonalised residual is
+                              breakdown_tol times its own norm */
 } mof_solver_params;
 
 /* One record per outer iteration k of mof_solve (host struct). */

@@ -37,7 +37,7 @@ class mof_solver_params(ctypes.Structure):
                 ("of_ell", ctypes.c_int), ("of_dr", ctypes.c_int), ("image_rule", ctypes.c_int),
                 ("eps", ctypes.c_double), ("eta", ctypes.c_double), ("noise_norm", ctypes.c_double),
                 ("lam_fixed", ctypes.c_double), ("breakdown_tol", ctypes.c_double), ("of_streams", ctypes.c_int),
-                ("of_scale", ctypes.c_int), ("temporal_tv", ctypes.c_int)]
+                ("of_scale", ctypes.c_int), ("temporal_tv", ctypes.c_int), ("of_pq", ctypes.c_int)]
 
 
 class mof_report(ctypes.Structure):

@@ -188,6 +188,7 @@ void mof_default_params(mof_solver_params *p) {
     p->of_streams = 0;
     p->of_scale = 1;
     p->temporal_tv = 0;
+    p->of_pq = 2;
 }
 
 mof_status mof_problem_create(const mof_geometry *g, int precision, mof_problem **out) {

@@ -138,6 +138,9 @@ struct WS {
     double *GA, *GL, *gof, *zof, *gam, *nrm_of, *coef_of, *coefU_of, *scale_of, *alpha_of, *alpha1_of, *beta_of,
         *beta1_of, *bb_of;
     int *Kv_of, *Ku_of, *grow_of, *gkb_of, *act_of, *app_of, *flag_of;
+    real *wf_of = nullptr, *wl_of = nullptr;  // IRLS weights of Solve-OF with p = q = 1 (P ns, 4 P ns)
+    double *rn_of = nullptr;                  // norm^2 of its residual before orthogonalisation (P)
+    int pq1 = 0;                              // workspace holds the p = q = 1 arrays
     double *partial;
     double *kaux;  // Krylov append scratch, 2 per problem
     int *iter;  // device index of the outer iteration (report slot)
@@ -269,20 +272,47 @@ static size_t theta_gram_smem(int Kmax) {
     return tile > red ? tile : red;
 }
 
+// Sizes of the weighted Gram of Solve-OF with p = q = 1 (k_of_wgram): threads, pixels
+// per tile, CTAs per pair, quads of columns, 4x4 blocks, partial doubles per CTA.
+constexpr int WG_T = 256, WG_P = 64, WG_CTAS = 64;
+__host__ __device__ constexpr int wg_k4f(int K) { return (K + 4) / 4; }  // quads of K + 1 columns
+__host__ __device__ constexpr int wg_k4l(int K) { return (K + 3) / 4; }
+__host__ __device__ constexpr int wg_nblk(int K) {
+    return wg_k4f(K) * (wg_k4f(K) + 1) / 2 + wg_k4l(K) * (wg_k4l(K) + 1) / 2;
+}
+__host__ __device__ constexpr int wg_pstride(int Kmax) { return wg_nblk(Kmax) * 16; }
+// shared memory: the staged rows, later reused for the per-slot FP64 sums
+template <typename real>
+constexpr size_t wg_smem(int Kmax) {
+    const size_t rows = ((size_t)wg_k4f(Kmax) * (WG_P + 1) + (size_t)wg_k4l(Kmax) * (4 * WG_P + 1)) * 4 * sizeof(real);
+    const size_t nsl = (size_t)(wg_nblk(Kmax) > WG_T ? wg_nblk(Kmax) : WG_T);
+    const size_t slots = nsl * 16 * sizeof(double);
+    return rows > slots ? rows : slots;
+}
+
+template <typename real>
+__global__ void __launch_bounds__(WG_T) k_of_wgram(const real *__restrict__ V, int Kmax, const int *__restrict__ K,
+                                                   const int *__restrict__ act, const real *__restrict__ ux,
+                                                   const real *__restrict__ uy, const real *__restrict__ bof,
+                                                   const real *__restrict__ wf, const real *__restrict__ wl, int nx, int ny,
+                                                   double *__restrict__ partial);
+
 // doubles of Krylov scratch per frame pair of Solve-OF: the Krylov kernels' chunk
 // partials, and the per-CTA partials of the Gram columns (of_ell columns at once)
 static long long of_partial_per_pair(const mof_problem *p, int Kof, int of_ell) {
     const long long ns = p->ns;
     const long long gram_chunks = (ns + 511) / 512;  // chunks of the FP64 Gram kernel (the smaller)
     const long long gram = (long long)std::min(of_ell, Kof) * gram_chunks * (2LL * Kof + 1);
-    return std::max(krylov_partial_doubles(2 * ns, Kof), gram);
+    const long long wgram = (long long)WG_CTAS * wg_pstride(Kof);
+    return std::max(std::max(krylov_partial_doubles(2 * ns, Kof), gram), wgram);
 }
 
 template <typename real>
 static mof_status ensure_ws(mof_problem *p, const mof_solver_params &prm, int n_outer, WS<real> *&w) {
     const int Kmax = prm.ell + n_outer;
     const int Kof = prm.of_ell + prm.of_iters;
-    if (w && w->Kmax >= Kmax && w->Kof >= Kof && w->of_ell >= prm.of_ell && w->ell >= prm.ell && w->max_outer >= n_outer)
+    if (w && w->Kmax >= Kmax && w->Kof >= Kof && w->of_ell >= prm.of_ell && w->ell >= prm.ell && w->max_outer >= n_outer &&
+        (prm.of_pq != 1 || w->pq1))
         return MOF_OK;
     free_ws(w);
     w = new WS<real>();
@@ -291,6 +321,7 @@ static mof_status ensure_ws(mof_problem *p, const mof_solver_params &prm, int n_
     w->of_ell = prm.of_ell;
     w->ell = prm.ell;
     w->max_outer = n_outer;
+    w->pq1 = prm.of_pq == 1;
     const long long n = p->n, m = p->m, ns = p->ns, P = p->nt - 1, N2 = 2 * ns;
     int dev_sms = 152;
     cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, p->device);
@@ -379,6 +410,9 @@ static mof_status ensure_ws(mof_problem *p, const mof_solver_params &prm, int n_
         w->act_of = a.take<int>(P);
         w->app_of = a.take<int>(P);
         w->flag_of = a.take<int>(P);
+        w->wf_of = a.take<real>(w->pq1 ? P * ns : 0);
+        w->wl_of = a.take<real>(w->pq1 ? 4 * P * ns : 0);
+        w->rn_of = a.take<double>(w->pq1 ? P : 0);
         w->partial = a.take<double>((size_t)partial);
         w->kaux = a.take<double>(2 * (size_t)std::max<long long>(P, 1) + 8);
         w->iter = a.take<int>(1);
@@ -405,6 +439,8 @@ static mof_status ensure_ws(mof_problem *p, const mof_solver_params &prm, int n_
     }
     const size_t sm = theta_gram_smem<real>(Kmax);
     (void)sm;
+    if (w->pq1)
+        MOF_CUDA(cudaFuncSetAttribute(k_of_wgram<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wg_smem<real>(Kof)));
     return MOF_OK;
 }
 
@@ -734,6 +770,338 @@ __global__ void k_of_gram_reduce(const double *__restrict__ partial, int nctas, 
     G[b * KK + (long long)j * Kmax + i] = sum;
 }
 
+// four consecutive values from 16-byte aligned shared memory
+template <typename real>
+struct Quad {
+    real x, y, z, w;
+};
+__device__ __forceinline__ Quad<float> load_quad(const float *p) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ Quad<double> load_quad(const double *p) {
+    const double2 a = *reinterpret_cast<const double2 *>(p), b = *reinterpret_cast<const double2 *>(p + 2);
+    return {a.x, a.y, b.x, b.y};
+}
+__device__ __forceinline__ void store_quad(float *p, const float (&v)[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void store_quad(double *p, const double (&v)[4]) {
+    *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+    *reinterpret_cast<double2 *>(p + 2) = make_double2(v[2], v[3]);
+}
+
+// ------------------------------------------------ Solve-OF with p = q = 1 (MM-GKS)
+// App. A applied to the flow problem of a pair: at every iteration the IRLS
+// weights of the current velocity s, wf = ((Ups s - b)^2 + eps^2)^(-1/2) per pixel
+// and wl = ((L s)^2 + eps^2)^(-1/2) per difference row (rows of L: the x and y
+// forward differences of each component; a row past the frame's last column or
+// row is zero and gets no weight). s = nullptr stands for s = 0 (first iteration).
+// The arrays hold the square roots of the weights (the Gram scales its rows by them).
+template <typename real>
+__global__ void k_of_irls_weights(const real *__restrict__ ux, const real *__restrict__ uy, const real *__restrict__ bof,
+                                  const real *__restrict__ s, real eps2, real *__restrict__ wf, real *__restrict__ wl,
+                                  int nx, int ny, const int *__restrict__ act) {
+    const int b = blockIdx.z;
+    if (!act[b]) return;
+    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    const long long ns = (long long)nx * ny, i = (long long)y * nx + x;
+    const real *v = s ? s + b * 2 * ns : nullptr;
+    const real res = (v ? ux[b * ns + i] * v[i] + uy[b * ns + i] * v[ns + i] : (real)0) - bof[b * ns + i];
+    wf[b * ns + i] = (real)1 / sqrt(sqrt(res * res + eps2));
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const real *vc = v ? v + c * ns : nullptr;
+        const real dx = (vc && x < nx - 1) ? vc[i + 1] - vc[i] : (real)0;
+        const real dy = (vc && y < ny - 1) ? vc[i + nx] - vc[i] : (real)0;
+        wl[(b * 4 + 2 * c) * ns + i] = (real)1 / sqrt(sqrt(dx * dx + eps2));
+        wl[(b * 4 + 2 * c + 1) * ns + i] = (real)1 / sqrt(sqrt(dy * dy + eps2));
+    }
+}
+
+// r = Ups^T W_f (Ups s - b) + gamma L^T W_L L s: the residual of the majorant's normal
+// equations at the new s (weights of the iteration's start).
+template <typename real>
+__global__ void k_of_resid_w(const real *__restrict__ ux, const real *__restrict__ uy, const real *__restrict__ bof,
+                             const real *__restrict__ s, const real *__restrict__ wf, const real *__restrict__ wl,
+                             const double *__restrict__ gam, real *__restrict__ r, int nx, int ny,
+                             const int *__restrict__ act) {
+    const int b = blockIdx.z;
+    if (!act[b]) return;
+    const real g = block_scalar<real>(gam + b);
+    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    const long long ns = (long long)nx * ny, i = (long long)y * nx + x;
+    const real *v = s + b * 2 * ns;
+    const real ax = ux[b * ns + i], ay = uy[b * ns + i];
+    const real sf = wf[b * ns + i];
+    const real e = sf * sf * (ax * v[i] + ay * v[ns + i] - bof[b * ns + i]);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const real *vc = v + c * ns;
+        const real *wx = wl + (b * 4 + 2 * c) * ns, *wy = wx + ns;
+        const real vi = vc[i];
+        real lap = 0;  // (L^T W_L L v_c)(i): weighted edge differences into and out of i
+        if (x > 0) lap += wx[i - 1] * wx[i - 1] * (vi - vc[i - 1]);
+        if (x < nx - 1) lap -= wx[i] * wx[i] * (vc[i + 1] - vi);
+        if (y > 0) lap += wy[i - nx] * wy[i - nx] * (vi - vc[i - nx]);
+        if (y < ny - 1) lap -= wy[i] * wy[i] * (vc[i + nx] - vi);
+        r[b * 2 * ns + c * ns + i] = (c == 0 ? ax : ay) * e + g * lap;
+    }
+}
+
+// The weighted Grams of the majorant over the first K basis vectors of a pair:
+//   [G_A g; g^T bb] = sum_pixels wf (a; b)(a; b)^T,  a_j = ux v_j + uy v_j' at the pixel,
+//   G_L = sum over the difference rows of wl d d^T,  d_j = the row applied to v_j.
+// A CTA owns a strided set of tiles of WG_P pixels of one pair. Per tile the
+// pixel factors (sqrt(wf) ux, sqrt(wf) uy, sqrt(wf) b, sqrt(wl) of the four
+// difference rows, zero where a row leaves the frame) are staged once, then the
+// rows times the square-root weights are staged as quads of columns (fidelity:
+// WG_P rows of K + 1 columns, the last one b; regulariser: 4 WG_P rows of K
+// columns), and each thread accumulates 4x4 blocks of the upper triangle over
+// its row group in the storage precision (a CTA adds ns / (WG_P gridDim.x)
+// tiles, about 1000 rows per sum at the bench size). The row groups of a
+// block meet in shared memory; the CTA writes one FP64 partial per block and
+// k_of_wgram_reduce adds the CTAs in FP64.
+template <typename real>
+__device__ __forceinline__ void wg_block(int idx, int nbf, int k4f, int k4l, bool &fid, int &I, int &J) {
+    fid = idx < nbf;
+    int rem = fid ? idx : idx - nbf;
+    const int k4 = fid ? k4f : k4l;
+    I = 0;
+    while (rem >= k4 - I) {
+        rem -= k4 - I;
+        ++I;
+    }
+    J = I + rem;
+}
+
+template <typename real>
+__global__ void __launch_bounds__(WG_T) k_of_wgram(const real *__restrict__ V, int Kmax, const int *__restrict__ K,
+                                                   const int *__restrict__ act, const real *__restrict__ ux,
+                                                   const real *__restrict__ uy, const real *__restrict__ bof,
+                                                   const real *__restrict__ wf, const real *__restrict__ wl, int nx, int ny,
+                                                   double *__restrict__ partial) {
+    static_assert(WG_P == 64 && WG_T == 256, "index arithmetic below uses shifts for WG_P = 64");
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ real s_ax[WG_P], s_ay[WG_P], s_b[WG_P], s_l[4 * WG_P];
+    const int b = blockIdx.y;
+    if (!act[b]) return;
+    const int Kb = min(K[b], Kmax);
+    const int k4f = wg_k4f(Kb), k4l = wg_k4l(Kb);
+    const int nbf = k4f * (k4f + 1) / 2, nbl = k4l * (k4l + 1) / 2, nbt = nbf + nbl;
+    const long long ns = (long long)nx * ny, N2 = 2 * ns;
+    const int ntiles = (int)((ns + WG_P - 1) / WG_P);
+    constexpr int RSF = WG_P + 1, RSL = 4 * WG_P + 1;  // padded row counts (bank spread per quad)
+    real *F = reinterpret_cast<real *>(smraw);          // [k4f][RSF][4]
+    real *Lr = F + (size_t)k4f * RSF * 4;               // [k4l][RSL][4]
+    const real *Vb = V + (long long)b * Kmax * N2;
+    const int tid = threadIdx.x;
+    // (block, row group) slots: a fidelity block has WG_P rows, a regulariser block
+    // 4 WG_P, so regulariser blocks get four times the groups; with more blocks than
+    // threads every thread takes two blocks over all rows
+    int RGf = 1, RGl = 1;
+    for (int rg = 32; rg >= 1; rg >>= 1) {
+        const int f = rg >= 4 ? rg / 4 : 1;
+        if (nbf * f + nbl * rg <= WG_T) {
+            RGf = f;
+            RGl = rg;
+            break;
+        }
+    }
+    const int nslot = nbf * RGf + nbl * RGl;
+    const int per = nslot <= WG_T ? 1 : 2;
+    const int nsl = per == 1 ? nslot : nbt;  // with two per thread: one slot per block, all rows
+    int bI[2], bJ[2], r0[2], r1[2];
+    bool bfid[2], on[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int slot = tid + q * WG_T;
+        on[q] = q < per && slot < nsl;
+        bI[q] = bJ[q] = r0[q] = r1[q] = 0;
+        bfid[q] = true;
+        if (!on[q]) continue;
+        int blk, g, rg;
+        if (per == 2) {
+            blk = slot;
+            g = 0;
+            rg = 1;
+        } else if (slot < nbf * RGf) {
+            blk = slot / RGf;
+            g = slot - blk * RGf;
+            rg = RGf;
+        } else {
+            blk = nbf + (slot - nbf * RGf) / RGl;
+            g = (slot - nbf * RGf) % RGl;
+            rg = RGl;
+        }
+        wg_block<real>(blk, nbf, k4f, k4l, bfid[q], bI[q], bJ[q]);
+        const int nrows = bfid[q] ? WG_P : 4 * WG_P;
+        r0[q] = g * nrows / rg;
+        r1[q] = (g + 1) * nrows / rg;
+    }
+    real sum[2][16];
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int e = 0; e < 16; ++e) sum[q][e] = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long long p0 = (long long)tile * WG_P;
+        __syncthreads();
+        {  // pixel factors: thread = (row d, pixel pl) with d = tid >> 6
+            const int d = tid >> 6, pl = tid & (WG_P - 1);
+            const long long pix = p0 + pl;
+            real sl = 0;
+            if (pix < ns) {
+                const int y = (int)(pix / nx), x = (int)(pix - (long long)y * nx);
+                const bool inside = (d & 1) ? (y < ny - 1) : (x < nx - 1);
+                if (inside) sl = wl[(b * 4 + d) * ns + pix];
+                if (d == 0) {
+                    const real sw = wf[b * ns + pix];
+                    s_ax[pl] = sw * ux[b * ns + pix];
+                    s_ay[pl] = sw * uy[b * ns + pix];
+                    s_b[pl] = sw * bof[b * ns + pix];
+                }
+            } else if (d == 0) {
+                s_ax[pl] = s_ay[pl] = s_b[pl] = 0;
+            }
+            s_l[tid] = sl;
+        }
+        __syncthreads();
+        // fidelity rows: column j < K: v_j ax + v_j' ay, column K: b (factors hold sqrt(wf)).
+        // Thread (pl, quad group): whole quads of columns, the eight loads of a quad in flight.
+        {
+            const int pl = tid & (WG_P - 1);
+            const long long pix = p0 + pl;
+            const bool ok = pix < ns;
+            const real ax = s_ax[pl], ay = s_ay[pl], bs = s_b[pl];
+            for (int q4 = tid >> 6; q4 < k4f; q4 += WG_T / WG_P) {
+                real vx[4], vy[4], out[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int j = 4 * q4 + c;
+                    const real *vj = Vb + (long long)j * N2;
+                    vx[c] = (ok && j < Kb) ? vj[pix] : (real)0;
+                    vy[c] = (ok && j < Kb) ? vj[ns + pix] : (real)0;
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int j = 4 * q4 + c;
+                    out[c] = j < Kb ? vx[c] * ax + vy[c] * ay : (j == Kb ? bs : (real)0);
+                }
+                store_quad(F + ((size_t)q4 * RSF + pl) * 4, out);
+            }
+        }
+        // regulariser rows: row rr = d * WG_P + pl = tid, d = 2 c + dir (component c, dir
+        // 0: x, 1: y); two quads of columns per step, sixteen loads in flight
+        {
+            const int rr = tid, d = rr >> 6, pl = rr & (WG_P - 1);
+            const real sl = s_l[rr];
+            const bool ok = sl != (real)0;  // a nonzero factor: the pixel and its neighbour exist
+            const long long pix = p0 + pl, cb = (long long)(d >> 1) * ns + pix;
+            const int off = (d & 1) ? nx : 1;
+            for (int q4 = 0; q4 < k4l; q4 += 2) {
+                real a[8], c2[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const int j = 4 * q4 + c;
+                    const bool on_ = ok && j < Kb;
+                    const real *vc = Vb + (long long)j * N2 + cb;
+                    a[c] = on_ ? vc[0] : (real)0;
+                    c2[c] = on_ ? vc[off] : (real)0;
+                }
+                real o0[4], o1[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    o0[c] = sl * (c2[c] - a[c]);
+                    o1[c] = sl * (c2[c + 4] - a[c + 4]);
+                }
+                store_quad(Lr + ((size_t)q4 * RSL + rr) * 4, o0);
+                if (q4 + 1 < k4l) store_quad(Lr + ((size_t)(q4 + 1) * RSL + rr) * 4, o1);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            if (!on[q]) continue;
+            const real *base = bfid[q] ? F : Lr;
+            const int rs = bfid[q] ? RSF : RSL;
+            const real *pa = base + (size_t)bI[q] * rs * 4, *pb = base + (size_t)bJ[q] * rs * 4;
+            for (int r = r0[q]; r < r1[q]; ++r) {
+                const Quad<real> A = load_quad(pa + (size_t)r * 4), B = load_quad(pb + (size_t)r * 4);
+                const real av[4] = {A.x, A.y, A.z, A.w}, bv[4] = {B.x, B.y, B.z, B.w};
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) sum[q][a * 4 + c] = fma(av[a], bv[c], sum[q][a * 4 + c]);
+            }
+        }
+    }
+    // the row groups of each block meet in shared memory (slot-major, FP64)
+    __syncthreads();
+    double *S = reinterpret_cast<double *>(smraw);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int slot = tid + q * WG_T;
+        if (!on[q]) continue;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) S[(size_t)slot * 16 + e] = (double)sum[q][e];
+    }
+    __syncthreads();
+    double *out = partial + ((long long)b * gridDim.x + blockIdx.x) * wg_pstride(Kmax);
+    for (int e = tid; e < nbt * 16; e += WG_T) {
+        const int blk = e >> 4, el = e & 15;
+        double v = 0.0;
+        if (per == 2) {
+            v = S[(size_t)blk * 16 + el];
+        } else if (blk < nbf) {
+            for (int g = 0; g < RGf; ++g) v += S[(size_t)(blk * RGf + g) * 16 + el];
+        } else {
+            const int s0 = nbf * RGf + (blk - nbf) * RGl;
+            for (int g = 0; g < RGl; ++g) v += S[(size_t)(s0 + g) * 16 + el];
+        }
+        out[e] = v;
+    }
+}
+
+// Sum the CTA partials of k_of_wgram in FP64 (one warp per block element) and write
+// G_A, G_L (symmetric, leading dimension Kmax), g and bb of each pair.
+__global__ void k_of_wgram_reduce(const double *__restrict__ partial, int nctas, int Kmax, const int *__restrict__ K,
+                                  const int *__restrict__ act, double *__restrict__ GA, double *__restrict__ GL,
+                                  double *__restrict__ g, double *__restrict__ bb) {
+    const int b = blockIdx.y;
+    if (!act[b]) return;
+    const int Kb = min(K[b], Kmax);
+    const int k4f = wg_k4f(Kb), k4l = wg_k4l(Kb);
+    const int nbf = k4f * (k4f + 1) / 2, nbt = nbf + k4l * (k4l + 1) / 2;
+    const int o = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (o >= nbt * 16) return;
+    const int blk = o >> 4, el = o & 15;
+    bool fid;
+    int I, J;
+    wg_block<double>(blk, nbf, k4f, k4l, fid, I, J);
+    const int i = 4 * I + (el >> 2), j = 4 * J + (el & 3);
+    if (i > j) return;  // the diagonal blocks hold both triangles
+    const int lim = fid ? Kb : Kb - 1;  // the fidelity Gram has the extra column Kb (b)
+    if (j > lim) return;
+    const long long stride = wg_pstride(Kmax);
+    const double *src = partial + (long long)b * nctas * stride + o;
+    double sum = 0.0;
+    for (int c = lane; c < nctas; c += 32) sum += src[(long long)c * stride];
+    sum = warp_sum(sum);
+    if (lane != 0) return;
+    const long long KK = (long long)Kmax * Kmax;
+    if (fid && j == Kb) {
+        if (i == Kb) bb[b] = sum;
+        else g[(long long)b * Kmax + i] = sum;
+        return;
+    }
+    double *G = (fid ? GA : GL) + b * KK;
+    G[(long long)i * Kmax + j] = sum;
+    G[(long long)j * Kmax + i] = sum;
+}
+
 // AtB = Upsilon^T b with b = -u_t, and bof = -u_t
 template <typename real>
 __global__ void k_of_rhs(const real *__restrict__ ux, const real *__restrict__ uy, const real *__restrict__ ut,
@@ -780,19 +1148,6 @@ __device__ __forceinline__ void warp_axis_s(int x, real v, int n, int &i0, int &
     i1 = min(i0 + 1, n - 1);
 }
 
-// four consecutive values from 16-byte aligned shared memory
-template <typename real>
-struct Quad {
-    real x, y, z, w;
-};
-__device__ __forceinline__ Quad<float> load_quad(const float *p) {
-    const float4 v = *reinterpret_cast<const float4 *>(p);
-    return {v.x, v.y, v.z, v.w};
-}
-__device__ __forceinline__ Quad<double> load_quad(const double *p) {
-    const double2 a = *reinterpret_cast<const double2 *>(p), b = *reinterpret_cast<const double2 *>(p + 2);
-    return {a.x, a.y, b.x, b.y};
-}
 
 template <typename real>
 __global__ void __launch_bounds__(TG_T, tg_min_blocks<real>()) k_theta_gram(const real *__restrict__ V, long long n, int Kmax, const int *__restrict__ Kp,
@@ -1066,7 +1421,9 @@ static mof_status solve_of_impl(mof_problem *p, const mof_solver_params &prm, WS
         const int gram_ctas = (int)((ns + ofc<real>() - 1) / ofc<real>());
         const int gram_red = (2 * Kof + 1 + 7) / 8;
         const real *bofg2 = w.bof + (long long)b0 * ns;
-        {
+        const bool pq1 = prm.of_pq == 1;
+        real *wfg = pq1 ? w.wf_of + (long long)b0 * ns : nullptr, *wlg = pq1 ? w.wl_of + (long long)b0 * 4 * ns : nullptr;
+        if (!pq1) {
             Scope sc(tm, "of_gram", gst);
             const int ncol = std::min(prm.of_ell, Kof);
             ::mof::count_launch(), k_of_gram_cols<real><<<dim3(gram_ctas, nb, ncol), OFG_T, 0, gst>>>(Vg, Kof, Kvg, actg, 0, uxg, uyg, bofg2,
@@ -1090,7 +1447,21 @@ static mof_status solve_of_impl(mof_problem *p, const mof_solver_params &prm, WS
         sa.flag = w.flag_of + b0;
         sa.err = w.err;
         BasisRef<real> BS{Vg, N2, Kof, nb, Kvg, nullptr};
+        const int wg_ctas = (int)std::min<long long>(WG_CTAS, (ns + WG_P - 1) / WG_P);
         for (int it = 0; it < prm.of_iters; ++it) {
+            if (pq1) {
+                // MM-GKS: IRLS weights of the current velocity (zero at the start), then the
+                // weighted Grams of the whole basis
+                Scope sc(tm, "of_irls", gst);
+                ::mof::count_launch(), k_of_irls_weights<real><<<gg, blk2, 0, gst>>>(uxg, uyg, bofg2, it == 0 ? nullptr : sg,
+                                                                                   (real)(prm.eps * prm.eps), wfg, wlg, p->nx,
+                                                                                   p->ny, actg);
+                ::mof::count_launch(), k_of_wgram<real><<<dim3(wg_ctas, nb), WG_T, wg_smem<real>(Kof), gst>>>(
+                    Vg, Kof, Kvg, actg, uxg, uyg, bofg2, wfg, wlg, p->nx, p->ny, kg.partial);
+                ::mof::count_launch(), k_of_wgram_reduce<<<dim3((wg_pstride(Kof) + 7) / 8, nb), 256, 0, gst>>>(
+                    kg.partial, wg_ctas, Kof, Kvg, actg, w.GA + b0 * KK, w.GL + b0 * KK, w.gof + (long long)b0 * Kof,
+                    w.bb_of + b0);
+            }
             {
                 Scope sc(tm, "of_small", gst);
                 MOF_TRY(launch_small_solve(sa, gst));
@@ -1100,7 +1471,14 @@ static mof_status solve_of_impl(mof_problem *p, const mof_solver_params &prm, WS
                 kg.combine(BS, sa.z, Kof, sg, N2, gst);
             }
             if (it == prm.of_iters - 1) break;
-            {
+            if (pq1) {
+                Scope sc(tm, "of_resid", gst);
+                ::mof::count_launch(), k_of_resid_w<real><<<gg, blk2, 0, gst>>>(uxg, uyg, bofg2, sg, wfg, wlg, sa.lam, wvg, p->nx,
+                                                                              p->ny, actg);
+                // the growth test compares with the residual's own norm (the weights rescale it)
+                kg.norm2(wvg, N2, N2, nb, w.rn_of + b0, gst);
+                ::mof::count_launch(), k_sqrt_into<<<pb, 64, 0, gst>>>(w.rn_of + b0, w.scale_of + b0, nb);
+            } else {
                 Scope sc(tm, "of_resid", gst);
                 ::mof::count_launch(), k_of_resid<real><<<gg, blk2, 0, gst>>>(uxg, uyg, AtBg, sg, sa.lam, wvg, p->nx, p->ny, actg);
             }
@@ -1129,7 +1507,7 @@ static mof_status solve_of_impl(mof_problem *p, const mof_solver_params &prm, WS
                 kg.append_parts(BAg, Kvg, wvg, N2, np, w.nrm_of + b0, w.scale_of + b0, tol, w.grow_of + b0, appg, nullptr, nullptr,
                                 nullptr, gst);
             }
-            {
+            if (!pq1) {
                 Scope sc(tm, "of_gram", gst);
                 ::mof::count_launch(), k_of_gram_cols<real><<<dim3(gram_ctas, nb, 1), OFG_T, 0, gst>>>(Vg, Kof, Kvg, appg, 1, uxg, uyg, bofg2,
                                                                                                     p->nx, p->ny, kg.partial);
@@ -1609,6 +1987,7 @@ static mof_status check_params(const mof_problem *p, const mof_solver_params *pr
                     prm->ell + n_outer, prm->of_ell + prm->of_iters);
     if (!(prm->eps > 0) || !std::isfinite(prm->eps)) return fail(MOF_EINVAL, "eps must be finite and > 0");
     if (prm->temporal_tv != 0 && prm->temporal_tv != 1) return fail(MOF_EINVAL, "temporal_tv must be 0 or 1");
+    if (prm->of_pq != 1 && prm->of_pq != 2) return fail(MOF_EINVAL, "of_pq must be 1 or 2 (got %d)", prm->of_pq);
     if (prm->of_scale < 1 || p->nx % prm->of_scale || p->ny % prm->of_scale || p->nx / prm->of_scale < 2 ||
         p->ny / prm->of_scale < 2)
         return fail(MOF_EINVAL, "of_scale must be >= 1, divide nx and ny and leave frames of at least 2x2 (got %d for %d x %d)",

@@ -60,6 +60,62 @@ def test_solve_of_matches_oracle(prec, tol):
     assert rel(got, want) <= tol, rel(got, want)
 
 
+@pytest.mark.parametrize("prec,tol", [(api.MOF_FP64, 1e-6), (api.MOF_FP32, 3e-3)])
+def test_solve_of_pq1_matches_oracle(prec, tol):
+    """Solve-OF with p = q = 1 (MM-GKS, App. A): IRLS weights from the current velocity,
+    the weighted Grams of the whole basis every iteration, the weighted residual."""
+    w = synth.moving_disks(48, 4, 8, 48, radii=(6.0, 9.0), seed=1)
+    p = problem(w, prec)
+    u = w.u_true.astype(npdt(prec))
+    ud = torch.tensor(u, device="cuda").reshape(-1)
+    s = torch.empty(p.nv, dtype=tdt(prec), device="cuda")
+    api.mof_solve_of(p, api.mof_default_params(of_ell=6, of_iters=8, of_pq=1), ud, s)
+    want = OS.solve_of(u.astype(np.float64), OS.Params(of_ell=6, of_iters=8, of_pq=1))
+    got = s.cpu().double().numpy().reshape(want.shape)
+    assert rel(got, want) <= tol, rel(got, want)
+    two = OS.solve_of(u.astype(np.float64), OS.Params(of_ell=6, of_iters=8))
+    assert rel(got, two) > 0.1  # the l1 norms give another flow
+
+
+@pytest.mark.parametrize("prec,tol", [(api.MOF_FP64, 1e-6), (api.MOF_FP32, 1e-2)])
+def test_solve_of_pq1_basis_beyond_32_and_ragged_tiles(prec, tol):
+    """p = q = 1 with the basis growing from 30 to 63 vectors (past 60 the weighted Gram
+    has more 4x4 blocks than threads and each thread takes two) on frames whose pixel
+    count is not a multiple of the Gram tile. FP32: 34 MM iterations whose weights reach
+    1/eps = 1e3 carry the FP32 rounding of the Grams into the iterates (3e-3 measured)."""
+    w = synth.moving_disks(37, 3, 8, 37, radii=(5.0, 7.0), seed=3)
+    p = problem(w, prec)
+    u = w.u_true.astype(npdt(prec))
+    s = torch.empty(p.nv, dtype=tdt(prec), device="cuda")
+    api.mof_solve_of(p, api.mof_default_params(of_ell=30, of_iters=34, of_pq=1), torch.tensor(u, device="cuda").reshape(-1), s)
+    want = OS.solve_of(u.astype(np.float64), OS.Params(of_ell=30, of_iters=34, of_pq=1))
+    got = s.cpu().double().numpy().reshape(want.shape)
+    assert rel(got, want) <= tol, rel(got, want)
+
+
+def test_solve_of_pq1_stream_groups_do_not_change_the_result():
+    w = synth.moving_disks(40, 8, 8, 40, radii=(5.0, 8.0), seed=6)
+    p = problem(w, api.MOF_FP32)
+    u = torch.tensor(w.u_true.astype(np.float32), device="cuda").reshape(-1)
+    out = []
+    for g in (1, 3, 7):
+        s = torch.empty(p.nv, dtype=torch.float32, device="cuda")
+        api.mof_solve_of(p, api.mof_default_params(of_ell=5, of_iters=6, of_streams=g, of_pq=1), u, s)
+        out.append(s.cpu())
+    for o in out[1:]:
+        assert torch.equal(o, out[0])
+
+
+def test_solve_of_rejects_unknown_norms():
+    w = synth.moving_disks(32, 3, 8, 32, radii=(5.0, 7.0), seed=2)
+    p = problem(w, api.MOF_FP32)
+    s = torch.empty(p.nv, dtype=torch.float32, device="cuda")
+    u = torch.tensor(w.u_true.astype(np.float32), device="cuda").reshape(-1)
+    for pq in (0, 3):
+        with pytest.raises(api.MofError):
+            api.mof_solve_of(p, api.mof_default_params(of_pq=pq), u, s)
+
+
 def test_solve_of_zero_pairs_give_zero_velocity():
     w = synth.moving_disks(32, 3, 8, 32, radii=(5.0, 7.0), seed=2)
     u = w.u_true.copy()
@@ -347,6 +403,20 @@ def test_mmgks_of_fp64_fan_beam_matches_oracle():
     for r, o in zip(rep, ores.report):
         assert r["flag"] == o["flag"] and r["basis"] == o["basis"]
     assert rel(u, w.u_true.ravel()) < 0.5
+
+
+def test_mmgks_of_fp64_pq1_solve_of_matches_oracle():
+    """MMGKS-OF whose Solve-OF uses p = q = 1 (MM-GKS) on the 64x64x8 two-disk workload,
+    4 outer iterations, against the oracle. The l1 flow amplifies perturbations of the
+    frames by about 1/eps (the oracle's own Solve-OF moves by 9e-6 when the frames move by
+    1e-8, against 2e-8 for p = q = 2), so the velocities get 5e-4 where the images get 1e-6."""
+    w = synth.plain_fp64(0)
+    ores = _oracle_solve(w, 4, of_pq=1)
+    u, s, rep = _gpu_solve(w, api.MOF_FP64, 4, of_pq=1)
+    assert rel(u, ores.u) <= 1e-6, rel(u, ores.u)
+    assert rel(s, ores.s) <= 5e-4, rel(s, ores.s)
+    for r, o in zip(rep, ores.report):
+        assert r["flag"] == o["flag"] and r["basis"] == o["basis"]
 
 
 def test_mmgks_of_fp32_d1_of_precision_form_small():
