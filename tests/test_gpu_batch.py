@@ -49,6 +49,33 @@ def test_batch_equals_individual_solves():
         assert [r["lambda"] for r in rep] == [r["lambda"] for r in rep1]
 
 
+def test_batch_mixes_geometries_warps_and_solver_variants():
+    """One batch holding a fan-beam problem, a rounding-warp problem, a p = q = 1 Solve-OF,
+    a D1-OF problem and a rescaled Solve-OF: each result is its own mof_solve's, bit for bit."""
+    ws = [synth.fan_form_small(0), synth.moving_disks(40, 4, 8, 40, radii=(5.0, 8.0), seed=11),
+          synth.moving_disks(48, 4, 8, 48, radii=(6.0, 9.0), seed=12),
+          synth.moving_disks(40, 5, 8, 40, radii=(5.0, 8.0), seed=13),
+          synth.moving_disks(64, 4, 8, 64, radii=(8.0, 12.0), seed=14)]
+    extra = [{}, {}, {"of_pq": 1}, {"temporal_tv": 1}, {"of_scale": 2, "tau": 2}]
+    probs, params, bs = [], [], []
+    for i, (w, ex) in enumerate(zip(ws, extra)):
+        p = api.mof_problem_create(w.nx, w.ny, w.nt, w.nb, w.na, w.angles, w.h, w.db, api.MOF_FP32, fan=w.fan)
+        if i == 1:
+            api.mof_set_warp(p, 1)
+        probs.append(p)
+        params.append(api.mof_default_params(noise_norm=w.noise_norm, ell=5, of_ell=4, of_iters=5, **ex))
+        bs.append(torch.tensor(w.b, dtype=torch.float32, device="cuda"))
+    n_outer = 4
+    us = [torch.empty(p.n, dtype=torch.float32, device="cuda") for p in probs]
+    ss = [torch.empty(p.nv, dtype=torch.float32, device="cuda") for p in probs]
+    reps = api.mof_solve_batch(probs, params, n_outer, bs, us, ss)
+    for p, prm, b, u, s, rep in zip(probs, params, bs, us, ss, reps):
+        u1, s1 = torch.empty_like(u), torch.empty_like(s)
+        rep1 = api.mof_solve(p, prm, n_outer, b, u1, s1)
+        assert torch.equal(u, u1) and torch.equal(s, s1)
+        assert [r["basis"] for r in rep] == [r["basis"] for r in rep1]
+
+
 def test_batch_rejects_bad_arguments_before_running():
     ws = _uneven(1)[:2]
     probs, params, bs = _setup(ws, [api.MOF_FP32, api.MOF_FP32])
