@@ -267,13 +267,11 @@ __global__ void __launch_bounds__(SDT) k_sub_dot(const real *__restrict__ V, lon
     const long long c0 = (long long)chunk * CH;
     const int len = (int)min((long long)CH, N - c0);
     const unsigned bar_a = smem_u32(&bar);
+    // the copies go out first (the thread that initialised the barrier issues them);
+    // the coefficients are read while they are in flight
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    for (int j = tid; j < Kb; j += SDT) sc[j] = (real)c[b * cstride + j];
-    __syncthreads();
-    if (tid == 0) {
         const unsigned bytes = (unsigned)len * (unsigned)sizeof(real);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a), "r"(bytes * (unsigned)(Kb + 1))
                      : "memory");
@@ -281,6 +279,8 @@ __global__ void __launch_bounds__(SDT) k_sub_dot(const real *__restrict__ V, lon
         const real *Vb = V + (long long)b * Kmax * N + c0;
         for (int j = 0; j < Kb; ++j) bulk_g2s(sV + (long long)j * CH, Vb + (long long)j * N, bytes, bar_a);
     }
+    for (int j = tid; j < Kb; j += SDT) sc[j] = (real)c[b * cstride + j];
+    __syncthreads();  // sc complete, and the barrier's initialisation visible to every thread
     if (!mbar_wait(bar_a, 0)) {
         if (tid == 0 && err) atomicOr(err, 4);
         mbar_wait(bar_a, 0);  // do not leave while copies may still land
