@@ -127,6 +127,7 @@ __global__ void __launch_bounds__(SUMT) k_sum_chunks(const double *__restrict__ 
     const DotOut &o = outs.o[v];
     if (!o.out) return;
     double s = 0.0;
+#pragma unroll 8
     for (int c = lane; c < nchunk; c += 32) s += partial[(((long long)b * nchunk + c) * NV + v) * Kmax + i];
     s = warp_sum(s);
     if (lane == 0) {
@@ -360,6 +361,7 @@ __global__ void k_sum_scalar_chunks(const double *__restrict__ partial, int nchu
     const int b = blockIdx.x, lane = threadIdx.x;
     if (b >= B) return;
     double s = 0.0;
+#pragma unroll 8
     for (int c = lane; c < nchunk; c += 32) s += partial[(long long)b * nchunk + c];
     s = warp_sum(s);
     if (lane == 0) out[b] = s;
@@ -406,6 +408,7 @@ __global__ void k_append_prep_sum(int *__restrict__ K, int Kmax, const double *_
     const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (b >= B) return;
     double s = 0.0;
+#pragma unroll 8
     for (int c = lane; c < nparts; c += 32) s += parts[(long long)b * nparts + c];
     s = warp_sum(s);
     if (lane != 0) return;

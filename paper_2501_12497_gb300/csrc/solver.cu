@@ -756,6 +756,7 @@ __global__ void k_of_gram_reduce(const double *__restrict__ partial, int nctas, 
     const int slot = o == nout - 1 ? 2 * Kmax : o;
     const double *src = partial + ((long long)b * gridDim.z + blockIdx.z) * nctas * (2 * Kmax + 1) + slot;
     double sum = 0.0;
+#pragma unroll 8
     for (int c = lane; c < nctas; c += 32) sum += src[(long long)c * (2 * Kmax + 1)];
     sum = warp_sum(sum);
     if (lane != 0) return;
@@ -1088,6 +1089,7 @@ __global__ void k_of_wgram_reduce(const double *__restrict__ partial, int nctas,
     const long long stride = wg_pstride(Kmax);
     const double *src = partial + (long long)b * nctas * stride + o;
     double sum = 0.0;
+#pragma unroll 8
     for (int c = lane; c < nctas; c += 32) sum += src[(long long)c * stride];
     sum = warp_sum(sum);
     if (lane != 0) return;
@@ -1322,6 +1324,7 @@ __global__ void k_gram_reduce(const double *__restrict__ partial, int nparts, in
         const int i = e / K, j = e % K;
         if (i > j) continue;
         double s = 0.0;
+#pragma unroll 8
         for (int c = lane; c < nparts; c += 32) s += partial[(long long)c * Kmax * Kmax + i * Kmax + j];
         s = warp_sum(s);
         if (lane == 0) {
