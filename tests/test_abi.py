@@ -67,3 +67,56 @@ def test_null_arguments_are_rejected(lib):
     prm = api.mof_default_params()
     assert lib.mof_solve(None, ctypes.byref(prm), 3, None, None, None, None, None, None) == api.MOF_EINVAL
     assert lib.mof_solve_of(None, ctypes.byref(prm), None, None, None) == api.MOF_EINVAL
+
+
+def _header_struct_fields(name):
+    """(type, field) pairs of `typedef struct { ... } name;` in include/mof.h, in order."""
+    text = open(os.path.join(ROOT, "include", "mof.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    body = re.search(r"typedef struct\s*\{([^}]*)\}\s*" + name + r"\s*;", text).group(1)
+    out = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        m = re.match(r"(const\s+)?(\w+)\s+(.*)$", decl, flags=re.S)
+        assert m, decl
+        for item in m.group(3).split(","):  # "int nx, ny" declares several fields
+            item = item.strip()
+            ptr = item.startswith("*")
+            out.append((m.group(2) + ("*" if ptr else ""), item.lstrip("*").strip()))
+    return out
+
+
+@pytest.mark.parametrize("name", ["mof_geometry", "mof_solver_params", "mof_report"])
+def test_ctypes_structs_follow_the_header(name):
+    """The binding's structures list the header's fields in the same order with the same
+    scalar types, so the layouts agree on any platform."""
+    ctype = {"int": ctypes.c_int, "double": ctypes.c_double}
+    fields = getattr(api, name)._fields_
+    hdr = _header_struct_fields(name)
+    assert len(fields) == len(hdr), (fields, hdr)
+    for (pyname, pytype), (ctyp, cname) in zip(fields, hdr):
+        assert pyname.rstrip("_") == cname, (pyname, cname)
+        if ctyp in ctype:
+            assert pytype is ctype[ctyp], (cname, pytype, ctyp)
+        else:
+            assert ctyp.endswith("*") and issubclass(pytype, ctypes._Pointer), (cname, pytype, ctyp)
+
+
+def test_defaults_of_the_widened_options(lib):
+    p = api.mof_default_params()
+    assert (p.of_scale, p.temporal_tv, p.of_pq, p.of_streams) == (1, 0, 2, 0)
+
+
+def test_fan_problem_rejects_bad_distances_on_the_host(lib):
+    na, ang = [2, 2], [0.0, 1.0, 0.5, 1.5]
+    # half the diagonal of a 32 x 32 frame is 22.6 pixels: a source inside the field
+    for rs, rd in ((20.0, 5.0), (24.0, 5.0), (60.0, -1.0), (float("inf"), 1.0), (60.0, float("nan"))):
+        with pytest.raises(api.MofError) as e:
+            api.mof_problem_create(32, 32, 2, 64, na, ang, fan=(rs, rd))
+        assert e.value.status == api.MOF_EINVAL
+
+
+def test_set_warp_rejects_a_null_problem(lib):
+    assert lib.mof_set_warp(None, 1) == api.MOF_EINVAL
