@@ -575,25 +575,6 @@ __device__ __forceinline__ real lap_at(const real *__restrict__ f, int nx, int n
     return v;
 }
 
-// y1 = Upsilon^T Upsilon v, y2 = (L(+)L)^T (L(+)L) v for v = src[b] (length 2 ns)
-template <typename real>
-__global__ void k_of_normal_parts(const real *__restrict__ ux, const real *__restrict__ uy, const real *__restrict__ src,
-                                  long long sstride, real *__restrict__ y1, real *__restrict__ y2, int nx, int ny,
-                                  const int *__restrict__ act) {
-    const int b = blockIdx.z;
-    if (act && !act[b]) return;
-    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
-    if (x >= nx || y >= ny) return;
-    const long long ns = (long long)nx * ny, i = (long long)y * nx + x;
-    const real *v = src + b * sstride;
-    const real ax = ux[b * ns + i], ay = uy[b * ns + i];
-    const real a = ax * v[i] + ay * v[ns + i];
-    y1[b * 2 * ns + i] = ax * a;
-    y1[b * 2 * ns + ns + i] = ay * a;
-    y2[b * 2 * ns + i] = lap_at(v, nx, ny, x, y);
-    y2[b * 2 * ns + ns + i] = lap_at(v + ns, nx, ny, x, y);
-}
-
 // r = Ups^T Ups s - Ups^T b + gamma (L(+)L)^T (L(+)L) s  (normal-equation residual of Alg. 2)
 template <typename real>
 __global__ void k_of_resid(const real *__restrict__ ux, const real *__restrict__ uy, const real *__restrict__ AtB,
