@@ -395,3 +395,45 @@ def test_d1_of_mm_step_full_subspace_equals_dense_normal_equations():
         w = 1.0 / np.sqrt((Th @ u) ** 2 + prm.eps ** 2)
         u = np.linalg.solve(Hd.T @ Hd + prm.lam_fixed * Th.T @ (w[:, None] * Th), Hd.T @ b)
         np.testing.assert_allclose(res.u.ravel(), u, rtol=1e-8, atol=1e-10)
+
+
+def test_round_warp_mm_step_full_subspace_equals_dense_normal_equations():
+    """Rounding-and-clipping M(s) inside MMGKS-OF: with V spanning R^n one step solves the dense
+    normal equations whose Mhat rows pick, per pixel, the frame value at the clamped rounded
+    displacement (assembled here pixel by pixel; halves away from zero)."""
+    import math
+    g, b = _tiny_problem(seed=3)
+    n = g.n
+    shape = (g.nt, g.ny, g.nx)
+    s = synth.random_velocities(g.nt - 1, g.ny, g.nx, 1.5, seed=7)
+    s[0, 0, 0, :] = 0.5  # exact halves in the first rows
+    s[0, 1, 1, :] = -0.5
+    prm = solver.Params(ell=n, tau=0, image_rule=solver.RULE_FIXED, lam_fixed=0.05, eps=0.1, warp_round=1)
+    Hd = _dense_of(lambda x: ops.project(g, x), n, shape)
+    sr = ops.reverse_flow(s)
+    Psi = _dense_of(lambda x: ops.grad(x), n, shape)
+    ns = g.ny * g.nx
+
+    def pick(v):
+        r = math.floor(abs(v) + 0.5)
+        return int(r if v >= 0 else -r)
+
+    rows = []
+    for t in range(g.nt - 1):
+        for fa, fb, vel in ((t, t + 1, s[t]), (t + 1, t, sr[t])):
+            for y in range(g.ny):
+                for x in range(g.nx):
+                    X = min(max(x + pick(vel[0, y, x]), 0), g.nx - 1)
+                    Y = min(max(y + pick(vel[1, y, x]), 0), g.ny - 1)
+                    row = np.zeros(n)
+                    row[fa * ns + y * g.nx + x] += 1.0
+                    row[fb * ns + Y * g.nx + X] -= 1.0
+                    rows.append(row)
+    Th = np.vstack([Psi, np.array(rows)])
+    u = np.zeros(n)
+    for n_outer in (1, 2):
+        res = solver.mmgks_of(g, b, prm, n_outer, s_init=s)
+        w = 1.0 / np.sqrt((Th @ u) ** 2 + prm.eps ** 2)
+        u = np.linalg.solve(Hd.T @ Hd + prm.lam_fixed * Th.T @ (w[:, None] * Th), Hd.T @ b)
+        np.testing.assert_allclose(res.u.ravel(), u, rtol=1e-8, atol=1e-10)
+
