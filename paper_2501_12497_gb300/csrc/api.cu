@@ -253,6 +253,11 @@ mof_status mof_problem_create_fan(const mof_geometry *g, double source_distance,
                     source_distance, half_diag + 2.0 * g->pixel_size);
     if (!(detector_distance >= 0.0) || !std::isfinite(detector_distance))
         return fail(MOF_EINVAL, "detector_distance must be finite and >= 0");
+    // the transpose finds a pixel's bins by central projection in FP32; beyond this ratio its
+    // rounding (about 1.2e-7 (rs + rd) / bin_size bins) would approach the bins' margin
+    if ((source_distance + detector_distance) / g->bin_size > 1e5)
+        return fail(MOF_EUNSUPPORTED, "(source_distance + detector_distance) / bin_size = %g exceeds 1e5",
+                    (source_distance + detector_distance) / g->bin_size);
     mof_problem *p = nullptr;
     MOF_TRY(mof_problem_create(g, precision, &p));
     p->fan = 1;

@@ -118,5 +118,11 @@ def test_fan_problem_rejects_bad_distances_on_the_host(lib):
         assert e.value.status == api.MOF_EINVAL
 
 
+def test_fan_problem_rejects_distances_beyond_the_fp32_bin_search(lib):
+    with pytest.raises(api.MofError) as e:
+        api.mof_problem_create(32, 32, 2, 64, [2, 2], [0.0, 1.0, 0.5, 1.5], bin_size=1.0, fan=(2e5, 0.0))
+    assert e.value.status == api.MOF_EUNSUPPORTED
+
+
 def test_set_warp_rejects_a_null_problem(lib):
     assert lib.mof_set_warp(None, 1) == api.MOF_EINVAL
