@@ -99,8 +99,8 @@ typedef struct {
                               p = q = 2 by GKS; 1: p = q = 1 by MM-GKS (App. A) with IRLS weights
                               ((.)^2 + eps^2)^(-1/2) on the flow residual and on (L+L) s, recomputed
                               from the current velocity (zero at the start) every iteration; the
-                              subspace stops growing when the orthogonalised residual is
-                              breakdown_tol times its own norm */
+                              subspace stops growing when the orthogonalised residual is at most
+                              breakdown_tol times its norm before the orthogonalisation */
 } mof_solver_params;
 
 /* One record per outer iteration k of mof_solve (host struct). */
