@@ -42,11 +42,32 @@ __device__ __forceinline__ double block_sum_to_double(acc_t v, double *sh) {
     return r;
 }
 
+// Error-free FP32 accumulation of a dot product ("double-float"): hi + lo carries the
+// running sum with the rounding error of every product (TwoProduct by an FMA) and of
+// every addition (Knuth's TwoSum) kept in lo, so a chunk's partial is accurate to a few
+// units of 2^-48 of the sum of |terms|, independent of cancellation. The _rn intrinsics
+// keep the compiler from contracting or reordering the steps.
+struct DFAcc {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add_prod(float a, float b) {
+        const float p = __fmul_rn(a, b);
+        const float e = __fmaf_rn(a, b, -p);
+        const float s = __fadd_rn(hi, p);
+        const float bp = __fsub_rn(s, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+        hi = s;
+        lo = __fadd_rn(lo, __fadd_rn(err, e));
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 // partial[b][chunk][v][j] = sum_{i in chunk} V[b][j][i] * x_v[b][i], j < K[b], v < NV.
+// EXACT (FP32 data only): error-free accumulation per lane (DFAcc), lanes summed in FP64;
+// used for the Gram matrices whose projected residual subtracts nearly equal terms.
 // The NV right-hand chunks are staged in shared memory; warp w streams the
 // basis vectors j = w, w + 8, ... of the chunk (16-byte loads when VEC) and
 // reduces each dot once.
-template <typename real, int NV, bool VEC>
+template <typename real, int NV, bool VEC, bool EXACT = false>
 __global__ void __launch_bounds__(KT) k_mdot(const real *__restrict__ V, long long N, int Kmax, const int *__restrict__ K,
                                              const int *__restrict__ act, DotVecs<real> xs, double *__restrict__ partial,
                                              int nchunk) {
@@ -65,6 +86,23 @@ __global__ void __launch_bounds__(KT) k_mdot(const real *__restrict__ V, long lo
     }
     __syncthreads();
     const real *Vb = V + (long long)b * Kmax * N + c0;
+    if constexpr (EXACT && sizeof(real) == 4) {
+        for (int j = w; j < Kb; j += KT / 32) {
+            const real *vj = Vb + (long long)j * N;
+            DFAcc a[NV];
+            for (int i = l; i < len; i += 32) {
+                const float q = vj[i];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) a[v].add_prod(q, sx[v][i]);
+            }
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const double t = warp_sum(a[v].value());
+                if (l == 0) partial[(((long long)b * nchunk + chunk) * NV + v) * Kmax + j] = t;
+            }
+        }
+        return;
+    }
     for (int j = w; j < Kb; j += KT / 32) {
         const real *vj = Vb + (long long)j * N;
         real a[NV];
@@ -337,12 +375,26 @@ __global__ void __launch_bounds__(SDT) k_sub_dot(const real *__restrict__ V, lon
 }
 
 // ||x[b]||^2 per chunk
-template <typename real>
+template <typename real, bool EXACT = false>
 __global__ void __launch_bounds__(KT) k_norm2(const real *__restrict__ x, long long N, long long xstride,
                                               double *__restrict__ partial, int nchunk) {
     __shared__ double sh[KT / 32];
     const int b = blockIdx.y, chunk = blockIdx.x;
     const long long i0 = (long long)chunk * CHUNK + threadIdx.x;
+    if constexpr (EXACT && sizeof(real) == 4) {
+        DFAcc a;
+#pragma unroll
+        for (int e = 0; e < KE; ++e) {
+            const long long i = i0 + (long long)e * KT;
+            if (i < N) {
+                const float v = x[b * xstride + i];
+                a.add_prod(v, v);
+            }
+        }
+        const double s = block_sum_to_double(a.value(), sh);
+        if (threadIdx.x == 0) partial[(long long)b * nchunk + chunk] = s;
+        return;
+    }
     real n2 = 0;
 #pragma unroll
     for (int e = 0; e < KE; ++e) {
@@ -463,12 +515,13 @@ static bool vec_ok(const void *base, long long N, long long stride) {
 
 template <typename real>
 void Krylov<real>::multidot(const BasisRef<real> &B, int nv, const DotVecs<real> &xs, const DotOuts &outs,
-                            cudaStream_t st) const {
+                            cudaStream_t st, bool exact) const {
     const int nc = (int)mdot_chunks<real>(B.N);
     const dim3 grid(nc, B.B);
     const bool vec = vec_ok<real>(B.V, B.N, (long long)B.Kmax * B.N);
 #define MDOT(NVv)                                                                                                       \
-    if (vec) ::mof::count_launch(), k_mdot<real, NVv, true><<<grid, KT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, xs, partial, nc); \
+    if (exact) ::mof::count_launch(), k_mdot<real, NVv, false, true><<<grid, KT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, xs, partial, nc); \
+    else if (vec) ::mof::count_launch(), k_mdot<real, NVv, true><<<grid, KT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, xs, partial, nc); \
     else ::mof::count_launch(), k_mdot<real, NVv, false><<<grid, KT, 0, st>>>(B.V, B.N, B.Kmax, B.K, B.act, xs, partial, nc);
     if (nv == 1) {
         MDOT(1)
@@ -539,9 +592,11 @@ int Krylov<real>::subtract_parts(const BasisRef<real> &B, const double *c, long 
 }
 
 template <typename real>
-void Krylov<real>::norm2(const real *x, long long N, long long xstride, int nb, double *out, cudaStream_t st) const {
+void Krylov<real>::norm2(const real *x, long long N, long long xstride, int nb, double *out, cudaStream_t st,
+                         bool exact) const {
     const int nc = (int)krylov_chunks(N);
-    ::mof::count_launch(), k_norm2<real><<<dim3(nc, nb), KT, 0, st>>>(x, N, xstride, partial, nc);
+    if (exact) ::mof::count_launch(), k_norm2<real, true><<<dim3(nc, nb), KT, 0, st>>>(x, N, xstride, partial, nc);
+    else ::mof::count_launch(), k_norm2<real><<<dim3(nc, nb), KT, 0, st>>>(x, N, xstride, partial, nc);
     ::mof::count_launch(), k_sum_scalar_chunks<<<nb, 32, 0, st>>>(partial, nc, out, nb);
 }
 

@@ -56,8 +56,10 @@ struct Krylov {
     // out[b][j] = sign * <V[b][j], x[b]>, j < K[b]
     void dots(const BasisRef<real> &B, const real *x, long long xstride, double *out, long long ostride, double sign,
               cudaStream_t st) const;
-    // dots of every basis vector with nv (1..3) vectors in one pass over V
-    void multidot(const BasisRef<real> &B, int nv, const DotVecs<real> &xs, const DotOuts &outs, cudaStream_t st) const;
+    // dots of every basis vector with nv (1..3) vectors in one pass over V; exact: error-free
+    // accumulation of FP32 products (for Grams whose projected residual cancels)
+    void multidot(const BasisRef<real> &B, int nv, const DotVecs<real> &xs, const DotOuts &outs, cudaStream_t st,
+                  bool exact = false) const;
     // out[b] = sum_j V[b][j] c[b][j]
     void combine(const BasisRef<real> &B, const double *c, long long cstride, real *out, long long ostride,
                  cudaStream_t st) const;
@@ -67,7 +69,8 @@ struct Krylov {
     // out[b] = x[b] - sum_j V[b][j] c[b][j]; optionally ||out[b]||^2 -> nrm2_out[b]
     void subtract(const BasisRef<real> &B, const double *c, long long cstride, const real *x, long long xstride, real *out,
                   long long ostride, double *nrm2_out, cudaStream_t st) const;
-    void norm2(const real *x, long long N, long long xstride, int nb, double *out, cudaStream_t st) const;
+    void norm2(const real *x, long long N, long long xstride, int nb, double *out, cudaStream_t st,
+               bool exact = false) const;
     // x[b] <- (I - V V^T)^2 x[b] (classical Gram-Schmidt twice); ||x||^2 -> nrm2_out
     void reorth(const BasisRef<real> &B, real *x, long long xstride, double *coef, double *nrm2_out, cudaStream_t st) const;
     // the same with the first projection's coefficients V^T x supplied by the caller from an
