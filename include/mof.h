@@ -309,30 +309,32 @@ long long mof_kernel_launches(void);
  *
  * Mhat^T r exactly as mof_apply_flowT (same kernels, bit-identical result,
  * Sec. 2.3), but without allocating: mof_apply_flowT takes its scratch (the
- * per-tile displacement radii of s and s' that bound the gather transpose)
- * from the problem's workspace, which the library allocates on first use;
- * this call takes it from a fixed device array owned by the library, one per
- * device, of MOF_FLOWT_NOALLOC_MAX_RADII ints (4 MiB). It is for callers that
- * cannot allocate device memory at call time: a process running against a
- * fixed device-memory budget, where the first-use allocation could fail with
- * MOF_ENOMEM in the middle of a run, or a latency-critical loop, where
- * cudaMalloc may synchronise the device.
- *  - Size limit: the problem needs 2 (nt-1) ceil(nx/32) ceil(ny/8) radii; a
- *    problem needing more than MOF_FLOWT_NOALLOC_MAX_RADII returns
- *    MOF_EUNSUPPORTED and enqueues nothing.
- *  - Zero state: each call clears the part of the array it uses before use
- *    (the radii are maxima accumulated from zero); the caller initialises
- *    nothing.
+ * per-tile bounds of the integer displacements of s and s' that bound the
+ * gather transpose's window) from the problem's workspace, which the library
+ * allocates on first use; this call takes it from a fixed device array owned
+ * by the library, one per device, of MOF_FLOWT_NOALLOC_MAX_INTS ints (16 MiB).
+ * It is for callers that cannot allocate device memory at call time: a
+ * process running against a fixed device-memory budget, where the first-use
+ * allocation could fail with MOF_ENOMEM in the middle of a run, or a
+ * latency-critical loop, where cudaMalloc may synchronise the device.
+ *  - Size limit: the problem needs 8 (nt-1) ceil(nx/32) ceil(ny/8) ints (four
+ *    per 32x8 tile for each of s and s'); a problem needing more than
+ *    MOF_FLOWT_NOALLOC_MAX_INTS returns MOF_EUNSUPPORTED and enqueues nothing.
+ *  - Initial state: each call resets the part of the array it uses before use
+ *    (the bounds are minima and maxima accumulated from an empty range); the
+ *    caller initialises nothing.
  *  - Set-up: the first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress, return code checked: MOF_ECUDA on failure) with
- *    the problem's device current; make that first call before any stream
- *    capture begins. Later calls on the device only enqueue kernels.
+ *    (cudaGetSymbolAddress, return code checked: MOF_ECUDA on failure) and
+ *    caches it; make that first call before any stream capture begins. Every
+ *    call must be made with the problem's device current (MOF_EINVAL
+ *    otherwise). The cached address does not survive cudaDeviceReset: do not
+ *    use this entry point on a device that was reset in the same process.
  *  - Concurrency: the array is shared by every problem and stream of the
  *    device. Calls whose kernels overlap in time (different streams, or
  *    different host threads without ordering) race on it and give undefined
  *    results; order them, e.g. on one stream.
  * Arguments, layouts and the other errors as mof_apply_flowT. */
-#define MOF_FLOWT_NOALLOC_MAX_RADII (1 << 20)
+#define MOF_FLOWT_NOALLOC_MAX_INTS (1 << 22)
 mof_status mof_apply_flowT_noalloc(mof_problem *p, const void *r, const void *s, const void *sr,
                                    void *u, void *stream);
 

@@ -363,12 +363,12 @@ mof_status mof_apply_flowT(mof_problem *p, const void *r, const void *s, const v
     if (!u || !s || !sr || !r) return fail(MOF_EINVAL, "null array");
     void *rad = nullptr;
     MOF_TRY(apply_scratch(p, SCR_RADIUS, &rad));
-    int *rs = (int *)rad, *rr = rs + (long long)(p->nt - 1) * tiles_count(p);
+    int *rs = (int *)rad, *rr = rs + (long long)(p->nt - 1) * tile_bound_ints(p);
     if (p->precision == MOF_FP64) {
-        MOF_TRY(launch_tile_radii<double>(p, CD(s), CD(sr), rs, rr, S(stream)));
+        MOF_TRY(launch_tile_bounds<double>(p, CD(s), CD(sr), rs, rr, S(stream)));
         return launch_flowT<double>(p, CD(r), CD(s), CD(sr), rs, rr, D(u), S(stream));
     }
-    MOF_TRY(launch_tile_radii<float>(p, CF(s), CF(sr), rs, rr, S(stream)));
+    MOF_TRY(launch_tile_bounds<float>(p, CF(s), CF(sr), rs, rr, S(stream)));
     return launch_flowT<float>(p, CF(r), CF(s), CF(sr), rs, rr, F(u), S(stream));
 }
 
@@ -381,10 +381,11 @@ mof_status mof_apply_flow_ds(mof_problem *p, const void *u, const void *s, const
                     launch_flow_ds<double>(p, CD(u), CD(s), CD(sr), CD(gr), D(gs), D(gsr), S(stream)));
 }
 
-// Allocation-free Mhat^T: the tile radii live in a fixed device array
-// instead of the problem's lazily allocated workspace (include/mof.h states
-// the size limit, the one-time set-up and the concurrency rule).
-static __device__ __align__(256) int g_flowT_noalloc_radii[MOF_FLOWT_NOALLOC_MAX_RADII];
+// Allocation-free Mhat^T: the per-tile displacement bounds of the gathers live
+// in a fixed device array instead of the problem's lazily allocated workspace
+// (include/mof.h states the size limit, the one-time set-up and the
+// concurrency rule).
+static __device__ __align__(256) int g_flowT_noalloc_bounds[MOF_FLOWT_NOALLOC_MAX_INTS];
 
 static mof_status flowT_noalloc_scratch(const mof_problem *p, int **out) {
     constexpr int MAX_DEVICES = 64;
@@ -392,14 +393,16 @@ static mof_status flowT_noalloc_scratch(const mof_problem *p, int **out) {
     static int *addr[MAX_DEVICES] = {};
     if (p->device < 0 || p->device >= MAX_DEVICES)
         return fail(MOF_EUNSUPPORTED, "device ordinal %d is outside the supported range", p->device);
+    // every call runs with the problem's device current: the kernels are launched on the
+    // current device, and the cached address belongs to the problem's device
+    int cur = -1;
+    MOF_CUDA(cudaGetDevice(&cur));
+    if (cur != p->device)
+        return fail(MOF_EINVAL, "problem on device %d, called with device %d current", p->device, cur);
     std::lock_guard<std::mutex> lock(mu);
     if (!addr[p->device]) {  // one-time set-up on this device
-        int cur = -1;
-        MOF_CUDA(cudaGetDevice(&cur));
-        if (cur != p->device)
-            return fail(MOF_EINVAL, "first call on device %d made with device %d current", p->device, cur);
         void *a = nullptr;
-        MOF_CUDA(cudaGetSymbolAddress(&a, g_flowT_noalloc_radii));
+        MOF_CUDA(cudaGetSymbolAddress(&a, g_flowT_noalloc_bounds));
         addr[p->device] = static_cast<int *>(a);
     }
     *out = addr[p->device];
@@ -410,20 +413,20 @@ mof_status mof_apply_flowT_noalloc(mof_problem *p, const void *r, const void *s,
     g_err[0] = 0;
     MOF_TRY(check_problem(p));
     if (!u || !s || !sr || !r) return fail(MOF_EINVAL, "null array");
-    const long long need = 2LL * (p->nt - 1) * tiles_count(p);
-    if (need > MOF_FLOWT_NOALLOC_MAX_RADII)
+    const long long need = 2LL * (p->nt - 1) * tile_bound_ints(p);
+    if (need > MOF_FLOWT_NOALLOC_MAX_INTS)
         return fail(MOF_EUNSUPPORTED,
-                    "mof_apply_flowT_noalloc: the problem needs %lld tile radii, more than the fixed %d "
+                    "mof_apply_flowT_noalloc: the problem needs %lld ints of tile bounds, more than the fixed %d "
                     "(use mof_apply_flowT)",
-                    need, MOF_FLOWT_NOALLOC_MAX_RADII);
+                    need, MOF_FLOWT_NOALLOC_MAX_INTS);
     int *rad = nullptr;
     MOF_TRY(flowT_noalloc_scratch(p, &rad));
-    int *rs = rad, *rr = rad + (long long)(p->nt - 1) * tiles_count(p);
+    int *rs = rad, *rr = rad + (long long)(p->nt - 1) * tile_bound_ints(p);
     if (p->precision == MOF_FP64) {
-        MOF_TRY(launch_tile_radii<double>(p, CD(s), CD(sr), rs, rr, S(stream)));
+        MOF_TRY(launch_tile_bounds<double>(p, CD(s), CD(sr), rs, rr, S(stream)));
         return launch_flowT<double>(p, CD(r), CD(s), CD(sr), rs, rr, D(u), S(stream));
     }
-    MOF_TRY(launch_tile_radii<float>(p, CF(s), CF(sr), rs, rr, S(stream)));
+    MOF_TRY(launch_tile_bounds<float>(p, CF(s), CF(sr), rs, rr, S(stream)));
     return launch_flowT<float>(p, CF(r), CF(s), CF(sr), rs, rr, F(u), S(stream));
 }
 
@@ -511,13 +514,13 @@ mof_status mof_apply_reg_normal(mof_problem *p, const void *x, const void *uk, c
     void *rad = nullptr, *q = nullptr;
     MOF_TRY(apply_scratch(p, SCR_RADIUS, &rad));
     MOF_TRY(apply_scratch(p, SCR_FLOWROWS, &q));
-    int *rs = (int *)rad, *rr = rs + (long long)(p->nt - 1) * tiles_count(p);
+    int *rs = (int *)rad, *rr = rs + (long long)(p->nt - 1) * tile_bound_ints(p);
     if (p->precision == MOF_FP64) {
-        MOF_TRY(launch_tile_radii<double>(p, CD(s), CD(sr), rs, rr, S(stream)));
+        MOF_TRY(launch_tile_bounds<double>(p, CD(s), CD(sr), rs, rr, S(stream)));
         return launch_reg_normal<double>(p, 0, CD(x), CD(uk), CD(s), CD(sr), rs, rr, eps, 1.0, nullptr, nullptr, D(q), D(y),
                                          S(stream));
     }
-    MOF_TRY(launch_tile_radii<float>(p, CF(s), CF(sr), rs, rr, S(stream)));
+    MOF_TRY(launch_tile_bounds<float>(p, CF(s), CF(sr), rs, rr, S(stream)));
     return launch_reg_normal<float>(p, 0, CF(x), CF(uk), CF(s), CF(sr), rs, rr, eps, 1.0, nullptr, nullptr, F(q), F(y),
                                     S(stream));
 }

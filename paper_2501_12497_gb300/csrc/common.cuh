@@ -127,10 +127,12 @@ template <typename real> mof_status launch_gradT(const mof_problem *p, int nf, c
 template <typename real> mof_status launch_flow(const mof_problem *p, const real *u, const real *s, const real *sr, real *r, cudaStream_t st);
 // Velocity VJP of Mhat(s, s') u: gs, gsr = (d r / d s)^T gr, (d r / d s')^T gr.
 template <typename real> mof_status launch_flow_ds(const mof_problem *p, const real *u, const real *s, const real *sr, const real *gr, real *gs, real *gsr, cudaStream_t st);
-// Per-tile gather radii of the warp transposes (rad_* hold (nt-1) * tiles_count ints).
+// Per-tile displacement bounds of the warp transposes' gathers: bnd_* hold
+// (nt-1) * tile_bound_ints ints (4 per 32x8 tile, 16-byte aligned).
 int tiles_count(const mof_problem *p);
-template <typename real> mof_status launch_tile_radii(const mof_problem *p, const real *s, const real *sr, int *rad_s, int *rad_sr, cudaStream_t st);
-template <typename real> mof_status launch_flowT(const mof_problem *p, const real *r, const real *s, const real *sr, const int *rad_s, const int *rad_sr, real *u, cudaStream_t st);
+long long tile_bound_ints(const mof_problem *p);
+template <typename real> mof_status launch_tile_bounds(const mof_problem *p, const real *s, const real *sr, int *bnd_s, int *bnd_sr, cudaStream_t st);
+template <typename real> mof_status launch_flowT(const mof_problem *p, const real *r, const real *s, const real *sr, const int *bnd_s, const int *bnd_sr, real *u, cudaStream_t st);
 template <typename real> mof_status launch_of_fields(const mof_problem *p, const real *u, int dr, real *ux, real *uy, real *ut, cudaStream_t st);
 // Rescaling for Solve-OF (Sec. 4.1.5): uc = a x a block means of every frame of u;
 // s = a * bilinear interpolation of the coarse velocities sc at the fine pixel centres.
@@ -138,13 +140,13 @@ template <typename real> mof_status launch_downsample(const mof_problem *p, int 
 template <typename real> mof_status launch_upsample_velocity(const mof_problem *p, int a, const real *sc, real *s, cudaStream_t st);
 template <typename real> mof_status launch_flow_lin(const mof_problem *p, const real *ux, const real *uy, const real *ut, const real *s, real *r, cudaStream_t st);
 template <typename real> mof_status launch_flow_linT(const mof_problem *p, const real *ux, const real *uy, const real *r, real *gs, cudaStream_t st);
-template <typename real> mof_status launch_reverse_flow(const mof_problem *p, const real *s, int *rad_scratch, int *dest_scratch, real *sr, cudaStream_t st);
+template <typename real> mof_status launch_reverse_flow(const mof_problem *p, const real *s, int *bnd_scratch, int *dest_scratch, real *sr, cudaStream_t st);
 // Weighted regulariser normal operator: y = y_add + scale * Theta^T W Theta x,
 // W from uk; q_scratch holds 2*(nt-1)*ns weighted flow rows. lam_dev (may be
 // null) multiplies `scale` by *lam_dev.
 // temporal: 1 adds L_t^T w_t L_t x (the temporal differences of D1-OF), 0 is M-OF
 template <typename real> mof_status launch_reg_normal(const mof_problem *p, int temporal, const real *x, const real *uk, const real *s, const real *sr,
-                                                      const int *rad_s, const int *rad_sr, double eps, double scale, const double *lam_dev,
+                                                      const int *bnd_s, const int *bnd_sr, double eps, double scale, const double *lam_dev,
                                                       const real *y_add, real *q_scratch, real *y, cudaStream_t st);
 
 // ----------------------------------------------------------- device helpers

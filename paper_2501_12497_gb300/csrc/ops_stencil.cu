@@ -8,11 +8,14 @@
 //
 // The transposes of the warp (and the reverse flow) are computed as
 // deterministic gathers: an output pixel q collects the contributions of the
-// sources p within a square window around q, in a fixed order, so repeated
-// runs are bit-identical. The window radius is per 32x8 output tile: every
-// source records, in the tile of each pixel it reaches, the Chebyshev
-// distance to that pixel (atomic max), so a tile scans only as far as its
-// farthest actual arrival.
+// sources p within a window around q, in row-major source order, so repeated
+// runs are bit-identical. The window is bounded per 32x8 output tile by the
+// range of the integer displacements of the sources that reach it: every
+// source p records, in each tile its footprint touches, its displacement
+// (x0(p) - px, y0(p) - py) to the first corner of the footprint (integer
+// atomic min and max), so a pixel scans only the sources whose displacement
+// could bring them to it: 2 x 2 positions where the flow is locally constant
+// at the integer level, one more row and column per unit of spread.
 #include "common.cuh"
 
 #include <algorithm>
@@ -75,13 +78,19 @@ __device__ __forceinline__ real warp_weight_to(int px, int py, real vx, real vy,
     return ax * ay;
 }
 
-// (M(v)^T r)(q) by a gather over the window of radius R around q.
+// Per-tile bounds of the integer displacements of the sources that reach a tile:
+// {dxmin, dxmax, dymin, dymax}; an empty tile keeps (BND_EMPTY, -BND_EMPTY, ...),
+// whose window is empty.
+constexpr int BND_EMPTY = 1 << 29;
+
+// (M(v)^T r)(q) by a gather over the sources p whose footprint can contain q:
+// px in [qx - 1 - dxmax, qx - dxmin] (x1(p) is x0(p) or x0(p) + 1), likewise py.
 template <typename real>
 __device__ __forceinline__ real warpT_gather(const real *__restrict__ r, const real *__restrict__ vx,
-                                             const real *__restrict__ vy, int nx, int ny, int qx, int qy, int R, int wm) {
+                                             const real *__restrict__ vy, int nx, int ny, int qx, int qy, int4 bd, int wm) {
     real acc = 0;
-    const int ylo = max(0, qy - R), yhi = min(ny - 1, qy + R);
-    const int xlo = max(0, qx - R), xhi = min(nx - 1, qx + R);
+    const int ylo = max(0, qy - 1 - bd.w), yhi = min(ny - 1, qy - bd.z);
+    const int xlo = max(0, qx - 1 - bd.y), xhi = min(nx - 1, qx - bd.x);
     for (int py = ylo; py <= yhi; ++py) {
         for (int px = xlo; px <= xhi; ++px) {
             const long long i = (long long)py * nx + px;
@@ -120,15 +129,76 @@ __global__ void k_gradT(const real *__restrict__ g, real *__restrict__ u, int nx
     u[t * ns + i] = v;
 }
 
+// FP32 forms with four consecutive pixels per thread (16-byte loads and stores of rows
+// whose length is a multiple of 4, buffers 16-byte aligned): the same subtractions in the
+// same order per pixel as k_grad / k_gradT, so the results are identical.
+constexpr int V4X = 64, V4Y = 4;  // threads per block: 64 x 4 (256 pixels of a row per warp pair)
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+__device__ __forceinline__ float4 ldcs4(const float *p) { return __ldcs(reinterpret_cast<const float4 *>(p)); }
+__device__ __forceinline__ void stcs4(float *p, float4 v) { __stcs(reinterpret_cast<float4 *>(p), v); }
+inline dim3 grid4(int nx, int ny, int nz) { return dim3((nx / 4 + V4X - 1) / V4X, (ny + V4Y - 1) / V4Y, nz); }
+inline bool al16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+__global__ void __launch_bounds__(V4X *V4Y) k_grad4(const float *__restrict__ u, float *__restrict__ g, int nx, int ny) {
+    const int x = 4 * (blockIdx.x * V4X + threadIdx.x), y = blockIdx.y * V4Y + threadIdx.y, t = blockIdx.z;
+    if (x >= nx || y >= ny) return;
+    const long long ns = (long long)nx * ny, i = (long long)y * nx + x;
+    const float *f = u + t * ns;
+    const float4 c = ld4(f + i);
+    const float e = (x + 4 < nx) ? f[i + 4] : 0.f;
+    float4 gx, gy;
+    gx.x = c.y - c.x;
+    gx.y = c.z - c.y;
+    gx.z = c.w - c.z;
+    gx.w = (x + 4 < nx) ? e - c.w : 0.f;
+    if (y < ny - 1) {
+        const float4 d = ld4(f + i + nx);
+        gy = make_float4(d.x - c.x, d.y - c.y, d.z - c.z, d.w - c.w);
+    } else {
+        gy = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    stcs4(g + (2LL * t) * ns + i, gx);
+    stcs4(g + (2LL * t + 1) * ns + i, gy);
+}
+
+__global__ void __launch_bounds__(V4X *V4Y) k_gradT4(const float *__restrict__ g, float *__restrict__ u, int nx, int ny) {
+    const int x = 4 * (blockIdx.x * V4X + threadIdx.x), y = blockIdx.y * V4Y + threadIdx.y, t = blockIdx.z;
+    if (x >= nx || y >= ny) return;
+    const long long ns = (long long)nx * ny, i = (long long)y * nx + x;
+    const float *gx = g + (2LL * t) * ns, *gy = g + (2LL * t + 1) * ns;
+    const float4 a = ld4(gx + i), c = ld4(gy + i);
+    const float al = x > 0 ? gx[i - 1] : 0.f;
+    const float4 cu = y > 0 ? ld4(gy + i - nx) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float gxa[4] = {a.x, a.y, a.z, a.w}, gya[4] = {c.x, c.y, c.z, c.w}, gyu[4] = {cu.x, cu.y, cu.z, cu.w};
+    float o[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float v = 0.f;
+        if (x + k > 0) v += k == 0 ? al : gxa[k - 1];
+        if (x + k < nx - 1) v -= gxa[k];
+        if (y > 0) v += gyu[k];
+        if (y < ny - 1) v -= gya[k];
+        o[k] = v;
+    }
+    stcs4(u + t * ns + i, make_float4(o[0], o[1], o[2], o[3]));
+}
+
 template <typename real>
 mof_status launch_grad(const mof_problem *p, int nf, const real *u, real *g, cudaStream_t st) {
-    ::mof::count_launch(), k_grad<real><<<grid2d(p->nx, p->ny, nf), dim3(TX, TY), 0, st>>>(u, g, p->nx, p->ny);
+    if (sizeof(real) == 4 && p->nx % 4 == 0 && al16(u) && al16(g))
+        ::mof::count_launch(), k_grad4<<<grid4(p->nx, p->ny, nf), dim3(V4X, V4Y), 0, st>>>((const float *)u, (float *)g, p->nx, p->ny);
+    else
+        ::mof::count_launch(), k_grad<real><<<grid2d(p->nx, p->ny, nf), dim3(TX, TY), 0, st>>>(u, g, p->nx, p->ny);
     MOF_LAUNCH_CHECK();
     return MOF_OK;
 }
 template <typename real>
 mof_status launch_gradT(const mof_problem *p, int nf, const real *g, real *u, cudaStream_t st) {
-    ::mof::count_launch(), k_gradT<real><<<grid2d(p->nx, p->ny, nf), dim3(TX, TY), 0, st>>>(g, u, p->nx, p->ny);
+    if (sizeof(real) == 4 && p->nx % 4 == 0 && al16(u) && al16(g))
+        ::mof::count_launch(), k_gradT4<<<grid4(p->nx, p->ny, nf), dim3(V4X, V4Y), 0, st>>>((const float *)g, (float *)u, p->nx, p->ny);
+    else
+        ::mof::count_launch(), k_gradT<real><<<grid2d(p->nx, p->ny, nf), dim3(TX, TY), 0, st>>>(g, u, p->nx, p->ny);
     MOF_LAUNCH_CHECK();
     return MOF_OK;
 }
@@ -146,23 +216,65 @@ __global__ void k_flow(const real *__restrict__ u, const real *__restrict__ s, c
     r[(np + p) * ns + i] = u1[i] - bilinear(u0, nx, ny, x, y, srp[i], srp[ns + i], wm);
 }
 
+// FP32 form of k_flow with four consecutive pixels per thread: the streamed arrays (u_t,
+// u_{t+1}, s, s', both residual rows) move as 16-byte vectors, the bilinear samples are
+// gathered per pixel with the same arithmetic (identical results).
+__global__ void __launch_bounds__(V4X *V4Y) k_flow4(const float *__restrict__ u, const float *__restrict__ s,
+                                                   const float *__restrict__ sr, float *__restrict__ r, int nx, int ny,
+                                                   int np, int wm) {
+    const int x = 4 * (blockIdx.x * V4X + threadIdx.x), y = blockIdx.y * V4Y + threadIdx.y, p = blockIdx.z;
+    if (x >= nx || y >= ny) return;
+    const long long ns = (long long)nx * ny, i = (long long)y * nx + x;
+    const float *u0 = u + p * ns, *u1 = u0 + ns;
+    const float *sp = s + 2LL * p * ns, *srp = sr + 2LL * p * ns;
+    const float4 a0 = ld4(u0 + i), a1 = ld4(u1 + i);
+    const float4 svx = ldcs4(sp + i), svy = ldcs4(sp + ns + i), rvx = ldcs4(srp + i), rvy = ldcs4(srp + ns + i);
+    const float A0[4] = {a0.x, a0.y, a0.z, a0.w}, A1[4] = {a1.x, a1.y, a1.z, a1.w};
+    const float SX[4] = {svx.x, svx.y, svx.z, svx.w}, SY[4] = {svy.x, svy.y, svy.z, svy.w};
+    const float RX[4] = {rvx.x, rvx.y, rvx.z, rvx.w}, RY[4] = {rvy.x, rvy.y, rvy.z, rvy.w};
+    float f[4], b[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        f[k] = A0[k] - bilinear(u1, nx, ny, x + k, y, SX[k], SY[k], wm);
+        b[k] = A1[k] - bilinear(u0, nx, ny, x + k, y, RX[k], RY[k], wm);
+    }
+    stcs4(r + p * ns + i, make_float4(f[0], f[1], f[2], f[3]));
+    stcs4(r + (np + p) * ns + i, make_float4(b[0], b[1], b[2], b[3]));
+}
+
 template <typename real>
 mof_status launch_flow(const mof_problem *p, const real *u, const real *s, const real *sr, real *r, cudaStream_t st) {
     const int np = p->nt - 1;
-    ::mof::count_launch(), k_flow<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(u, s, sr, r, p->nx, p->ny, np, p->warp_mode);
+    if (np <= 0) return MOF_OK;
+    if (sizeof(real) == 4 && p->nx % 4 == 0 && al16(u) && al16(s) && al16(sr) && al16(r))
+        ::mof::count_launch(), k_flow4<<<grid4(p->nx, p->ny, np), dim3(V4X, V4Y), 0, st>>>(
+            (const float *)u, (const float *)s, (const float *)sr, (float *)r, p->nx, p->ny, np, p->warp_mode);
+    else
+        ::mof::count_launch(), k_flow<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(u, s, sr, r, p->nx, p->ny, np, p->warp_mode);
     MOF_LAUNCH_CHECK();
     return MOF_OK;
 }
 
-// Per-tile gather radii of M(v)^T for nf velocity fields v[f] (each [2][ny][nx]):
-// rad[f][tile] = max over sources p and the pixels q of their bilinear
-// footprint, q in the tile, of |p - q|_inf. Launched with the gather tiling.
+// Per-tile displacement bounds of M(v)^T for nf velocity fields v[f] (each [2][ny][nx]):
+// bnd[f][tile] = {min, max} of x0(p) - px and of y0(p) - py over the sources p whose
+// bilinear footprint {x0, x1} x {y0, y1} touches the tile (integer atomics: exact and
+// order independent). Launched with the gather tiling; bounds of the block's own tile
+// are reduced in shared memory first.
+__device__ __forceinline__ void bnd_update(int *b, int dx, int dy) {
+    atomicMin(b + 0, dx);
+    atomicMax(b + 1, dx);
+    atomicMin(b + 2, dy);
+    atomicMax(b + 3, dy);
+}
+
 template <typename real>
-__global__ void k_tile_radius(const real *__restrict__ v, int nx, int ny, int *__restrict__ rad, int tiles_x, int tiles, int wm) {
-    __shared__ int own;
+__global__ void k_tile_bounds(const real *__restrict__ v, int nx, int ny, int *__restrict__ bnd, int tiles_x, int tiles, int wm) {
+    __shared__ int own[4];
     const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, f = blockIdx.z;
     const int tid = threadIdx.y * TX + threadIdx.x;
-    if (tid == 0) own = 0;
+    if (tid == 0) {
+        own[0] = BND_EMPTY; own[1] = -BND_EMPTY; own[2] = BND_EMPTY; own[3] = -BND_EMPTY;
+    }
     __syncthreads();
     if (x < nx && y < ny) {
         const long long ns = (long long)nx * ny, i = (long long)y * nx + x;
@@ -171,19 +283,33 @@ __global__ void k_tile_radius(const real *__restrict__ v, int nx, int ny, int *_
         real wx, wy;
         warp_axis(x, vf[i], nx, x0, x1, wx, wm);
         warp_axis(y, vf[ns + i], ny, y0, y1, wy, wm);
-        const int qx[2] = {x0, x1}, qy[2] = {y0, y1};
+        const int dx = x0 - x, dy = y0 - y;
+        const int tx0 = x0 / TX, tx1 = x1 / TX, ty0 = y0 / TY, ty1 = y1 / TY;
 #pragma unroll
-        for (int a = 0; a < 2; ++a)
+        for (int a = 0; a < 2; ++a) {
+            if (a == 1 && tx1 == tx0) break;
+            const int tx = a ? tx1 : tx0;
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
-                const int d = max(abs(qx[a] - x), abs(qy[c] - y));
-                const int tx = qx[a] / TX, ty = qy[c] / TY;
-                if (tx == (int)blockIdx.x && ty == (int)blockIdx.y) atomicMax(&own, d);
-                else atomicMax(&rad[(long long)f * tiles + ty * tiles_x + tx], d);
+                if (c == 1 && ty1 == ty0) break;
+                const int ty = c ? ty1 : ty0;
+                if (tx == (int)blockIdx.x && ty == (int)blockIdx.y) bnd_update(own, dx, dy);
+                else bnd_update(bnd + 4 * ((long long)f * tiles + ty * tiles_x + tx), dx, dy);
             }
+        }
     }
     __syncthreads();
-    if (tid == 0) atomicMax(&rad[(long long)f * tiles + blockIdx.y * tiles_x + blockIdx.x], own);
+    if (tid == 0 && own[0] != BND_EMPTY) {
+        int *b = bnd + 4 * ((long long)f * tiles + blockIdx.y * tiles_x + blockIdx.x);
+        bnd_update(b, own[0], own[2]);
+        bnd_update(b, own[1], own[3]);
+    }
+}
+
+// every tile's bounds to the empty window
+__global__ void k_bounds_empty(int *p, long long ntiles) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ntiles; i += (long long)gridDim.x * blockDim.x)
+        reinterpret_cast<int4 *>(p)[i] = make_int4(BND_EMPTY, -BND_EMPTY, BND_EMPTY, -BND_EMPTY);
 }
 
 __global__ void k_zero_ints(int *p, long long n) {
@@ -192,18 +318,22 @@ __global__ void k_zero_ints(int *p, long long n) {
 
 int tiles_x(const mof_problem *p) { return (p->nx + TX - 1) / TX; }
 int tiles_count(const mof_problem *p) { return tiles_x(p) * ((p->ny + TY - 1) / TY); }
+long long tile_bound_ints(const mof_problem *p) { return 4LL * tiles_count(p); }
+
+static int bounds_blocks(long long ntiles) { return (int)std::min<long long>(152 * 4, (ntiles + 255) / 256); }
 
 template <typename real>
-mof_status launch_tile_radii(const mof_problem *p, const real *s, const real *sr, int *rad_s, int *rad_sr, cudaStream_t st) {
+mof_status launch_tile_bounds(const mof_problem *p, const real *s, const real *sr, int *bnd_s, int *bnd_sr, cudaStream_t st) {
     const int np = p->nt - 1, tiles = tiles_count(p);
-    ::mof::count_launch(), k_zero_ints<<<8, 256, 0, st>>>(rad_s, (long long)np * tiles);
+    if (np <= 0) return MOF_OK;
+    ::mof::count_launch(), k_bounds_empty<<<bounds_blocks((long long)np * tiles), 256, 0, st>>>(bnd_s, (long long)np * tiles);
     MOF_LAUNCH_CHECK();
-    ::mof::count_launch(), k_tile_radius<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(s, p->nx, p->ny, rad_s, tiles_x(p), tiles, p->warp_mode);
+    ::mof::count_launch(), k_tile_bounds<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(s, p->nx, p->ny, bnd_s, tiles_x(p), tiles, p->warp_mode);
     MOF_LAUNCH_CHECK();
     if (sr) {
-        ::mof::count_launch(), k_zero_ints<<<8, 256, 0, st>>>(rad_sr, (long long)np * tiles);
+        ::mof::count_launch(), k_bounds_empty<<<bounds_blocks((long long)np * tiles), 256, 0, st>>>(bnd_sr, (long long)np * tiles);
         MOF_LAUNCH_CHECK();
-        ::mof::count_launch(), k_tile_radius<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(sr, p->nx, p->ny, rad_sr, tiles_x(p), tiles, p->warp_mode);
+        ::mof::count_launch(), k_tile_bounds<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(sr, p->nx, p->ny, bnd_sr, tiles_x(p), tiles, p->warp_mode);
         MOF_LAUNCH_CHECK();
     }
     return MOF_OK;
@@ -213,39 +343,41 @@ mof_status launch_tile_radii(const mof_problem *p, const real *s, const real *sr
 //   u_t = [t<P] r0_t + [t>0] r1_{t-1} - [t<P] M(sr_t)^T r1_t - [t>0] M(s_{t-1})^T r0_{t-1}
 template <typename real>
 __device__ __forceinline__ real flowT_at(const real *__restrict__ r, const real *__restrict__ s, const real *__restrict__ sr,
-                                         int nx, int ny, int np, int t, int x, int y, const int *__restrict__ rad_s,
-                                         const int *__restrict__ rad_sr, int tiles, int tile, int wm) {
+                                         int nx, int ny, int np, int t, int x, int y, const int *__restrict__ bnd_s,
+                                         const int *__restrict__ bnd_sr, int tiles, int tile, int wm) {
     const long long ns = (long long)nx * ny, i = (long long)y * nx + x;
     real v = 0;
     if (t < np) {
         const real *r1 = r + (np + t) * ns;
         const real *srp = sr + 2LL * t * ns;
         v += r[t * ns + i];
-        v -= warpT_gather(r1, srp, srp + ns, nx, ny, x, y, rad_sr[(long long)t * tiles + tile], wm);
+        const int4 bd = __ldg(reinterpret_cast<const int4 *>(bnd_sr) + (long long)t * tiles + tile);
+        v -= warpT_gather(r1, srp, srp + ns, nx, ny, x, y, bd, wm);
     }
     if (t > 0) {
         const real *r0 = r + (long long)(t - 1) * ns;
         const real *sp = s + 2LL * (t - 1) * ns;
         v += r[(np + t - 1) * ns + i];
-        v -= warpT_gather(r0, sp, sp + ns, nx, ny, x, y, rad_s[(long long)(t - 1) * tiles + tile], wm);
+        const int4 bd = __ldg(reinterpret_cast<const int4 *>(bnd_s) + (long long)(t - 1) * tiles + tile);
+        v -= warpT_gather(r0, sp, sp + ns, nx, ny, x, y, bd, wm);
     }
     return v;
 }
 
 template <typename real>
 __global__ void k_flowT(const real *__restrict__ r, const real *__restrict__ s, const real *__restrict__ sr,
-                        const int *__restrict__ rad_s, const int *__restrict__ rad_sr, real *__restrict__ u, int nx, int ny,
+                        const int *__restrict__ bnd_s, const int *__restrict__ bnd_sr, real *__restrict__ u, int nx, int ny,
                         int np, int tiles, int wm) {
     const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, t = blockIdx.z;
     if (x >= nx || y >= ny) return;
     const int tile = blockIdx.y * gridDim.x + blockIdx.x;
-    u[(long long)t * nx * ny + (long long)y * nx + x] = flowT_at(r, s, sr, nx, ny, np, t, x, y, rad_s, rad_sr, tiles, tile, wm);
+    u[(long long)t * nx * ny + (long long)y * nx + x] = flowT_at(r, s, sr, nx, ny, np, t, x, y, bnd_s, bnd_sr, tiles, tile, wm);
 }
 
 template <typename real>
-mof_status launch_flowT(const mof_problem *p, const real *r, const real *s, const real *sr, const int *rad_s,
-                        const int *rad_sr, real *u, cudaStream_t st) {
-    ::mof::count_launch(), k_flowT<real><<<grid2d(p->nx, p->ny, p->nt), dim3(TX, TY), 0, st>>>(r, s, sr, rad_s, rad_sr, u, p->nx, p->ny, p->nt - 1,
+mof_status launch_flowT(const mof_problem *p, const real *r, const real *s, const real *sr, const int *bnd_s,
+                        const int *bnd_sr, real *u, cudaStream_t st) {
+    ::mof::count_launch(), k_flowT<real><<<grid2d(p->nx, p->ny, p->nt), dim3(TX, TY), 0, st>>>(r, s, sr, bnd_s, bnd_sr, u, p->nx, p->ny, p->nt - 1,
                                                                       tiles_count(p), p->warp_mode);
     MOF_LAUNCH_CHECK();
     return MOF_OK;
@@ -332,41 +464,48 @@ __device__ __forceinline__ int round_axis(int x, real v, int n) {
 }
 
 template <typename real>
-__global__ void k_rev_dest(const real *__restrict__ s, int *__restrict__ dest, int *__restrict__ rad, int nx, int ny,
+__global__ void k_rev_dest(const real *__restrict__ s, int *__restrict__ dest, int *__restrict__ bnd, int nx, int ny,
                            int tiles_x, int tiles) {
-    __shared__ int own;
+    __shared__ int own[4];
     const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, p = blockIdx.z;
     const int tid = threadIdx.y * TX + threadIdx.x;
-    if (tid == 0) own = 0;
+    if (tid == 0) {
+        own[0] = BND_EMPTY; own[1] = -BND_EMPTY; own[2] = BND_EMPTY; own[3] = -BND_EMPTY;
+    }
     __syncthreads();
     if (x < nx && y < ny) {
         const long long ns = (long long)nx * ny, i = (long long)y * nx + x;
         const real *sp = s + 2LL * p * ns;
         const int dx = round_axis(x, sp[i], nx), dy = round_axis(y, sp[ns + i], ny);
         dest[p * ns + i] = dy * nx + dx;
-        const int d = max(abs(dx - x), abs(dy - y));
         const int tx = dx / TX, ty = dy / TY;
-        if (tx == (int)blockIdx.x && ty == (int)blockIdx.y) atomicMax(&own, d);
-        else atomicMax(&rad[(long long)p * tiles + ty * tiles_x + tx], d);
+        if (tx == (int)blockIdx.x && ty == (int)blockIdx.y) bnd_update(own, dx - x, dy - y);
+        else bnd_update(bnd + 4 * ((long long)p * tiles + ty * tiles_x + tx), dx - x, dy - y);
     }
     __syncthreads();
-    if (tid == 0) atomicMax(&rad[(long long)p * tiles + blockIdx.y * tiles_x + blockIdx.x], own);
+    if (tid == 0 && own[0] != BND_EMPTY) {
+        int *b = bnd + 4 * ((long long)p * tiles + blockIdx.y * tiles_x + blockIdx.x);
+        bnd_update(b, own[0], own[2]);
+        bnd_update(b, own[1], own[3]);
+    }
 }
 
+// s'(q) = -(mean of s(p) over the sources p with dest(p) = q), sources in row-major
+// order within the window px in [qx - dxmax, qx - dxmin], py likewise (the tile's bounds)
 template <typename real>
-__global__ void k_rev_gather(const real *__restrict__ s, const int *__restrict__ dest, const int *__restrict__ rad,
+__global__ void k_rev_gather(const real *__restrict__ s, const int *__restrict__ dest, const int *__restrict__ bnd,
                              real *__restrict__ sr, int nx, int ny, int tiles) {
     const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, p = blockIdx.z;
     if (x >= nx || y >= ny) return;
     const long long ns = (long long)nx * ny, q = (long long)y * nx + x;
     const real *sx = s + 2LL * p * ns, *sy = sx + ns;
     const int *dp = dest + p * ns;
-    const int R = rad[(long long)p * tiles + blockIdx.y * gridDim.x + blockIdx.x];
+    const int4 bd = __ldg(reinterpret_cast<const int4 *>(bnd) + (long long)p * tiles + blockIdx.y * gridDim.x + blockIdx.x);
     double ax = 0.0, ay = 0.0;
     int cnt = 0;
     // sources in row-major order, as the arrivals are accumulated in order of source
-    const int ylo = max(0, y - R), yhi = min(ny - 1, y + R);
-    const int xlo = max(0, x - R), xhi = min(nx - 1, x + R);
+    const int ylo = max(0, y - bd.w), yhi = min(ny - 1, y - bd.z);
+    const int xlo = max(0, x - bd.y), xhi = min(nx - 1, x - bd.x);
     for (int py = ylo; py <= yhi; ++py)
         for (int px = xlo; px <= xhi; ++px) {
             const long long i = (long long)py * nx + px;
@@ -382,13 +521,14 @@ __global__ void k_rev_gather(const real *__restrict__ s, const int *__restrict__
 }
 
 template <typename real>
-mof_status launch_reverse_flow(const mof_problem *p, const real *s, int *rad, int *dest, real *sr, cudaStream_t st) {
+mof_status launch_reverse_flow(const mof_problem *p, const real *s, int *bnd, int *dest, real *sr, cudaStream_t st) {
     const int np = p->nt - 1, tiles = tiles_count(p);
-    ::mof::count_launch(), k_zero_ints<<<8, 256, 0, st>>>(rad, (long long)np * tiles);
+    if (np <= 0) return MOF_OK;
+    ::mof::count_launch(), k_bounds_empty<<<bounds_blocks((long long)np * tiles), 256, 0, st>>>(bnd, (long long)np * tiles);
     MOF_LAUNCH_CHECK();
-    ::mof::count_launch(), k_rev_dest<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(s, dest, rad, p->nx, p->ny, tiles_x(p), tiles);
+    ::mof::count_launch(), k_rev_dest<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(s, dest, bnd, p->nx, p->ny, tiles_x(p), tiles);
     MOF_LAUNCH_CHECK();
-    ::mof::count_launch(), k_rev_gather<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(s, dest, rad, sr, p->nx, p->ny, tiles);
+    ::mof::count_launch(), k_rev_gather<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(s, dest, bnd, sr, p->nx, p->ny, tiles);
     MOF_LAUNCH_CHECK();
     return MOF_OK;
 }
@@ -428,9 +568,67 @@ __global__ void k_of_fields(const real *__restrict__ u, int dr, real *__restrict
     ut[i] = st / (box * box);
 }
 
+// The same fields from shared-memory tiles: a CTA owns a 32 x 8 tile of every pair and
+// walks the frames in order, so each frame's tile (with its reflected halo of DR pixels)
+// is loaded once and serves as frame t + 1 of pair t and frame t of pair t + 1; the sums
+// take the terms in the order of k_of_fields (identical results).
+template <typename real, int DR>
+__global__ void __launch_bounds__(TX *TY) k_of_fields_tiled(const real *__restrict__ u, real *__restrict__ ux,
+                                                             real *__restrict__ uy, real *__restrict__ ut, int nx, int ny,
+                                                             int np) {
+    constexpr int W = TX + 2 * DR, H = TY + 2 * DR;
+    __shared__ real tile[2][H][W];
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    const long long ns = (long long)nx * ny;
+    const real inv2 = (real)1 / (real)(2 * DR), box = (real)(2 * DR + 1);
+    auto load = [&](int buf, int t) {
+        const real *f = u + (long long)t * ns;
+        for (int q = tid; q < W * H; q += TX * TY) {
+            const int ly = q / W, lx = q - ly * W;
+            const int gy = reflect_idx(y0 + ly - DR, ny), gx = reflect_idx(x0 + lx - DR, nx);
+            tile[buf][ly][lx] = ldg(f + (long long)gy * nx + gx);
+        }
+    };
+    load(0, 0);
+    for (int p = 0; p < np; ++p) {
+        const int ca = p & 1, cb = ca ^ 1;
+        load(cb, p + 1);
+        __syncthreads();
+        if (x < nx && y < ny) {
+            const int lx = threadIdx.x + DR, ly = threadIdx.y + DR;
+            // the reflected neighbours of k_of_fields, as offsets in the halo tile
+            real sx = 0, sy = 0, st = 0;
+#pragma unroll
+            for (int k = -DR; k <= DR; ++k) {
+                sx += (tile[ca][ly + k][lx + DR] - tile[ca][ly + k][lx - DR]) * inv2;
+                sy += (tile[ca][ly + DR][lx + k] - tile[ca][ly - DR][lx + k]) * inv2;
+#pragma unroll
+                for (int j = -DR; j <= DR; ++j) st += tile[cb][ly + k][lx + j] - tile[ca][ly + k][lx + j];
+            }
+            const long long i = p * ns + (long long)y * nx + x;
+            ux[i] = sx / box;
+            uy[i] = sy / box;
+            ut[i] = st / (box * box);
+        }
+        __syncthreads();
+    }
+}
+
 template <typename real>
 mof_status launch_of_fields(const mof_problem *p, const real *u, int dr, real *ux, real *uy, real *ut, cudaStream_t st) {
-    ::mof::count_launch(), k_of_fields<real><<<grid2d(p->nx, p->ny, p->nt - 1), dim3(TX, TY), 0, st>>>(u, dr, ux, uy, ut, p->nx, p->ny);
+    const int np = p->nt - 1;
+    if (np <= 0) return MOF_OK;
+    // each halo element is the reflected pixel of its own coordinate, as in k_of_fields
+    if (dr == 1)
+        ::mof::count_launch(), k_of_fields_tiled<real, 1><<<dim3((p->nx + TX - 1) / TX, (p->ny + TY - 1) / TY), dim3(TX, TY), 0, st>>>(
+            u, ux, uy, ut, p->nx, p->ny, np);
+    else if (dr == 2)
+        ::mof::count_launch(), k_of_fields_tiled<real, 2><<<dim3((p->nx + TX - 1) / TX, (p->ny + TY - 1) / TY), dim3(TX, TY), 0, st>>>(
+            u, ux, uy, ut, p->nx, p->ny, np);
+    else
+        ::mof::count_launch(), k_of_fields<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(u, dr, ux, uy, ut, p->nx, p->ny);
     MOF_LAUNCH_CHECK();
     return MOF_OK;
 }
@@ -496,8 +694,8 @@ __global__ void k_regn_flow_rows(const real *__restrict__ x, const real *__restr
 // Stage 2: y = y_add + scale * (Psi^T W_Psi Psi x + Mhat^T q).
 template <typename real>
 __global__ void k_regn_apply(const real *__restrict__ x, const real *__restrict__ uk, const real *__restrict__ s,
-                             const real *__restrict__ sr, const real *__restrict__ q, const int *__restrict__ rad_s,
-                             const int *__restrict__ rad_sr, int tiles, real eps2, double scale,
+                             const real *__restrict__ sr, const real *__restrict__ q, const int *__restrict__ bnd_s,
+                             const int *__restrict__ bnd_sr, int tiles, real eps2, double scale,
                              const double *__restrict__ lam, const real *__restrict__ y_add, real *__restrict__ y, int nx,
                              int ny, int np, int temporal, int wm) {
     const int xx = blockIdx.x * TX + threadIdx.x, yy = blockIdx.y * TY + threadIdx.y, t = blockIdx.z;
@@ -529,14 +727,14 @@ __global__ void k_regn_apply(const real *__restrict__ x, const real *__restrict_
         if (t > 0) v += wdt(f - ns, k - ns);
         if (t < np) v -= wdt(f, k);
     }
-    if (np > 0) v += flowT_at(q, s, sr, nx, ny, np, t, xx, yy, rad_s, rad_sr, tiles, blockIdx.y * gridDim.x + blockIdx.x, wm);
+    if (np > 0) v += flowT_at(q, s, sr, nx, ny, np, t, xx, yy, bnd_s, bnd_sr, tiles, blockIdx.y * gridDim.x + blockIdx.x, wm);
     const real out = s_sc * v;
     y[t * ns + i] = y_add ? y_add[t * ns + i] + out : out;
 }
 
 template <typename real>
 mof_status launch_reg_normal(const mof_problem *p, int temporal, const real *x, const real *uk, const real *s, const real *sr,
-                             const int *rad_s, const int *rad_sr, double eps, double scale, const double *lam_dev,
+                             const int *bnd_s, const int *bnd_sr, double eps, double scale, const double *lam_dev,
                              const real *y_add, real *q, real *y, cudaStream_t st) {
     const int np = p->nt - 1;
     const real eps2 = (real)(eps * eps);
@@ -544,7 +742,7 @@ mof_status launch_reg_normal(const mof_problem *p, int temporal, const real *x, 
         ::mof::count_launch(), k_regn_flow_rows<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(x, uk, s, sr, eps2, q, p->nx, p->ny, np, p->warp_mode);
         MOF_LAUNCH_CHECK();
     }
-    ::mof::count_launch(), k_regn_apply<real><<<grid2d(p->nx, p->ny, p->nt), dim3(TX, TY), 0, st>>>(x, uk, s, sr, q, rad_s, rad_sr, tiles_count(p),
+    ::mof::count_launch(), k_regn_apply<real><<<grid2d(p->nx, p->ny, p->nt), dim3(TX, TY), 0, st>>>(x, uk, s, sr, q, bnd_s, bnd_sr, tiles_count(p),
                                                                             eps2, scale, lam_dev, y_add, y, p->nx, p->ny, np, temporal,
                                                                             p->warp_mode);
     MOF_LAUNCH_CHECK();
@@ -555,7 +753,7 @@ mof_status launch_reg_normal(const mof_problem *p, int temporal, const real *x, 
     template mof_status launch_grad<real>(const mof_problem *, int, const real *, real *, cudaStream_t);                      \
     template mof_status launch_gradT<real>(const mof_problem *, int, const real *, real *, cudaStream_t);                     \
     template mof_status launch_flow<real>(const mof_problem *, const real *, const real *, const real *, real *, cudaStream_t); \
-    template mof_status launch_tile_radii<real>(const mof_problem *, const real *, const real *, int *, int *, cudaStream_t);  \
+    template mof_status launch_tile_bounds<real>(const mof_problem *, const real *, const real *, int *, int *, cudaStream_t); \
     template mof_status launch_flow_ds<real>(const mof_problem *, const real *, const real *, const real *, const real *,      \
                                              real *, real *, cudaStream_t);                                                   \
     template mof_status launch_flowT<real>(const mof_problem *, const real *, const real *, const real *, const int *,         \

@@ -243,7 +243,7 @@ mof_status apply_scratch(mof_problem *p, ScratchKind kind, void **out) {
         size_t bytes = 0;
         switch (kind) {
             case SCR_IMAGE: bytes = es * p->n; break;
-            case SCR_RADIUS: bytes = sizeof(int) * (2 * (size_t)(p->nt - 1) * tiles_count(p) + 16); break;
+            case SCR_RADIUS: bytes = sizeof(int) * (2 * (size_t)(p->nt - 1) * tile_bound_ints(p) + 16); break;
             case SCR_DEST: bytes = sizeof(int) * (p->nt - 1) * p->ns; break;
             case SCR_FLOWROWS: bytes = es * 2 * (p->nt - 1) * p->ns; break;
             default: return fail(MOF_EINVAL, "bad scratch kind");
@@ -346,10 +346,10 @@ static mof_status ensure_ws(mof_problem *p, const mof_solver_params &prm, int n_
         w->sr = a.take<real>(P * N2);
         w->vnew = a.take<real>(n);
         w->hvnew = a.take<real>(m);
-        const long long tiles = (long long)tiles_count(p) * P;
-        w->rad_s = a.take<int>(tiles);
-        w->rad_sr = a.take<int>(tiles);
-        w->rad_rev = a.take<int>(tiles);
+        const long long bints = tile_bound_ints(p) * P;
+        w->rad_s = a.take<int>(bints);
+        w->rad_sr = a.take<int>(bints);
+        w->rad_rev = a.take<int>(bints);
         w->dest = a.take<int>(P * ns);
         w->GH = a.take<double>((size_t)Kmax * Kmax);
         w->GT = a.take<double>((size_t)Kmax * Kmax);
@@ -1638,12 +1638,12 @@ mof_status SolveRun<real>::begin(cudaStream_t ust) {
         ::mof::count_launch(), k_fill<real><<<fb(2 * P * ns), 256, 0, st>>>(w.s, 2 * P * ns, (real)0);
         ::mof::count_launch(), k_fill<real><<<fb(2 * P * ns), 256, 0, st>>>(w.sr, 2 * P * ns, (real)0);
         ::mof::count_launch(), k_copy<real><<<fb(m), 256, 0, st>>>(b_in, w.b, m);
-        MOF_TRY(launch_tile_radii<real>(p, w.s, w.sr, w.rad_s, w.rad_sr, st));
+        MOF_TRY(launch_tile_bounds<real>(p, w.s, w.sr, w.rad_s, w.rad_sr, st));
     }
     // ---- GKB on H from b / ||b|| (Sec. 4.1.1), H V_l = U_{l+1} B_l
     {
         Scope sc(tm, "gkb", st);
-        kr.norm2(w.b, m, m, 1, w.bb, st);
+        kr.norm2(w.b, m, m, 1, w.bb, st, true);  // ||b||^2 enters rho0^2 = ||b||^2 - ||c||^2 of DP
         ::mof::count_launch(), k_sqrt_into<<<1, 1, 0, st>>>(w.bb, w.beta1, 1);
         kr.append(BU, w.KU, w.b, m, w.bb, nullptr, 0.0, w.gkb, nullptr, nullptr, st);
         for (int j = 0; j < prm.ell; ++j) {
@@ -1667,7 +1667,7 @@ mof_status SolveRun<real>::begin(cudaStream_t ust) {
             DotOuts o{};
             o.o[0] = DotOut{w.GH + j, 0, Kmax, 0, 0, 1.0};
             o.o[1] = DotOut{w.gH, 0, 1, 0, 0, 1.0};
-            kr.multidot(BH, 2, xs, o, st);
+            kr.multidot(BH, 2, xs, o, st, true);
         }
     }
     sa = SmallArgs{};
@@ -1734,7 +1734,7 @@ mof_status SolveRun<real>::iteration(bool of_now, bool expand) {
             MOF_TRY(of_step<real>(p, prm, w, w.u, w.s, tm, st));
             Scope sc(tm, "reverse_flow", st);
             MOF_TRY(launch_reverse_flow<real>(p, w.s, w.rad_rev, w.dest, w.sr, st));
-            MOF_TRY(launch_tile_radii<real>(p, w.s, w.sr, w.rad_s, w.rad_sr, st));
+            MOF_TRY(launch_tile_bounds<real>(p, w.s, w.sr, w.rad_s, w.rad_sr, st));
         }
         {
             Scope sc(tm, "theta_gram", st);
@@ -1781,7 +1781,7 @@ mof_status SolveRun<real>::iteration(bool of_now, bool expand) {
                 DotOuts o{};
                 o.o[0] = DotOut{w.GH, 0, Kmax, 1, 1, 1.0};
                 o.o[1] = DotOut{w.gH, 0, 1, 0, 0, 1.0};
-                kr.multidot(BHn, 2, xs, o, st);
+                kr.multidot(BHn, 2, xs, o, st, true);
                 ::mof::count_launch(), k_sym_last<<<1, 64, 0, st>>>(w.GH, Kmax, w.K, w.appended);
             }
         }

@@ -46,13 +46,39 @@ def test_noalloc_flowT_matches_allocating_entry_on_two_calls(prec):
         assert torch.equal(got, want), "call %d differs" % call
 
 
+def _compare_once(p, seed, vmax, dt):
+    nx, ny, nt = p.nx, p.ny, p.nt
+    r = torch.tensor(synth.random_images(2 * (nt - 1), ny, nx, seed=seed), dtype=dt, device="cuda").reshape(-1)
+    s = torch.tensor(synth.random_velocities(nt - 1, ny, nx, vmax=vmax, seed=seed + 10), dtype=dt,
+                     device="cuda").reshape(-1)
+    sr = torch.empty_like(s)
+    api.mof_reverse_flow(p, s, sr)
+    want = torch.empty(p.n, dtype=dt, device="cuda")
+    got = torch.full((p.n,), float("nan"), dtype=dt, device="cuda")
+    api.mof_apply_flowT(p, r, s, sr, want)
+    api.mof_apply_flowT_noalloc(p, r, s, sr, got)
+    torch.cuda.synchronize()
+    return torch.equal(got, want)
+
+
+def test_noalloc_flowT_after_a_larger_problem_used_the_array():
+    """A larger problem (another tile layout, large displacements) fills more of the shared
+    array first; the smaller problem's call that follows must still equal the allocating
+    entry point bit for bit."""
+    big = _problem(160, 96, 6, api.MOF_FP32)
+    small = _problem(70, 45, 5, api.MOF_FP32)
+    assert _compare_once(big, 3, 9.0, torch.float32)
+    assert _compare_once(small, 4, 0.7, torch.float32)
+    assert _compare_once(small, 5, 2.5, torch.float32)
+
+
 def test_noalloc_flowT_rejects_problems_beyond_its_fixed_scratch():
-    # 4096 x 4096 frames: 128 x 512 tiles of 32 x 8 pixels, 2 * 9 * 65536 radii > 2^20
+    # 4096 x 4096 frames: 128 x 512 tiles of 32 x 8 pixels, 8 * 9 * 65536 ints of bounds > 2^22
     p = _problem(4096, 4096, 10, api.MOF_FP32)
     dummy = torch.zeros(16, dtype=torch.float32, device="cuda")
     ptr = ctypes.c_void_p(dummy.data_ptr())
     lib = api.load()
     st = lib.mof_apply_flowT_noalloc(p.handle, ptr, ptr, ptr, ptr, None)
     assert st == api.MOF_EUNSUPPORTED
-    assert b"tile radii" in lib.mof_last_error()
+    assert b"tile bounds" in lib.mof_last_error()
     torch.cuda.synchronize()
