@@ -1,0 +1,91 @@
+"""End-to-end parity of MMGKS-OF on the benchmark configurations: Alg. 1 for 30 outer
+iterations, each with Solve-OF (Alg. 2) of 20 GKS iterations on every frame pair, the
+GPU against the FP64 oracle's stored results (tests/golden/make_oracle_results.py,
+which runs the oracle only).
+
+Bars: FP64 1e-6 and FP32 operators with FP64 Krylov bookkeeping 1e-4, relative, on the
+image sequence u and on the velocities s, both norm-wise and element-wise (the largest
+difference against the largest value of the reference); the per-iteration reports
+(lambda, DP flag, basis size) follow the oracle's.
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2501_12497_gb300 import api, synth
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _solve(w, prec, n_outer=30):
+    p = api.mof_problem_create(w.nx, w.ny, w.nt, w.nb, w.na, w.angles, w.h, w.db, prec)
+    dt = torch.float64 if prec == api.MOF_FP64 else torch.float32
+    prm = api.mof_default_params(noise_norm=w.noise_norm)
+    b = torch.tensor(w.b, dtype=dt, device="cuda")
+    u = torch.empty(p.n, dtype=dt, device="cuda")
+    s = torch.empty(p.nv, dtype=dt, device="cuda")
+    rep = api.mof_solve(p, prm, n_outer, b, u, s)
+    out = u.cpu().double().numpy(), s.cpu().double().numpy(), rep
+    p.close()
+    return out
+
+
+def _errors(got, want):
+    got, want = np.ravel(got), np.ravel(want)
+    norm = np.linalg.norm(got - want) / np.linalg.norm(want)
+    elem = np.max(np.abs(got - want)) / np.max(np.abs(want))
+    return norm, elem
+
+
+def _check_reports(rep, g, lam_tol):
+    for k, r in enumerate(rep):
+        assert r["flag"] == g["flag"][k] and r["basis"] == g["basis"][k], (k, r)
+        assert abs(r["lambda"] / g["lam"][k] - 1) <= lam_tol, (k, r["lambda"], g["lam"][k])
+
+
+@pytest.mark.parametrize("prec,tol", [(api.MOF_FP64, 1e-6), (api.MOF_FP32, 1e-4)])
+def test_disks64x64x8_30_outer_iterations_match_the_oracle(prec, tol):
+    """The plain method's configuration: 64x64 frames, T = 8, 16 angles, 64 bins, two
+    disks at 1 px/frame, 1% noise (FP64 is this configuration's own precision; FP32
+    operators are checked on it as well)."""
+    g = np.load(os.path.join(GOLDEN, "disks64x64x8_oracle_30x20.npz"))
+    w = synth.plain_fp64(0)
+    u, s, rep = _solve(w, prec)
+    eu, eu_el = _errors(u, g["u"])
+    es, es_el = _errors(s, g["s"])
+    print("disks64 prec %d: u %.3g (elem %.3g) s %.3g (elem %.3g)" % (prec, eu, eu_el, es, es_el))
+    assert eu <= tol and eu_el <= tol, (eu, eu_el)
+    assert es <= tol and es_el <= tol, (es, es_el)
+    _check_reports(rep, g, tol)
+
+
+def test_ellipses256x256x32_fp32_30_outer_iterations_match_the_oracle():
+    """The precision form's configuration: 256x256 frames, T = 32, 30 angles rotating across
+    frames, 363 bins, six ellipses in rigid motion, 1% noise; FP32 operators, FP64 Krylov
+    bookkeeping and projected solves. The stored reference holds frames 0, 11, 22, 31 and
+    pairs 0, 10, 20, 30 (and the norms of the whole results)."""
+    path = os.path.join(GOLDEN, "ellipses256x256x32_oracle_30x20_sample.npz")
+    g = np.load(path)
+    w = synth.precision_form(0)
+    u, s, rep = _solve(w, api.MOF_FP32)
+    u = u.reshape(w.nt, w.ny, w.nx)
+    s = s.reshape(w.nt - 1, 2, w.ny, w.nx)
+    eu, eu_el = _errors(u[list(g["frames"])], g["u"])
+    es, es_el = _errors(s[list(g["pairs"])], g["s"])
+    print("ellipses256 fp32: u %.3g (elem %.3g) s %.3g (elem %.3g)" % (eu, eu_el, es, es_el))
+    assert abs(np.linalg.norm(u) / g["u_norm"] - 1) <= 1e-4
+    assert abs(np.linalg.norm(s) / g["s_norm"] - 1) <= 1e-4
+    assert eu <= 1e-4 and eu_el <= 1e-4, (eu, eu_el)
+    assert es <= 1e-4 and es_el <= 1e-4, (es, es_el)
+    _check_reports(rep, g, 1e-4)
