@@ -101,6 +101,13 @@ typedef struct {
                               from the current velocity (zero at the start) every iteration; the
                               subspace stops growing when the orthogonalised residual is at most
                               breakdown_tol times its norm before the orthogonalisation */
+    int plain;             /* execution form (results equal up to rounding): 0 (default) the
+                              batched form, every outer iteration replayed from a CUDA graph and
+                              the frame pairs of Solve-OF in concurrent groups; 1 the plain
+                              unbatched per-frame form, every kernel launched from the host as it
+                              comes, Solve-OF one frame pair after another on one stream and the
+                              projector and its adjoint one frame per launch (the reference point
+                              the batched form is measured against) */
 } mof_solver_params;
 
 /* One record per outer iteration k of mof_solve (host struct). */
@@ -300,6 +307,25 @@ mof_status mof_autotune(mof_problem *const *problems, int count, mof_solver_para
 mof_status mof_set_timing(mof_problem *p, int enable);
 mof_status mof_get_timing(const mof_problem *p, int cap, const char **names, double *ms,
                           long long *launches, int *count);
+
+/* Bound of the device waits on tile copies (library plumbing; the paper has no
+ * counterpart). The fused reorthogonalisation pass stages its tiles with bulk
+ * copies that complete on a shared-memory barrier, and each CTA polls that barrier
+ * at most `polls` times (default 2^22; polls < 0 restores it) before it records a
+ * timeout in the problem's device error word, waits with the default bound for its
+ * own copies to land, and returns; the next synchronising call (the end of
+ * mof_solve, mof_solve_of, ...) returns MOF_ETIMEOUT. Applies to the current device
+ * and to launches made after the call (the device is synchronised first). For tests
+ * of the timeout path: polls = 0 makes every such wait give up at once. */
+mof_status mof_debug_set_wait_limit(long long polls);
+
+/* Measured FP32 ceilings of the current device (library plumbing; the paper has no
+ * counterpart), the roofline of the projector pair, whose Joseph taps are FP32 and
+ * L1-load work rather than DRAM traffic: *fma_tflops the FP32 FMA rate (2 flops per
+ * FMA) of a kernel of independent FMA chains, *l1_gloads_per_s the rate of 4-byte
+ * loads served by L1 (billions per second). Best of five timed launches each; takes
+ * about a second; allocates and frees its own small buffers. */
+mof_status mof_measure_fp32_peaks(double *fma_tflops, double *l1_gloads_per_s);
 
 /* Number of CUDA kernels this library has launched in the process so far
  * (all threads, all problems); differences bracket a region of interest. */

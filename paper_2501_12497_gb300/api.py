@@ -37,7 +37,8 @@ class mof_solver_params(ctypes.Structure):
                 ("of_ell", ctypes.c_int), ("of_dr", ctypes.c_int), ("image_rule", ctypes.c_int),
                 ("eps", ctypes.c_double), ("eta", ctypes.c_double), ("noise_norm", ctypes.c_double),
                 ("lam_fixed", ctypes.c_double), ("breakdown_tol", ctypes.c_double), ("of_streams", ctypes.c_int),
-                ("of_scale", ctypes.c_int), ("temporal_tv", ctypes.c_int), ("of_pq", ctypes.c_int)]
+                ("of_scale", ctypes.c_int), ("temporal_tv", ctypes.c_int), ("of_pq", ctypes.c_int),
+                ("plain", ctypes.c_int)]
 
 
 class mof_report(ctypes.Structure):
@@ -82,6 +83,8 @@ _SIGS = {
     "mof_set_warp": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "mof_get_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_void_p]),
+    "mof_debug_set_wait_limit": (ctypes.c_int, [ctypes.c_longlong]),
+    "mof_measure_fp32_peaks": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "mof_last_error": (ctypes.c_char_p, []),
     "mof_kernel_launches": (ctypes.c_longlong, []),
 }
@@ -400,6 +403,18 @@ def mof_get_timing(p):
     count = ctypes.c_int()
     _check(_lib.mof_get_timing(p.handle, cap, names, ms, cnt, ctypes.byref(count)))
     return {names[i].decode(): (ms[i], cnt[i]) for i in range(min(count.value, cap))}
+
+
+def mof_debug_set_wait_limit(polls):
+    """Bound of the device waits on tile copies (test hook of the timeout path; < 0: default)."""
+    _check(load().mof_debug_set_wait_limit(int(polls)))
+
+
+def mof_measure_fp32_peaks():
+    """(FP32 FMA TFLOP/s, L1 4-byte loads in 1e9/s) measured on the current device."""
+    a, b = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(load().mof_measure_fp32_peaks(ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def mof_last_error():

@@ -189,6 +189,7 @@ void mof_default_params(mof_solver_params *p) {
     p->of_scale = 1;
     p->temporal_tv = 0;
     p->of_pq = 2;
+    p->plain = 0;
 }
 
 mof_status mof_problem_create(const mof_geometry *g, int precision, mof_problem **out) {
@@ -523,6 +524,11 @@ mof_status mof_apply_reg_normal(mof_problem *p, const void *x, const void *uk, c
     MOF_TRY(launch_tile_bounds<float>(p, CF(s), CF(sr), rs, rr, S(stream)));
     return launch_reg_normal<float>(p, 0, CF(x), CF(uk), CF(s), CF(sr), rs, rr, eps, 1.0, nullptr, nullptr, F(q), F(y),
                                     S(stream));
+}
+
+mof_status mof_debug_set_wait_limit(long long polls) {
+    g_err[0] = 0;
+    return set_wait_polls(polls);
 }
 
 mof_status mof_set_timing(mof_problem *p, int enable) {

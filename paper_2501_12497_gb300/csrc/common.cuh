@@ -120,8 +120,9 @@ namespace mof {
 
 // Operator launchers (ops_*.cu). Templated on the element type; `stream` is
 // the caller's stream. All return MOF_OK or a launch error.
-template <typename real> mof_status launch_project(const mof_problem *p, const real *u, real *uT_scratch, real *b, cudaStream_t st);
-template <typename real> mof_status launch_backproject(const mof_problem *p, const real *b, real *u, cudaStream_t st);
+// per_frame: one launch per frame (the plain execution form), else one for the sequence
+template <typename real> mof_status launch_project(const mof_problem *p, const real *u, real *uT_scratch, real *b, cudaStream_t st, bool per_frame = false);
+template <typename real> mof_status launch_backproject(const mof_problem *p, const real *b, real *u, cudaStream_t st, bool per_frame = false);
 template <typename real> mof_status launch_grad(const mof_problem *p, int nf, const real *u, real *g, cudaStream_t st);
 template <typename real> mof_status launch_gradT(const mof_problem *p, int nf, const real *g, real *u, cudaStream_t st);
 template <typename real> mof_status launch_flow(const mof_problem *p, const real *u, const real *s, const real *sr, real *r, cudaStream_t st);
@@ -181,5 +182,33 @@ __device__ __forceinline__ void affine_frac(int ibase, float fbase, float hi, fl
     ifl = ibase + (int)pf + (int)rf;
     frac = r - rf;
 }
+
+// Error-free FP32 accumulation of a dot product ("double-float"): hi + lo carries the
+// running sum with the rounding error of every product (TwoProduct by an FMA) and of
+// every addition (Knuth's TwoSum) kept in lo, so a chunk's partial is accurate to a few
+// units of 2^-48 of the sum of |terms|, independent of cancellation. The _rn intrinsics
+// keep the compiler from contracting or reordering the steps.
+struct DFAcc {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add_prod(float a, float b) {
+        const float p = __fmul_rn(a, b);
+        const float e = __fmaf_rn(a, b, -p);
+        const float s = __fadd_rn(hi, p);
+        const float bp = __fsub_rn(s, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+        hi = s;
+        lo = __fadd_rn(lo, __fadd_rn(err, e));
+    }
+    // add x with its rounding error kept in lo (TwoSum): a running sum of short FP32
+    // partials that does not grow its error with the number of partials
+    __device__ __forceinline__ void add(float x) {
+        const float s = __fadd_rn(hi, x);
+        const float bp = __fsub_rn(s, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+        hi = s;
+        lo = __fadd_rn(lo, err);
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
 
 }  // namespace mof

@@ -42,25 +42,6 @@ __device__ __forceinline__ double block_sum_to_double(acc_t v, double *sh) {
     return r;
 }
 
-// Error-free FP32 accumulation of a dot product ("double-float"): hi + lo carries the
-// running sum with the rounding error of every product (TwoProduct by an FMA) and of
-// every addition (Knuth's TwoSum) kept in lo, so a chunk's partial is accurate to a few
-// units of 2^-48 of the sum of |terms|, independent of cancellation. The _rn intrinsics
-// keep the compiler from contracting or reordering the steps.
-struct DFAcc {
-    float hi = 0.f, lo = 0.f;
-    __device__ __forceinline__ void add_prod(float a, float b) {
-        const float p = __fmul_rn(a, b);
-        const float e = __fmaf_rn(a, b, -p);
-        const float s = __fadd_rn(hi, p);
-        const float bp = __fsub_rn(s, hi);
-        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));
-        hi = s;
-        lo = __fadd_rn(lo, __fadd_rn(err, e));
-    }
-    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
-};
-
 // partial[b][chunk][v][j] = sum_{i in chunk} V[b][j][i] * x_v[b][i], j < K[b], v < NV.
 // EXACT (FP32 data only): error-free accumulation per lane (DFAcc), lanes summed in FP64;
 // used for the Gram matrices whose projected residual subtracts nearly equal terms.
@@ -105,10 +86,10 @@ __global__ void __launch_bounds__(KT) k_mdot(const real *__restrict__ V, long lo
     }
     for (int j = w; j < Kb; j += KT / 32) {
         const real *vj = Vb + (long long)j * N;
-        real a[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) a[v] = 0;
         if constexpr (VEC) {
+            // FP32: each step's 16 products per right-hand side summed in FP32, the steps'
+            // partials accumulated with their rounding errors (DFAcc::add), lanes in FP64
+            DFAcc a[NV];
             const float4 *v4 = reinterpret_cast<const float4 *>(vj);
             const int n4 = len >> 2;
             int i = l;
@@ -119,10 +100,11 @@ __global__ void __launch_bounds__(KT) k_mdot(const real *__restrict__ V, long lo
                 for (int v = 0; v < NV; ++v) {
                     const float4 *x4 = reinterpret_cast<const float4 *>(sx[v]);
                     const float4 y0 = x4[i], y1 = x4[i + 32], y2 = x4[i + 64], y3 = x4[i + 96];
-                    a[v] += q0.x * y0.x + q0.y * y0.y + q0.z * y0.z + q0.w * y0.w;
-                    a[v] += q1.x * y1.x + q1.y * y1.y + q1.z * y1.z + q1.w * y1.w;
-                    a[v] += q2.x * y2.x + q2.y * y2.y + q2.z * y2.z + q2.w * y2.w;
-                    a[v] += q3.x * y3.x + q3.y * y3.y + q3.z * y3.z + q3.w * y3.w;
+                    float t = q0.x * y0.x + q0.y * y0.y + q0.z * y0.z + q0.w * y0.w;
+                    t += q1.x * y1.x + q1.y * y1.y + q1.z * y1.z + q1.w * y1.w;
+                    t += q2.x * y2.x + q2.y * y2.y + q2.z * y2.z + q2.w * y2.w;
+                    t += q3.x * y3.x + q3.y * y3.y + q3.z * y3.z + q3.w * y3.w;
+                    a[v].add(t);
                 }
             }
             for (; i < n4; i += 32) {
@@ -130,22 +112,30 @@ __global__ void __launch_bounds__(KT) k_mdot(const real *__restrict__ V, long lo
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
                     const float4 y = reinterpret_cast<const float4 *>(sx[v])[i];
-                    a[v] += q.x * y.x + q.y * y.y + q.z * y.z + q.w * y.w;
+                    a[v].add(q.x * y.x + q.y * y.y + q.z * y.z + q.w * y.w);
                 }
             }
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const double t = warp_sum(a[v].value());
+                if (l == 0) partial[(((long long)b * nchunk + chunk) * NV + v) * Kmax + j] = t;
+            }
         } else {
+            real a[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) a[v] = 0;
             for (int i = l; i < len; i += 32) {
                 const real q = vj[i];
 #pragma unroll
                 for (int v = 0; v < NV; ++v) a[v] += q * sx[v][i];
             }
-        }
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            real t = a[v];
-            if constexpr (sizeof(real) == 4) t = warp_sumf(t);
-            else t = warp_sum(t);
-            if (l == 0) partial[(((long long)b * nchunk + chunk) * NV + v) * Kmax + j] = (double)t;
+            for (int v = 0; v < NV; ++v) {
+                real t = a[v];
+                if constexpr (sizeof(real) == 4) t = warp_sumf(t);
+                else t = warp_sum(t);
+                if (l == 0) partial[(((long long)b * nchunk + chunk) * NV + v) * Kmax + j] = (double)t;
+            }
         }
     }
 }
@@ -259,7 +249,7 @@ long long subdot_chunks(long long N, int elem_bytes) { return (N * elem_bytes + 
 long long krylov_partial_doubles(long long N, int Kmax) {
     // multi-dot (<= 3 right-hand sides), norms and combines; fused pass, whose fixed-size
     // chunks hold the fewest elements (so are the most numerous) for FP64
-    const long long a = krylov_chunks(N) * 3 * Kmax, b = subdot_chunks(N, 8) * Kmax;
+    const long long a = krylov_chunks(N) * 3 * Kmax, b = subdot_chunks(N, 8) * (Kmax + 1);
     return a > b ? a : b;
 }
 
@@ -269,9 +259,14 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
                  "l"(src), "r"(bytes), "r"(bar)
                  : "memory");
 }
+// Bound of the first wait of a tile (polls of the mbarrier); mof_debug_set_wait_limit
+// lowers it to make the timeout path run in tests. The wait after a timeout, which only
+// keeps the CTA alive until its own copies have landed, always uses MBAR_MAX_POLLS.
+__device__ long long g_wait_polls = MBAR_MAX_POLLS;
+
 // poll the mbarrier phase with a bound; false when the bound ran out
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned phase) {
-    for (long long it = 0; it < MBAR_MAX_POLLS; ++it) {
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned phase, long long limit = MBAR_MAX_POLLS) {
+    for (long long it = 0; it < limit; ++it) {
         unsigned done;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}\n"
@@ -287,7 +282,8 @@ template <typename real>
 __global__ void __launch_bounds__(SDT) k_sub_dot(const real *__restrict__ V, long long N, int Kmax, const int *__restrict__ K,
                                                  const int *__restrict__ act, const double *__restrict__ c, long long cstride,
                                                  const real *x, long long xstride, real *out, long long ostride,
-                                                 double *__restrict__ partial, int nchunk, int *__restrict__ err, int kcap) {
+                                                 double *__restrict__ partial, int nchunk, int *__restrict__ err, int kcap,
+                                                 double *__restrict__ nrm_partial) {
     constexpr int CH = sdch<real>();
     constexpr int EPT = CH / SDT;  // elements per thread: 4 (FP32) or 2 (FP64), 16 bytes
     using vec_t = typename std::conditional<sizeof(real) == 4, float4, double2>::type;
@@ -320,7 +316,7 @@ __global__ void __launch_bounds__(SDT) k_sub_dot(const real *__restrict__ V, lon
     }
     for (int j = tid; j < Kb; j += SDT) sc[j] = (real)c[b * cstride + j];
     __syncthreads();  // sc complete, and the barrier's initialisation visible to every thread
-    if (!mbar_wait(bar_a, 0)) {
+    if (!mbar_wait(bar_a, 0, g_wait_polls)) {
         if (tid == 0 && err) atomicOr(err, 4);
         mbar_wait(bar_a, 0);  // do not leave while copies may still land
         return;
@@ -351,6 +347,22 @@ __global__ void __launch_bounds__(SDT) k_sub_dot(const real *__restrict__ V, lon
             for (int e = 0; e < EPT; ++e)
                 if (i0 + e < len) ob[i0 + e] = xx[e];
         }
+        if (nrm_partial) {  // ||x'||^2 of the chunk (the padding is zero), FP64 across the warps
+            real q = 0;
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) q += xx[e] * xx[e];
+            double dq;
+            if constexpr (sizeof(real) == 4) dq = (double)warp_sumf(q);
+            else dq = warp_sum(q);
+            __shared__ double s_nq[SDT / 32];
+            if ((tid & 31) == 0) s_nq[tid >> 5] = dq;
+            __syncthreads();
+            if (tid == 0) {
+                double t = 0.0;
+                for (int wq = 0; wq < SDT / 32; ++wq) t += s_nq[wq];
+                nrm_partial[(long long)b * nchunk + chunk] = t;
+            }
+        }
     }
     __syncthreads();
     // partial dots V_j^T x' of the chunk: warp w takes j = w, w + 4, ...
@@ -372,6 +384,219 @@ __global__ void __launch_bounds__(SDT) k_sub_dot(const real *__restrict__ V, lon
         else a = warp_sum(a);
         if (l == 0) partial[((long long)b * nchunk + chunk) * Kmax + j] = (double)a;
     }
+}
+
+// ------------------------------------------------ Solve-OF: projection and new Gram column in one pass
+// For every frame pair b (p = q = 2 GKS, one basis V of K vectors of [2][ns] values):
+//   x' = r - V d                                (d = Mg^-1 V^T r, the projection coefficients)
+//   y  = Ups^T Ups x'                           (pointwise: u_c (u_x x'_x + u_y x'_y))
+//   dots  V^T x', V^T y, V^T q                  (q = L^T L r, the graph Laplacian of r, precomputed)
+//   scalars ||x'||^2, x'^T y, x'^T q, x'^T Ups^T b
+// A CTA owns OPX pixels of both components: TMA bulk copies stage, for each basis vector and for
+// r and q and Ups^T b, the two 1 KB segments of those pixels, and the segments of u_x and u_y,
+// completing on one mbarrier (bounded wait). The chunk partials (3 Kmax + 4 per chunk,
+// FP32 16-element partials accumulated with their rounding errors, FP64 across lanes) are
+// reduced by k_of_pass_reduce. With x' = r - V d the new vector is v = x' / ||x'|| and its Gram
+// column follows from these without another pass over the basis (k_of_pass_finish):
+//   G_A[i][v] = (V^T y)_i / ||x'||,   G_L[i][v] = ((V^T q)_i - (G_L d)_i) / ||x'||,
+//   g[v] = x'^T Ups^T b / ||x'||,     G_A[v][v] = x'^T y / ||x'||^2,
+//   G_L[v][v] = (x'^T q - d^T V^T q + d^T G_L d) / ||x'||^2,   Mg[i][v] = (V^T x')_i / ||x'||.
+constexpr int OP_T = 128;  // threads per CTA
+template <typename real>
+constexpr int opx() { return 1024 / (int)sizeof(real); }  // pixels per CTA: 256 (FP32), 128 (FP64): 1 KB copies
+
+long long of_pass_chunks(long long ns, int elem_bytes) { return (ns * elem_bytes + 1023) / 1024; }
+int of_pass_stride(int Kmax) { return 3 * Kmax + 4; }
+
+template <typename real>
+__global__ void __launch_bounds__(OP_T) k_of_proj_gram_pass(const real *__restrict__ V, long long ns, int Kmax,
+                                                           const int *__restrict__ K, const int *__restrict__ act,
+                                                           const double *__restrict__ d, real *x, const real *__restrict__ q,
+                                                           const real *__restrict__ AtB, const real *__restrict__ ux,
+                                                           const real *__restrict__ uy, double *__restrict__ partial,
+                                                           int nchunk, int *__restrict__ err, int kcap) {
+    constexpr int PX = opx<real>(), CH = 2 * PX;  // elements of one vector in the tile
+    constexpr int EPT = CH / OP_T;                // 4 (FP32) or 2 (FP64): 16 bytes per thread
+    using vec_t = typename std::conditional<sizeof(real) == 4, float4, double2>::type;
+    extern __shared__ __align__(128) unsigned char op_smem[];
+    real *sx = reinterpret_cast<real *>(op_smem);  // [CH] r, then x'
+    real *sq = sx + CH, *sa = sq + CH;             // [CH] q, Ups^T b
+    real *sfx = sa + CH, *sfy = sfx + PX;           // [PX] u_x, u_y
+    real *sy = sfy + PX;                            // [CH] y
+    real *sV = sy + CH;                             // [kcap][CH]
+    __shared__ real sd[64];
+    __shared__ __align__(8) unsigned long long bar;
+    __shared__ double s_red[OP_T / 32][4];
+    const int b = blockIdx.y, chunk = blockIdx.x, tid = threadIdx.x;
+    if (act && !act[b]) return;
+    int Kb = min(K[b], Kmax);
+    if (Kb > kcap) {
+        if (tid == 0 && err) atomicOr(err, 8);
+        Kb = kcap;
+    }
+    const long long p0 = (long long)chunk * PX;
+    const int len = (int)min((long long)PX, ns - p0);  // pixels of this chunk (a multiple of 16 bytes)
+    const unsigned bar_a = smem_u32(&bar);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        const unsigned bytes = (unsigned)len * (unsigned)sizeof(real);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a),
+                     "r"(bytes * (unsigned)(2 * Kb + 8))
+                     : "memory");
+        const long long N2 = 2 * ns;
+        const real *xb = x + b * N2, *qb = q + b * N2, *ab = AtB + b * N2;
+        bulk_g2s(sx, xb + p0, bytes, bar_a);
+        bulk_g2s(sx + PX, xb + ns + p0, bytes, bar_a);
+        bulk_g2s(sq, qb + p0, bytes, bar_a);
+        bulk_g2s(sq + PX, qb + ns + p0, bytes, bar_a);
+        bulk_g2s(sa, ab + p0, bytes, bar_a);
+        bulk_g2s(sa + PX, ab + ns + p0, bytes, bar_a);
+        bulk_g2s(sfx, ux + b * ns + p0, bytes, bar_a);
+        bulk_g2s(sfy, uy + b * ns + p0, bytes, bar_a);
+        const real *Vb = V + (long long)b * Kmax * N2;
+        for (int j = 0; j < Kb; ++j) {
+            bulk_g2s(sV + (long long)j * CH, Vb + (long long)j * N2 + p0, bytes, bar_a);
+            bulk_g2s(sV + (long long)j * CH + PX, Vb + (long long)j * N2 + ns + p0, bytes, bar_a);
+        }
+    }
+    for (int j = tid; j < Kb; j += OP_T) sd[j] = (real)d[(long long)b * Kmax + j];
+    __syncthreads();
+    if (!mbar_wait(bar_a, 0, g_wait_polls)) {
+        if (tid == 0 && err) atomicOr(err, 4);
+        mbar_wait(bar_a, 0);
+        return;
+    }
+    // x' = r - V d on this thread's EPT consecutive elements (comp = i0 / PX)
+    const int i0 = tid * EPT, pix0 = i0 % PX;
+    {
+        real acc[EPT];
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) acc[e] = 0;
+        for (int j = 0; j < Kb; ++j) {
+            const vec_t v = *reinterpret_cast<const vec_t *>(sV + (long long)j * CH + i0);
+            const real *vv = reinterpret_cast<const real *>(&v);
+            const real dj = sd[j];
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) acc[e] += vv[e] * dj;
+        }
+        vec_t xv = *reinterpret_cast<const vec_t *>(sx + i0);
+        real *xx = reinterpret_cast<real *>(&xv);
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) xx[e] = (pix0 + e < len) ? xx[e] - acc[e] : (real)0;
+        *reinterpret_cast<vec_t *>(sx + i0) = xv;
+        real *ob = x + b * 2 * ns + (i0 < PX ? 0 : ns) + p0 + pix0;
+        if (pix0 + EPT <= len) {
+            *reinterpret_cast<vec_t *>(ob) = xv;
+        } else {
+#pragma unroll
+            for (int e = 0; e < EPT; ++e)
+                if (pix0 + e < len) ob[e] = xx[e];
+        }
+    }
+    __syncthreads();
+    // y = Ups^T Ups x' and the four scalars
+    double s4[4] = {0.0, 0.0, 0.0, 0.0};
+    {
+        real a4[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+            const int i = i0 + e, p = i % PX;
+            real yv = 0;
+            if (p < len) {
+                const real w = sfx[p] * sx[p] + sfy[p] * sx[PX + p];
+                yv = (i < PX ? sfx[p] : sfy[p]) * w;
+            }
+            sy[i] = yv;
+            if (p < len) {  // the tile beyond len holds no copied data
+                const real xi = sx[i];
+                a4[0] += xi * xi;
+                a4[1] += xi * yv;
+                a4[2] += xi * sq[i];
+                a4[3] += xi * sa[i];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if constexpr (sizeof(real) == 4) s4[k] = (double)warp_sumf(a4[k]);
+            else s4[k] = warp_sum(a4[k]);
+        }
+    }
+    const int w = tid >> 5, l = tid & 31;
+    if (l == 0)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) s_red[w][k] = s4[k];
+    __syncthreads();
+    // partials stored output-major, [b][output][chunk], so that the reduction reads each
+    // output's chunks contiguously
+    double *out = partial + (long long)b * (3 * Kmax + 4) * nchunk + chunk;
+    if (tid < 4) {
+        double t = 0.0;
+        for (int ww = 0; ww < OP_T / 32; ++ww) t += s_red[ww][tid];
+        out[(long long)(3 * Kmax + tid) * nchunk] = t;
+    }
+    // dots of every basis vector with x', y and q: warp w takes j = w, w + 2, ...; lane l holds
+    // the elements l + 32 e of x', y, q in registers (consecutive lanes read consecutive words:
+    // no bank conflicts); elements beyond the chunk's pixels count as zero
+    constexpr int LE = CH / 32;
+    real rx[LE], ry[LE], rq[LE];
+#pragma unroll
+    for (int e = 0; e < LE; ++e) {
+        const int i = l + 32 * e;
+        const bool in = (i % PX) < len;
+        rx[e] = in ? sx[i] : (real)0;
+        ry[e] = in ? sy[i] : (real)0;
+        rq[e] = in ? sq[i] : (real)0;
+    }
+    for (int j = w; j < Kb; j += OP_T / 32) {
+        const real *vj = sV + (long long)j * CH + l;
+        real t1 = 0, t2 = 0, t3 = 0;
+#pragma unroll
+        for (int e = 0; e < LE; ++e) {
+            if (((l + 32 * e) % PX) < len) {
+                const real v = vj[32 * e];
+                t1 += v * rx[e];
+                t2 += v * ry[e];
+                t3 += v * rq[e];
+            }
+        }
+        // the warp's partial sums in the storage precision (FP64 work is slow on this GPU), then
+        // FP64 across the chunks
+        double o1, o2, o3;
+        if constexpr (sizeof(real) == 4) {
+            o1 = (double)warp_sumf(t1);
+            o2 = (double)warp_sumf(t2);
+            o3 = (double)warp_sumf(t3);
+        } else {
+            o1 = warp_sum(t1);
+            o2 = warp_sum(t2);
+            o3 = warp_sum(t3);
+        }
+        if (l == 0) {
+            out[(long long)j * nchunk] = o1;
+            out[(long long)(Kmax + j) * nchunk] = o2;
+            out[(long long)(2 * Kmax + j) * nchunk] = o3;
+        }
+    }
+}
+
+// sums of the chunk partials of k_of_proj_gram_pass in FP64 (one warp per output, lanes over
+// its contiguous chunks, fixed order): res[b][0..3 Kmax + 4)
+__global__ void k_of_pass_reduce(const double *__restrict__ partial, int nchunk, int Kmax, const int *__restrict__ K,
+                                 const int *__restrict__ act, double *__restrict__ res) {
+    const int b = blockIdx.y;
+    if (act && !act[b]) return;
+    const int stride = 3 * Kmax + 4, Kb = min(K[b], Kmax);
+    const int o = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (o >= stride) return;
+    const int j = o < 3 * Kmax ? o % Kmax : 0;
+    if (o < 3 * Kmax && j >= Kb) return;
+    const double *src = partial + ((long long)b * stride + o) * nchunk;
+    double sum = 0.0;
+#pragma unroll 8
+    for (int c = lane; c < nchunk; c += 32) sum += src[c];
+    sum = warp_sum(sum);
+    if (lane == 0) res[(long long)b * stride + o] = sum;
 }
 
 // ||x[b]||^2 per chunk
@@ -496,6 +721,13 @@ __global__ void __launch_bounds__(KT) k_append(real *__restrict__ V, long long N
     }
 }
 
+mof_status set_wait_polls(long long polls) {
+    const long long v = polls < 0 ? MBAR_MAX_POLLS : (polls > MBAR_MAX_POLLS ? MBAR_MAX_POLLS : polls);
+    MOF_CUDA(cudaMemcpyToSymbol(g_wait_polls, &v, sizeof(v)));
+    MOF_CUDA(cudaDeviceSynchronize());
+    return MOF_OK;
+}
+
 // ------------------------------------------------------------ host launchers
 template <typename real>
 void Krylov<real>::dots(const BasisRef<real> &B, const real *x, long long xstride, double *out, long long ostride, double sign,
@@ -602,7 +834,7 @@ void Krylov<real>::norm2(const real *x, long long N, long long xstride, int nb, 
 
 template <typename real>
 bool Krylov<real>::sub_dot(const BasisRef<real> &B, const double *c, long long cstride, real *x, long long xstride,
-                           double *out, cudaStream_t st, int kcap) const {
+                           double *out, cudaStream_t st, int kcap, int *nparts) const {
     const long long es = sizeof(real);
     const bool ok = B.Kmax <= 64 && (B.N * es) % 16 == 0 && (xstride * es) % 16 == 0 &&
                     (reinterpret_cast<uintptr_t>(B.V) % 16) == 0 && (reinterpret_cast<uintptr_t>(x) % 16) == 0;
@@ -617,11 +849,13 @@ bool Krylov<real>::sub_dot(const BasisRef<real> &B, const double *c, long long c
     const int kc = kcap > 0 ? std::min(kcap, B.Kmax) : B.Kmax;  // vectors the tile holds
     const size_t smem = (size_t)(kc + 1) * SD_BYTES;
     ::mof::count_launch(), k_sub_dot<real><<<dim3(nc, B.B), SDT, smem, st>>>(B.V, B.N, B.Kmax, B.K, B.act, c, cstride, x, xstride,
-                                                                         x, xstride, partial, nc, err, kc);
+                                                                         x, xstride, partial, nc, err, kc,
+                                                                         nparts ? partial + (long long)B.B * nc * B.Kmax : nullptr);
     DotOuts o{};
     o.o[0] = DotOut{out, B.Kmax, 1, 0, 0, 1.0};
     ::mof::count_launch(), k_sum_chunks<<<dim3((B.Kmax + SUMT / 32 - 1) / (SUMT / 32), B.B), SUMT, 0, st>>>(partial, nc, 1, B.Kmax,
                                                                                                           B.K, B.act, o);
+    if (nparts) *nparts = nc;
     return true;
 }
 
@@ -666,11 +900,12 @@ int Krylov<real>::reorth_second_parts(const BasisRef<real> &B, real *x, long lon
 template <typename real>
 void Krylov<real>::append_parts(const BasisRef<real> &B, int *Kmut, const real *x, long long xstride, int nparts,
                                 double *nrm2_out, const double *scale, double tol, int *grow, int *appended, real *stage,
-                                double *sq1, double *sq2, cudaStream_t st) const {
+                                double *sq1, double *sq2, cudaStream_t st, const double *parts) const {
     int *slot = reinterpret_cast<int *>(aux);
     real *inv = reinterpret_cast<real *>(aux + B.B);
-    ::mof::count_launch(), k_append_prep_sum<real><<<(B.B + 1) / 2, 64, 0, st>>>(Kmut, B.Kmax, partial, nparts, nrm2_out, scale, tol,
-                                                                                grow, B.B, slot, inv, appended, sq1, sq2);
+    ::mof::count_launch(), k_append_prep_sum<real><<<(B.B + 1) / 2, 64, 0, st>>>(Kmut, B.Kmax, parts ? parts : partial, nparts,
+                                                                                nrm2_out, scale, tol, grow, B.B, slot, inv,
+                                                                                appended, sq1, sq2);
     const int blocks = (int)std::min<long long>(1024, (B.N + KT - 1) / KT);
     ::mof::count_launch(), k_append<real><<<dim3(blocks, B.B), KT, 0, st>>>(B.V, B.N, B.Kmax, slot, inv, x, xstride, stage);
 }
@@ -685,6 +920,140 @@ void Krylov<real>::append(const BasisRef<real> &B, int *Kmut, const real *x, lon
     const int blocks = (int)std::min<long long>(1024, (B.N + KT - 1) / KT);
     ::mof::count_launch(), k_append<real><<<dim3(blocks, B.B), KT, 0, st>>>(B.V, B.N, B.Kmax, slot, inv, x, xstride, stage);
 }
+
+// Per pair (one warp): the append decision on ||x'|| (as k_append_prep), and for an appended
+// vector v = x' / ||x'||, its Gram columns G_A, G_L, g, its Euclidean overlaps Mg and the slot
+// and scale of k_append (see k_of_proj_gram_pass for the formulas).
+template <typename real>
+__global__ void k_of_pass_finish(const double *__restrict__ res, const double *__restrict__ d, int Kmax, int *__restrict__ K,
+                                 const int *__restrict__ act, const double *__restrict__ scale, double tol,
+                                 int *__restrict__ grow, double *__restrict__ GA, double *__restrict__ GL,
+                                 double *__restrict__ g, double *__restrict__ Mg, double *__restrict__ nrm2_out,
+                                 int *__restrict__ appended, int *__restrict__ slot, real *__restrict__ inv) {
+    const int b = blockIdx.x, lane = threadIdx.x;
+    if (act && !act[b]) {
+        if (lane == 0) {
+            slot[b] = -1;
+            if (appended) appended[b] = 0;
+        }
+        return;
+    }
+    const int stride = 3 * Kmax + 4, Kb = min(K[b], Kmax);
+    const double *rs = res + (long long)b * stride;
+    const double *c2 = rs, *ay = rs + Kmax, *aq = rs + 2 * Kmax, *sc = rs + 3 * Kmax;
+    const double *db = d + (long long)b * Kmax;
+    const long long KK = (long long)Kmax * Kmax;
+    double *A = GA + b * KK, *L = GL + b * KK, *M = Mg + b * KK;
+    const double nr2 = sc[0];
+    const bool ok = append_ok(grow[b], Kb, Kmax, nr2, scale, b, tol);
+    // (G_L d)_i and d^T (V^T q) - d^T G_L d for the new column of G_L
+    double dq = 0.0, dGd = 0.0;
+    for (int i = lane; i < Kb; i += 32) {
+        double gd = 0.0;
+        for (int k = 0; k < Kb; ++k) gd += L[(long long)i * Kmax + k] * db[k];
+        dq += db[i] * aq[i];
+        dGd += db[i] * gd;
+    }
+    dq = warp_sum(dq);
+    dGd = warp_sum(dGd);
+    if (ok) {
+        const double ib = 1.0 / sqrt(nr2), ib2 = 1.0 / nr2;
+        for (int i = lane; i < Kb; i += 32) {
+            double gd = 0.0;
+            for (int k = 0; k < Kb; ++k) gd += L[(long long)i * Kmax + k] * db[k];
+            const double va = ay[i] * ib, vl = (aq[i] - gd) * ib, vm = c2[i] * ib;
+            A[(long long)i * Kmax + Kb] = va;
+            A[(long long)Kb * Kmax + i] = va;
+            L[(long long)i * Kmax + Kb] = vl;
+            L[(long long)Kb * Kmax + i] = vl;
+            M[(long long)i * Kmax + Kb] = vm;
+            M[(long long)Kb * Kmax + i] = vm;
+        }
+        __syncwarp();
+        if (lane == 0) {
+            A[(long long)Kb * Kmax + Kb] = sc[1] * ib2;
+            L[(long long)Kb * Kmax + Kb] = (sc[2] - dq + dGd) * ib2;
+            M[(long long)Kb * Kmax + Kb] = 1.0;
+            g[(long long)b * Kmax + Kb] = sc[3] * ib;
+        }
+    }
+    if (lane == 0) {
+        nrm2_out[b] = nr2;
+        slot[b] = ok ? Kb : -1;
+        inv[b] = ok ? (real)(1.0 / sqrt(nr2)) : (real)0;
+        if (ok) K[b] = Kb + 1;
+        else grow[b] = 0;
+        if (appended) appended[b] = ok;
+    }
+}
+
+// q[b] = L^T L r[b] on both components (the graph Laplacian with free boundary, one thread
+// per pixel and component)
+template <typename real>
+__global__ void k_of_lap(const real *__restrict__ r, real *__restrict__ q, int nx, int ny, const int *__restrict__ act) {
+    const int b = blockIdx.z >> 1, c = blockIdx.z & 1;
+    if (act && !act[b]) return;
+    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    const long long ns = (long long)nx * ny, i = (long long)y * nx + x;
+    const real *f = r + (2LL * b + c) * ns;
+    const real v0 = f[i];
+    real v = 0;
+    if (x > 0) v += v0 - f[i - 1];
+    if (x < nx - 1) v += v0 - f[i + 1];
+    if (y > 0) v += v0 - f[i - nx];
+    if (y < ny - 1) v += v0 - f[i + nx];
+    q[(2LL * b + c) * ns + i] = v;
+}
+
+template <typename real>
+bool of_pass_applicable(long long ns, const void *V, const void *x) {
+    const long long es = sizeof(real);
+    return (ns * es) % 16 == 0 && (reinterpret_cast<uintptr_t>(V) % 16) == 0 && (reinterpret_cast<uintptr_t>(x) % 16) == 0;
+}
+
+template <typename real>
+mof_status launch_of_proj_gram_pass(const BasisRef<real> &B, int *Kmut, long long ns, int nx, int ny, const double *d, real *x,
+                                    real *q, const real *AtB, const real *ux, const real *uy, double *partial,
+                                    double *res, int *err, int kcap, const double *scale, double tol, int *grow,
+                                    double *GA, double *GL, double *g, double *Mg, double *nrm2_out, int *appended,
+                                    double *aux, cudaStream_t st) {
+    static std::atomic<bool> configured{false};
+    if (!configured.load()) {
+        if (cudaFuncSetAttribute(k_of_proj_gram_pass<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024) !=
+            cudaSuccess)
+            return fail(MOF_ECUDA, "shared-memory attribute of the Solve-OF pass");
+        configured.store(true);
+    }
+    const int nc = (int)of_pass_chunks(ns, (int)sizeof(real));
+    const int kc = kcap > 0 ? std::min(kcap, B.Kmax) : B.Kmax;
+    const size_t smem = (size_t)(kc + 5) * 2048;
+    const dim3 lg((nx + 31) / 32, (ny + 7) / 8, 2 * B.B);
+    ::mof::count_launch(), k_of_lap<real><<<lg, dim3(32, 8), 0, st>>>(x, q, nx, ny, B.act);
+    ::mof::count_launch(), k_of_proj_gram_pass<real><<<dim3(nc, B.B), OP_T, smem, st>>>(B.V, ns, B.Kmax, B.K, B.act, d, x, q, AtB,
+                                                                                     ux, uy, partial, nc, err, kc);
+    const int stride = of_pass_stride(B.Kmax);
+    ::mof::count_launch(), k_of_pass_reduce<<<dim3((stride + 7) / 8, B.B), 256, 0, st>>>(partial, nc, B.Kmax, B.K, B.act, res);
+    int *slot = reinterpret_cast<int *>(aux);
+    real *inv = reinterpret_cast<real *>(aux + B.B);
+    ::mof::count_launch(), k_of_pass_finish<real><<<B.B, 32, 0, st>>>(res, d, B.Kmax, Kmut, B.act, scale, tol, grow, GA, GL, g,
+                                                                     Mg, nrm2_out, appended, slot, inv);
+    const int blocks = (int)std::min<long long>(1024, (B.N + KT - 1) / KT);
+    ::mof::count_launch(), k_append<real><<<dim3(blocks, B.B), KT, 0, st>>>(B.V, B.N, B.Kmax, slot, inv, x, B.N, nullptr);
+    MOF_LAUNCH_CHECK();
+    return MOF_OK;
+}
+
+template bool of_pass_applicable<float>(long long, const void *, const void *);
+template bool of_pass_applicable<double>(long long, const void *, const void *);
+template mof_status launch_of_proj_gram_pass<float>(const BasisRef<float> &, int *, long long, int, int, const double *, float *,
+                                                    float *, const float *, const float *, const float *, double *, double *,
+                                                    int *, int, const double *, double, int *, double *, double *, double *,
+                                                    double *, double *, int *, double *, cudaStream_t);
+template mof_status launch_of_proj_gram_pass<double>(const BasisRef<double> &, int *, long long, int, int, const double *, double *,
+                                                     double *, const double *, const double *, const double *, double *,
+                                                     double *, int *, int, const double *, double, int *, double *, double *,
+                                                     double *, double *, double *, int *, double *, cudaStream_t);
 
 template struct Krylov<float>;
 template struct Krylov<double>;

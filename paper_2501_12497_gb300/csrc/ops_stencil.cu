@@ -83,22 +83,37 @@ __device__ __forceinline__ real warp_weight_to(int px, int py, real vx, real vy,
 // whose window is empty.
 constexpr int BND_EMPTY = 1 << 29;
 
-// (M(v)^T r)(q) by a gather over the sources p whose footprint can contain q:
-// px in [qx - 1 - dxmax, qx - dxmin] (x1(p) is x0(p) or x0(p) + 1), likewise py.
+// Compensated sum of the terms of one output pixel of a transpose: in FP32 each term's
+// rounding error is kept (DFAcc::add), so the result does not lose the digits that the
+// cancellation between the terms of Mhat^T and Psi^T would otherwise cost; FP64 sums plainly.
+template <typename real> struct CAcc;
+template <> struct CAcc<float> {
+    DFAcc a;
+    __device__ __forceinline__ void add(float x) { a.add(x); }
+    __device__ __forceinline__ double value() const { return a.value(); }
+};
+template <> struct CAcc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
+// acc -= (M(v)^T r)(q), by a gather over the sources p whose footprint can contain q:
+// px in [qx - 1 - dxmax, qx - dxmin] (x1(p) is x0(p) or x0(p) + 1), likewise py, in
+// row-major source order.
 template <typename real>
-__device__ __forceinline__ real warpT_gather(const real *__restrict__ r, const real *__restrict__ vx,
-                                             const real *__restrict__ vy, int nx, int ny, int qx, int qy, int4 bd, int wm) {
-    real acc = 0;
+__device__ __forceinline__ void warpT_gather_sub(CAcc<real> &acc, const real *__restrict__ r, const real *__restrict__ vx,
+                                                 const real *__restrict__ vy, int nx, int ny, int qx, int qy, int4 bd,
+                                                 int wm) {
     const int ylo = max(0, qy - 1 - bd.w), yhi = min(ny - 1, qy - bd.z);
     const int xlo = max(0, qx - 1 - bd.y), xhi = min(nx - 1, qx - bd.x);
     for (int py = ylo; py <= yhi; ++py) {
         for (int px = xlo; px <= xhi; ++px) {
             const long long i = (long long)py * nx + px;
             const real w = warp_weight_to(px, py, ldg(vx + i), ldg(vy + i), nx, ny, qx, qy, wm);
-            if (w != (real)0) acc += w * ldg(r + i);
+            if (w != (real)0) acc.add(-(w * ldg(r + i)));
         }
     }
-    return acc;
 }
 
 }  // namespace
@@ -342,26 +357,25 @@ mof_status launch_tile_bounds(const mof_problem *p, const real *s, const real *s
 // u = Mhat^T r (+ optional addend, times scale), one thread per pixel of a frame:
 //   u_t = [t<P] r0_t + [t>0] r1_{t-1} - [t<P] M(sr_t)^T r1_t - [t>0] M(s_{t-1})^T r0_{t-1}
 template <typename real>
-__device__ __forceinline__ real flowT_at(const real *__restrict__ r, const real *__restrict__ s, const real *__restrict__ sr,
-                                         int nx, int ny, int np, int t, int x, int y, const int *__restrict__ bnd_s,
-                                         const int *__restrict__ bnd_sr, int tiles, int tile, int wm) {
+__device__ __forceinline__ void flowT_at(CAcc<real> &v, const real *__restrict__ r, const real *__restrict__ s,
+                                         const real *__restrict__ sr, int nx, int ny, int np, int t, int x, int y,
+                                         const int *__restrict__ bnd_s, const int *__restrict__ bnd_sr, int tiles, int tile,
+                                         int wm) {
     const long long ns = (long long)nx * ny, i = (long long)y * nx + x;
-    real v = 0;
     if (t < np) {
         const real *r1 = r + (np + t) * ns;
         const real *srp = sr + 2LL * t * ns;
-        v += r[t * ns + i];
+        v.add(r[t * ns + i]);
         const int4 bd = __ldg(reinterpret_cast<const int4 *>(bnd_sr) + (long long)t * tiles + tile);
-        v -= warpT_gather(r1, srp, srp + ns, nx, ny, x, y, bd, wm);
+        warpT_gather_sub(v, r1, srp, srp + ns, nx, ny, x, y, bd, wm);
     }
     if (t > 0) {
         const real *r0 = r + (long long)(t - 1) * ns;
         const real *sp = s + 2LL * (t - 1) * ns;
-        v += r[(np + t - 1) * ns + i];
+        v.add(r[(np + t - 1) * ns + i]);
         const int4 bd = __ldg(reinterpret_cast<const int4 *>(bnd_s) + (long long)(t - 1) * tiles + tile);
-        v -= warpT_gather(r0, sp, sp + ns, nx, ny, x, y, bd, wm);
+        warpT_gather_sub(v, r0, sp, sp + ns, nx, ny, x, y, bd, wm);
     }
-    return v;
 }
 
 template <typename real>
@@ -371,7 +385,9 @@ __global__ void k_flowT(const real *__restrict__ r, const real *__restrict__ s, 
     const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, t = blockIdx.z;
     if (x >= nx || y >= ny) return;
     const int tile = blockIdx.y * gridDim.x + blockIdx.x;
-    u[(long long)t * nx * ny + (long long)y * nx + x] = flowT_at(r, s, sr, nx, ny, np, t, x, y, bnd_s, bnd_sr, tiles, tile, wm);
+    CAcc<real> v;
+    flowT_at(v, r, s, sr, nx, ny, np, t, x, y, bnd_s, bnd_sr, tiles, tile, wm);
+    u[(long long)t * nx * ny + (long long)y * nx + x] = (real)v.value();
 }
 
 template <typename real>
@@ -714,21 +730,21 @@ __global__ void k_regn_apply(const real *__restrict__ x, const real *__restrict_
         const real g = f[j + nx] - f[j], gk = k[j + nx] - k[j];
         return g / sqrt(gk * gk + eps2);
     };
-    real v = 0;
-    if (xx > 0) v += wdx(i - 1);
-    if (xx < nx - 1) v -= wdx(i);
-    if (yy > 0) v += wdy(i - nx);
-    if (yy < ny - 1) v -= wdy(i);
+    CAcc<real> v;
+    if (xx > 0) v.add(wdx(i - 1));
+    if (xx < nx - 1) v.add(-wdx(i));
+    if (yy > 0) v.add(wdy(i - nx));
+    if (yy < ny - 1) v.add(-wdy(i));
     if (temporal) {  // L_t^T w_t L_t x: the weighted differences to the previous and next frame
         auto wdt = [&](const real *fa, const real *ka) -> real {
             const real g = fa[i + ns] - fa[i], gk = ka[i + ns] - ka[i];
             return g / sqrt(gk * gk + eps2);
         };
-        if (t > 0) v += wdt(f - ns, k - ns);
-        if (t < np) v -= wdt(f, k);
+        if (t > 0) v.add(wdt(f - ns, k - ns));
+        if (t < np) v.add(-wdt(f, k));
     }
-    if (np > 0) v += flowT_at(q, s, sr, nx, ny, np, t, xx, yy, bnd_s, bnd_sr, tiles, blockIdx.y * gridDim.x + blockIdx.x, wm);
-    const real out = s_sc * v;
+    if (np > 0) flowT_at(v, q, s, sr, nx, ny, np, t, xx, yy, bnd_s, bnd_sr, tiles, blockIdx.y * gridDim.x + blockIdx.x, wm);
+    const real out = (real)((double)s_sc * v.value());
     y[t * ns + i] = y_add ? y_add[t * ns + i] + out : out;
 }
 

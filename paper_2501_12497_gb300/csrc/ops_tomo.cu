@@ -39,7 +39,9 @@ __global__ void k_transpose(const real *__restrict__ u, real *__restrict__ uT, i
 // -------------------------------------------------------------- K1 project
 // One thread per ray (angle a = blockIdx.y, bin k). Rays of one warp are 32
 // adjacent bins of one angle, so at each step they read adjacent pixels of
-// one image row (of the transposed frame for steep angles): coalesced.
+// one image row (of the transposed frame for steep angles): coalesced. In FP32
+// the ray sum is compensated (Kahan, per step of two taps): its rounding stays
+// at a few units of FP32 however long the ray.
 template <typename real>
 __global__ void __launch_bounds__(128) k_project(const real *__restrict__ u, const real *__restrict__ uT,
                                                  real *__restrict__ b, const AngleParams *__restrict__ ang,
@@ -78,14 +80,19 @@ __global__ void __launch_bounds__(128) k_project(const real *__restrict__ u, con
         } else if (!(f0 > -1.0f && f0 < (float)nfast)) {
             jhi = -1;
         }
+        float cmp = 0.f;  // Kahan compensation of the ray sum (a ray adds up to 2 nx taps)
 #pragma unroll 4
         for (int j = jlo; j <= jhi; ++j) {
             int i0;
             float w1;
             affine_frac(ib, fb, P.df_hi, P.df_lo, j, i0, w1);
             const real *row = img + (long long)j * nfast;
-            if (i0 >= 0 && i0 < nfast) acc = fmaf(1.0f - w1, ldg(row + i0), acc);
-            if (i0 + 1 >= 0 && i0 + 1 < nfast) acc = fmaf(w1, ldg(row + i0 + 1), acc);
+            float tap = 0.f;
+            if (i0 >= 0 && i0 < nfast) tap = (1.0f - w1) * ldg(row + i0);
+            if (i0 + 1 >= 0 && i0 + 1 < nfast) tap = fmaf(w1, ldg(row + i0 + 1), tap);
+            const float y = __fsub_rn(tap, cmp), t = __fadd_rn(acc, y);
+            cmp = __fsub_rn(__fsub_rn(t, acc), y);
+            acc = t;
         }
         b[(long long)a * nb + k] = acc * P.wstep;
     } else {
@@ -171,8 +178,20 @@ __global__ void __launch_bounds__(128) k_project_fan(const real *__restrict__ u,
 }
 
 template <typename real>
-mof_status launch_project(const mof_problem *p, const real *u, real *uT, real *b, cudaStream_t st) {
+mof_status launch_project(const mof_problem *p, const real *u, real *uT, real *b, cudaStream_t st, bool per_frame) {
     dim3 tb(32, 8), tg((p->nx + 31) / 32, (p->ny + 31) / 32, p->nt);
+    if (per_frame && !p->fan) {  // the plain form: frame by frame (the angles' tables hold their frame)
+        const long long ns = (long long)p->nx * p->ny;
+        for (int t = 0; t < p->nt; ++t) {
+            dim3 tg1((p->nx + 31) / 32, (p->ny + 31) / 32, 1);
+            ::mof::count_launch(), k_transpose<real><<<tg1, tb, 0, st>>>(u + t * ns, uT + t * ns, p->nx, p->ny);
+            const int a0 = p->aoff[t], na = p->aoff[t + 1] - a0;
+            ::mof::count_launch(), k_project<real><<<dim3((p->nb + 127) / 128, na), 128, 0, st>>>(u, uT, b + (long long)a0 * p->nb,
+                                                                                             p->d_ang + a0, p->nx, p->ny, p->nb);
+        }
+        MOF_LAUNCH_CHECK();
+        return MOF_OK;
+    }
     ::mof::count_launch(), k_transpose<real><<<tg, tb, 0, st>>>(u, uT, p->nx, p->ny);
     MOF_LAUNCH_CHECK();
     if (p->fan) {
@@ -199,14 +218,14 @@ constexpr int BP_TX = 32, BP_TY = 8, BP_CHUNK = 64;
 template <typename real>
 __global__ void __launch_bounds__(BP_TX *BP_TY) k_backproject(const real *__restrict__ b, real *__restrict__ u,
                                                               const AngleParams *__restrict__ ang,
-                                                              const int *__restrict__ aoff, int nx, int ny, int nb) {
+                                                              const int *__restrict__ aoff, int nx, int ny, int nb, int t0) {
     // per angle of the chunk: the bin coordinate at the tile origin (integer + fraction,
     // from FP64) and the constants of the footprint, shared by the block's pixels
     __shared__ int s_ib[BP_CHUNK];
     __shared__ float s_fb[BP_CHUNK], s_tAh[BP_CHUNK], s_tAl[BP_CHUNK], s_tBh[BP_CHUNK], s_tBl[BP_CHUNK];
     __shared__ float s_r[BP_CHUNK], s_ir[BP_CHUNK], s_wf[BP_CHUNK];
     __shared__ double s_tb[BP_CHUNK];
-    const int t = blockIdx.z;
+    const int t = t0 + blockIdx.z;
     const int x0 = blockIdx.x * BP_TX, y0 = blockIdx.y * BP_TY;
     const int di = threadIdx.x, dj = threadIdx.y;
     const int x = x0 + di, y = y0 + dj;
@@ -277,6 +296,91 @@ __global__ void __launch_bounds__(BP_TX *BP_TY) k_backproject(const real *__rest
     if (x < nx && y < ny) u[(long long)t * nx * ny + (long long)y * nx + x] = acc;
 }
 
+// FP32 form with BP_PX pixels per thread (x = x0 + di + 32 e, e < BP_PX: a 128 x 8 tile
+// per CTA): the per-angle constants come from shared memory as two 16-byte records
+// and are reused for the thread's pixels, and the tile origin's FP64 set-up is shared
+// by four times as many pixels. Each pixel's bin coordinate and weights are those of
+// k_backproject (the same split products); a pixel's sum over the angles is compensated
+// (Kahan), so its rounding does not grow with the number of angles.
+constexpr int BP_PX = 4;
+struct __align__(16) BpAngle {
+    float fb, tAh, tAl, tBh;
+    float tBl, r, ir, wf;
+};
+
+__global__ void __launch_bounds__(BP_TX *BP_TY) k_backproject4(const float *__restrict__ b, float *__restrict__ u,
+                                                               const AngleParams *__restrict__ ang,
+                                                               const int *__restrict__ aoff, int nx, int ny, int nb, int t0) {
+    __shared__ BpAngle s_a[BP_CHUNK];
+    __shared__ int s_ib[BP_CHUNK];
+    const int t = t0 + blockIdx.z;
+    const int x0 = blockIdx.x * BP_TX * BP_PX, y0 = blockIdx.y * BP_TY;
+    const int di = threadIdx.x, dj = threadIdx.y;
+    const int y = y0 + dj;
+    const int tid = threadIdx.y * BP_TX + threadIdx.x;
+    const int a_begin = aoff[t], a_end = aoff[t + 1];
+    float acc[BP_PX];
+#pragma unroll
+    for (int e = 0; e < BP_PX; ++e) acc[e] = 0.f;
+    float cmp[BP_PX];
+#pragma unroll
+    for (int e = 0; e < BP_PX; ++e) cmp[e] = 0.f;
+    for (int ac = a_begin; ac < a_end; ac += BP_CHUNK) {
+        const int cn = min(BP_CHUNK, a_end - ac);
+        __syncthreads();
+        if (tid < cn) {
+            const AngleParams &P = ang[ac + tid];
+            const double tb = P.t0 + (double)x0 * P.tA + (double)y0 * P.tB;
+            const double fl = floor(tb);
+            s_ib[tid] = (int)fmax(fmin(fl, 1e9), -1e9);
+            s_a[tid] = BpAngle{(float)(tb - fl), P.tA_hi, P.tA_lo, P.tB_hi, P.tB_lo, P.rfoot, P.inv_rfoot, P.wfoot};
+        }
+        __syncthreads();
+        if (y < ny) {
+            for (int q = 0; q < cn; ++q) {
+                const float *row = b + (long long)(ac + q) * nb;
+                const BpAngle A = s_a[q];
+                const int ib0 = s_ib[q];
+                const float pb = (float)dj * A.tBh, pfb = floorf(pb);
+                const float bl = (float)dj * A.tBl;
+#pragma unroll
+                for (int e = 0; e < BP_PX; ++e) {
+                    const int dx = di + BP_TX * e;
+                    if (x0 + dx >= nx) break;
+                    const float pa = (float)dx * A.tAh, pfa = floorf(pa);
+                    float fr = A.fb + (pa - pfa) + (pb - pfb) + fmaf((float)dx, A.tAl, bl);
+                    const float ff = floorf(fr);
+                    const int ib = ib0 + (int)pfa + (int)pfb + (int)ff;
+                    fr -= ff;
+                    if (A.r <= 1.0f) {  // at most the two bins around t
+                        const float d1 = 1.0f - fr;
+                        float tap = 0.f;
+                        if (fr < A.r && ib >= 0 && ib < nb) tap = A.wf * (1.0f - fr * A.ir) * ldg(row + ib);
+                        if (d1 < A.r && ib + 1 >= 0 && ib + 1 < nb) tap = fmaf(A.wf * (1.0f - d1 * A.ir), ldg(row + ib + 1), tap);
+                        const float y = __fsub_rn(tap, cmp[e]), tt = __fadd_rn(acc[e], y);
+                        cmp[e] = __fsub_rn(__fsub_rn(tt, acc[e]), y);
+                        acc[e] = tt;
+                    } else {
+                        for (int m = 0; (float)m < A.r; ++m) {
+                            const float d0 = fr + (float)m, d1 = 1.0f - fr + (float)m;
+                            const int k0 = ib - m, k1 = ib + 1 + m;
+                            if (d0 < A.r && k0 >= 0 && k0 < nb) acc[e] = fmaf(A.wf * (1.0f - d0 * A.ir), ldg(row + k0), acc[e]);
+                            if (d1 < A.r && k1 >= 0 && k1 < nb) acc[e] = fmaf(A.wf * (1.0f - d1 * A.ir), ldg(row + k1), acc[e]);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    if (y < ny) {
+#pragma unroll
+        for (int e = 0; e < BP_PX; ++e) {
+            const int x = x0 + di + BP_TX * e;
+            if (x < nx) u[(long long)t * nx * ny + (long long)y * nx + x] = acc[e];
+        }
+    }
+}
+
 // ---------------------------------------------------------- K2 fan beam
 // One thread per pixel. A ray steps over rows (or columns) and gives the pixel
 // a weight only at the step of the pixel's row (column), when its crossing
@@ -341,7 +445,7 @@ __global__ void __launch_bounds__(BP_TX *BP_TY) k_backproject_fan(const real *__
 }
 
 template <typename real>
-mof_status launch_backproject(const mof_problem *p, const real *b, real *u, cudaStream_t st) {
+mof_status launch_backproject(const mof_problem *p, const real *b, real *u, cudaStream_t st, bool per_frame) {
     dim3 grid((p->nx + BP_TX - 1) / BP_TX, (p->ny + BP_TY - 1) / BP_TY, p->nt);
     if (p->fan) {
         ::mof::count_launch(), k_backproject_fan<real><<<grid, dim3(BP_TX, BP_TY), 0, st>>>(
@@ -350,14 +454,26 @@ mof_status launch_backproject(const mof_problem *p, const real *b, real *u, cuda
         MOF_LAUNCH_CHECK();
         return MOF_OK;
     }
-    ::mof::count_launch(), k_backproject<real><<<grid, dim3(BP_TX, BP_TY), 0, st>>>(b, u, p->d_ang, p->d_aoff, p->nx, p->ny, p->nb);
+    // the plain form launches one frame at a time (t0 = t, one z slice), else all frames
+    const int nlaunch = per_frame ? p->nt : 1, nz = per_frame ? 1 : p->nt;
+    for (int t0 = 0; t0 < nlaunch; ++t0) {
+        if (sizeof(real) == 4) {
+            dim3 g4((p->nx + BP_TX * BP_PX - 1) / (BP_TX * BP_PX), (p->ny + BP_TY - 1) / BP_TY, nz);
+            ::mof::count_launch(), k_backproject4<<<g4, dim3(BP_TX, BP_TY), 0, st>>>((const float *)b, (float *)u, p->d_ang,
+                                                                                     p->d_aoff, p->nx, p->ny, p->nb, t0);
+        } else {
+            dim3 g1(grid.x, grid.y, nz);
+            ::mof::count_launch(), k_backproject<real><<<g1, dim3(BP_TX, BP_TY), 0, st>>>(b, u, p->d_ang, p->d_aoff, p->nx, p->ny,
+                                                                                         p->nb, t0);
+        }
+    }
     MOF_LAUNCH_CHECK();
     return MOF_OK;
 }
 
-template mof_status launch_project<float>(const mof_problem *, const float *, float *, float *, cudaStream_t);
-template mof_status launch_project<double>(const mof_problem *, const double *, double *, double *, cudaStream_t);
-template mof_status launch_backproject<float>(const mof_problem *, const float *, float *, cudaStream_t);
-template mof_status launch_backproject<double>(const mof_problem *, const double *, double *, cudaStream_t);
+template mof_status launch_project<float>(const mof_problem *, const float *, float *, float *, cudaStream_t, bool);
+template mof_status launch_project<double>(const mof_problem *, const double *, double *, double *, cudaStream_t, bool);
+template mof_status launch_backproject<float>(const mof_problem *, const float *, float *, cudaStream_t, bool);
+template mof_status launch_backproject<double>(const mof_problem *, const double *, double *, cudaStream_t, bool);
 
 }  // namespace mof

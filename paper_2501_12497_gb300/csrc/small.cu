@@ -629,9 +629,8 @@ __device__ __forceinline__ R newton_step(R t, R f, R f1, R &A, R &B) {
 __global__ void __launch_bounds__(ST, 1) k_small_solve(SmallArgs a) {
     extern __shared__ double sm[];
     __shared__ double s_rho, s_rho0sq, s_t, s_scale;
-    __shared__ double s_refv[NREF];
-    __shared__ int s_refi[NREF];
-    __shared__ float s_redf[NW], s_redv[NW];
+    __shared__ double s_grid[GRID_POINTS];
+    __shared__ float s_redf[NW];
     __shared__ int s_fail, s_flag, s_idx[NW], s_end[4];
     __shared__ JacobiShared<float> jf;
     __shared__ JacobiShared<double> jd;
@@ -805,59 +804,39 @@ __global__ void __launch_bounds__(ST, 1) k_small_solve(SmallArgs a) {
         const double lo = lrho - BRACKET_DECADES, hi = lrho + BRACKET_DECADES;
         const double step = (hi - lo) / (GRID_POINTS - 1);
         if (a.rule == MOF_RULE_GCV) {
-            // FP32 scan of the grid, argmin with ties to the smaller index
-            float vb = FLT_MAX;
-            int ib = tid;
-            if (tid < GRID_POINTS) {
-                float N, D;
-                grid_nd(SF, exp10f((float)(-BRACKET_DECADES + tid * step)), N, D);
-                vb = __fdividef(N, D * D);
-                if (!(vb == vb)) vb = FLT_MAX;
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                const float vo = __shfl_xor_sync(0xffffffffu, vb, o);
-                const int io = __shfl_xor_sync(0xffffffffu, ib, o);
-                if (vo < vb || (vo == vb && io < ib)) {
-                    vb = vo;
-                    ib = io;
-                }
-            }
-            if (lane == 0) {
-                s_redv[wid] = vb;
-                s_idx[wid] = ib;
-            }
-            __syncthreads();
-            int i32 = s_idx[0];
-            {
-                float bv = s_redv[0];
-                for (int w = 1; w < NW; ++w)
-                    if (s_redv[w] < bv || (s_redv[w] == bv && s_idx[w] < i32)) {
-                        bv = s_redv[w];
-                        i32 = s_idx[w];
-                    }
-            }
-            // FP64 values of the grid points around the FP32 minimum decide it
-            if (wid < NREF) {
-                const int idx = min(max(i32 - NREF / 2 + wid, 0), GRID_POINTS - 1);
+            // GCV at every grid point in FP64 (warps over the points) and its first minimum
+            // (ties to the smaller lambda), as the grid search defines it; a scan in lower
+            // precision can pick another of two nearly equal minima
+            for (int gi = wid; gi < GRID_POINTS; gi += NW) {
                 double N, D;
-                lam_terms_nd(S, exp10(lo + idx * step) / rho, N, D);
+                lam_terms_nd(S, exp10(lo + gi * step) / rho, N, D);
                 warp_sum2(N, D);
                 if (lane == 0) {
-                    s_refv[wid] = gcv_value(N, D);
-                    s_refi[wid] = idx;
+                    const double v = gcv_value(N, D);
+                    s_grid[gi] = v == v ? v : DBL_MAX;
                 }
             }
             __syncthreads();
             if (wid == 0) {
-                double bv = s_refv[0], vmax = s_refv[0];
-                int ig = s_refi[0];
-                for (int w = 1; w < NREF; ++w) {
-                    if (s_refv[w] < bv || (s_refv[w] == bv && s_refi[w] < ig)) {
-                        bv = s_refv[w];
-                        ig = s_refi[w];
+                double bv = DBL_MAX;
+                int ig = GRID_POINTS;
+                for (int gi = lane; gi < GRID_POINTS; gi += 32)
+                    if (s_grid[gi] < bv) {
+                        bv = s_grid[gi];
+                        ig = gi;
                     }
-                    vmax = fmax(vmax, s_refv[w]);
+                for (int o = 16; o > 0; o >>= 1) {
+                    const double bo = __shfl_xor_sync(0xffffffffu, bv, o);
+                    const int io = __shfl_xor_sync(0xffffffffu, ig, o);
+                    if (bo < bv || (bo == bv && io < ig)) {
+                        bv = bo;
+                        ig = io;
+                    }
                 }
+                if (ig >= GRID_POINTS) ig = 0;
+                bv = s_grid[ig];
+                double vmax = bv;  // the flatness test over the NREF points around the minimum
+                for (int w = -(NREF / 2); w <= NREF / 2; ++w) vmax = fmax(vmax, s_grid[min(max(ig + w, 0), GRID_POINTS - 1)]);
                 const bool flat = vmax - bv <= 1e-13 * bv;
                 // safeguarded Newton on dG/dt = 0 inside [t_{i-1}, t_{i+1}]: FP32 steps
                 // (in t - log10 rho) to a starting point, then FP64 steps on the full cell pair

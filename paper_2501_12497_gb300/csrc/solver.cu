@@ -134,9 +134,9 @@ struct WS {
     int *K, *KU, *grow, *gkb, *flag, *err, *appended;
     double *report;  // [max_outer][8]
     // ---- Solve-OF (P pairs)
-    real *ux, *uy, *ut, *bof, *Vof, *Uof, *AtB, *wv, *wu, *y1, *y2, *sof, *vnew_of;
+    real *ux, *uy, *ut, *bof, *Vof, *Uof, *AtB, *wv, *wu, *y1, *y2, *sof, *vnew_of, *q_of;
     double *GA, *GL, *gof, *zof, *gam, *nrm_of, *coef_of, *coefU_of, *scale_of, *alpha_of, *alpha1_of, *beta_of,
-        *beta1_of, *bb_of;
+        *beta1_of, *bb_of, *Mg_of, *pres_of;
     int *Kv_of, *Ku_of, *grow_of, *gkb_of, *act_of, *app_of, *flag_of;
     real *wf_of = nullptr, *wl_of = nullptr;  // IRLS weights of Solve-OF with p = q = 1 (P ns, 4 P ns)
     double *rn_of = nullptr;                  // norm^2 of its residual before orthogonalisation (P)
@@ -304,7 +304,8 @@ static long long of_partial_per_pair(const mof_problem *p, int Kof, int of_ell) 
     const long long gram_chunks = (ns + 511) / 512;  // chunks of the FP64 Gram kernel (the smaller)
     const long long gram = (long long)std::min(of_ell, Kof) * gram_chunks * (2LL * Kof + 1);
     const long long wgram = (long long)WG_CTAS * wg_pstride(Kof);
-    return std::max(std::max(krylov_partial_doubles(2 * ns, Kof), gram), wgram);
+    const long long pass = of_pass_chunks(ns, 8) * of_pass_stride(Kof);  // k_of_proj_gram_pass (FP64 chunks)
+    return std::max(std::max(std::max(krylov_partial_doubles(2 * ns, Kof), gram), wgram), pass);
 }
 
 template <typename real>
@@ -396,6 +397,9 @@ static mof_status ensure_ws(mof_problem *p, const mof_solver_params &prm, int n_
         w->gam = a.take<double>(P);
         w->nrm_of = a.take<double>(P);
         w->coef_of = a.take<double>((size_t)P * Kof);
+        w->Mg_of = a.take<double>((size_t)P * Kof * Kof);
+        w->pres_of = a.take<double>((size_t)P * of_pass_stride(Kof));
+        w->q_of = a.take<real>((size_t)P * N2);
         w->coefU_of = a.take<double>((size_t)P * (prm.of_ell + 1));
         w->scale_of = a.take<double>(P);
         w->alpha_of = a.take<double>(P);
@@ -481,6 +485,10 @@ __global__ void k_axpy_dev(real *__restrict__ x, long long xstride, const real *
     const real c = block_scalar<real>(coef + b);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
         x[b * xstride + i] -= c * y[b * ystride + i];
+}
+// err |= 16 when the data's squared norm is not finite (a NaN or an infinity in b)
+__global__ void k_flag_nonfinite(const double *__restrict__ v, int *__restrict__ err) {
+    if (threadIdx.x == 0 && !isfinite(v[0])) atomicOr(err, 16);
 }
 __global__ void k_sqrt_into(const double *__restrict__ a, double *__restrict__ b, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -593,6 +601,85 @@ __global__ void k_of_resid(const real *__restrict__ ux, const real *__restrict__
     r[b * 2 * ns + ns + i] = ay * a - AtB[b * 2 * ns + ns + i] + g * lap_at(v + ns, nx, ny, x, y);
 }
 
+// ---- Euclidean Gram Mg = V^T V of a pair's stored Solve-OF basis. The Golub-Kahan start
+// leaves orthonormal vectors (Mg = I there); each GKS append stores x'/||x'|| where x' is the
+// residual after ONE projection pass, and records its inner products with the earlier vectors
+// (the second pass's coefficients c2 = V^T x', which the fused pass computes anyway) in Mg.
+// The projection of the next residual then uses d = Mg^-1 (V^T r), the orthogonal projection
+// onto the stored basis's span; so the second update pass over the basis (x' - V c2) is never
+// applied to the vectors. The span, the Grams of the stored vectors and everything the small
+// solver computes from them (z, the parameter, s = V z) are those of the basis CGS twice
+// would store, up to rounding.
+__global__ void k_of_mg_init(double *__restrict__ Mg, int ld, const int *__restrict__ act, int B) {
+    const int b = blockIdx.x;
+    if (b >= B || (act && !act[b])) return;
+    double *M = Mg + (long long)b * ld * ld;
+    for (int e = threadIdx.x; e < ld * ld; e += blockDim.x) M[e] = (e / ld == e % ld) ? 1.0 : 0.0;
+}
+
+// c[b] <- Mg[b]^-1 c[b] over the first K[b] entries: Cholesky in shared memory by one warp
+// (lanes over rows), then the two triangular solves. Mg is near I (unit diagonal, off
+// diagonal the stored vectors' residual overlaps), so the factorisation is well conditioned.
+__global__ void __launch_bounds__(32) k_of_mg_solve(const double *__restrict__ Mg, double *__restrict__ c, int ld,
+                                                    const int *__restrict__ K, const int *__restrict__ act) {
+    extern __shared__ double mg_sm[];  // [ld][ld + 1] Cholesky factor (lower), then [ld] the right side
+    const int b = blockIdx.x, lane = threadIdx.x;
+    if (act && !act[b]) return;
+    const int Kb = min(K[b], ld), L = ld + 1;
+    double *Lm = mg_sm, *y = mg_sm + (long long)ld * L;
+    const double *M = Mg + (long long)b * ld * ld;
+    double *cb = c + (long long)b * ld;
+    for (int e = lane; e < Kb * Kb; e += 32) Lm[(e / Kb) * L + e % Kb] = M[(e / Kb) * ld + e % Kb];
+    for (int i = lane; i < Kb; i += 32) y[i] = cb[i];
+    __syncwarp();
+    for (int j = 0; j < Kb; ++j) {
+        // column j: rows i >= j, s_i = M[i][j] - sum_{k<j} L[i][k] L[j][k]
+        for (int i = j + lane; i < Kb; i += 32) {
+            double sum = Lm[i * L + j];
+            for (int k = 0; k < j; ++k) sum -= Lm[i * L + k] * Lm[j * L + k];
+            Lm[i * L + j] = sum;
+        }
+        __syncwarp();
+        const double d = sqrt(fmax(Lm[j * L + j], 1e-300));
+        for (int i = j + 1 + lane; i < Kb; i += 32) Lm[i * L + j] /= d;
+        __syncwarp();
+        if (lane == 0) Lm[j * L + j] = d;
+        __syncwarp();
+    }
+    if (lane == 0) {  // L y = c, then L^T d = y (K <= 64 sequential steps)
+        for (int i = 0; i < Kb; ++i) {
+            double t = y[i];
+            for (int k = 0; k < i; ++k) t -= Lm[i * L + k] * y[k];
+            y[i] = t / Lm[i * L + i];
+        }
+        for (int i = Kb - 1; i >= 0; --i) {
+            double t = y[i];
+            for (int k = i + 1; k < Kb; ++k) t -= Lm[k * L + i] * y[k];
+            y[i] = t / Lm[i * L + i];
+        }
+    }
+    __syncwarp();
+    for (int i = lane; i < Kb; i += 32) cb[i] = y[i];
+}
+
+// After an append (appended[b]; K[b] already counts the new vector): the new column of Mg,
+// Mg[i][new] = Mg[new][i] = c2[b][i] / ||x'|| for the earlier vectors, 1 on the diagonal.
+__global__ void k_of_mg_update(double *__restrict__ Mg, const double *__restrict__ c2, const double *__restrict__ nrm2,
+                               int ld, const int *__restrict__ K, const int *__restrict__ appended,
+                               const int *__restrict__ act) {
+    const int b = blockIdx.x;
+    if ((act && !act[b]) || !appended[b]) return;
+    const int knew = min(K[b], ld) - 1;
+    const double inv = 1.0 / sqrt(nrm2[b]);
+    double *M = Mg + (long long)b * ld * ld;
+    for (int i = threadIdx.x; i < knew; i += blockDim.x) {
+        const double v = c2[(long long)b * ld + i] * inv;
+        M[(long long)i * ld + knew] = v;
+        M[(long long)knew * ld + i] = v;
+    }
+    if (threadIdx.x == 0) M[(long long)knew * ld + knew] = 1.0;
+}
+
 // First CGS projection of the GKS residual from the Gram matrices: with
 // r = (Ups^T Ups + gamma (L(+)L)^T (L(+)L)) V z - Ups^T b, V^T r = (G_A + gamma G_L) z - g
 // exactly, so the coefficients need no pass over V. One warp per pair.
@@ -694,17 +781,32 @@ __global__ void __launch_bounds__(OFG_T) k_of_gram_cols(const real *__restrict__
         const real *vi = Vb + (long long)i * N2 + c0;
         real ga = 0, gl = 0;
         if (quad) {
+            // each step's eight products summed in FP32, the steps' partials accumulated
+            // with their rounding errors (DFAcc::add), the lanes in FP64
             const float4 *X4 = reinterpret_cast<const float4 *>(vi);
             const float4 *Y4 = reinterpret_cast<const float4 *>(vi + ns);
             const float4 *A0 = reinterpret_cast<const float4 *>(s_y[0]), *A1 = reinterpret_cast<const float4 *>(s_y[1]);
             const float4 *L0 = reinterpret_cast<const float4 *>(s_y[2]), *L1 = reinterpret_cast<const float4 *>(s_y[3]);
-#pragma unroll 2
-            for (int q = lane; q < OFC / 4; q += 32) {
-                const float4 X = __ldcs(X4 + q), Y = __ldcs(Y4 + q);
+            DFAcc da, dl;
+            // two quads of both components per step (16 products per partial); OFC / 4 is a
+            // multiple of 64, so every lane takes the same number of steps
+            for (int q = lane; q < OFC / 4; q += 64) {
+                const float4 X = __ldcs(X4 + q), Y = __ldcs(Y4 + q), X2 = __ldcs(X4 + q + 32), Y2 = __ldcs(Y4 + q + 32);
                 const float4 a0 = A0[q], a1 = A1[q], l0 = L0[q], l1 = L1[q];
-                ga += X.x * a0.x + X.y * a0.y + X.z * a0.z + X.w * a0.w + Y.x * a1.x + Y.y * a1.y + Y.z * a1.z + Y.w * a1.w;
-                gl += X.x * l0.x + X.y * l0.y + X.z * l0.z + X.w * l0.w + Y.x * l1.x + Y.y * l1.y + Y.z * l1.z + Y.w * l1.w;
+                const float4 b0 = A0[q + 32], b1 = A1[q + 32], m0 = L0[q + 32], m1 = L1[q + 32];
+                float pa = X.x * a0.x + X.y * a0.y + X.z * a0.z + X.w * a0.w + Y.x * a1.x + Y.y * a1.y + Y.z * a1.z + Y.w * a1.w;
+                pa += X2.x * b0.x + X2.y * b0.y + X2.z * b0.z + X2.w * b0.w + Y2.x * b1.x + Y2.y * b1.y + Y2.z * b1.z + Y2.w * b1.w;
+                float pl = X.x * l0.x + X.y * l0.y + X.z * l0.z + X.w * l0.w + Y.x * l1.x + Y.y * l1.y + Y.z * l1.z + Y.w * l1.w;
+                pl += X2.x * m0.x + X2.y * m0.y + X2.z * m0.z + X2.w * m0.w + Y2.x * m1.x + Y2.y * m1.y + Y2.z * m1.z + Y2.w * m1.w;
+                da.add(pa);
+                dl.add(pl);
             }
+            const double sa = warp_sum(da.value()), sl = warp_sum(dl.value());
+            if (lane == 0) {
+                out[2 * i] = sa;
+                out[2 * i + 1] = sl;
+            }
+            continue;
         } else {
             for (int q = lane; q < len; q += 32) {
                 const real vx = vi[q], vy = vi[ns + q];
@@ -1117,6 +1219,7 @@ constexpr int TG_S = TG_ROWS + 4;  // column stride of the shared row tile
 // blocks touch on eight different bank quads
 __host__ __device__ constexpr int tg_col(int j) { return j * TG_S + 4 * (j / 4); }
 constexpr int TG_MAXG = 8;         // row groups per 4x4 block at most
+constexpr int TG_VEC = 8;          // basis vectors per step of the difference rows (16 loads in flight)
 
 template <typename real>
 __device__ __forceinline__ void warp_axis_s(int x, real v, int n, int &i0, int &i1, real &w, int wm) {
@@ -1223,18 +1326,37 @@ __global__ void __launch_bounds__(TG_T, tg_min_blocks<real>()) k_theta_gram(cons
             sw = (real)1 / sqrt(sqrt(nu * nu + eps2));
         }
         const real *f = V;
-        for (int j = 0; j < K4 * 4; j += 4, f += 4 * n) {
-            real val[4];
+        if (rows == 1 || rows == 3) {
+            // difference rows (Psi, L_t): f[oc] - f[o00], two loads per vector (the general form
+            // below gives the same value, its other weights being zero)
+            for (int j = 0; j < K4 * 4; j += TG_VEC, f += TG_VEC * n) {
+                real val[TG_VEC];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                val[u] = 0;
-                if (valid && j + u < K) {
-                    const real *fu = f + (long long)u * n;
-                    val[u] = fu[oc] - (w00 * fu[o00] + w01 * fu[o01] + w10 * fu[o10] + w11 * fu[o11]);
+                for (int u = 0; u < TG_VEC; ++u) {
+                    val[u] = 0;
+                    if (valid && j + u < K) {
+                        const real *fu = f + (long long)u * n;
+                        val[u] = fu[oc] - fu[o00];
+                    }
                 }
-            }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) As[tg_col(j + u) + tid] = sw * val[u];
+                for (int u = 0; u < TG_VEC; ++u)
+                    if (j + u < K4 * 4) As[tg_col(j + u) + tid] = sw * val[u];
+            }
+        } else {
+            for (int j = 0; j < K4 * 4; j += 4, f += 4 * n) {
+                real val[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    val[u] = 0;
+                    if (valid && j + u < K) {
+                        const real *fu = f + (long long)u * n;
+                        val[u] = fu[oc] - (w00 * fu[o00] + w01 * fu[o01] + w10 * fu[o10] + w11 * fu[o11]);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) As[tg_col(j + u) + tid] = sw * val[u];
+            }
         }
         __syncthreads();
         if (acc_on) {
@@ -1339,6 +1461,7 @@ __global__ void k_report(double *__restrict__ rep, int *__restrict__ iter, const
 }
 
 static inline int fb(long long n) { return (int)std::min<long long>(152 * 8, (n + 255) / 256); }
+static inline size_t mg_solve_smem(int ld) { return sizeof(double) * ((size_t)ld * (ld + 1) + ld); }
 
 // ============================================================ Solve-OF
 template <typename real>
@@ -1359,13 +1482,14 @@ static mof_status solve_of_impl(mof_problem *p, const mof_solver_params &prm, WS
     // FP64 solves occupy one SM per pair and are latency bound, and its GKB steps
     // are short launches, so the groups fill the GPU together. Every kernel works
     // per pair, so the grouping does not change the result.
-    const int G = std::max(1, std::min(prm.of_streams > 0 ? prm.of_streams : AUTO_OF_STREAMS, P));
+    // the plain form: one pair per group, all on the solver's stream one after another
+    const int G = prm.plain ? P : std::max(1, std::min(prm.of_streams > 0 ? prm.of_streams : AUTO_OF_STREAMS, P));
     const long long part_pair = of_partial_per_pair(p, Kof, w.of_ell);
-    MOF_CUDA(cudaEventRecord(w.gfork, st));
+    if (!prm.plain) MOF_CUDA(cudaEventRecord(w.gfork, st));
     for (int gi = 0; gi < G; ++gi) {
         const int b0 = (int)((long long)gi * P / G), nb = (int)((long long)(gi + 1) * P / G) - b0;
-        const cudaStream_t gst = w.gs[gi];
-        MOF_CUDA(cudaStreamWaitEvent(gst, w.gfork, 0));
+        const cudaStream_t gst = prm.plain ? st : w.gs[gi];
+        if (!prm.plain) MOF_CUDA(cudaStreamWaitEvent(gst, w.gfork, 0));
         Krylov<real> kg;
         kg.partial = w.partial + b0 * part_pair;
         kg.err = w.err;
@@ -1416,6 +1540,9 @@ static mof_status solve_of_impl(mof_problem *p, const mof_solver_params &prm, WS
                                                                                              w.GA + b0 * KK, w.GL + b0 * KK,
                                                                                              w.gof + (long long)b0 * Kof);
         }
+        ::mof::count_launch(), k_of_mg_init<<<nb, 256, 0, gst>>>(w.Mg_of + (long long)b0 * KK, Kof, actg, nb);
+        // the one-pass projection with the Gram column needs 16-byte aligned component segments
+        const bool pass_ok = !pq1 && Kof <= 64 && of_pass_applicable<real>(ns, Vg, wvg);
         SmallArgs sa{};
         sa.GA = w.GA + b0 * KK;
         sa.GL = w.GL + b0 * KK;
@@ -1467,29 +1594,47 @@ static mof_status solve_of_impl(mof_problem *p, const mof_solver_params &prm, WS
                 ::mof::count_launch(), k_of_resid<real><<<gg, blk2, 0, gst>>>(uxg, uyg, AtBg, sg, sa.lam, wvg, p->nx, p->ny, actg);
             }
             {
-                // CGS2: the first projection's coefficients from the Grams, the second by
-                // dot products (fused with the first update); then the second update. The
-                // fused pass has a timing class of its own.
+                // Projection of the residual onto the complement of the stored basis's span in
+                // one pass over the basis: V^T r from the Grams, d = Mg^-1 V^T r, then the fused
+                // pass x' = r - V d with c2 = V^T x' and ||x'||^2; the append stores x'/||x'|| and
+                // c2 / ||x'|| becomes the new column of Mg (see k_of_mg_init).
                 double *cg = w.coef_of + (long long)b0 * Kof;
+                double *Mgg = w.Mg_of + (long long)b0 * KK;
                 {
                     Scope sc(tm, "of_reorth", gst);
                     ::mof::count_launch(), k_of_proj_gram<<<nb, 32, 0, gst>>>(sa.GA, sa.GL, sa.g, sa.z, sa.lam, Kvg, actg, Kof, cg);
+                    ::mof::count_launch(), k_of_mg_solve<<<nb, 32, mg_solve_smem(Kof), gst>>>(Mgg, cg, Kof, Kvg, actg);
                 }
                 // at GKS iteration it the basis holds at most of_ell + it vectors (one append per iteration)
                 const int kcap = std::min(Kof, prm.of_ell + it);
+                if (pass_ok) {
+                    // p = q = 2: the projection, the new vector's Gram columns and the append in
+                    // one pass over the basis (no separate Gram-column pass after it)
+                    Scope sc(tm, "of_subdot", gst);
+                    MOF_TRY(launch_of_proj_gram_pass<real>(BAg, Kvg, ns, p->nx, p->ny, cg, wvg, w.q_of + (long long)b0 * N2, AtBg,
+                                                           uxg, uyg, kg.partial, w.pres_of + (long long)b0 * of_pass_stride(Kof),
+                                                           w.err, kcap, w.scale_of + b0, tol, w.grow_of + b0, w.GA + b0 * KK,
+                                                           w.GL + b0 * KK,
+                                                           w.gof + (long long)b0 * Kof, Mgg, w.nrm_of + b0, appg, kg.aux, gst));
+                    continue;
+                }
                 bool fused;
+                int nparts = 0;
                 {
                     Scope sc(tm, "of_subdot", gst);
-                    fused = kg.sub_dot(BAg, cg, Kof, wvg, N2, cg, gst, kcap);
+                    fused = kg.sub_dot(BAg, cg, Kof, wvg, N2, cg, gst, kcap, &nparts);
                 }
                 Scope sc(tm, "of_reorth", gst);
-                if (!fused) {
+                if (fused) {
+                    kg.append_parts(BAg, Kvg, wvg, N2, nparts, w.nrm_of + b0, w.scale_of + b0, tol, w.grow_of + b0, appg, nullptr,
+                                    nullptr, nullptr, gst, kg.partial + (long long)nb * nparts * Kof);
+                } else {
                     kg.subtract(BAg, cg, Kof, wvg, N2, wvg, N2, nullptr, gst);
                     kg.dots(BAg, wvg, N2, cg, Kof, 1.0, gst);
+                    kg.norm2(wvg, N2, N2, nb, w.nrm_of + b0, gst);
+                    kg.append(BAg, Kvg, wvg, N2, w.nrm_of + b0, w.scale_of + b0, tol, w.grow_of + b0, appg, nullptr, gst);
                 }
-                const int np = kg.subtract_parts(BAg, cg, Kof, wvg, N2, wvg, N2, gst);
-                kg.append_parts(BAg, Kvg, wvg, N2, np, w.nrm_of + b0, w.scale_of + b0, tol, w.grow_of + b0, appg, nullptr, nullptr,
-                                nullptr, gst);
+                ::mof::count_launch(), k_of_mg_update<<<nb, 64, 0, gst>>>(Mgg, cg, w.nrm_of + b0, Kof, Kvg, appg, actg);
             }
             if (!pq1) {
                 Scope sc(tm, "of_gram", gst);
@@ -1500,9 +1645,10 @@ static mof_status solve_of_impl(mof_problem *p, const mof_solver_params &prm, WS
                                                                                               w.gof + (long long)b0 * Kof);
             }
         }
-        MOF_CUDA(cudaEventRecord(w.gdone[gi], gst));
+        if (!prm.plain) MOF_CUDA(cudaEventRecord(w.gdone[gi], gst));
     }
-    for (int gi = 0; gi < G; ++gi) MOF_CUDA(cudaStreamWaitEvent(st, w.gdone[gi], 0));
+    if (!prm.plain)
+        for (int gi = 0; gi < G; ++gi) MOF_CUDA(cudaStreamWaitEvent(st, w.gdone[gi], 0));
     MOF_LAUNCH_CHECK();
     return MOF_OK;
 }
@@ -1644,16 +1790,17 @@ mof_status SolveRun<real>::begin(cudaStream_t ust) {
     {
         Scope sc(tm, "gkb", st);
         kr.norm2(w.b, m, m, 1, w.bb, st, true);  // ||b||^2 enters rho0^2 = ||b||^2 - ||c||^2 of DP
+        ::mof::count_launch(), k_flag_nonfinite<<<1, 32, 0, st>>>(w.bb, w.err);
         ::mof::count_launch(), k_sqrt_into<<<1, 1, 0, st>>>(w.bb, w.beta1, 1);
         kr.append(BU, w.KU, w.b, m, w.bb, nullptr, 0.0, w.gkb, nullptr, nullptr, st);
         for (int j = 0; j < prm.ell; ++j) {
-            MOF_TRY(launch_backproject<real>(p, w.U + (long long)j * m, w.r, st));
+            MOF_TRY(launch_backproject<real>(p, w.U + (long long)j * m, w.r, st, prm.plain));
             if (j > 0) ::mof::count_launch(), k_axpy_dev<real><<<dim3(fb(n), 1), 256, 0, st>>>(w.r, n, w.V + (long long)(j - 1) * n, n, w.beta, n, w.gkb);
             kr.reorth_second(BV, w.r, n, nullptr, w.coef, w.nrm2, st);  // V^T x = 0 by the recurrence
             if (j == 0) ::mof::count_launch(), k_sqrt_into_if<<<1, 1, 0, st>>>(w.nrm2, w.alpha1, 1, w.gkb);
             ::mof::count_launch(), k_sqrt_into_if<<<1, 1, 0, st>>>(w.nrm2, w.alpha, 1, w.gkb);
             kr.append(BV, w.K, w.r, n, w.nrm2, j == 0 ? nullptr : w.alpha1, tol, w.gkb, nullptr, nullptr, st);
-            MOF_TRY(launch_project<real>(p, w.V + (long long)j * n, w.uT, w.HV + (long long)j * m, st));
+            MOF_TRY(launch_project<real>(p, w.V + (long long)j * n, w.uT, w.HV + (long long)j * m, st, prm.plain));
             ::mof::count_launch(), k_copy<real><<<fb(m), 256, 0, st>>>(w.HV + (long long)j * m, w.tm, m);
             ::mof::count_launch(), k_axpy_dev<real><<<dim3(fb(m), 1), 256, 0, st>>>(w.tm, m, w.U + (long long)j * m, m, w.alpha, m, w.gkb);
             kr.reorth_second(BU, w.tm, m, nullptr, w.coef, w.nrm2, st);
@@ -1755,7 +1902,7 @@ mof_status SolveRun<real>::iteration(bool of_now, bool expand) {
         if (expand) {
             {
                 Scope sc(tm, "backproject", st);
-                MOF_TRY(launch_backproject<real>(p, w.tm, w.tn, st));
+                MOF_TRY(launch_backproject<real>(p, w.tm, w.tn, st, prm.plain));
             }
             {
                 Scope sc(tm, "reg_normal", st);
@@ -1771,7 +1918,7 @@ mof_status SolveRun<real>::iteration(bool of_now, bool expand) {
             }
             {
                 Scope sc(tm, "project", st);
-                MOF_TRY(launch_project<real>(p, w.vnew, w.uT, w.hvnew, st));
+                MOF_TRY(launch_project<real>(p, w.vnew, w.uT, w.hvnew, st, prm.plain));
                 ::mof::count_launch(), k_store_slot<real><<<fb(m), 256, 0, st>>>(w.HV, m, w.K, w.appended, w.hvnew);
             }
             {
@@ -1803,6 +1950,7 @@ mof_status SolveRun<real>::step(int k) {
     WS<real> &w = *wp;
     const bool of_now = prm.tau > 0 && (k % prm.tau) == 0;
     const bool expand = k < n_outer - 1;
+    if (prm.plain) return iteration(of_now, expand);  // every launch from the host, no graph
     auto &G = w.graphs[(of_now ? 1 : 0) | (expand ? 2 : 0) | (tm ? 4 : 0)];
     if (!G.exec) {
         if (tm) {
@@ -1872,6 +2020,7 @@ mof_status SolveRun<real>::result() {
             report[k].of_basis_max = (int)r[6];
         }
     if (err & 4) return fail(MOF_ETIMEOUT, "a bounded device wait ran out (code %d)", err);
+    if (err & 16) return fail(MOF_ENUMERIC, "the data b hold a non-finite value (code %d)", err);
     if (err & 8) return fail(MOF_ENUMERIC, "a basis exceeded an internal size bound (code %d)", err);
     if (err) return fail(MOF_ENUMERIC, "device reported a numerical failure (code %d): factorisation or non-finite value", err);
     return MOF_OK;
@@ -1914,7 +2063,7 @@ static mof_status solve_of_entry(mof_problem *p, const mof_solver_params &prm, c
     MOF_CUDA(cudaEventRecord(w.join, ust));
     MOF_CUDA(cudaStreamWaitEvent(st, w.join, 0));
     const long long nimg = p->n, nvel = (long long)(p->nt - 1) * 2 * p->ns;
-    if (tm) {  // timed calls run eagerly (the scopes record events around each class)
+    if (tm || prm.plain) {  // timed calls and the plain form run eagerly
         ::mof::count_launch(), k_fill_int<<<1, 32, 0, st>>>(w.err, 1, 0);
         MOF_TRY(of_step<real>(p, prm, w, u, s, tm, st));
     } else {
@@ -1972,6 +2121,7 @@ static mof_status check_params(const mof_problem *p, const mof_solver_params *pr
     if (!(prm->eps > 0) || !std::isfinite(prm->eps)) return fail(MOF_EINVAL, "eps must be finite and > 0");
     if (prm->temporal_tv != 0 && prm->temporal_tv != 1) return fail(MOF_EINVAL, "temporal_tv must be 0 or 1");
     if (prm->of_pq != 1 && prm->of_pq != 2) return fail(MOF_EINVAL, "of_pq must be 1 or 2 (got %d)", prm->of_pq);
+    if (prm->plain != 0 && prm->plain != 1) return fail(MOF_EINVAL, "plain must be 0 or 1 (got %d)", prm->plain);
     if (prm->of_scale < 1 || p->nx % prm->of_scale || p->ny % prm->of_scale || p->nx / prm->of_scale < 2 ||
         p->ny / prm->of_scale < 2)
         return fail(MOF_EINVAL, "of_scale must be >= 1, divide nx and ny and leave frames of at least 2x2 (got %d for %d x %d)",

@@ -82,8 +82,10 @@ struct Krylov {
                        double *nrm2_out, cudaStream_t st, int kcap = 0) const;
     // x[b] <- x[b] - V[b] c[b] and out[b] = V[b]^T x[b] in one pass over V (false: not
     // applicable to this layout, nothing enqueued)
+    // nparts (may be null): also the chunk partials of ||x'[b]||^2, after the dot partials in
+    // partial (at partial + B.B * nparts * Kmax), their number per problem in *nparts
     bool sub_dot(const BasisRef<real> &B, const double *c, long long cstride, real *x, long long xstride, double *out,
-                 cudaStream_t st, int kcap = 0) const;
+                 cudaStream_t st, int kcap = 0, int *nparts = nullptr) const;
     // x[b] <- x[b] - V[b] c[b], the per-block partials of ||x[b]||^2 left in partial;
     // returns their number per problem (for append_parts)
     int subtract_parts(const BasisRef<real> &B, const double *c, long long cstride, const real *x, long long xstride,
@@ -93,14 +95,34 @@ struct Krylov {
                             cudaStream_t st, int kcap = 0) const;
     // append with ||x||^2 summed from the nparts partials of the preceding update (written to
     // nrm2_out), and sqrt(||x||^2) written to sq1 / sq2 (may be null) for problems still growing
+    // (parts: where the partials are, default the start of partial)
     void append_parts(const BasisRef<real> &B, int *Kmut, const real *x, long long xstride, int nparts, double *nrm2_out,
                       const double *scale, double tol, int *grow, int *appended, real *stage, double *sq1, double *sq2,
-                      cudaStream_t st) const;
+                      cudaStream_t st, const double *parts = nullptr) const;
     // V[b][K[b]] = x[b]/||x[b]||, K[b]++ unless ||x[b]|| <= tol*scale[b] (then grow[b] = 0);
     // scale may be null (only ||x|| > 0 required); stage[b] (may be null) receives the new vector
     void append(const BasisRef<real> &B, int *Kmut, const real *x, long long xstride, const double *nrm2,
                 const double *scale, double tol, int *grow, int *appended, real *stage, cudaStream_t st) const;
 };
+
+// Solve-OF (p = q = 2) GKS step after the projection coefficients d: the graph Laplacian q of
+// the residual x, then one pass over the basis forming x' = x - V d (in x) with the dot
+// products that give the new vector's Gram columns, the append decision, the new columns of
+// G_A, G_L, g and Mg, and the append of x'/||x'|| (krylov.cu, k_of_proj_gram_pass).
+// partial: [B][chunks][3 Kmax + 4] doubles; res: [B][3 Kmax + 4]; q: [B][2 ns] scratch.
+long long of_pass_chunks(long long ns, int elem_bytes);
+int of_pass_stride(int Kmax);
+template <typename real> bool of_pass_applicable(long long ns, const void *V, const void *x);
+template <typename real>
+mof_status launch_of_proj_gram_pass(const BasisRef<real> &B, int *Kmut, long long ns, int nx, int ny, const double *d, real *x,
+                                    real *q, const real *AtB, const real *ux, const real *uy, double *partial,
+                                    double *res, int *err, int kcap, const double *scale, double tol, int *grow,
+                                    double *GA, double *GL, double *g, double *Mg, double *nrm2_out, int *appended,
+                                    double *aux, cudaStream_t st);
+
+// Bound of the device waits on tile copies for the current device (polls; < 0: the
+// default); used by mof_debug_set_wait_limit.
+mof_status set_wait_polls(long long polls);
 
 // ------------------------------------------------------ small FP64 solver
 // One projected problem per block: min ||A V z - b||^2 + lam ||L V z||^2
