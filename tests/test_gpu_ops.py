@@ -273,6 +273,7 @@ def test_reg_normal(shape, prec):
     nu = th(host(uk))
     w = 1.0 / np.sqrt(nu * nu + eps * eps)
     want = th.T(w * th(host(x)))
+    print("reg_normal %s rel %.3g" % (prec, rel(host(y), want)))
     assert rel(host(y), want) <= 3 * TOL[prec]
 
 
@@ -342,6 +343,7 @@ def test_round_warp_reg_normal(prec):
     th = OS.Theta((nt, ny, nx), host(s).reshape(sh), host(sr).reshape(sh), warp_round=True)
     nu = th(host(uk))
     want = th.T(th(host(x)) / np.sqrt(nu * nu + eps * eps))
+    print("reg_normal %s rel %.3g" % (prec, rel(host(y), want)))
     assert rel(host(y), want) <= 3 * TOL[prec]
 
 

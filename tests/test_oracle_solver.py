@@ -437,3 +437,23 @@ def test_round_warp_mm_step_full_subspace_equals_dense_normal_equations():
         u = np.linalg.solve(Hd.T @ Hd + prm.lam_fixed * Th.T @ (w[:, None] * Th), Hd.T @ b)
         np.testing.assert_allclose(res.u.ravel(), u, rtol=1e-8, atol=1e-10)
 
+
+
+def test_solve_of_pq1_is_sensitive_at_the_rounding_level():
+    """The conditioning behind the p = q = 1 parity bound: the oracle's own Solve-OF with
+    p = q = 1 (MM-GKS, App. A, default 10 + 20 iterations) on the 64x64x8 two-disk frames
+    moves by more than 1e-6 when the frames are perturbed by 1e-15 relative (the IRLS
+    weights reach 1/eps and each GCV minimum is resolved to about the square root of the
+    FP64 rounding), while p = q = 2 moves by less than 1e-6. Two FP64 implementations that
+    round differently therefore agree on p = q = 1 velocities only to about 1e-5."""
+    from paper_2501_12497_gb300 import synth
+    w = synth.plain_fp64(0)
+    u = w.u_true
+    up = u * (1 + 1e-15 * np.random.default_rng(5).standard_normal(u.shape))
+
+    def rel(a, b):
+        return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+    d1 = rel(solver.solve_of(up, solver.Params(of_pq=1)), solver.solve_of(u, solver.Params(of_pq=1)))
+    d2 = rel(solver.solve_of(up, solver.Params()), solver.solve_of(u, solver.Params()))
+    assert d1 > 1e-6 and d2 < 1e-6, (d1, d2)
