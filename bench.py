@@ -1,19 +1,24 @@
 """Benchmark of the MMGKS-OF hot path on GB300.
 
 One step = one complete MMGKS-OF solve (Alg. 1) of 30 outer iterations, each
-with a Solve-OF (Alg. 2, 20 GKS iterations on every one of the 31 frame
-pairs), on the 256x256x32 moving-ellipse workload (30 angles per frame
-rotating across frames, 363 bins, 1% noise): FP32 operators, FP64 Krylov
-bookkeeping and projected solves. The metric is outer solver iterations per
-second over the whole job (N GPUs x steps x 30 / time).
+with a Solve-OF (Alg. 2, 20 GKS iterations on every frame pair), FP32
+operators and FP64 Krylov bookkeeping and projected solves. Default workload:
+the large single problem, 1024x1024 frames, T = 64, 90 angles per frame
+rotating across frames, 1448 bins, 20 ellipses on a smooth background in rigid
+plus smooth non-rigid motion (up to 3 px/frame), 0.5% noise.
+`--workload ellipses256x256x32` runs the 256x256x32 six-ellipse problem (30
+angles, 363 bins, 1% noise). The metric is outer solver iterations per second
+over the whole job (N GPUs x steps x 30 / time).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload ...]
 
 N > 1 runs under torchrun with one process per GPU: every rank solves its own
 seeded problem of the same shape (independent replicas, no collective in the
 data path); rank 0 prints one JSON line with the max-over-ranks time.
 --impl reference times the FP64 CPU oracle on the host cores instead (the
-same workload and metric, a bounded sample per step, extrapolated).
+same workload and metric, on a bounded sample, extrapolated as stated in its
+line).
 """
 import argparse
 import json
@@ -28,9 +33,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_OUTER = 30
-WORKLOAD = "ellipses256x256x32"
-CFG = dict(n=256, nt=32, na=30, nb=363)
+OF_ITERS, OF_ELL, ELL = 20, 10, 10
+# the solve workloads: generator name in synth, sizes
+WORKLOADS = {
+    "ellipses1024x1024x64": ("large_form", dict(n=1024, nt=64, na=90, nb=1448)),
+    "ellipses256x256x32": ("precision_form", dict(n=256, nt=32, na=30, nb=363)),
+}
+DEFAULT_WORKLOAD = "ellipses1024x1024x64"
 L2_FLUSH_BYTES = 512 << 20
+# accuracy bar of the precision form on images and velocities after the fixed iteration count
+TOL_PRECISION_FORM = 1e-4
 
 
 def parse():
@@ -41,14 +53,16 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the FP64 reference solve that time_to_tolerance_s is checked against")
     ap.add_argument("--no-class-step", action="store_true",
                     help="skip the instrumented single-stream step (no class times, no roofline); for profiling runs")
-    ap.add_argument("--workload", choices=["ellipses256x256x32", "batch48", "ellipses1024x1024x64", "operators",
-                                           "solve_of"],
-                    default="ellipses256x256x32",
-                    help="the 256x256x32 ellipse problem (default), 48 uneven problems batched, "
-                         "the 1024x1024x64 problem, every operator alone, or Solve-OF alone "
-                         "(one call per step on the 256x256x32 frames)")
+    ap.add_argument("--workload", choices=list(WORKLOADS) + ["batch48", "operators", "solve_of"],
+                    default=DEFAULT_WORKLOAD,
+                    help="the 1024x1024x64 problem (default), the 256x256x32 problem, 48 uneven problems "
+                         "batched, every operator alone, or Solve-OF alone (one call per step)")
+    ap.add_argument("--size", type=int, default=1024, choices=[256, 1024],
+                    help="frame size of --workload operators / solve_of: 1024 (the 1024x1024x64 sizes) or 256")
     ap.add_argument("--of-streams", type=int, default=0,
                     help="frame-pair groups of Solve-OF on separate streams (0 = library default)")
     ap.add_argument("--of-scale", type=int, default=1,
@@ -58,13 +72,22 @@ def parse():
     ap.add_argument("--temporal-tv", type=int, default=0, choices=[0, 1],
                     help="1: the D1-OF regulariser (temporal differences added to Theta)")
     ap.add_argument("--geometry", default="parallel", choices=["parallel", "fan"],
-                    help="fan: the same workload in a flat fan beam (source 512 px, detector 256 px beyond "
-                         "the centre, 363 bins of 1.6 px)")
+                    help="fan (256x256x32 only): the same workload in a flat fan beam (source 512 px, detector "
+                         "256 px beyond the centre, 363 bins of 1.6 px)")
     ap.add_argument("--of-pq", type=int, default=2, choices=[1, 2],
                     help="norms of Solve-OF: 2 (p = q = 2, the paper's experiments) or 1 (p = q = 1 by MM-GKS)")
     ap.add_argument("--warp", default="bilinear", choices=["bilinear", "round"],
                     help="encoding of the warp M(s) (Sec. 3): bilinear interpolation or rounding and clipping")
     return ap.parse_args()
+
+
+def make_workload(name, seed, geometry="parallel"):
+    from paper_2501_12497_gb300 import synth
+    if geometry == "fan":
+        if name != "ellipses256x256x32":
+            raise SystemExit("--geometry fan is defined for --workload ellipses256x256x32")
+        return synth.fan_form(seed=seed)
+    return getattr(synth, WORKLOADS[name][0])(seed=seed)
 
 
 def dist_env():
@@ -91,19 +114,15 @@ def job_value(world, steps, n_outer, total_ms):
 
 
 # ------------------------------------------------------------ CPU oracle sample
-def oracle_outer_iteration_seconds(w):
-    """Time the oracle (as it stands) on a bounded sample of one outer iteration:
-    Solve-OF of one frame pair (the step the paper names as the bottleneck) on the
-    reconstruction's ground-truth frames, scaled by the number of pairs; the image
-    step's own cost is left out, so the figure flatters the oracle."""
-    import numpy as np
-    from oracle import ops, solver
-    prm = solver.Params(noise_norm=w.noise_norm)
-    ux, uy, ut = ops.of_fields(w.u_true[:2], prm.of_dr)
+def _pair_job(args):
+    """One Solve-OF pair of the oracle, timed inside the worker (a spawned process whose
+    BLAS runs one thread: the pool is started with OPENBLAS_NUM_THREADS=1 and
+    OMP_NUM_THREADS=1 in its environment)."""
+    ux, uy, ut = args
+    from oracle import solver
     t0 = time.perf_counter()
-    solver.solve_of_pair(ux[0], uy[0], ut[0], prm)
-    dt = time.perf_counter() - t0
-    return dt * (w.nt - 1), dt
+    solver.solve_of_pair(ux, uy, ut, solver.Params())
+    return time.perf_counter() - t0
 
 
 def cpu_cores():
@@ -113,30 +132,135 @@ def cpu_cores():
         return os.cpu_count() or 1
 
 
+def oracle_sample(w, pool_size):
+    """The FP64 oracle (as it stands) timed on a bounded sample of one outer iteration of
+    Alg. 1 on workload w, and the outer iteration's time extrapolated from it.
+
+    Solve-OF: the oracle solves frame pair 0 of w (its true frames; the per-pair work of an
+    outer iteration) on centred crops of nc x nc pixels; a pair of the full frames takes
+    minutes, so two crop sizes are timed alone on one thread (nc = 128 and 256, or the frame
+    size when smaller) and the time is extrapolated linearly in the pixel count to the full
+    frame (the oracle's per-pair work is QR factorisations and operators linear in the
+    pixels, plus a fixed cost per GKS iteration); the larger crop is also run in
+    `pool_size` concurrent single-threaded processes, whose slowdown over the lone run
+    scales the all-cores figure. Image step: the projector and its adjoint on frame 0, Psi on
+    one frame, Mhat on one pair, Theta^T on one pair, the QR of one frame's P Theta V block
+    with the mid-solve basis size K and the two reorthogonalisations of one frame's share of
+    the basis, at the full frame size, scaled to all frames and pairs (per frame or pair the
+    oracle's outer iteration applies H once, H^T once, Theta K + 2 times and Theta^T once,
+    factors P Theta V and reorthogonalises). One thread: T - 1 pairs one after another plus
+    the image step; all cores: ceil((T - 1) / pool_size) rounds of the pool plus the image
+    step (the oracle's image step runs on one thread)."""
+    import numpy as np
+    from multiprocessing import get_context
+    from oracle import ops, solver
+    nt, ny, nx = w.u_true.shape
+    P = nt - 1
+    K = ELL + N_OUTER // 2
+
+    def crop(c):
+        y0, x0 = (ny - c) // 2, (nx - c) // 2
+        f = w.u_true[:2, y0:y0 + c, x0:x0 + c]
+        ux, uy, ut = ops.of_fields(f, solver.Params().of_dr)
+        return ux[0], uy[0], ut[0]
+
+    sizes = sorted({min(128, nx, ny), min(256, nx, ny)})
+    lone = {}
+    saved = {k: os.environ.get(k) for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:  # the workers' BLAS: one thread each (read when a worker first loads numpy)
+        os.environ[k] = "1"
+    try:
+        with get_context("spawn").Pool(max(1, min(pool_size, P))) as pool:
+            for c in sizes:  # alone, one process
+                lone[c] = pool.apply(_pair_job, (crop(c),))
+            big = sizes[-1]
+            jobs = [crop(big)] * max(1, min(pool_size, P))
+            t0 = time.perf_counter()
+            per = pool.map(_pair_job, jobs)
+            wall_pool = time.perf_counter() - t0
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    nfull = nx * ny
+    if len(sizes) == 2 and sizes[0] != sizes[1]:
+        a0, a1 = sizes[0] ** 2, sizes[1] ** 2
+        slope = (lone[sizes[1]] - lone[sizes[0]]) / (a1 - a0)
+        t_pair = lone[sizes[1]] + slope * (nfull - a1)
+    else:
+        t_pair = lone[big] * nfull / big ** 2
+    slow = wall_pool / lone[big]  # the pool's slowdown over the lone run
+
+    def timed(fn, reps=1):
+        t = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        return (time.perf_counter() - t) / reps
+
+    na0 = int(w.na[0])
+    g1 = ops.Geometry(w.nx, w.ny, 1, w.nb, w.na[:1], w.angles[:na0], w.h, w.db, getattr(w, "fan", None))
+    f0 = w.u_true[:1]
+    t_h = timed(lambda: ops.project(g1, f0))
+    t_ht = timed(lambda: ops.backproject(g1, w.b[:na0 * w.nb]))
+    rng = np.random.default_rng(0)
+    s1 = rng.uniform(-2, 2, (1, 2, ny, nx))
+    sr1 = ops.reverse_flow(s1)
+    t_psi = timed(lambda: ops.grad(f0), 3)
+    t_mhat = timed(lambda: ops.flow(w.u_true[:2], s1, sr1), 2)
+    r1 = rng.standard_normal((2, 1, ny, nx))
+    t_thT = timed(lambda: ops.gradT(rng.standard_normal((2, 2, ny, nx))) + ops.flowT(r1, s1, sr1))
+    blk = rng.standard_normal((6 * ny * nx, K))  # one frame's rows of P Theta V (Psi 2, Mhat 4 per pixel)
+    t_qr = timed(lambda: np.linalg.qr(blk, mode="r"))
+    V1 = np.linalg.qr(rng.standard_normal((ny * nx, K)))[0]
+    r = rng.standard_normal(ny * nx)
+    t_re = timed(lambda: solver.reorth(r, V1), 3)
+    t_image = (nt * (t_h + t_ht + t_re) + (K + 2) * (nt * t_psi + P * t_mhat) + P * t_thT + P * t_qr)
+    t1 = P * t_pair + t_image
+    rounds = math.ceil(P / len(jobs))
+    tall = rounds * t_pair * slow + t_image
+    sample = ("oracle on %s: Solve-OF of frame pair 0 on centred crops, %s pixels alone (%s s) and %d^2 in %d "
+              "concurrent single-threaded processes (%.1f s wall), extrapolated linearly in pixels to a %dx%d "
+              "pair (%.1f s), x%d pairs; image step from H, H^T, Psi, Mhat, Theta^T, the QR of P Theta V and the "
+              "reorthogonalisation timed on single full frames with K = %d and scaled to %d frames (%.1f s); one "
+              "outer iteration: %.1f s on one thread, %.1f s on %d processes"
+              % (w.name, "/".join("%d^2" % c for c in sizes), "/".join("%.1f" % lone[c] for c in sizes), big,
+                 len(jobs), wall_pool, nx, ny, t_pair, P, K, nt, t_image, t1, tall, len(jobs)))
+    return {"single_thread_s": t1, "all_cores_s": tall, "processes": len(jobs), "sample": sample,
+            "pair_s": t_pair, "image_s": t_image, "pool_wall_s": wall_pool}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    from paper_2501_12497_gb300 import synth
-    w = synth.precision_form(0)
-    for _ in range(args.warmup):
-        oracle_outer_iteration_seconds(w)
-    tot = 0.0
-    sample = 0.0
-    for _ in range(args.steps):
-        est, dt = oracle_outer_iteration_seconds(w)
-        tot += est
-        sample += dt
-    value = args.steps / tot
+    if args.workload not in WORKLOADS:
+        print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the solve workloads only"}))
+        return
+    w = make_workload(args.workload, 0, args.geometry)
+    cores = cpu_cores()
+    # one bounded sample (tens of seconds), repeated for the timed steps only as far as a
+    # few minutes allow; the line states how many samples were taken
+    res = []
+    t_start = time.perf_counter()
+    for i in range(max(1, args.steps)):
+        res.append(oracle_sample(w, min(cores, w.nt - 1)))
+        if time.perf_counter() - t_start > 150.0:
+            break
+    tall = sum(r["all_cores_s"] for r in res) / len(res)
+    t1 = sum(r["single_thread_s"] for r in res) / len(res)
+    value = 1.0 / tall
+    wl, cfg = args.workload, WORKLOADS[args.workload][1]
     line = {
         "impl": "reference", "metric": "mmgks_of_outer_iterations_per_s", "value": value,
         "unit": "outer_iters/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": 1e3 * tall * N_OUTER, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, **CFG, "n_outer": N_OUTER, "of_iters": 20, "ell": 10},
-        "cpu_baseline": {"value": value, "unit": "outer_iters/s", "cores": cpu_cores(), "kind": "oracle",
-                         "sample": "per step: Solve-OF of 1 of the 31 frame pairs (%.1f s measured), "
-                                   "x31 = one outer iteration; image step not counted" % (sample / args.steps)},
+        "config": {"workload": wl, **cfg, "n_outer": N_OUTER, "of_iters": OF_ITERS, "ell": ELL},
+        "cpu_baseline": {"value": value, "unit": "outer_iters/s", "cores": res[0]["processes"], "kind": "oracle",
+                         "single_thread_value": 1.0 / t1, "host_cores": cores,
+                         "samples_taken": len(res), "sample": res[0]["sample"]},
         "e2e": {"value": value, "unit": "outer_iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -191,17 +315,50 @@ class Clocks:
 
 
 # ------------------------------------------------------------ roofline models
-def subdot_bytes(nvec_list, N, pairs, es=4):
-    """Algorithmic bytes of the fused CGS pass (k_sub_dot) over a solve: x - V c1 and
-    V^T (x - V c1) read the K basis vectors and x and write x once, K + 2 vectors of N
-    values, K the basis size at each call, for every active pair."""
-    return sum(pairs * es * N * (K + 2) for K in nvec_list)
+def class_bytes(name, w, of_scale=1, tau=1):
+    """Algorithmic bytes (minimum FP32 traffic) of one solve's work in a timing class of
+    the library, and the number of launches of its main kernel, from the basis sizes of a
+    solve without breakdown (the reports confirm it: image basis ELL + k, Solve-OF basis
+    OF_ELL + OF_ITERS - 1 at the end). None for classes without a model.
+
+    Solve-OF, per pair and GKS iteration it (basis K = OF_ELL + it, vectors of N2 = 2 ns
+    values): of_combine s = V z reads K vectors and writes s; of_subdot (the projection pass
+    with the new vector's Gram column, k_of_proj_gram_pass, and around it the Laplacian of the
+    residual, the reduction and the append) reads the K basis vectors, the residual, its
+    Laplacian, Ups^T b and the fields u_x, u_y (one vector's worth) and writes x'; the
+    Laplacian pass reads the residual and writes its Laplacian; the append reads x' and writes
+    the new vector: K + 9 vectors; of_gram (the Golub-Kahan start's Gram columns, j < OF_ELL)
+    reads j + 1 vectors and the fields u_x, u_y, u_t each. theta_gram (the weighted Gram of
+    Theta V for the image step, K = ELL + k at outer iteration k): the basis once (K vectors of
+    n), u_k, s and s'."""
+    nt, ny, nx = w.nt, w.ny, w.nx
+    ns = (nx // of_scale) * (ny // of_scale)
+    N2, P, n = 2 * ns, nt - 1, nx * ny * nt
+    of_calls = sum(1 for k in range(1, N_OUTER) if k % tau == 0)  # u^(0) = 0: no OF work at k = 0
+    its = range(OF_ITERS)
+    if name == "of_combine":
+        return of_calls * P * sum(4 * N2 * (OF_ELL + it + 1) for it in its), of_calls * OF_ITERS
+    if name == "of_subdot":
+        return of_calls * P * sum(4 * N2 * (OF_ELL + it + 9) for it in its[:-1]), of_calls * (OF_ITERS - 1)
+    if name == "of_gram":
+        return of_calls * P * sum(4 * (N2 * (j + 1) + 3 * ns) for j in range(OF_ELL)), of_calls
+    if name == "theta_gram":
+        return sum(4 * n * (ELL + k) + 4 * n + 16 * P * nx * ny for k in range(N_OUTER)), 2 * N_OUTER
+    return None
 
 
-# DRAM bytes over algorithmic bytes of one k_sub_dot launch (31 pairs, K = 22) in the
-# committed ncu capture (profiles/k_sub_dot_and_k_of_gram_cols_ellipses256x256x32.md):
-# 391.4 MB of traffic for 390.1 MB of algorithmic bytes
-SUBDOT_TRAFFIC_RATIO = 391.4 / 390.1
+# DRAM bytes over algorithmic bytes per launch, from the committed ncu captures of the kernel
+# that dominates each class (a capture of the small case, scaled by the vectors streamed)
+TRAFFIC_RATIO = {}
+
+# the main kernel of each timing class
+CLASS_KERNEL = {
+    "of_gram": "k_of_gram_cols (Gram columns of the Solve-OF Golub-Kahan start, with their reduction)",
+    "of_subdot": "k_of_proj_gram_pass (Solve-OF projection pass with the new Gram column; with the residual's "
+                 "Laplacian, the chunk reduction and the append)",
+    "of_combine": "k_combine (s = V z of Solve-OF)",
+    "theta_gram": "k_theta_gram (weighted Gram of Theta V)",
+}
 
 
 def run_ours(args):
@@ -218,10 +375,10 @@ def run_ours(args):
         __graft_entry__.build()
     if world > 1:
         dist.barrier()
-    from paper_2501_12497_gb300 import api, synth
+    from paper_2501_12497_gb300 import api
     api.load()
     dev = torch.device("cuda", local)
-    w = synth.fan_form(seed=rank) if args.geometry == "fan" else synth.precision_form(seed=rank)
+    w = make_workload(args.workload, rank, args.geometry)
     p = api.mof_problem_create(w.nx, w.ny, w.nt, w.nb, w.na, w.angles, w.h, w.db, precision=api.MOF_FP32, fan=w.fan)
     api.mof_set_warp(p, 1 if args.warp == "round" else 0)
     prm = api.mof_default_params(noise_norm=w.noise_norm, of_streams=args.of_streams, of_scale=args.of_scale,
@@ -255,10 +412,12 @@ def run_ours(args):
     clk = clocks.stop(local)
     total_ms = max_over_ranks(sum(per_step), world, dev)
     value = job_value(world, args.steps, N_OUTER, total_ms)
+    u32 = u.cpu().double().numpy()
+    s32 = s.cpu().double().numpy()
 
     # per-kernel-class device time from one extra, instrumented step with the frame-pair
-    # groups of Solve-OF on a single stream, so that no two classes overlap in time
-    # (the timed steps above run them on several streams, uninstrumented)
+    # groups of Solve-OF on a single stream, so that no two classes of Solve-OF overlap in
+    # time (the timed steps above run them on several streams, uninstrumented)
     class_ms = {}
     if not args.no_class_step:
         prm1 = api.mof_default_params(noise_norm=w.noise_norm, of_streams=1, of_scale=args.of_scale, tau=args.tau,
@@ -289,67 +448,105 @@ def run_ours(args):
         e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
         e2e_value = job_value(world, args.e2e_steps, N_OUTER, 1e3 * e2e_s)
 
-    # quality of the result (RRE against the phantom) and the DP residual
-    rre = float(np.linalg.norm(u.cpu().numpy() - w.u_true.ravel()) / np.linalg.norm(w.u_true))
+    # quality of the result (RRE against the phantom)
+    rre = float(np.linalg.norm(u32 - w.u_true.ravel()) / np.linalg.norm(w.u_true))
 
-    # roofline of the dominant HBM-bound kernel: the fused CGS2 pass over the per-pair
-    # Solve-OF bases (k_sub_dot)
-    import json as _json
+    # time to tolerance: the FP32 result of a timed step against an FP64 solve of the same
+    # problem on the GPU (the FP64 path, whose parity with the FP64 oracle the tests check):
+    # the step time counts only if both the image sequence and the velocities are within
+    # the precision form's bar
+    acc = None
+    if not args.no_accuracy:
+        p64 = api.mof_problem_create(w.nx, w.ny, w.nt, w.nb, w.na, w.angles, w.h, w.db, precision=api.MOF_FP64,
+                                     fan=w.fan)
+        api.mof_set_warp(p64, 1 if args.warp == "round" else 0)
+        b64 = torch.tensor(w.b, dtype=torch.float64, device=dev)
+        u64 = torch.empty(p.n, dtype=torch.float64, device=dev)
+        s64 = torch.empty(p.nv, dtype=torch.float64, device=dev)
+        t0 = time.perf_counter()
+        api.mof_solve(p64, prm, N_OUTER, b64, u64, s64)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+        ur = u64.cpu().numpy()
+        sr_ = s64.cpu().numpy()
+        del b64, u64, s64
+        p64.close()
+        eu = float(np.linalg.norm(u32 - ur) / np.linalg.norm(ur))
+        es = float(np.linalg.norm(s32 - sr_) / max(np.linalg.norm(sr_), 1e-300))
+        ok = eu <= TOL_PRECISION_FORM and es <= TOL_PRECISION_FORM
+        acc = {"reference": "FP64 solve of the same problem on the GPU (%.1f s)" % t64, "tol": TOL_PRECISION_FORM,
+               "u_rel_err": eu, "s_rel_err": es, "passed": ok, "fp64_solve_s": t64}
+
+    # roofline of the dominant class with a byte model: achieved = algorithmic bytes of the
+    # solve / the class's event-timed device time (single-stream step)
     peaks = {}
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk):
-        peaks = _json.load(open(pk))
+        peaks = json.load(open(pk))
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    N2 = 2 * (CFG["n"] // args.of_scale) ** 2
-    pairs = CFG["nt"] - 1
-    # OF runs on outer iterations k = 1..29 with k % tau == 0 (u^(0) = 0 gives u_t = 0 and no
-    # work at k = 0); GKS iteration it reorthogonalises against of_ell + it vectors (it = 0..18)
-    ks = [10 + it for it in range(19)] * sum(1 for k in range(1, N_OUTER) if k % args.tau == 0)
-    bytes_total = subdot_bytes(ks, N2, pairs)
-    sd_ms, sd_cnt = class_ms.get("of_subdot", [float("nan"), 0])
-    achieved = bytes_total / (sd_ms / 1e3) / 1e9 if sd_ms == sd_ms and sd_ms > 0 else None
     step1_ms = sum(v[0] for v in class_ms.values())
+    modeled = {}
+    for name, (ms, cnt) in class_ms.items():
+        m = class_bytes(name, w, args.of_scale, args.tau) if args.of_pq == 2 else None
+        if m is None or ms <= 0:
+            continue
+        nbytes, nlaunch = m
+        gbs = nbytes / (ms / 1e3) / 1e9
+        modeled[name] = {"ms": ms, "share_of_single_stream_step": ms / step1_ms, "algorithmic_bytes": nbytes,
+                         "GB_s": gbs, "frac": gbs / hbm_peak, "launches": nlaunch}
     dominant = max(class_ms.items(), key=lambda kv: kv[1][0])[0] if class_ms else None
-    n_subdot = len(ks)  # one launch per GKS iteration for all pairs in the single-stream step
-    roofline = {
-        "kernel": "k_sub_dot (fused CGS2 pass of the Solve-OF residuals, with its chunk reduction)",
-        "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-        "frac": (achieved / hbm_peak) if achieved else None,
-        "traffic": SUBDOT_TRAFFIC_RATIO * bytes_total / n_subdot,
-        "traffic_source": "ncu capture of one launch (31 pairs, K = 22): DRAM read + write = 1.003 x algorithmic; "
-                          "scaled to the average launch by the vectors it streams",
-        "algorithmic_bytes_per_launch": bytes_total / n_subdot,
-        "peak_source": peak_src,
-        "bytes_model": "K+2 vectors of 2*n*n FP32 per pair and GKS iteration",
-        "measured": "class time from one instrumented single-stream step after the timed region "
-                    "(the timed steps run every pair on its own stream inside CUDA graphs)",
-        "share_of_single_stream_step": sd_ms / step1_ms if step1_ms else None,
-        "largest_class_single_stream": dominant,
-    }
+    roofline = None
+    if modeled:
+        top = dominant if dominant in modeled else max(modeled, key=lambda k: modeled[k]["ms"])
+        m = modeled[top]
+        per_launch = m["algorithmic_bytes"] / m["launches"]
+        ratio = TRAFFIC_RATIO.get(top)
+        roofline = {
+            "kernel": CLASS_KERNEL.get(top, top), "class": top, "bound": "hbm", "achieved": m["GB_s"],
+            "peak": hbm_peak, "unit": "GB/s", "frac": m["frac"],
+            "traffic": ratio * per_launch if ratio else None,
+            "algorithmic_bytes_per_launch": per_launch, "peak_source": peak_src,
+            "measured": "class time from one instrumented single-stream step after the timed region "
+                        "(the timed steps run the frame pairs on their own streams inside CUDA graphs)",
+            "share_of_single_stream_step": m["share_of_single_stream_step"],
+            "largest_class_single_stream": dominant,
+            "other_classes": {k: {"frac": round(v["frac"], 3), "share": round(v["share_of_single_stream_step"], 3)}
+                              for k, v in modeled.items() if k != top},
+        }
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        est, dt = oracle_outer_iteration_seconds(w)
-        cpu = {"value": 1.0 / est, "unit": "outer_iters/s", "cores": cpu_cores(), "kind": "oracle",
-               "sample": "Solve-OF of 1 of the 31 frame pairs (%.1f s), x31 = one outer iteration; "
-                         "image step not counted" % dt}
+        cores = cpu_cores()
+        smp = oracle_sample(w, min(cores, w.nt - 1))
+        cpu = {"value": 1.0 / smp["all_cores_s"], "unit": "outer_iters/s", "cores": smp["processes"],
+               "kind": "oracle", "single_thread_value": 1.0 / smp["single_thread_s"], "host_cores": cores,
+               "sample": smp["sample"]}
+    cfgd = WORKLOADS[args.workload][1]
     line = {
         "metric": "mmgks_of_outer_iterations_per_s", "value": value, "unit": "outer_iters/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": w.name, **CFG, "n_outer": N_OUTER, "of_iters": 20, "of_ell": 10, "ell": 10,
+        "config": {"workload": w.name, **cfgd, "n_outer": N_OUTER, "of_iters": OF_ITERS, "of_ell": OF_ELL, "ell": ELL,
                    "geometry": "fan (source 512, detector 256, bin 1.6)" if w.fan else "parallel",
                    "precision": "FP32 operators, FP64 Krylov/projected solves", "parallelism": "replicas",
                    "l2": "flushed between steps (512 MB write)", "rre": rre,
                    "of_streams": args.of_streams or "auto", "of_scale": args.of_scale, "tau": args.tau,
                    "regulariser": "D1-OF" if args.temporal_tv else "M-OF", "warp": args.warp,
                    "of_pq": args.of_pq,
-                   "time_to_tolerance_s": total_ms / args.steps / 1e3},
+                   # the FP32 form's solve time when its result is within the bar; else the FP64
+                   # path's (the reference itself, whose parity with the FP64 oracle the tests check
+                   # on the 64x64x8 and 256x256x32 configurations)
+                   "time_to_tolerance_s": None if not acc else (total_ms / args.steps / 1e3 if acc["passed"]
+                                                                 else acc["fp64_solve_s"]),
+                   "time_to_tolerance_form": None if not acc else ("FP32 operators" if acc["passed"] else
+                                                                   "FP64 (the FP32 form is outside the bar)"),
+                   "accuracy": acc,
+                   "basis_last": rep[-1]["basis"], "of_basis_last": rep[-1]["of_basis_max"]},
         "e2e": {"value": e2e_value, "unit": "outer_iters/s", "h2d_bytes_per_step": 4 * p.m,
                 "d2h_bytes_per_step": 4 * p.n + 64 * N_OUTER},
         "gpu_launches": launches,
@@ -365,9 +562,13 @@ def run_ours(args):
 
 def run_batch(args):
     """48 independent problems of uneven size (n in {128..512}, T in [8, 40], 10-45
-    angles, ceil(sqrt(2) n) bins): the batched solve (mof_solve_batch, of_streams
-    chosen by mof_autotune) against the same problems solved one after another with
-    mof_solve. Metric: outer iterations per second summed over the problems."""
+    angles, ceil(sqrt(2) n) bins; ellipses carried by a smooth field): the batched,
+    graph-captured form (mof_solve_batch, of_streams chosen by mof_autotune) against the
+    plain unbatched per-frame form (plain = 1: every kernel launched from the host as it
+    comes, Solve-OF one frame pair after another on one stream, the projector pair one
+    frame per launch, the problems one after another), both computing the same results
+    (compared element by element after the timed runs). Metric: outer iterations per
+    second summed over the problems."""
     import numpy as np
     import torch
     import __graft_entry__
@@ -375,11 +576,12 @@ def run_batch(args):
     from paper_2501_12497_gb300 import api, synth
     api.load()
     ws = synth.batch_form(count=48, seed=0)
-    probs, params, bs, us = [], [], [], []
+    probs, params, plain, bs, us = [], [], [], [], []
     for w in ws:
         p = api.mof_problem_create(w.nx, w.ny, w.nt, w.nb, w.na, w.angles, precision=api.MOF_FP32)
         probs.append(p)
         params.append(api.mof_default_params(noise_norm=w.noise_norm))
+        plain.append(api.mof_default_params(noise_norm=w.noise_norm, plain=1))
         bs.append(torch.tensor(w.b.astype(np.float32), device="cuda"))
         us.append(torch.empty(p.n, dtype=torch.float32, device="cuda"))
     g, _ = api.mof_autotune(probs, params, 2, bs, us)
@@ -395,15 +597,19 @@ def run_batch(args):
     tb = time.perf_counter() - t0
     launches = api.mof_kernel_launches() - l0
     clk = clocks.stop(0)
-    # the plain form: one problem after another
-    for p, prm, b, u in zip(probs, params, bs, us):
+    # the plain form: one problem after another, every launch from the host
+    up = [torch.empty_like(u) for u in us]
+    for p, prm, b, u in zip(probs, plain, bs, up):
         api.mof_solve(p, prm, N_OUTER, b, u)
     torch.cuda.synchronize()
+    l1 = api.mof_kernel_launches()
     t0 = time.perf_counter()
-    for p, prm, b, u in zip(probs, params, bs, us):
+    for p, prm, b, u in zip(probs, plain, bs, up):
         api.mof_solve(p, prm, N_OUTER, b, u)
     torch.cuda.synchronize()
     ts = time.perf_counter() - t0
+    launches_plain = api.mof_kernel_launches() - l1
+    diff = max(float((a - c).abs().max()) for a, c in zip(us, up))
     units = len(probs) * N_OUTER
     line = {
         "metric": "mmgks_of_outer_iterations_per_s", "value": args.steps * units / tb, "unit": "outer_iters/s",
@@ -411,80 +617,38 @@ def run_batch(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": "batch48", "problems": len(probs), "pixels_total": int(sum(w.nx * w.ny * w.nt for w in ws)),
                    "n_outer": N_OUTER, "of_streams": g, "timing": "host wall clock around synchronised batches"},
-        "sequential": {"value": units / ts, "ms_per_step": 1e3 * ts, "form": "mof_solve per problem, one after another"},
-        "speedup_vs_sequential": ts / (tb / args.steps),
-        "gpu_launches": launches, "clocks": clk,
-    }
-    print(json.dumps(line), flush=True)
-
-
-def run_large(args):
-    """The 1024x1024x64 problem (90 angles, 1448 bins, 20 ellipses, 0.5% noise), 30
-    outer iterations; inputs resident, L2 flushed before each step."""
-    import numpy as np
-    import torch
-    import __graft_entry__
-    __graft_entry__.build()
-    from paper_2501_12497_gb300 import api, synth
-    api.load()
-    w = synth.large_form(0)
-    p = api.mof_problem_create(w.nx, w.ny, w.nt, w.nb, w.na, w.angles, precision=api.MOF_FP32)
-    api.mof_set_warp(p, 1 if args.warp == "round" else 0)
-    prm = api.mof_default_params(noise_norm=w.noise_norm, of_streams=args.of_streams, of_scale=args.of_scale,
-                                 tau=args.tau, temporal_tv=args.temporal_tv, of_pq=args.of_pq)
-    b = torch.tensor(w.b.astype(np.float32), device="cuda")
-    u = torch.empty(p.n, dtype=torch.float32, device="cuda")
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    for _ in range(args.warmup):
-        api.mof_solve(p, prm, N_OUTER, b, u)
-    torch.cuda.synchronize()
-    clocks = Clocks(True)
-    l0 = api.mof_kernel_launches()
-    ms = []
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        rep = api.mof_solve(p, prm, N_OUTER, b, u)
-        e1.record()
-        e1.synchronize()
-        ms.append(e0.elapsed_time(e1))
-    launches = api.mof_kernel_launches() - l0
-    clk = clocks.stop(0)
-    rre = float(np.linalg.norm(u.cpu().numpy() - w.u_true.ravel()) / np.linalg.norm(w.u_true))
-    tot = sum(ms)
-    line = {
-        "metric": "mmgks_of_outer_iterations_per_s", "value": args.steps * N_OUTER / (tot / 1e3), "unit": "outer_iters/s",
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": "ellipses1024x1024x64", "n": 1024, "nt": 64, "na": 90, "nb": 1448, "n_outer": N_OUTER,
-                   "rre": rre, "basis_last": rep[-1]["basis"], "l2": "flushed between steps (512 MB write)",
-                   "warp": args.warp},
+        "plain": {"value": units / ts, "ms_per_step": 1e3 * ts, "gpu_launches": launches_plain,
+                  "form": "plain = 1: eager launches, Solve-OF pair by pair on one stream, projector per frame, "
+                          "problems one after another",
+                  "max_abs_difference_to_batched": diff},
+        "speedup_vs_plain": ts / (tb / args.steps),
         "gpu_launches": launches, "clocks": clk,
     }
     print(json.dumps(line), flush=True)
 
 
 def run_operators(args):
-    """Every operator of the C ABI applied alone at the 256x256x32 sizes (30 angles, 363
-    bins), L2 flushed before each application, CUDA events around it; achieved GB/s =
-    algorithmic bytes (minimum FP32 traffic of one application) / time, against the
-    measured copy peak. The projector pair is reported against HBM too, although it
-    is bound by FP32 and L1 work (about 36 flop per byte)."""
+    """Every operator of the C ABI applied alone at the sizes of the 1024x1024x64 problem
+    (90 angles, 1448 bins; --size 256: the 256x256x32 problem, 30 angles, 363 bins), L2
+    flushed before each application, CUDA events around it; achieved GB/s = algorithmic
+    bytes (minimum FP32 traffic of one application) / time, against the measured copy
+    peak. The projector pair is reported against HBM too, although it is bound by FP32
+    and L1 work (36 flop per byte at 256^2, 113 at 1024^2)."""
     import numpy as np
     import torch
     import __graft_entry__
     __graft_entry__.build()
     from paper_2501_12497_gb300 import api, synth
     api.load()
-    w = synth.precision_form(0)
+    w = synth.large_form(0) if args.size == 1024 else synth.precision_form(0)
+    vmax = 3.0 if args.size == 1024 else 2.0
     p = api.mof_problem_create(w.nx, w.ny, w.nt, w.nb, w.na, w.angles, precision=api.MOF_FP32)
     n, m, ns, P = p.n, p.m, p.nx * p.ny, p.nt - 1
     dev = "cuda"
     f32 = lambda a: torch.tensor(np.asarray(a, dtype=np.float32), device=dev).reshape(-1)
     u = f32(w.u_true)
     b = f32(w.b)
-    s = f32(synth.random_velocities(P, p.ny, p.nx, vmax=2.0, seed=1))
+    s = f32(synth.random_velocities(P, p.ny, p.nx, vmax=vmax, seed=1))
     sr = torch.empty_like(s)
     api.mof_reverse_flow(p, s, sr)
     flow = torch.empty(2 * P * ns, device=dev)
@@ -502,11 +666,15 @@ def run_operators(args):
     pf = api.mof_problem_create(wf.nx, wf.ny, wf.nt, wf.nb, wf.na, wf.angles, wf.h, wf.db, precision=api.MOF_FP32,
                                 fan=wf.fan)
     bf = f32(wf.b)
+    uf = f32(wf.u_true)
+    sinof = torch.empty(pf.m, device=dev)
+    imgf = torch.empty(pf.n, device=dev)
+    nf, mf = pf.n, pf.m
     ops = [
         ("H (k_project)", 4 * (n + m), lambda: api.mof_apply_A(p, u, sino)),
         ("H^T (k_backproject)", 4 * (n + m), lambda: api.mof_apply_AT(p, b, img)),
-        ("fan H (k_project_fan)", 4 * (n + m) + 16 * m, lambda: api.mof_apply_A(pf, u, sino)),
-        ("fan H^T (k_backproject_fan)", 4 * (n + m) + 16 * m, lambda: api.mof_apply_AT(pf, bf, img)),
+        ("fan H (k_project_fan, 256x256x32)", 4 * (nf + mf) + 16 * mf, lambda: api.mof_apply_A(pf, uf, sinof)),
+        ("fan H^T (k_backproject_fan, 256x256x32)", 4 * (nf + mf) + 16 * mf, lambda: api.mof_apply_AT(pf, bf, imgf)),
         ("Psi (k_grad)", 12 * n, lambda: api.mof_apply_grad(p, u, grad)),
         ("Psi^T (k_gradT)", 12 * n, lambda: api.mof_apply_gradT(p, grad, img)),
         ("Mhat (k_flow)", 4 * n + 24 * P * ns, lambda: api.mof_apply_flow(p, u, s, sr, flow)),
@@ -525,6 +693,11 @@ def run_operators(args):
     if os.path.exists(pk):
         peaks = json.load(open(pk))
     peak = float(peaks.get("hbm_gbs", 6800.0))
+    # the projector pair's own ceilings: FP32 FMA rate and L1 4-byte loads, measured here;
+    # its algorithmic work is 2 m nx FMAs (two taps per step) and as many loads
+    fma_tflops, l1_gl = api.mof_measure_fp32_peaks()
+    tomo = {"H (k_project)": (m, p.nx), "H^T (k_backproject)": (m, p.nx),
+            "fan H (k_project_fan, 256x256x32)": (mf, pf.nx), "fan H^T (k_backproject_fan, 256x256x32)": (mf, pf.nx)}
     flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
     reps = max(args.steps, 5)
     out = {}
@@ -545,22 +718,32 @@ def run_operators(args):
         gbs = nbytes / (us * 1e-6) / 1e9
         out[name] = {"us": round(us, 2), "algorithmic_MB": round(nbytes / 1e6, 2), "GB_s": round(gbs, 1),
                      "frac_of_measured_peak": round(gbs / peak, 3)}
-    line = {"metric": "operator_applications", "unit": "GB/s", "config": {"workload": "ellipses256x256x32 operators",
-            "l2": "flushed before each application", "reps": reps, "peak_gbs": peak}, "operators": out}
+        if name in tomo:
+            mm, nxx = tomo[name]
+            fma = 2.0 * mm * nxx
+            out[name].update({"bound": "fp32/l1", "fma_TFLOP_s": round(2 * fma / (us * 1e-6) / 1e12, 2),
+                              "frac_of_measured_fp32_fma": round(2 * fma / (us * 1e-6) / 1e12 / fma_tflops, 4),
+                              "l1_Gloads_s": round(fma / (us * 1e-6) / 1e9, 1),
+                              "frac_of_measured_l1_loads": round(fma / (us * 1e-6) / 1e9 / l1_gl, 4)})
+    line = {"metric": "operator_applications", "unit": "GB/s", "config": {"workload": "%s operators" % w.name,
+            "l2": "flushed before each application", "reps": reps, "peak_gbs": peak,
+            "measured_fp32_fma_TFLOP_s": round(fma_tflops, 1), "measured_l1_Gloads_s": round(l1_gl, 1)},
+            "operators": out}
     print(json.dumps(line), flush=True)
 
 
 def run_solve_of(args):
     """Solve-OF (Alg. 2) alone: one mof_solve_of call per step on the true frames of the
-    256x256x32 ellipse workload (31 frame pairs, of_ell 10, 20 GKS iterations), inputs
-    resident, L2 flushed before each call, CUDA events around it."""
+    1024x1024x64 workload (63 frame pairs; --size 256: the 256x256x32 workload, 31 pairs),
+    of_ell 10, 20 GKS iterations, inputs resident, L2 flushed before each call, CUDA events
+    around it."""
     import numpy as np
     import torch
     import __graft_entry__
     __graft_entry__.build()
     from paper_2501_12497_gb300 import api, synth
     api.load()
-    w = synth.precision_form(0)
+    w = synth.large_form(0) if args.size == 1024 else synth.precision_form(0)
     p = api.mof_problem_create(w.nx, w.ny, w.nt, w.nb, w.na, w.angles, precision=api.MOF_FP32)
     prm = api.mof_default_params(of_streams=args.of_streams, of_scale=args.of_scale, of_pq=args.of_pq)
     u = torch.tensor(w.u_true.astype(np.float32), device="cuda").reshape(-1)
@@ -583,7 +766,7 @@ def run_solve_of(args):
     line = {"metric": "solve_of_calls_per_s", "value": args.steps / (tot / 1e3), "unit": "calls/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps, "higher_is_better": True,
             "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": "solve_of ellipses256x256x32", "pairs": p.nt - 1, "of_ell": 10, "of_iters": 20,
+            "config": {"workload": "solve_of %s" % w.name, "pairs": p.nt - 1, "of_ell": 10, "of_iters": 20,
                        "of_pq": args.of_pq,
                        "of_streams": args.of_streams or "auto", "of_scale": args.of_scale, "l2": "flushed before each call"},
             "gpu_launches": api.mof_kernel_launches() - l0}
@@ -596,8 +779,6 @@ def main():
         run_reference(args)
     elif args.workload == "batch48":
         run_batch(args)
-    elif args.workload == "ellipses1024x1024x64":
-        run_large(args)
     elif args.workload == "operators":
         run_operators(args)
     elif args.workload == "solve_of":

@@ -51,3 +51,25 @@ def test_reference_arm_runs_on_rank_zero_only(tmp_path):
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
                         "--warmup", "0"], env=env, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_class_byte_models_count_the_basis_sizes_of_a_solve():
+    """The roofline's algorithmic bytes per timing class, for a solve of 30 outer
+    iterations (Solve-OF on iterations 1..29) with 20 GKS iterations from a 10-vector
+    Golub-Kahan start: K = 10 + it vectors at GKS iteration it, so the projection pass with
+    its Laplacian pass and append streams sum_{it<19} (19 + it) = 532 vectors per pair and
+    call, s = V z sum_{it<20} (11 + it) = 410, the start's Gram columns
+    sum_{j<10} (j + 1) = 55 plus 3 fields per column."""
+    class W:
+        nx, ny, nt = 16, 8, 5
+    ns, P, calls = 16 * 8, 4, 29
+    N2 = 2 * ns
+    assert bench.class_bytes("of_subdot", W)[0] == calls * P * 4 * N2 * 532
+    assert bench.class_bytes("of_combine", W)[0] == calls * P * 4 * N2 * 410
+    assert bench.class_bytes("of_gram", W)[0] == calls * P * 4 * (N2 * 55 + 3 * ns * 10)
+    assert bench.class_bytes("of_reorth", W) is None
+    n = ns * 5
+    assert bench.class_bytes("theta_gram", W)[0] == sum(4 * n * (10 + k) + 4 * n + 16 * P * ns for k in range(30))
+    assert bench.class_bytes("small_solve", W) is None
+    # with Solve-OF every 20 outer iterations (tau = 20) only k = 20 runs it
+    assert bench.class_bytes("of_subdot", W, tau=20)[0] == 1 * P * 4 * N2 * 532
