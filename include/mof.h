@@ -184,7 +184,10 @@ mof_status mof_set_warp(mof_problem *p, int mode);
 mof_status mof_apply_flow(mof_problem *p, const void *u, const void *s, const void *sr,
                           void *r, void *stream);
 
-/* u = Mhat(s, s')^T r (exact transpose of mof_apply_flow; deterministic gather). */
+/* u = Mhat(s, s')^T r (exact transpose of mof_apply_flow). Deterministic: the
+ * terms of each output pixel are summed exactly in 64-bit fixed point (scaled per
+ * 64x16 tile by the tile's largest term), then rounded once; a non-finite value
+ * among a tile's terms makes that tile's outputs NaN. */
 mof_status mof_apply_flowT(mof_problem *p, const void *r, const void *s, const void *sr,
                            void *u, void *stream);
 
@@ -243,7 +246,8 @@ mof_status mof_reverse_flow(mof_problem *p, const void *s, void *sr, void *strea
 
 /* y = Theta^T W Theta x with Theta = [Psi; Mhat(s, s')] and IRLS weights
  * W = diag(((Theta uk)^2 + eps^2)^(-1/2)) recomputed from uk (Alg. 1:
- * P^2 with P = diag((nu^2 + eps^2)^(-1/4)), nu = Theta u^(k)). x, uk, y: n. */
+ * P^2 with P = diag((nu^2 + eps^2)^(-1/4)), nu = Theta u^(k)). x, uk, y: n.
+ * The terms of each output pixel are summed as in mof_apply_flowT. */
 mof_status mof_apply_reg_normal(mof_problem *p, const void *x, const void *uk, const void *s,
                                 const void *sr, double eps, void *y, void *stream);
 
@@ -335,20 +339,21 @@ long long mof_kernel_launches(void);
  *
  * Mhat^T r exactly as mof_apply_flowT (same kernels, bit-identical result,
  * Sec. 2.3), but without allocating: mof_apply_flowT takes its scratch (the
- * per-tile bounds of the integer displacements of s and s' that bound the
- * gather transpose's window) from the problem's workspace, which the library
+ * per-tile bounds of the integer displacements of s and s' that tell each
+ * output tile which sources can reach it) from the problem's workspace, which the library
  * allocates on first use; this call takes it from a fixed device array owned
  * by the library, one per device, of MOF_FLOWT_NOALLOC_MAX_INTS ints (16 MiB).
  * It is for callers that cannot allocate device memory at call time: a
  * process running against a fixed device-memory budget, where the first-use
  * allocation could fail with MOF_ENOMEM in the middle of a run, or a
  * latency-critical loop, where cudaMalloc may synchronise the device.
- *  - Size limit: the problem needs 8 (nt-1) ceil(nx/32) ceil(ny/8) ints (four
- *    per 32x8 tile for each of s and s'); a problem needing more than
- *    MOF_FLOWT_NOALLOC_MAX_INTS returns MOF_EUNSUPPORTED and enqueues nothing.
- *  - Initial state: each call resets the part of the array it uses before use
- *    (the bounds are minima and maxima accumulated from an empty range); the
- *    caller initialises nothing.
+ *  - Size limit: the problem needs 8 (nt-1) (ceil(nx/64) ceil(ny/16) + 1) ints
+ *    (four per 64x16 tile and four for the field's reach, for each of s and s');
+ *    a problem needing more than MOF_FLOWT_NOALLOC_MAX_INTS returns
+ *    MOF_EUNSUPPORTED and enqueues nothing.
+ *  - Initial state: each call writes the part of the array it uses before
+ *    reading it (the tile bounds are overwritten, the reach is set to zero
+ *    and then raised); the caller initialises nothing.
  *  - Set-up: the first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress, return code checked: MOF_ECUDA on failure) and
  *    caches it; make that first call before any stream capture begins. Every

@@ -6,21 +6,21 @@
 //   K7  App. C derivative fields u_x, u_y, u_t
 //   K8  Upsilon s + u_t, Upsilon^T r (Sec. 2.2)
 //
-// The transposes of the warp (and the reverse flow) are computed as
-// deterministic gathers: an output pixel q collects the contributions of the
-// sources p within a window around q, in row-major source order, so repeated
-// runs are bit-identical. The window is bounded per 32x8 output tile by the
-// range of the integer displacements of the sources that reach it: every
-// source p records, in each tile its footprint touches, its displacement
-// (x0(p) - px, y0(p) - py) to the first corner of the footprint (integer
-// atomic min and max), so a pixel scans only the sources whose displacement
-// could bring them to it: 2 x 2 positions where the flow is locally constant
-// at the integer level, one more row and column per unit of spread.
+// The transposes of the warp (and the reverse flow) are computed per output tile
+// from the sources that can reach it: every velocity field carries, per source tile,
+// the bounds of its pixels' integer displacements and, for the whole field, the
+// largest reach, so a destination tile visits only the rows and columns of the
+// neighbouring source tiles whose footprints can fall into it (no atomics on
+// global data). Mhat^T and Theta^T W Theta scatter the sources' weighted values into
+// the tile in exact 64-bit fixed point (order independent, so repeated runs are
+// bit-identical); the reverse flow averages the arrivals of each pixel in row-major
+// source order.
 #include "common.cuh"
 
 #include <algorithm>
 
 #include <cfloat>
+#include <climits>
 
 namespace mof {
 
@@ -65,56 +65,109 @@ __device__ __forceinline__ real bilinear(const real *__restrict__ f, int nx, int
     return (1 - wy) * top + wy * bot;
 }
 
-// Weight with which the source pixel (px, py), sampling at r + s(r), reaches
-// the pixel (qx, qy): the transposed bilinear weight.
+// Destination of a source pixel under the reverse flow (remark of Sec. 3), one axis:
+// round half away from zero of x + v, clipped. With v = fv + fr (fv = floor(v), fr in
+// [0,1) exact) and I = x + fv: for I >= 0 the position is >= 0 and rounds up iff
+// fr >= 1/2; for I < 0 it is negative and rounds up (towards zero) iff fr > 1/2. This
+// takes the decision exactly, as an FP64 evaluation of x + v would.
 template <typename real>
-__device__ __forceinline__ real warp_weight_to(int px, int py, real vx, real vy, int nx, int ny, int qx, int qy, int wm) {
-    int x0, x1, y0, y1;
-    real wx, wy;
-    warp_axis(px, vx, nx, x0, x1, wx, wm);
-    warp_axis(py, vy, ny, y0, y1, wy, wm);
-    const real ax = (qx == x0 ? 1 - wx : (real)0) + (qx == x1 ? wx : (real)0);
-    const real ay = (qy == y0 ? 1 - wy : (real)0) + (qy == y1 ? wy : (real)0);
-    return ax * ay;
+__device__ __forceinline__ int round_axis(int x, real v, int n) {
+    const real vc = v > (real)16777216 ? (real)16777216 : (v < (real)-16777216 ? (real)-16777216 : v);
+    const real fv = floor(vc);
+    const real fr = vc - fv;
+    int I = x + (int)fv;
+    if (I >= 0) I += (fr >= (real)0.5) ? 1 : 0;
+    else I += (fr > (real)0.5) ? 1 : 0;
+    if (!(v == v)) I = x;
+    return I < 0 ? 0 : (I > n - 1 ? n - 1 : I);
 }
 
-// Per-tile bounds of the integer displacements of the sources that reach a tile:
-// {dxmin, dxmax, dymin, dymax}; an empty tile keeps (BND_EMPTY, -BND_EMPTY, ...),
-// whose window is empty.
-constexpr int BND_EMPTY = 1 << 29;
+// ---------------------------------------------------------------- tiles of the transposes
+// The warp transposes (Mhat^T, the flow part of Theta^T W Theta) and the reverse flow
+// work on BW x BH pixel tiles, one CTA of BT threads per tile (BPT pixels per thread).
+// For every velocity field the source tiles carry the bounds of the integer
+// displacements of their pixels (x0(p) - px, y0(p) - py: the first pixel of the
+// footprint, or the destination), and the field carries its reach: the largest
+// distance between a source and any pixel of its footprint. A destination tile then
+// finds every source that can reach it among the source tiles within the reach, each
+// restricted to the rows and columns its own bounds allow.
+constexpr int BW = 64, BH = 16, BT = 256, BPT = BW * BH / BT;
 
-// Compensated sum of the terms of one output pixel of a transpose: in FP32 each term's
-// rounding error is kept (DFAcc::add), so the result does not lose the digits that the
-// cancellation between the terms of Mhat^T and Psi^T would otherwise cost; FP64 sums plainly.
-template <typename real> struct CAcc;
-template <> struct CAcc<float> {
-    DFAcc a;
-    __device__ __forceinline__ void add(float x) { a.add(x); }
-    __device__ __forceinline__ double value() const { return a.value(); }
-};
-template <> struct CAcc<double> {
-    double s = 0.0;
-    __device__ __forceinline__ void add(double x) { s += x; }
-    __device__ __forceinline__ double value() const { return s; }
-};
-
-// acc -= (M(v)^T r)(q), by a gather over the sources p whose footprint can contain q:
-// px in [qx - 1 - dxmax, qx - dxmin] (x1(p) is x0(p) or x0(p) + 1), likewise py, in
-// row-major source order.
-template <typename real>
-__device__ __forceinline__ void warpT_gather_sub(CAcc<real> &acc, const real *__restrict__ r, const real *__restrict__ vx,
-                                                 const real *__restrict__ vy, int nx, int ny, int qx, int qy, int4 bd,
-                                                 int wm) {
-    const int ylo = max(0, qy - 1 - bd.w), yhi = min(ny - 1, qy - bd.z);
-    const int xlo = max(0, qx - 1 - bd.y), xhi = min(nx - 1, qx - bd.x);
-    for (int py = ylo; py <= yhi; ++py) {
-        for (int px = xlo; px <= xhi; ++px) {
-            const long long i = (long long)py * nx + px;
-            const real w = warp_weight_to(px, py, ldg(vx + i), ldg(vy + i), nx, ny, qx, qy, wm);
-            if (w != (real)0) acc.add(-(w * ldg(r + i)));
-        }
-    }
+// Exact fixed-point accumulation of the terms of one output pixel: every term is scaled
+// by 2^E, chosen per tile so that the sum of all terms of a pixel stays below 2^62 in
+// magnitude, rounded to an integer and added into a 64-bit integer. Integer addition is
+// associative, so the result is independent of the order in which the terms arrive
+// (deterministic); the roundings are the terms' own (at 2^-E, far below the precision
+// of the inputs) and the final conversion. An FP32 term is rounded with the FP32 adder
+// (the 1.5 * 2^23 magic constant) in three exact 22-bit pieces: conversions between
+// 64-bit integers and floating point run on the FP64 pipe, which this GPU runs at a
+// small fraction of its FP32 rate.
+__device__ __forceinline__ long long fx_term(float x) {  // round(x) for |x| < 2^62
+    const float MAG = 12582912.0f;                      // 1.5 * 2^23
+    const float h2 = (x * 5.684341886080802e-14f + MAG) - MAG;  // round(x / 2^44), |.| < 2^18
+    const float r1 = fmaf(-h2, 17592186044416.0f, x);           // exact, |.| <= 2^43
+    const float h1 = (r1 * 2.384185791015625e-07f + MAG) - MAG; // round(r1 / 2^22), |.| <= 2^21
+    const float r0 = fmaf(-h1, 4194304.0f, r1);                 // exact, |.| <= 2^21
+    const long long a = __float_as_int(h2 + MAG) - 0x4B400000, b = __float_as_int(h1 + MAG) - 0x4B400000;
+    const long long c = __float_as_int(r0 + MAG) - 0x4B400000;
+    return (a << 44) + (b << 22) + c;
 }
+__device__ __forceinline__ long long fx_term(double x) { return __double2ll_rn(x); }
+// 2^E as the element type (E within the normal range of the type)
+__device__ __forceinline__ void fx_pow2(int E, float &sc) { sc = __int_as_float((E + 127) << 23); }
+__device__ __forceinline__ void fx_pow2(int E, double &sc) { sc = __longlong_as_double((long long)(E + 1023) << 52); }
+// tot * 2^-E * f. FP32: the integer in three 22-bit pieces, each turned into a float by the
+// magic constant (exact), combined by two FMAs (within an ulp), then two exact power-of-two
+// factors and f; FP64 directly.
+__device__ __forceinline__ float fx_out(long long tot, int E, float f) {
+    const unsigned long long u = (unsigned long long)tot;
+    const int c = (int)(u & 0x3fffffull), b = (int)((u >> 22) & 0x3fffffull);
+    const int a = (int)(tot >> 44);  // signed, |a| < 2^19
+    const float MAG = 12582912.0f;
+    const float fc = __int_as_float(0x4B400000 + c) - MAG, fb = __int_as_float(0x4B400000 + b) - MAG;
+    const float fa = __int_as_float(0x4B400000 + a) - MAG;
+    const float v = fmaf(fa, 17592186044416.0f, fmaf(fb, 4194304.0f, fc));
+    const int e1 = E / 2, e2 = E - E / 2;
+    return v * __int_as_float((127 - e1) << 23) * __int_as_float((127 - e2) << 23) * f;
+}
+__device__ __forceinline__ double fx_out(long long tot, int E, double f) {
+    return (double)tot * __longlong_as_double((long long)(1023 - E) << 52) * f;
+}
+// scale exponent E of a tile whose largest term is below 2^ex and whose pixels receive at
+// most cb terms each
+template <typename real>
+__device__ __forceinline__ int fx_exponent(int ex, long long cb) { return 62 - (64 - __clzll(cb - 1)) - ex; }
+// bit pattern of |v| (ordered like the magnitudes; non-finite values above every finite one)
+__device__ __forceinline__ unsigned long long abs_bits(float v) { return (unsigned long long)(__float_as_uint(v) & 0x7fffffffu); }
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+    return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ bool bits_finite(unsigned long long b, float) { return b < 0x7f800000ull; }
+__device__ __forceinline__ bool bits_finite(unsigned long long b, double) { return b < 0x7ff0000000000000ull; }
+// exponent ex with |v| < 2^ex for the magnitude whose bits are b (b > 0, finite)
+__device__ __forceinline__ int bits_exp(unsigned long long b, float) {
+    int ex = 0;
+    frexpf(__uint_as_float((unsigned)b), &ex);
+    return ex;
+}
+__device__ __forceinline__ int bits_exp(unsigned long long b, double) {
+    int ex = 0;
+    frexp(__longlong_as_double((long long)b), &ex);
+    return ex;
+}
+template <typename real> struct FxLimits;
+template <> struct FxLimits<float> { static constexpr int EMAX = 126, EMIN = -126; };
+template <> struct FxLimits<double> { static constexpr int EMAX = 1000, EMIN = -1000; };
+
+// A rectangle of candidate source pixels of one destination tile: w columns from x0,
+// rows from y0, its pixels numbered from `start` in the tile's flat candidate list;
+// magic = ceil(2^64 / w) turns a pixel's number into its row with one multiply-high.
+struct SrcRect {
+    int x0, y0, w, start;
+    unsigned long long magic;
+    int term, pad_;
+};
+constexpr int MAXR = 64;  // rectangles per round of a destination tile
 
 }  // namespace
 
@@ -270,131 +323,357 @@ mof_status launch_flow(const mof_problem *p, const real *u, const real *s, const
     return MOF_OK;
 }
 
-// Per-tile displacement bounds of M(v)^T for nf velocity fields v[f] (each [2][ny][nx]):
-// bnd[f][tile] = {min, max} of x0(p) - px and of y0(p) - py over the sources p whose
-// bilinear footprint {x0, x1} x {y0, y1} touches the tile (integer atomics: exact and
-// order independent). Launched with the gather tiling; bounds of the block's own tile
-// are reduced in shared memory first.
-__device__ __forceinline__ void bnd_update(int *b, int dx, int dy) {
-    atomicMin(b + 0, dx);
-    atomicMax(b + 1, dx);
-    atomicMin(b + 2, dy);
-    atomicMax(b + 3, dy);
+// ------------------------------------------------------------ K4/K5/K6 source-tile bounds
+int tiles_x(const mof_problem *p) { return (p->nx + BW - 1) / BW; }
+int tiles_count(const mof_problem *p) { return tiles_x(p) * ((p->ny + BH - 1) / BH); }
+// per velocity field: one int4 per source tile, then one int4 {Rx, Ry, 0, 0}, the reach
+long long tile_bound_ints(const mof_problem *p) { return 4LL * (tiles_count(p) + 1); }
+
+// reach of every field to zero (the bounds kernels raise it with integer maxima)
+__global__ void k_zero_reach(int *__restrict__ bnd_a, int *__restrict__ bnd_b, int nf, int tiles) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= 2 * nf) return;
+    int *b = f < nf ? bnd_a : bnd_b;
+    if (!b) return;
+    reinterpret_cast<int4 *>(b)[(long long)(f % nf) * (tiles + 1) + tiles] = make_int4(0, 0, 0, 0);
 }
 
-template <typename real>
-__global__ void k_tile_bounds(const real *__restrict__ v, int nx, int ny, int *__restrict__ bnd, int tiles_x, int tiles, int wm) {
-    __shared__ int own[4];
-    const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, f = blockIdx.z;
-    const int tid = threadIdx.y * TX + threadIdx.x;
-    if (tid == 0) {
-        own[0] = BND_EMPTY; own[1] = -BND_EMPTY; own[2] = BND_EMPTY; own[3] = -BND_EMPTY;
-    }
-    __syncthreads();
-    if (x < nx && y < ny) {
-        const long long ns = (long long)nx * ny, i = (long long)y * nx + x;
-        const real *vf = v + 2LL * f * ns;
-        int x0, x1, y0, y1;
-        real wx, wy;
-        warp_axis(x, vf[i], nx, x0, x1, wx, wm);
-        warp_axis(y, vf[ns + i], ny, y0, y1, wy, wm);
-        const int dx = x0 - x, dy = y0 - y;
-        const int tx0 = x0 / TX, tx1 = x1 / TX, ty0 = y0 / TY, ty1 = y1 / TY;
+// Bounds of one source tile of velocity field f (fields f < nf from va, the next nf
+// from vb): {min, max} over its pixels p of x0(p) - px and y0(p) - py, with x0, y0 the
+// first pixel of the bilinear footprint {x0, x0 or x0 + 1} of M(v) (MODE 0), or the
+// reverse flow's destination (MODE 1, which also stores it in dest). The field's reach
+// max(-min, max + 1) (MODE 0; max(-min, max) in MODE 1) is raised with one integer
+// atomicMax per tile and axis (exact and order independent).
+template <typename real, int MODE>
+__global__ void __launch_bounds__(BT) k_src_bounds(const real *__restrict__ va, const real *__restrict__ vb, int nf, int nx,
+                                                   int ny, int wm, int *__restrict__ bnd_a, int *__restrict__ bnd_b, int tiles_x,
+                                                   int tiles, int *__restrict__ dest) {
+    const int fz = blockIdx.z, f = fz % nf;
+    const real *v = fz < nf ? va : vb;
+    int *bnd = fz < nf ? bnd_a : bnd_b;
+    const long long ns = (long long)nx * ny;
+    const real *vx = v + 2LL * f * ns, *vy = vx + ns;
+    int dxmin = INT_MAX, dxmax = INT_MIN, dymin = INT_MAX, dymax = INT_MIN;
 #pragma unroll
-        for (int a = 0; a < 2; ++a) {
-            if (a == 1 && tx1 == tx0) break;
-            const int tx = a ? tx1 : tx0;
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                if (c == 1 && ty1 == ty0) break;
-                const int ty = c ? ty1 : ty0;
-                if (tx == (int)blockIdx.x && ty == (int)blockIdx.y) bnd_update(own, dx, dy);
-                else bnd_update(bnd + 4 * ((long long)f * tiles + ty * tiles_x + tx), dx, dy);
-            }
+    for (int k = 0; k < BPT; ++k) {
+        const int l = threadIdx.x + k * BT;
+        const int x = blockIdx.x * BW + (l % BW), y = blockIdx.y * BH + l / BW;
+        if (x >= nx || y >= ny) continue;
+        const long long i = (long long)y * nx + x;
+        int dx, dy;
+        if (MODE == 0) {
+            int x0, x1, y0, y1;
+            real wx, wy;
+            warp_axis(x, vx[i], nx, x0, x1, wx, wm);
+            warp_axis(y, vy[i], ny, y0, y1, wy, wm);
+            dx = x0 - x;
+            dy = y0 - y;
+        } else {
+            const int qx = round_axis(x, vx[i], nx), qy = round_axis(y, vy[i], ny);
+            dest[(long long)f * ns + i] = qy * nx + qx;
+            dx = qx - x;
+            dy = qy - y;
         }
+        dxmin = min(dxmin, dx);
+        dxmax = max(dxmax, dx);
+        dymin = min(dymin, dy);
+        dymax = max(dymax, dy);
+    }
+    dxmin = __reduce_min_sync(0xffffffffu, dxmin);
+    dxmax = __reduce_max_sync(0xffffffffu, dxmax);
+    dymin = __reduce_min_sync(0xffffffffu, dymin);
+    dymax = __reduce_max_sync(0xffffffffu, dymax);
+    __shared__ int red[BT / 32][4];
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        red[w][0] = dxmin;
+        red[w][1] = dxmax;
+        red[w][2] = dymin;
+        red[w][3] = dymax;
     }
     __syncthreads();
-    if (tid == 0 && own[0] != BND_EMPTY) {
-        int *b = bnd + 4 * ((long long)f * tiles + blockIdx.y * tiles_x + blockIdx.x);
-        bnd_update(b, own[0], own[2]);
-        bnd_update(b, own[1], own[3]);
+    if (threadIdx.x == 0) {
+        for (int j = 1; j < BT / 32; ++j) {
+            dxmin = min(dxmin, red[j][0]);
+            dxmax = max(dxmax, red[j][1]);
+            dymin = min(dymin, red[j][2]);
+            dymax = max(dymax, red[j][3]);
+        }
+        const int tile = blockIdx.y * tiles_x + blockIdx.x;
+        int4 *b4 = reinterpret_cast<int4 *>(bnd) + (long long)f * (tiles + 1);
+        b4[tile] = make_int4(dxmin, dxmax, dymin, dymax);
+        const int ext = MODE == 0 ? 1 : 0;
+        int *reach = reinterpret_cast<int *>(b4 + tiles);
+        atomicMax(reach, max(-dxmin, dxmax + ext));
+        atomicMax(reach + 1, max(-dymin, dymax + ext));
     }
 }
 
-// every tile's bounds to the empty window
-__global__ void k_bounds_empty(int *p, long long ntiles) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ntiles; i += (long long)gridDim.x * blockDim.x)
-        reinterpret_cast<int4 *>(p)[i] = make_int4(BND_EMPTY, -BND_EMPTY, BND_EMPTY, -BND_EMPTY);
-}
-
-__global__ void k_zero_ints(int *p, long long n) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) p[i] = 0;
-}
-
-int tiles_x(const mof_problem *p) { return (p->nx + TX - 1) / TX; }
-int tiles_count(const mof_problem *p) { return tiles_x(p) * ((p->ny + TY - 1) / TY); }
-long long tile_bound_ints(const mof_problem *p) { return 4LL * tiles_count(p); }
-
-static int bounds_blocks(long long ntiles) { return (int)std::min<long long>(152 * 4, (ntiles + 255) / 256); }
+inline dim3 grid_tiles(const mof_problem *p, int nz) { return dim3(tiles_x(p), (p->ny + BH - 1) / BH, nz); }
 
 template <typename real>
 mof_status launch_tile_bounds(const mof_problem *p, const real *s, const real *sr, int *bnd_s, int *bnd_sr, cudaStream_t st) {
     const int np = p->nt - 1, tiles = tiles_count(p);
     if (np <= 0) return MOF_OK;
-    ::mof::count_launch(), k_bounds_empty<<<bounds_blocks((long long)np * tiles), 256, 0, st>>>(bnd_s, (long long)np * tiles);
+    ::mof::count_launch(), k_zero_reach<<<(2 * np + 127) / 128, 128, 0, st>>>(bnd_s, sr ? bnd_sr : nullptr, np, tiles);
     MOF_LAUNCH_CHECK();
-    ::mof::count_launch(), k_tile_bounds<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(s, p->nx, p->ny, bnd_s, tiles_x(p), tiles, p->warp_mode);
+    ::mof::count_launch(), k_src_bounds<real, 0><<<grid_tiles(p, sr ? 2 * np : np), BT, 0, st>>>(
+        s, sr, np, p->nx, p->ny, p->warp_mode, bnd_s, bnd_sr, tiles_x(p), tiles, nullptr);
     MOF_LAUNCH_CHECK();
-    if (sr) {
-        ::mof::count_launch(), k_bounds_empty<<<bounds_blocks((long long)np * tiles), 256, 0, st>>>(bnd_sr, (long long)np * tiles);
-        MOF_LAUNCH_CHECK();
-        ::mof::count_launch(), k_tile_bounds<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(sr, p->nx, p->ny, bnd_sr, tiles_x(p), tiles, p->warp_mode);
-        MOF_LAUNCH_CHECK();
-    }
     return MOF_OK;
 }
 
-// u = Mhat^T r (+ optional addend, times scale), one thread per pixel of a frame:
-//   u_t = [t<P] r0_t + [t>0] r1_{t-1} - [t<P] M(sr_t)^T r1_t - [t>0] M(s_{t-1})^T r0_{t-1}
-template <typename real>
-__device__ __forceinline__ void flowT_at(CAcc<real> &v, const real *__restrict__ r, const real *__restrict__ s,
-                                         const real *__restrict__ sr, int nx, int ny, int np, int t, int x, int y,
-                                         const int *__restrict__ bnd_s, const int *__restrict__ bnd_sr, int tiles, int tile,
-                                         int wm) {
-    const long long ns = (long long)nx * ny, i = (long long)y * nx + x;
-    if (t < np) {
-        const real *r1 = r + (np + t) * ns;
-        const real *srp = sr + 2LL * t * ns;
-        v.add(r[t * ns + i]);
-        const int4 bd = __ldg(reinterpret_cast<const int4 *>(bnd_sr) + (long long)t * tiles + tile);
-        warpT_gather_sub(v, r1, srp, srp + ns, nx, ny, x, y, bd, wm);
+// Warp 0 of a destination tile [X0, X1] x [Y0, Y1] appends to rect[] the candidate
+// rectangles of the velocity fields' source tiles, numbered c in [cursor, nc0 + nc1)
+// (the candidate tiles of term 0, then of term 1), until the list is full or the tiles
+// are exhausted; MODE 0 (bilinear footprints) or MODE 1 (single destinations). Writes the
+// number of rectangles and of their pixels and the next cursor to sh[0..2].
+struct TermTiles {
+    const int4 *bnd;  // the field's source-tile bounds (its reach after them)
+    int txa, tya, ntx, nc;
+};
+
+__device__ __forceinline__ TermTiles term_tiles(const int *bnd_f, int tiles, int tiles_xn, int tiles_yn, int X0, int X1, int Y0,
+                                                int Y1, int nx, int ny) {
+    TermTiles T;
+    T.bnd = reinterpret_cast<const int4 *>(bnd_f);
+    const int4 R = __ldg(T.bnd + tiles);
+    const int txa = max(0, X0 - R.x) / BW, txb = min(nx - 1, X1 + R.x) / BW;
+    const int tya = max(0, Y0 - R.y) / BH, tyb = min(ny - 1, Y1 + R.y) / BH;
+    T.txa = txa;
+    T.tya = tya;
+    T.ntx = min(txb, tiles_xn - 1) - txa + 1;
+    T.nc = T.ntx * (min(tyb, tiles_yn - 1) - tya + 1);
+    return T;
+}
+
+template <int MODE>
+__device__ void build_rects(const TermTiles &T0, const TermTiles &T1, int cursor, int X0, int X1, int Y0, int Y1, int nx,
+                            int ny, SrcRect *rect, int *sh) {
+    const int lane = threadIdx.x & 31;
+    const int total = T0.nc + T1.nc, ext = MODE == 0 ? 1 : 0;
+    int cnt = 0, npx = 0;
+    while (cursor < total && cnt <= MAXR - 32) {
+        const int c = cursor + lane;
+        bool valid = false;
+        int rx0 = 0, ry0 = 0, w = 0, h = 0, term = 0;
+        if (c < total) {
+            term = c < T0.nc ? 0 : 1;
+            const TermTiles &T = term ? T1 : T0;
+            const int j = term ? c - T0.nc : c;
+            const int tx = T.txa + j % T.ntx, ty = T.tya + j / T.ntx;
+            const int4 b = __ldg(T.bnd + ty * ((nx + BW - 1) / BW) + tx);
+            const int S0 = tx * BW, S1 = min(S0 + BW - 1, nx - 1), R0 = ty * BH, R1 = min(R0 + BH - 1, ny - 1);
+            rx0 = max(S0, X0 - ext - b.y);
+            const int rx1 = min(S1, X1 - b.x);
+            ry0 = max(R0, Y0 - ext - b.w);
+            const int ry1 = min(R1, Y1 - b.z);
+            w = rx1 - rx0 + 1;
+            h = ry1 - ry0 + 1;
+            valid = w > 0 && h > 0;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, valid);
+        const int mine = valid ? w * h : 0;
+        int incl = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (valid) {
+            SrcRect &R = rect[cnt + __popc(m & ((1u << lane) - 1u))];
+            R.x0 = rx0;
+            R.y0 = ry0;
+            R.w = w;
+            R.start = npx + incl - mine;
+            R.magic = w > 1 ? (~0ull) / (unsigned long long)w + 1ull : 0ull;
+            R.term = term;
+        }
+        cnt += __popc(m);
+        npx += __shfl_sync(0xffffffffu, incl, 31);
+        cursor += 32;
     }
-    if (t > 0) {
-        const real *r0 = r + (long long)(t - 1) * ns;
-        const real *sp = s + 2LL * (t - 1) * ns;
-        v.add(r[(np + t - 1) * ns + i]);
-        const int4 bd = __ldg(reinterpret_cast<const int4 *>(bnd_s) + (long long)(t - 1) * tiles + tile);
-        warpT_gather_sub(v, r0, sp, sp + ns, nx, ny, x, y, bd, wm);
+    if (lane == 0) {
+        sh[0] = cnt;
+        sh[1] = npx;
+        sh[2] = cursor;
     }
 }
 
-template <typename real>
-__global__ void k_flowT(const real *__restrict__ r, const real *__restrict__ s, const real *__restrict__ sr,
-                        const int *__restrict__ bnd_s, const int *__restrict__ bnd_sr, real *__restrict__ u, int nx, int ny,
-                        int np, int tiles, int wm) {
-    const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, t = blockIdx.z;
-    if (x >= nx || y >= ny) return;
-    const int tile = blockIdx.y * gridDim.x + blockIdx.x;
-    CAcc<real> v;
-    flowT_at(v, r, s, sr, nx, ny, np, t, x, y, bnd_s, bnd_sr, tiles, tile, wm);
-    u[(long long)t * nx * ny + (long long)y * nx + x] = (real)v.value();
+// pixel number k of the current round -> (term, px, py); r is the caller's running rectangle
+// index (k only grows within a thread, so the search resumes where it stopped)
+__device__ __forceinline__ void rect_pixel(const SrcRect *rect, int nrect, int k, int &r, int &term, int &px, int &py) {
+    while (r + 1 < nrect && rect[r + 1].start <= k) ++r;
+    const SrcRect &R = rect[r];
+    const unsigned long long loc = (unsigned long long)(k - R.start);
+    const int row = R.magic ? (int)__umul64hi(loc, R.magic) : (int)loc;
+    px = R.x0 + (int)loc - row * R.w;
+    py = R.y0 + row;
+    term = R.term;
+}
+
+// ------------------------------------------------------------ K4 Mhat^T, K5 Theta^T W Theta
+// One CTA per BW x BH tile D of frame t computes
+//   out_t = [t<P] r0_t + [t>0] r1_{t-1} - [t<P] M(sr_t)^T r1_t - [t>0] M(s_{t-1})^T r0_{t-1}
+// (REGN: r holds the weighted flow rows, plus the weighted differences Psi^T w Psi x and,
+// with `temporal`, L_t^T w_t L_t x, all times scale * lam, plus y_add) as a scatter into
+// the tile: every source p whose bilinear footprint can touch D (the candidate rectangles
+// of the two velocity fields) adds w * r(p) to the pixels of its footprint inside D. The
+// terms are summed exactly in 64-bit fixed point (shared-memory integer atomics), so the
+// result does not depend on the order of the additions. Pass 0 finds the largest term
+// magnitude of the tile (it sets the fixed-point scale), pass 1 scatters. A non-finite
+// term makes the tile's outputs NaN.
+template <typename real, bool REGN>
+__global__ void __launch_bounds__(BT) k_warpT_tile(const real *__restrict__ r, const real *__restrict__ s,
+                                                   const real *__restrict__ sr, const int *__restrict__ bnd_s,
+                                                   const int *__restrict__ bnd_sr, int tiles, int nx, int ny, int np, int wm,
+                                                   const real *__restrict__ x, const real *__restrict__ uk, real eps2,
+                                                   double scale, const double *__restrict__ lam, const real *__restrict__ y_add,
+                                                   int temporal, real *__restrict__ out) {
+    __shared__ long long acc[BW * BH];
+    __shared__ SrcRect rect[MAXR];
+    __shared__ int sh[3];
+    __shared__ unsigned long long s_max;
+    __shared__ long long s_total;
+    __shared__ real s_sc;  // scale * lam, once per block (FP64 kept out of the threads)
+    const int t = blockIdx.z, tid = threadIdx.x;
+    const int X0 = blockIdx.x * BW, Y0 = blockIdx.y * BH;
+    const int X1 = min(X0 + BW - 1, nx - 1), Y1 = min(Y0 + BH - 1, ny - 1);
+    const long long ns = (long long)nx * ny;
+    const int txn = (nx + BW - 1) / BW, tyn = (ny + BH - 1) / BH;
+    // term 0: rows r1 of pair t (sources on frame t+1, velocity sr_t); term 1: rows r0 of
+    // pair t-1 (sources on frame t-1, velocity s_{t-1})
+    TermTiles T0{nullptr, 0, 0, 1, 0}, T1{nullptr, 0, 0, 1, 0};
+    if (t < np) T0 = term_tiles(bnd_sr + 4LL * t * (tiles + 1), tiles, txn, tyn, X0, X1, Y0, Y1, nx, ny);
+    if (t > 0) T1 = term_tiles(bnd_s + 4LL * (t - 1) * (tiles + 1), tiles, txn, tyn, X0, X1, Y0, Y1, nx, ny);
+    const real *val0 = r + (np + t) * ns, *val1 = r + (long long)(t - 1) * ns;
+    const real *v0 = sr + 2LL * t * ns, *v1 = s + 2LL * (t - 1) * ns;
+    for (int l = tid; l < BW * BH; l += BT) acc[l] = 0;
+    if (tid == 0) {
+        s_max = 0;
+        s_total = 0;
+        s_sc = REGN ? (real)(lam ? scale * *lam : scale) : (real)1;
+    }
+
+    // the pixel's own terms: the identity parts of Mhat^T and (REGN) the weighted differences
+    constexpr int NOWN = REGN ? 8 : 2;
+    real own[BPT][NOWN];
+    unsigned long long mb = 0;
+#pragma unroll
+    for (int k = 0; k < BPT; ++k) {
+        const int l = tid + k * BT, xx = X0 + (l % BW), yy = Y0 + l / BW;
+#pragma unroll
+        for (int e = 0; e < NOWN; ++e) own[k][e] = 0;
+        if (xx > X1 || yy > Y1) continue;
+        const long long i = (long long)yy * nx + xx;
+        if (t < np) own[k][0] = r[t * ns + i];
+        if (t > 0) own[k][1] = r[(np + t - 1) * ns + i];
+        if (REGN) {
+            const real *f = x + t * ns, *kk = uk + t * ns;
+            auto wd = [&](const real *fa, const real *ka, long long j, long long step) -> real {
+                const real g = fa[j + step] - fa[j], gk = ka[j + step] - ka[j];
+                return g / sqrt(gk * gk + eps2);
+            };
+            if (xx > 0) own[k][2] = wd(f, kk, i - 1, 1);
+            if (xx < nx - 1) own[k][3] = -wd(f, kk, i, 1);
+            if (yy > 0) own[k][4] = wd(f, kk, i - nx, nx);
+            if (yy < ny - 1) own[k][5] = -wd(f, kk, i, nx);
+            if (temporal) {
+                if (t > 0) own[k][6] = wd(f - ns, kk - ns, i, ns);
+                if (t < np) own[k][7] = -wd(f, kk, i, ns);
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < NOWN; ++e) mb = max(mb, abs_bits(own[k][e]));
+    }
+
+    real sc = 0;
+    int E = 0;
+    bool finite = true;
+    for (int pass = 0; pass < 2; ++pass) {
+        int cursor = 0;
+        do {
+            __syncthreads();  // the previous round's rectangles are consumed
+            if (tid < 32) build_rects<0>(T0, T1, cursor, X0, X1, Y0, Y1, nx, ny, rect, sh);
+            __syncthreads();
+            const int nrect = sh[0], npx = sh[1];
+            cursor = sh[2];
+            if (pass == 0 && tid == 0) s_total += npx;
+            int ri = 0;
+            for (int k = tid; k < npx; k += BT) {
+                int term, px, py;
+                rect_pixel(rect, nrect, k, ri, term, px, py);
+                const long long i = (long long)py * nx + px;
+                const real val = term ? val1[i] : val0[i];
+                if (pass == 0) {
+                    mb = max(mb, abs_bits(val));
+                    continue;
+                }
+                const real *vv = term ? v1 : v0;
+                int x0, x1, y0, y1;
+                real wx, wy;
+                warp_axis(px, vv[i], nx, x0, x1, wx, wm);
+                warp_axis(py, vv[ns + i], ny, y0, y1, wy, wm);
+                // footprint corners with their axis weights (x1 == x0 only where the sample sits
+                // on the last column, with wx = 0: one corner of weight (1 - wx) + wx); the
+                // scaled value times the y weight, then times the x weight
+                const bool xs = x1 == x0, ys = y1 == y0;
+                const real ax0 = xs ? (1 - wx) + wx : 1 - wx, ay0 = ys ? (1 - wy) + wy : 1 - wy;
+                const real vs = -(val * sc);
+#pragma unroll
+                for (int cy = 0; cy < 2; ++cy) {
+                    const int yc = cy ? y1 : y0;
+                    const real ay = cy ? wy : ay0;
+                    if ((cy && ys) || yc < Y0 || yc > Y1 || ay == (real)0) continue;
+                    const real vy = vs * ay;
+#pragma unroll
+                    for (int cx = 0; cx < 2; ++cx) {
+                        const int xc = cx ? x1 : x0;
+                        const real ax = cx ? wx : ax0;
+                        if ((cx && xs) || xc < X0 || xc > X1 || ax == (real)0) continue;
+                        atomicAdd(reinterpret_cast<unsigned long long *>(&acc[(yc - Y0) * BW + (xc - X0)]),
+                                  (unsigned long long)fx_term(vy * ax));
+                    }
+                }
+            }
+        } while (cursor < T0.nc + T1.nc);
+        if (pass == 0) {
+            // the tile's largest magnitude (warp maximum of the 64-bit patterns in two 32-bit
+            // halves, then the CTA maximum) and the fixed-point scale 2^E
+            const unsigned hi = __reduce_max_sync(0xffffffffu, (unsigned)(mb >> 32));
+            const unsigned lo = __reduce_max_sync(0xffffffffu, (unsigned)(mb >> 32) == hi ? (unsigned)mb : 0u);
+            if ((tid & 31) == 0) atomicMax(&s_max, ((unsigned long long)hi << 32) | lo);
+            __syncthreads();
+            const unsigned long long M = s_max;
+            finite = bits_finite(M, real(0));
+            E = fx_exponent<real>(M ? bits_exp(M, real(0)) : 0, 4 * s_total + NOWN + 1);
+            E = min(max(E, FxLimits<real>::EMIN), FxLimits<real>::EMAX);
+            fx_pow2(E, sc);
+            if (!finite) break;
+        }
+    }
+    __syncthreads();
+    const real f_out = s_sc;
+#pragma unroll
+    for (int k = 0; k < BPT; ++k) {
+        const int l = tid + k * BT, xx = X0 + (l % BW), yy = Y0 + l / BW;
+        if (xx > X1 || yy > Y1) continue;
+        const long long o = t * ns + (long long)yy * nx + xx;
+        long long tot = acc[l];
+#pragma unroll
+        for (int e = 0; e < NOWN; ++e) tot += fx_term(own[k][e] * sc);
+        real res = fx_out(tot, E, f_out);
+        if (!finite) res = (real)NAN;
+        out[o] = (REGN && y_add) ? y_add[o] + res : res;
+    }
 }
 
 template <typename real>
 mof_status launch_flowT(const mof_problem *p, const real *r, const real *s, const real *sr, const int *bnd_s,
                         const int *bnd_sr, real *u, cudaStream_t st) {
-    ::mof::count_launch(), k_flowT<real><<<grid2d(p->nx, p->ny, p->nt), dim3(TX, TY), 0, st>>>(r, s, sr, bnd_s, bnd_sr, u, p->nx, p->ny, p->nt - 1,
-                                                                      tiles_count(p), p->warp_mode);
+    ::mof::count_launch(), k_warpT_tile<real, false><<<grid_tiles(p, p->nt), BT, 0, st>>>(
+        r, s, sr, bnd_s, bnd_sr, tiles_count(p), p->nx, p->ny, p->nt - 1, p->warp_mode, nullptr, nullptr, (real)0, 1.0,
+        nullptr, nullptr, 0, u);
     MOF_LAUNCH_CHECK();
     return MOF_OK;
 }
@@ -462,89 +741,111 @@ mof_status launch_flow_ds(const mof_problem *p, const real *u, const real *s, co
 }
 
 // ============================================================ K6 reverse flow
-// Destination of each source pixel, round half away from zero of r + s(r),
-// clipped. With v = fv + fr (fv = floor(v), fr in [0,1) exact) and
-// I = x + fv: for I >= 0 the position is >= 0 and rounds up iff fr >= 1/2;
-// for I < 0 it is negative and rounds up (towards zero) iff fr > 1/2. This
-// takes the decision exactly, as an FP64 evaluation of x + v would.
+// s'(q) = -(mean of s(p) over the sources p with dest(p) = q), dest(p) = round(p + s(p))
+// clipped (k_src_bounds, MODE 1). One CTA per BW x BH destination tile: warp 0 takes the
+// union of the displacement bounds of the source tiles whose destinations can fall into
+// the tile; each pixel then scans the sources of its window in row-major order and sums
+// their velocities in FP64 in that order, so the result is that of a sequential pass over
+// the sources.
 template <typename real>
-__device__ __forceinline__ int round_axis(int x, real v, int n) {
-    const real vc = v > (real)16777216 ? (real)16777216 : (v < (real)-16777216 ? (real)-16777216 : v);
-    const real fv = floor(vc);
-    const real fr = vc - fv;
-    int I = x + (int)fv;
-    if (I >= 0) I += (fr >= (real)0.5) ? 1 : 0;
-    else I += (fr > (real)0.5) ? 1 : 0;
-    if (!(v == v)) I = x;
-    return I < 0 ? 0 : (I > n - 1 ? n - 1 : I);
-}
-
-template <typename real>
-__global__ void k_rev_dest(const real *__restrict__ s, int *__restrict__ dest, int *__restrict__ bnd, int nx, int ny,
-                           int tiles_x, int tiles) {
-    __shared__ int own[4];
-    const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, p = blockIdx.z;
-    const int tid = threadIdx.y * TX + threadIdx.x;
-    if (tid == 0) {
-        own[0] = BND_EMPTY; own[1] = -BND_EMPTY; own[2] = BND_EMPTY; own[3] = -BND_EMPTY;
-    }
-    __syncthreads();
-    if (x < nx && y < ny) {
-        const long long ns = (long long)nx * ny, i = (long long)y * nx + x;
-        const real *sp = s + 2LL * p * ns;
-        const int dx = round_axis(x, sp[i], nx), dy = round_axis(y, sp[ns + i], ny);
-        dest[p * ns + i] = dy * nx + dx;
-        const int tx = dx / TX, ty = dy / TY;
-        if (tx == (int)blockIdx.x && ty == (int)blockIdx.y) bnd_update(own, dx - x, dy - y);
-        else bnd_update(bnd + 4 * ((long long)p * tiles + ty * tiles_x + tx), dx - x, dy - y);
-    }
-    __syncthreads();
-    if (tid == 0 && own[0] != BND_EMPTY) {
-        int *b = bnd + 4 * ((long long)p * tiles + blockIdx.y * tiles_x + blockIdx.x);
-        bnd_update(b, own[0], own[2]);
-        bnd_update(b, own[1], own[3]);
-    }
-}
-
-// s'(q) = -(mean of s(p) over the sources p with dest(p) = q), sources in row-major
-// order within the window px in [qx - dxmax, qx - dxmin], py likewise (the tile's bounds)
-template <typename real>
-__global__ void k_rev_gather(const real *__restrict__ s, const int *__restrict__ dest, const int *__restrict__ bnd,
-                             real *__restrict__ sr, int nx, int ny, int tiles) {
-    const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y, p = blockIdx.z;
-    if (x >= nx || y >= ny) return;
-    const long long ns = (long long)nx * ny, q = (long long)y * nx + x;
-    const real *sx = s + 2LL * p * ns, *sy = sx + ns;
-    const int *dp = dest + p * ns;
-    const int4 bd = __ldg(reinterpret_cast<const int4 *>(bnd) + (long long)p * tiles + blockIdx.y * gridDim.x + blockIdx.x);
-    double ax = 0.0, ay = 0.0;
-    int cnt = 0;
-    // sources in row-major order, as the arrivals are accumulated in order of source
-    const int ylo = max(0, y - bd.w), yhi = min(ny - 1, y - bd.z);
-    const int xlo = max(0, x - bd.y), xhi = min(nx - 1, x - bd.x);
-    for (int py = ylo; py <= yhi; ++py)
-        for (int px = xlo; px <= xhi; ++px) {
-            const long long i = (long long)py * nx + px;
-            if (ldg(dp + i) == (int)q) {
-                ax -= (double)ldg(sx + i);
-                ay -= (double)ldg(sy + i);
-                ++cnt;
+__global__ void __launch_bounds__(BT) k_rev_gather(const real *__restrict__ s, const int *__restrict__ dest,
+                                                   const int *__restrict__ bnd, real *__restrict__ sr, int nx, int ny,
+                                                   int tiles) {
+    __shared__ int4 ub;
+    const int p = blockIdx.z, tid = threadIdx.x;
+    const int X0 = blockIdx.x * BW, Y0 = blockIdx.y * BH;
+    const int X1 = min(X0 + BW - 1, nx - 1), Y1 = min(Y0 + BH - 1, ny - 1);
+    const int txn = (nx + BW - 1) / BW, tyn = (ny + BH - 1) / BH;
+    if (tid < 32) {
+        const TermTiles T = term_tiles(bnd + 4LL * p * (tiles + 1), tiles, txn, tyn, X0, X1, Y0, Y1, nx, ny);
+        int dxmin = INT_MAX, dxmax = INT_MIN, dymin = INT_MAX, dymax = INT_MIN;
+        for (int j = tid; j < T.nc; j += 32) {
+            const int tx = T.txa + j % T.ntx, ty = T.tya + j / T.ntx;
+            const int4 b = __ldg(T.bnd + ty * txn + tx);
+            const int S0 = tx * BW, S1 = min(S0 + BW - 1, nx - 1), R0 = ty * BH, R1 = min(R0 + BH - 1, ny - 1);
+            // destinations of this source tile lie in [S0 + b.x, S1 + b.y] x [R0 + b.z, R1 + b.w]
+            if (S0 + b.x <= X1 && S1 + b.y >= X0 && R0 + b.z <= Y1 && R1 + b.w >= Y0) {
+                dxmin = min(dxmin, b.x);
+                dxmax = max(dxmax, b.y);
+                dymin = min(dymin, b.z);
+                dymax = max(dymax, b.w);
             }
         }
+        dxmin = __reduce_min_sync(0xffffffffu, dxmin);
+        dxmax = __reduce_max_sync(0xffffffffu, dxmax);
+        dymin = __reduce_min_sync(0xffffffffu, dymin);
+        dymax = __reduce_max_sync(0xffffffffu, dymax);
+        if (tid == 0) ub = make_int4(dxmin, dxmax, dymin, dymax);
+    }
+    __syncthreads();
+    const int4 bd = ub;
+    const long long ns = (long long)nx * ny;
+    const real *sx = s + 2LL * p * ns, *sy = sx + ns;
+    const int *dp = dest + p * ns;
     real *rx = sr + 2LL * p * ns, *ry = rx + ns;
-    rx[q] = cnt ? (real)(ax / cnt) : (real)0;
-    ry[q] = cnt ? (real)(ay / cnt) : (real)0;
+#pragma unroll
+    for (int k = 0; k < BPT; ++k) {
+        const int l = tid + k * BT, x = X0 + (l % BW), y = Y0 + l / BW;
+        if (x > X1 || y > Y1) continue;
+        const long long q = (long long)y * nx + x;
+        // the first two arrivals in the element type, FP64 sums from the third: the mean of
+        // one or two values (x, or (x0 + x1) / 2 with an exact halving) rounds as the FP64
+        // mean does, so FP64 work is left to the pixels where three or more sources collide
+        real a0 = 0, a1 = 0, b0 = 0, b1 = 0;
+        double ax = 0.0, ay = 0.0;
+        int cnt = 0;
+        if (bd.x <= bd.y) {  // some source tile can reach this tile
+            const int ylo = max(0, y - bd.w), yhi = min(ny - 1, y - bd.z);
+            const int xlo = max(0, x - bd.y), xhi = min(nx - 1, x - bd.x);
+            for (int py = ylo; py <= yhi; ++py)
+                for (int px = xlo; px <= xhi; ++px) {
+                    const long long i = (long long)py * nx + px;
+                    if (ldg(dp + i) == (int)q) {
+                        const real vx = ldg(sx + i), vy = ldg(sy + i);
+                        if (cnt == 0) {
+                            a0 = vx;
+                            b0 = vy;
+                        } else if (cnt == 1) {
+                            a1 = vx;
+                            b1 = vy;
+                        } else {
+                            if (cnt == 2) {  // in source order, as a sequential FP64 sum
+                                ax = (double)a0 + (double)a1;
+                                ay = (double)b0 + (double)b1;
+                            }
+                            ax += (double)vx;
+                            ay += (double)vy;
+                        }
+                        ++cnt;
+                    }
+                }
+        }
+        real ox = 0, oy = 0;
+        if (cnt == 1) {
+            ox = -a0;
+            oy = -b0;
+        } else if (cnt == 2) {
+            ox = -((a0 + a1) * (real)0.5);
+            oy = -((b0 + b1) * (real)0.5);
+        } else if (cnt > 2) {
+            ox = (real)(-ax / cnt);
+            oy = (real)(-ay / cnt);
+        }
+        rx[q] = ox;
+        ry[q] = oy;
+    }
 }
 
 template <typename real>
 mof_status launch_reverse_flow(const mof_problem *p, const real *s, int *bnd, int *dest, real *sr, cudaStream_t st) {
     const int np = p->nt - 1, tiles = tiles_count(p);
     if (np <= 0) return MOF_OK;
-    ::mof::count_launch(), k_bounds_empty<<<bounds_blocks((long long)np * tiles), 256, 0, st>>>(bnd, (long long)np * tiles);
+    ::mof::count_launch(), k_zero_reach<<<(np + 127) / 128, 128, 0, st>>>(bnd, nullptr, np, tiles);
     MOF_LAUNCH_CHECK();
-    ::mof::count_launch(), k_rev_dest<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(s, dest, bnd, p->nx, p->ny, tiles_x(p), tiles);
+    ::mof::count_launch(), k_src_bounds<real, 1><<<grid_tiles(p, np), BT, 0, st>>>(s, s, np, p->nx, p->ny, 0, bnd, bnd,
+                                                                                  tiles_x(p), tiles, dest);
     MOF_LAUNCH_CHECK();
-    ::mof::count_launch(), k_rev_gather<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(s, dest, bnd, sr, p->nx, p->ny, tiles);
+    ::mof::count_launch(), k_rev_gather<real><<<grid_tiles(p, np), BT, 0, st>>>(s, dest, bnd, sr, p->nx, p->ny, tiles);
     MOF_LAUNCH_CHECK();
     return MOF_OK;
 }
@@ -707,47 +1008,8 @@ __global__ void k_regn_flow_rows(const real *__restrict__ x, const real *__restr
     q[(np + p) * ns + i] = bx / sqrt(bk * bk + eps2);
 }
 
-// Stage 2: y = y_add + scale * (Psi^T W_Psi Psi x + Mhat^T q).
-template <typename real>
-__global__ void k_regn_apply(const real *__restrict__ x, const real *__restrict__ uk, const real *__restrict__ s,
-                             const real *__restrict__ sr, const real *__restrict__ q, const int *__restrict__ bnd_s,
-                             const int *__restrict__ bnd_sr, int tiles, real eps2, double scale,
-                             const double *__restrict__ lam, const real *__restrict__ y_add, real *__restrict__ y, int nx,
-                             int ny, int np, int temporal, int wm) {
-    const int xx = blockIdx.x * TX + threadIdx.x, yy = blockIdx.y * TY + threadIdx.y, t = blockIdx.z;
-    __shared__ real s_sc;  // scale * lam once per block (FP64 kept out of the threads)
-    if (threadIdx.x == 0 && threadIdx.y == 0) s_sc = (real)(lam ? scale * *lam : scale);
-    __syncthreads();
-    if (xx >= nx || yy >= ny) return;
-    const long long ns = (long long)nx * ny, i = (long long)yy * nx + xx;
-    const real *f = x + t * ns, *k = uk + t * ns;
-    // weighted differences d(i) = w(i) * (f(i+e) - f(i)), w from uk
-    auto wdx = [&](long long j) -> real {
-        const real g = f[j + 1] - f[j], gk = k[j + 1] - k[j];
-        return g / sqrt(gk * gk + eps2);
-    };
-    auto wdy = [&](long long j) -> real {
-        const real g = f[j + nx] - f[j], gk = k[j + nx] - k[j];
-        return g / sqrt(gk * gk + eps2);
-    };
-    CAcc<real> v;
-    if (xx > 0) v.add(wdx(i - 1));
-    if (xx < nx - 1) v.add(-wdx(i));
-    if (yy > 0) v.add(wdy(i - nx));
-    if (yy < ny - 1) v.add(-wdy(i));
-    if (temporal) {  // L_t^T w_t L_t x: the weighted differences to the previous and next frame
-        auto wdt = [&](const real *fa, const real *ka) -> real {
-            const real g = fa[i + ns] - fa[i], gk = ka[i + ns] - ka[i];
-            return g / sqrt(gk * gk + eps2);
-        };
-        if (t > 0) v.add(wdt(f - ns, k - ns));
-        if (t < np) v.add(-wdt(f, k));
-    }
-    if (np > 0) flowT_at(v, q, s, sr, nx, ny, np, t, xx, yy, bnd_s, bnd_sr, tiles, blockIdx.y * gridDim.x + blockIdx.x, wm);
-    const real out = (real)((double)s_sc * v.value());
-    y[t * ns + i] = y_add ? y_add[t * ns + i] + out : out;
-}
-
+// Stage 2: y = y_add + scale * lam * (Psi^T W_Psi Psi x [+ L_t^T W_t L_t x] + Mhat^T q), the
+// transpose scatter of k_warpT_tile with the pixel's weighted differences as own terms.
 template <typename real>
 mof_status launch_reg_normal(const mof_problem *p, int temporal, const real *x, const real *uk, const real *s, const real *sr,
                              const int *bnd_s, const int *bnd_sr, double eps, double scale, const double *lam_dev,
@@ -758,9 +1020,9 @@ mof_status launch_reg_normal(const mof_problem *p, int temporal, const real *x, 
         ::mof::count_launch(), k_regn_flow_rows<real><<<grid2d(p->nx, p->ny, np), dim3(TX, TY), 0, st>>>(x, uk, s, sr, eps2, q, p->nx, p->ny, np, p->warp_mode);
         MOF_LAUNCH_CHECK();
     }
-    ::mof::count_launch(), k_regn_apply<real><<<grid2d(p->nx, p->ny, p->nt), dim3(TX, TY), 0, st>>>(x, uk, s, sr, q, bnd_s, bnd_sr, tiles_count(p),
-                                                                            eps2, scale, lam_dev, y_add, y, p->nx, p->ny, np, temporal,
-                                                                            p->warp_mode);
+    ::mof::count_launch(), k_warpT_tile<real, true><<<grid_tiles(p, p->nt), BT, 0, st>>>(
+        q, s, sr, bnd_s, bnd_sr, tiles_count(p), p->nx, p->ny, np, p->warp_mode, x, uk, eps2, scale, lam_dev, y_add,
+        temporal, y);
     MOF_LAUNCH_CHECK();
     return MOF_OK;
 }

@@ -73,8 +73,9 @@ def test_noalloc_flowT_after_a_larger_problem_used_the_array():
 
 
 def test_noalloc_flowT_rejects_problems_beyond_its_fixed_scratch():
-    # 4096 x 4096 frames: 128 x 512 tiles of 32 x 8 pixels, 8 * 9 * 65536 ints of bounds > 2^22
-    p = _problem(4096, 4096, 10, api.MOF_FP32)
+    # 4096 x 4096 frames, 40 of them: 64 x 256 tiles of 64 x 16 pixels,
+    # 8 * 39 * (16384 + 1) ints of bounds > 2^22
+    p = _problem(4096, 4096, 40, api.MOF_FP32)
     dummy = torch.zeros(16, dtype=torch.float32, device="cuda")
     ptr = ctypes.c_void_p(dummy.data_ptr())
     lib = api.load()
