@@ -1,9 +1,10 @@
 """GPU parity of every operator of the hot path against the FP64 oracle.
 
 Inputs are seeded; the oracle receives exactly the values the GPU received
-(float32 inputs widened to float64). Bars: relative 2-norm error <= 1e-5 for
-the FP32 operators (the per-operator tolerance of the precision form), <= 1e-12
-for the FP64 build, bit-exact for the integer decisions (reverse-flow
+(float32 inputs widened to float64). Bars, on the relative 2-norm error and on the
+element-wise error (largest difference over the largest reference value) alike:
+<= 1e-5 for the FP32 operators (the per-operator tolerance of the precision form),
+<= 1e-12 for the FP64 build, bit-exact for the integer decisions (reverse-flow
 destinations). Sizes span several tiles with ragged tails, the 64x64x8
 workload and full 256x256 frames with 30 angles and 363 bins.
 """
@@ -31,7 +32,13 @@ def _build():
 
 
 def rel(a, b):
-    return np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300)
+    """The larger of the relative 2-norm error and the element-wise error (the largest
+    difference over the largest reference value), so that every bar holds for both."""
+    a, b = np.ravel(a), np.ravel(b)
+    e_norm = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+    e_elem = np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300) if b.size else 0.0
+    print("  errors: norm-wise %.3g element-wise %.3g" % (e_norm, e_elem))
+    return max(e_norm, e_elem)
 
 
 def make(shape, prec, seed=0, h=1.0, db=1.0):
@@ -274,7 +281,7 @@ def test_reg_normal(shape, prec):
     w = 1.0 / np.sqrt(nu * nu + eps * eps)
     want = th.T(w * th(host(x)))
     print("reg_normal %s rel %.3g" % (prec, rel(host(y), want)))
-    assert rel(host(y), want) <= 3 * TOL[prec]
+    assert rel(host(y), want) <= TOL[prec]
 
 
 # ------------------------------------------------ rounding-and-clipping M(s)
@@ -344,7 +351,7 @@ def test_round_warp_reg_normal(prec):
     nu = th(host(uk))
     want = th.T(th(host(x)) / np.sqrt(nu * nu + eps * eps))
     print("reg_normal %s rel %.3g" % (prec, rel(host(y), want)))
-    assert rel(host(y), want) <= 3 * TOL[prec]
+    assert rel(host(y), want) <= TOL[prec]
 
 
 def test_set_warp_rejects_unknown_modes():
