@@ -65,6 +65,8 @@ def parse():
                     default=DEFAULT_WORKLOAD,
                     help="the 1024x1024x64 problem (default), the 256x256x32 problem, 48 uneven problems "
                          "batched, every operator alone, or Solve-OF alone (one call per step)")
+    ap.add_argument("--frames", type=int, default=0,
+                    help="--workload operators: use only the first this many frames of the workload (0: all)")
     ap.add_argument("--size", type=int, default=1024, choices=[256, 1024],
                     help="frame size of --workload operators / solve_of: 1024 (the 1024x1024x64 sizes) or 256")
     ap.add_argument("--of-streams", type=int, default=0,
@@ -357,9 +359,11 @@ def class_bytes(name, w, of_scale=1, tau=1):
     return None
 
 
-# DRAM bytes over algorithmic bytes per launch, from the committed ncu captures of the kernel
-# that dominates each class (a capture of the small case, scaled by the vectors streamed)
-TRAFFIC_RATIO = {}
+# DRAM bytes over algorithmic bytes per launch of the kernel that dominates a class, from an
+# ncu capture of that kernel (k_of_proj_gram_pass: 31 pairs of 256x256 frames at K = 20 and
+# 21, 408.9 MB for 406.3 MB and 425.1 MB for 422.6 MB); the class's traffic per launch is
+# estimated as this ratio times the class's algorithmic bytes per launch
+TRAFFIC_RATIO = {"of_subdot": 1.006}
 
 # the main kernel of each timing class
 CLASS_KERNEL = {
@@ -554,6 +558,9 @@ def run_ours(args):
             "kernel": CLASS_KERNEL.get(top, top), "class": top, "bound": "hbm", "achieved": m["GB_s"],
             "peak": hbm_peak, "unit": "GB/s", "frac": m["frac"],
             "traffic": ratio * per_launch if ratio else None,
+            "traffic_source": ("ncu capture of the main kernel on the 256x256x32 workload: DRAM read + write = "
+                               "%.3f x its algorithmic bytes, applied to the class's bytes per launch" % ratio)
+            if ratio else None,
             "algorithmic_bytes_per_launch": per_launch, "peak_source": peak_src,
             "measured": "class time from one instrumented single-stream step after the timed region "
                         "(the timed steps run the frame pairs on their own streams inside CUDA graphs)",
@@ -695,6 +702,11 @@ def run_operators(args):
     api.load()
     w = synth.large_form(0) if args.size == 1024 else synth.precision_form(0)
     vmax = 3.0 if args.size == 1024 else 2.0
+    if 1 < args.frames < w.nt:  # a shorter sequence of the same frames, angles and data
+        import dataclasses
+        nt, na = args.frames, w.na[:args.frames]
+        w = dataclasses.replace(w, nt=nt, na=na, angles=w.angles[:int(np.sum(na))], u_true=w.u_true[:nt],
+                                b=w.b[:int(np.sum(na)) * w.nb])
     p = api.mof_problem_create(w.nx, w.ny, w.nt, w.nb, w.na, w.angles, precision=api.MOF_FP32)
     n, m, ns, P = p.n, p.m, p.nx * p.ny, p.nt - 1
     dev = "cuda"
