@@ -804,17 +804,22 @@ __global__ void __launch_bounds__(ST, 1) k_small_solve(SmallArgs a) {
         const double lo = lrho - BRACKET_DECADES, hi = lrho + BRACKET_DECADES;
         const double step = (hi - lo) / (GRID_POINTS - 1);
         if (a.rule == MOF_RULE_GCV) {
-            // GCV at every grid point in FP64 (warps over the points) and its first minimum
-            // (ties to the smaller lambda), as the grid search defines it; a scan in lower
-            // precision can pick another of two nearly equal minima
-            for (int gi = wid; gi < GRID_POINTS; gi += NW) {
-                double N, D;
-                lam_terms_nd(S, exp10(lo + gi * step) / rho, N, D);
-                warp_sum2(N, D);
-                if (lane == 0) {
-                    const double v = gcv_value(N, D);
-                    s_grid[gi] = v == v ? v : DBL_MAX;
+            // GCV at every grid point in FP64 and its first minimum (ties to the smaller
+            // lambda), as the grid search defines it; a scan in lower precision can pick another
+            // of two nearly equal minima. One thread per point, its terms summed in order: a
+            // warp's FP64 instruction occupies the pipe as long with one active lane as with 32,
+            // so lanes over points take far fewer FP64 instructions than lanes over the terms
+            // with a reduction (and one exp10 per point instead of one per lane)
+            for (int gi = tid; gi < GRID_POINTS; gi += ST) {
+                const double mu = exp10(lo + gi * step) / rho;
+                double N = 0.0, D = 0.0;
+                for (int i = 0; i < S.K; ++i) {
+                    const double th = S.theta[i], am = 1.0 - th, d = th + mu * am;
+                    const double g = d > 0.0 ? mu * am / d : 1.0;
+                    N += S.c2[i] * g * g;
+                    D += g;
                 }
+                s_grid[gi] = gcv_value(N, D);
             }
             __syncthreads();
             if (wid == 0) {
