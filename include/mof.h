@@ -141,10 +141,14 @@ void mof_problem_destroy(mof_problem *p);
  * mof_apply_AT is its exact transpose (pixel-driven gather). Every other
  * entry point is unchanged. Distances are in the units of pixel_size.
  * Returns MOF_EINVAL unless source_distance exceeds half the frame diagonal
- * plus two pixels and detector_distance >= 0, and MOF_EUNSUPPORTED when
- * (source_distance + detector_distance) / bin_size > 1e5 (the transpose
- * locates a pixel's bins in FP32); holds a ray table of 16 (FP32) or 40
- * (FP64) bytes per data value on the device. */
+ * plus two pixels and detector_distance >= 0, and MOF_EUNSUPPORTED when the
+ * rounding bound of the transpose's FP32 search for a pixel's bins,
+ * 12 u (1 + t)^2 S + 2 u nb bins with u = 2^-24, S = (source_distance +
+ * detector_distance) / bin_size and t = (nb / 2 + 1) / S, exceeds half its
+ * margin of 0.02 bins (S up to about 14000 for a narrow fan, about 7000 when
+ * the detector's half width is 0.4 (source_distance + detector_distance));
+ * holds a ray table of 16 (FP32) or 40 (FP64) bytes per data value on the
+ * device. */
 mof_status mof_problem_create_fan(const mof_geometry *g, double source_distance, double detector_distance,
                                   int precision, mof_problem **out);
 

@@ -254,11 +254,22 @@ mof_status mof_problem_create_fan(const mof_geometry *g, double source_distance,
                     source_distance, half_diag + 2.0 * g->pixel_size);
     if (!(detector_distance >= 0.0) || !std::isfinite(detector_distance))
         return fail(MOF_EINVAL, "detector_distance must be finite and >= 0");
-    // the transpose finds a pixel's bins by central projection in FP32; beyond this ratio its
-    // rounding (about 1.2e-7 (rs + rd) / bin_size bins) would approach the bins' margin
-    if ((source_distance + detector_distance) / g->bin_size > 1e5)
-        return fail(MOF_EUNSUPPORTED, "(source_distance + detector_distance) / bin_size = %g exceeds 1e5",
-                    (source_distance + detector_distance) / g->bin_size);
+    // The transpose finds a pixel's bins from the central projections t = (q . f) / (q . e) of
+    // its segments' end points (q the point seen from the source), scaled by (rs + rd) / bin_size,
+    // in FP32 with a margin of FAN_PAD_BINS. Each of about a dozen roundings (the stored source
+    // offset and directions, the pixel position, the two dot products, the approximate
+    // division) contributes at most the unit roundoff u = 2^-24 relative to
+    // |q| / (q . e) <= 1 + |t|, which the division scales by 1 + |t| again; |t| is at most the
+    // detector's half width over rs + rd, and the bin coordinate's own roundings add 2 u nb. A
+    // geometry whose bound exceeds half the margin is rejected.
+    const double fan_u = std::ldexp(1.0, -24), fan_scale = (source_distance + detector_distance) / g->bin_size;
+    const double fan_tmax = (0.5 * g->nb + 1.0) / fan_scale;
+    const double fan_bound = 12.0 * fan_u * (1.0 + fan_tmax) * (1.0 + fan_tmax) * fan_scale + 2.0 * fan_u * g->nb;
+    if (!(fan_bound <= 0.5 * FAN_PAD_BINS))
+        return fail(MOF_EUNSUPPORTED,
+                    "fan geometry: the FP32 bin search's rounding bound %.3g bins (from (source_distance + "
+                    "detector_distance) / bin_size = %g) exceeds half its margin of %g bins",
+                    fan_bound, fan_scale, FAN_PAD_BINS);
     mof_problem *p = nullptr;
     MOF_TRY(mof_problem_create(g, precision, &p));
     p->fan = 1;

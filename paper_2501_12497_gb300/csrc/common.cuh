@@ -93,6 +93,9 @@ template <> struct FanRay<double> {
 struct FanView {
     float qx0, qy0, ex, ey, fx, fy;
 };
+// Margin, in bins, of the transpose's FP32 search for the bins a pixel can reach (the host
+// rejects geometries whose rounding bound exceeds half of it)
+constexpr double FAN_PAD_BINS = 0.02;
 
 }  // namespace mof
 

@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(BP_TX *BP_TY) k_backproject4(const float *__re
 // is re-evaluated with the forward's own arithmetic. Steps the forward march
 // skips have crossings more than a pixel outside the frame, so they cannot
 // reach a pixel and need no test here.
-constexpr float FAN_PAD = 0.02f;
+constexpr float FAN_PAD = (float)FAN_PAD_BINS;
 
 template <typename real>
 __global__ void __launch_bounds__(BP_TX *BP_TY) k_backproject_fan(const real *__restrict__ b, real *__restrict__ u,
