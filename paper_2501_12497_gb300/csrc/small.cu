@@ -22,9 +22,9 @@
 //      ||R_A z - Q_A^T b||^2 = sum chat_i^2 (1 - f_i)^2 and
 //      trace(I - S) = sum (1 - f_i), with closed-form derivatives in lam;
 //   4. picks lam on the bracket 10^[log10 rho - 12, log10 rho + 12]:
-//      GCV: the minimum of a 200-point log grid (ties to the smaller lam),
-//      scanned in FP32 and decided in FP64 among the five points around the
-//      FP32 minimum, then refined between its two grid neighbours by
+//      GCV: the first minimum of a 200-point log grid (ties to the smaller
+//      lam), every point evaluated in FP64 (one thread per point), then
+//      refined between its two grid neighbours by
 //      safeguarded Newton steps on dG/dlog10(lam) = 0 (FP32 steps, then FP64
 //      steps, which stop after a Newton step below 1e-6 -- the next would be
 //      below ~1e-12 -- or once the derivative is at its rounding level), kept
