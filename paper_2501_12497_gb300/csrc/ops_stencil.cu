@@ -10,8 +10,9 @@
 // from the sources that can reach it: every velocity field carries, per source tile,
 // the bounds of its pixels' integer displacements and, for the whole field, the
 // largest reach, so a destination tile visits only the rows and columns of the
-// neighbouring source tiles whose footprints can fall into it (no atomics on
-// global data). Mhat^T and Theta^T W Theta scatter the sources' weighted values into
+// neighbouring source tiles whose footprints can fall into it (the only global
+// atomics: one integer maximum per source tile for the field's reach). Mhat^T and
+// Theta^T W Theta scatter the sources' weighted values into
 // the tile in exact 64-bit fixed point (order independent, so repeated runs are
 // bit-identical); the reverse flow averages the arrivals of each pixel in row-major
 // source order.
